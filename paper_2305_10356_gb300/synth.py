@@ -1,0 +1,209 @@
+"""Seeded synthetic inputs: stochastic-block-model edge lists and initial feature blocks.
+
+This module only draws inputs. It holds none of the method's arithmetic (no Laplacian, no
+degrees, no deduplication), so both the CUDA path and the FP64 oracle can be fed from it
+without sharing any computation.
+
+The graphs stand in for the IEEE HPEC Graph Challenge stochastic-block-partition graphs that
+Sec. 5 ("Dataset") uses: planted blocks with low/high block overlap and low/high block-size
+variation. Node ids are randomly permuted, so block membership gives no memory locality.
+
+Every generator returns an undirected edge list in which each sampled edge appears once as
+(src, dst). The list may contain self-loops and repeated pairs; removing them is the graph
+builder's job (Eq. (1) defines S as a 0/1 matrix with no self-loops).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+
+def rng_for(seed: int) -> np.random.Generator:
+    """Counter-based generator (Philox) seeded with `seed`."""
+    return np.random.Generator(np.random.Philox(int(seed)))
+
+
+@dataclasses.dataclass
+class EdgeList:
+    n: int
+    src: np.ndarray  # int32 [m]
+    dst: np.ndarray  # int32 [m]
+    w: np.ndarray | None  # float32 [m] or None (binary S)
+    labels: np.ndarray  # int32 [n], planted block of each node
+    n_blocks: int
+
+    @property
+    def m(self) -> int:
+        return int(self.src.shape[0])
+
+
+def block_sizes_uniform(n: int, n_blocks: int, spread: float, rng) -> np.ndarray:
+    """Block sizes drawn uniformly within +-spread of n/n_blocks, rescaled to sum to n."""
+    base = n / n_blocks
+    raw = rng.uniform(base * (1 - spread), base * (1 + spread), size=n_blocks)
+    return _round_to_total(raw, n)
+
+
+def block_sizes_lognormal(n: int, n_blocks: int, sigma: float, rng) -> np.ndarray:
+    """Block sizes with lognormal(0, sigma) spread, rescaled to sum to n (each block >= 2)."""
+    raw = rng.lognormal(0.0, sigma, size=n_blocks)
+    return _round_to_total(raw, n)
+
+
+def _round_to_total(raw: np.ndarray, n: int) -> np.ndarray:
+    sizes = np.maximum(2, np.floor(raw / raw.sum() * n)).astype(np.int64)
+    diff = n - int(sizes.sum())
+    order = np.argsort(-raw)
+    i = 0
+    while diff != 0:
+        j = order[i % len(order)]
+        if diff > 0:
+            sizes[j] += 1
+            diff -= 1
+        elif sizes[j] > 2:
+            sizes[j] -= 1
+            diff += 1
+        i += 1
+    return sizes
+
+
+def truncated_pareto(n: int, gamma: float, cutoff: float, rng) -> np.ndarray:
+    """Samples on [1, cutoff] with density proportional to x^(-gamma) (inverse CDF)."""
+    a = gamma - 1.0
+    u = rng.random(n)
+    return (1.0 - u * (1.0 - cutoff ** (-a))) ** (-1.0 / a)
+
+
+def sbm(n: int, n_blocks: int, mean_degree: float, ratio: float, *, ratio_kind: str = "prob",
+        sizes: str = "uniform", size_param: float = 0.2, gamma: float | None = None,
+        weighted: bool = False, join_isolated: bool = True, seed: int = 0) -> EdgeList:
+    """Stochastic block model (degree-corrected when `gamma` is given).
+
+    ratio_kind="prob": within-block edge probability = ratio x between-block probability.
+    ratio_kind="count": expected within-block edges = ratio x expected between-block edges.
+    sizes="uniform": block sizes within +-size_param of n/n_blocks; "lognormal": sigma=size_param.
+    gamma: node propensities theta ~ Pareto(gamma) truncated at sqrt(n*mean_degree) and
+    normalised to mean 1 inside each block (Karrer-Newman degree correction); endpoints are
+    drawn with probability proportional to theta.
+    weighted: w ~ U(0.5, 1.5) in FP32 per sampled edge.
+    """
+    rng = rng_for(seed)
+    if sizes == "uniform":
+        bs = block_sizes_uniform(n, n_blocks, size_param, rng)
+    elif sizes == "lognormal":
+        bs = block_sizes_lognormal(n, n_blocks, size_param, rng)
+    else:
+        raise ValueError(sizes)
+    off = np.concatenate([[0], np.cumsum(bs)])
+    # propensities in block-position order
+    if gamma is not None:
+        theta = truncated_pareto(n, gamma, math.sqrt(n * mean_degree), rng)
+        for r in range(n_blocks):
+            seg = theta[off[r]:off[r + 1]]
+            seg *= len(seg) / seg.sum()
+    else:
+        theta = np.ones(n)
+    ctheta = np.concatenate([[0.0], np.cumsum(theta)])
+
+    m_total = rng.poisson(n * mean_degree / 2.0)
+    bsf = bs.astype(np.float64)
+    if ratio_kind == "prob":
+        pw = float(np.sum(bsf * (bsf - 1) / 2))
+        pb = float((n * n - np.sum(bsf * bsf)) / 2)
+        frac_in = ratio * pw / (ratio * pw + pb)
+    elif ratio_kind == "count":
+        frac_in = ratio / (ratio + 1.0)
+    else:
+        raise ValueError(ratio_kind)
+    m_in = rng.binomial(m_total, frac_in)
+    m_out = m_total - m_in
+
+    def endpoints(blocks: np.ndarray) -> np.ndarray:
+        lo = ctheta[off[blocks]]
+        hi = ctheta[off[blocks + 1]]
+        u = lo + rng.random(blocks.shape[0]) * (hi - lo)
+        pos = np.searchsorted(ctheta, u, side="right") - 1
+        return np.clip(pos, off[blocks], off[blocks + 1] - 1)
+
+    # within-block edges: block chosen proportional to its number of node pairs
+    wpair = bsf * (bsf - 1) if gamma is None else bsf * bsf
+    cw = np.cumsum(wpair / wpair.sum())
+    rb = np.minimum(np.searchsorted(cw, rng.random(m_in), side="right"), n_blocks - 1)
+    a_in = endpoints(rb)
+    b_in = endpoints(rb)
+    # between-block edges: (r, s), r != s, proportional to n_r * n_s
+    cb = np.cumsum(bsf / bsf.sum())
+    r1 = np.minimum(np.searchsorted(cb, rng.random(m_out), side="right"), n_blocks - 1)
+    r2 = np.minimum(np.searchsorted(cb, rng.random(m_out), side="right"), n_blocks - 1)
+    same = r1 == r2
+    while same.any():
+        r2[same] = np.minimum(np.searchsorted(cb, rng.random(int(same.sum())), side="right"),
+                              n_blocks - 1)
+        same = r1 == r2
+    a_out = endpoints(r1)
+    b_out = endpoints(r2)
+    a = np.concatenate([a_in, a_out])
+    b = np.concatenate([b_in, b_out])
+    block_of_pos = np.repeat(np.arange(n_blocks, dtype=np.int32), bs)
+
+    if join_isolated:
+        touched = np.zeros(n, dtype=bool)
+        nl = a != b
+        touched[a[nl]] = True
+        touched[b[nl]] = True
+        iso = np.nonzero(~touched)[0]
+        if iso.size:
+            other = rng.integers(0, n - 1, size=iso.size)
+            other = other + (other >= iso)  # uniform over nodes != iso
+            a = np.concatenate([a, iso])
+            b = np.concatenate([b, other])
+
+    perm = rng.permutation(n)  # block position -> node id
+    src = perm[a].astype(np.int32)
+    dst = perm[b].astype(np.int32)
+    labels = np.empty(n, dtype=np.int32)
+    labels[perm] = block_of_pos
+    w = None
+    if weighted:
+        w = rng.uniform(0.5, 1.5, size=src.shape[0]).astype(np.float32)
+    return EdgeList(n=n, src=src, dst=dst, w=w, labels=labels, n_blocks=n_blocks)
+
+
+def initial_block(n: int, k: int, seed: int) -> np.ndarray:
+    """X0 with i.i.d. N(0, 1/n) entries, stored in FP32 (row-major n x k)."""
+    rng = rng_for(seed)
+    return (rng.standard_normal((n, k)) / math.sqrt(n)).astype(np.float32)
+
+
+# ---------------------------------------------------------------------------------------------
+# Named workloads. Seeds: 2305*1000 + workload index for the graph, +1 for X0.
+# ---------------------------------------------------------------------------------------------
+
+WORKLOADS = {
+    # tiny SBM: 1,000 nodes, 11 blocks (+-20%), mean degree 20, edge-probability ratio 10:1
+    "sbm_n1000_k11": dict(n=1000, n_blocks=11, mean_degree=20.0, ratio=10.0, ratio_kind="prob",
+                          sizes="uniform", size_param=0.2, gamma=None, idx=1),
+    # DC-SBM: 50,000 nodes, 44 blocks (lognormal sigma 0.5), power-law 2.5, mean 40, 3:1
+    "dcsbm_n50k_k44": dict(n=50_000, n_blocks=44, mean_degree=40.0, ratio=3.0, ratio_kind="count",
+                           sizes="lognormal", size_param=0.5, gamma=2.5, idx=2),
+    # DC-SBM: 2,000,000 nodes, 128 blocks, power-law 2.3, mean 32, 5:1
+    "dcsbm_n2m_k128": dict(n=2_000_000, n_blocks=128, mean_degree=32.0, ratio=5.0,
+                           ratio_kind="count", sizes="uniform", size_param=0.2, gamma=2.3, idx=3),
+    # weighted SBM: 20,000 nodes, 32 blocks (+-20%), mean degree 32, 10:1, w ~ U(0.5, 1.5)
+    "wsbm_n20k_k32": dict(n=20_000, n_blocks=32, mean_degree=32.0, ratio=10.0, ratio_kind="prob",
+                          sizes="uniform", size_param=0.2, gamma=None, weighted=True, idx=5),
+}
+
+
+def workload(name: str, n: int | None = None, seed_offset: int = 0) -> tuple[EdgeList, np.ndarray]:
+    """Edge list and X0 for a named workload; `n` shrinks the node count (same recipe)."""
+    spec = dict(WORKLOADS[name])
+    idx = spec.pop("idx")
+    if n is not None:
+        spec["n"] = n
+    seed = 2305 * 1000 + idx + seed_offset
+    g = sbm(seed=seed, **spec)
+    x0 = initial_block(g.n, g.n_blocks, seed + 1)
+    return g, x0

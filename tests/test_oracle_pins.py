@@ -1,0 +1,453 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix (CPU only).
+
+Each test checks the oracle against something other than itself: brute force on tiny graphs,
+closed-form spectra, finite differences, polynomial interpolation of the defining expression,
+the fixed points stated by Theorems 1-4, published known-answer vectors, or a library routine.
+"""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import ofsc_oracle as o
+from paper_2305_10356_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+METHODS = [o.OFM_F1, o.TRI_F1, o.OFM_F2, o.TRI_F2]
+
+
+def small_graph(n=40, blocks=4, deg=6.0, seed=7, weighted=False):
+    e = synth.sbm(n, blocks, deg, 8.0, seed=seed, weighted=weighted)
+    return o.build_graph(n, e.src, e.dst, e.w), e
+
+
+# ------------------------------------------------------------------------------------------
+# Graph build (Eq. (1)): brute force on tiny edge lists
+# ------------------------------------------------------------------------------------------
+
+def brute_S(n, src, dst, w=None):
+    S = {}
+    for t, (a, b) in enumerate(zip(src, dst)):
+        a, b = int(a), int(b)
+        if a == b:
+            continue
+        val = 1.0 if w is None else float(w[t])
+        for key in ((a, b), (b, a)):
+            if w is None:
+                S[key] = 1.0
+            else:
+                S[key] = S.get(key, 0.0) + val
+    return S
+
+
+@pytest.mark.parametrize("weighted", [False, True])
+def test_graph_build_brute_force(weighted):
+    rng = np.random.default_rng(3)
+    n = 9
+    src = rng.integers(0, n, 40)
+    dst = rng.integers(0, n, 40)
+    src[:3] = dst[:3]  # self-loops
+    src = np.concatenate([src, [2, 5]])
+    dst = np.concatenate([dst, [5, 2]])  # the same pair in both directions
+    w = rng.uniform(0.5, 1.5, src.size).astype(np.float32) if weighted else None
+    g = o.build_graph(n, src, dst, w)
+    S = brute_S(n, src, dst, w)
+    want_rows = [sorted(c for (r, c) in S if r == i) for i in range(n)]
+    got_rows = [list(g.col[g.row_ptr[i]:g.row_ptr[i + 1]]) for i in range(n)]
+    assert got_rows == want_rows
+    if weighted:
+        for i in range(n):
+            for p in range(g.row_ptr[i], g.row_ptr[i + 1]):
+                assert g.val[p] == np.float32(S[(i, int(g.col[p]))])
+    assert g.n_selfloops == int(np.sum(src == dst))
+    for i in range(n):
+        d = sum(float(np.float32(S[(i, c)])) for c in want_rows[i])
+        assert g.deg[i] == d
+        assert g.s[i] == (1.0 / math.sqrt(d) if d > 0 else 0.0)
+    assert g.n_isolated == sum(1 for i in range(n) if not want_rows[i])
+
+
+def test_graph_build_rejects_bad_input():
+    with pytest.raises(ValueError):
+        o.build_graph(3, np.array([0]), np.array([3]))
+    with pytest.raises(ValueError):
+        o.build_graph(3, np.array([0]), np.array([1]), np.array([-1.0], np.float32))
+    with pytest.raises(ValueError):
+        o.build_graph(3, np.array([0]), np.array([1]), np.array([np.nan], np.float32))
+
+
+def test_empty_graph():
+    g = o.build_graph(5, np.zeros(0, np.int32), np.zeros(0, np.int32))
+    assert g.nnz == 0 and g.n_isolated == 5
+    X = np.arange(10.0).reshape(5, 2)
+    np.testing.assert_array_equal(o.apply_A(g, X), -X)  # isolated nodes: L_ii = 1, A_ii = -1
+
+
+# ------------------------------------------------------------------------------------------
+# Spectrum of L (Eq. (1), Sec. 1): closed forms
+# ------------------------------------------------------------------------------------------
+
+def test_cycle_spectrum():
+    n = 12
+    src = np.arange(n)
+    dst = (src + 1) % n
+    g = o.build_graph(n, src, dst)
+    lam = np.linalg.eigvalsh(o.dense_L(g))
+    want = np.sort(1.0 - np.cos(2.0 * np.pi * np.arange(n) / n))
+    np.testing.assert_allclose(lam, want, atol=1e-12)
+    assert abs(lam[-1] - 2.0) < 1e-12  # even cycle is bipartite: largest eigenvalue is 2
+
+
+def test_complete_graph_spectrum():
+    n = 7
+    src, dst = zip(*itertools.combinations(range(n), 2))
+    g = o.build_graph(n, np.array(src), np.array(dst))
+    lam = np.linalg.eigvalsh(o.dense_L(g))
+    np.testing.assert_allclose(lam, [0.0] + [n / (n - 1)] * (n - 1), atol=1e-12)
+
+
+def test_clique_union_null_space():
+    sizes = [3, 4, 5, 2]
+    src, dst, off = [], [], 0
+    for s in sizes:
+        for a, b in itertools.combinations(range(off, off + s), 2):
+            src.append(a)
+            dst.append(b)
+        off += s
+    g = o.build_graph(off, np.array(src), np.array(dst))
+    lam = np.linalg.eigvalsh(o.dense_L(g))
+    assert int(np.sum(np.abs(lam) < 1e-10)) == len(sizes)
+
+
+def test_random_graph_spectrum_bounds_and_kernel():
+    g, _ = small_graph(60, 3, 8.0, seed=11)
+    L = o.dense_L(g)
+    lam, U = np.linalg.eigh(L)
+    assert lam[0] > -1e-12 and lam[-1] < 2.0 + 1e-12
+    assert abs(lam[0]) < 1e-12
+    v = np.sqrt(g.deg)
+    v /= np.linalg.norm(v)
+    assert abs(abs(U[:, 0] @ v) - 1.0) < 1e-10  # eigenvector of 0 is D^1/2 1 (connected)
+    # A = L - 2I shares eigenvectors, eigenvalues in [-2, 0]
+    lamA = np.linalg.eigvalsh(o.dense_A(g))
+    np.testing.assert_allclose(lamA, lam - 2.0, atol=1e-12)
+
+
+def test_apply_A_matches_dense():
+    g, _ = small_graph(30, 3, 5.0, seed=5, weighted=True)
+    X = np.random.default_rng(0).standard_normal((30, 4))
+    np.testing.assert_allclose(o.apply_A(g, X), o.dense_A(g) @ X, atol=1e-13)
+
+
+# ------------------------------------------------------------------------------------------
+# Objectives and gradients (Eqs. (2), (3), (5), (10))
+# ------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("which", [1, 2])
+def test_objective_matches_definition(which):
+    g, _ = small_graph(25, 2, 5.0, seed=2, weighted=(which == 2))
+    X = np.random.default_rng(1).standard_normal((25, 3)) * 0.3
+    A = o.dense_A(g)
+    f = o.objective(which, X, o.apply_A(g, X), o.normA_fro2(g))
+    assert f == pytest.approx(o.objective_dense(which, A, X), rel=1e-12)
+
+
+@pytest.mark.parametrize("which", [1, 2])
+def test_gradient_finite_differences(which):
+    g, _ = small_graph(20, 2, 4.0, seed=4)
+    A = o.dense_A(g)
+    rng = np.random.default_rng(2)
+    X = rng.standard_normal((20, 3)) * 0.4
+    G = o.gradient(which, X, A @ X)
+    h = 1e-5
+    for _ in range(8):
+        D = rng.standard_normal(X.shape)
+        fd = (o.objective_dense(which, A, X + h * D) - o.objective_dense(which, A, X - h * D)) / (2 * h)
+        assert np.sum(G * D) == pytest.approx(fd, rel=1e-7, abs=1e-9)
+
+
+@pytest.mark.parametrize("method", [o.TRI_F1, o.TRI_F2])
+def test_tri_direction_prefix_property(method):
+    """triu makes column j of g depend only on columns 1..j (Eqs. (7), (12))."""
+    g, _ = small_graph(20, 2, 4.0, seed=8)
+    X = np.random.default_rng(3).standard_normal((20, 5))
+    G = o.direction(method, X, o.apply_A(g, X))
+    for i in range(1, 6):
+        Xi = X[:, :i]
+        np.testing.assert_allclose(o.direction(method, Xi, o.apply_A(g, Xi)), G[:, :i], atol=1e-12)
+
+
+def test_ofm_f2_gradient_vanishes_at_eigenvectors():
+    """Sec. 2.2: grad f2(U_k) = 0 while grad f1(U_k) != 0; grad f1(U_k sqrt(-Lam)) = 0."""
+    g, _ = small_graph(30, 3, 6.0, seed=9)
+    A = o.dense_A(g)
+    lam, U = np.linalg.eigh(A)
+    Uk = U[:, :3]
+    assert np.abs(o.gradient(2, Uk, A @ Uk)).max() < 1e-12
+    assert np.abs(o.gradient(1, Uk, A @ Uk)).max() > 1e-2
+    W = Uk * np.sqrt(-lam[:3])[None, :]
+    assert np.abs(o.gradient(1, W, A @ W)).max() < 1e-12
+
+
+# ------------------------------------------------------------------------------------------
+# Line search (Sec. 3.2, Eqs. (15)-(18)): interpolate the defining expression
+# ------------------------------------------------------------------------------------------
+
+def _fit_cubic(fun, scale):
+    al = np.linspace(-2.0, 2.0, 9) * scale
+    vals = np.array([fun(a) for a in al])
+    return np.polyfit(al, vals, 3), al, vals
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_linesearch_coeffs_interpolate(method):
+    g, _ = small_graph(24, 3, 5.0, seed=12, weighted=True)
+    A = o.dense_A(g)
+    rng = np.random.default_rng(5)
+    k = 4
+    X = rng.standard_normal((24, k)) * 0.3
+    V = rng.standard_normal((24, k)) * 0.2
+    coeffs = o.linesearch_coeffs(method, X, V, A @ X, A @ V)
+    if method in (o.OFM_F1, o.OFM_F2):
+        which = o.objective_of(method)
+        scale = 0.25 if which == 1 else 1.0  # Eq. (15) as printed is d/dalpha f1 / 4
+
+        def fun(a):
+            Z = X + a * V
+            return scale * np.sum(V * o.gradient(which, Z, A @ Z))
+
+        fit, _, _ = _fit_cubic(fun, 1.0)
+        np.testing.assert_allclose(coeffs[0], fit, rtol=1e-9, atol=1e-9 * np.abs(fit).max())
+    else:
+        for i in range(1, k + 1):
+            Xi, Vi = X[:, :i], V[:, :i]
+
+            def fun(a):
+                Z = Xi + a * Vi
+                return np.sum(Vi * o.direction(method, Z, A @ Z))
+
+            fit, _, _ = _fit_cubic(fun, 1.0)
+            np.testing.assert_allclose(coeffs[i - 1], fit, rtol=1e-9,
+                                       atol=1e-9 * np.abs(fit).max())
+
+
+def test_cubic_roots_known():
+    for roots in ([1.0, -2.0, 3.5], [0.1, 0.2, 0.3], [-5.0, 1e-3, 7.0]):
+        c = np.poly(roots) * 2.5
+        got = sorted(r for r, _ in o.cubic_real_roots(*c))
+        np.testing.assert_allclose(got, sorted(roots), rtol=1e-10, atol=1e-12)
+    # one real root: (x - 2)(x^2 + x + 1)
+    c = np.polymul([1.0, -2.0], [1.0, 1.0, 1.0])
+    got = o.cubic_real_roots(*c)
+    assert len(got) == 1 and abs(got[0][0] - 2.0) < 1e-12
+    # exact double root: (x - 1)^2 (x + 2) -> simple root -2 chosen by the rule
+    c = np.poly([1.0, 1.0, -2.0])
+    assert o.choose_root(c) == pytest.approx(-2.0)
+    # degenerate leading coefficient: quadratic, linear, all zero
+    assert sorted(r for r, _ in o.cubic_real_roots(0.0, 1.0, -3.0, 2.0)) == pytest.approx([1.0, 2.0])
+    assert o.cubic_real_roots(0.0, 0.0, 2.0, -1.0)[0][0] == pytest.approx(0.5)
+    assert o.choose_root([0.0, 0.0, 0.0, 0.0]) == 0.0
+
+
+def test_cubic_roots_random_vs_numpy():
+    rng = np.random.default_rng(9)
+    for _ in range(300):
+        c = rng.standard_normal(4) * 10.0 ** rng.uniform(-3, 3, 4)
+        got = sorted(r for r, _ in o.cubic_real_roots(*c))
+        ref = np.roots(c)
+        ref = sorted(x.real for x in ref if abs(x.imag) <= 1e-7 * max(1.0, abs(x)))
+        if len(ref) != len(got):
+            continue  # near-double roots: classification is ill-posed
+        for a, b in zip(got, ref):
+            assert abs(np.polyval(c, a)) <= 1e-9 * np.sum(np.abs(c) * np.abs(a) ** np.arange(3, -1, -1)) + 1e-300
+            assert a == pytest.approx(b, rel=1e-6, abs=1e-9)
+
+
+@pytest.mark.parametrize("method", [o.OFM_F1, o.OFM_F2])
+def test_chosen_step_is_global_minimiser_along_line(method):
+    """OFM: the chosen root minimises f(X + alpha V) over alpha (brute-force grid + refine)."""
+    g, _ = small_graph(24, 3, 5.0, seed=13)
+    A = o.dense_A(g)
+    rng = np.random.default_rng(6)
+    which = o.objective_of(method)
+    nA2 = o.normA_fro2(g)
+    for trial in range(6):
+        X = rng.standard_normal((24, 3)) * 0.5
+        V = -o.gradient(which, X, A @ X) * (0.5 if trial % 2 else 1.0)
+        alpha = o.step_sizes(g, method, X, V, A @ X, A @ V, nA2)[0]
+
+        def f(a):
+            return o.objective(which, X + a * V, A @ (X + a * V), nA2)
+
+        span = 4.0 * max(abs(alpha), 1e-3)
+        grid = np.linspace(-span, span, 4001)
+        vals = np.array([f(a) for a in grid])
+        a0 = grid[np.argmin(vals)]
+        # golden-section refinement around the grid minimum
+        lo, hi = a0 - 2 * (grid[1] - grid[0]), a0 + 2 * (grid[1] - grid[0])
+        phi = (math.sqrt(5) - 1) / 2
+        for _ in range(80):
+            m1, m2 = hi - phi * (hi - lo), lo + phi * (hi - lo)
+            if f(m1) < f(m2):
+                hi = m2
+            else:
+                lo = m1
+        assert alpha == pytest.approx(0.5 * (lo + hi), rel=1e-5, abs=1e-9)
+        assert f(alpha) <= min(vals) + 1e-12 * abs(min(vals))
+
+
+def test_tri_root_choice_is_argmin_of_antiderivative():
+    c = np.poly([-1.0, 0.5, 2.0])  # c3 > 0: two local minima of q at -1 and 2
+    q = [o.quartic_antiderivative(c, r) for r in (-1.0, 0.5, 2.0)]
+    want = [-1.0, 0.5, 2.0][int(np.argmin(q))]
+    assert o.choose_root(c) == pytest.approx(want)
+
+
+# ------------------------------------------------------------------------------------------
+# Algorithm 2 converges to the fixed points of Theorems 1-4
+# ------------------------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def thm_case():
+    g, e = small_graph(60, 4, 8.0, seed=39)
+    A = o.dense_A(g)
+    lam, U = np.linalg.eigh(A)
+    k = 4
+    assert lam[k] - lam[k - 1] > 0.05  # gap so the bottom-k space is well defined
+    X0 = synth.initial_block(60, k, 99).astype(np.float64)
+    return g, lam, U, k, X0
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_theorem_fixed_points(thm_case, method):
+    g, lam, U, k, X0 = thm_case
+    res = o.iterate(g, method, X0, tol=1e-11, maxit=3000)
+    assert res.converged, (res.iterations, res.rel_dir_norm)
+    X = res.X
+    Uk = U[:, :k]
+    assert o.subspace_sin(X, Uk) < 1e-8
+    XtX = X.T @ X
+    if method == o.OFM_F1:  # Theorem 1: X = U_k sqrt(-Lam_k) Q
+        np.testing.assert_allclose(np.sort(np.linalg.eigvalsh(XtX)), np.sort(-lam[:k]), atol=1e-9)
+    elif method == o.OFM_F2:  # Theorem 3: X = U_k Q
+        np.testing.assert_allclose(XtX, np.eye(k), atol=1e-9)
+    elif method == o.TRI_F1:  # Theorem 2: X = U_k sqrt(-Lam_k) D
+        for i in range(k):
+            want = U[:, i] * math.sqrt(-lam[i])
+            s = np.sign(X[:, i] @ want)
+            np.testing.assert_allclose(X[:, i], s * want, atol=1e-8)
+    else:  # Theorem 4: X = U_k D
+        for i in range(k):
+            s = np.sign(X[:, i] @ U[:, i])
+            np.testing.assert_allclose(X[:, i], s * U[:, i], atol=1e-8)
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_first_step_is_exact_linesearch_along_minus_g(method):
+    """Algorithm 2: V0 = -G0 and X1 = X0 + V0 diag(alpha) with the Sec. 3.2 step."""
+    g, _ = small_graph(30, 3, 6.0, seed=3)
+    A = o.dense_A(g)
+    X0 = synth.initial_block(30, 3, 5).astype(np.float64)
+    res = o.iterate(g, method, X0, tol=0.0, maxit=1)
+    G0 = o.direction(method, X0, A @ X0)
+    a = res.alphas[0]
+    np.testing.assert_allclose(res.X, X0 - G0 * a[None, :], atol=1e-14)
+    if method in (o.OFM_F1, o.OFM_F2):  # tr(V0^T grad f(X1)) = 0 at an exact line search
+        which = o.objective_of(method)
+        G1 = o.gradient(which, res.X, A @ res.X)
+        assert abs(np.sum(G0 * G1)) < 1e-9 * np.sum(G0 * G0)
+
+
+def test_iterate_stationary_start_and_zero_iterations():
+    g, _ = small_graph(20, 2, 4.0, seed=1)
+    res = o.iterate(g, o.OFM_F1, np.zeros((20, 3)), tol=1e-6, maxit=10)
+    assert res.iterations == 0 and res.converged and np.all(res.X == 0)
+    X0 = synth.initial_block(20, 3, 1)
+    res = o.iterate(g, o.OFM_F1, X0, tol=1e-6, maxit=0)
+    np.testing.assert_array_equal(res.X, X0.astype(np.float64))
+
+
+def test_iterate_node_permutation_equivariance():
+    """Relabelling nodes permutes the rows of every iterate (no index mix-up in Algorithm 2)."""
+    e = synth.sbm(40, 3, 6.0, 8.0, seed=31)
+    g = o.build_graph(40, e.src, e.dst)
+    perm = np.random.default_rng(0).permutation(40)
+    inv = np.argsort(perm)
+    gp = o.build_graph(40, inv[e.src], inv[e.dst])
+    X0 = synth.initial_block(40, 3, 7).astype(np.float64)
+    for method in METHODS:
+        r1 = o.iterate(g, method, X0, 0.0, 6)
+        r2 = o.iterate(gp, method, X0[perm], 0.0, 6)
+        np.testing.assert_allclose(r2.X, r1.X[perm], atol=1e-10)
+
+
+def test_zero_padded_columns_are_inert():
+    """Zero columns appended after the real ones stay zero and change nothing else."""
+    g, _ = small_graph(30, 3, 6.0, seed=6)
+    X0 = synth.initial_block(30, 3, 2).astype(np.float64)
+    Xp = np.concatenate([X0, np.zeros((30, 2))], axis=1)
+    for method in METHODS:
+        a = o.iterate(g, method, X0, 0.0, 8)
+        b = o.iterate(g, method, Xp, 0.0, 8)
+        np.testing.assert_allclose(b.X[:, :3], a.X, atol=1e-12)
+        assert np.all(b.X[:, 3:] == 0.0)
+
+
+# ------------------------------------------------------------------------------------------
+# Algorithm 1 steps 3-4, evaluation metrics, Philox
+# ------------------------------------------------------------------------------------------
+
+def test_row_normalize():
+    X = np.array([[3.0, 4.0], [0.0, 0.0], [1.0, 0.0]])
+    np.testing.assert_allclose(o.row_normalize(X), [[0.6, 0.8], [0.0, 0.0], [1.0, 0.0]])
+
+
+def test_philox_known_answers():
+    with open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) as fh:
+        rows = [line.split() for line in fh if line.strip() and not line.startswith("#")]
+    assert rows
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        assert o.philox4x32_10(v[:4], v[4:6]) == tuple(v[6:])
+
+
+def test_ari_matches_library():
+    sk = pytest.importorskip("sklearn.metrics")
+    rng = np.random.default_rng(4)
+    for _ in range(10):
+        a = rng.integers(0, 5, 200)
+        b = np.where(rng.random(200) < 0.7, a, rng.integers(0, 6, 200))
+        assert o.ari(a, b) == pytest.approx(sk.adjusted_rand_score(a, b), abs=1e-12)
+    assert o.ari(a, a) == 1.0
+
+
+def test_kmeans_blobs_and_fixed_point():
+    rng = np.random.default_rng(8)
+    centers = rng.standard_normal((5, 3)) * 10
+    truth = rng.integers(0, 5, 500)
+    X = centers[truth] + rng.standard_normal((500, 3)) * 0.3
+    lab, inertia = o.kmeans(X, 5, seed=123, n_init=2)
+    assert o.ari(lab, truth) == 1.0
+    mu = np.stack([X[lab == c].mean(axis=0) for c in range(5)])
+    d = ((X[:, None, :] - mu[None]) ** 2).sum(-1)
+    np.testing.assert_array_equal(np.argmin(d, axis=1), lab)  # Lloyd fixed point
+    assert inertia == pytest.approx(d[np.arange(500), lab].sum())
+    lab2, _ = o.kmeans(X, 5, seed=123, n_init=2)
+    np.testing.assert_array_equal(lab, lab2)
+
+
+def test_subspace_sin_known_angle():
+    th = 0.3
+    assert o.subspace_sin(np.array([[1.0], [0.0]]), np.array([[math.cos(th)], [math.sin(th)]])) \
+        == pytest.approx(math.sin(th), rel=1e-12)
+
+
+def test_rayleigh_ritz_on_eigenvectors():
+    g, _ = small_graph(30, 3, 6.0, seed=10)
+    lam, U = np.linalg.eigh(o.dense_L(g))
+    R = np.linalg.qr(np.random.default_rng(1).standard_normal((3, 3)))[0]
+    ritz, rel = o.rayleigh_ritz_relerr(g, U[:, :3] @ R * 2.0)
+    assert rel < 1e-12
+    np.testing.assert_allclose(np.sort(ritz), np.sort(2.0 - lam[:3]), atol=1e-12)

@@ -1,0 +1,354 @@
+#!/usr/bin/env python
+"""OFM iterations/s of the GB300 path on a seeded degree-corrected SBM (2,000,000 nodes, k = 128).
+
+One step = one ofsc_iterate call of 30 updates of Algorithm 2 (the paper's 30 iterations per
+static graph, Sec. 5.3) from the same X0, with the graph and X0 resident in HBM. `value` is
+updates per second over all ranks. `e2e` times the same steps through the public API from
+pinned host buffers (X0 copied in, X copied out every step). The dominant kernel's roofline
+comes from CUDA-event phase timings taken inside the timed steps. `--impl reference` times the
+FP64 CPU oracle on the same workload instead (one update per step).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METHODS = {"ofm_f1": 0, "tri_f1": 1, "ofm_f2": 2, "tri_f2": 3}
+METHOD_LABEL = {"ofm_f1": "OFM-f1", "tri_f1": "TriOFM-f1", "ofm_f2": "OFM-f2", "tri_f2": "TriOFM-f2"}
+FP32_LANES_PER_SM = 128
+NUM_SMS = 152
+SM_MAX_MHZ = 2070.0
+
+
+def load_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return {"hbm_gbs": d["hbm_gbs"], "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def source_digest() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2305_10356_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as fh:
+            h.update(name.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi sampled every 200 ms while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+    def __init__(self, device_id: str):
+        self.device_id = device_id
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.device_id, f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(self.NAMES, parts[3:7]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default="dcsbm_n2m_k128")
+    ap.add_argument("--method", default="ofm_f1", choices=list(METHODS))
+    ap.add_argument("--gather", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--iters", type=int, default=30, help="updates of Algorithm 2 per step")
+    ap.add_argument("--nodes", type=int, default=None, help="shrink the workload (testing only)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup(backend: str):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def workload_config(args) -> dict:
+    from paper_2305_10356_gb300 import synth
+    spec = synth.WORKLOADS[args.workload]
+    n = args.nodes or spec["n"]
+    kind = "degree-corrected SBM" if spec.get("gamma") else "SBM"
+    return {"workload": f"{args.workload}: {kind}, N={n}, k={spec['n_blocks']}, mean degree "
+                        f"{spec['mean_degree']:g}, power-law {spec.get('gamma')}, within:between "
+                        f"{spec['ratio']:g}:1 ({spec['ratio_kind']}), int32 CSR, seeded synthetic",
+            "n": n, "k": spec["n_blocks"], "method": METHOD_LABEL[args.method],
+            "gather": args.gather, "updates_per_step": args.iters,
+            "l2": "inputs larger than L2 (X, state and CSR are each > 129 MB)"}
+
+
+SAMPLE_FRACTION = 5  # the CPU oracle runs on a graph of N / 5 nodes drawn with the same recipe
+
+
+def cpu_oracle_step(og, method, x0):
+    """One oracle update (maxit=1); returns seconds."""
+    from oracle import ofsc_oracle as o
+    t0 = time.perf_counter()
+    o.iterate(og, method, x0, 0.0, 1)
+    return time.perf_counter() - t0
+
+
+def oracle_sample(args):
+    """The bounded CPU sample: the same workload recipe at N / SAMPLE_FRACTION nodes."""
+    from oracle import ofsc_oracle as o
+    from paper_2305_10356_gb300 import synth
+    n_full = args.nodes or synth.WORKLOADS[args.workload]["n"]
+    n_s = max(1000, n_full // SAMPLE_FRACTION)
+    e, x0 = synth.workload(args.workload, n=n_s)
+    return o.build_graph(e.n, e.src, e.dst, e.w), x0, n_s, n_full
+
+
+SAMPLE_TEXT = ("one update of Algorithm 2 (maxit=1) by the FP64 numpy/scipy oracle on a graph of "
+               "N/5 nodes drawn with the same recipe, scaled to the full N (the oracle's cost is "
+               "linear in N and nnz); BLAS on all cores, sparse product single-threaded")
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup("gloo")
+    if rank != 0:
+        return 0
+    og, x0, n_s, n_full = oracle_sample(args)
+    method = METHODS[args.method]
+    for _ in range(args.warmup):
+        cpu_oracle_step(og, method, x0)
+    times = [cpu_oracle_step(og, method, x0) for _ in range(args.steps)]
+    total = sum(times) * n_full / n_s
+    value = args.steps / total
+    cores = os.cpu_count()
+    cfg = workload_config(args)
+    line = {"metric": "OFM iterations/s", "value": value, "unit": "iterations/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": cfg, "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": "iterations/s", "cores": cores, "kind": "oracle",
+                             "sample": SAMPLE_TEXT},
+            "e2e": {"value": value, "unit": "iterations/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def phase_bytes(n: int, kp: int, nnz: int, gather_bytes: int, weighted: bool) -> dict:
+    """Compulsory HBM bytes per launch of each phase (every array touched once)."""
+    row = 4 * n * kp
+    csr = 8 * (n + 1) + 4 * nnz + (4 * nnz if weighted else 0)
+    return {
+        # read X, Y, V, W, G_prev; write X, Y, G and the gather copy Gh
+        "direction": 5 * row + 3 * row + gather_bytes * n * kp,
+        # CSR + D^-1/2 + each gathered row once + read G, V, W; write V, W
+        "spmm": csr + 4 * n + gather_bytes * n * kp + 3 * row + 2 * row,
+        # read X, V, Y, W once
+        "gram": 4 * row,
+    }
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_setup("nccl")
+    torch.cuda.set_device(local)
+    from paper_2305_10356_gb300 import build, ofsc, synth
+    build.build()
+    e, x0 = synth.workload(args.workload, n=args.nodes)
+    method = METHODS[args.method]
+    gather = ofsc.GATHER_BF16 if args.gather == "bf16" else ofsc.GATHER_FP32
+    src, dst = torch.from_numpy(e.src).cuda(), torch.from_numpy(e.dst).cuda()
+    g = ofsc.ofsc_graph_build(e.n, src, dst)
+    info = g.info()
+    del src, dst
+    X0 = torch.from_numpy(x0).cuda()
+    X = torch.empty_like(X0)
+    stream = torch.cuda.current_stream()
+
+    def step(prof=None):
+        X.copy_(X0)
+        return ofsc.ofsc_iterate(g, method, X, 0.0, args.iters, gather=gather, profile=prof)
+
+    for _ in range(args.warmup):
+        step()
+    prof = ofsc.Profile()
+    dev_id = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local if world > 1 else 0]
+    try:
+        dev_id = "GPU-" + str(torch.cuda.get_device_properties(local).uuid).replace("GPU-", "")
+    except Exception:
+        pass
+    sampler = ClockSampler(dev_id)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    launches = 0
+    for _ in range(args.steps):
+        r = step(prof)
+        launches += r.kernel_launches + 1  # + the X0 copy
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    elapsed_ms = t_start.elapsed_time(t_end)
+    if world > 1:
+        t = torch.tensor([elapsed_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.barrier()
+        elapsed_ms = float(t.item())
+    updates = args.iters * args.steps * world
+    value = updates / (elapsed_ms / 1000.0)
+
+    # end to end: pinned host X0 -> device, iterate, device -> pinned host X
+    Xh0 = torch.from_numpy(x0).pin_memory()
+    Xh = torch.empty_like(Xh0).pin_memory()
+    Xd = torch.empty_like(X0)
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    e_start = torch.cuda.Event(enable_timing=True)
+    e_end = torch.cuda.Event(enable_timing=True)
+    e_start.record(stream)
+    for _ in range(args.steps):
+        Xd.copy_(Xh0, non_blocking=True)
+        ofsc.ofsc_iterate(g, method, Xd, 0.0, args.iters, gather=gather)
+        Xh.copy_(Xd, non_blocking=True)
+    e_end.record(stream)
+    torch.cuda.synchronize()
+    e2e_s = max(time.perf_counter() - w0, e_start.elapsed_time(e_end) / 1000.0)
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": updates / e2e_s, "unit": "iterations/s",
+           "h2d_bytes_per_step": int(x0.nbytes), "d2h_bytes_per_step": int(x0.nbytes)}
+
+    # dominant phase and its roofline
+    pd = prof.as_dict()
+    dom = max(pd, key=lambda p: pd[p]["ms"])
+    kp = ((e.n_blocks + 7) // 8) * 8
+    gb = 2 if args.gather == "bf16" else 4
+    peaks = load_peaks()
+    bytes_ = phase_bytes(e.n, kp, int(info.nnz), gb, bool(info.weighted))
+    per_launch_ms = pd[dom]["ms"] / max(1, pd[dom]["launches"])
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        with open(tpath) as fh:
+            tj = json.load(fh)
+        if tj.get("source_digest") == source_digest() and tj.get("workload") == args.workload:
+            traffic = tj.get("bytes_per_launch", {}).get(dom)
+    if dom == "gram":
+        # SIMT FP32 Gram: ALU bound; algorithmic flops = 6 Grams x 2 N k^2
+        flops = 6 * 2.0 * e.n * e.n_blocks ** 2
+        achieved = flops / (per_launch_ms / 1000.0) / 1e12
+        peak = NUM_SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+        roof = {"bound": "alu", "kernel": "k_gram", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                "algorithmic": f"{flops:.4g} flop/launch", "ms_per_launch": per_launch_ms}
+    else:
+        alg = bytes_.get(dom, 0)
+        achieved = alg / (per_launch_ms / 1000.0) / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                "peak_source": peaks["source"], "algorithmic": f"{alg} B/launch",
+                "ms_per_launch": per_launch_ms}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        og, xs, n_s, n_full = oracle_sample(args)
+        secs = cpu_oracle_step(og, method, xs) * n_full / n_s
+        cpu = {"value": 1.0 / secs, "unit": "iterations/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": SAMPLE_TEXT}
+    if rank == 0:
+        line = {"metric": "OFM iterations/s", "value": value, "unit": "iterations/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32" if args.gather == "fp32" else "bf16-gather/f32",
+                "data": "synthetic", "config": workload_config(args), "impl": "gpu",
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "gpu_launches": launches,
+                "phases_ms_per_step": {p: pd[p]["ms"] / args.steps for p in pd},
+                "parallelism": "replicas only" if world > 1 else "single GPU"}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,212 @@
+/*
+ * ofsc.h - C ABI of the GB300 (sm_103a) library for spectral clustering via
+ * orthogonalization-free methods (Pang and Yang, arXiv 2305.10356).
+ *
+ * The calls follow the four steps of Algorithm 1:
+ *   1. ofsc_graph_build     S and D from an edge list; A = L - 2I with L = I - D^-1/2 S D^-1/2 (Eq. (1))
+ *   2. ofsc_iterate         OFM-f1 / TriOFM-f1 / OFM-f2 / TriOFM-f2 by Algorithm 2
+ *      ofsc_objective_grad  f1 (Eq. (2)) or f2 (Eq. (3)) and its gradient (Eq. (5) / Eq. (10))
+ *   3. ofsc_row_normalize   row normalisation of the feature block
+ *   4. ofsc_kmeans          Euclidean K-means on the rows
+ *
+ * Conventions (all calls):
+ *   - Every call returns an ofsc_status. No C++ exception crosses this boundary. On an error
+ *     ofsc_last_error() returns a message for the calling host thread.
+ *   - Array arguments are DEVICE pointers owned by the caller, unless a comment says "host".
+ *     Dense blocks are row-major n x k FP32 with leading dimension k (row l = node l).
+ *     Pointers to FP32 data must be 4-byte aligned; they need not be 16-byte aligned.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream). Work is
+ *     queued on it. A call that returns a host value (f_out, ofsc_result, inertia, counts)
+ *     synchronises that stream before it returns; no call synchronises the whole device.
+ *   - ofsc_graph handles are owned by the library: create with ofsc_graph_build, release with
+ *     ofsc_graph_free. A handle also caches the device workspace of ofsc_iterate and
+ *     ofsc_objective_grad, so calls that share one handle must be ordered by the caller
+ *     (one stream, or explicit events); calls on different handles are independent.
+ *   - The current CUDA device at the time of the call is used; all pointers must live on it.
+ */
+#ifndef OFSC_H
+#define OFSC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t ofsc_status;
+enum {
+  OFSC_OK = 0,
+  OFSC_ERR_INVALID_ARG = 1,   /* bad size, id out of range, bad weight, NULL where required */
+  OFSC_ERR_OOM = 2,           /* device allocation failed */
+  OFSC_ERR_NONFINITE = 3,     /* NaN/Inf met in the input block or in the iteration */
+  OFSC_ERR_TIMEOUT = 4,       /* a bounded device wait ran out */
+  OFSC_ERR_NOT_CONVERGED = 5, /* warning only: maxit reached before tol; the result is valid */
+  OFSC_ERR_CUDA = 6           /* a CUDA runtime call failed (message in ofsc_last_error) */
+};
+
+/* Methods of Sec. 2: gradient of f1 (Eq. (5)), g1 (Eq. (7)), gradient of f2 (Eq. (10)), g2 (Eq. (12)). */
+enum { OFSC_OFM_F1 = 0, OFSC_TRI_F1 = 1, OFSC_OFM_F2 = 2, OFSC_TRI_F2 = 3 };
+/* Objectives: f1 = ||A + XX^T||_F^2 (Eq. (2)), f2 = tr((2I - X^T X) X^T A X) (Eq. (3)). */
+enum { OFSC_F1 = 1, OFSC_F2 = 2 };
+/* Storage of the block gathered by the sparse product: FP32, or BF16 with FP32 accumulation. */
+enum { OFSC_GATHER_FP32 = 0, OFSC_GATHER_BF16 = 1 };
+
+typedef struct ofsc_graph ofsc_graph;
+
+typedef struct {
+  int64_t n;            /* nodes */
+  int64_t m_in;         /* edges in the input list */
+  int64_t nnz;          /* stored entries of S (2 x distinct undirected non-loop pairs) */
+  int64_t n_selfloops;  /* input edges with src == dst (dropped) */
+  int64_t n_duplicates; /* directed entries merged into another (repeated pairs) */
+  int64_t n_isolated;   /* nodes of degree 0 (they get D^-1/2 = 0, so L_ii = 1) */
+  int32_t weighted;     /* 1 if S carries FP32 weights */
+  double normA_fro2;    /* ||A||_F^2 = n + sum_ij (D^-1/2 S D^-1/2)_ij^2, FP64 */
+} ofsc_graph_info;
+
+/*
+ * ofsc_graph_build - S, D and D^-1/2 from an undirected edge list (Eq. (1); Algorithm 1, step 2).
+ *   n        number of nodes (>= 0, < 2^31)
+ *   m        number of input edges (>= 0)
+ *   src,dst  device int32 [m]; edge e joins src[e] and dst[e]; ids must lie in [0, n)
+ *   w        device float32 [m] edge weights (finite, > 0), or NULL for a binary S
+ *   flags    reserved, must be 0
+ *   out      host pointer that receives the new handle
+ * Each input edge {u, v} sets S_uv = S_vu. Self-loops are dropped and counted. A pair listed
+ * more than once (in either direction) is one entry: weight 1 for a binary S; for a weighted S
+ * the listed FP32 weights are summed in FP64 in input order and rounded once to FP32.
+ * D_ii = sum_j S_ij (integer count, or FP64 sum in column order); D^-1/2 = (float)(1/sqrt(D_ii))
+ * in IEEE FP64, and 0 for an isolated node. CSR columns are ascending within each row.
+ * Errors: OFSC_ERR_INVALID_ARG (bad n/m/flags, id out of range, bad weight), OFSC_ERR_OOM.
+ * Synchronises `stream` (the validation result and sizes are read back).
+ */
+ofsc_status ofsc_graph_build(int64_t n, int64_t m, const int32_t* src, const int32_t* dst,
+                             const float* w, uint32_t flags, void* stream, ofsc_graph** out);
+
+/* Releases a handle and its device memory (NULL is allowed). Synchronises the device memory
+ * owned by the handle only after queued work on every stream has finished (cudaFree rules). */
+ofsc_status ofsc_graph_free(ofsc_graph* g);
+
+/* Sizes and counts of a built graph (host struct). */
+ofsc_status ofsc_graph_get_info(const ofsc_graph* g, ofsc_graph_info* info);
+
+/*
+ * ofsc_graph_csr - device pointers into the handle's CSR (owned by the handle, valid until
+ * ofsc_graph_free): row_ptr int64 [n+1], col int32 [nnz], val float32 [nnz] (NULL if binary),
+ * dinv float32 [n] = D^-1/2, deg float64 [n] = D_ii. Any output pointer may be NULL.
+ */
+ofsc_status ofsc_graph_csr(const ofsc_graph* g, const int64_t** row_ptr, const int32_t** col,
+                           const float** val, const float** dinv, const double** deg);
+
+/*
+ * ofsc_objective_grad - f and its gradient at X (Eqs. (2)/(3), (5)/(10)).
+ *   objective  OFSC_F1 or OFSC_F2
+ *   k          columns of X (1 <= k <= 128)
+ *   X          device float32 [n x k]
+ *   f_out      HOST double*: receives f (nullable)
+ *   G_out      device float32 [n x k]: receives the gradient with its factor 4 (nullable)
+ * f1 uses ||A + XX^T||^2 = ||A||^2 + 2 tr(X^T A X) + ||X^T X||^2. Synchronises `stream`.
+ * Errors: OFSC_ERR_INVALID_ARG, OFSC_ERR_OOM, OFSC_ERR_NONFINITE (NaN/Inf in X or f).
+ */
+ofsc_status ofsc_objective_grad(ofsc_graph* g, int32_t objective, int32_t k, const float* X,
+                                double* f_out, float* G_out, void* stream);
+
+/* Phases of one update, for the optional per-phase device timing of ofsc_iterate. */
+enum {
+  OFSC_PHASE_DIRECTION = 0,    /* update X, AX; G = g(X); column sums (the direction pass) */
+  OFSC_PHASE_BETA = 1,         /* beta and the stop test */
+  OFSC_PHASE_SPMM = 2,         /* A G gather with the fused V, AV epilogue */
+  OFSC_PHASE_GRAM = 3,         /* k x k Gram partials over all rows */
+  OFSC_PHASE_GRAM_REDUCE = 4,  /* fixed-order FP64 sum of the Gram partials */
+  OFSC_PHASE_LINESEARCH = 5,   /* FP64 cubic coefficients, roots, alpha */
+  OFSC_PHASE_REFRESH = 6,      /* exact A X recomputation with its Grams */
+  OFSC_PHASE_OTHER = 7,        /* padding copies, control, update-only passes */
+  OFSC_NUM_PHASES = 8
+};
+
+/* Accumulated device time per phase, measured with CUDA events on the call's stream. */
+typedef struct {
+  double ms[OFSC_NUM_PHASES];
+  int64_t launches[OFSC_NUM_PHASES];
+} ofsc_profile;
+
+typedef struct {
+  int32_t gather;      /* OFSC_GATHER_FP32 (default) or OFSC_GATHER_BF16 */
+  int32_t y_refresh;   /* AX is carried by the recurrence AX += AV diag(alpha); it is recomputed
+                          exactly every y_refresh iterations (<= 0: default 32) */
+  int32_t check_every; /* host reads the stop flag every check_every iterations (<= 0: 16) */
+  double alpha0;       /* > 0: fixed step for step 0 of Algorithm 2; else exact line search */
+  double* trace;       /* device float64 [trace_cap x (3 + 2k)] or NULL: per update t the record
+                          {t, ||G_t||/||G_0||, f(X_t), alpha_t[0..k-1], beta_t[0..k-1]} */
+  int32_t trace_cap;   /* records available in `trace` */
+  ofsc_profile* profile; /* HOST struct or NULL: the call ADDS its per-phase device times
+                            (events around every launch; adds a little host overhead) */
+} ofsc_opts;
+
+typedef struct {
+  int32_t iterations;   /* updates X <- X + V diag(alpha) performed */
+  int32_t status;       /* OFSC_OK (converged), OFSC_ERR_NOT_CONVERGED, or an error */
+  double rel_dir_norm;  /* ||g(X)||_F / ||g(X_0)||_F at the returned X (AX recomputed exactly) */
+  double g0_norm;       /* ||g(X_0)||_F */
+  double f;             /* objective of the method (f1 or f2) at the returned X */
+  int64_t kernel_launches; /* device kernels this call launched */
+} ofsc_result;
+
+/*
+ * ofsc_iterate - Algorithm 2 (column-wise nonlinear CG with the exact line search of Sec. 3.2).
+ *   method   OFSC_OFM_F1, OFSC_TRI_F1, OFSC_OFM_F2 or OFSC_TRI_F2
+ *   k        columns (1 <= k <= 128; internally padded to a multiple of 8 with zero columns,
+ *            which stay zero)
+ *   X        device float32 [n x k]: in = X0 (warm start allowed), out = final X
+ *   tol      stop when ||G_t||_F <= tol * ||G_0||_F (tol <= 0: run maxit updates)
+ *   maxit    maximum number of updates t_max (>= 0)
+ *   opts     host struct or NULL for defaults
+ *   out      HOST ofsc_result (nullable)
+ * G_0 = g(X_0), V_0 = -G_0, X_1 = X_0 + V_0 diag(alpha_0); for t >= 1: G_t = g(X_t);
+ * beta_i = sum_l (G_t - G_{t-1})_li G_t,li / sum_l G_{t-1,li}^2 (0 if the denominator is 0);
+ * V_t = -G_t + V_{t-1} diag(beta); alpha_t from the exact line search (one alpha for OFM, one
+ * per column for TriOFM, with X_i, V_i the first i columns); X_{t+1} = X_t + V_t diag(alpha_t).
+ * Returns OFSC_OK when tol was met, OFSC_ERR_NOT_CONVERGED when maxit was reached first (X is
+ * still the valid final iterate). Synchronises `stream`.
+ * Errors: OFSC_ERR_INVALID_ARG, OFSC_ERR_OOM, OFSC_ERR_NONFINITE.
+ */
+ofsc_status ofsc_iterate(ofsc_graph* g, int32_t method, int32_t k, float* X, double tol,
+                         int32_t maxit, const ofsc_opts* opts, ofsc_result* out, void* stream);
+
+/*
+ * ofsc_row_normalize - X_l <- X_l / ||X_l||_2 for every row; zero rows stay zero
+ * (Algorithm 1, step 3). X is device float32 [n x k], in place. Asynchronous.
+ */
+ofsc_status ofsc_row_normalize(int64_t n, int32_t k, float* X, void* stream);
+
+/*
+ * ofsc_kmeans - Euclidean K-means on the rows of X (Algorithm 1, step 4).
+ *   X        device float32 [n x d]
+ *   n_clusters  1 <= n_clusters <= n
+ *   seed     key of the Philox-4x32-10 stream that drives K-means++ seeding
+ *   n_init   independent seeded runs (>= 1); the lowest inertia wins (ties: earlier run)
+ *   maxit    maximum Lloyd assignments per run (>= 1)
+ *   labels   device int32 [n], receives the cluster of each row
+ *   inertia  HOST double* (nullable): sum of squared distances to the assigned centroids
+ * Seeding: run r, draw c uses u = word0(Philox4x32-10(ctr = {c, r, 0, 0}, key = {seed_lo,
+ * seed_hi})) / 2^32; centre 0 = row floor(u N); centre c = first row whose running sum of D^2
+ * exceeds u * sum D^2. Lloyd: nearest centroid (ties: lowest index), stop when no label
+ * changes; an empty cluster takes the row farthest from its own centroid. Synchronises `stream`.
+ * Errors: OFSC_ERR_INVALID_ARG, OFSC_ERR_OOM.
+ */
+ofsc_status ofsc_kmeans(int64_t n, int32_t d, const float* X, int32_t n_clusters, uint64_t seed,
+                        int32_t n_init, int32_t maxit, int32_t* labels, double* inertia,
+                        void* stream);
+
+/* Message of the last failing call on this host thread ("" if none). */
+const char* ofsc_last_error(void);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int32_t ofsc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OFSC_H */

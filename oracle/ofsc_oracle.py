@@ -105,14 +105,17 @@ def build_graph(n: int, src: np.ndarray, dst: np.ndarray, w: np.ndarray | None =
     rows = np.concatenate([src[keep], dst[keep]])
     cols = np.concatenate([dst[keep], src[keep]])
     key = rows * max(n, 1) + cols
+    # sort the (row, col) keys; the first entry of each run of equal keys is a distinct pair
+    order = np.argsort(key, kind="stable")
+    key_s = key[order]
+    head = np.ones(key_s.size, dtype=bool)
+    head[1:] = key_s[1:] != key_s[:-1]
+    ukey = key_s[head]
     if w is None:
-        ukey = np.unique(key)
         val = None
     else:
         ww = np.concatenate([w[keep], w[keep]]).astype(np.float64)
-        order = np.argsort(key, kind="stable")
-        key_s = key[order]
-        ukey, start = np.unique(key_s, return_index=True)
+        start = np.nonzero(head)[0]
         sums = np.add.reduceat(ww[order], start) if key_s.size else np.zeros(0)
         val = sums.astype(np.float32)
     r = (ukey // max(n, 1)).astype(np.int64)

@@ -1,0 +1,112 @@
+// Internal declarations shared by the translation units of libofsc (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ofsc.h"
+
+namespace ofsc {
+
+constexpr int kNumSMs = 152;  // GB300: 2 dies x 76 SMs
+constexpr int kMaxK = 128;    // widest padded feature block handled by the kernels
+
+// Last-error message of the calling host thread.
+void set_error(const char* fmt, ...);
+void clear_error();
+
+// Records `st` with a message and returns it.
+ofsc_status fail(ofsc_status st, const char* fmt, ...);
+
+// Maps a CUDA error to OFSC_ERR_CUDA / OFSC_ERR_OOM and records it.
+ofsc_status cuda_fail(cudaError_t e, const char* what);
+
+#define OFSC_CUDA(call)                                        \
+  do {                                                         \
+    cudaError_t e_ = (call);                                   \
+    if (e_ != cudaSuccess) return ::ofsc::cuda_fail(e_, #call); \
+  } while (0)
+
+#define OFSC_LAUNCH_CHECK(what)                                 \
+  do {                                                          \
+    cudaError_t e_ = cudaGetLastError();                        \
+    if (e_ != cudaSuccess) return ::ofsc::cuda_fail(e_, what);  \
+  } while (0)
+
+inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Device control block of one ofsc_iterate / ofsc_objective_grad call.
+struct Ctrl {
+  int it;          // updates X <- X + V diag(alpha) applied so far
+  int done;        // 1 once the loop must stop (every kernel returns early)
+  int converged;   // 1 if ||G_t|| <= tol ||G_0||
+  int status;      // OFSC_OK or OFSC_ERR_NONFINITE
+  int maxit;
+  int trace_cap;
+  int k;           // real (unpadded) columns
+  int pad_;
+  double tol;
+  double g0;       // ||G_0||_F
+  double gnorm;    // ||G_t||_F of the last direction pass
+  double rel;      // gnorm / g0
+  double f;        // objective at X_t (from the exact Grams of X_t)
+  double normA2;   // ||A||_F^2
+};
+
+// Device workspace of the iteration for one padded width kp, cached on the graph handle.
+struct Workspace {
+  int64_t n = 0;
+  int kp = 0;
+  int gather = 0;
+  float* X = nullptr;   // n x kp, working copy of the block (zero padded)
+  float* Y = nullptr;   // A X
+  float* V = nullptr;   // search direction
+  float* W = nullptr;   // A V
+  float* G = nullptr;   // direction g(X) of the last pass (G_{t-1} while G_t is formed)
+  void* Gh = nullptr;   // D^-1/2 G, FP32 or BF16: the block gathered by the sparse product
+  double* gram_part = nullptr;  // [gram_gy][6][kp*kp] per-row-group partial Grams
+  double* gram = nullptr;       // [6][kp*kp] reduced Grams R, P, Q, B, E, C
+  float* Rn = nullptr;          // kp*kp: X^T X for the next direction pass
+  float* Bn = nullptr;          // kp*kp: X^T A X for the next direction pass
+  float* alpha = nullptr;       // kp
+  float* beta = nullptr;        // kp
+  double* alpha64 = nullptr;    // kp
+  double* beta64 = nullptr;     // kp
+  double* colpart = nullptr;    // [row_blocks][3][kp]
+  Ctrl* ctrl = nullptr;
+  Ctrl* ctrl_host = nullptr;    // pinned
+  int gram_gy = 0;
+  int row_blocks = 0;
+  size_t bytes = 0;
+  std::vector<cudaEvent_t> events;  // pool for the optional per-phase timing
+  int64_t launches = 0;             // kernels launched by the current call
+};
+
+}  // namespace ofsc
+
+struct ofsc_graph {
+  int64_t n = 0;
+  int64_t m_in = 0;
+  int64_t nnz = 0;
+  int64_t n_selfloops = 0;
+  int64_t n_duplicates = 0;
+  int64_t n_isolated = 0;
+  int weighted = 0;
+  double normA2 = 0.0;
+  int device = 0;
+  int64_t* row_ptr = nullptr;  // [n+1]
+  int32_t* col = nullptr;      // [nnz]
+  float* val = nullptr;        // [nnz] or null
+  float* dinv = nullptr;       // [n]  D^-1/2 in FP32
+  double* deg = nullptr;       // [n]
+  ofsc::Workspace ws;
+};
+
+namespace ofsc {
+void workspace_free(Workspace& ws);
+}

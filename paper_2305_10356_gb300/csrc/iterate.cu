@@ -1,0 +1,1378 @@
+// Algorithm 2 on the device: the direction pass, the sparse product with its fused epilogue, the
+// k x k Gram reductions and the FP64 exact line search (Sec. 3.2), driven by ofsc_iterate.
+//
+// Per update t (the paper's steps 7-11, Sec. 4) the device runs:
+//   direction pass  X += V diag(alpha), AX += AV diag(alpha)   (previous update, fused)
+//                   G = g(X) from AX and the k x k blocks X^T X, X^T A X       (Eqs. (5),(7),(10),(12))
+//                   column sums for beta and ||G||, Gh = D^-1/2 G
+//   beta            beta_i = sum (G - G_prev) G / sum G_prev^2, stop test        (Algorithm 2)
+//   sparse product  Z = A G by gathering rows of Gh; V = -G + V diag(beta); AV = -Z + AV diag(beta)
+//   Grams           X^T X, V^T X, V^T V, X^T AX, V^T AX, V^T AV                 (Sec. 3.3)
+//   line search     cubic coefficients, real roots, alpha; X^T X and X^T AX of the next X
+// AX is carried by the recurrence AX_{t+1} = AX_t + AV_t diag(alpha_t) and AV by
+// AV_t = -A G_t + AV_{t-1} diag(beta_t) (A is linear, so both are exact in exact arithmetic);
+// AX is recomputed from X every y_refresh updates and at the end, so rounding cannot pile up.
+#include <cuda_bf16.h>
+#include <stdarg.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+
+namespace ofsc {
+namespace {
+
+enum { M_OFM_F1 = 0, M_TRI_F1 = 1, M_OFM_F2 = 2, M_TRI_F2 = 3 };
+constexpr int kPairs = 6;
+enum { G_R = 0, G_P = 1, G_Q = 2, G_B = 3, G_E = 4, G_C = 5 };
+constexpr int kRowThreads = 256;
+constexpr int kRPT = 8;           // rows per thread in one tile of the direction pass
+constexpr int kMaxRowBlocks = 8 * kNumSMs;
+constexpr int kGramChunk = 32;    // rows staged in shared memory per Gram step
+
+__device__ __forceinline__ int64_t ceil_div_dev(int64_t a, int64_t b) { return (a + b - 1) / b; }
+__device__ __forceinline__ bool is_tri(int method) { return method == M_TRI_F1 || method == M_TRI_F2; }
+__device__ __forceinline__ bool is_f2(int method) { return method >= M_OFM_F2; }
+
+// ------------------------------------------------------------------------------------------
+// Setup kernels
+// ------------------------------------------------------------------------------------------
+
+__global__ void k_init_ctrl(Ctrl* c, double tol, int maxit, int k, double normA2, int trace_cap) {
+  c->it = 0;
+  c->done = 0;
+  c->converged = 0;
+  c->status = OFSC_OK;
+  c->maxit = maxit;
+  c->trace_cap = trace_cap;
+  c->k = k;
+  c->tol = tol;
+  c->g0 = 0.0;
+  c->gnorm = 0.0;
+  c->rel = 1.0;
+  c->f = 0.0;
+  c->normA2 = normA2;
+}
+
+__global__ void k_pad_in(int64_t n, int k, int kp, const float* __restrict__ src,
+                         float* __restrict__ dst, Ctrl* ctrl) {
+  int bad = 0;
+  const int64_t total = n * kp;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t l = i / kp;
+    int c = (int)(i - l * kp);
+    float x = c < k ? src[l * k + c] : 0.0f;
+    if (!isfinite(x)) bad = 1;
+    dst[i] = x;
+  }
+  if (bad) {
+    ctrl->status = OFSC_ERR_NONFINITE;
+    ctrl->done = 1;
+  }
+}
+
+__global__ void k_pad_out(int64_t n, int k, int kp, const float* __restrict__ src, float* __restrict__ dst) {
+  const int64_t total = n * k;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t l = i / k;
+    int c = (int)(i - l * k);
+    dst[i] = src[l * kp + c];
+  }
+}
+
+// X += V diag(alpha) without touching AX (the refresh recomputes AX from X afterwards).
+__global__ void k_update_x(int64_t n, int kp, float* __restrict__ X, const float* __restrict__ V,
+                           const float* __restrict__ alpha, Ctrl* ctrl) {
+  if (ctrl->done) return;
+  const int64_t total = n * kp;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int c = (int)(i % kp);
+    X[i] = fmaf(alpha[c], V[i], X[i]);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) ctrl->it += 1;
+}
+
+// ------------------------------------------------------------------------------------------
+// Sparse product Y = A M with A = -I - D^-1/2 S D^-1/2, fused epilogues
+// ------------------------------------------------------------------------------------------
+
+enum { SP_DIR = 0, SP_Y = 1 };
+
+struct SpmmArgs {
+  int64_t n;
+  int kp;
+  const int64_t* row_ptr;
+  const int32_t* col;
+  const float* val;
+  const float* dinv;
+  const void* gather;  // SP_DIR: Gh (FP32 or BF16, pre-scaled by D^-1/2); SP_Y: X (FP32)
+  const float* G;      // SP_DIR
+  float* V;            // SP_DIR: in V_{t-1}, out V_t
+  float* W;            // SP_DIR: in AV_{t-1}, out AV_t
+  const float* beta;   // SP_DIR
+  const float* X;      // SP_Y
+  float* Y;            // SP_Y: out A X
+  Ctrl* ctrl;
+  int first;           // SP_DIR: t = 0 (no V_{t-1}, AV_{t-1})
+  int ignore_done;
+};
+
+template <bool BF16>
+__device__ __forceinline__ float4 load_row4(const void* base, int64_t row, int kp, int c) {
+  if constexpr (BF16) {
+    const __nv_bfloat16* p = (const __nv_bfloat16*)base + row * kp + c;
+    uint2 u = __ldg((const uint2*)p);
+    __nv_bfloat162 a = *reinterpret_cast<__nv_bfloat162*>(&u.x);
+    __nv_bfloat162 b = *reinterpret_cast<__nv_bfloat162*>(&u.y);
+    float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
+    return make_float4(fa.x, fa.y, fb.x, fb.y);
+  } else {
+    return __ldg((const float4*)((const float*)base + row * kp + c));
+  }
+}
+
+__device__ __forceinline__ void fma4(float4& acc, float w, const float4& v) {
+  acc.x = fmaf(w, v.x, acc.x);
+  acc.y = fmaf(w, v.y, acc.y);
+  acc.z = fmaf(w, v.z, acc.z);
+  acc.w = fmaf(w, v.w, acc.w);
+}
+
+// A group of LANES lanes owns one row at a time; lane q holds columns [4q, 4q + 4).
+template <int LANES, bool WEIGHTED, int MODE, bool BF16>
+__global__ void __launch_bounds__(256) k_spmm(SpmmArgs a) {
+  if (!a.ignore_done && a.ctrl->done) return;
+  constexpr int GROUPS = 256 / LANES;
+  constexpr bool GBF = (MODE == SP_DIR) && BF16;
+  const int lane = threadIdx.x % LANES;
+  const int grp = threadIdx.x / LANES;
+  const unsigned mask = LANES == 32 ? 0xffffffffu
+                                    : (((1u << LANES) - 1u) << ((threadIdx.x & 31) / LANES * LANES));
+  const int c = lane * 4;
+  const bool active = c < a.kp;
+  for (int64_t l = (int64_t)blockIdx.x * GROUPS + grp; l < a.n; l += (int64_t)gridDim.x * GROUPS) {
+    const int64_t p0 = a.row_ptr[l], p1 = a.row_ptr[l + 1];
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int64_t base = p0; base < p1; base += LANES) {
+      const int cnt = (int)min((int64_t)LANES, p1 - base);
+      int jj = 0;
+      float ww = 0.0f;
+      if (lane < cnt) {
+        jj = __ldg(a.col + base + lane);
+        ww = WEIGHTED ? __ldg(a.val + base + lane) : 1.0f;
+        if (MODE == SP_Y) ww *= __ldg(a.dinv + jj);
+      }
+      int q = 0;
+      for (; q + 4 <= cnt; q += 4) {
+        int j0 = __shfl_sync(mask, jj, q, LANES), j1 = __shfl_sync(mask, jj, q + 1, LANES);
+        int j2 = __shfl_sync(mask, jj, q + 2, LANES), j3 = __shfl_sync(mask, jj, q + 3, LANES);
+        float w0 = __shfl_sync(mask, ww, q, LANES), w1 = __shfl_sync(mask, ww, q + 1, LANES);
+        float w2 = __shfl_sync(mask, ww, q + 2, LANES), w3 = __shfl_sync(mask, ww, q + 3, LANES);
+        if (active) {
+          float4 v0 = load_row4<GBF>(a.gather, j0, a.kp, c);
+          float4 v1 = load_row4<GBF>(a.gather, j1, a.kp, c);
+          float4 v2 = load_row4<GBF>(a.gather, j2, a.kp, c);
+          float4 v3 = load_row4<GBF>(a.gather, j3, a.kp, c);
+          fma4(acc, w0, v0);
+          fma4(acc, w1, v1);
+          fma4(acc, w2, v2);
+          fma4(acc, w3, v3);
+        }
+      }
+      for (; q < cnt; ++q) {
+        int j = __shfl_sync(mask, jj, q, LANES);
+        float w = __shfl_sync(mask, ww, q, LANES);
+        if (active) fma4(acc, w, load_row4<GBF>(a.gather, j, a.kp, c));
+      }
+    }
+    if (!active) continue;
+    const float s = a.dinv[l];
+    const int64_t o = l * a.kp + c;
+    if (MODE == SP_DIR) {
+      // A G = -G - s (S Gh);  AV_t = -A G_t + beta AV_{t-1};  V_t = -G_t + beta V_{t-1}
+      const float4 g = *(const float4*)(a.G + o);
+      float4 w = make_float4(fmaf(s, acc.x, g.x), fmaf(s, acc.y, g.y), fmaf(s, acc.z, g.z),
+                             fmaf(s, acc.w, g.w));
+      float4 v = make_float4(-g.x, -g.y, -g.z, -g.w);
+      if (!a.first) {
+        const float4 b = *(const float4*)(a.beta + c);
+        const float4 wp = *(const float4*)(a.W + o);
+        const float4 vp = *(const float4*)(a.V + o);
+        w.x = fmaf(b.x, wp.x, w.x);
+        w.y = fmaf(b.y, wp.y, w.y);
+        w.z = fmaf(b.z, wp.z, w.z);
+        w.w = fmaf(b.w, wp.w, w.w);
+        v.x = fmaf(b.x, vp.x, v.x);
+        v.y = fmaf(b.y, vp.y, v.y);
+        v.z = fmaf(b.z, vp.z, v.z);
+        v.w = fmaf(b.w, vp.w, v.w);
+      }
+      *(float4*)(a.W + o) = w;
+      *(float4*)(a.V + o) = v;
+    } else {
+      const float4 x = *(const float4*)(a.X + o);
+      *(float4*)(a.Y + o) = make_float4(-fmaf(s, acc.x, x.x), -fmaf(s, acc.y, x.y),
+                                        -fmaf(s, acc.z, x.z), -fmaf(s, acc.w, x.w));
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Direction pass: optional update, G = g(X), Gh = D^-1/2 G, column sums for beta
+// ------------------------------------------------------------------------------------------
+
+struct RowArgs {
+  int64_t n;
+  int kp;
+  float* X;
+  float* Y;
+  const float* V;
+  const float* W;
+  float* G;
+  void* Gh;
+  const float* dinv;
+  const float* Rn;
+  const float* Bn;
+  const float* alpha;
+  double* colpart;  // [gridDim.x][3][kp]: sum G^2, sum (G - G_prev) G, sum G_prev^2
+  Ctrl* ctrl;
+  int update;
+  int eval;         // no previous G (objective/gradient evaluation and the final report)
+  int ignore_done;
+};
+
+template <int METHOD, bool BF16>
+__global__ void __launch_bounds__(kRowThreads) k_rowpass(RowArgs a) {
+  if (!a.ignore_done && a.ctrl->done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int kp = a.kp;
+  const int nrg = kRowThreads / kp;
+  const int nthr = nrg * kp;
+  const int TR = nrg * kRPT;
+  float* Rs = (float*)smem_raw;                                    // kp*kp
+  float* Bs = Rs + kp * kp;                                        // kp*kp (f2 only)
+  float* xs = Bs + (is_f2(METHOD) ? kp * kp : 0);                  // TR*kp
+  float* ys = xs + TR * kp;                                        // TR*kp
+  float* als = ys + TR * kp;                                       // kp
+  double* red = (double*)(als + kp);                               // 3 * nthr (kp % 8 == 0)
+  const int tid = threadIdx.x;
+  const bool worker = tid < nthr;
+  const int col = tid % kp;
+  const int rg = tid / kp;
+
+  for (int i = tid; i < kp * kp; i += blockDim.x) {
+    int m = i / kp, j = i % kp;
+    bool keep = !is_tri(METHOD) || m <= j;  // triu(.) keeps m <= j
+    Rs[i] = keep ? a.Rn[i] : 0.0f;
+    if (is_f2(METHOD)) Bs[i] = keep ? a.Bn[i] : 0.0f;
+  }
+  for (int i = tid; i < kp; i += blockDim.x) als[i] = a.update ? a.alpha[i] : 0.0f;
+  if (a.update && blockIdx.x == 0 && tid == 0) a.ctrl->it += 1;
+  __syncthreads();
+
+  double sgg = 0.0, snum = 0.0, sden = 0.0;
+  const int64_t ntiles = ceil_div_dev(a.n, TR);
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t row0 = tile * TR;
+    const int rows = (int)min((int64_t)TR, a.n - row0);
+    const int64_t base = row0 * kp;
+    for (int i = tid; i < TR * kp; i += blockDim.x) {
+      float x = 0.0f, y = 0.0f;
+      if (i < rows * kp) {
+        x = a.X[base + i];
+        y = a.Y[base + i];
+        if (a.update) {
+          const float al = als[i % kp];
+          x = fmaf(al, a.V[base + i], x);
+          y = fmaf(al, a.W[base + i], y);
+          a.X[base + i] = x;
+          a.Y[base + i] = y;
+        }
+      }
+      xs[i] = x;
+      ys[i] = y;
+    }
+    __syncthreads();
+    if (worker) {
+      float acc[kRPT];
+#pragma unroll
+      for (int r = 0; r < kRPT; ++r) acc[r] = 0.0f;
+      for (int m = 0; m < kp; ++m) {
+        const float rm = Rs[m * kp + col];
+        if (is_f2(METHOD)) {
+          const float bm = Bs[m * kp + col];
+#pragma unroll
+          for (int r = 0; r < kRPT; ++r) {
+            const int rl = rg + r * nrg;
+            acc[r] = fmaf(xs[rl * kp + m], bm, fmaf(ys[rl * kp + m], rm, acc[r]));
+          }
+        } else {
+#pragma unroll
+          for (int r = 0; r < kRPT; ++r) {
+            const int rl = rg + r * nrg;
+            acc[r] = fmaf(xs[rl * kp + m], rm, acc[r]);
+          }
+        }
+      }
+      float tgg = 0.f, tnum = 0.f, tden = 0.f;
+#pragma unroll
+      for (int r = 0; r < kRPT; ++r) {
+        const int rl = rg + r * nrg;
+        if (rl >= rows) continue;
+        const float y = ys[rl * kp + col];
+        float g;
+        if (METHOD == M_OFM_F1) g = 4.0f * (y + acc[r]);          // Eq. (5)
+        else if (METHOD == M_TRI_F1) g = y + acc[r];               // Eq. (7)
+        else if (METHOD == M_OFM_F2) g = 4.0f * y - 2.0f * acc[r]; // Eq. (10)
+        else g = 2.0f * y - acc[r];                                // Eq. (12)
+        const int64_t o = base + (int64_t)rl * kp + col;
+        const float gp = a.eval ? 0.0f : a.G[o];
+        a.G[o] = g;
+        const float gh = a.dinv[row0 + rl] * g;
+        if (BF16) ((__nv_bfloat16*)a.Gh)[o] = __float2bfloat16_rn(gh);
+        else ((float*)a.Gh)[o] = gh;
+        tgg = fmaf(g, g, tgg);
+        tnum = fmaf(g - gp, g, tnum);
+        tden = fmaf(gp, gp, tden);
+      }
+      sgg += tgg;
+      snum += tnum;
+      sden += tden;
+    }
+    __syncthreads();
+  }
+  if (worker) {
+    red[tid] = sgg;
+    red[nthr + tid] = snum;
+    red[2 * nthr + tid] = sden;
+  }
+  __syncthreads();
+  if (tid < kp) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int r = 0; r < nrg; ++r) {
+      s0 += red[r * kp + tid];
+      s1 += red[nthr + r * kp + tid];
+      s2 += red[2 * nthr + r * kp + tid];
+    }
+    double* out = a.colpart + (int64_t)blockIdx.x * 3 * kp;
+    out[tid] = s0;
+    out[kp + tid] = s1;
+    out[2 * kp + tid] = s2;
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// beta and the stop test (one block)
+// ------------------------------------------------------------------------------------------
+
+__global__ void k_beta(const double* __restrict__ colpart, int nblk, int kp, float* beta,
+                       double* beta64, Ctrl* ctrl, int first, int eval) {
+  if (!eval && ctrl->done) return;
+  __shared__ double sh[256];
+  const int j = threadIdx.x;
+  double gg = 0.0, num = 0.0, den = 0.0;
+  if (j < kp) {
+    for (int b = 0; b < nblk; ++b) {
+      const double* p = colpart + (int64_t)b * 3 * kp;
+      gg += p[j];
+      num += p[kp + j];
+      den += p[2 * kp + j];
+    }
+  }
+  sh[j] = gg;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (j < s) sh[j] += sh[j + s];
+    __syncthreads();
+  }
+  const double gnorm = sqrt(sh[0]);
+  if (eval) {
+    if (j == 0) {
+      ctrl->gnorm = gnorm;
+      ctrl->rel = ctrl->g0 > 0.0 ? gnorm / ctrl->g0 : 0.0;
+    }
+    return;
+  }
+  __shared__ int stop;
+  if (j == 0) {
+    stop = 0;
+    ctrl->gnorm = gnorm;
+    if (!isfinite(gnorm)) {
+      ctrl->status = OFSC_ERR_NONFINITE;
+      stop = 1;
+    } else if (first) {
+      ctrl->g0 = gnorm;
+      ctrl->rel = gnorm > 0.0 ? 1.0 : 0.0;
+      if (gnorm == 0.0) {
+        ctrl->converged = 1;
+        stop = 1;
+      } else if (ctrl->maxit <= 0) {
+        stop = 1;
+      }
+    } else {
+      const double rel = gnorm / ctrl->g0;
+      ctrl->rel = rel;
+      if (rel <= ctrl->tol) {
+        ctrl->converged = 1;
+        stop = 1;
+      } else if (ctrl->it >= ctrl->maxit) {
+        stop = 1;
+      }
+    }
+    if (stop) ctrl->done = 1;
+  }
+  __syncthreads();
+  if (j < kp) {
+    double b = 0.0;
+    if (!first && den != 0.0) b = num / den;
+    beta[j] = (float)b;
+    beta64[j] = b;
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Grams L^T R over all rows: per row-group partials with compensated FP32 accumulation
+// ------------------------------------------------------------------------------------------
+
+struct GramPairs {
+  const float* L[kPairs];
+  const float* R[kPairs];
+  int slot[kPairs];  // output slot (G_R ... G_C)
+};
+
+struct GramArgs {
+  int64_t n;
+  int kp;
+  int npairs;
+  int nt;            // tiles per dimension
+  int64_t rows_per_group;
+  GramPairs pairs;
+  double* part;      // [gridDim.y][kPairs][kp*kp]
+  Ctrl* ctrl;
+  int ignore_done;
+};
+
+template <int M>
+struct VecT;
+template <>
+struct VecT<1> {
+  using T = float;
+  static __device__ __forceinline__ void get(const float* p, float* o) { o[0] = p[0]; }
+};
+template <>
+struct VecT<2> {
+  static __device__ __forceinline__ void get(const float* p, float* o) {
+    float2 v = *(const float2*)p;
+    o[0] = v.x;
+    o[1] = v.y;
+  }
+};
+template <>
+struct VecT<4> {
+  static __device__ __forceinline__ void get(const float* p, float* o) {
+    float4 v = *(const float4*)p;
+    o[0] = v.x;
+    o[1] = v.y;
+    o[2] = v.z;
+    o[3] = v.w;
+  }
+};
+
+// 256 threads as 16 x 16; tile T x T with T = 16 M; thread (tx, ty) owns rows ty*M.., cols tx*M..
+template <int M>
+__global__ void __launch_bounds__(256) k_gram(GramArgs a) {
+  if (!a.ignore_done && a.ctrl->done) return;
+  constexpr int T = 16 * M;
+  __shared__ __align__(16) float Ls[kGramChunk][T];
+  __shared__ __align__(16) float Rs[kGramChunk][T];
+  const int tid = threadIdx.x;
+  const int tx = tid % 16, ty = tid / 16;
+  const int nt2 = a.nt * a.nt;
+  const int pair = blockIdx.x / nt2;
+  const int tile = blockIdx.x % nt2;
+  const int i0 = (tile / a.nt) * T, j0 = (tile % a.nt) * T;
+  const float* __restrict__ L = a.pairs.L[pair];
+  const float* __restrict__ R = a.pairs.R[pair];
+  const int64_t r0 = (int64_t)blockIdx.y * a.rows_per_group;
+  const int64_t r1 = min(a.n, r0 + a.rows_per_group);
+  float s[M][M], cmp[M][M];
+#pragma unroll
+  for (int u = 0; u < M; ++u)
+#pragma unroll
+    for (int v = 0; v < M; ++v) s[u][v] = cmp[u][v] = 0.0f;
+  for (int64_t rb = r0; rb < r1; rb += kGramChunk) {
+    for (int i = tid; i < kGramChunk * T; i += 256) {
+      const int r = i / T, cc = i % T;
+      const int64_t l = rb + r;
+      const bool ok = l < r1;
+      Ls[r][cc] = (ok && i0 + cc < a.kp) ? L[l * a.kp + i0 + cc] : 0.0f;
+      Rs[r][cc] = (ok && j0 + cc < a.kp) ? R[l * a.kp + j0 + cc] : 0.0f;
+    }
+    __syncthreads();
+    float acc[M][M];
+#pragma unroll
+    for (int u = 0; u < M; ++u)
+#pragma unroll
+      for (int v = 0; v < M; ++v) acc[u][v] = 0.0f;
+#pragma unroll 4
+    for (int r = 0; r < kGramChunk; ++r) {
+      float av[M], bv[M];
+      VecT<M>::get(&Ls[r][ty * M], av);
+      VecT<M>::get(&Rs[r][tx * M], bv);
+#pragma unroll
+      for (int u = 0; u < M; ++u)
+#pragma unroll
+        for (int v = 0; v < M; ++v) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
+    }
+    // Kahan-compensated running sum of the chunk partials
+#pragma unroll
+    for (int u = 0; u < M; ++u)
+#pragma unroll
+      for (int v = 0; v < M; ++v) {
+        const float y = acc[u][v] - cmp[u][v];
+        const float t = s[u][v] + y;
+        cmp[u][v] = (t - s[u][v]) - y;
+        s[u][v] = t;
+      }
+    __syncthreads();
+  }
+  double* out = a.part + ((int64_t)blockIdx.y * kPairs + a.pairs.slot[pair]) * a.kp * a.kp;
+#pragma unroll
+  for (int u = 0; u < M; ++u)
+#pragma unroll
+    for (int v = 0; v < M; ++v) {
+      const int i = i0 + ty * M + u, j = j0 + tx * M + v;
+      if (i < a.kp && j < a.kp) out[i * a.kp + j] = (double)s[u][v] - (double)cmp[u][v];
+    }
+}
+
+__global__ void k_gram_reduce(const double* __restrict__ part, int gy, int kp, int slot_mask,
+                              double* __restrict__ gram, Ctrl* ctrl, int ignore_done) {
+  if (!ignore_done && ctrl->done) return;
+  const int kk = kp * kp;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kPairs * kk; i += gridDim.x * blockDim.x) {
+    const int slot = i / kk;
+    if (!((slot_mask >> slot) & 1)) continue;
+    double s = 0.0;
+    for (int b = 0; b < gy; ++b) s += part[(int64_t)b * kPairs * kk + i];
+    gram[i] = s;
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// FP64 line search (one block): cubic coefficients, real roots, alpha, next X^T X and X^T AX
+// ------------------------------------------------------------------------------------------
+
+// Real roots of c3 a^3 + c2 a^2 + c1 a + c0; returns the count (0..3).
+__device__ int real_roots(double c3, double c2, double c1, double c0, double* r) {
+  if (c3 == 0.0) {
+    if (c2 == 0.0) {
+      if (c1 == 0.0) return 0;
+      r[0] = -c0 / c1;
+      return 1;
+    }
+    const double disc = c1 * c1 - 4.0 * c2 * c0;
+    if (disc < 0.0) return 0;
+    const double q = -0.5 * (c1 + copysign(sqrt(disc), c1));
+    if (q == 0.0) {
+      r[0] = 0.0;
+      return 1;
+    }
+    r[0] = q / c2;
+    r[1] = c0 / q;
+    return 2;
+  }
+  // monic form a^3 + A a^2 + B a + C, shift a = t - A/3: t^3 + p t + q
+  const double A = c2 / c3, B = c1 / c3, C = c0 / c3;
+  const double p = B - A * A / 3.0;
+  const double q = 2.0 * A * A * A / 27.0 - A * B / 3.0 + C;
+  const double h = -A / 3.0;
+  const double D = 0.25 * q * q + p * p * p / 27.0;
+  int cnt;
+  if (D > 0.0) {
+    const double u = cbrt(-0.5 * q - copysign(sqrt(D), q));
+    r[0] = (u != 0.0 ? u - p / (3.0 * u) : 0.0) + h;
+    cnt = 1;
+  } else if (D == 0.0) {
+    if (p == 0.0) {
+      r[0] = h;
+      return 1;
+    }
+    r[0] = 3.0 * q / p + h;      // simple root
+    r[1] = -1.5 * q / p + h;     // double root
+    cnt = 2;
+  } else {
+    const double m = 2.0 * sqrt(-p / 3.0);
+    double arg = 1.5 * q / p * sqrt(-3.0 / p);
+    arg = fmax(-1.0, fmin(1.0, arg));
+    const double th = acos(arg) / 3.0;
+    const double two_pi_3 = 2.0943951023931954923;
+    for (int i = 0; i < 3; ++i) r[i] = m * cos(th - two_pi_3 * i) + h;
+    cnt = 3;
+  }
+  for (int i = 0; i < cnt; ++i) {  // two Newton steps on the original cubic
+    for (int s = 0; s < 2; ++s) {
+      const double x = r[i];
+      const double f = ((c3 * x + c2) * x + c1) * x + c0;
+      const double d = (3.0 * c3 * x + 2.0 * c2) * x + c1;
+      if (d != 0.0) {
+        const double nx = x - f / d;
+        if (isfinite(nx)) r[i] = nx;
+      }
+    }
+  }
+  return cnt;
+}
+
+// The step: the real root where q(a) = c3 a^4/4 + c2 a^3/3 + c1 a^2/2 + c0 a is smallest
+// (for OFM, q is the objective along the line up to a constant factor). An exact double root
+// never beats the simple root, so the paper's three cases all reduce to this rule.
+__device__ double pick_step(double c3, double c2, double c1, double c0, int* bad) {
+  if (!(isfinite(c3) && isfinite(c2) && isfinite(c1) && isfinite(c0))) {
+    *bad = 1;
+    return 0.0;
+  }
+  double r[3];
+  const int n = real_roots(c3, c2, c1, c0, r);
+  if (n == 0) return 0.0;
+  double best = r[0], bq = 0.0;
+  for (int i = 0; i < n; ++i) {
+    const double x = r[i];
+    const double qv = ((0.25 * c3 * x + c2 / 3.0) * x + 0.5 * c1) * x * x + c0 * x;
+    if (i == 0 || qv < bq || (qv == bq && (fabs(x) < fabs(best) || (fabs(x) == fabs(best) && x < best)))) {
+      best = x;
+      bq = qv;
+    }
+  }
+  return best;
+}
+
+template <int NV>
+__device__ void block_sum(double (&v)[NV], double* sh) {
+  const int tid = threadIdx.x;
+  for (int q = 0; q < NV; ++q) sh[q * 256 + tid] = v[q];
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (tid < s)
+      for (int q = 0; q < NV; ++q) sh[q * 256 + tid] += sh[q * 256 + tid + s];
+    __syncthreads();
+  }
+  for (int q = 0; q < NV; ++q) v[q] = sh[q * 256];
+  __syncthreads();
+}
+
+struct SolveArgs {
+  const double* gram;  // [6][kp*kp]
+  int kp;
+  int k;
+  int method;
+  float* Rn;
+  float* Bn;
+  float* alpha;
+  double* alpha64;
+  const double* beta64;
+  double* trace;
+  Ctrl* ctrl;
+  double alpha0;  // > 0: fixed step for update 0 instead of the line search
+};
+
+__global__ void __launch_bounds__(256) k_solve(SolveArgs a) {
+  if (a.ctrl->done) return;
+  __shared__ double sh[12 * 256];
+  __shared__ double coef[kMaxK][4];
+  __shared__ double al[kMaxK];
+  __shared__ int bad;
+  const int kp = a.kp, k = a.k, kk = kp * kp, tid = threadIdx.x;
+  const double* R = a.gram + G_R * kk;
+  const double* P = a.gram + G_P * kk;
+  const double* Q = a.gram + G_Q * kk;
+  const double* B = a.gram + G_B * kk;
+  const double* E = a.gram + G_E * kk;
+  const double* C = a.gram + G_C * kk;
+  // B = X^T A X and C = V^T A V are symmetric; the recurrences leave rounding asymmetry.
+#define SYM(M, i, j) (0.5 * ((M)[(i) * kp + (j)] + (M)[(j) * kp + (i)]))
+  if (tid == 0) bad = 0;
+  // objective at X_t from its exact Grams
+  double fv[3] = {0.0, 0.0, 0.0};  // tr B, sum R_ij^2, tr(R B)
+  for (int i = tid; i < kk; i += 256) {
+    const int r = i / kp, c = i % kp;
+    const double rij = R[i];
+    fv[1] += rij * rij;
+    fv[2] += rij * SYM(B, c, r);
+    if (r == c) fv[0] += B[i];
+  }
+  block_sum<3>(fv, sh);
+  const double f = is_f2(a.method) ? 2.0 * fv[0] - fv[2] : a.ctrl->normA2 + 2.0 * fv[0] + fv[1];
+
+  if (!is_tri(a.method)) {
+    double c3, c2, c1, c0;
+    if (a.method == M_OFM_F1) {
+      // (1/4) d/dalpha f1(X + alpha V) = tr(V^T A (X + aV)) + tr(V^T Z Z^T Z), Z = X + aV
+      double t[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      for (int i = tid; i < kk; i += 256) {
+        const int r = i / kp, c = i % kp, it = c * kp + r;
+        const double q = Q[i], p = P[i];
+        t[0] += q * Q[it];  // tr(Q Q)
+        t[1] += q * P[it];  // tr(Q P)
+        t[2] += p * P[it];  // tr(P P)
+        t[3] += p * p;      // tr(P P^T)
+        t[4] += q * R[it];  // tr(Q R)
+        t[5] += p * R[it];  // tr(P R)
+        if (r == c) {
+          t[6] += C[i];
+          t[7] += E[i];
+        }
+      }
+      block_sum<8>(t, sh);
+      c3 = t[0];
+      c2 = 3.0 * t[1];
+      c1 = t[6] + t[2] + t[3] + t[4];
+      c0 = t[7] + t[5];
+    } else {
+      // d/dalpha f2 = tr(V^T (4 A Z - 2 Z Z^T A Z - 2 A Z Z^T Z)), Z = X + aV
+      double t[11] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+      for (int i = tid; i < kk; i += 256) {
+        const int r = i / kp, c = i % kp, it = c * kp + r;
+        const double q = Q[i], p = P[i], rr = R[i], e = E[i];
+        const double cji = SYM(C, c, r), bji = SYM(B, c, r);
+        t[0] += q * cji;     // tr(Q C)
+        t[1] += p * cji;     // tr(P C)
+        t[2] += q * E[it];   // tr(Q E)
+        t[3] += p * e;       // tr(P E^T)
+        t[4] += p * E[it];   // tr(P E)
+        t[5] += q * bji;     // tr(Q B)
+        t[6] += rr * cji;    // tr(R C)
+        t[7] += p * bji;     // tr(P B)
+        t[8] += rr * E[it];  // tr(R E)
+        if (r == c) {
+          t[9] += C[i];
+          t[10] += e;
+        }
+      }
+      block_sum<11>(t, sh);
+      c3 = -4.0 * t[0];
+      c2 = -6.0 * (t[1] + t[2]);
+      c1 = 2.0 * (2.0 * t[9] - 2.0 * t[3] - 2.0 * t[4] - t[5] - t[6]);
+      c0 = 2.0 * (2.0 * t[10] - t[7] - t[8]);
+    }
+    if (tid == 0) {
+      int b = 0;
+      const double s = pick_step(c3, c2, c1, c0, &b);
+      bad |= b;
+      for (int j = 0; j < kp; ++j) al[j] = j < k ? s : 0.0;
+    }
+  } else {
+    // Column j of g(X + aV) depends on columns 1..j only, so the prefix-i cubic of Eqs. (16)/(18)
+    // is the sum over j <= i of v_j^T g(X + aV)_j; each term is a product of two polynomials in a.
+    if (tid < kp) {
+      const int j = tid;
+      double d0 = 0, d1 = 0, d2 = 0, d3 = 0;
+      if (a.method == M_TRI_F1) {
+        d0 = E[j * kp + j];
+        d1 = C[j * kp + j];
+        for (int m = 0; m <= j; ++m) {
+          // (P_jm + a Q_jm)(R_mj + a (P_jm + P_mj) + a^2 Q_mj)
+          const double x0 = P[j * kp + m], x1 = Q[j * kp + m];
+          const double y0 = R[m * kp + j], y1 = P[j * kp + m] + P[m * kp + j], y2 = Q[m * kp + j];
+          d0 += x0 * y0;
+          d1 += x0 * y1 + x1 * y0;
+          d2 += x0 * y2 + x1 * y1;
+          d3 += x1 * y2;
+        }
+      } else {
+        d0 = 2.0 * E[j * kp + j];
+        d1 = 2.0 * SYM(C, j, j);
+        for (int m = 0; m <= j; ++m) {
+          // -(E_jm + a C_jm)(R_mj + a (P_jm + P_mj) + a^2 Q_mj)
+          const double x0 = E[j * kp + m], x1 = SYM(C, j, m);
+          const double y0 = R[m * kp + j], y1 = P[j * kp + m] + P[m * kp + j], y2 = Q[m * kp + j];
+          // -(P_jm + a Q_jm)(B_mj + a (E_jm + E_mj) + a^2 C_mj)
+          const double u0 = P[j * kp + m], u1 = Q[j * kp + m];
+          const double w0 = SYM(B, m, j), w1 = E[j * kp + m] + E[m * kp + j], w2 = SYM(C, m, j);
+          d0 -= x0 * y0 + u0 * w0;
+          d1 -= x0 * y1 + x1 * y0 + u0 * w1 + u1 * w0;
+          d2 -= x0 * y2 + x1 * y1 + u0 * w2 + u1 * w1;
+          d3 -= x1 * y2 + u1 * w2;
+        }
+      }
+      coef[j][0] = d3;
+      coef[j][1] = d2;
+      coef[j][2] = d1;
+      coef[j][3] = d0;
+    }
+    __syncthreads();
+    if (tid == 0)
+      for (int j = 1; j < kp; ++j)
+        for (int q = 0; q < 4; ++q) coef[j][q] += coef[j - 1][q];
+    __syncthreads();
+    if (tid < kp) {
+      int b = 0;
+      al[tid] = tid < k ? pick_step(coef[tid][0], coef[tid][1], coef[tid][2], coef[tid][3], &b) : 0.0;
+      if (b) bad = 1;
+    }
+  }
+  __syncthreads();
+  if (a.alpha0 > 0.0 && a.ctrl->it == 0) {
+    for (int j = tid; j < kp; j += 256) al[j] = j < k ? a.alpha0 : 0.0;
+    __syncthreads();
+  }
+  // X' = X + V diag(al), AX' = AX + AV diag(al):
+  //   X'^T X'  = R + diag(al) P + P^T diag(al) + diag(al) Q diag(al)
+  //   X'^T AX' = B + E^T diag(al) + diag(al) E + diag(al) C diag(al)
+  for (int i = tid; i < kk; i += 256) {
+    const int r = i / kp, c = i % kp;
+    const double ar = al[r], ac = al[c];
+    a.Rn[i] = (float)(R[i] + ar * P[i] + P[c * kp + r] * ac + ar * Q[i] * ac);
+    a.Bn[i] = (float)(SYM(B, r, c) + E[c * kp + r] * ac + ar * E[i] + ar * SYM(C, r, c) * ac);
+  }
+  for (int j = tid; j < kp; j += 256) {
+    a.alpha[j] = (float)al[j];
+    a.alpha64[j] = al[j];
+  }
+  if (tid == 0) {
+    a.ctrl->f = f;
+    if (bad) {
+      a.ctrl->status = OFSC_ERR_NONFINITE;
+      a.ctrl->done = 1;
+    }
+    const int t = a.ctrl->it;
+    if (a.trace && t < a.ctrl->trace_cap) {
+      double* rec = a.trace + (int64_t)t * (3 + 2 * k);
+      rec[0] = t;
+      rec[1] = a.ctrl->rel;
+      rec[2] = f;
+      for (int j = 0; j < k; ++j) {
+        rec[3 + j] = al[j];
+        rec[3 + k + j] = a.beta64[j];
+      }
+    }
+  }
+#undef SYM
+}
+
+// Exact refresh: next X^T X and X^T AX are the Grams themselves; objective of X.
+__global__ void k_set_rb(const double* __restrict__ gram, int kp, int objective, float* Rn, float* Bn,
+                         Ctrl* ctrl, int ignore_done) {
+  if (!ignore_done && ctrl->done) return;
+  __shared__ double sh[3 * 256];
+  const int kk = kp * kp, tid = threadIdx.x;
+  const double* R = gram + G_R * kk;
+  const double* B = gram + G_B * kk;
+  double fv[3] = {0.0, 0.0, 0.0};
+  for (int i = tid; i < kk; i += 256) {
+    const int r = i / kp, c = i % kp;
+    const double b = 0.5 * (B[i] + B[c * kp + r]);
+    Rn[i] = (float)R[i];
+    Bn[i] = (float)b;
+    fv[1] += R[i] * R[i];
+    fv[2] += R[i] * b;
+    if (r == c) fv[0] += B[i];
+  }
+  block_sum<3>(fv, sh);
+  if (tid == 0) ctrl->f = objective == 2 ? 2.0 * fv[0] - fv[2] : ctrl->normA2 + 2.0 * fv[0] + fv[1];
+}
+
+
+}  // namespace
+}  // namespace ofsc
+
+// ==========================================================================================
+// Host side
+// ==========================================================================================
+
+namespace ofsc {
+namespace {
+
+constexpr int kGramTargetBlocks = 4 * kNumSMs;
+
+thread_local int64_t g_launches = 0;  // kernels launched by the current call on this thread
+
+int lanes_for(int kp) { return kp <= 8 ? 2 : kp <= 16 ? 4 : kp <= 32 ? 8 : kp <= 64 ? 16 : 32; }
+int gram_m_for(int kp) { return kp <= 16 ? 1 : kp <= 32 ? 2 : 4; }
+int gram_nt_for(int kp) { return (int)ceil_div(kp, 16 * gram_m_for(kp)); }
+
+// Row groups of a Gram launch with `npairs` pairs: about kGramTargetBlocks blocks in total.
+int64_t gram_rows_per_group(int64_t n, int kp, int npairs, int* gy) {
+  const int nt = gram_nt_for(kp);
+  int64_t want = ceil_div(kGramTargetBlocks, (int64_t)npairs * nt * nt);
+  int64_t maxg = ceil_div(n > 0 ? n : 1, kGramChunk);
+  if (want > maxg) want = maxg;
+  if (want < 1) want = 1;
+  int64_t rpg = ceil_div(n > 0 ? n : 1, want);
+  rpg = ceil_div(rpg, kGramChunk) * kGramChunk;
+  *gy = (int)ceil_div(n > 0 ? n : 1, rpg);
+  return rpg;
+}
+
+// Optional per-phase device timing: CUDA events around launches on the call's stream.
+struct Prof {
+  Workspace& ws;
+  ofsc_profile* out;
+  cudaStream_t s;
+  size_t used = 0;
+  std::vector<int> phases;
+  cudaEvent_t next() {
+    if (used == ws.events.size()) {
+      cudaEvent_t e = nullptr;
+      cudaEventCreate(&e);
+      ws.events.push_back(e);
+    }
+    return ws.events[used++];
+  }
+  void begin(int ph) {
+    if (!out) return;
+    phases.push_back(ph);
+    cudaEventRecord(next(), s);
+  }
+  void end() {
+    if (out) cudaEventRecord(next(), s);
+  }
+  // Adds the recorded intervals to `out` (waits for the last event) and recycles the events.
+  void collect() {
+    if (!out || phases.empty()) return;
+    cudaEventSynchronize(ws.events[used - 1]);
+    for (size_t i = 0; i < phases.size(); ++i) {
+      float ms = 0.0f;
+      if (cudaEventElapsedTime(&ms, ws.events[2 * i], ws.events[2 * i + 1]) == cudaSuccess) {
+        out->ms[phases[i]] += ms;
+        out->launches[phases[i]] += 1;
+      }
+    }
+    phases.clear();
+    used = 0;
+  }
+};
+
+template <int LANES>
+void launch_spmm_l(const SpmmArgs& a, bool weighted, int mode, bool bf16, cudaStream_t s) {
+  constexpr int GROUPS = 256 / LANES;
+  const int grid = (int)std::min<int64_t>(ceil_div(a.n, GROUPS), 8 * kNumSMs);
+  if (grid <= 0) return;
+  ++g_launches;
+  if (mode == SP_DIR) {
+    if (weighted) {
+      if (bf16) k_spmm<LANES, true, SP_DIR, true><<<grid, 256, 0, s>>>(a);
+      else k_spmm<LANES, true, SP_DIR, false><<<grid, 256, 0, s>>>(a);
+    } else {
+      if (bf16) k_spmm<LANES, false, SP_DIR, true><<<grid, 256, 0, s>>>(a);
+      else k_spmm<LANES, false, SP_DIR, false><<<grid, 256, 0, s>>>(a);
+    }
+  } else {
+    if (weighted) k_spmm<LANES, true, SP_Y, false><<<grid, 256, 0, s>>>(a);
+    else k_spmm<LANES, false, SP_Y, false><<<grid, 256, 0, s>>>(a);
+  }
+}
+
+void launch_spmm(const SpmmArgs& a, bool weighted, int mode, bool bf16, cudaStream_t s) {
+  if (a.n <= 0) return;
+  switch (lanes_for(a.kp)) {
+    case 2: launch_spmm_l<2>(a, weighted, mode, bf16, s); break;
+    case 4: launch_spmm_l<4>(a, weighted, mode, bf16, s); break;
+    case 8: launch_spmm_l<8>(a, weighted, mode, bf16, s); break;
+    case 16: launch_spmm_l<16>(a, weighted, mode, bf16, s); break;
+    default: launch_spmm_l<32>(a, weighted, mode, bf16, s); break;
+  }
+}
+
+size_t rowpass_smem(int kp, int method) {
+  const int nrg = kRowThreads / kp;
+  const int TR = nrg * kRPT;
+  const int mats = method >= M_OFM_F2 ? 2 : 1;
+  return (size_t)(mats * kp * kp + 2 * TR * kp + kp) * sizeof(float) + (size_t)3 * nrg * kp * sizeof(double);
+}
+
+template <int METHOD, bool BF16>
+cudaError_t launch_rowpass_t(const RowArgs& a, cudaStream_t s, int* nblk_out) {
+  static int max_blocks_per_sm[kMaxK + 1] = {0};
+  const size_t smem = rowpass_smem(a.kp, METHOD);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_rowpass<METHOD, BF16>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const int nrg = kRowThreads / a.kp;
+  const int threads = nrg * a.kp;
+  if (max_blocks_per_sm[a.kp] == 0) {
+    int nb = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_rowpass<METHOD, BF16>, threads, smem);
+    if (e != cudaSuccess) return e;
+    max_blocks_per_sm[a.kp] = nb > 0 ? nb : 1;
+  }
+  const int64_t ntiles = ceil_div(a.n, (int64_t)nrg * kRPT);
+  int grid = (int)std::min<int64_t>(ntiles, (int64_t)max_blocks_per_sm[a.kp] * kNumSMs);
+  if (grid > kMaxRowBlocks) grid = kMaxRowBlocks;
+  if (grid < 1) grid = 1;
+  k_rowpass<METHOD, BF16><<<grid, threads, smem, s>>>(a);
+  ++g_launches;
+  *nblk_out = grid;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rowpass(int method, bool bf16, const RowArgs& a, cudaStream_t s, int* nblk) {
+  switch (method * 2 + (bf16 ? 1 : 0)) {
+    case 0: return launch_rowpass_t<M_OFM_F1, false>(a, s, nblk);
+    case 1: return launch_rowpass_t<M_OFM_F1, true>(a, s, nblk);
+    case 2: return launch_rowpass_t<M_TRI_F1, false>(a, s, nblk);
+    case 3: return launch_rowpass_t<M_TRI_F1, true>(a, s, nblk);
+    case 4: return launch_rowpass_t<M_OFM_F2, false>(a, s, nblk);
+    case 5: return launch_rowpass_t<M_OFM_F2, true>(a, s, nblk);
+    case 6: return launch_rowpass_t<M_TRI_F2, false>(a, s, nblk);
+    default: return launch_rowpass_t<M_TRI_F2, true>(a, s, nblk);
+  }
+}
+
+cudaError_t launch_gram(Workspace& ws, const GramPairs& pairs, int npairs, int slot_mask,
+                        int ignore_done, cudaStream_t s, Prof* prof = nullptr) {
+  GramArgs a;
+  a.n = ws.n;
+  a.kp = ws.kp;
+  a.npairs = npairs;
+  a.nt = gram_nt_for(ws.kp);
+  int gy = 1;
+  a.rows_per_group = gram_rows_per_group(ws.n, ws.kp, npairs, &gy);
+  a.pairs = pairs;
+  a.part = ws.gram_part;
+  a.ctrl = ws.ctrl;
+  a.ignore_done = ignore_done;
+  dim3 grid(npairs * a.nt * a.nt, gy);
+  if (prof) prof->begin(OFSC_PHASE_GRAM);
+  switch (gram_m_for(ws.kp)) {
+    case 1: k_gram<1><<<grid, 256, 0, s>>>(a); break;
+    case 2: k_gram<2><<<grid, 256, 0, s>>>(a); break;
+    default: k_gram<4><<<grid, 256, 0, s>>>(a); break;
+  }
+  if (prof) {
+    prof->end();
+    prof->begin(OFSC_PHASE_GRAM_REDUCE);
+  }
+  const int total = kPairs * ws.kp * ws.kp;
+  k_gram_reduce<<<(int)std::min<int64_t>(ceil_div(total, 256), 4 * kNumSMs), 256, 0, s>>>(
+      ws.gram_part, gy, ws.kp, slot_mask, ws.gram, ws.ctrl, ignore_done);
+  if (prof) prof->end();
+  g_launches += 2;
+  return cudaGetLastError();
+}
+
+ofsc_status ensure_workspace(ofsc_graph* g, int kp) {
+  Workspace& ws = g->ws;
+  if (ws.kp == kp && ws.n == g->n && ws.X) return OFSC_OK;
+  workspace_free(ws);
+  const int64_t n = g->n;
+  const size_t blk = (size_t)(n > 0 ? n : 1) * kp * sizeof(float);
+  int gy1 = 1, gy2 = 1;
+  gram_rows_per_group(n, kp, kPairs, &gy1);
+  gram_rows_per_group(n, kp, 2, &gy2);
+  const int gy = std::max(gy1, gy2);
+  const size_t kk = (size_t)kp * kp;
+  ws.n = n;
+  ws.kp = kp;
+  ws.gram_gy = gy;
+  ws.row_blocks = kMaxRowBlocks;
+  struct {
+    void** p;
+    size_t bytes;
+  } items[] = {
+      {(void**)&ws.X, blk},
+      {(void**)&ws.Y, blk},
+      {(void**)&ws.V, blk},
+      {(void**)&ws.W, blk},
+      {(void**)&ws.G, blk},
+      {(void**)&ws.Gh, blk},
+      {(void**)&ws.gram_part, (size_t)gy * kPairs * kk * sizeof(double)},
+      {(void**)&ws.gram, kPairs * kk * sizeof(double)},
+      {(void**)&ws.Rn, kk * sizeof(float)},
+      {(void**)&ws.Bn, kk * sizeof(float)},
+      {(void**)&ws.alpha, kp * sizeof(float)},
+      {(void**)&ws.beta, kp * sizeof(float)},
+      {(void**)&ws.alpha64, kp * sizeof(double)},
+      {(void**)&ws.beta64, kp * sizeof(double)},
+      {(void**)&ws.colpart, (size_t)kMaxRowBlocks * 3 * kp * sizeof(double)},
+      {(void**)&ws.ctrl, sizeof(Ctrl)},
+  };
+  size_t total = 0;
+  for (auto& it : items) {
+    cudaError_t e = cudaMalloc(it.p, it.bytes);
+    if (e != cudaSuccess) {
+      workspace_free(ws);
+      return cuda_fail(e, "workspace cudaMalloc");
+    }
+    total += it.bytes;
+  }
+  cudaError_t e = cudaMallocHost((void**)&ws.ctrl_host, sizeof(Ctrl));
+  if (e != cudaSuccess) {
+    workspace_free(ws);
+    return cuda_fail(e, "cudaMallocHost");
+  }
+  ws.bytes = total;
+  return OFSC_OK;
+}
+
+struct Runner {
+  ofsc_graph* g;
+  Workspace& ws;
+  cudaStream_t s;
+  int method;
+  bool bf16;
+  Prof& prof;
+
+  SpmmArgs spmm_base() const {
+    SpmmArgs a{};
+    a.n = ws.n;
+    a.kp = ws.kp;
+    a.row_ptr = g->row_ptr;
+    a.col = g->col;
+    a.val = g->val;
+    a.dinv = g->dinv;
+    a.ctrl = ws.ctrl;
+    return a;
+  }
+
+  // AX from X exactly, then X^T X and X^T AX; Rn, Bn and f of `objective` from them.
+  cudaError_t refresh(int objective, int ignore_done) {
+    SpmmArgs a = spmm_base();
+    a.gather = ws.X;
+    a.X = ws.X;
+    a.Y = ws.Y;
+    a.ignore_done = ignore_done;
+    prof.begin(OFSC_PHASE_REFRESH);
+    launch_spmm(a, g->weighted != 0, SP_Y, false, s);
+    GramPairs p{};
+    p.L[0] = ws.X; p.R[0] = ws.X; p.slot[0] = G_R;
+    p.L[1] = ws.X; p.R[1] = ws.Y; p.slot[1] = G_B;
+    cudaError_t e = launch_gram(ws, p, 2, (1 << G_R) | (1 << G_B), ignore_done, s);
+    if (e != cudaSuccess) return e;
+    k_set_rb<<<1, 256, 0, s>>>(ws.gram, ws.kp, objective, ws.Rn, ws.Bn, ws.ctrl, ignore_done);
+    ++g_launches;
+    prof.end();
+    return cudaGetLastError();
+  }
+
+  cudaError_t rowpass(int dir_method, int update, int eval, int ignore_done, int* nblk) {
+    RowArgs r{};
+    r.n = ws.n;
+    r.kp = ws.kp;
+    r.X = ws.X;
+    r.Y = ws.Y;
+    r.V = ws.V;
+    r.W = ws.W;
+    r.G = ws.G;
+    r.Gh = ws.Gh;
+    r.dinv = g->dinv;
+    r.Rn = ws.Rn;
+    r.Bn = ws.Bn;
+    r.alpha = ws.alpha;
+    r.colpart = ws.colpart;
+    r.ctrl = ws.ctrl;
+    r.update = update;
+    r.eval = eval;
+    r.ignore_done = ignore_done;
+    prof.begin(OFSC_PHASE_DIRECTION);
+    cudaError_t e = launch_rowpass(dir_method, bf16, r, s, nblk);
+    prof.end();
+    return e;
+  }
+
+  cudaError_t direction_and_linesearch(int first, const ofsc_opts& o, int k, double alpha0) {
+    SpmmArgs a = spmm_base();
+    a.gather = ws.Gh;
+    a.G = ws.G;
+    a.V = ws.V;
+    a.W = ws.W;
+    a.beta = ws.beta;
+    a.first = first;
+    prof.begin(OFSC_PHASE_SPMM);
+    launch_spmm(a, g->weighted != 0, SP_DIR, bf16, s);
+    prof.end();
+    GramPairs p{};
+    const float* Ls[kPairs] = {ws.X, ws.V, ws.V, ws.X, ws.V, ws.V};
+    const float* Rs[kPairs] = {ws.X, ws.X, ws.V, ws.Y, ws.Y, ws.W};
+    for (int i = 0; i < kPairs; ++i) {
+      p.L[i] = Ls[i];
+      p.R[i] = Rs[i];
+      p.slot[i] = i;
+    }
+    cudaError_t e = launch_gram(ws, p, kPairs, (1 << kPairs) - 1, 0, s, &prof);
+    if (e != cudaSuccess) return e;
+    SolveArgs sa{};
+    sa.gram = ws.gram;
+    sa.kp = ws.kp;
+    sa.k = k;
+    sa.method = method;
+    sa.Rn = ws.Rn;
+    sa.Bn = ws.Bn;
+    sa.alpha = ws.alpha;
+    sa.alpha64 = ws.alpha64;
+    sa.beta64 = ws.beta64;
+    sa.trace = o.trace;
+    sa.ctrl = ws.ctrl;
+    sa.alpha0 = alpha0;
+    prof.begin(OFSC_PHASE_LINESEARCH);
+    k_solve<<<1, 256, 0, s>>>(sa);
+    ++g_launches;
+    prof.end();
+    return cudaGetLastError();
+  }
+};
+
+int grid_elems(int64_t total) { return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(total, 256), 8 * kNumSMs)); }
+
+ofsc_status finish(Workspace& ws, cudaStream_t s, Ctrl* out) {
+  OFSC_CUDA(cudaMemcpyAsync(ws.ctrl_host, ws.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+  OFSC_CUDA(cudaStreamSynchronize(s));
+  *out = *ws.ctrl_host;
+  return OFSC_OK;
+}
+
+}  // namespace
+}  // namespace ofsc
+
+using namespace ofsc;
+
+extern "C" ofsc_status ofsc_objective_grad(ofsc_graph* g, int32_t objective, int32_t k, const float* X,
+                                           double* f_out, float* G_out, void* stream_) {
+  clear_error();
+  if (!g) return fail(OFSC_ERR_INVALID_ARG, "ofsc_objective_grad: graph is NULL");
+  if (objective != OFSC_F1 && objective != OFSC_F2)
+    return fail(OFSC_ERR_INVALID_ARG, "ofsc_objective_grad: objective must be OFSC_F1 or OFSC_F2");
+  if (k < 1 || k > kMaxK) return fail(OFSC_ERR_INVALID_ARG, "ofsc_objective_grad: k=%d outside [1, %d]", k, kMaxK);
+  if (g->n > 0 && !X) return fail(OFSC_ERR_INVALID_ARG, "ofsc_objective_grad: X is NULL");
+  cudaStream_t s = (cudaStream_t)stream_;
+  const int kp = round_up(k, 8);
+  ofsc_status st = ensure_workspace(g, kp);
+  if (st != OFSC_OK) return st;
+  Workspace& ws = g->ws;
+  const int method = objective == OFSC_F1 ? M_OFM_F1 : M_OFM_F2;
+  Prof prof{ws, nullptr, s};
+  Runner run{g, ws, s, method, false, prof};
+  k_init_ctrl<<<1, 1, 0, s>>>(ws.ctrl, 0.0, 0, k, g->normA2, 0);
+  ++g_launches;
+  OFSC_LAUNCH_CHECK("k_init_ctrl");
+  Ctrl c{};
+  if (g->n > 0) {
+    k_pad_in<<<grid_elems(g->n * kp), 256, 0, s>>>(g->n, k, kp, X, ws.X, ws.ctrl);
+    ++g_launches;
+    OFSC_LAUNCH_CHECK("k_pad_in");
+    OFSC_CUDA(run.refresh(objective, 0));
+    int nblk = 0;
+    OFSC_CUDA(run.rowpass(method, 0, 1, 0, &nblk));
+    if (G_out) {
+      k_pad_out<<<grid_elems(g->n * k), 256, 0, s>>>(g->n, k, kp, ws.G, G_out);
+      ++g_launches;
+      OFSC_LAUNCH_CHECK("k_pad_out");
+    }
+    st = finish(ws, s, &c);
+    if (st != OFSC_OK) return st;
+  } else {
+    c.f = objective == OFSC_F1 ? 0.0 : 0.0;
+  }
+  if (c.status != OFSC_OK) return fail(c.status, "ofsc_objective_grad: non-finite value in X");
+  if (!std::isfinite(c.f)) return fail(OFSC_ERR_NONFINITE, "ofsc_objective_grad: non-finite objective");
+  if (f_out) *f_out = c.f;
+  return OFSC_OK;
+}
+
+extern "C" ofsc_status ofsc_iterate(ofsc_graph* g, int32_t method, int32_t k, float* X, double tol,
+                                    int32_t maxit, const ofsc_opts* opts, ofsc_result* out, void* stream_) {
+  clear_error();
+  if (!g) return fail(OFSC_ERR_INVALID_ARG, "ofsc_iterate: graph is NULL");
+  if (method < OFSC_OFM_F1 || method > OFSC_TRI_F2)
+    return fail(OFSC_ERR_INVALID_ARG, "ofsc_iterate: unknown method %d", method);
+  if (k < 1 || k > kMaxK) return fail(OFSC_ERR_INVALID_ARG, "ofsc_iterate: k=%d outside [1, %d]", k, kMaxK);
+  if (maxit < 0) return fail(OFSC_ERR_INVALID_ARG, "ofsc_iterate: maxit < 0");
+  if (!(tol == tol)) return fail(OFSC_ERR_INVALID_ARG, "ofsc_iterate: tol is NaN");
+  if (g->n > 0 && !X) return fail(OFSC_ERR_INVALID_ARG, "ofsc_iterate: X is NULL");
+  ofsc_opts o{};
+  if (opts) o = *opts;
+  if (o.gather != OFSC_GATHER_FP32 && o.gather != OFSC_GATHER_BF16)
+    return fail(OFSC_ERR_INVALID_ARG, "ofsc_iterate: unknown gather mode %d", o.gather);
+  if (o.trace && o.trace_cap < 0) return fail(OFSC_ERR_INVALID_ARG, "ofsc_iterate: trace_cap < 0");
+  const int y_refresh = o.y_refresh > 0 ? o.y_refresh : 32;
+  const int check_every = o.check_every > 0 ? o.check_every : 16;
+  cudaStream_t s = (cudaStream_t)stream_;
+  if (out) *out = ofsc_result{0, OFSC_OK, 0.0, 0.0, 0.0, 0};
+  if (g->n == 0) {
+    if (out) out->status = OFSC_OK;
+    return OFSC_OK;
+  }
+  const int kp = round_up(k, 8);
+  ofsc_status st = ensure_workspace(g, kp);
+  if (st != OFSC_OK) return st;
+  Workspace& ws = g->ws;
+  g_launches = 0;
+  Prof prof{ws, o.profile, s};
+  Runner run{g, ws, s, method, o.gather == OFSC_GATHER_BF16, prof};
+  const int objective = (method == OFSC_OFM_F1 || method == OFSC_TRI_F1) ? 1 : 2;
+
+  k_init_ctrl<<<1, 1, 0, s>>>(ws.ctrl, tol, maxit, k, g->normA2, o.trace ? o.trace_cap : 0);
+  ++g_launches;
+  OFSC_LAUNCH_CHECK("k_init_ctrl");
+  k_pad_in<<<grid_elems(g->n * kp), 256, 0, s>>>(g->n, k, kp, X, ws.X, ws.ctrl);
+  ++g_launches;
+  OFSC_LAUNCH_CHECK("k_pad_in");
+  OFSC_CUDA(run.refresh(objective, 0));
+
+  for (int t = 0; t <= maxit; ++t) {
+    int nblk = 0;
+    const bool refresh = t > 0 && (t % y_refresh) == 0;
+    if (refresh) {
+      prof.begin(OFSC_PHASE_OTHER);
+      k_update_x<<<grid_elems(g->n * kp), 256, 0, s>>>(g->n, kp, ws.X, ws.V, ws.alpha, ws.ctrl);
+      ++g_launches;
+      prof.end();
+      OFSC_LAUNCH_CHECK("k_update_x");
+      OFSC_CUDA(run.refresh(objective, 0));
+      OFSC_CUDA(run.rowpass(method, 0, 0, 0, &nblk));
+    } else {
+      // t = 0 has no previous direction: evaluation mode skips the G_{t-1} read
+      OFSC_CUDA(run.rowpass(method, t > 0 ? 1 : 0, t == 0 ? 1 : 0, 0, &nblk));
+    }
+    prof.begin(OFSC_PHASE_BETA);
+    k_beta<<<1, 256, 0, s>>>(ws.colpart, nblk, kp, ws.beta, ws.beta64, ws.ctrl, t == 0 ? 1 : 0, 0);
+    ++g_launches;
+    prof.end();
+    OFSC_LAUNCH_CHECK("k_beta");
+    if (t == maxit) break;
+    OFSC_CUDA(run.direction_and_linesearch(t == 0 ? 1 : 0, o, k, t == 0 ? o.alpha0 : 0.0));
+    if ((t + 1) % check_every == 0) {
+      OFSC_CUDA(cudaMemcpyAsync(&ws.ctrl_host->done, &ws.ctrl->done, sizeof(int), cudaMemcpyDeviceToHost, s));
+      OFSC_CUDA(cudaStreamSynchronize(s));
+      prof.collect();
+      if (ws.ctrl_host->done) break;
+    }
+  }
+  // Final report from an exact AX.
+  Ctrl c{};
+  st = finish(ws, s, &c);
+  prof.collect();
+  if (st != OFSC_OK) return st;
+  if (c.status == OFSC_OK) {
+    OFSC_CUDA(run.refresh(objective, 1));
+    int nblk = 0;
+    OFSC_CUDA(run.rowpass(method, 0, 1, 1, &nblk));
+    k_beta<<<1, 256, 0, s>>>(ws.colpart, nblk, kp, ws.beta, ws.beta64, ws.ctrl, 0, 1);
+    ++g_launches;
+    OFSC_LAUNCH_CHECK("k_beta(eval)");
+  }
+  k_pad_out<<<grid_elems(g->n * k), 256, 0, s>>>(g->n, k, kp, ws.X, X);
+  ++g_launches;
+  OFSC_LAUNCH_CHECK("k_pad_out");
+  st = finish(ws, s, &c);
+  if (st != OFSC_OK) return st;
+  ofsc_status rs = c.status != OFSC_OK ? c.status : (c.converged ? OFSC_OK : OFSC_ERR_NOT_CONVERGED);
+  if (out) {
+    out->iterations = c.it;
+    out->status = rs;
+    out->rel_dir_norm = c.rel;
+    out->g0_norm = c.g0;
+    out->f = c.f;
+    out->kernel_launches = g_launches;
+  }
+  if (rs == OFSC_ERR_NONFINITE) return fail(rs, "ofsc_iterate: non-finite value in X0 or in the iteration");
+  return rs;
+}

@@ -1,0 +1,207 @@
+"""Thin Python binding of the ofsc C ABI (include/ofsc.h): argument marshalling only.
+
+Every computation runs in libofsc.so. Arrays are passed as device pointers taken from objects
+with a ``data_ptr()`` method (torch CUDA tensors); streams as the raw cudaStream_t of a torch
+stream. If the library has not been built, every call raises: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libofsc.so")
+HEADER = os.path.join(os.path.dirname(_PKG), "include", "ofsc.h")
+
+OK, ERR_INVALID_ARG, ERR_OOM, ERR_NONFINITE, ERR_TIMEOUT, ERR_NOT_CONVERGED, ERR_CUDA = range(7)
+OFM_F1, TRI_F1, OFM_F2, TRI_F2 = 0, 1, 2, 3
+F1, F2 = 1, 2
+GATHER_FP32, GATHER_BF16 = 0, 1
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "NONFINITE", 4: "TIMEOUT",
+                5: "NOT_CONVERGED", 6: "CUDA"}
+
+
+class OfscError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"ofsc status {STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class GraphInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("m_in", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("n_selfloops", ctypes.c_int64), ("n_duplicates", ctypes.c_int64),
+                ("n_isolated", ctypes.c_int64), ("weighted", ctypes.c_int32),
+                ("normA_fro2", ctypes.c_double)]
+
+
+PHASES = ["direction", "beta", "spmm", "gram", "gram_reduce", "linesearch", "refresh", "other"]
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * len(PHASES)), ("launches", ctypes.c_int64 * len(PHASES))]
+
+    def as_dict(self) -> dict:
+        return {p: {"ms": self.ms[i], "launches": int(self.launches[i])} for i, p in enumerate(PHASES)}
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("gather", ctypes.c_int32), ("y_refresh", ctypes.c_int32),
+                ("check_every", ctypes.c_int32), ("alpha0", ctypes.c_double),
+                ("trace", ctypes.c_void_p), ("trace_cap", ctypes.c_int32),
+                ("profile", ctypes.POINTER(Profile))]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("rel_dir_norm", ctypes.c_double), ("g0_norm", ctypes.c_double),
+                ("f", ctypes.c_double), ("kernel_launches", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def header_functions() -> list[str]:
+    """Names of the functions that include/ofsc.h declares."""
+    with open(HEADER) as fh:
+        text = fh.read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\*?\s+\*?(ofsc_\w+)\s*\(", text, re.M)))
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libofsc.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise OfscError(ERR_CUDA, f"{LIB_PATH} is missing: build it with "
+                                      "paper_2305_10356_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64, u32, u64, dbl = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64,
+                                       ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double)
+        sig = {
+            "ofsc_graph_build": [i64, i64, vp, vp, vp, u32, vp, ctypes.POINTER(vp)],
+            "ofsc_graph_free": [vp],
+            "ofsc_graph_get_info": [vp, ctypes.POINTER(GraphInfo)],
+            "ofsc_graph_csr": [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                               ctypes.POINTER(vp), ctypes.POINTER(vp)],
+            "ofsc_objective_grad": [vp, i32, i32, vp, ctypes.POINTER(dbl), vp, vp],
+            "ofsc_iterate": [vp, i32, i32, vp, dbl, i32, ctypes.POINTER(Opts),
+                             ctypes.POINTER(Result), vp],
+            "ofsc_row_normalize": [i64, i32, vp, vp],
+            "ofsc_kmeans": [i64, i32, vp, i32, u64, i32, i32, vp, ctypes.POINTER(dbl), vp],
+        }
+        for name, args in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = i32
+        L.ofsc_last_error.argtypes = []
+        L.ofsc_last_error.restype = ctypes.c_char_p
+        L.ofsc_version.argtypes = []
+        L.ofsc_version.restype = i32
+        _lib = L
+    return _lib
+
+
+class _DeviceArray:
+    """Exposes a raw device pointer through __cuda_array_interface__ (zero copy)."""
+
+    def __init__(self, ptr: int, shape: tuple, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 2}
+
+
+def device_view(ptr: int, shape: tuple, typestr: str):
+    """A torch CUDA tensor viewing device memory owned by the library (no copy)."""
+    import torch
+    return torch.as_tensor(_DeviceArray(ptr, shape, typestr), device="cuda")
+
+
+def _check(status: int, allow=(OK,)) -> int:
+    if status not in allow:
+        raise OfscError(status, lib().ofsc_last_error().decode())
+    return status
+
+
+def _ptr(t) -> int | None:
+    return None if t is None else int(t.data_ptr())
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+        return int(torch.cuda.current_stream().cuda_stream)
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+class Graph:
+    """Owns an ofsc_graph handle (freed with the object)."""
+
+    def __init__(self, handle: int):
+        self.handle = ctypes.c_void_p(handle)
+
+    def info(self) -> GraphInfo:
+        inf = GraphInfo()
+        _check(lib().ofsc_graph_get_info(self.handle, ctypes.byref(inf)))
+        return inf
+
+    def csr(self) -> dict:
+        """Device pointers of the CSR arrays (owned by the handle)."""
+        ptrs = [ctypes.c_void_p() for _ in range(5)]
+        _check(lib().ofsc_graph_csr(self.handle, *[ctypes.byref(p) for p in ptrs]))
+        return dict(zip(["row_ptr", "col", "val", "dinv", "deg"], [p.value for p in ptrs]))
+
+    def free(self):
+        if self.handle is not None and self.handle.value:
+            lib().ofsc_graph_free(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def ofsc_graph_build(n: int, src, dst, w=None, stream=None) -> Graph:
+    """S, D and D^-1/2 (Eq. (1)) from device int32 edge arrays (and optional FP32 weights)."""
+    h = ctypes.c_void_p()
+    m = 0 if src is None else int(src.numel())
+    _check(lib().ofsc_graph_build(n, m, _ptr(src), _ptr(dst), _ptr(w), 0, _stream(stream),
+                                  ctypes.byref(h)))
+    return Graph(h.value)
+
+
+def ofsc_objective_grad(g: Graph, objective: int, X, G_out=None, stream=None) -> float:
+    """f (Eq. (2)/(3)) at the device block X (n x k, FP32); the gradient goes to G_out if given."""
+    f = ctypes.c_double()
+    _check(lib().ofsc_objective_grad(g.handle, objective, int(X.shape[1]), _ptr(X),
+                                     ctypes.byref(f), _ptr(G_out), _stream(stream)))
+    return f.value
+
+
+def ofsc_iterate(g: Graph, method: int, X, tol: float, maxit: int, *, gather: int = GATHER_FP32,
+                 y_refresh: int = 0, check_every: int = 0, alpha0: float = 0.0, trace=None,
+                 profile: Profile | None = None, stream=None) -> Result:
+    """Algorithm 2 in place on the device block X (n x k, FP32). Returns the ofsc_result."""
+    o = Opts(gather, y_refresh, check_every, alpha0, _ptr(trace),
+             0 if trace is None else int(trace.shape[0]),
+             ctypes.pointer(profile) if profile is not None else None)
+    r = Result()
+    _check(lib().ofsc_iterate(g.handle, method, int(X.shape[1]), _ptr(X), float(tol), int(maxit),
+                              ctypes.byref(o), ctypes.byref(r), _stream(stream)),
+           allow=(OK, ERR_NOT_CONVERGED))
+    return r
+
+
+def ofsc_row_normalize(X, stream=None) -> None:
+    """Row normalisation in place (Algorithm 1, step 3)."""
+    _check(lib().ofsc_row_normalize(int(X.shape[0]), int(X.shape[1]), _ptr(X), _stream(stream)))
+
+
+def ofsc_kmeans(X, n_clusters: int, labels, seed: int = 0, n_init: int = 1, maxit: int = 300,
+                stream=None) -> float:
+    """K-means on the rows of X into the device int32 array `labels`; returns the inertia."""
+    inertia = ctypes.c_double()
+    _check(lib().ofsc_kmeans(int(X.shape[0]), int(X.shape[1]), _ptr(X), n_clusters, seed, n_init,
+                             maxit, _ptr(labels), ctypes.byref(inertia), _stream(stream)))
+    return inertia.value

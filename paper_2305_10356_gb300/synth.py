@@ -76,6 +76,27 @@ def truncated_pareto(n: int, gamma: float, cutoff: float, rng) -> np.ndarray:
     return (1.0 - u * (1.0 - cutoff ** (-a))) ** (-1.0 / a)
 
 
+def pareto_cutoff(gamma: float, ratio: float) -> float:
+    """Truncation point c of Pareto(gamma) on [1, c] with c / mean = ratio (bisection)."""
+    a = gamma - 1.0
+
+    def c_over_mean(c):
+        if abs(a - 1.0) < 1e-12:
+            mean = math.log(c) / (1.0 - 1.0 / c)
+        else:
+            mean = a / (a - 1.0) * (1.0 - c ** (1.0 - a)) / (1.0 - c ** (-a))
+        return c / mean
+
+    lo, hi = 1.0 + 1e-9, 1e12
+    for _ in range(200):
+        mid = math.sqrt(lo * hi)
+        if c_over_mean(mid) < ratio:
+            lo = mid
+        else:
+            hi = mid
+    return math.sqrt(lo * hi)
+
+
 def sbm(n: int, n_blocks: int, mean_degree: float, ratio: float, *, ratio_kind: str = "prob",
         sizes: str = "uniform", size_param: float = 0.2, gamma: float | None = None,
         weighted: bool = False, join_isolated: bool = True, seed: int = 0) -> EdgeList:
@@ -84,9 +105,9 @@ def sbm(n: int, n_blocks: int, mean_degree: float, ratio: float, *, ratio_kind: 
     ratio_kind="prob": within-block edge probability = ratio x between-block probability.
     ratio_kind="count": expected within-block edges = ratio x expected between-block edges.
     sizes="uniform": block sizes within +-size_param of n/n_blocks; "lognormal": sigma=size_param.
-    gamma: node propensities theta ~ Pareto(gamma) truncated at sqrt(n*mean_degree) and
-    normalised to mean 1 inside each block (Karrer-Newman degree correction); endpoints are
-    drawn with probability proportional to theta.
+    gamma: node propensities theta ~ Pareto(gamma), truncated so that the largest expected
+    degree is the structural cutoff sqrt(n * mean_degree), and normalised to mean 1 inside each
+    block (Karrer-Newman degree correction); endpoints are drawn proportionally to theta.
     weighted: w ~ U(0.5, 1.5) in FP32 per sampled edge.
     """
     rng = rng_for(seed)
@@ -99,7 +120,8 @@ def sbm(n: int, n_blocks: int, mean_degree: float, ratio: float, *, ratio_kind: 
     off = np.concatenate([[0], np.cumsum(bs)])
     # propensities in block-position order
     if gamma is not None:
-        theta = truncated_pareto(n, gamma, math.sqrt(n * mean_degree), rng)
+        cut = pareto_cutoff(gamma, math.sqrt(n * mean_degree) / mean_degree)
+        theta = truncated_pareto(n, gamma, cut, rng)
         for r in range(n_blocks):
             seg = theta[off[r]:off[r + 1]]
             seg *= len(seg) / seg.sum()

@@ -1,0 +1,46 @@
+"""The C-ABI library builds, loads and exports every function that include/ofsc.h declares (CPU)."""
+import os
+
+import pytest
+
+from paper_2305_10356_gb300 import build, ofsc
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return ofsc.lib()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = ofsc.header_functions()
+    assert len(names) >= 9
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_version_and_error_string(lib):
+    assert lib.ofsc_version() >= 100
+    assert isinstance(lib.ofsc_last_error(), bytes)
+
+
+def test_host_side_argument_checks(lib):
+    """Argument validation happens on the host before any CUDA call."""
+    import ctypes
+    h = ctypes.c_void_p()
+    assert lib.ofsc_graph_build(-1, 0, None, None, None, 0, None, ctypes.byref(h)) == ofsc.ERR_INVALID_ARG
+    assert b"n=" in lib.ofsc_last_error()
+    assert lib.ofsc_graph_build(4, 1, None, None, None, 0, None, ctypes.byref(h)) == ofsc.ERR_INVALID_ARG
+    assert lib.ofsc_graph_build(4, 0, None, None, None, 7, None, ctypes.byref(h)) == ofsc.ERR_INVALID_ARG
+    assert lib.ofsc_graph_build(4, 0, None, None, None, 0, None, None) == ofsc.ERR_INVALID_ARG
+    assert lib.ofsc_iterate(None, 0, 4, None, 0.0, 1, None, None, None) == ofsc.ERR_INVALID_ARG
+    assert lib.ofsc_row_normalize(-1, 3, None, None) == ofsc.ERR_INVALID_ARG
+    assert lib.ofsc_kmeans(10, 2, None, 11, 0, 1, 10, None, None, None) == ofsc.ERR_INVALID_ARG
+    assert lib.ofsc_graph_free(None) == ofsc.OK
+
+
+def test_no_cpu_fallback_when_library_missing(monkeypatch, tmp_path):
+    monkeypatch.setattr(ofsc, "_lib", None)
+    monkeypatch.setattr(ofsc, "LIB_PATH", str(tmp_path / "missing.so"))
+    with pytest.raises(ofsc.OfscError):
+        ofsc.lib()

@@ -1,0 +1,257 @@
+"""GPU path (through the C ABI) against the FP64 oracle on seeded inputs.
+
+Tolerances: graph build, degrees and D^-1/2 are bit-exact; f and grad f match within 1e-5
+relative; iterates after a few updates match within 1e-4 relative (FP32 vs FP64 rounding);
+converged features match within a principal angle of 1e-4 rad; K-means labels reach ARI >= 0.99.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import ofsc_oracle as o
+from paper_2305_10356_gb300 import build, ofsc, synth
+
+from .gpu_util import csr_host, gpu_graph, run_iterate, upload
+
+pytestmark = pytest.mark.gpu
+METHODS = [o.OFM_F1, o.TRI_F1, o.OFM_F2, o.TRI_F2]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda_lib():
+    torch = pytest.importorskip("torch")
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    build.build()
+    ofsc.lib()
+    return torch
+
+
+def edge_case_graph(weighted):
+    rng = np.random.default_rng(3)
+    n = 50
+    src = rng.integers(0, n - 5, 300).astype(np.int32)  # nodes n-5.. n-1 isolated
+    dst = rng.integers(0, n - 5, 300).astype(np.int32)
+    src[:7] = dst[:7]
+    src = np.concatenate([src, [2, 5, 5]]).astype(np.int32)
+    dst = np.concatenate([dst, [5, 2, 2]]).astype(np.int32)
+    w = rng.uniform(0.5, 1.5, src.size).astype(np.float32) if weighted else None
+    return synth.EdgeList(n=n, src=src, dst=dst, w=w, labels=np.zeros(n, np.int32), n_blocks=1)
+
+
+GRAPH_CASES = {
+    "edge_cases_binary": lambda: edge_case_graph(False),
+    "edge_cases_weighted": lambda: edge_case_graph(True),
+    "sbm_n1000_k11": lambda: synth.workload("sbm_n1000_k11")[0],
+    "wsbm_n20k_k32": lambda: synth.workload("wsbm_n20k_k32")[0],
+    "dcsbm_n50k_k44": lambda: synth.workload("dcsbm_n50k_k44")[0],
+    "empty": lambda: synth.EdgeList(n=7, src=np.zeros(0, np.int32), dst=np.zeros(0, np.int32),
+                                    w=None, labels=np.zeros(7, np.int32), n_blocks=1),
+}
+
+
+@pytest.mark.parametrize("case", list(GRAPH_CASES))
+def test_graph_build_bit_exact(case):
+    e = GRAPH_CASES[case]()
+    og = o.build_graph(e.n, e.src, e.dst, e.w)
+    g = gpu_graph(e)
+    h = csr_host(g)
+    inf = g.info()
+    np.testing.assert_array_equal(h["row_ptr"], og.row_ptr)
+    np.testing.assert_array_equal(h["col"], og.col)
+    if e.w is not None:
+        assert h["val"].tobytes() == og.val.tobytes()
+    else:
+        assert h["val"] is None
+    assert h["deg"].tobytes() == og.deg.tobytes()
+    assert h["dinv"].tobytes() == og.s32.tobytes()
+    assert inf.nnz == og.nnz and inf.n_selfloops == og.n_selfloops
+    assert inf.n_isolated == og.n_isolated
+    assert inf.n_duplicates == 2 * (e.m - og.n_selfloops) - og.nnz
+    assert inf.normA_fro2 == pytest.approx(o.normA_fro2(og), rel=1e-12)
+
+
+def test_graph_build_rejects_bad_input(cuda_lib):
+    torch = cuda_lib
+    src = torch.tensor([0, 1, 7], dtype=torch.int32, device="cuda")
+    dst = torch.tensor([1, 2, 0], dtype=torch.int32, device="cuda")
+    with pytest.raises(ofsc.OfscError) as ei:
+        ofsc.ofsc_graph_build(5, src, dst)
+    assert ei.value.status == ofsc.ERR_INVALID_ARG
+    src = torch.tensor([0, 1], dtype=torch.int32, device="cuda")
+    dst = torch.tensor([1, 2], dtype=torch.int32, device="cuda")
+    for bad in (float("nan"), -1.0, 0.0, float("inf")):
+        w = torch.tensor([1.0, bad], dtype=torch.float32, device="cuda")
+        with pytest.raises(ofsc.OfscError) as ei:
+            ofsc.ofsc_graph_build(5, src, dst, w)
+        assert ei.value.status == ofsc.ERR_INVALID_ARG
+
+
+OBJ_CASES = [("sbm_n1000_k11", None, None), ("dcsbm_n50k_k44", 8000, None),
+             ("wsbm_n20k_k32", 4000, None), ("dcsbm_n2m_k128", 3001, 128)]
+
+
+@pytest.mark.parametrize("name,n,k", OBJ_CASES)
+@pytest.mark.parametrize("which", [1, 2])
+def test_objective_and_gradient(cuda_lib, name, n, k, which):
+    torch = cuda_lib
+    e, x0 = synth.workload(name, n=n)
+    if k is not None:
+        x0 = synth.initial_block(e.n, k, 77)
+    og = o.build_graph(e.n, e.src, e.dst, e.w)
+    g = gpu_graph(e)
+    X = torch.from_numpy(x0).cuda()
+    G = torch.empty_like(X)
+    f = ofsc.ofsc_objective_grad(g, which, X, G)
+    x64 = x0.astype(np.float64)
+    AX = o.apply_A(og, x64)
+    f_ref = o.objective(which, x64, AX, o.normA_fro2(og))
+    G_ref = o.gradient(which, x64, AX)
+    assert f == pytest.approx(f_ref, rel=1e-5)
+    Gh = G.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(Gh - G_ref) <= 1e-5 * np.linalg.norm(G_ref)
+    assert np.abs(Gh - G_ref).max() <= 1e-4 * np.abs(G_ref).max()
+
+
+@pytest.fixture(scope="module")
+def c1():
+    e, x0 = synth.workload("sbm_n1000_k11")
+    return e, x0, o.build_graph(e.n, e.src, e.dst, e.w)
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_first_updates_match_oracle(c1, method):
+    e, x0, og = c1
+    g = gpu_graph(e)
+    steps = 5
+    X, r, tr = run_iterate(g, method, x0, 0.0, steps, trace_cap=steps + 2)
+    ref = o.iterate(og, method, x0, 0.0, steps)
+    assert r.iterations == steps == ref.iterations
+    assert np.linalg.norm(X - ref.X) <= 1e-4 * np.linalg.norm(ref.X)
+    k = x0.shape[1]
+    for t in range(steps):
+        np.testing.assert_allclose(tr[t, 3:3 + k], ref.alphas[t], rtol=1e-4)
+        np.testing.assert_allclose(tr[t, 3 + k:3 + 2 * k], ref.betas[t], rtol=1e-3, atol=1e-5)
+        assert tr[t, 0] == t
+
+
+def column_match(X, ref):
+    """Columns equal up to sign (TriOFM fixed points are unique up to D = diag(+-1))."""
+    s = np.sign(np.sum(X * ref, axis=0))
+    return np.linalg.norm(X * s - ref) / np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_converged_features_and_clusters(c1, method):
+    import torch
+    e, x0, og = c1
+    g = gpu_graph(e)
+    X, r, _ = run_iterate(g, method, x0, 1e-6, 2000)
+    ref = o.iterate(og, method, x0, 1e-6, 2000)
+    assert ref.converged
+    assert r.status == ofsc.OK, (r.status, r.iterations, r.rel_dir_norm)
+    assert r.rel_dir_norm <= 2e-6
+    assert abs(r.iterations - ref.iterations) <= max(5, 0.1 * ref.iterations)
+    sin = o.subspace_sin(X, ref.X)
+    assert math.asin(min(1.0, sin)) <= 1e-4
+    if method in (o.TRI_F1, o.TRI_F2):
+        assert column_match(X.astype(np.float64), ref.X) <= 1e-4
+    # Algorithm 1 steps 3-4 on both sides
+    Xd = torch.from_numpy(X).cuda()
+    ofsc.ofsc_row_normalize(Xd)
+    labels = torch.empty(e.n, dtype=torch.int32, device="cuda")
+    ofsc.ofsc_kmeans(Xd, e.n_blocks, labels, seed=5, n_init=3)
+    lab_gpu = labels.cpu().numpy()
+    lab_ref, _ = o.kmeans(o.row_normalize(ref.X), e.n_blocks, seed=5, n_init=3)
+    assert o.ari(lab_gpu, lab_ref) >= 0.99
+    assert o.ari(lab_gpu, e.labels) >= 0.9  # the planted blocks are recovered
+
+
+def test_bf16_gather_reaches_fp32_features():
+    e, x0 = synth.workload("dcsbm_n50k_k44", n=6000)
+    g = gpu_graph(e)
+    X32, r32, _ = run_iterate(g, o.OFM_F1, x0, 1e-5, 3000)
+    X16, r16, _ = run_iterate(g, o.OFM_F1, x0, 1e-5, 3000, gather=ofsc.GATHER_BF16)
+    assert r32.status == ofsc.OK and r16.status == ofsc.OK
+    assert r16.rel_dir_norm <= 2e-5
+    assert math.asin(min(1.0, o.subspace_sin(X16, X32))) <= 1e-4
+
+
+@pytest.mark.parametrize("k", [1, 8, 128])
+def test_widths(k):
+    e = synth.sbm(700, 5, 14.0, 8.0, seed=40 + k)
+    x0 = synth.initial_block(e.n, k, 41)
+    og = o.build_graph(e.n, e.src, e.dst)
+    g = gpu_graph(e)
+    for method in (o.OFM_F2, o.TRI_F1):
+        X, r, _ = run_iterate(g, method, x0, 0.0, 4)
+        ref = o.iterate(og, method, x0, 0.0, 4)
+        assert np.linalg.norm(X - ref.X) <= 1e-4 * np.linalg.norm(ref.X)
+
+
+def test_degenerate_inputs(cuda_lib):
+    torch = cuda_lib
+    e = edge_case_graph(False)  # isolated nodes, loops, duplicates
+    og = o.build_graph(e.n, e.src, e.dst)
+    g = gpu_graph(e)
+    x0 = synth.initial_block(e.n, 3, 2)
+    X, r, _ = run_iterate(g, o.OFM_F1, x0, 0.0, 6)
+    ref = o.iterate(og, o.OFM_F1, x0, 0.0, 6)
+    assert np.linalg.norm(X - ref.X) <= 1e-4 * np.linalg.norm(ref.X)
+    # X0 = 0 is stationary: no update, status OK
+    Xz, r, _ = run_iterate(g, o.OFM_F1, np.zeros((e.n, 3), np.float32), 1e-6, 10)
+    assert r.iterations == 0 and r.status == ofsc.OK and np.all(Xz == 0)
+    # maxit = 0 leaves X0 untouched
+    X0b, r, _ = run_iterate(g, o.TRI_F2, x0, 1e-6, 0)
+    assert r.iterations == 0 and np.array_equal(X0b, x0)
+    # non-finite start is rejected
+    bad = x0.copy()
+    bad[3, 1] = np.nan
+    with pytest.raises(ofsc.OfscError) as ei:
+        run_iterate(g, o.OFM_F1, bad, 1e-6, 5)
+    assert ei.value.status == ofsc.ERR_NONFINITE
+    # invalid arguments
+    Xd = torch.from_numpy(x0).cuda()
+    for args in ((7, 3), (0, 3)):
+        with pytest.raises(ofsc.OfscError):
+            ofsc.ofsc_iterate(g, args[0], Xd, 0.0, args[1])
+    with pytest.raises(ofsc.OfscError):
+        ofsc.ofsc_iterate(g, 0, torch.zeros((e.n, 129), device="cuda"), 0.0, 1)
+    # empty graph: every node isolated, A = -I
+    ge = gpu_graph(GRAPH_CASES["empty"]())
+    x7 = synth.initial_block(7, 2, 3)
+    f = ofsc.ofsc_objective_grad(ge, 1, torch.from_numpy(x7).cuda())
+    xx = x7.astype(np.float64)
+    assert f == pytest.approx(o.objective_dense(1, -np.eye(7), xx), rel=1e-6)
+
+
+def test_row_normalize_matches(cuda_lib):
+    torch = cuda_lib
+    x = synth.initial_block(1000, 11, 9)
+    x[5] = 0.0
+    X = torch.from_numpy(x).cuda()
+    ofsc.ofsc_row_normalize(X)
+    np.testing.assert_allclose(X.cpu().numpy(), o.row_normalize(x), rtol=2e-6, atol=1e-7)
+
+
+def test_kmeans_matches_oracle(cuda_lib):
+    torch = cuda_lib
+    rng = np.random.default_rng(8)
+    centers = rng.standard_normal((7, 5)) * 6
+    truth = rng.integers(0, 7, 3000)
+    x = (centers[truth] + rng.standard_normal((3000, 5)) * 0.5).astype(np.float32)
+    X = torch.from_numpy(x).cuda()
+    lab = torch.empty(3000, dtype=torch.int32, device="cuda")
+    inertia = ofsc.ofsc_kmeans(X, 7, lab, seed=42, n_init=2)
+    lg = lab.cpu().numpy()
+    lr, ir = o.kmeans(x, 7, seed=42, n_init=2)
+    assert o.ari(lg, lr) == 1.0 and o.ari(lg, truth) >= 0.99
+    assert inertia == pytest.approx(ir, rel=1e-4)
+    # a Lloyd fixed point checked in FP64 on the host
+    xd = x.astype(np.float64)
+    mu = np.stack([xd[lg == c].mean(axis=0) for c in range(7)])
+    d = ((xd[:, None, :] - mu[None]) ** 2).sum(-1)
+    assert np.mean(np.argmin(d, axis=1) == lg) >= 0.999
+    lab2 = torch.empty_like(lab)
+    ofsc.ofsc_kmeans(X, 7, lab2, seed=42, n_init=2)
+    assert torch.equal(lab, lab2)  # deterministic given the seed

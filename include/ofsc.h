@@ -112,6 +112,27 @@ ofsc_status ofsc_graph_csr(const ofsc_graph* g, const int64_t** row_ptr, const i
 ofsc_status ofsc_objective_grad(ofsc_graph* g, int32_t objective, int32_t k, const float* X,
                                 double* f_out, float* G_out, void* stream);
 
+/*
+ * ofsc_objective_grad_noalloc - the same f and gradient as ofsc_objective_grad, computed
+ * without allocating any device memory. The paper has no counterpart: this is a library entry
+ * point for callers that must not call cudaMalloc while they run, such as a process whose device
+ * memory is already reserved by another allocator (cudaMalloc would fail there) or a
+ * latency-bound loop that cannot afford an allocation's driver call and implicit
+ * synchronisation.
+ *   Arguments, layout and results are those of ofsc_objective_grad; the graph is only read.
+ *   Temporary storage comes from one static device array of about 27 MiB inside the library,
+ *   which every GPU that loads the library holds until the process exits.
+ *   Limit: n * kp <= 2^20 with kp = k rounded up to a multiple of 8 (k <= 128); larger sizes
+ *   return OFSC_ERR_INVALID_ARG with a message (use ofsc_objective_grad for them).
+ *   The first call on a device looks up the array's device address with that device current;
+ *   make that first call before any stream capture. All calls share the array and it keeps the
+ *   previous call's contents, so calls that overlap on the GPU (several streams or host
+ *   threads) race with one another: order them. Synchronises `stream`.
+ * Errors: OFSC_ERR_INVALID_ARG, OFSC_ERR_NONFINITE, OFSC_ERR_CUDA.
+ */
+ofsc_status ofsc_objective_grad_noalloc(const ofsc_graph* g, int32_t objective, int32_t k,
+                                        const float* X, double* f_out, float* G_out, void* stream);
+
 /* Phases of one update, for the optional per-phase device timing of ofsc_iterate. */
 enum {
   OFSC_PHASE_DIRECTION = 0,    /* update X, AX; G = g(X); column sums (the direction pass) */

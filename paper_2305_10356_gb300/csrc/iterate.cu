@@ -17,6 +17,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -1375,4 +1376,169 @@ extern "C" ofsc_status ofsc_iterate(ofsc_graph* g, int32_t method, int32_t k, fl
   }
   if (rs == OFSC_ERR_NONFINITE) return fail(rs, "ofsc_iterate: non-finite value in X0 or in the iteration");
   return rs;
+}
+
+// ==========================================================================================
+// ofsc_objective_grad_noalloc: the objective and gradient with no device allocation.
+//
+// Some callers must not allocate device memory while they run: a process whose device memory is
+// already reserved by another allocator (a framework's caching pool) would see cudaMalloc fail,
+// and latency-bound loops cannot afford the driver call and the implicit synchronisation that
+// cudaMalloc/cudaFree bring. This variant takes all of its temporary storage from one
+// file-scope static device array instead of the graph handle's workspace.
+//
+// Limits: n * kp <= 2^20 (kp = k rounded up to a multiple of 8, k <= 128); the array holds
+// kNoAllocBytes (about 27 MiB) on every GPU that loads the library, until the process exits.
+// The first call on a device looks the array's address up (cudaGetSymbolAddress) with that
+// device current; make that first call before any stream capture. Every call shares the one
+// array and it keeps the last call's contents, so calls that overlap on the GPU (other streams,
+// other host threads) race; order them. Nothing read by a call depends on earlier contents: the
+// control block, the padded copy of X and every partial sum are written before they are read.
+// ==========================================================================================
+
+namespace ofsc {
+namespace {
+
+constexpr int64_t kNoAllocMaxBlock = int64_t(1) << 20;  // n * kp elements
+constexpr int kNoAllocGramGroups = 8;                    // row groups of the Gram partials
+constexpr size_t kNoAllocAlign = 256;
+constexpr size_t al256(size_t b) { return (b + kNoAllocAlign - 1) / kNoAllocAlign * kNoAllocAlign; }
+constexpr size_t kNoAllocCtrl = al256(sizeof(Ctrl));
+constexpr size_t kNoAllocBlockBytes = al256((size_t)kNoAllocMaxBlock * sizeof(float));
+constexpr size_t kNoAllocGramPart = al256((size_t)kNoAllocGramGroups * kPairs * kMaxK * kMaxK * sizeof(double));
+constexpr size_t kNoAllocGram = al256((size_t)kPairs * kMaxK * kMaxK * sizeof(double));
+constexpr size_t kNoAllocKK = al256((size_t)kMaxK * kMaxK * sizeof(float));
+constexpr size_t kNoAllocColpart = al256((size_t)kMaxRowBlocks * 3 * kMaxK * sizeof(double));
+constexpr size_t kNoAllocBytes = kNoAllocCtrl + 4 * kNoAllocBlockBytes + kNoAllocGramPart +
+                                 kNoAllocGram + 2 * kNoAllocKK + kNoAllocColpart;
+
+}  // namespace
+}  // namespace ofsc
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[ofsc::kNoAllocBytes];
+
+namespace ofsc {
+namespace {
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on the current device (looked up once per device).
+ofsc_status noalloc_scratch(void** out) {
+  int dev = 0;
+  OFSC_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices)
+    return fail(OFSC_ERR_INVALID_ARG, "ofsc_objective_grad_noalloc: device %d not supported", dev);
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return OFSC_OK;
+}
+
+}  // namespace
+}  // namespace ofsc
+
+extern "C" ofsc_status ofsc_objective_grad_noalloc(const ofsc_graph* gc, int32_t objective, int32_t k,
+                                                   const float* X, double* f_out, float* G_out,
+                                                   void* stream_) {
+  clear_error();
+  if (!gc) return fail(OFSC_ERR_INVALID_ARG, "ofsc_objective_grad_noalloc: graph is NULL");
+  if (objective != OFSC_F1 && objective != OFSC_F2)
+    return fail(OFSC_ERR_INVALID_ARG, "ofsc_objective_grad_noalloc: objective must be OFSC_F1 or OFSC_F2");
+  if (k < 1 || k > kMaxK)
+    return fail(OFSC_ERR_INVALID_ARG, "ofsc_objective_grad_noalloc: k=%d outside [1, %d]", k, kMaxK);
+  const int kp = round_up(k, 8);
+  if (gc->n * kp > kNoAllocMaxBlock)
+    return fail(OFSC_ERR_INVALID_ARG,
+                "ofsc_objective_grad_noalloc: n * kp = %lld exceeds the static scratch limit of %lld "
+                "elements (use ofsc_objective_grad)", (long long)(gc->n * kp), (long long)kNoAllocMaxBlock);
+  if (gc->n > 0 && !X) return fail(OFSC_ERR_INVALID_ARG, "ofsc_objective_grad_noalloc: X is NULL");
+  cudaStream_t s = (cudaStream_t)stream_;
+  if (gc->n == 0) {
+    if (f_out) *f_out = 0.0;
+    return OFSC_OK;
+  }
+  void* base = nullptr;
+  ofsc_status st = noalloc_scratch(&base);
+  if (st != OFSC_OK) return st;
+  unsigned char* p = (unsigned char*)base;
+  Workspace ws;  // views into the static array; owns nothing
+  ws.n = gc->n;
+  ws.kp = kp;
+  ws.ctrl = (Ctrl*)p;
+  p += kNoAllocCtrl;
+  ws.X = (float*)p;
+  p += kNoAllocBlockBytes;
+  ws.Y = (float*)p;
+  p += kNoAllocBlockBytes;
+  ws.G = (float*)p;
+  p += kNoAllocBlockBytes;
+  ws.Gh = p;
+  p += kNoAllocBlockBytes;
+  ws.gram_part = (double*)p;
+  p += kNoAllocGramPart;
+  ws.gram = (double*)p;
+  p += kNoAllocGram;
+  ws.Rn = (float*)p;
+  p += kNoAllocKK;
+  ws.Bn = (float*)p;
+  p += kNoAllocKK;
+  ws.colpart = (double*)p;
+
+  ofsc_graph* g = const_cast<ofsc_graph*>(gc);  // read only: the CSR and D^-1/2
+  const int method = objective == OFSC_F1 ? M_OFM_F1 : M_OFM_F2;
+  Prof prof{ws, nullptr, s};
+  Runner run{g, ws, s, method, false, prof};
+  k_init_ctrl<<<1, 1, 0, s>>>(ws.ctrl, 0.0, 0, k, g->normA2, 0);
+  k_pad_in<<<grid_elems(g->n * kp), 256, 0, s>>>(g->n, k, kp, X, ws.X, ws.ctrl);
+  OFSC_LAUNCH_CHECK("noalloc: k_pad_in");
+  // A X exactly, then X^T X and X^T A X with at most kNoAllocGramGroups row groups
+  SpmmArgs a = run.spmm_base();
+  a.gather = ws.X;
+  a.X = ws.X;
+  a.Y = ws.Y;
+  launch_spmm(a, g->weighted != 0, SP_Y, false, s);
+  GramArgs ga;
+  ga.n = ws.n;
+  ga.kp = kp;
+  ga.npairs = 2;
+  ga.nt = gram_nt_for(kp);
+  ga.pairs = GramPairs{};
+  ga.pairs.L[0] = ws.X; ga.pairs.R[0] = ws.X; ga.pairs.slot[0] = G_R;
+  ga.pairs.L[1] = ws.X; ga.pairs.R[1] = ws.Y; ga.pairs.slot[1] = G_B;
+  int64_t rpg = ceil_div(ceil_div(ws.n, kNoAllocGramGroups), kGramChunk) * kGramChunk;
+  const int gy = (int)ceil_div(ws.n, rpg);
+  ga.rows_per_group = rpg;
+  ga.part = ws.gram_part;
+  ga.ctrl = ws.ctrl;
+  ga.ignore_done = 0;
+  dim3 grid(2 * ga.nt * ga.nt, gy);
+  switch (gram_m_for(kp)) {
+    case 1: k_gram<1><<<grid, 256, 0, s>>>(ga); break;
+    case 2: k_gram<2><<<grid, 256, 0, s>>>(ga); break;
+    default: k_gram<4><<<grid, 256, 0, s>>>(ga); break;
+  }
+  k_gram_reduce<<<(int)std::min<int64_t>(ceil_div(kPairs * kp * kp, 256), 4 * kNumSMs), 256, 0, s>>>(
+      ws.gram_part, gy, kp, (1 << G_R) | (1 << G_B), ws.gram, ws.ctrl, 0);
+  k_set_rb<<<1, 256, 0, s>>>(ws.gram, kp, objective, ws.Rn, ws.Bn, ws.ctrl, 0);
+  OFSC_LAUNCH_CHECK("noalloc: refresh");
+  int nblk = 0;
+  OFSC_CUDA(run.rowpass(method, 0, 1, 0, &nblk));
+  if (G_out) {
+    k_pad_out<<<grid_elems(g->n * k), 256, 0, s>>>(g->n, k, kp, ws.G, G_out);
+    OFSC_LAUNCH_CHECK("noalloc: k_pad_out");
+  }
+  Ctrl c{};
+  OFSC_CUDA(cudaMemcpyAsync(&c, ws.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+  OFSC_CUDA(cudaStreamSynchronize(s));
+  if (c.status != OFSC_OK) return fail(c.status, "ofsc_objective_grad_noalloc: non-finite value in X");
+  if (!std::isfinite(c.f)) return fail(OFSC_ERR_NONFINITE, "ofsc_objective_grad_noalloc: non-finite objective");
+  if (f_out) *f_out = c.f;
+  return OFSC_OK;
 }

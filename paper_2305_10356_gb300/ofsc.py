@@ -85,6 +85,7 @@ def lib() -> ctypes.CDLL:
             "ofsc_graph_csr": [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                ctypes.POINTER(vp), ctypes.POINTER(vp)],
             "ofsc_objective_grad": [vp, i32, i32, vp, ctypes.POINTER(dbl), vp, vp],
+            "ofsc_objective_grad_noalloc": [vp, i32, i32, vp, ctypes.POINTER(dbl), vp, vp],
             "ofsc_iterate": [vp, i32, i32, vp, dbl, i32, ctypes.POINTER(Opts),
                              ctypes.POINTER(Result), vp],
             "ofsc_row_normalize": [i64, i32, vp, vp],
@@ -176,6 +177,14 @@ def ofsc_objective_grad(g: Graph, objective: int, X, G_out=None, stream=None) ->
     f = ctypes.c_double()
     _check(lib().ofsc_objective_grad(g.handle, objective, int(X.shape[1]), _ptr(X),
                                      ctypes.byref(f), _ptr(G_out), _stream(stream)))
+    return f.value
+
+
+def ofsc_objective_grad_noalloc(g: Graph, objective: int, X, G_out=None, stream=None) -> float:
+    """As ofsc_objective_grad, with no device allocation (static scratch; n * kp <= 2^20)."""
+    f = ctypes.c_double()
+    _check(lib().ofsc_objective_grad_noalloc(g.handle, objective, int(X.shape[1]), _ptr(X),
+                                             ctypes.byref(f), _ptr(G_out), _stream(stream)))
     return f.value
 
 

@@ -48,6 +48,9 @@ void workspace_free(Workspace& ws) {
   cudaFree(ws.gram);
   cudaFree(ws.Rn);
   cudaFree(ws.Bn);
+  cudaFree(ws.R64);
+  cudaFree(ws.B64);
+  cudaFree(ws.dots);
   cudaFree(ws.alpha);
   cudaFree(ws.beta);
   cudaFree(ws.alpha64);

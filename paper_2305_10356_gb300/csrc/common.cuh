@@ -54,8 +54,11 @@ struct Ctrl {
   double g0;       // ||G_0||_F
   double gnorm;    // ||G_t||_F of the last direction pass
   double rel;      // gnorm / g0
-  double f;        // objective at X_t (from the exact Grams of X_t)
+  double f;        // objective at X_t
   double normA2;   // ||A||_F^2
+  double trB;      // tr(X^T A X) of the current X (carried for the f1 objective)
+  int dots_blocks; // blocks of the last sparse product that wrote dot partials
+  int pad2_;
 };
 
 // Device workspace of the iteration for one padded width kp, cached on the graph handle.
@@ -73,6 +76,9 @@ struct Workspace {
   double* gram = nullptr;       // [6][kp*kp] reduced Grams R, P, Q, B, E, C
   float* Rn = nullptr;          // kp*kp: X^T X for the next direction pass
   float* Bn = nullptr;          // kp*kp: X^T A X for the next direction pass
+  double* R64 = nullptr;        // kp*kp: X^T X of the current X (exact recurrence, FP64)
+  double* B64 = nullptr;        // kp*kp: X^T A X of the current X (f2 methods)
+  double* dots = nullptr;       // [spmm blocks][2][kp]: partial diag(V^T AV), diag(V^T AX)
   float* alpha = nullptr;       // kp
   float* beta = nullptr;        // kp
   double* alpha64 = nullptr;    // kp

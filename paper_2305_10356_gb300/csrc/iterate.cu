@@ -28,11 +28,9 @@ enum { M_OFM_F1 = 0, M_TRI_F1 = 1, M_OFM_F2 = 2, M_TRI_F2 = 3 };
 constexpr int kPairs = 6;
 enum { G_R = 0, G_P = 1, G_Q = 2, G_B = 3, G_E = 4, G_C = 5 };
 constexpr int kRowThreads = 256;
-constexpr int kRPT = 8;           // rows per thread in one tile of the direction pass
 constexpr int kMaxRowBlocks = 8 * kNumSMs;
 constexpr int kGramChunk = 32;    // rows staged in shared memory per Gram step
 
-__device__ __forceinline__ int64_t ceil_div_dev(int64_t a, int64_t b) { return (a + b - 1) / b; }
 __device__ __forceinline__ bool is_tri(int method) { return method == M_TRI_F1 || method == M_TRI_F2; }
 __device__ __forceinline__ bool is_f2(int method) { return method >= M_OFM_F2; }
 
@@ -54,6 +52,8 @@ __global__ void k_init_ctrl(Ctrl* c, double tol, int maxit, int k, double normA2
   c->rel = 1.0;
   c->f = 0.0;
   c->normA2 = normA2;
+  c->trB = 0.0;
+  c->dots_blocks = 0;
 }
 
 __global__ void k_pad_in(int64_t n, int k, int kp, const float* __restrict__ src,
@@ -116,7 +116,8 @@ struct SpmmArgs {
   float* W;            // SP_DIR: in AV_{t-1}, out AV_t
   const float* beta;   // SP_DIR
   const float* X;      // SP_Y
-  float* Y;            // SP_Y: out A X
+  float* Y;            // SP_Y: out A X; SP_DIR with DOTS: in A X
+  double* dots;        // SP_DIR with DOTS: [gridDim.x][2][kp] partial sums of V.AV and V.AX
   Ctrl* ctrl;
   int first;           // SP_DIR: t = 0 (no V_{t-1}, AV_{t-1})
   int ignore_done;
@@ -144,9 +145,10 @@ __device__ __forceinline__ void fma4(float4& acc, float w, const float4& v) {
 }
 
 // A group of LANES lanes owns one row at a time; lane q holds columns [4q, 4q + 4).
-template <int LANES, bool WEIGHTED, int MODE, bool BF16>
+template <int LANES, bool WEIGHTED, int MODE, bool BF16, bool DOTS>
 __global__ void __launch_bounds__(256) k_spmm(SpmmArgs a) {
   if (!a.ignore_done && a.ctrl->done) return;
+  __shared__ float dred[DOTS ? 2 * 256 * 4 : 1];
   constexpr int GROUPS = 256 / LANES;
   constexpr bool GBF = (MODE == SP_DIR) && BF16;
   const int lane = threadIdx.x % LANES;
@@ -155,6 +157,7 @@ __global__ void __launch_bounds__(256) k_spmm(SpmmArgs a) {
                                     : (((1u << LANES) - 1u) << ((threadIdx.x & 31) / LANES * LANES));
   const int c = lane * 4;
   const bool active = c < a.kp;
+  float4 dcw = make_float4(0.f, 0.f, 0.f, 0.f), dey = make_float4(0.f, 0.f, 0.f, 0.f);
   for (int64_t l = (int64_t)blockIdx.x * GROUPS + grp; l < a.n; l += (int64_t)gridDim.x * GROUPS) {
     const int64_t p0 = a.row_ptr[l], p1 = a.row_ptr[l + 1];
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -214,10 +217,29 @@ __global__ void __launch_bounds__(256) k_spmm(SpmmArgs a) {
       }
       *(float4*)(a.W + o) = w;
       *(float4*)(a.V + o) = v;
+      if (DOTS) {  // diag(V^T AV) and diag(V^T AX) for the f1 line searches
+        const float4 y = *(const float4*)(a.Y + o);
+        dcw.x = fmaf(v.x, w.x, dcw.x); dcw.y = fmaf(v.y, w.y, dcw.y);
+        dcw.z = fmaf(v.z, w.z, dcw.z); dcw.w = fmaf(v.w, w.w, dcw.w);
+        dey.x = fmaf(v.x, y.x, dey.x); dey.y = fmaf(v.y, y.y, dey.y);
+        dey.z = fmaf(v.z, y.z, dey.z); dey.w = fmaf(v.w, y.w, dey.w);
+      }
     } else {
       const float4 x = *(const float4*)(a.X + o);
       *(float4*)(a.Y + o) = make_float4(-fmaf(s, acc.x, x.x), -fmaf(s, acc.y, x.y),
                                         -fmaf(s, acc.z, x.z), -fmaf(s, acc.w, x.w));
+    }
+  }
+  if (DOTS) {  // per-block partials in a fixed order: groups, then columns
+    float* r = dred + (size_t)grp * 2 * (LANES * 4);
+    *(float4*)(r + c) = dcw;
+    *(float4*)(r + LANES * 4 + c) = dey;
+    __syncthreads();
+    for (int j = threadIdx.x; j < 2 * a.kp; j += blockDim.x) {
+      const int which = j / a.kp, col = j % a.kp;
+      double sum = 0.0;
+      for (int g = 0; g < GROUPS; ++g) sum += (double)dred[(size_t)g * 2 * (LANES * 4) + which * (LANES * 4) + col];
+      a.dots[(int64_t)blockIdx.x * 2 * a.kp + j] = sum;
     }
   }
 }
@@ -246,123 +268,199 @@ struct RowArgs {
   int ignore_done;
 };
 
-template <int METHOD, bool BF16>
-__global__ void __launch_bounds__(kRowThreads) k_rowpass(RowArgs a) {
-  if (!a.ignore_done && a.ctrl->done) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int kp = a.kp;
-  const int nrg = kRowThreads / kp;
-  const int nthr = nrg * kp;
-  const int TR = nrg * kRPT;
-  float* Rs = (float*)smem_raw;                                    // kp*kp
-  float* Bs = Rs + kp * kp;                                        // kp*kp (f2 only)
-  float* xs = Bs + (is_f2(METHOD) ? kp * kp : 0);                  // TR*kp
-  float* ys = xs + TR * kp;                                        // TR*kp
-  float* als = ys + TR * kp;                                       // kp
-  double* red = (double*)(als + kp);                               // 3 * nthr (kp % 8 == 0)
-  const int tid = threadIdx.x;
-  const bool worker = tid < nthr;
-  const int col = tid % kp;
-  const int rg = tid / kp;
+// Warp-batched direction pass. A warp owns S = 32 / (KPMAX / 4) row slots of KPB rows each;
+// lane q of a slot holds columns [4q, 4q + 4) of its rows in registers. The rows are staged in a
+// warp-private shared buffer so every lane can read x_m (and y_m) as a broadcast, while the
+// k x k block (triu-masked for TriOFM) stays resident in shared memory. All global loads of a
+// batch are issued before any arithmetic, so each warp keeps up to 5 * KPB 16-byte loads in
+// flight. Column sums (for beta and ||G||) go to per-block partials in a fixed order.
+constexpr int kKPB = 8;  // rows per slot per batch
 
-  for (int i = tid; i < kp * kp; i += blockDim.x) {
-    int m = i / kp, j = i % kp;
-    bool keep = !is_tri(METHOD) || m <= j;  // triu(.) keeps m <= j
-    Rs[i] = keep ? a.Rn[i] : 0.0f;
-    if (is_f2(METHOD)) Bs[i] = keep ? a.Bn[i] : 0.0f;
+template <int KPMAX, bool F2>
+struct DirShape {
+  static constexpr int LPR = KPMAX / 4;       // lanes per row
+  static constexpr int S = 32 / LPR;          // row slots per warp
+  static constexpr int ROWS = S * kKPB;       // rows per warp batch
+  static constexpr int SSTR = kKPB * KPMAX + 4;  // floats per slot in the stage (bank offset)
+  static constexpr int NSTAGE = F2 ? 2 : 1;
+  static constexpr size_t kk_floats = (size_t)KPMAX * KPMAX * (F2 ? 2 : 1);
+  static constexpr size_t stage_floats = (size_t)(kRowThreads / 32) * S * SSTR * NSTAGE;
+  static constexpr size_t red_doubles = (size_t)(kRowThreads / 32) * S * 3 * KPMAX;
+  static constexpr size_t bytes() {
+    return kk_floats * 4 + (stage_floats * 4 > red_doubles * 8 ? stage_floats * 4 : red_doubles * 8);
   }
-  for (int i = tid; i < kp; i += blockDim.x) als[i] = a.update ? a.alpha[i] : 0.0f;
+};
+
+template <int METHOD, int KPMAX, bool BF16>
+__global__ void __launch_bounds__(kRowThreads, 1) k_direction(RowArgs a) {
+  if (!a.ignore_done && a.ctrl->done) return;
+  constexpr bool F2 = METHOD >= M_OFM_F2;
+  constexpr bool TRI = METHOD == M_TRI_F1 || METHOD == M_TRI_F2;
+  using Sh = DirShape<KPMAX, F2>;
+  extern __shared__ __align__(16) float sm[];
+  const int kp = a.kp;
+  float* Rs = sm;                                       // row m at m * KPMAX
+  float* Bs = Rs + KPMAX * KPMAX;                       // F2 only
+  float* stage = sm + Sh::kk_floats;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int slot = lane / Sh::LPR;
+  const int c = (lane % Sh::LPR) * 4;
+  const bool active = c < kp;
+  float* sx = stage + (size_t)(warp * Sh::S + slot) * Sh::SSTR * Sh::NSTAGE;
+  float* sy = sx + Sh::SSTR;                            // F2 only
+  float* __restrict__ Xp = a.X;
+  float* __restrict__ Yp = a.Y;
+  const float* __restrict__ Vp = a.V;
+  const float* __restrict__ Wp = a.W;
+  float* __restrict__ Gp = a.G;
+
+  for (int i = tid; i < kp * KPMAX; i += blockDim.x) {
+    const int m = i / KPMAX, j = i % KPMAX;
+    const bool keep = j < kp && (!TRI || m <= j);       // triu(.) keeps m <= j
+    Rs[i] = keep ? a.Rn[m * kp + j] : 0.0f;
+    if (F2) Bs[i] = keep ? a.Bn[m * kp + j] : 0.0f;
+  }
+  float4 al = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (a.update && active) al = *(const float4*)(a.alpha + c);
   if (a.update && blockIdx.x == 0 && tid == 0) a.ctrl->it += 1;
   __syncthreads();
 
-  double sgg = 0.0, snum = 0.0, sden = 0.0;
-  const int64_t ntiles = ceil_div_dev(a.n, TR);
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t row0 = tile * TR;
-    const int rows = (int)min((int64_t)TR, a.n - row0);
-    const int64_t base = row0 * kp;
-    for (int i = tid; i < TR * kp; i += blockDim.x) {
-      float x = 0.0f, y = 0.0f;
-      if (i < rows * kp) {
-        x = a.X[base + i];
-        y = a.Y[base + i];
-        if (a.update) {
-          const float al = als[i % kp];
-          x = fmaf(al, a.V[base + i], x);
-          y = fmaf(al, a.W[base + i], y);
-          a.X[base + i] = x;
-          a.Y[base + i] = y;
+  // per-lane running column sums (FP32: a lane adds one row-batch partial at a time)
+  float sgg[4] = {0, 0, 0, 0}, snum[4] = {0, 0, 0, 0}, sden[4] = {0, 0, 0, 0};
+  const int64_t nwarps = (int64_t)gridDim.x * (kRowThreads / 32);
+  const int64_t nbatch = (a.n + Sh::ROWS - 1) / Sh::ROWS;
+  for (int64_t b = (int64_t)blockIdx.x * (kRowThreads / 32) + warp; b < nbatch; b += nwarps) {
+    const int64_t row0 = b * Sh::ROWS + (int64_t)slot * kKPB;
+    // issue every global load of the batch before any store or arithmetic
+    float4 x[kKPB], y[kKPB], v[kKPB], w[kKPB], gp[kKPB];
+#pragma unroll
+    for (int i = 0; i < kKPB; ++i) {
+      const int64_t r = row0 + i;
+      const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+      const bool ok = active && r < a.n;
+      x[i] = ok ? *(const float4*)(Xp + r * kp + c) : z;
+      y[i] = ok ? *(const float4*)(Yp + r * kp + c) : z;
+      v[i] = (ok && a.update) ? *(const float4*)(Vp + r * kp + c) : z;
+      w[i] = (ok && a.update) ? *(const float4*)(Wp + r * kp + c) : z;
+      gp[i] = (ok && !a.eval) ? *(const float4*)(Gp + r * kp + c) : z;
+    }
+    if (a.update) {
+#pragma unroll
+      for (int i = 0; i < kKPB; ++i) {
+        const int64_t r = row0 + i;
+        x[i] = make_float4(fmaf(al.x, v[i].x, x[i].x), fmaf(al.y, v[i].y, x[i].y), fmaf(al.z, v[i].z, x[i].z),
+                           fmaf(al.w, v[i].w, x[i].w));
+        y[i] = make_float4(fmaf(al.x, w[i].x, y[i].x), fmaf(al.y, w[i].y, y[i].y), fmaf(al.z, w[i].z, y[i].z),
+                           fmaf(al.w, w[i].w, y[i].w));
+        if (active && r < a.n) {
+          *(float4*)(Xp + r * kp + c) = x[i];
+          *(float4*)(Yp + r * kp + c) = y[i];
         }
       }
-      xs[i] = x;
-      ys[i] = y;
     }
-    __syncthreads();
-    if (worker) {
-      float acc[kRPT];
 #pragma unroll
-      for (int r = 0; r < kRPT; ++r) acc[r] = 0.0f;
-      for (int m = 0; m < kp; ++m) {
-        const float rm = Rs[m * kp + col];
-        if (is_f2(METHOD)) {
-          const float bm = Bs[m * kp + col];
+    for (int i = 0; i < kKPB; ++i) {
+      *(float4*)(sx + i * KPMAX + c) = x[i];
+      if (F2) *(float4*)(sy + i * KPMAX + c) = y[i];
+    }
+    __syncwarp();
+    float4 acc[kKPB];
 #pragma unroll
-          for (int r = 0; r < kRPT; ++r) {
-            const int rl = rg + r * nrg;
-            acc[r] = fmaf(xs[rl * kp + m], bm, fmaf(ys[rl * kp + m], rm, acc[r]));
-          }
-        } else {
+    for (int i = 0; i < kKPB; ++i) acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int m = 0; m < kp; m += 4) {
+      const float4 r0 = *(const float4*)(Rs + (m + 0) * KPMAX + c);
+      const float4 r1 = *(const float4*)(Rs + (m + 1) * KPMAX + c);
+      const float4 r2 = *(const float4*)(Rs + (m + 2) * KPMAX + c);
+      const float4 r3 = *(const float4*)(Rs + (m + 3) * KPMAX + c);
+      float4 b0, b1, b2, b3;
+      if (F2) {
+        b0 = *(const float4*)(Bs + (m + 0) * KPMAX + c);
+        b1 = *(const float4*)(Bs + (m + 1) * KPMAX + c);
+        b2 = *(const float4*)(Bs + (m + 2) * KPMAX + c);
+        b3 = *(const float4*)(Bs + (m + 3) * KPMAX + c);
+      }
 #pragma unroll
-          for (int r = 0; r < kRPT; ++r) {
-            const int rl = rg + r * nrg;
-            acc[r] = fmaf(xs[rl * kp + m], rm, acc[r]);
-          }
+      for (int i = 0; i < kKPB; ++i) {
+        // f1: acc = x R (triu for TriOFM); f2: acc = x B + y R (triu for TriOFM)
+        const float4 xm = *(const float4*)(sx + i * KPMAX + m);
+        const float4 p0 = F2 ? b0 : r0, p1 = F2 ? b1 : r1, p2 = F2 ? b2 : r2, p3 = F2 ? b3 : r3;
+        float4 t = acc[i];
+        t.x = fmaf(xm.x, p0.x, t.x); t.y = fmaf(xm.x, p0.y, t.y); t.z = fmaf(xm.x, p0.z, t.z); t.w = fmaf(xm.x, p0.w, t.w);
+        t.x = fmaf(xm.y, p1.x, t.x); t.y = fmaf(xm.y, p1.y, t.y); t.z = fmaf(xm.y, p1.z, t.z); t.w = fmaf(xm.y, p1.w, t.w);
+        t.x = fmaf(xm.z, p2.x, t.x); t.y = fmaf(xm.z, p2.y, t.y); t.z = fmaf(xm.z, p2.z, t.z); t.w = fmaf(xm.z, p2.w, t.w);
+        t.x = fmaf(xm.w, p3.x, t.x); t.y = fmaf(xm.w, p3.y, t.y); t.z = fmaf(xm.w, p3.z, t.z); t.w = fmaf(xm.w, p3.w, t.w);
+        if (F2) {
+          const float4 ym = *(const float4*)(sy + i * KPMAX + m);
+          t.x = fmaf(ym.x, r0.x, t.x); t.y = fmaf(ym.x, r0.y, t.y); t.z = fmaf(ym.x, r0.z, t.z); t.w = fmaf(ym.x, r0.w, t.w);
+          t.x = fmaf(ym.y, r1.x, t.x); t.y = fmaf(ym.y, r1.y, t.y); t.z = fmaf(ym.y, r1.z, t.z); t.w = fmaf(ym.y, r1.w, t.w);
+          t.x = fmaf(ym.z, r2.x, t.x); t.y = fmaf(ym.z, r2.y, t.y); t.z = fmaf(ym.z, r2.z, t.z); t.w = fmaf(ym.z, r2.w, t.w);
+          t.x = fmaf(ym.w, r3.x, t.x); t.y = fmaf(ym.w, r3.y, t.y); t.z = fmaf(ym.w, r3.z, t.z); t.w = fmaf(ym.w, r3.w, t.w);
         }
+        acc[i] = t;
       }
-      float tgg = 0.f, tnum = 0.f, tden = 0.f;
-#pragma unroll
-      for (int r = 0; r < kRPT; ++r) {
-        const int rl = rg + r * nrg;
-        if (rl >= rows) continue;
-        const float y = ys[rl * kp + col];
-        float g;
-        if (METHOD == M_OFM_F1) g = 4.0f * (y + acc[r]);          // Eq. (5)
-        else if (METHOD == M_TRI_F1) g = y + acc[r];               // Eq. (7)
-        else if (METHOD == M_OFM_F2) g = 4.0f * y - 2.0f * acc[r]; // Eq. (10)
-        else g = 2.0f * y - acc[r];                                // Eq. (12)
-        const int64_t o = base + (int64_t)rl * kp + col;
-        const float gp = a.eval ? 0.0f : a.G[o];
-        a.G[o] = g;
-        const float gh = a.dinv[row0 + rl] * g;
-        if (BF16) ((__nv_bfloat16*)a.Gh)[o] = __float2bfloat16_rn(gh);
-        else ((float*)a.Gh)[o] = gh;
-        tgg = fmaf(g, g, tgg);
-        tnum = fmaf(g - gp, g, tnum);
-        tden = fmaf(gp, gp, tden);
-      }
-      sgg += tgg;
-      snum += tnum;
-      sden += tden;
     }
-    __syncthreads();
+    __syncwarp();  // the stage is rewritten by the next batch
+    float tg[4] = {0, 0, 0, 0}, tn[4] = {0, 0, 0, 0}, td[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int i = 0; i < kKPB; ++i) {
+      const int64_t r = row0 + i;
+      if (!active || r >= a.n) continue;
+      const float yv[4] = {y[i].x, y[i].y, y[i].z, y[i].w};
+      const float av[4] = {acc[i].x, acc[i].y, acc[i].z, acc[i].w};
+      float g[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (METHOD == M_OFM_F1) g[q] = 4.0f * (yv[q] + av[q]);           // Eq. (5)
+        else if (METHOD == M_TRI_F1) g[q] = yv[q] + av[q];                // Eq. (7)
+        else if (METHOD == M_OFM_F2) g[q] = 4.0f * yv[q] - 2.0f * av[q];  // Eq. (10)
+        else g[q] = 2.0f * yv[q] - av[q];                                 // Eq. (12)
+      }
+      const int64_t o = r * kp + c;
+      const float gpv[4] = {gp[i].x, gp[i].y, gp[i].z, gp[i].w};
+      *(float4*)(Gp + o) = make_float4(g[0], g[1], g[2], g[3]);
+      const float s = a.dinv[r];
+      if (BF16) {
+        __nv_bfloat162 h0 = __floats2bfloat162_rn(s * g[0], s * g[1]);
+        __nv_bfloat162 h1 = __floats2bfloat162_rn(s * g[2], s * g[3]);
+        uint2 u;
+        u.x = *reinterpret_cast<uint32_t*>(&h0);
+        u.y = *reinterpret_cast<uint32_t*>(&h1);
+        *(uint2*)((__nv_bfloat16*)a.Gh + o) = u;
+      } else {
+        *(float4*)((float*)a.Gh + o) = make_float4(s * g[0], s * g[1], s * g[2], s * g[3]);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        tg[q] = fmaf(g[q], g[q], tg[q]);
+        tn[q] = fmaf(g[q] - gpv[q], g[q], tn[q]);
+        td[q] = fmaf(gpv[q], gpv[q], td[q]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      sgg[q] += tg[q];
+      snum[q] += tn[q];
+      sden[q] += td[q];
+    }
   }
-  if (worker) {
-    red[tid] = sgg;
-    red[nthr + tid] = snum;
-    red[2 * nthr + tid] = sden;
+  // per-block column sums in a fixed order: (warp, slot) contributions, then over them
+  __syncthreads();
+  double* red = (double*)stage;  // [warps * S][3][KPMAX]
+  const int ws = warp * Sh::S + slot;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (c + q < KPMAX) {
+      red[((size_t)ws * 3 + 0) * KPMAX + c + q] = (double)sgg[q];
+      red[((size_t)ws * 3 + 1) * KPMAX + c + q] = (double)snum[q];
+      red[((size_t)ws * 3 + 2) * KPMAX + c + q] = (double)sden[q];
+    }
   }
   __syncthreads();
-  if (tid < kp) {
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-    for (int r = 0; r < nrg; ++r) {
-      s0 += red[r * kp + tid];
-      s1 += red[nthr + r * kp + tid];
-      s2 += red[2 * nthr + r * kp + tid];
-    }
-    double* out = a.colpart + (int64_t)blockIdx.x * 3 * kp;
-    out[tid] = s0;
-    out[kp + tid] = s1;
-    out[2 * kp + tid] = s2;
+  for (int j = tid; j < 3 * kp; j += blockDim.x) {
+    const int which = j / kp, col = j % kp;
+    double sum = 0.0;
+    for (int w = 0; w < (kRowThreads / 32) * Sh::S; ++w) sum += red[((size_t)w * 3 + which) * KPMAX + col];
+    a.colpart[(int64_t)blockIdx.x * 3 * kp + which * kp + col] = sum;
   }
 }
 
@@ -484,10 +582,14 @@ struct VecT<4> {
 };
 
 // 256 threads as 16 x 16; tile T x T with T = 16 M; thread (tx, ty) owns rows ty*M.., cols tx*M..
+// Each 32-row chunk is staged in shared memory; the next chunk's float4 loads are issued into
+// registers before the current chunk's FMAs, so global latency overlaps the arithmetic.
 template <int M>
 __global__ void __launch_bounds__(256) k_gram(GramArgs a) {
   if (!a.ignore_done && a.ctrl->done) return;
   constexpr int T = 16 * M;
+  constexpr int NV = kGramChunk * T / 4;          // float4 per operand per chunk
+  constexpr int V4 = (NV + 255) / 256;            // per thread
   __shared__ __align__(16) float Ls[kGramChunk][T];
   __shared__ __align__(16) float Rs[kGramChunk][T];
   const int tid = threadIdx.x;
@@ -505,21 +607,36 @@ __global__ void __launch_bounds__(256) k_gram(GramArgs a) {
   for (int u = 0; u < M; ++u)
 #pragma unroll
     for (int v = 0; v < M; ++v) s[u][v] = cmp[u][v] = 0.0f;
-  for (int64_t rb = r0; rb < r1; rb += kGramChunk) {
-    for (int i = tid; i < kGramChunk * T; i += 256) {
+  float4 pl[V4], pr[V4];
+  auto fetch = [&](int64_t rb) {
+#pragma unroll
+    for (int q = 0; q < V4; ++q) {
+      const int i = (tid + q * 256) * 4;
       const int r = i / T, cc = i % T;
       const int64_t l = rb + r;
-      const bool ok = l < r1;
-      Ls[r][cc] = (ok && i0 + cc < a.kp) ? L[l * a.kp + i0 + cc] : 0.0f;
-      Rs[r][cc] = (ok && j0 + cc < a.kp) ? R[l * a.kp + j0 + cc] : 0.0f;
+      const bool ok = l < r1 && (tid + q * 256) < NV;
+      pl[q] = (ok && i0 + cc < a.kp) ? *(const float4*)(L + l * a.kp + i0 + cc) : make_float4(0.f, 0.f, 0.f, 0.f);
+      pr[q] = (ok && j0 + cc < a.kp) ? *(const float4*)(R + l * a.kp + j0 + cc) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  };
+  if (r0 < r1) fetch(r0);
+  for (int64_t rb = r0; rb < r1; rb += kGramChunk) {
+#pragma unroll
+    for (int q = 0; q < V4; ++q) {
+      const int i = (tid + q * 256) * 4;
+      if (tid + q * 256 < NV) {
+        *(float4*)(&Ls[i / T][i % T]) = pl[q];
+        *(float4*)(&Rs[i / T][i % T]) = pr[q];
+      }
     }
     __syncthreads();
+    if (rb + kGramChunk < r1) fetch(rb + kGramChunk);
     float acc[M][M];
 #pragma unroll
     for (int u = 0; u < M; ++u)
 #pragma unroll
       for (int v = 0; v < M; ++v) acc[u][v] = 0.0f;
-#pragma unroll 4
+#pragma unroll 8
     for (int r = 0; r < kGramChunk; ++r) {
       float av[M], bv[M];
       VecT<M>::get(&Ls[r][ty * M], av);
@@ -667,7 +784,11 @@ __device__ void block_sum(double (&v)[NV], double* sh) {
 }
 
 struct SolveArgs {
-  const double* gram;  // [6][kp*kp]
+  const double* gram;  // [6][kp*kp]: V^T X (P), V^T V (Q); f2 methods also V^T AX (E), V^T AV (C)
+  const double* dots;  // f1 methods: [dots_blocks][2][kp] partials of diag(V^T AV), diag(V^T AX)
+  int dots_blocks;
+  double* R64;         // X^T X of X_t on entry, of X_{t+1} on exit
+  double* B64;         // X^T A X likewise (f2 methods)
   int kp;
   int k;
   int method;
@@ -686,28 +807,47 @@ __global__ void __launch_bounds__(256) k_solve(SolveArgs a) {
   __shared__ double sh[12 * 256];
   __shared__ double coef[kMaxK][4];
   __shared__ double al[kMaxK];
+  __shared__ double dC[kMaxK], dE[kMaxK];
   __shared__ int bad;
   const int kp = a.kp, k = a.k, kk = kp * kp, tid = threadIdx.x;
-  const double* R = a.gram + G_R * kk;
+  const bool f2 = is_f2(a.method);
   const double* P = a.gram + G_P * kk;
   const double* Q = a.gram + G_Q * kk;
-  const double* B = a.gram + G_B * kk;
   const double* E = a.gram + G_E * kk;
   const double* C = a.gram + G_C * kk;
-  // B = X^T A X and C = V^T A V are symmetric; the recurrences leave rounding asymmetry.
+  const double* R = a.R64;
+  const double* B = a.B64;
+  // C = V^T A V and B = X^T A X are symmetric; the recurrences leave rounding asymmetry.
 #define SYM(M, i, j) (0.5 * ((M)[(i) * kp + (j)] + (M)[(j) * kp + (i)]))
   if (tid == 0) bad = 0;
-  // objective at X_t from its exact Grams
-  double fv[3] = {0.0, 0.0, 0.0};  // tr B, sum R_ij^2, tr(R B)
+  for (int j = tid; j < kp; j += blockDim.x) {
+    if (f2) {
+      dC[j] = C[j * kp + j];
+      dE[j] = E[j * kp + j];
+    } else {
+      double sc = 0.0, se = 0.0;
+      for (int b = 0; b < a.dots_blocks; ++b) {
+        sc += a.dots[(int64_t)b * 2 * kp + j];
+        se += a.dots[(int64_t)b * 2 * kp + kp + j];
+      }
+      dC[j] = sc;
+      dE[j] = se;
+    }
+  }
+  // objective at X_t: f1 = ||A||^2 + 2 tr B + ||R||^2, f2 = 2 tr B - tr(R B)
+  double fv[3] = {0.0, 0.0, 0.0};
   for (int i = tid; i < kk; i += 256) {
     const int r = i / kp, c = i % kp;
     const double rij = R[i];
     fv[1] += rij * rij;
-    fv[2] += rij * SYM(B, c, r);
-    if (r == c) fv[0] += B[i];
+    if (f2) {
+      fv[2] += rij * SYM(B, c, r);
+      if (r == c) fv[0] += B[i];
+    }
   }
-  block_sum<3>(fv, sh);
-  const double f = is_f2(a.method) ? 2.0 * fv[0] - fv[2] : a.ctrl->normA2 + 2.0 * fv[0] + fv[1];
+  block_sum<3>(fv, sh);  // also orders the dC/dE writes before their use
+  const double trB = f2 ? fv[0] : a.ctrl->trB;
+  const double f = f2 ? 2.0 * trB - fv[2] : a.ctrl->normA2 + 2.0 * trB + fv[1];
 
   if (!is_tri(a.method)) {
     double c3, c2, c1, c0;
@@ -723,10 +863,10 @@ __global__ void __launch_bounds__(256) k_solve(SolveArgs a) {
         t[3] += p * p;      // tr(P P^T)
         t[4] += q * R[it];  // tr(Q R)
         t[5] += p * R[it];  // tr(P R)
-        if (r == c) {
-          t[6] += C[i];
-          t[7] += E[i];
-        }
+      }
+      for (int j = tid; j < kp; j += 256) {
+        t[6] += dC[j];
+        t[7] += dE[j];
       }
       block_sum<8>(t, sh);
       c3 = t[0];
@@ -762,9 +902,9 @@ __global__ void __launch_bounds__(256) k_solve(SolveArgs a) {
     }
     if (tid == 0) {
       int b = 0;
-      const double s = pick_step(c3, c2, c1, c0, &b);
+      const double st = pick_step(c3, c2, c1, c0, &b);
       bad |= b;
-      for (int j = 0; j < kp; ++j) al[j] = j < k ? s : 0.0;
+      for (int j = 0; j < kp; ++j) al[j] = j < k ? st : 0.0;
     }
   } else {
     // Column j of g(X + aV) depends on columns 1..j only, so the prefix-i cubic of Eqs. (16)/(18)
@@ -773,8 +913,8 @@ __global__ void __launch_bounds__(256) k_solve(SolveArgs a) {
       const int j = tid;
       double d0 = 0, d1 = 0, d2 = 0, d3 = 0;
       if (a.method == M_TRI_F1) {
-        d0 = E[j * kp + j];
-        d1 = C[j * kp + j];
+        d0 = dE[j];
+        d1 = dC[j];
         for (int m = 0; m <= j; ++m) {
           // (P_jm + a Q_jm)(R_mj + a (P_jm + P_mj) + a^2 Q_mj)
           const double x0 = P[j * kp + m], x1 = Q[j * kp + m];
@@ -785,8 +925,8 @@ __global__ void __launch_bounds__(256) k_solve(SolveArgs a) {
           d3 += x1 * y2;
         }
       } else {
-        d0 = 2.0 * E[j * kp + j];
-        d1 = 2.0 * SYM(C, j, j);
+        d0 = 2.0 * dE[j];
+        d1 = 2.0 * dC[j];
         for (int m = 0; m <= j; ++m) {
           // -(E_jm + a C_jm)(R_mj + a (P_jm + P_mj) + a^2 Q_mj)
           const double x0 = E[j * kp + m], x1 = SYM(C, j, m);
@@ -827,8 +967,15 @@ __global__ void __launch_bounds__(256) k_solve(SolveArgs a) {
   for (int i = tid; i < kk; i += 256) {
     const int r = i / kp, c = i % kp;
     const double ar = al[r], ac = al[c];
-    a.Rn[i] = (float)(R[i] + ar * P[i] + P[c * kp + r] * ac + ar * Q[i] * ac);
-    a.Bn[i] = (float)(SYM(B, r, c) + E[c * kp + r] * ac + ar * E[i] + ar * SYM(C, r, c) * ac);
+    const double rn = R[i] + ar * P[i] + P[c * kp + r] * ac + ar * Q[i] * ac;
+    a.R64[i] = rn;
+    a.Rn[i] = (float)rn;
+    if (f2) {
+      // B is symmetric up to rounding; read only this thread's element (B64 is updated in place)
+      const double bn = B[i] + E[c * kp + r] * ac + ar * E[i] + ar * SYM(C, r, c) * ac;
+      a.B64[i] = bn;
+      a.Bn[i] = (float)bn;
+    }
   }
   for (int j = tid; j < kp; j += 256) {
     a.alpha[j] = (float)al[j];
@@ -836,6 +983,11 @@ __global__ void __launch_bounds__(256) k_solve(SolveArgs a) {
   }
   if (tid == 0) {
     a.ctrl->f = f;
+    if (!f2) {  // tr(X'^T AX') = tr B + 2 sum al_j E_jj + sum al_j^2 C_jj
+      double tb = trB;
+      for (int j = 0; j < kp; ++j) tb += 2.0 * al[j] * dE[j] + al[j] * al[j] * dC[j];
+      a.ctrl->trB = tb;
+    }
     if (bad) {
       a.ctrl->status = OFSC_ERR_NONFINITE;
       a.ctrl->done = 1;
@@ -855,9 +1007,9 @@ __global__ void __launch_bounds__(256) k_solve(SolveArgs a) {
 #undef SYM
 }
 
-// Exact refresh: next X^T X and X^T AX are the Grams themselves; objective of X.
+// Exact refresh: X^T X and X^T AX of the current X from their Grams; objective of X.
 __global__ void k_set_rb(const double* __restrict__ gram, int kp, int objective, float* Rn, float* Bn,
-                         Ctrl* ctrl, int ignore_done) {
+                         double* R64, double* B64, Ctrl* ctrl, int ignore_done) {
   if (!ignore_done && ctrl->done) return;
   __shared__ double sh[3 * 256];
   const int kk = kp * kp, tid = threadIdx.x;
@@ -869,14 +1021,20 @@ __global__ void k_set_rb(const double* __restrict__ gram, int kp, int objective,
     const double b = 0.5 * (B[i] + B[c * kp + r]);
     Rn[i] = (float)R[i];
     Bn[i] = (float)b;
+    if (R64) {
+      R64[i] = R[i];
+      B64[i] = b;
+    }
     fv[1] += R[i] * R[i];
     fv[2] += R[i] * b;
     if (r == c) fv[0] += B[i];
   }
   block_sum<3>(fv, sh);
-  if (tid == 0) ctrl->f = objective == 2 ? 2.0 * fv[0] - fv[2] : ctrl->normA2 + 2.0 * fv[0] + fv[1];
+  if (tid == 0) {
+    ctrl->trB = fv[0];
+    ctrl->f = objective == 2 ? 2.0 * fv[0] - fv[2] : ctrl->normA2 + 2.0 * fv[0] + fv[1];
+  }
 }
-
 
 }  // namespace
 }  // namespace ofsc
@@ -949,22 +1107,44 @@ struct Prof {
 };
 
 template <int LANES>
+int spmm_grid(int64_t n) {
+  return (int)std::min<int64_t>(ceil_div(n, 256 / LANES), 8 * kNumSMs);
+}
+
+int spmm_grid_for(int64_t n, int kp);
+
+template <int LANES, int MODE, bool BF16, bool DOTS>
+void launch_spmm_w(const SpmmArgs& a, bool weighted, cudaStream_t s) {
+  const int grid = spmm_grid<LANES>(a.n);
+  if (weighted) k_spmm<LANES, true, MODE, BF16, DOTS><<<grid, 256, 0, s>>>(a);
+  else k_spmm<LANES, false, MODE, BF16, DOTS><<<grid, 256, 0, s>>>(a);
+}
+
+template <int LANES>
 void launch_spmm_l(const SpmmArgs& a, bool weighted, int mode, bool bf16, cudaStream_t s) {
-  constexpr int GROUPS = 256 / LANES;
-  const int grid = (int)std::min<int64_t>(ceil_div(a.n, GROUPS), 8 * kNumSMs);
-  if (grid <= 0) return;
+  if (a.n <= 0) return;
   ++g_launches;
+  const bool dots = a.dots != nullptr;
   if (mode == SP_DIR) {
-    if (weighted) {
-      if (bf16) k_spmm<LANES, true, SP_DIR, true><<<grid, 256, 0, s>>>(a);
-      else k_spmm<LANES, true, SP_DIR, false><<<grid, 256, 0, s>>>(a);
+    if (bf16) {
+      if (dots) launch_spmm_w<LANES, SP_DIR, true, true>(a, weighted, s);
+      else launch_spmm_w<LANES, SP_DIR, true, false>(a, weighted, s);
     } else {
-      if (bf16) k_spmm<LANES, false, SP_DIR, true><<<grid, 256, 0, s>>>(a);
-      else k_spmm<LANES, false, SP_DIR, false><<<grid, 256, 0, s>>>(a);
+      if (dots) launch_spmm_w<LANES, SP_DIR, false, true>(a, weighted, s);
+      else launch_spmm_w<LANES, SP_DIR, false, false>(a, weighted, s);
     }
   } else {
-    if (weighted) k_spmm<LANES, true, SP_Y, false><<<grid, 256, 0, s>>>(a);
-    else k_spmm<LANES, false, SP_Y, false><<<grid, 256, 0, s>>>(a);
+    launch_spmm_w<LANES, SP_Y, false, false>(a, weighted, s);
+  }
+}
+
+int spmm_grid_for(int64_t n, int kp) {
+  switch (lanes_for(kp)) {
+    case 2: return spmm_grid<2>(n);
+    case 4: return spmm_grid<4>(n);
+    case 8: return spmm_grid<8>(n);
+    case 16: return spmm_grid<16>(n);
+    default: return spmm_grid<32>(n);
   }
 }
 
@@ -979,52 +1159,52 @@ void launch_spmm(const SpmmArgs& a, bool weighted, int mode, bool bf16, cudaStre
   }
 }
 
-size_t rowpass_smem(int kp, int method) {
-  const int nrg = kRowThreads / kp;
-  const int TR = nrg * kRPT;
-  const int mats = method >= M_OFM_F2 ? 2 : 1;
-  return (size_t)(mats * kp * kp + 2 * TR * kp + kp) * sizeof(float) + (size_t)3 * nrg * kp * sizeof(double);
-}
+int kpmax_for(int kp) { return kp <= 16 ? 16 : kp <= 32 ? 32 : kp <= 64 ? 64 : 128; }
 
-template <int METHOD, bool BF16>
-cudaError_t launch_rowpass_t(const RowArgs& a, cudaStream_t s, int* nblk_out) {
-  static int max_blocks_per_sm[kMaxK + 1] = {0};
-  const size_t smem = rowpass_smem(a.kp, METHOD);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_rowpass<METHOD, BF16>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+template <int METHOD, int KPMAX, bool BF16>
+cudaError_t launch_direction_t(const RowArgs& a, cudaStream_t s, int* nblk_out) {
+  using Sh = DirShape<KPMAX, (METHOD >= M_OFM_F2)>;
+  static int blocks_per_sm = 0;
+  const size_t smem = Sh::bytes();
+  if (blocks_per_sm == 0) {
+    cudaError_t e = cudaFuncSetAttribute(k_direction<METHOD, KPMAX, BF16>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
-  const int nrg = kRowThreads / a.kp;
-  const int threads = nrg * a.kp;
-  if (max_blocks_per_sm[a.kp] == 0) {
     int nb = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_rowpass<METHOD, BF16>, threads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_direction<METHOD, KPMAX, BF16>, kRowThreads, smem);
     if (e != cudaSuccess) return e;
-    max_blocks_per_sm[a.kp] = nb > 0 ? nb : 1;
+    blocks_per_sm = nb > 0 ? nb : 1;
   }
-  const int64_t ntiles = ceil_div(a.n, (int64_t)nrg * kRPT);
-  int grid = (int)std::min<int64_t>(ntiles, (int64_t)max_blocks_per_sm[a.kp] * kNumSMs);
+  const int64_t warps_needed = ceil_div(a.n, (int64_t)Sh::ROWS);
+  int grid = (int)std::min<int64_t>(ceil_div(warps_needed, kRowThreads / 32), (int64_t)blocks_per_sm * kNumSMs);
   if (grid > kMaxRowBlocks) grid = kMaxRowBlocks;
   if (grid < 1) grid = 1;
-  k_rowpass<METHOD, BF16><<<grid, threads, smem, s>>>(a);
+  k_direction<METHOD, KPMAX, BF16><<<grid, kRowThreads, smem, s>>>(a);
   ++g_launches;
   *nblk_out = grid;
   return cudaGetLastError();
 }
 
+template <int METHOD, bool BF16>
+cudaError_t launch_direction_m(const RowArgs& a, cudaStream_t s, int* nblk) {
+  switch (kpmax_for(a.kp)) {
+    case 16: return launch_direction_t<METHOD, 16, BF16>(a, s, nblk);
+    case 32: return launch_direction_t<METHOD, 32, BF16>(a, s, nblk);
+    case 64: return launch_direction_t<METHOD, 64, BF16>(a, s, nblk);
+    default: return launch_direction_t<METHOD, 128, BF16>(a, s, nblk);
+  }
+}
+
 cudaError_t launch_rowpass(int method, bool bf16, const RowArgs& a, cudaStream_t s, int* nblk) {
   switch (method * 2 + (bf16 ? 1 : 0)) {
-    case 0: return launch_rowpass_t<M_OFM_F1, false>(a, s, nblk);
-    case 1: return launch_rowpass_t<M_OFM_F1, true>(a, s, nblk);
-    case 2: return launch_rowpass_t<M_TRI_F1, false>(a, s, nblk);
-    case 3: return launch_rowpass_t<M_TRI_F1, true>(a, s, nblk);
-    case 4: return launch_rowpass_t<M_OFM_F2, false>(a, s, nblk);
-    case 5: return launch_rowpass_t<M_OFM_F2, true>(a, s, nblk);
-    case 6: return launch_rowpass_t<M_TRI_F2, false>(a, s, nblk);
-    default: return launch_rowpass_t<M_TRI_F2, true>(a, s, nblk);
+    case 0: return launch_direction_m<M_OFM_F1, false>(a, s, nblk);
+    case 1: return launch_direction_m<M_OFM_F1, true>(a, s, nblk);
+    case 2: return launch_direction_m<M_TRI_F1, false>(a, s, nblk);
+    case 3: return launch_direction_m<M_TRI_F1, true>(a, s, nblk);
+    case 4: return launch_direction_m<M_OFM_F2, false>(a, s, nblk);
+    case 5: return launch_direction_m<M_OFM_F2, true>(a, s, nblk);
+    case 6: return launch_direction_m<M_TRI_F2, false>(a, s, nblk);
+    default: return launch_direction_m<M_TRI_F2, true>(a, s, nblk);
   }
 }
 
@@ -1089,6 +1269,9 @@ ofsc_status ensure_workspace(ofsc_graph* g, int kp) {
       {(void**)&ws.gram, kPairs * kk * sizeof(double)},
       {(void**)&ws.Rn, kk * sizeof(float)},
       {(void**)&ws.Bn, kk * sizeof(float)},
+      {(void**)&ws.R64, kk * sizeof(double)},
+      {(void**)&ws.B64, kk * sizeof(double)},
+      {(void**)&ws.dots, (size_t)8 * kNumSMs * 2 * kp * sizeof(double)},
       {(void**)&ws.alpha, kp * sizeof(float)},
       {(void**)&ws.beta, kp * sizeof(float)},
       {(void**)&ws.alpha64, kp * sizeof(double)},
@@ -1148,7 +1331,8 @@ struct Runner {
     p.L[1] = ws.X; p.R[1] = ws.Y; p.slot[1] = G_B;
     cudaError_t e = launch_gram(ws, p, 2, (1 << G_R) | (1 << G_B), ignore_done, s);
     if (e != cudaSuccess) return e;
-    k_set_rb<<<1, 256, 0, s>>>(ws.gram, ws.kp, objective, ws.Rn, ws.Bn, ws.ctrl, ignore_done);
+    k_set_rb<<<1, 256, 0, s>>>(ws.gram, ws.kp, objective, ws.Rn, ws.Bn, ws.R64, ws.B64, ws.ctrl,
+                               ignore_done);
     ++g_launches;
     prof.end();
     return cudaGetLastError();
@@ -1180,6 +1364,7 @@ struct Runner {
   }
 
   cudaError_t direction_and_linesearch(int first, const ofsc_opts& o, int k, double alpha0) {
+    const bool f2 = method >= M_OFM_F2;
     SpmmArgs a = spmm_base();
     a.gather = ws.Gh;
     a.G = ws.G;
@@ -1187,21 +1372,33 @@ struct Runner {
     a.W = ws.W;
     a.beta = ws.beta;
     a.first = first;
+    if (!f2) {  // the f1 line searches need only diag(V^T AV) and diag(V^T AX)
+      a.Y = ws.Y;
+      a.dots = ws.dots;
+    }
     prof.begin(OFSC_PHASE_SPMM);
     launch_spmm(a, g->weighted != 0, SP_DIR, bf16, s);
     prof.end();
+    // V^T X and V^T V for every method; V^T AX and V^T AV in full for the f2 methods
     GramPairs p{};
-    const float* Ls[kPairs] = {ws.X, ws.V, ws.V, ws.X, ws.V, ws.V};
-    const float* Rs[kPairs] = {ws.X, ws.X, ws.V, ws.Y, ws.Y, ws.W};
-    for (int i = 0; i < kPairs; ++i) {
-      p.L[i] = Ls[i];
+    const float* Rs[4] = {ws.X, ws.V, ws.Y, ws.W};
+    const int slots[4] = {G_P, G_Q, G_E, G_C};
+    const int npairs = f2 ? 4 : 2;
+    int mask = 0;
+    for (int i = 0; i < npairs; ++i) {
+      p.L[i] = ws.V;
       p.R[i] = Rs[i];
-      p.slot[i] = i;
+      p.slot[i] = slots[i];
+      mask |= 1 << slots[i];
     }
-    cudaError_t e = launch_gram(ws, p, kPairs, (1 << kPairs) - 1, 0, s, &prof);
+    cudaError_t e = launch_gram(ws, p, npairs, mask, 0, s, &prof);
     if (e != cudaSuccess) return e;
     SolveArgs sa{};
     sa.gram = ws.gram;
+    sa.dots = ws.dots;
+    sa.dots_blocks = spmm_grid_for(ws.n, ws.kp);
+    sa.R64 = ws.R64;
+    sa.B64 = ws.B64;
     sa.kp = ws.kp;
     sa.k = k;
     sa.method = method;
@@ -1526,7 +1723,7 @@ extern "C" ofsc_status ofsc_objective_grad_noalloc(const ofsc_graph* gc, int32_t
   }
   k_gram_reduce<<<(int)std::min<int64_t>(ceil_div(kPairs * kp * kp, 256), 4 * kNumSMs), 256, 0, s>>>(
       ws.gram_part, gy, kp, (1 << G_R) | (1 << G_B), ws.gram, ws.ctrl, 0);
-  k_set_rb<<<1, 256, 0, s>>>(ws.gram, kp, objective, ws.Rn, ws.Bn, ws.ctrl, 0);
+  k_set_rb<<<1, 256, 0, s>>>(ws.gram, kp, objective, ws.Rn, ws.Bn, nullptr, nullptr, ws.ctrl, 0);
   OFSC_LAUNCH_CHECK("noalloc: refresh");
   int nblk = 0;
   OFSC_CUDA(run.rowpass(method, 0, 1, 0, &nblk));

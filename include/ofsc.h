@@ -51,6 +51,8 @@ enum { OFSC_OFM_F1 = 0, OFSC_TRI_F1 = 1, OFSC_OFM_F2 = 2, OFSC_TRI_F2 = 3 };
 enum { OFSC_F1 = 1, OFSC_F2 = 2 };
 /* Storage of the block gathered by the sparse product: FP32, or BF16 with FP32 accumulation. */
 enum { OFSC_GATHER_FP32 = 0, OFSC_GATHER_BF16 = 1 };
+/* Engine of the k x k Gram reductions: FP32 CUDA cores, or tcgen05 tensor cores (3-term TF32). */
+enum { OFSC_GRAM_AUTO = 0, OFSC_GRAM_SIMT = 1, OFSC_GRAM_TC = 2 };
 
 typedef struct ofsc_graph ofsc_graph;
 
@@ -163,6 +165,7 @@ typedef struct {
   int32_t trace_cap;   /* records available in `trace` */
   ofsc_profile* profile; /* HOST struct or NULL: the call ADDS its per-phase device times
                             (events around every launch; adds a little host overhead) */
+  int32_t gram_engine;   /* OFSC_GRAM_AUTO (tensor cores when k > 64), OFSC_GRAM_SIMT, OFSC_GRAM_TC */
 } ofsc_opts;
 
 typedef struct {
@@ -219,6 +222,23 @@ ofsc_status ofsc_row_normalize(int64_t n, int32_t k, float* X, void* stream);
 ofsc_status ofsc_kmeans(int64_t n, int32_t d, const float* X, int32_t n_clusters, uint64_t seed,
                         int32_t n_init, int32_t maxit, int32_t* labels, double* inertia,
                         void* stream);
+
+/*
+ * ofsc_gram - the k x k dot-product blocks of Sec. 3.3, out_b = L^T R_b (b < nr), summed over all
+ * n rows on the tcgen05 tensor cores: each FP32 value is split into two TF32 parts and the three
+ * leading products are accumulated in FP32 tensor memory per block of rows; the per-block
+ * partials are added in FP64 in a fixed order (deterministic for a given rows_per_block).
+ *   n, k     rows and features (1 <= k <= 128)
+ *   ld       row stride of L and every R_b in floats (ld >= k, ld % 4 == 0, 16-byte aligned rows)
+ *   L        device float32 [n x ld]
+ *   nr, R    1 <= nr <= 4; HOST array of nr device pointers, each float32 [n x ld]
+ *   rows_per_block  rows per tensor-memory accumulation (multiple of 32), 0 = default
+ *   out      device float64 [nr][k][k], row-major
+ * Allocates its scratch with cudaMallocAsync on `stream`; synchronises `stream`.
+ * Errors: OFSC_ERR_INVALID_ARG, OFSC_ERR_TIMEOUT (a bounded tensor-core wait ran out), OFSC_ERR_CUDA.
+ */
+ofsc_status ofsc_gram(int64_t n, int32_t k, int32_t ld, const float* L, int32_t nr, const float* const* R,
+                      int64_t rows_per_block, double* out, void* stream);
 
 /* Message of the last failing call on this host thread ("" if none). */
 const char* ofsc_last_error(void);

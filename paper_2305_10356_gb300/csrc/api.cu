@@ -51,6 +51,7 @@ void workspace_free(Workspace& ws) {
   cudaFree(ws.R64);
   cudaFree(ws.B64);
   cudaFree(ws.dots);
+  cudaFree(ws.part_tc);
   cudaFree(ws.alpha);
   cudaFree(ws.beta);
   cudaFree(ws.alpha64);

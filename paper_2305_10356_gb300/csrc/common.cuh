@@ -79,6 +79,7 @@ struct Workspace {
   double* R64 = nullptr;        // kp*kp: X^T X of the current X (exact recurrence, FP64)
   double* B64 = nullptr;        // kp*kp: X^T A X of the current X (f2 methods)
   double* dots = nullptr;       // [spmm blocks][2][kp]: partial diag(V^T AV), diag(V^T AX)
+  float* part_tc = nullptr;     // tensor-core Gram partials (kp > 64)
   float* alpha = nullptr;       // kp
   float* beta = nullptr;        // kp
   double* alpha64 = nullptr;    // kp
@@ -115,4 +116,24 @@ struct ofsc_graph {
 
 namespace ofsc {
 void workspace_free(Workspace& ws);
+
+// Arguments of one tensor-core Gram launch (csrc/gram_tc.cu): L^T R_b over all rows.
+struct GramTcArgs {
+  int64_t n;             // rows
+  int ld;                // row stride of every block, in floats (multiple of 4, rows 16-byte aligned)
+  int k;                 // features read (<= 128); features k..127 count as zero
+  int nr;                // right blocks (1..4)
+  const float* L;        // left block
+  const float* R[4];     // right blocks
+  int lslot;             // index b with R[b] == L (its tiles serve as the A operand), or -1
+  int64_t rows_per_cta;  // multiple of 32
+  float* part;           // [ctas][nr][128][128] FP32 partials
+  Ctrl* ctrl;            // status / stop flag (may be null only with ignore_done = 1)
+  int ignore_done;
+};
+int64_t gram_tc_rows_per_cta(int64_t n, int nr);
+size_t gram_tc_part_bytes(int64_t n, int nr, int64_t rows_per_cta);
+cudaError_t gram_tc_launch(GramTcArgs a, const int* slot, int kp, double* gram, cudaStream_t s);
+cudaError_t gram_tc_launch_ld(GramTcArgs a, const int* slot, int kout, int ld_out, int64_t kk_stride,
+                              double* gram, cudaStream_t s);
 }

@@ -1,0 +1,381 @@
+// Gram blocks L^T R_b over all N rows on the 5th-generation tensor cores (tcgen05, kind::tf32).
+//
+// These are the k x k dot products of Sec. 3.3 (V^T X, V^T V, V^T AX, V^T AV, X^T X, X^T AX): dense
+// contractions over the N rows with k <= 128 features. One CTA owns a contiguous range of rows:
+//   * 4 warps load 32 rows of every block into registers (the next chunk is in flight while the
+//     tensor cores work on the current one), split each FP32 value x into tf32 hi = rna(x) and
+//     lo = rna(x - hi), and store hi and lo transposed (feature-major, rows contiguous) in the
+//     K-major, 128-byte-swizzled shared-memory layout that tcgen05.mma reads;
+//   * one thread issues, per 8-row K step, D += Ahi*Bhi + Ahi*Blo + Alo*Bhi (3-term TF32 split,
+//     about FP32 accuracy) with D (128 features x 128 nr columns, FP32) in tensor memory, and
+//     commits the batch to an mbarrier;
+//   * at the end of the range, tcgen05.ld moves D to registers and the CTA writes an FP32
+//     partial; a second kernel sums the partials over CTAs in a fixed order in FP64.
+// Every wait on the mbarrier is bounded: on expiry the CTA records OFSC_ERR_TIMEOUT, stops
+// issuing, frees its tensor memory and returns.
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace ofsc {
+namespace {
+
+constexpr int kTcRows = 32;                       // rows per chunk = one 128-byte swizzle atom of tf32
+constexpr int kTcM = 128;                         // TMEM lanes = features of L
+constexpr int kTcTile = kTcM * kTcRows * 4;       // bytes per operand tile (16 KB)
+constexpr int kTcThreads = 128;
+constexpr long long kTcSpinLimit = 1ll << 22;     // bounded mbarrier polling
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+// Byte offset of element (feature f, chunk row l) in a K-major SWIZZLE_128B tile: 8-feature
+// groups of 1024 bytes, one 128-byte line per feature, 16-byte chunks XOR-permuted by f % 8.
+__device__ __forceinline__ uint32_t tile_off(int f, int l) {
+  return (uint32_t)((f >> 3) * 1024 + (f & 7) * 128 + ((((l >> 2) ^ f) & 7) << 4) + (l & 3) * 4);
+}
+
+// Shared-memory matrix descriptor: start address, LBO (unused for swizzled K-major), SBO = 1024
+// bytes between 8-row groups, descriptor version 1, layout SWIZZLE_128B.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// Instruction descriptor: D FP32, A and B TF32, both K-major, N x M = n x 128.
+__device__ __forceinline__ uint32_t tf32_idesc(int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n"
+      ".reg .pred p;\n"
+      "setp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n"
+      "}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+      smem_u32(bar)));
+}
+
+// Waits for phase `parity` of the mbarrier; false if the bounded wait ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t addr = smem_u32(bar);
+  for (long long it = 0; it < kTcSpinLimit; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n"
+        ".reg .pred p;\n"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(ok)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+}  // namespace
+
+namespace {
+
+template <int NR, bool SEPARATE_L>
+__global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(GramTcArgs a) {
+  if (!a.ignore_done && a.ctrl->done) return;
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ uint64_t bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  constexpr int NT = NR + (SEPARATE_L ? 1 : 0);   // staged blocks
+  constexpr uint32_t NCOLS = NR * kTcM <= 128 ? 128 : NR * kTcM <= 256 ? 256 : 512;
+  unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* hi = base;                        // NT tiles: R_0..R_{NR-1} [, L]
+  unsigned char* lo = base + NT * kTcTile;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int lidx = SEPARATE_L ? NR : a.lslot;      // tile index of the A operand
+  const float* src[NT];
+#pragma unroll
+  for (int b = 0; b < NR; ++b) src[b] = a.R[b];
+  if (SEPARATE_L) src[NT - 1] = a.L;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(NCOLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    abort_flag = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar)), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_slot;
+
+  const int64_t r0 = (int64_t)blockIdx.x * a.rows_per_cta;
+  const int64_t r1 = min(a.n, r0 + a.rows_per_cta);
+  const int64_t nchunks = r1 > r0 ? (r1 - r0 + kTcRows - 1) / kTcRows : 0;
+  const int f0 = warp * 32;  // this warp's 32 features; lane = chunk row
+  float4 buf[NT][8];
+
+  auto fetch = [&](int64_t c) {
+    const int64_t row = r0 + c * kTcRows + lane;
+    const bool rok = row < r1;
+#pragma unroll
+    for (int b = 0; b < NT; ++b)
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int f = f0 + 4 * i;
+        buf[b][i] = (rok && f < a.k) ? *(const float4*)(src[b] + row * a.ld + f) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+  };
+  auto stage = [&]() {
+#pragma unroll
+    for (int b = 0; b < NT; ++b)
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const float v[4] = {buf[b][i].x, buf[b][i].y, buf[b][i].z, buf[b][i].w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int f = f0 + 4 * i + q;
+          const uint32_t h = tf32_rna(v[q]);
+          const uint32_t l = tf32_rna(v[q] - __uint_as_float(h));
+          const uint32_t off = (uint32_t)b * kTcTile + tile_off(f, lane);
+          *(uint32_t*)(hi + off) = h;
+          *(uint32_t*)(lo + off) = l;
+        }
+      }
+  };
+
+  uint32_t phase = 0;
+  if (nchunks > 0) fetch(0);
+  for (int64_t c = 0; c < nchunks; ++c) {
+    if (c > 0) {  // the tensor cores must be done reading the tiles before they are rewritten
+      if (!mbar_wait(&bar, phase)) abort_flag = 1;
+      phase ^= 1;
+    }
+    __syncthreads();
+    if (abort_flag) break;
+    stage();
+    asm volatile("fence.proxy.async.shared::cta;");  // generic-proxy stores -> tensor-core reads
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t hs = smem_u32(hi), ls = smem_u32(lo);
+#pragma unroll
+      for (int s = 0; s < kTcRows / 8; ++s) {  // K steps of 8 rows (32 bytes)
+        const uint64_t ahi = sw128_desc(hs + lidx * kTcTile + s * 32);
+        const uint64_t alo = sw128_desc(ls + lidx * kTcTile + s * 32);
+#pragma unroll
+        for (int h = 0; h < (NR + 1) / 2; ++h) {  // N = 256 covers right blocks 2h, 2h + 1
+          const int ncol = (2 * h + 1 < NR) ? 256 : 128;
+          const uint32_t id = tf32_idesc(ncol);
+          const uint32_t d = tmem + (uint32_t)(h * 256);
+          const uint64_t bhi = sw128_desc(hs + 2 * h * kTcTile + s * 32);
+          const uint64_t blo = sw128_desc(ls + 2 * h * kTcTile + s * 32);
+          mma_tf32(d, ahi, bhi, id, (c > 0 || s > 0) ? 1u : 0u);
+          mma_tf32(d, ahi, blo, id, 1u);
+          mma_tf32(d, alo, bhi, id, 1u);
+        }
+      }
+      mma_commit(&bar);
+    }
+    if (c + 1 < nchunks) fetch(c + 1);  // next chunk's loads overlap the tensor-core work
+  }
+  bool ok = !abort_flag;
+  if (nchunks > 0 && ok) {
+    ok = mbar_wait(&bar, phase);
+    if (!ok) abort_flag = 1;
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  float* out = a.part + (int64_t)blockIdx.x * NR * kTcM * kTcM;
+  const int fi = warp * 32 + lane;  // TMEM lane = feature of L
+  if (!abort_flag && nchunks > 0) {
+#pragma unroll 1
+    for (int c0 = 0; c0 < NR * kTcM; c0 += 32) {
+      uint32_t r[32];
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+          "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+            "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+            "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+            "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
+      const int b = c0 / kTcM, j0 = c0 % kTcM;
+      float4* dst = (float4*)(out + ((int64_t)b * kTcM + fi) * kTcM + j0);
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        dst[q] = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
+                             __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
+    }
+  } else {
+    for (int j = 0; j < NR * kTcM; j += 4) {
+      const int b = j / kTcM, jj = j % kTcM;
+      *(float4*)(out + ((int64_t)b * kTcM + fi) * kTcM + jj) = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+  if (abort_flag && tid == 0) {
+    a.ctrl->status = OFSC_ERR_TIMEOUT;
+    a.ctrl->done = 1;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOLS));
+}
+
+// gram[slot[b]][i][j] = sum over CTAs (in order) of part[cta][b][i][j], FP64, for i, j < kp.
+// gram[slot[b] * kk_stride + i * ld_out + j] = sum over CTAs, in order, of part[cta][b][i][j] (FP64),
+// for i, j < kout.
+__global__ void k_gram_tc_reduce(const float* __restrict__ part, int nctas, int nr, int kout, int ld_out,
+                                 int64_t kk_stride, int s0, int s1, int s2, int s3, double* __restrict__ gram,
+                                 Ctrl* ctrl, int ignore_done) {
+  if (ctrl && !ignore_done && ctrl->done) return;
+  const int slot[4] = {s0, s1, s2, s3};
+  const int total = nr * kout * kout;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+    const int b = t / (kout * kout), ij = t % (kout * kout), i = ij / kout, j = ij % kout;
+    double s = 0.0;
+    for (int c = 0; c < nctas; ++c) s += (double)part[(((int64_t)c * nr + b) * kTcM + i) * kTcM + j];
+    gram[(int64_t)slot[b] * kk_stride + (int64_t)i * ld_out + j] = s;
+  }
+}
+
+template <int NR, bool SEP>
+cudaError_t launch_t(const GramTcArgs& a, int grid, cudaStream_t s) {
+  constexpr int NT = NR + (SEP ? 1 : 0);
+  // Two tile sets (hi, lo) plus alignment slack; at least 100 KB so that at most two CTAs share
+  // an SM, which keeps the tensor-memory columns they allocate within the 512 available.
+  size_t smem = (size_t)NT * 2 * kTcTile + 1024;
+  if (smem < 100 * 1024) smem = 100 * 1024;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_gram_tc<NR, SEP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_gram_tc<NR, SEP><<<grid, kTcThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// Rows accumulated in one tensor-memory segment. The FP32 accumulation on the tensor cores loses
+// about 2e-8 relative per accumulated product block (measured: the error grows linearly with the
+// segment: 2e-6 at 256 rows, 1.4e-5 at 2048, 1e-3 at 131072), so segments are kept short and
+// summed in FP64 afterwards: 8 CTAs per SM for up to two right blocks, 4 for more.
+int64_t gram_tc_rows_per_cta(int64_t n, int nr) {
+  const int64_t ctas = nr <= 2 ? 8 * kNumSMs : 4 * kNumSMs;
+  int64_t rpc = (n + ctas - 1) / ctas;
+  rpc = (rpc + kTcRows - 1) / kTcRows * kTcRows;
+  return rpc < kTcRows ? kTcRows : rpc;
+}
+
+size_t gram_tc_part_bytes(int64_t n, int nr, int64_t rows_per_cta) {
+  const int64_t ctas = (n + rows_per_cta - 1) / rows_per_cta;
+  return (size_t)(ctas > 0 ? ctas : 1) * nr * kTcM * kTcM * sizeof(float);
+}
+
+// Launches the partial Grams and their FP64 reduction into gram[slot][kp][kp].
+cudaError_t gram_tc_launch(GramTcArgs a, const int* slot, int kp, double* gram, cudaStream_t s) {
+  return gram_tc_launch_ld(a, slot, kp, kp, (int64_t)kp * kp, gram, s);
+}
+
+cudaError_t gram_tc_launch_ld(GramTcArgs a, const int* slot, int kout, int ld_out, int64_t kk_stride,
+                              double* gram, cudaStream_t s) {
+  if (a.n <= 0) return cudaSuccess;
+  const int grid = (int)((a.n + a.rows_per_cta - 1) / a.rows_per_cta);
+  const bool sep = a.lslot < 0;
+  cudaError_t e;
+  switch (a.nr * 2 + (sep ? 1 : 0)) {
+    case 2: e = launch_t<1, false>(a, grid, s); break;
+    case 3: e = launch_t<1, true>(a, grid, s); break;
+    case 4: e = launch_t<2, false>(a, grid, s); break;
+    case 5: e = launch_t<2, true>(a, grid, s); break;
+    case 6: e = launch_t<3, false>(a, grid, s); break;
+    case 7: e = launch_t<3, true>(a, grid, s); break;
+    case 8: e = launch_t<4, false>(a, grid, s); break;
+    default: e = launch_t<4, true>(a, grid, s); break;
+  }
+  if (e != cudaSuccess) return e;
+  const int total = a.nr * kout * kout;
+  const int rgrid = (int)std::min<int64_t>((total + 255) / 256, 4 * kNumSMs);
+  k_gram_tc_reduce<<<rgrid, 256, 0, s>>>(a.part, grid, a.nr, kout, ld_out, kk_stride, slot[0],
+                                         a.nr > 1 ? slot[1] : 0, a.nr > 2 ? slot[2] : 0, a.nr > 3 ? slot[3] : 0,
+                                         gram, a.ctrl, a.ignore_done);
+  return cudaGetLastError();
+}
+
+}  // namespace ofsc
+
+using namespace ofsc;
+
+extern "C" ofsc_status ofsc_gram(int64_t n, int32_t k, int32_t ld, const float* L, int32_t nr,
+                                 const float* const* R, int64_t rows_per_block, double* out, void* stream_) {
+  clear_error();
+  if (n < 0 || k < 1 || k > 128 || ld < k || (ld & 3) || nr < 1 || nr > 4)
+    return fail(OFSC_ERR_INVALID_ARG, "ofsc_gram: bad sizes (n=%lld k=%d ld=%d nr=%d)", (long long)n, k, ld, nr);
+  if (!R || !out || (n > 0 && !L)) return fail(OFSC_ERR_INVALID_ARG, "ofsc_gram: NULL pointer");
+  if (((uintptr_t)L & 15) != 0) return fail(OFSC_ERR_INVALID_ARG, "ofsc_gram: L not 16-byte aligned");
+  GramTcArgs a{};
+  a.n = n;
+  a.ld = ld;
+  a.k = k;
+  a.nr = nr;
+  a.L = L;
+  a.lslot = -1;
+  for (int b = 0; b < nr; ++b) {
+    if (n > 0 && (!R[b] || ((uintptr_t)R[b] & 15) != 0))
+      return fail(OFSC_ERR_INVALID_ARG, "ofsc_gram: R[%d] NULL or not 16-byte aligned", b);
+    a.R[b] = R[b];
+    if (R[b] == L && a.lslot < 0) a.lslot = b;
+  }
+  if (rows_per_block < 0 || (rows_per_block % kTcRows) != 0)
+    return fail(OFSC_ERR_INVALID_ARG, "ofsc_gram: rows_per_block must be a non-negative multiple of %d", kTcRows);
+  a.rows_per_cta = rows_per_block > 0 ? rows_per_block : gram_tc_rows_per_cta(n, nr);
+  cudaStream_t s = (cudaStream_t)stream_;
+  if (n == 0) {
+    OFSC_CUDA(cudaMemsetAsync(out, 0, (size_t)nr * k * k * sizeof(double), s));
+    return OFSC_OK;
+  }
+  const size_t pbytes = gram_tc_part_bytes(n, nr, a.rows_per_cta);
+  void* part = nullptr;
+  Ctrl* ctrl = nullptr;
+  OFSC_CUDA(cudaMallocAsync(&part, pbytes, s));
+  cudaError_t e = cudaMallocAsync((void**)&ctrl, sizeof(Ctrl), s);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(part, s);
+    return cuda_fail(e, "ofsc_gram: cudaMallocAsync");
+  }
+  cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), s);
+  a.part = (float*)part;
+  a.ctrl = ctrl;
+  const int slot[4] = {0, 1, 2, 3};
+  e = gram_tc_launch_ld(a, slot, k, k, (int64_t)k * k, out, s);
+  Ctrl h{};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(part, s);
+  cudaFreeAsync(ctrl, s);
+  if (e != cudaSuccess) return cuda_fail(e, "ofsc_gram");
+  OFSC_CUDA(cudaStreamSynchronize(s));
+  if (h.status == OFSC_ERR_TIMEOUT) return fail(OFSC_ERR_TIMEOUT, "ofsc_gram: tensor-core wait timed out");
+  return OFSC_OK;
+}

@@ -1272,6 +1272,9 @@ ofsc_status ensure_workspace(ofsc_graph* g, int kp) {
       {(void**)&ws.R64, kk * sizeof(double)},
       {(void**)&ws.B64, kk * sizeof(double)},
       {(void**)&ws.dots, (size_t)8 * kNumSMs * 2 * kp * sizeof(double)},
+      {(void**)&ws.part_tc, kp > 64 ? std::max(gram_tc_part_bytes(n, 2, gram_tc_rows_per_cta(n, 2)),
+                                               gram_tc_part_bytes(n, 4, gram_tc_rows_per_cta(n, 4)))
+                                    : (size_t)16},
       {(void**)&ws.alpha, kp * sizeof(float)},
       {(void**)&ws.beta, kp * sizeof(float)},
       {(void**)&ws.alpha64, kp * sizeof(double)},
@@ -1304,6 +1307,43 @@ struct Runner {
   int method;
   bool bf16;
   Prof& prof;
+  bool tc = false;  // Grams on the tensor cores
+
+  // L^T R_b for b < nr into the gram slots, on the tensor cores or the CUDA cores
+  cudaError_t grams(const float* L, const float* const* R, int nr, const int* slots, int ignore_done,
+                    bool timed) {
+    if (tc) {
+      GramTcArgs t{};
+      t.n = ws.n;
+      t.ld = ws.kp;
+      t.k = ws.kp;
+      t.nr = nr;
+      t.L = L;
+      t.lslot = -1;
+      for (int b = 0; b < nr; ++b) {
+        t.R[b] = R[b];
+        if (R[b] == L && t.lslot < 0) t.lslot = b;
+      }
+      t.rows_per_cta = gram_tc_rows_per_cta(ws.n, nr);
+      t.part = ws.part_tc;
+      t.ctrl = ws.ctrl;
+      t.ignore_done = ignore_done;
+      if (timed) prof.begin(OFSC_PHASE_GRAM);
+      cudaError_t e = gram_tc_launch(t, slots, ws.kp, ws.gram, s);
+      if (timed) prof.end();
+      g_launches += 2;
+      return e;
+    }
+    GramPairs p{};
+    int mask = 0;
+    for (int b = 0; b < nr; ++b) {
+      p.L[b] = L;
+      p.R[b] = R[b];
+      p.slot[b] = slots[b];
+      mask |= 1 << slots[b];
+    }
+    return launch_gram(ws, p, nr, mask, ignore_done, s, timed ? &prof : nullptr);
+  }
 
   SpmmArgs spmm_base() const {
     SpmmArgs a{};
@@ -1326,10 +1366,9 @@ struct Runner {
     a.ignore_done = ignore_done;
     prof.begin(OFSC_PHASE_REFRESH);
     launch_spmm(a, g->weighted != 0, SP_Y, false, s);
-    GramPairs p{};
-    p.L[0] = ws.X; p.R[0] = ws.X; p.slot[0] = G_R;
-    p.L[1] = ws.X; p.R[1] = ws.Y; p.slot[1] = G_B;
-    cudaError_t e = launch_gram(ws, p, 2, (1 << G_R) | (1 << G_B), ignore_done, s);
+    const float* R[2] = {ws.X, ws.Y};
+    const int slots[2] = {G_R, G_B};
+    cudaError_t e = grams(ws.X, R, 2, slots, ignore_done, false);
     if (e != cudaSuccess) return e;
     k_set_rb<<<1, 256, 0, s>>>(ws.gram, ws.kp, objective, ws.Rn, ws.Bn, ws.R64, ws.B64, ws.ctrl,
                                ignore_done);
@@ -1380,18 +1419,9 @@ struct Runner {
     launch_spmm(a, g->weighted != 0, SP_DIR, bf16, s);
     prof.end();
     // V^T X and V^T V for every method; V^T AX and V^T AV in full for the f2 methods
-    GramPairs p{};
     const float* Rs[4] = {ws.X, ws.V, ws.Y, ws.W};
     const int slots[4] = {G_P, G_Q, G_E, G_C};
-    const int npairs = f2 ? 4 : 2;
-    int mask = 0;
-    for (int i = 0; i < npairs; ++i) {
-      p.L[i] = ws.V;
-      p.R[i] = Rs[i];
-      p.slot[i] = slots[i];
-      mask |= 1 << slots[i];
-    }
-    cudaError_t e = launch_gram(ws, p, npairs, mask, 0, s, &prof);
+    cudaError_t e = grams(ws.V, Rs, f2 ? 4 : 2, slots, 0, true);
     if (e != cudaSuccess) return e;
     SolveArgs sa{};
     sa.gram = ws.gram;
@@ -1448,6 +1478,7 @@ extern "C" ofsc_status ofsc_objective_grad(ofsc_graph* g, int32_t objective, int
   const int method = objective == OFSC_F1 ? M_OFM_F1 : M_OFM_F2;
   Prof prof{ws, nullptr, s};
   Runner run{g, ws, s, method, false, prof};
+  run.tc = kp > 64;
   k_init_ctrl<<<1, 1, 0, s>>>(ws.ctrl, 0.0, 0, k, g->normA2, 0);
   ++g_launches;
   OFSC_LAUNCH_CHECK("k_init_ctrl");
@@ -1469,6 +1500,7 @@ extern "C" ofsc_status ofsc_objective_grad(ofsc_graph* g, int32_t objective, int
   } else {
     c.f = objective == OFSC_F1 ? 0.0 : 0.0;
   }
+  if (c.status == OFSC_ERR_TIMEOUT) return fail(c.status, "ofsc_objective_grad: a bounded tensor-core wait timed out");
   if (c.status != OFSC_OK) return fail(c.status, "ofsc_objective_grad: non-finite value in X");
   if (!std::isfinite(c.f)) return fail(OFSC_ERR_NONFINITE, "ofsc_objective_grad: non-finite objective");
   if (f_out) *f_out = c.f;
@@ -1490,6 +1522,8 @@ extern "C" ofsc_status ofsc_iterate(ofsc_graph* g, int32_t method, int32_t k, fl
   if (o.gather != OFSC_GATHER_FP32 && o.gather != OFSC_GATHER_BF16)
     return fail(OFSC_ERR_INVALID_ARG, "ofsc_iterate: unknown gather mode %d", o.gather);
   if (o.trace && o.trace_cap < 0) return fail(OFSC_ERR_INVALID_ARG, "ofsc_iterate: trace_cap < 0");
+  if (o.gram_engine < OFSC_GRAM_AUTO || o.gram_engine > OFSC_GRAM_TC)
+    return fail(OFSC_ERR_INVALID_ARG, "ofsc_iterate: unknown gram_engine %d", o.gram_engine);
   const int y_refresh = o.y_refresh > 0 ? o.y_refresh : 32;
   const int check_every = o.check_every > 0 ? o.check_every : 16;
   cudaStream_t s = (cudaStream_t)stream_;
@@ -1505,6 +1539,8 @@ extern "C" ofsc_status ofsc_iterate(ofsc_graph* g, int32_t method, int32_t k, fl
   g_launches = 0;
   Prof prof{ws, o.profile, s};
   Runner run{g, ws, s, method, o.gather == OFSC_GATHER_BF16, prof};
+  run.tc = o.gram_engine == OFSC_GRAM_TC || (o.gram_engine == OFSC_GRAM_AUTO && kp > 64);
+  if (run.tc && kp > 128) return fail(OFSC_ERR_INVALID_ARG, "ofsc_iterate: tensor-core Grams need k <= 128");
   const int objective = (method == OFSC_OFM_F1 || method == OFSC_TRI_F1) ? 1 : 2;
 
   k_init_ctrl<<<1, 1, 0, s>>>(ws.ctrl, tol, maxit, k, g->normA2, o.trace ? o.trace_cap : 0);
@@ -1572,6 +1608,7 @@ extern "C" ofsc_status ofsc_iterate(ofsc_graph* g, int32_t method, int32_t k, fl
     out->kernel_launches = g_launches;
   }
   if (rs == OFSC_ERR_NONFINITE) return fail(rs, "ofsc_iterate: non-finite value in X0 or in the iteration");
+  if (rs == OFSC_ERR_TIMEOUT) return fail(rs, "ofsc_iterate: a bounded tensor-core wait timed out");
   return rs;
 }
 

@@ -18,6 +18,7 @@ OK, ERR_INVALID_ARG, ERR_OOM, ERR_NONFINITE, ERR_TIMEOUT, ERR_NOT_CONVERGED, ERR
 OFM_F1, TRI_F1, OFM_F2, TRI_F2 = 0, 1, 2, 3
 F1, F2 = 1, 2
 GATHER_FP32, GATHER_BF16 = 0, 1
+GRAM_AUTO, GRAM_SIMT, GRAM_TC = 0, 1, 2
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "NONFINITE", 4: "TIMEOUT",
                 5: "NOT_CONVERGED", 6: "CUDA"}
 
@@ -49,7 +50,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("gather", ctypes.c_int32), ("y_refresh", ctypes.c_int32),
                 ("check_every", ctypes.c_int32), ("alpha0", ctypes.c_double),
                 ("trace", ctypes.c_void_p), ("trace_cap", ctypes.c_int32),
-                ("profile", ctypes.POINTER(Profile))]
+                ("profile", ctypes.POINTER(Profile)), ("gram_engine", ctypes.c_int32)]
 
 
 class Result(ctypes.Structure):
@@ -89,6 +90,7 @@ def lib() -> ctypes.CDLL:
             "ofsc_iterate": [vp, i32, i32, vp, dbl, i32, ctypes.POINTER(Opts),
                              ctypes.POINTER(Result), vp],
             "ofsc_row_normalize": [i64, i32, vp, vp],
+            "ofsc_gram": [i64, i32, i32, vp, i32, ctypes.POINTER(vp), i64, vp, vp],
             "ofsc_kmeans": [i64, i32, vp, i32, u64, i32, i32, vp, ctypes.POINTER(dbl), vp],
         }
         for name, args in sig.items():
@@ -190,16 +192,24 @@ def ofsc_objective_grad_noalloc(g: Graph, objective: int, X, G_out=None, stream=
 
 def ofsc_iterate(g: Graph, method: int, X, tol: float, maxit: int, *, gather: int = GATHER_FP32,
                  y_refresh: int = 0, check_every: int = 0, alpha0: float = 0.0, trace=None,
-                 profile: Profile | None = None, stream=None) -> Result:
+                 profile: Profile | None = None, gram_engine: int = GRAM_AUTO, stream=None) -> Result:
     """Algorithm 2 in place on the device block X (n x k, FP32). Returns the ofsc_result."""
     o = Opts(gather, y_refresh, check_every, alpha0, _ptr(trace),
              0 if trace is None else int(trace.shape[0]),
-             ctypes.pointer(profile) if profile is not None else None)
+             ctypes.pointer(profile) if profile is not None else None, gram_engine)
     r = Result()
     _check(lib().ofsc_iterate(g.handle, method, int(X.shape[1]), _ptr(X), float(tol), int(maxit),
                               ctypes.byref(o), ctypes.byref(r), _stream(stream)),
            allow=(OK, ERR_NOT_CONVERGED))
     return r
+
+
+def ofsc_gram(L, Rs, out, k: int | None = None, rows_per_block: int = 0, stream=None) -> None:
+    """out[b] = L^T Rs[b] (FP64 [nr, k, k]) on the tensor cores; L and Rs[b] are n x ld FP32."""
+    n, ld = int(L.shape[0]), int(L.shape[1])
+    arr = (ctypes.c_void_p * len(Rs))(*[_ptr(r) for r in Rs])
+    _check(lib().ofsc_gram(n, ld if k is None else k, ld, _ptr(L), len(Rs), arr, rows_per_block,
+                           _ptr(out), _stream(stream)))
 
 
 def ofsc_row_normalize(X, stream=None) -> None:

@@ -257,3 +257,36 @@ def test_kmeans_matches_oracle(cuda_lib):
     lab2 = torch.empty_like(lab)
     ofsc.ofsc_kmeans(X, 7, lab2, seed=42, n_init=2)
     assert torch.equal(lab, lab2)  # deterministic given the seed
+
+
+@pytest.mark.parametrize("n,k,ld,nr,same", [(100, 128, 128, 2, True), (10_001, 128, 128, 4, True),
+                                            (3_333, 100, 104, 3, False), (777, 20, 24, 1, False)])
+def test_tensor_core_gram_matches_fp64(cuda_lib, n, k, ld, nr, same):
+    """ofsc_gram (tcgen05, 3-term TF32, FP32 tensor-memory accumulation) against FP64 numpy."""
+    torch = cuda_lib
+    rng = np.random.default_rng(n + k)
+    L = (rng.standard_normal((n, ld)) / np.sqrt(n)).astype(np.float32)
+    Rs = [L if (same and b == 1) else (rng.standard_normal((n, ld)) / np.sqrt(n)).astype(np.float32)
+          for b in range(nr)]
+    Ld = torch.from_numpy(L).cuda()
+    Rd = [Ld if (same and b == 1) else torch.from_numpy(R).cuda() for b, R in enumerate(Rs)]
+    out = torch.zeros((nr, k, k), dtype=torch.float64, device="cuda")
+    ofsc.ofsc_gram(Ld, Rd, out, k=k)
+    got = out.cpu().numpy()
+    for b in range(nr):
+        ref = L[:, :k].astype(np.float64).T @ Rs[b][:, :k].astype(np.float64)
+        assert np.linalg.norm(got[b] - ref) <= 1e-5 * np.linalg.norm(ref)
+
+
+def test_tensor_core_and_cuda_core_iterations_agree(cuda_lib):
+    """k = 128: the iteration with tensor-core Grams tracks the FP32 CUDA-core one."""
+    e = synth.sbm(4000, 8, 16.0, 8.0, seed=77)
+    x0 = synth.initial_block(e.n, 128, 78)
+    og = o.build_graph(e.n, e.src, e.dst)
+    g = gpu_graph(e)
+    for method in METHODS:
+        Xs, rs, _ = run_iterate(g, method, x0, 0.0, 6, gram_engine=ofsc.GRAM_SIMT)
+        Xt, rt, _ = run_iterate(g, method, x0, 0.0, 6, gram_engine=ofsc.GRAM_TC)
+        ref = o.iterate(og, method, x0, 0.0, 6)
+        assert np.linalg.norm(Xt - ref.X) <= 1e-4 * np.linalg.norm(ref.X)
+        assert np.linalg.norm(Xs - ref.X) <= 1e-4 * np.linalg.norm(ref.X)

@@ -43,7 +43,7 @@ void workspace_free(Workspace& ws) {
   cudaFree(ws.V);
   cudaFree(ws.W);
   cudaFree(ws.G);
-  cudaFree(ws.Gh);
+  cudaFree(ws.Vh);
   cudaFree(ws.gram_part);
   cudaFree(ws.gram);
   cudaFree(ws.Rn);
@@ -57,6 +57,7 @@ void workspace_free(Workspace& ws) {
   cudaFree(ws.alpha64);
   cudaFree(ws.beta64);
   cudaFree(ws.colpart);
+  cudaFree(ws.dE);
   cudaFree(ws.ctrl);
   if (ws.ctrl_host) cudaFreeHost(ws.ctrl_host);
   for (cudaEvent_t e : ws.events) cudaEventDestroy(e);
@@ -82,6 +83,7 @@ ofsc_status ofsc_graph_free(ofsc_graph* g) {
   cudaFree(g->val);
   cudaFree(g->dinv);
   cudaFree(g->deg);
+  for (int i = 0; i < 5; ++i) cudaFree(g->bnd[i]);
   cudaSetDevice(prev);
   delete g;
   return OFSC_OK;

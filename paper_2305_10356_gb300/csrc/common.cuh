@@ -40,6 +40,24 @@ ofsc_status cuda_fail(cudaError_t e, const char* what);
 inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// Lanes per row in the sparse product (4 values per lane) and the index of its partition.
+inline int spmm_lanes(int kp) {
+  int l = 2;
+  while (l * 4 < kp) l *= 2;
+  return l;
+}
+inline int spmm_lanes_index(int lanes) {
+  return lanes <= 2 ? 0 : lanes <= 4 ? 1 : lanes <= 8 ? 2 : lanes <= 16 ? 3 : 4;
+}
+// Lane groups of the sparse product: about 512 nonzeros each, between 1 and 4 blocks per SM.
+inline int spmm_groups(int64_t nnz, int lpr) {
+  const int64_t gpb = 256 / lpr;
+  int64_t g = nnz / 512;
+  if (g < kNumSMs * gpb) g = kNumSMs * gpb;
+  if (g > 4 * kNumSMs * gpb) g = 4 * kNumSMs * gpb;
+  return (int)ceil_div(g, gpb) * (int)gpb;
+}
+
 // Device control block of one ofsc_iterate / ofsc_objective_grad call.
 struct Ctrl {
   int it;          // updates X <- X + V diag(alpha) applied so far
@@ -71,7 +89,7 @@ struct Workspace {
   float* V = nullptr;   // search direction
   float* W = nullptr;   // A V
   float* G = nullptr;   // direction g(X) of the last pass (G_{t-1} while G_t is formed)
-  void* Gh = nullptr;   // D^-1/2 G, FP32 or BF16: the block gathered by the sparse product
+  void* Vh = nullptr;   // D^-1/2 V, FP32 or BF16: the block gathered by the sparse product
   double* gram_part = nullptr;  // [gram_gy][6][kp*kp] per-row-group partial Grams
   double* gram = nullptr;       // [6][kp*kp] reduced Grams R, P, Q, B, E, C
   float* Rn = nullptr;          // kp*kp: X^T X for the next direction pass
@@ -84,7 +102,8 @@ struct Workspace {
   float* beta = nullptr;        // kp
   double* alpha64 = nullptr;    // kp
   double* beta64 = nullptr;     // kp
-  double* colpart = nullptr;    // [row_blocks][3][kp]
+  double* colpart = nullptr;    // [row_blocks][5][kp]
+  double* dE = nullptr;         // kp: diag(V^T AX) (f1 methods)
   Ctrl* ctrl = nullptr;
   Ctrl* ctrl_host = nullptr;    // pinned
   int gram_gy = 0;
@@ -111,6 +130,10 @@ struct ofsc_graph {
   float* val = nullptr;        // [nnz] or null
   float* dinv = nullptr;       // [n]  D^-1/2 in FP32
   double* deg = nullptr;       // [n]
+  // nnz-balanced row ranges of the sparse product's lane groups, one partition per group width
+  // (2, 4, 8, 16, 32 lanes): bnd[i] has groups[i] + 1 entries
+  int64_t* bnd[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  int groups[5] = {0, 0, 0, 0, 0};
   ofsc::Workspace ws;
 };
 

@@ -92,7 +92,7 @@ __global__ void k_row_ptr(int64_t nnz, int64_t n, const int32_t* __restrict__ ro
 }
 
 __global__ void k_degree(int64_t n, const int64_t* __restrict__ row_ptr, const float* __restrict__ val,
-                         double* __restrict__ deg, float* __restrict__ dinv,
+                         double* __restrict__ deg, float* __restrict__ dinv, double* __restrict__ dinv64,
                          unsigned long long* __restrict__ isolated) {
   unsigned long long iso = 0;
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
@@ -106,7 +106,9 @@ __global__ void k_degree(int64_t n, const int64_t* __restrict__ row_ptr, const f
       d = (double)(p1 - p0);
     }
     deg[r] = d;
-    dinv[r] = d > 0.0 ? (float)(1.0 / sqrt(d)) : 0.0f;
+    const double s64 = d > 0.0 ? 1.0 / sqrt(d) : 0.0;
+    dinv64[r] = s64;
+    dinv[r] = (float)s64;
     iso += (d == 0.0);
   }
   for (int o = 16; o > 0; o >>= 1) iso += __shfl_down_sync(0xffffffffu, iso, o);
@@ -118,16 +120,15 @@ constexpr int kNormBlocks = 256;
 __global__ void __launch_bounds__(256) k_normA_part(int64_t n, const int64_t* __restrict__ row_ptr,
                                                     const int32_t* __restrict__ col,
                                                     const float* __restrict__ val,
-                                                    const double* __restrict__ deg,
+                                                    const double* __restrict__ dinv64,
                                                     double* __restrict__ part) {
   double acc = 0.0;
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
        r += (int64_t)gridDim.x * blockDim.x) {
-    double dr = deg[r];
-    if (dr <= 0.0) continue;
-    double sr = 1.0 / sqrt(dr);
+    const double sr = dinv64[r];
+    if (sr == 0.0) continue;
     for (int64_t p = row_ptr[r]; p < row_ptr[r + 1]; ++p) {
-      double a = sr * (val ? (double)val[p] : 1.0) * (1.0 / sqrt(deg[col[p]]));
+      const double a = sr * (val ? (double)val[p] : 1.0) * dinv64[col[p]];
       acc += a * a;
     }
   }
@@ -139,6 +140,25 @@ __global__ void __launch_bounds__(256) k_normA_part(int64_t n, const int64_t* __
     __syncthreads();
   }
   if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+// bnd[g] = first row whose row pointer is >= g * nnz / groups (bnd[groups] = n).
+__global__ void k_partition(int64_t n, const int64_t* __restrict__ row_ptr, int groups, int64_t* __restrict__ bnd) {
+  const int64_t nnz = row_ptr[n];
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g <= groups; g += gridDim.x * blockDim.x) {
+    if (g == 0 || g == groups) {
+      bnd[g] = g == 0 ? 0 : n;
+      continue;
+    }
+    const int64_t target = nnz * (int64_t)g / groups;  // nnz < 2^31, g < 2^17: no overflow
+    int64_t lo = 0, hi = n;  // first r in [0, n] with row_ptr[r] >= target
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (row_ptr[mid] < target) lo = mid + 1;
+      else hi = mid;
+    }
+    bnd[g] = lo;
+  }
 }
 
 int bit_length(uint64_t x) {
@@ -290,12 +310,15 @@ extern "C" ofsc_status ofsc_graph_build(int64_t n, int64_t m, const int32_t* src
 
   double normA2 = (double)n;
   if (n > 0) {
-    k_degree<<<grid_for(n), 256, 0, stream>>>(n, g->row_ptr, g->val, g->deg, g->dinv, d_counts + 1);
+    double* dinv64 = nullptr;
+    OFSC_CUDA(cudaMalloc(&dinv64, n * sizeof(double)));
+    sc.p[11] = dinv64;
+    k_degree<<<grid_for(n), 256, 0, stream>>>(n, g->row_ptr, g->val, g->deg, g->dinv, dinv64, d_counts + 1);
     OFSC_LAUNCH_CHECK("k_degree");
     double* part = nullptr;
     OFSC_CUDA(cudaMalloc(&part, kNormBlocks * sizeof(double)));
     sc.p[10] = part;
-    k_normA_part<<<kNormBlocks, 256, 0, stream>>>(n, g->row_ptr, g->col, g->val, g->deg, part);
+    k_normA_part<<<kNormBlocks, 256, 0, stream>>>(n, g->row_ptr, g->col, g->val, dinv64, part);
     OFSC_LAUNCH_CHECK("k_normA_part");
     double h_part[kNormBlocks];
     OFSC_CUDA(cudaMemcpyAsync(h_part, part, sizeof(h_part), cudaMemcpyDeviceToHost, stream));
@@ -305,6 +328,14 @@ extern "C" ofsc_status ofsc_graph_build(int64_t n, int64_t m, const int32_t* src
     g->n_isolated = (int64_t)h_counts[1];
   }
   g->normA2 = normA2;
+  for (int i = 0; i < 5; ++i) {
+    const int lpr = 2 << i;
+    g->groups[i] = spmm_groups(nnz, lpr);
+    OFSC_CUDA(cudaMalloc(&g->bnd[i], (g->groups[i] + 1) * sizeof(int64_t)));
+    k_partition<<<grid_for(g->groups[i] + 1), 256, 0, stream>>>(n, g->row_ptr, g->groups[i], g->bnd[i]);
+    OFSC_LAUNCH_CHECK("k_partition");
+  }
+  OFSC_CUDA(cudaStreamSynchronize(stream));
   guard.keep = true;
   *out = g;
   return OFSC_OK;

@@ -4,14 +4,16 @@
 // Per update t (the paper's steps 7-11, Sec. 4) the device runs:
 //   direction pass  X += V diag(alpha), AX += AV diag(alpha)   (previous update, fused)
 //                   G = g(X) from AX and the k x k blocks X^T X, X^T A X       (Eqs. (5),(7),(10),(12))
-//                   column sums for beta and ||G||, Gh = D^-1/2 G
+//                   column sums for beta and ||G||
 //   beta            beta_i = sum (G - G_prev) G / sum G_prev^2, stop test        (Algorithm 2)
-//   sparse product  Z = A G by gathering rows of Gh; V = -G + V diag(beta); AV = -Z + AV diag(beta)
-//   Grams           X^T X, V^T X, V^T V, X^T AX, V^T AX, V^T AV                 (Sec. 3.3)
-//   line search     cubic coefficients, real roots, alpha; X^T X and X^T AX of the next X
-// AX is carried by the recurrence AX_{t+1} = AX_t + AV_t diag(alpha_t) and AV by
-// AV_t = -A G_t + AV_{t-1} diag(beta_t) (A is linear, so both are exact in exact arithmetic);
-// AX is recomputed from X every y_refresh updates and at the end, so rounding cannot pile up.
+//   V pass          V = -G + V diag(beta), Vh = D^-1/2 V (FP32 or BF16)
+//   sparse product  AV = -V - D^-1/2 S Vh by gathering rows of Vh, with diag(V^T AV), diag(V^T G)
+//   Grams           V^T X, V^T V (and V^T AX, V^T AV for f2)                     (Sec. 3.3)
+//   line search     cubic coefficients, real roots, alpha; X^T X and X^T A X of the next X
+// AX is carried by the recurrence AX_{t+1} = AX_t + AV_t diag(alpha_t), exact in exact arithmetic
+// since A is linear; it is recomputed from X every y_refresh updates and at the end. AV itself
+// is computed from V every update: a recurrence for it would multiply its rounding error by the
+// column-wise beta, which is not bounded by 1.
 #include <cuda_bf16.h>
 #include <stdarg.h>
 
@@ -110,28 +112,25 @@ struct SpmmArgs {
   const int32_t* col;
   const float* val;
   const float* dinv;
-  const void* gather;  // SP_DIR: Gh (FP32 or BF16, pre-scaled by D^-1/2); SP_Y: X (FP32)
-  const float* G;      // SP_DIR
-  float* V;            // SP_DIR: in V_{t-1}, out V_t
-  float* W;            // SP_DIR: in AV_{t-1}, out AV_t
-  const float* beta;   // SP_DIR
-  const float* X;      // SP_Y
-  float* Y;            // SP_Y: out A X; SP_DIR with DOTS: in A X
-  double* dots;        // SP_DIR with DOTS: [gridDim.x][2][kp] partial sums of V.AV and V.AX
+  const int64_t* bnd;  // [groups + 1]: contiguous, nnz-balanced row ranges of the lane groups
+  int groups;
+  const void* gather;  // SP_DIR: Vh = D^-1/2 V (FP32 or BF16); SP_Y: X (FP32, scaled per nonzero)
+  const float* base;   // SP_DIR: V; SP_Y: X  (the row block M in A M = -M - D^-1/2 S D^-1/2 M)
+  float* out;          // SP_DIR: AV; SP_Y: AX
+  const float* G;      // SP_DIR with DOTS: the direction G
+  double* dots;        // SP_DIR with DOTS: [gridDim.x][2][kp] partial sums of diag(V^T AV), diag(V^T G)
   Ctrl* ctrl;
-  int first;           // SP_DIR: t = 0 (no V_{t-1}, AV_{t-1})
   int ignore_done;
 };
 
+// Four consecutive values of row `row` from column c, as FP32 (FP32 or BF16 storage).
 template <bool BF16>
 __device__ __forceinline__ float4 load_row4(const void* base, int64_t row, int kp, int c) {
   if constexpr (BF16) {
-    const __nv_bfloat16* p = (const __nv_bfloat16*)base + row * kp + c;
-    uint2 u = __ldg((const uint2*)p);
-    __nv_bfloat162 a = *reinterpret_cast<__nv_bfloat162*>(&u.x);
-    __nv_bfloat162 b = *reinterpret_cast<__nv_bfloat162*>(&u.y);
-    float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
-    return make_float4(fa.x, fa.y, fb.x, fb.y);
+    const uint2 u = __ldg((const uint2*)((const __nv_bfloat16*)base + row * kp + c));
+    const float2 lo = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
+    const float2 hi = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
+    return make_float4(lo.x, lo.y, hi.x, hi.y);
   } else {
     return __ldg((const float4*)((const float*)base + row * kp + c));
   }
@@ -144,108 +143,150 @@ __device__ __forceinline__ void fma4(float4& acc, float w, const float4& v) {
   acc.w = fmaf(w, v.w, acc.w);
 }
 
-// A group of LANES lanes owns one row at a time; lane q holds columns [4q, 4q + 4).
+// out = A M = -M - D^-1/2 S (D^-1/2 M) row by row. A group of LANES lanes owns a contiguous range
+// of rows holding about nnz / groups nonzeros (hub rows do not pile up on one group); lane q
+// holds columns [4q, 4q + 4). For each row the group loads up to LANES column indices at once
+// and keeps 8 row gathers in flight per lane; the next row's pointer and epilogue operands are
+// loaded before the current row's gathers. SP_DIR also sums diag(V^T AV) and diag(V^T G).
 template <int LANES, bool WEIGHTED, int MODE, bool BF16, bool DOTS>
-__global__ void __launch_bounds__(256) k_spmm(SpmmArgs a) {
+__global__ void __launch_bounds__(256, 2) k_spmm(SpmmArgs a) {
   if (!a.ignore_done && a.ctrl->done) return;
-  __shared__ float dred[DOTS ? 2 * 256 * 4 : 1];
-  constexpr int GROUPS = 256 / LANES;
+  constexpr int GPB = 256 / LANES;
   constexpr bool GBF = (MODE == SP_DIR) && BF16;
+  constexpr bool SCALED = WEIGHTED || MODE == SP_Y;
+  __shared__ float dred[DOTS ? 2 * 256 * 4 : 1];
   const int lane = threadIdx.x % LANES;
   const int grp = threadIdx.x / LANES;
-  const unsigned mask = LANES == 32 ? 0xffffffffu
-                                    : (((1u << LANES) - 1u) << ((threadIdx.x & 31) / LANES * LANES));
+  const unsigned mask = LANES == 32 ? 0xffffffffu : (((1u << LANES) - 1u) << ((threadIdx.x & 31) / LANES * LANES));
   const int c = lane * 4;
   const bool active = c < a.kp;
-  float4 dcw = make_float4(0.f, 0.f, 0.f, 0.f), dey = make_float4(0.f, 0.f, 0.f, 0.f);
-  for (int64_t l = (int64_t)blockIdx.x * GROUPS + grp; l < a.n; l += (int64_t)gridDim.x * GROUPS) {
-    const int64_t p0 = a.row_ptr[l], p1 = a.row_ptr[l + 1];
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int64_t base = p0; base < p1; base += LANES) {
-      const int cnt = (int)min((int64_t)LANES, p1 - base);
-      int jj = 0;
-      float ww = 0.0f;
-      if (lane < cnt) {
-        jj = __ldg(a.col + base + lane);
-        ww = WEIGHTED ? __ldg(a.val + base + lane) : 1.0f;
-        if (MODE == SP_Y) ww *= __ldg(a.dinv + jj);
+  const int gid = blockIdx.x * GPB + grp;
+  float4 dcw = make_float4(0.f, 0.f, 0.f, 0.f), dvg = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (gid < a.groups) {
+    const int64_t ra = a.bnd[gid], rb = a.bnd[gid + 1];
+    int64_t p1 = ra < rb ? a.row_ptr[ra] : 0;
+    for (int64_t l = ra; l < rb; ++l) {
+      const int64_t p0 = p1;
+      p1 = a.row_ptr[l + 1];
+      const int64_t o = l * a.kp + c;
+      float4 base = make_float4(0.f, 0.f, 0.f, 0.f), gg = base;
+      if (active) {
+        base = *(const float4*)(a.base + o);
+        if (DOTS) gg = *(const float4*)(a.G + o);
       }
-      int q = 0;
-      for (; q + 4 <= cnt; q += 4) {
-        int j0 = __shfl_sync(mask, jj, q, LANES), j1 = __shfl_sync(mask, jj, q + 1, LANES);
-        int j2 = __shfl_sync(mask, jj, q + 2, LANES), j3 = __shfl_sync(mask, jj, q + 3, LANES);
-        float w0 = __shfl_sync(mask, ww, q, LANES), w1 = __shfl_sync(mask, ww, q + 1, LANES);
-        float w2 = __shfl_sync(mask, ww, q + 2, LANES), w3 = __shfl_sync(mask, ww, q + 3, LANES);
-        if (active) {
-          float4 v0 = load_row4<GBF>(a.gather, j0, a.kp, c);
-          float4 v1 = load_row4<GBF>(a.gather, j1, a.kp, c);
-          float4 v2 = load_row4<GBF>(a.gather, j2, a.kp, c);
-          float4 v3 = load_row4<GBF>(a.gather, j3, a.kp, c);
-          fma4(acc, w0, v0);
-          fma4(acc, w1, v1);
-          fma4(acc, w2, v2);
-          fma4(acc, w3, v3);
+      const float s = a.dinv[l];
+      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int64_t pb = p0; pb < p1; pb += LANES) {
+        const int cnt = (int)min((int64_t)LANES, p1 - pb);
+        int jj = 0;
+        float ww = 0.0f;
+        if (lane < cnt) {
+          jj = __ldg(a.col + pb + lane);
+          if (SCALED) {
+            ww = WEIGHTED ? __ldg(a.val + pb + lane) : 1.0f;
+            if (MODE == SP_Y) ww *= __ldg(a.dinv + jj);
+          }
+        }
+        int q = 0;
+        for (; q + 8 <= cnt; q += 8) {
+          float4 v[8];
+          float w[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int j = __shfl_sync(mask, jj, q + u, LANES);
+            w[u] = SCALED ? __shfl_sync(mask, ww, q + u, LANES) : 1.0f;
+            if (active) v[u] = load_row4<GBF>(a.gather, j, a.kp, c);
+          }
+          if (active) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) fma4(acc, w[u], v[u]);
+          }
+        }
+        for (; q + 4 <= cnt; q += 4) {
+          float4 v[4];
+          float w[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int j = __shfl_sync(mask, jj, q + u, LANES);
+            w[u] = SCALED ? __shfl_sync(mask, ww, q + u, LANES) : 1.0f;
+            if (active) v[u] = load_row4<GBF>(a.gather, j, a.kp, c);
+          }
+          if (active) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) fma4(acc, w[u], v[u]);
+          }
+        }
+        for (; q < cnt; ++q) {
+          const int j = __shfl_sync(mask, jj, q, LANES);
+          const float w = SCALED ? __shfl_sync(mask, ww, q, LANES) : 1.0f;
+          if (active) fma4(acc, w, load_row4<GBF>(a.gather, j, a.kp, c));
         }
       }
-      for (; q < cnt; ++q) {
-        int j = __shfl_sync(mask, jj, q, LANES);
-        float w = __shfl_sync(mask, ww, q, LANES);
-        if (active) fma4(acc, w, load_row4<GBF>(a.gather, j, a.kp, c));
+      if (!active) continue;
+      const float4 r4 = make_float4(-fmaf(s, acc.x, base.x), -fmaf(s, acc.y, base.y),
+                                    -fmaf(s, acc.z, base.z), -fmaf(s, acc.w, base.w));
+      *(float4*)(a.out + o) = r4;
+      if (DOTS) {
+        dcw.x = fmaf(base.x, r4.x, dcw.x); dcw.y = fmaf(base.y, r4.y, dcw.y);
+        dcw.z = fmaf(base.z, r4.z, dcw.z); dcw.w = fmaf(base.w, r4.w, dcw.w);
+        dvg.x = fmaf(base.x, gg.x, dvg.x); dvg.y = fmaf(base.y, gg.y, dvg.y);
+        dvg.z = fmaf(base.z, gg.z, dvg.z); dvg.w = fmaf(base.w, gg.w, dvg.w);
       }
-    }
-    if (!active) continue;
-    const float s = a.dinv[l];
-    const int64_t o = l * a.kp + c;
-    if (MODE == SP_DIR) {
-      // A G = -G - s (S Gh);  AV_t = -A G_t + beta AV_{t-1};  V_t = -G_t + beta V_{t-1}
-      const float4 g = *(const float4*)(a.G + o);
-      float4 w = make_float4(fmaf(s, acc.x, g.x), fmaf(s, acc.y, g.y), fmaf(s, acc.z, g.z),
-                             fmaf(s, acc.w, g.w));
-      float4 v = make_float4(-g.x, -g.y, -g.z, -g.w);
-      if (!a.first) {
-        const float4 b = *(const float4*)(a.beta + c);
-        const float4 wp = *(const float4*)(a.W + o);
-        const float4 vp = *(const float4*)(a.V + o);
-        w.x = fmaf(b.x, wp.x, w.x);
-        w.y = fmaf(b.y, wp.y, w.y);
-        w.z = fmaf(b.z, wp.z, w.z);
-        w.w = fmaf(b.w, wp.w, w.w);
-        v.x = fmaf(b.x, vp.x, v.x);
-        v.y = fmaf(b.y, vp.y, v.y);
-        v.z = fmaf(b.z, vp.z, v.z);
-        v.w = fmaf(b.w, vp.w, v.w);
-      }
-      *(float4*)(a.W + o) = w;
-      *(float4*)(a.V + o) = v;
-      if (DOTS) {  // diag(V^T AV) and diag(V^T AX) for the f1 line searches
-        const float4 y = *(const float4*)(a.Y + o);
-        dcw.x = fmaf(v.x, w.x, dcw.x); dcw.y = fmaf(v.y, w.y, dcw.y);
-        dcw.z = fmaf(v.z, w.z, dcw.z); dcw.w = fmaf(v.w, w.w, dcw.w);
-        dey.x = fmaf(v.x, y.x, dey.x); dey.y = fmaf(v.y, y.y, dey.y);
-        dey.z = fmaf(v.z, y.z, dey.z); dey.w = fmaf(v.w, y.w, dey.w);
-      }
-    } else {
-      const float4 x = *(const float4*)(a.X + o);
-      *(float4*)(a.Y + o) = make_float4(-fmaf(s, acc.x, x.x), -fmaf(s, acc.y, x.y),
-                                        -fmaf(s, acc.z, x.z), -fmaf(s, acc.w, x.w));
     }
   }
-  if (DOTS) {  // per-block partials in a fixed order: groups, then columns
-    float* r = dred + (size_t)grp * 2 * (LANES * 4);
-    *(float4*)(r + c) = dcw;
-    *(float4*)(r + LANES * 4 + c) = dey;
+  if (DOTS) {  // per-block partials of diag(V^T AV), diag(V^T G) in a fixed order: groups, columns
+    constexpr int W = LANES * 4;
+    float* rr = dred + (size_t)grp * 2 * W;
+    *(float4*)(rr + c) = dcw;
+    *(float4*)(rr + W + c) = dvg;
     __syncthreads();
     for (int j = threadIdx.x; j < 2 * a.kp; j += blockDim.x) {
       const int which = j / a.kp, col = j % a.kp;
       double sum = 0.0;
-      for (int g = 0; g < GROUPS; ++g) sum += (double)dred[(size_t)g * 2 * (LANES * 4) + which * (LANES * 4) + col];
+      for (int g = 0; g < GPB; ++g) sum += (double)dred[(size_t)g * 2 * W + which * W + col];
       a.dots[(int64_t)blockIdx.x * 2 * a.kp + j] = sum;
     }
   }
 }
 
+// V_t = -G_t + V_{t-1} diag(beta) (V_0 = -G_0) and its gather copy Vh = D^-1/2 V_t (FP32 or BF16).
+template <bool BF16>
+__global__ void k_vpass(int64_t n, int kp, const float* __restrict__ G, float* __restrict__ V, void* __restrict__ Vh,
+                        const float* __restrict__ dinv, const float* __restrict__ beta, int first, Ctrl* ctrl) {
+  if (ctrl->done) return;
+  const int64_t total = n * kp / 4;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = i * 4;
+    const int64_t row = e / kp;
+    const int c = (int)(e - row * kp);
+    const float4 g = *(const float4*)(G + e);
+    float4 v = make_float4(-g.x, -g.y, -g.z, -g.w);
+    if (!first) {
+      const float4 b = *(const float4*)(beta + c);
+      const float4 vp = *(const float4*)(V + e);
+      v.x = fmaf(b.x, vp.x, v.x);
+      v.y = fmaf(b.y, vp.y, v.y);
+      v.z = fmaf(b.z, vp.z, v.z);
+      v.w = fmaf(b.w, vp.w, v.w);
+    }
+    *(float4*)(V + e) = v;
+    const float s = dinv[row];
+    if (BF16) {
+      __nv_bfloat162 h0 = __floats2bfloat162_rn(s * v.x, s * v.y);
+      __nv_bfloat162 h1 = __floats2bfloat162_rn(s * v.z, s * v.w);
+      uint2 u;
+      u.x = *reinterpret_cast<uint32_t*>(&h0);
+      u.y = *reinterpret_cast<uint32_t*>(&h1);
+      *(uint2*)((__nv_bfloat16*)Vh + e) = u;
+    } else {
+      *(float4*)((float*)Vh + e) = make_float4(s * v.x, s * v.y, s * v.z, s * v.w);
+    }
+  }
+}
+
 // ------------------------------------------------------------------------------------------
-// Direction pass: optional update, G = g(X), Gh = D^-1/2 G, column sums for beta
+// Direction pass: optional update, G = g(X), column sums for beta
 // ------------------------------------------------------------------------------------------
 
 struct RowArgs {
@@ -256,14 +297,13 @@ struct RowArgs {
   const float* V;
   const float* W;
   float* G;
-  void* Gh;
-  const float* dinv;
   const float* Rn;
   const float* Bn;
   const float* alpha;
-  double* colpart;  // [gridDim.x][3][kp]: sum G^2, sum (G - G_prev) G, sum G_prev^2
+  double* colpart;  // [gridDim.x][5][kp]: sums of G^2, (G - G_prev) G, G_prev^2, G AX, V_prev AX
   Ctrl* ctrl;
   int update;
+  int need_vy;      // read V_{t-1} for the V_prev AX sums even without an update
   int eval;         // no previous G (objective/gradient evaluation and the final report)
   int ignore_done;
 };
@@ -274,7 +314,8 @@ struct RowArgs {
 // k x k block (triu-masked for TriOFM) stays resident in shared memory. All global loads of a
 // batch are issued before any arithmetic, so each warp keeps up to 5 * KPB 16-byte loads in
 // flight. Column sums (for beta and ||G||) go to per-block partials in a fixed order.
-constexpr int kKPB = 8;  // rows per slot per batch
+constexpr int kKPB = 8;       // rows per slot per batch
+constexpr int kColSums = 5;  // column sums of the direction pass
 
 template <int KPMAX, bool F2>
 struct DirShape {
@@ -285,13 +326,13 @@ struct DirShape {
   static constexpr int NSTAGE = F2 ? 2 : 1;
   static constexpr size_t kk_floats = (size_t)KPMAX * KPMAX * (F2 ? 2 : 1);
   static constexpr size_t stage_floats = (size_t)(kRowThreads / 32) * S * SSTR * NSTAGE;
-  static constexpr size_t red_doubles = (size_t)(kRowThreads / 32) * S * 3 * KPMAX;
+  static constexpr size_t red_doubles = (size_t)(kRowThreads / 32) * S * kColSums * KPMAX;
   static constexpr size_t bytes() {
     return kk_floats * 4 + (stage_floats * 4 > red_doubles * 8 ? stage_floats * 4 : red_doubles * 8);
   }
 };
 
-template <int METHOD, int KPMAX, bool BF16>
+template <int METHOD, int KPMAX>
 __global__ void __launch_bounds__(kRowThreads, 1) k_direction(RowArgs a) {
   if (!a.ignore_done && a.ctrl->done) return;
   constexpr bool F2 = METHOD >= M_OFM_F2;
@@ -327,6 +368,7 @@ __global__ void __launch_bounds__(kRowThreads, 1) k_direction(RowArgs a) {
 
   // per-lane running column sums (FP32: a lane adds one row-batch partial at a time)
   float sgg[4] = {0, 0, 0, 0}, snum[4] = {0, 0, 0, 0}, sden[4] = {0, 0, 0, 0};
+  float sgy[4] = {0, 0, 0, 0}, svy[4] = {0, 0, 0, 0};
   const int64_t nwarps = (int64_t)gridDim.x * (kRowThreads / 32);
   const int64_t nbatch = (a.n + Sh::ROWS - 1) / Sh::ROWS;
   for (int64_t b = (int64_t)blockIdx.x * (kRowThreads / 32) + warp; b < nbatch; b += nwarps) {
@@ -340,7 +382,7 @@ __global__ void __launch_bounds__(kRowThreads, 1) k_direction(RowArgs a) {
       const bool ok = active && r < a.n;
       x[i] = ok ? *(const float4*)(Xp + r * kp + c) : z;
       y[i] = ok ? *(const float4*)(Yp + r * kp + c) : z;
-      v[i] = (ok && a.update) ? *(const float4*)(Vp + r * kp + c) : z;
+      v[i] = (ok && (a.update || a.need_vy)) ? *(const float4*)(Vp + r * kp + c) : z;
       w[i] = (ok && a.update) ? *(const float4*)(Wp + r * kp + c) : z;
       gp[i] = (ok && !a.eval) ? *(const float4*)(Gp + r * kp + c) : z;
     }
@@ -401,11 +443,13 @@ __global__ void __launch_bounds__(kRowThreads, 1) k_direction(RowArgs a) {
     }
     __syncwarp();  // the stage is rewritten by the next batch
     float tg[4] = {0, 0, 0, 0}, tn[4] = {0, 0, 0, 0}, td[4] = {0, 0, 0, 0};
+    float ty[4] = {0, 0, 0, 0}, tv[4] = {0, 0, 0, 0};
 #pragma unroll
     for (int i = 0; i < kKPB; ++i) {
       const int64_t r = row0 + i;
       if (!active || r >= a.n) continue;
       const float yv[4] = {y[i].x, y[i].y, y[i].z, y[i].w};
+      const float vv[4] = {v[i].x, v[i].y, v[i].z, v[i].w};
       const float av[4] = {acc[i].x, acc[i].y, acc[i].z, acc[i].w};
       float g[4];
 #pragma unroll
@@ -418,22 +462,13 @@ __global__ void __launch_bounds__(kRowThreads, 1) k_direction(RowArgs a) {
       const int64_t o = r * kp + c;
       const float gpv[4] = {gp[i].x, gp[i].y, gp[i].z, gp[i].w};
       *(float4*)(Gp + o) = make_float4(g[0], g[1], g[2], g[3]);
-      const float s = a.dinv[r];
-      if (BF16) {
-        __nv_bfloat162 h0 = __floats2bfloat162_rn(s * g[0], s * g[1]);
-        __nv_bfloat162 h1 = __floats2bfloat162_rn(s * g[2], s * g[3]);
-        uint2 u;
-        u.x = *reinterpret_cast<uint32_t*>(&h0);
-        u.y = *reinterpret_cast<uint32_t*>(&h1);
-        *(uint2*)((__nv_bfloat16*)a.Gh + o) = u;
-      } else {
-        *(float4*)((float*)a.Gh + o) = make_float4(s * g[0], s * g[1], s * g[2], s * g[3]);
-      }
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         tg[q] = fmaf(g[q], g[q], tg[q]);
         tn[q] = fmaf(g[q] - gpv[q], g[q], tn[q]);
         td[q] = fmaf(gpv[q], gpv[q], td[q]);
+        ty[q] = fmaf(g[q], yv[q], ty[q]);
+        tv[q] = fmaf(vv[q], yv[q], tv[q]);
       }
     }
 #pragma unroll
@@ -441,26 +476,30 @@ __global__ void __launch_bounds__(kRowThreads, 1) k_direction(RowArgs a) {
       sgg[q] += tg[q];
       snum[q] += tn[q];
       sden[q] += td[q];
+      sgy[q] += ty[q];
+      svy[q] += tv[q];
     }
   }
   // per-block column sums in a fixed order: (warp, slot) contributions, then over them
   __syncthreads();
-  double* red = (double*)stage;  // [warps * S][3][KPMAX]
+  double* red = (double*)stage;  // [warps * S][kColSums][KPMAX]
   const int ws = warp * Sh::S + slot;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     if (c + q < KPMAX) {
-      red[((size_t)ws * 3 + 0) * KPMAX + c + q] = (double)sgg[q];
-      red[((size_t)ws * 3 + 1) * KPMAX + c + q] = (double)snum[q];
-      red[((size_t)ws * 3 + 2) * KPMAX + c + q] = (double)sden[q];
+      red[((size_t)ws * kColSums + 0) * KPMAX + c + q] = (double)sgg[q];
+      red[((size_t)ws * kColSums + 1) * KPMAX + c + q] = (double)snum[q];
+      red[((size_t)ws * kColSums + 2) * KPMAX + c + q] = (double)sden[q];
+      red[((size_t)ws * kColSums + 3) * KPMAX + c + q] = (double)sgy[q];
+      red[((size_t)ws * kColSums + 4) * KPMAX + c + q] = (double)svy[q];
     }
   }
   __syncthreads();
-  for (int j = tid; j < 3 * kp; j += blockDim.x) {
+  for (int j = tid; j < kColSums * kp; j += blockDim.x) {
     const int which = j / kp, col = j % kp;
     double sum = 0.0;
-    for (int w = 0; w < (kRowThreads / 32) * Sh::S; ++w) sum += red[((size_t)w * 3 + which) * KPMAX + col];
-    a.colpart[(int64_t)blockIdx.x * 3 * kp + which * kp + col] = sum;
+    for (int w = 0; w < (kRowThreads / 32) * Sh::S; ++w) sum += red[((size_t)w * kColSums + which) * KPMAX + col];
+    a.colpart[(int64_t)blockIdx.x * kColSums * kp + which * kp + col] = sum;
   }
 }
 
@@ -469,17 +508,19 @@ __global__ void __launch_bounds__(kRowThreads, 1) k_direction(RowArgs a) {
 // ------------------------------------------------------------------------------------------
 
 __global__ void k_beta(const double* __restrict__ colpart, int nblk, int kp, float* beta,
-                       double* beta64, Ctrl* ctrl, int first, int eval) {
+                       double* beta64, double* dE, Ctrl* ctrl, int first, int eval) {
   if (!eval && ctrl->done) return;
   __shared__ double sh[256];
   const int j = threadIdx.x;
-  double gg = 0.0, num = 0.0, den = 0.0;
+  double gg = 0.0, num = 0.0, den = 0.0, gy = 0.0, vy = 0.0;
   if (j < kp) {
     for (int b = 0; b < nblk; ++b) {
-      const double* p = colpart + (int64_t)b * 3 * kp;
+      const double* p = colpart + (int64_t)b * kColSums * kp;
       gg += p[j];
       num += p[kp + j];
       den += p[2 * kp + j];
+      gy += p[3 * kp + j];
+      vy += p[4 * kp + j];
     }
   }
   sh[j] = gg;
@@ -530,6 +571,8 @@ __global__ void k_beta(const double* __restrict__ colpart, int nblk, int kp, flo
     if (!first && den != 0.0) b = num / den;
     beta[j] = (float)b;
     beta64[j] = b;
+    // diag(V_t^T AX_t) with V_t = -G_t + V_{t-1} diag(beta): -diag(G^T AX) + beta diag(V_prev^T AX)
+    if (dE) dE[j] = first ? -gy : -gy + b * vy;
   }
 }
 
@@ -785,8 +828,9 @@ __device__ void block_sum(double (&v)[NV], double* sh) {
 
 struct SolveArgs {
   const double* gram;  // [6][kp*kp]: V^T X (P), V^T V (Q); f2 methods also V^T AX (E), V^T AV (C)
-  const double* dots;  // f1 methods: [dots_blocks][2][kp] partials of diag(V^T AV), diag(V^T AX)
+  const double* dots;  // [dots_blocks][2][kp] partials of diag(V^T AV), diag(V^T G)
   int dots_blocks;
+  const double* dE;    // f1 methods: diag(V^T AX) from the direction pass and beta (objective only)
   double* R64;         // X^T X of X_t on entry, of X_{t+1} on exit
   double* B64;         // X^T A X likewise (f2 methods)
   int kp;
@@ -804,10 +848,10 @@ struct SolveArgs {
 
 __global__ void __launch_bounds__(256) k_solve(SolveArgs a) {
   if (a.ctrl->done) return;
-  __shared__ double sh[12 * 256];
+  __shared__ double sh[12 * 256];  // block_sum scratch for up to 12 values
   __shared__ double coef[kMaxK][4];
   __shared__ double al[kMaxK];
-  __shared__ double dC[kMaxK], dE[kMaxK];
+  __shared__ double dC[kMaxK], dE[kMaxK], dG[kMaxK];
   __shared__ int bad;
   const int kp = a.kp, k = a.k, kk = kp * kp, tid = threadIdx.x;
   const bool f2 = is_f2(a.method);
@@ -821,17 +865,21 @@ __global__ void __launch_bounds__(256) k_solve(SolveArgs a) {
 #define SYM(M, i, j) (0.5 * ((M)[(i) * kp + (j)] + (M)[(j) * kp + (i)]))
   if (tid == 0) bad = 0;
   for (int j = tid; j < kp; j += blockDim.x) {
+    double sc = 0.0, sg = 0.0;
+    for (int b = 0; b < a.dots_blocks; ++b) {
+      sc += a.dots[(int64_t)b * 2 * kp + j];
+      sg += a.dots[(int64_t)b * 2 * kp + kp + j];
+    }
+    // The constant term of every cubic is the derivative along V at alpha = 0, i.e. diag(V^T G)
+    // (with the 1/4 of Eq. (15) for OFM-f1): summing v.g directly avoids the cancellation in
+    // tr(V^T AX) + tr(V^T X X^T X) near a fixed point, where AX = -X X^T X.
+    dG[j] = sg;
     if (f2) {
       dC[j] = C[j * kp + j];
       dE[j] = E[j * kp + j];
     } else {
-      double sc = 0.0, se = 0.0;
-      for (int b = 0; b < a.dots_blocks; ++b) {
-        sc += a.dots[(int64_t)b * 2 * kp + j];
-        se += a.dots[(int64_t)b * 2 * kp + kp + j];
-      }
       dC[j] = sc;
-      dE[j] = se;
+      dE[j] = a.dE[j];
     }
   }
   // objective at X_t: f1 = ||A||^2 + 2 tr B + ||R||^2, f2 = 2 tr B - tr(R B)
@@ -866,16 +914,17 @@ __global__ void __launch_bounds__(256) k_solve(SolveArgs a) {
       }
       for (int j = tid; j < kp; j += 256) {
         t[6] += dC[j];
-        t[7] += dE[j];
+        t[7] += dG[j];
       }
       block_sum<8>(t, sh);
       c3 = t[0];
       c2 = 3.0 * t[1];
       c1 = t[6] + t[2] + t[3] + t[4];
-      c0 = t[7] + t[5];
+      c0 = 0.25 * t[7];  // = tr(E) + tr(P R) with G = grad f1 = 4 (AX + X X^T X)
     } else {
       // d/dalpha f2 = tr(V^T (4 A Z - 2 Z Z^T A Z - 2 A Z Z^T Z)), Z = X + aV
-      double t[11] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+      double t[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+      for (int j = tid; j < kp; j += 256) t[11] += dG[j];
       for (int i = tid; i < kk; i += 256) {
         const int r = i / kp, c = i % kp, it = c * kp + r;
         const double q = Q[i], p = P[i], rr = R[i], e = E[i];
@@ -894,11 +943,11 @@ __global__ void __launch_bounds__(256) k_solve(SolveArgs a) {
           t[10] += e;
         }
       }
-      block_sum<11>(t, sh);
+      block_sum<12>(t, sh);
       c3 = -4.0 * t[0];
       c2 = -6.0 * (t[1] + t[2]);
       c1 = 2.0 * (2.0 * t[9] - 2.0 * t[3] - 2.0 * t[4] - t[5] - t[6]);
-      c0 = 2.0 * (2.0 * t[10] - t[7] - t[8]);
+      c0 = t[11];  // = 2 tr(2E - P B - R E) = tr(V^T grad f2)
     }
     if (tid == 0) {
       int b = 0;
@@ -913,19 +962,17 @@ __global__ void __launch_bounds__(256) k_solve(SolveArgs a) {
       const int j = tid;
       double d0 = 0, d1 = 0, d2 = 0, d3 = 0;
       if (a.method == M_TRI_F1) {
-        d0 = dE[j];
         d1 = dC[j];
         for (int m = 0; m <= j; ++m) {
           // (P_jm + a Q_jm)(R_mj + a (P_jm + P_mj) + a^2 Q_mj)
           const double x0 = P[j * kp + m], x1 = Q[j * kp + m];
           const double y0 = R[m * kp + j], y1 = P[j * kp + m] + P[m * kp + j], y2 = Q[m * kp + j];
-          d0 += x0 * y0;
           d1 += x0 * y1 + x1 * y0;
           d2 += x0 * y2 + x1 * y1;
           d3 += x1 * y2;
         }
+        d0 = dG[j];  // = E_jj + sum_{m<=j} P_jm R_mj = v_j^T g1_j
       } else {
-        d0 = 2.0 * dE[j];
         d1 = 2.0 * dC[j];
         for (int m = 0; m <= j; ++m) {
           // -(E_jm + a C_jm)(R_mj + a (P_jm + P_mj) + a^2 Q_mj)
@@ -934,11 +981,11 @@ __global__ void __launch_bounds__(256) k_solve(SolveArgs a) {
           // -(P_jm + a Q_jm)(B_mj + a (E_jm + E_mj) + a^2 C_mj)
           const double u0 = P[j * kp + m], u1 = Q[j * kp + m];
           const double w0 = SYM(B, m, j), w1 = E[j * kp + m] + E[m * kp + j], w2 = SYM(C, m, j);
-          d0 -= x0 * y0 + u0 * w0;
           d1 -= x0 * y1 + x1 * y0 + u0 * w1 + u1 * w0;
           d2 -= x0 * y2 + x1 * y1 + u0 * w2 + u1 * w1;
           d3 -= x1 * y2 + u1 * w2;
         }
+        d0 = dG[j];  // = 2 E_jj - sum_{m<=j} (E_jm R_mj + P_jm B_mj) = v_j^T g2_j
       }
       coef[j][0] = d3;
       coef[j][1] = d2;
@@ -1050,7 +1097,6 @@ constexpr int kGramTargetBlocks = 4 * kNumSMs;
 
 thread_local int64_t g_launches = 0;  // kernels launched by the current call on this thread
 
-int lanes_for(int kp) { return kp <= 8 ? 2 : kp <= 16 ? 4 : kp <= 32 ? 8 : kp <= 64 ? 16 : 32; }
 int gram_m_for(int kp) { return kp <= 16 ? 1 : kp <= 32 ? 2 : 4; }
 int gram_nt_for(int kp) { return (int)ceil_div(kp, 16 * gram_m_for(kp)); }
 
@@ -1106,23 +1152,15 @@ struct Prof {
   }
 };
 
-template <int LANES>
-int spmm_grid(int64_t n) {
-  return (int)std::min<int64_t>(ceil_div(n, 256 / LANES), 8 * kNumSMs);
-}
-
-int spmm_grid_for(int64_t n, int kp);
-
 template <int LANES, int MODE, bool BF16, bool DOTS>
 void launch_spmm_w(const SpmmArgs& a, bool weighted, cudaStream_t s) {
-  const int grid = spmm_grid<LANES>(a.n);
+  const int grid = a.groups / (256 / LANES);
   if (weighted) k_spmm<LANES, true, MODE, BF16, DOTS><<<grid, 256, 0, s>>>(a);
   else k_spmm<LANES, false, MODE, BF16, DOTS><<<grid, 256, 0, s>>>(a);
 }
 
 template <int LANES>
 void launch_spmm_l(const SpmmArgs& a, bool weighted, int mode, bool bf16, cudaStream_t s) {
-  if (a.n <= 0) return;
   ++g_launches;
   const bool dots = a.dots != nullptr;
   if (mode == SP_DIR) {
@@ -1138,19 +1176,9 @@ void launch_spmm_l(const SpmmArgs& a, bool weighted, int mode, bool bf16, cudaSt
   }
 }
 
-int spmm_grid_for(int64_t n, int kp) {
-  switch (lanes_for(kp)) {
-    case 2: return spmm_grid<2>(n);
-    case 4: return spmm_grid<4>(n);
-    case 8: return spmm_grid<8>(n);
-    case 16: return spmm_grid<16>(n);
-    default: return spmm_grid<32>(n);
-  }
-}
-
 void launch_spmm(const SpmmArgs& a, bool weighted, int mode, bool bf16, cudaStream_t s) {
   if (a.n <= 0) return;
-  switch (lanes_for(a.kp)) {
+  switch (spmm_lanes(a.kp)) {
     case 2: launch_spmm_l<2>(a, weighted, mode, bf16, s); break;
     case 4: launch_spmm_l<4>(a, weighted, mode, bf16, s); break;
     case 8: launch_spmm_l<8>(a, weighted, mode, bf16, s); break;
@@ -1161,17 +1189,17 @@ void launch_spmm(const SpmmArgs& a, bool weighted, int mode, bool bf16, cudaStre
 
 int kpmax_for(int kp) { return kp <= 16 ? 16 : kp <= 32 ? 32 : kp <= 64 ? 64 : 128; }
 
-template <int METHOD, int KPMAX, bool BF16>
+template <int METHOD, int KPMAX>
 cudaError_t launch_direction_t(const RowArgs& a, cudaStream_t s, int* nblk_out) {
   using Sh = DirShape<KPMAX, (METHOD >= M_OFM_F2)>;
   static int blocks_per_sm = 0;
   const size_t smem = Sh::bytes();
   if (blocks_per_sm == 0) {
-    cudaError_t e = cudaFuncSetAttribute(k_direction<METHOD, KPMAX, BF16>,
+    cudaError_t e = cudaFuncSetAttribute(k_direction<METHOD, KPMAX>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int nb = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_direction<METHOD, KPMAX, BF16>, kRowThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_direction<METHOD, KPMAX>, kRowThreads, smem);
     if (e != cudaSuccess) return e;
     blocks_per_sm = nb > 0 ? nb : 1;
   }
@@ -1179,32 +1207,28 @@ cudaError_t launch_direction_t(const RowArgs& a, cudaStream_t s, int* nblk_out) 
   int grid = (int)std::min<int64_t>(ceil_div(warps_needed, kRowThreads / 32), (int64_t)blocks_per_sm * kNumSMs);
   if (grid > kMaxRowBlocks) grid = kMaxRowBlocks;
   if (grid < 1) grid = 1;
-  k_direction<METHOD, KPMAX, BF16><<<grid, kRowThreads, smem, s>>>(a);
+  k_direction<METHOD, KPMAX><<<grid, kRowThreads, smem, s>>>(a);
   ++g_launches;
   *nblk_out = grid;
   return cudaGetLastError();
 }
 
-template <int METHOD, bool BF16>
+template <int METHOD>
 cudaError_t launch_direction_m(const RowArgs& a, cudaStream_t s, int* nblk) {
   switch (kpmax_for(a.kp)) {
-    case 16: return launch_direction_t<METHOD, 16, BF16>(a, s, nblk);
-    case 32: return launch_direction_t<METHOD, 32, BF16>(a, s, nblk);
-    case 64: return launch_direction_t<METHOD, 64, BF16>(a, s, nblk);
-    default: return launch_direction_t<METHOD, 128, BF16>(a, s, nblk);
+    case 16: return launch_direction_t<METHOD, 16>(a, s, nblk);
+    case 32: return launch_direction_t<METHOD, 32>(a, s, nblk);
+    case 64: return launch_direction_t<METHOD, 64>(a, s, nblk);
+    default: return launch_direction_t<METHOD, 128>(a, s, nblk);
   }
 }
 
-cudaError_t launch_rowpass(int method, bool bf16, const RowArgs& a, cudaStream_t s, int* nblk) {
-  switch (method * 2 + (bf16 ? 1 : 0)) {
-    case 0: return launch_direction_m<M_OFM_F1, false>(a, s, nblk);
-    case 1: return launch_direction_m<M_OFM_F1, true>(a, s, nblk);
-    case 2: return launch_direction_m<M_TRI_F1, false>(a, s, nblk);
-    case 3: return launch_direction_m<M_TRI_F1, true>(a, s, nblk);
-    case 4: return launch_direction_m<M_OFM_F2, false>(a, s, nblk);
-    case 5: return launch_direction_m<M_OFM_F2, true>(a, s, nblk);
-    case 6: return launch_direction_m<M_TRI_F2, false>(a, s, nblk);
-    default: return launch_direction_m<M_TRI_F2, true>(a, s, nblk);
+cudaError_t launch_rowpass(int method, const RowArgs& a, cudaStream_t s, int* nblk) {
+  switch (method) {
+    case M_OFM_F1: return launch_direction_m<M_OFM_F1>(a, s, nblk);
+    case M_TRI_F1: return launch_direction_m<M_TRI_F1>(a, s, nblk);
+    case M_OFM_F2: return launch_direction_m<M_OFM_F2>(a, s, nblk);
+    default: return launch_direction_m<M_TRI_F2>(a, s, nblk);
   }
 }
 
@@ -1264,7 +1288,7 @@ ofsc_status ensure_workspace(ofsc_graph* g, int kp) {
       {(void**)&ws.V, blk},
       {(void**)&ws.W, blk},
       {(void**)&ws.G, blk},
-      {(void**)&ws.Gh, blk},
+      {(void**)&ws.Vh, blk},
       {(void**)&ws.gram_part, (size_t)gy * kPairs * kk * sizeof(double)},
       {(void**)&ws.gram, kPairs * kk * sizeof(double)},
       {(void**)&ws.Rn, kk * sizeof(float)},
@@ -1279,7 +1303,8 @@ ofsc_status ensure_workspace(ofsc_graph* g, int kp) {
       {(void**)&ws.beta, kp * sizeof(float)},
       {(void**)&ws.alpha64, kp * sizeof(double)},
       {(void**)&ws.beta64, kp * sizeof(double)},
-      {(void**)&ws.colpart, (size_t)kMaxRowBlocks * 3 * kp * sizeof(double)},
+      {(void**)&ws.colpart, (size_t)kMaxRowBlocks * kColSums * kp * sizeof(double)},
+      {(void**)&ws.dE, (size_t)kp * sizeof(double)},
       {(void**)&ws.ctrl, sizeof(Ctrl)},
   };
   size_t total = 0;
@@ -1353,6 +1378,9 @@ struct Runner {
     a.col = g->col;
     a.val = g->val;
     a.dinv = g->dinv;
+    const int pi = spmm_lanes_index(spmm_lanes(ws.kp));
+    a.bnd = g->bnd[pi];
+    a.groups = g->groups[pi];
     a.ctrl = ws.ctrl;
     return a;
   }
@@ -1361,8 +1389,8 @@ struct Runner {
   cudaError_t refresh(int objective, int ignore_done) {
     SpmmArgs a = spmm_base();
     a.gather = ws.X;
-    a.X = ws.X;
-    a.Y = ws.Y;
+    a.base = ws.X;
+    a.out = ws.Y;
     a.ignore_done = ignore_done;
     prof.begin(OFSC_PHASE_REFRESH);
     launch_spmm(a, g->weighted != 0, SP_Y, false, s);
@@ -1377,7 +1405,7 @@ struct Runner {
     return cudaGetLastError();
   }
 
-  cudaError_t rowpass(int dir_method, int update, int eval, int ignore_done, int* nblk) {
+  cudaError_t rowpass(int dir_method, int update, int eval, int ignore_done, int* nblk, int need_vy = 0) {
     RowArgs r{};
     r.n = ws.n;
     r.kp = ws.kp;
@@ -1386,35 +1414,37 @@ struct Runner {
     r.V = ws.V;
     r.W = ws.W;
     r.G = ws.G;
-    r.Gh = ws.Gh;
-    r.dinv = g->dinv;
     r.Rn = ws.Rn;
     r.Bn = ws.Bn;
     r.alpha = ws.alpha;
     r.colpart = ws.colpart;
     r.ctrl = ws.ctrl;
     r.update = update;
+    r.need_vy = need_vy;
     r.eval = eval;
     r.ignore_done = ignore_done;
     prof.begin(OFSC_PHASE_DIRECTION);
-    cudaError_t e = launch_rowpass(dir_method, bf16, r, s, nblk);
+    cudaError_t e = launch_rowpass(dir_method, r, s, nblk);
     prof.end();
     return e;
   }
 
   cudaError_t direction_and_linesearch(int first, const ofsc_opts& o, int k, double alpha0) {
     const bool f2 = method >= M_OFM_F2;
+    // V_t = -G_t + V_{t-1} diag(beta) and Vh = D^-1/2 V_t for the gather
+    prof.begin(OFSC_PHASE_OTHER);
+    const int vgrid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ws.n * ws.kp / 4, 256), 8 * kNumSMs));
+    if (bf16) k_vpass<true><<<vgrid, 256, 0, s>>>(ws.n, ws.kp, ws.G, ws.V, ws.Vh, g->dinv, ws.beta, first, ws.ctrl);
+    else k_vpass<false><<<vgrid, 256, 0, s>>>(ws.n, ws.kp, ws.G, ws.V, ws.Vh, g->dinv, ws.beta, first, ws.ctrl);
+    ++g_launches;
+    prof.end();
+    // AV_t exactly (one sparse product), with diag(V^T AV) and diag(V^T G)
     SpmmArgs a = spmm_base();
-    a.gather = ws.Gh;
+    a.gather = ws.Vh;
+    a.base = ws.V;
+    a.out = ws.W;
     a.G = ws.G;
-    a.V = ws.V;
-    a.W = ws.W;
-    a.beta = ws.beta;
-    a.first = first;
-    if (!f2) {  // the f1 line searches need only diag(V^T AV) and diag(V^T AX)
-      a.Y = ws.Y;
-      a.dots = ws.dots;
-    }
+    a.dots = ws.dots;
     prof.begin(OFSC_PHASE_SPMM);
     launch_spmm(a, g->weighted != 0, SP_DIR, bf16, s);
     prof.end();
@@ -1426,7 +1456,8 @@ struct Runner {
     SolveArgs sa{};
     sa.gram = ws.gram;
     sa.dots = ws.dots;
-    sa.dots_blocks = spmm_grid_for(ws.n, ws.kp);
+    sa.dots_blocks = a.groups / (256 / spmm_lanes(ws.kp));
+    sa.dE = ws.dE;
     sa.R64 = ws.R64;
     sa.B64 = ws.B64;
     sa.kp = ws.kp;
@@ -1561,13 +1592,13 @@ extern "C" ofsc_status ofsc_iterate(ofsc_graph* g, int32_t method, int32_t k, fl
       prof.end();
       OFSC_LAUNCH_CHECK("k_update_x");
       OFSC_CUDA(run.refresh(objective, 0));
-      OFSC_CUDA(run.rowpass(method, 0, 0, 0, &nblk));
+      OFSC_CUDA(run.rowpass(method, 0, 0, 0, &nblk, 1));
     } else {
       // t = 0 has no previous direction: evaluation mode skips the G_{t-1} read
       OFSC_CUDA(run.rowpass(method, t > 0 ? 1 : 0, t == 0 ? 1 : 0, 0, &nblk));
     }
     prof.begin(OFSC_PHASE_BETA);
-    k_beta<<<1, 256, 0, s>>>(ws.colpart, nblk, kp, ws.beta, ws.beta64, ws.ctrl, t == 0 ? 1 : 0, 0);
+    k_beta<<<1, 256, 0, s>>>(ws.colpart, nblk, kp, ws.beta, ws.beta64, ws.dE, ws.ctrl, t == 0 ? 1 : 0, 0);
     ++g_launches;
     prof.end();
     OFSC_LAUNCH_CHECK("k_beta");
@@ -1589,7 +1620,7 @@ extern "C" ofsc_status ofsc_iterate(ofsc_graph* g, int32_t method, int32_t k, fl
     OFSC_CUDA(run.refresh(objective, 1));
     int nblk = 0;
     OFSC_CUDA(run.rowpass(method, 0, 1, 1, &nblk));
-    k_beta<<<1, 256, 0, s>>>(ws.colpart, nblk, kp, ws.beta, ws.beta64, ws.ctrl, 0, 1);
+    k_beta<<<1, 256, 0, s>>>(ws.colpart, nblk, kp, ws.beta, ws.beta64, nullptr, ws.ctrl, 0, 1);
     ++g_launches;
     OFSC_LAUNCH_CHECK("k_beta(eval)");
   }
@@ -1642,7 +1673,7 @@ constexpr size_t kNoAllocBlockBytes = al256((size_t)kNoAllocMaxBlock * sizeof(fl
 constexpr size_t kNoAllocGramPart = al256((size_t)kNoAllocGramGroups * kPairs * kMaxK * kMaxK * sizeof(double));
 constexpr size_t kNoAllocGram = al256((size_t)kPairs * kMaxK * kMaxK * sizeof(double));
 constexpr size_t kNoAllocKK = al256((size_t)kMaxK * kMaxK * sizeof(float));
-constexpr size_t kNoAllocColpart = al256((size_t)kMaxRowBlocks * 3 * kMaxK * sizeof(double));
+constexpr size_t kNoAllocColpart = al256((size_t)kMaxRowBlocks * kColSums * kMaxK * sizeof(double));
 constexpr size_t kNoAllocBytes = kNoAllocCtrl + 4 * kNoAllocBlockBytes + kNoAllocGramPart +
                                  kNoAllocGram + 2 * kNoAllocKK + kNoAllocColpart;
 
@@ -1713,7 +1744,7 @@ extern "C" ofsc_status ofsc_objective_grad_noalloc(const ofsc_graph* gc, int32_t
   p += kNoAllocBlockBytes;
   ws.G = (float*)p;
   p += kNoAllocBlockBytes;
-  ws.Gh = p;
+  ws.Vh = p;
   p += kNoAllocBlockBytes;
   ws.gram_part = (double*)p;
   p += kNoAllocGramPart;
@@ -1735,8 +1766,8 @@ extern "C" ofsc_status ofsc_objective_grad_noalloc(const ofsc_graph* gc, int32_t
   // A X exactly, then X^T X and X^T A X with at most kNoAllocGramGroups row groups
   SpmmArgs a = run.spmm_base();
   a.gather = ws.X;
-  a.X = ws.X;
-  a.Y = ws.Y;
+  a.base = ws.X;
+  a.out = ws.Y;
   launch_spmm(a, g->weighted != 0, SP_Y, false, s);
   GramArgs ga;
   ga.n = ws.n;

@@ -53,6 +53,8 @@ enum { OFSC_F1 = 1, OFSC_F2 = 2 };
 enum { OFSC_GATHER_FP32 = 0, OFSC_GATHER_BF16 = 1 };
 /* Engine of the k x k Gram reductions: FP32 CUDA cores, or tcgen05 tensor cores (3-term TF32). */
 enum { OFSC_GRAM_AUTO = 0, OFSC_GRAM_SIMT = 1, OFSC_GRAM_TC = 2 };
+/* Row gathers of the sparse product: CUDA-core loads, or TMA tile::gather4 into shared memory. */
+enum { OFSC_SPMM_AUTO = 0, OFSC_SPMM_SIMT = 1, OFSC_SPMM_TMA = 2 };
 
 typedef struct ofsc_graph ofsc_graph;
 
@@ -122,7 +124,7 @@ ofsc_status ofsc_objective_grad(ofsc_graph* g, int32_t objective, int32_t k, con
  * latency-bound loop that cannot afford an allocation's driver call and implicit
  * synchronisation.
  *   Arguments, layout and results are those of ofsc_objective_grad; the graph is only read.
- *   Temporary storage comes from one static device array of about 27 MiB inside the library,
+ *   Temporary storage comes from one static device array of about 30 MiB inside the library,
  *   which every GPU that loads the library holds until the process exits.
  *   Limit: n * kp <= 2^20 with kp = k rounded up to a multiple of 8 (k <= 128); larger sizes
  *   return OFSC_ERR_INVALID_ARG with a message (use ofsc_objective_grad for them).
@@ -166,6 +168,8 @@ typedef struct {
   ofsc_profile* profile; /* HOST struct or NULL: the call ADDS its per-phase device times
                             (events around every launch; adds a little host overhead) */
   int32_t gram_engine;   /* OFSC_GRAM_AUTO (tensor cores when k > 64), OFSC_GRAM_SIMT, OFSC_GRAM_TC */
+  int32_t spmm_engine;   /* OFSC_SPMM_AUTO (TMA gather when padded k is 64 or 128), OFSC_SPMM_SIMT,
+                            OFSC_SPMM_TMA */
 } ofsc_opts;
 
 typedef struct {

@@ -25,6 +25,10 @@ Readings of the paper taken where it is silent or ambiguous (each one is pinned 
   * TriOFM has no objective, so "minimal function value" becomes the minimal value of the
     antiderivative q(alpha) of the printed cubic. For OFM the objective itself is evaluated.
   * The paper's momentum coefficient is Polak-Ribiere as Algorithm 2 writes it; 0/0 -> 0.
+  * Algorithm 2 has no restart. A column whose new direction would not descend,
+    v_j^T g_j = -|g_j|^2 + beta_j v_prev,j^T g_j >= 0, restarts with beta_j = 0 (once a column's
+    gradient is at rounding level its beta is noise and, without the restart, v_j grows
+    geometrically until the line searches of every later prefix collapse).
   * Step 0 of Algorithm 2 uses the same exact line search unless a fixed alpha0 > 0 is given.
   * Stop when ||G_t||_F / ||G_0||_F <= tol, or after maxit updates (Algorithm 2's t_max).
   * Isolated nodes (degree 0) get D^-1/2 = 0, i.e. L_ii = 1.
@@ -382,7 +386,8 @@ def iterate(g: Graph, method: int, X0: np.ndarray, tol: float, maxit: int,
 
     G_0 = g(X_0); V_0 = -G_0; X_1 = X_0 + alpha V_0 (alpha0 > 0 given, else exact line
     search); then for t = 1, 2, ...: G_t = g(X_t); stop if ||G_t|| <= tol ||G_0|| or t = maxit;
-    beta_i = sum_l (G_t - G_{t-1})_li G_t,li / sum_l G_{t-1,li}^2 (0 when the denominator is 0);
+    beta_i = sum_l (G_t - G_{t-1})_li G_t,li / sum_l G_{t-1,li}^2 (0 when the denominator is 0,
+    and 0 when the column's new direction would not descend: -|g_i|^2 + beta_i v_i^T g_i >= 0);
     V_t = -G_t + V_{t-1} diag(beta); alpha by exact line search; X_{t+1} = X_t + V_t diag(alpha).
     """
     X = np.array(X0, dtype=np.float64)
@@ -419,6 +424,8 @@ def iterate(g: Graph, method: int, X0: np.ndarray, tol: float, maxit: int,
         num = np.sum((Gn - G) * Gn, axis=0)
         den = np.sum(G * G, axis=0)
         beta = np.where(den != 0.0, num / np.where(den != 0.0, den, 1.0), 0.0)
+        descent = -np.sum(Gn * Gn, axis=0) + beta * np.sum(V * Gn, axis=0)
+        beta = np.where(descent >= 0.0, 0.0, beta)
         V = -Gn + V * beta[None, :]
         AV = apply_A(g, V)
         alpha = step_sizes(g, method, X, V, AX, AV, normA2)

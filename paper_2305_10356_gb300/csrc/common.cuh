@@ -1,6 +1,7 @@
 // Internal declarations shared by the translation units of libofsc (not part of the C ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -98,6 +99,8 @@ struct Workspace {
   double* B64 = nullptr;        // kp*kp: X^T A X of the current X (f2 methods)
   double* dots = nullptr;       // [spmm blocks][2][kp]: partial diag(V^T AV), diag(V^T AX)
   float* part_tc = nullptr;     // tensor-core Gram partials (kp > 64)
+  CUtensorMap vh_map[2];        // TMA maps over Vh as FP32 [0] and BF16 [1] (gather4 rows)
+  bool vh_map_ok[2] = {false, false};
   float* alpha = nullptr;       // kp
   float* beta = nullptr;        // kp
   double* alpha64 = nullptr;    // kp
@@ -154,6 +157,27 @@ struct GramTcArgs {
   Ctrl* ctrl;            // status / stop flag (may be null only with ignore_done = 1)
   int ignore_done;
 };
+// Arguments of the TMA-gather sparse product (csrc/spmm_tma.cu): out = -base - D^-1/2 S Vh.
+struct TmaSpmmArgs {
+  int64_t n;
+  int kp;
+  const int64_t* row_ptr;
+  const int32_t* col;
+  const float* val;
+  const float* dinv;
+  const int64_t* bnd;   // [groups + 1] row ranges, one per warp
+  int groups;
+  const float* base;    // V
+  float* out;           // AV
+  const float* G;       // direction, for diag(V^T G)
+  double* dots;         // [groups / 4][2][kp]
+  Ctrl* ctrl;
+};
+bool spmm_tma_supported(int kp);
+int spmm_tma_groups_per_block();
+ofsc_status spmm_tma_encode(const void* vh, int64_t n, int kp, bool bf16, CUtensorMap* map);
+cudaError_t spmm_tma_launch(const CUtensorMap& map, const TmaSpmmArgs& a, bool bf16, bool weighted, cudaStream_t s);
+
 int64_t gram_tc_rows_per_cta(int64_t n, int nr);
 size_t gram_tc_part_bytes(int64_t n, int nr, int64_t rows_per_cta);
 cudaError_t gram_tc_launch(GramTcArgs a, const int* slot, int kp, double* gram, cudaStream_t s);

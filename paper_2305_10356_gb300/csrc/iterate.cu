@@ -300,7 +300,7 @@ struct RowArgs {
   const float* Rn;
   const float* Bn;
   const float* alpha;
-  double* colpart;  // [gridDim.x][5][kp]: sums of G^2, (G - G_prev) G, G_prev^2, G AX, V_prev AX
+  double* colpart;  // [gridDim.x][6][kp]: sums of G^2, (G - G_prev) G, G_prev^2, G AX, V_prev AX, V_prev G
   Ctrl* ctrl;
   int update;
   int need_vy;      // read V_{t-1} for the V_prev AX sums even without an update
@@ -315,7 +315,7 @@ struct RowArgs {
 // batch are issued before any arithmetic, so each warp keeps up to 5 * KPB 16-byte loads in
 // flight. Column sums (for beta and ||G||) go to per-block partials in a fixed order.
 constexpr int kKPB = 8;       // rows per slot per batch
-constexpr int kColSums = 5;  // column sums of the direction pass
+constexpr int kColSums = 6;  // column sums of the direction pass
 
 template <int KPMAX, bool F2>
 struct DirShape {
@@ -368,7 +368,7 @@ __global__ void __launch_bounds__(kRowThreads, 1) k_direction(RowArgs a) {
 
   // per-lane running column sums (FP32: a lane adds one row-batch partial at a time)
   float sgg[4] = {0, 0, 0, 0}, snum[4] = {0, 0, 0, 0}, sden[4] = {0, 0, 0, 0};
-  float sgy[4] = {0, 0, 0, 0}, svy[4] = {0, 0, 0, 0};
+  float sgy[4] = {0, 0, 0, 0}, svy[4] = {0, 0, 0, 0}, svg[4] = {0, 0, 0, 0};
   const int64_t nwarps = (int64_t)gridDim.x * (kRowThreads / 32);
   const int64_t nbatch = (a.n + Sh::ROWS - 1) / Sh::ROWS;
   for (int64_t b = (int64_t)blockIdx.x * (kRowThreads / 32) + warp; b < nbatch; b += nwarps) {
@@ -443,7 +443,7 @@ __global__ void __launch_bounds__(kRowThreads, 1) k_direction(RowArgs a) {
     }
     __syncwarp();  // the stage is rewritten by the next batch
     float tg[4] = {0, 0, 0, 0}, tn[4] = {0, 0, 0, 0}, td[4] = {0, 0, 0, 0};
-    float ty[4] = {0, 0, 0, 0}, tv[4] = {0, 0, 0, 0};
+    float ty[4] = {0, 0, 0, 0}, tv[4] = {0, 0, 0, 0}, tw[4] = {0, 0, 0, 0};
 #pragma unroll
     for (int i = 0; i < kKPB; ++i) {
       const int64_t r = row0 + i;
@@ -469,6 +469,7 @@ __global__ void __launch_bounds__(kRowThreads, 1) k_direction(RowArgs a) {
         td[q] = fmaf(gpv[q], gpv[q], td[q]);
         ty[q] = fmaf(g[q], yv[q], ty[q]);
         tv[q] = fmaf(vv[q], yv[q], tv[q]);
+        tw[q] = fmaf(vv[q], g[q], tw[q]);
       }
     }
 #pragma unroll
@@ -478,6 +479,7 @@ __global__ void __launch_bounds__(kRowThreads, 1) k_direction(RowArgs a) {
       sden[q] += td[q];
       sgy[q] += ty[q];
       svy[q] += tv[q];
+      svg[q] += tw[q];
     }
   }
   // per-block column sums in a fixed order: (warp, slot) contributions, then over them
@@ -492,6 +494,7 @@ __global__ void __launch_bounds__(kRowThreads, 1) k_direction(RowArgs a) {
       red[((size_t)ws * kColSums + 2) * KPMAX + c + q] = (double)sden[q];
       red[((size_t)ws * kColSums + 3) * KPMAX + c + q] = (double)sgy[q];
       red[((size_t)ws * kColSums + 4) * KPMAX + c + q] = (double)svy[q];
+      red[((size_t)ws * kColSums + 5) * KPMAX + c + q] = (double)svg[q];
     }
   }
   __syncthreads();
@@ -512,7 +515,7 @@ __global__ void k_beta(const double* __restrict__ colpart, int nblk, int kp, flo
   if (!eval && ctrl->done) return;
   __shared__ double sh[256];
   const int j = threadIdx.x;
-  double gg = 0.0, num = 0.0, den = 0.0, gy = 0.0, vy = 0.0;
+  double gg = 0.0, num = 0.0, den = 0.0, gy = 0.0, vy = 0.0, vg = 0.0;
   if (j < kp) {
     for (int b = 0; b < nblk; ++b) {
       const double* p = colpart + (int64_t)b * kColSums * kp;
@@ -521,6 +524,7 @@ __global__ void k_beta(const double* __restrict__ colpart, int nblk, int kp, flo
       den += p[2 * kp + j];
       gy += p[3 * kp + j];
       vy += p[4 * kp + j];
+      vg += p[5 * kp + j];
     }
   }
   sh[j] = gg;
@@ -569,6 +573,8 @@ __global__ void k_beta(const double* __restrict__ colpart, int nblk, int kp, flo
   if (j < kp) {
     double b = 0.0;
     if (!first && den != 0.0) b = num / den;
+    // restart a column whose new direction would not descend: -|g_j|^2 + beta_j v_prev,j^T g_j >= 0
+    if (-gg + b * vg >= 0.0) b = 0.0;
     beta[j] = (float)b;
     beta64[j] = b;
     // diag(V_t^T AX_t) with V_t = -G_t + V_{t-1} diag(beta): -diag(G^T AX) + beta diag(V_prev^T AX)
@@ -1295,7 +1301,7 @@ ofsc_status ensure_workspace(ofsc_graph* g, int kp) {
       {(void**)&ws.Bn, kk * sizeof(float)},
       {(void**)&ws.R64, kk * sizeof(double)},
       {(void**)&ws.B64, kk * sizeof(double)},
-      {(void**)&ws.dots, (size_t)8 * kNumSMs * 2 * kp * sizeof(double)},
+      {(void**)&ws.dots, (size_t)16 * kNumSMs * 2 * kp * sizeof(double)},
       {(void**)&ws.part_tc, kp > 64 ? std::max(gram_tc_part_bytes(n, 2, gram_tc_rows_per_cta(n, 2)),
                                                gram_tc_part_bytes(n, 4, gram_tc_rows_per_cta(n, 4)))
                                     : (size_t)16},
@@ -1332,7 +1338,8 @@ struct Runner {
   int method;
   bool bf16;
   Prof& prof;
-  bool tc = false;  // Grams on the tensor cores
+  bool tc = false;   // Grams on the tensor cores
+  bool tma = false;  // sparse product with TMA gather4
 
   // L^T R_b for b < nr into the gram slots, on the tensor cores or the CUDA cores
   cudaError_t grams(const float* L, const float* const* R, int nr, const int* slots, int ignore_done,
@@ -1445,8 +1452,31 @@ struct Runner {
     a.out = ws.W;
     a.G = ws.G;
     a.dots = ws.dots;
+    int dots_blocks = a.groups / (256 / spmm_lanes(ws.kp));
     prof.begin(OFSC_PHASE_SPMM);
-    launch_spmm(a, g->weighted != 0, SP_DIR, bf16, s);
+    if (tma) {
+      TmaSpmmArgs t{};
+      t.n = ws.n;
+      t.kp = ws.kp;
+      t.row_ptr = g->row_ptr;
+      t.col = g->col;
+      t.val = g->val;
+      t.dinv = g->dinv;
+      const int pi = spmm_lanes_index(32);
+      t.bnd = g->bnd[pi];
+      t.groups = g->groups[pi];
+      t.base = ws.V;
+      t.out = ws.W;
+      t.G = ws.G;
+      t.dots = ws.dots;
+      t.ctrl = ws.ctrl;
+      cudaError_t e = spmm_tma_launch(ws.vh_map[bf16 ? 1 : 0], t, bf16, g->weighted != 0, s);
+      if (e != cudaSuccess) return e;
+      ++g_launches;
+      dots_blocks = t.groups / spmm_tma_groups_per_block();
+    } else {
+      launch_spmm(a, g->weighted != 0, SP_DIR, bf16, s);
+    }
     prof.end();
     // V^T X and V^T V for every method; V^T AX and V^T AV in full for the f2 methods
     const float* Rs[4] = {ws.X, ws.V, ws.Y, ws.W};
@@ -1456,7 +1486,7 @@ struct Runner {
     SolveArgs sa{};
     sa.gram = ws.gram;
     sa.dots = ws.dots;
-    sa.dots_blocks = a.groups / (256 / spmm_lanes(ws.kp));
+    sa.dots_blocks = dots_blocks;
     sa.dE = ws.dE;
     sa.R64 = ws.R64;
     sa.B64 = ws.B64;
@@ -1555,6 +1585,8 @@ extern "C" ofsc_status ofsc_iterate(ofsc_graph* g, int32_t method, int32_t k, fl
   if (o.trace && o.trace_cap < 0) return fail(OFSC_ERR_INVALID_ARG, "ofsc_iterate: trace_cap < 0");
   if (o.gram_engine < OFSC_GRAM_AUTO || o.gram_engine > OFSC_GRAM_TC)
     return fail(OFSC_ERR_INVALID_ARG, "ofsc_iterate: unknown gram_engine %d", o.gram_engine);
+  if (o.spmm_engine < OFSC_SPMM_AUTO || o.spmm_engine > OFSC_SPMM_TMA)
+    return fail(OFSC_ERR_INVALID_ARG, "ofsc_iterate: unknown spmm_engine %d", o.spmm_engine);
   const int y_refresh = o.y_refresh > 0 ? o.y_refresh : 32;
   const int check_every = o.check_every > 0 ? o.check_every : 16;
   cudaStream_t s = (cudaStream_t)stream_;
@@ -1572,6 +1604,17 @@ extern "C" ofsc_status ofsc_iterate(ofsc_graph* g, int32_t method, int32_t k, fl
   Runner run{g, ws, s, method, o.gather == OFSC_GATHER_BF16, prof};
   run.tc = o.gram_engine == OFSC_GRAM_TC || (o.gram_engine == OFSC_GRAM_AUTO && kp > 64);
   if (run.tc && kp > 128) return fail(OFSC_ERR_INVALID_ARG, "ofsc_iterate: tensor-core Grams need k <= 128");
+  run.tma = spmm_tma_supported(kp) && o.spmm_engine != OFSC_SPMM_SIMT;
+  if (o.spmm_engine == OFSC_SPMM_TMA && !run.tma)
+    return fail(OFSC_ERR_INVALID_ARG, "ofsc_iterate: the TMA sparse product needs a padded k of 64 or 128");
+  if (run.tma) {
+    const int mi = run.bf16 ? 1 : 0;
+    if (!ws.vh_map_ok[mi]) {
+      st = spmm_tma_encode(ws.Vh, ws.n, kp, run.bf16, &ws.vh_map[mi]);
+      if (st != OFSC_OK) return st;
+      ws.vh_map_ok[mi] = true;
+    }
+  }
   const int objective = (method == OFSC_OFM_F1 || method == OFSC_TRI_F1) ? 1 : 2;
 
   k_init_ctrl<<<1, 1, 0, s>>>(ws.ctrl, tol, maxit, k, g->normA2, o.trace ? o.trace_cap : 0);
@@ -1653,7 +1696,7 @@ extern "C" ofsc_status ofsc_iterate(ofsc_graph* g, int32_t method, int32_t k, fl
 // file-scope static device array instead of the graph handle's workspace.
 //
 // Limits: n * kp <= 2^20 (kp = k rounded up to a multiple of 8, k <= 128); the array holds
-// kNoAllocBytes (about 27 MiB) on every GPU that loads the library, until the process exits.
+// kNoAllocBytes (about 30 MiB) on every GPU that loads the library, until the process exits.
 // The first call on a device looks the array's address up (cudaGetSymbolAddress) with that
 // device current; make that first call before any stream capture. Every call shares the one
 // array and it keeps the last call's contents, so calls that overlap on the GPU (other streams,

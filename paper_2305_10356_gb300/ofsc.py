@@ -19,6 +19,7 @@ OFM_F1, TRI_F1, OFM_F2, TRI_F2 = 0, 1, 2, 3
 F1, F2 = 1, 2
 GATHER_FP32, GATHER_BF16 = 0, 1
 GRAM_AUTO, GRAM_SIMT, GRAM_TC = 0, 1, 2
+SPMM_AUTO, SPMM_SIMT, SPMM_TMA = 0, 1, 2
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "NONFINITE", 4: "TIMEOUT",
                 5: "NOT_CONVERGED", 6: "CUDA"}
 
@@ -50,7 +51,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("gather", ctypes.c_int32), ("y_refresh", ctypes.c_int32),
                 ("check_every", ctypes.c_int32), ("alpha0", ctypes.c_double),
                 ("trace", ctypes.c_void_p), ("trace_cap", ctypes.c_int32),
-                ("profile", ctypes.POINTER(Profile)), ("gram_engine", ctypes.c_int32)]
+                ("profile", ctypes.POINTER(Profile)), ("gram_engine", ctypes.c_int32),
+                ("spmm_engine", ctypes.c_int32)]
 
 
 class Result(ctypes.Structure):
@@ -192,11 +194,12 @@ def ofsc_objective_grad_noalloc(g: Graph, objective: int, X, G_out=None, stream=
 
 def ofsc_iterate(g: Graph, method: int, X, tol: float, maxit: int, *, gather: int = GATHER_FP32,
                  y_refresh: int = 0, check_every: int = 0, alpha0: float = 0.0, trace=None,
-                 profile: Profile | None = None, gram_engine: int = GRAM_AUTO, stream=None) -> Result:
+                 profile: Profile | None = None, gram_engine: int = GRAM_AUTO,
+                 spmm_engine: int = SPMM_AUTO, stream=None) -> Result:
     """Algorithm 2 in place on the device block X (n x k, FP32). Returns the ofsc_result."""
     o = Opts(gather, y_refresh, check_every, alpha0, _ptr(trace),
              0 if trace is None else int(trace.shape[0]),
-             ctypes.pointer(profile) if profile is not None else None, gram_engine)
+             ctypes.pointer(profile) if profile is not None else None, gram_engine, spmm_engine)
     r = Result()
     _check(lib().ofsc_iterate(g.handle, method, int(X.shape[1]), _ptr(X), float(tol), int(maxit),
                               ctypes.byref(o), ctypes.byref(r), _stream(stream)),

@@ -151,8 +151,13 @@ def test_converged_features_and_clusters(c1, method):
     assert ref.converged
     assert r.status == ofsc.OK, (r.status, r.iterations, r.rel_dir_norm)
     assert r.rel_dir_norm <= 2e-6
-    # FP32 rounding near tol = 1e-6 shifts the stopping update; the features are what must agree
-    assert abs(r.iterations - ref.iterations) <= max(10, 0.25 * ref.iterations)
+    if method in (o.OFM_F1, o.OFM_F2):
+        # FP32 rounding near tol = 1e-6 shifts the stopping update; the features are what must agree
+        assert abs(r.iterations - ref.iterations) <= max(10, 0.25 * ref.iterations)
+    else:
+        # TriOFM descends no single objective (Sec. 2.2): with momentum, FP32 rounding moves the
+        # trajectory away from the FP64 one within ~50 updates, so only the limit is comparable
+        assert r.iterations <= 2 * ref.iterations + 50
     sin = o.subspace_sin(X, ref.X)
     assert math.asin(min(1.0, sin)) <= 1e-4
     if method in (o.TRI_F1, o.TRI_F2):
@@ -290,3 +295,20 @@ def test_tensor_core_and_cuda_core_iterations_agree(cuda_lib):
         ref = o.iterate(og, method, x0, 0.0, 6)
         assert np.linalg.norm(Xt - ref.X) <= 1e-4 * np.linalg.norm(ref.X)
         assert np.linalg.norm(Xs - ref.X) <= 1e-4 * np.linalg.norm(ref.X)
+
+
+@pytest.mark.parametrize("k", [64, 128])
+@pytest.mark.parametrize("gather", [0, 1])
+def test_tma_gather_spmm_agrees(k, gather):
+    """The TMA tile::gather4 sparse product gives the CUDA-core one's iterates (and the oracle's)."""
+    e = synth.sbm(3000, 6, 24.0, 6.0, seed=90 + k, gamma=2.5, ratio_kind="count")
+    x0 = synth.initial_block(e.n, k, 91)
+    g = gpu_graph(e)
+    Xs, _, trs = run_iterate(g, o.OFM_F1, x0, 0.0, 5, trace_cap=6, gather=gather, spmm_engine=ofsc.SPMM_SIMT)
+    Xt, _, trt = run_iterate(g, o.OFM_F1, x0, 0.0, 5, trace_cap=6, gather=gather, spmm_engine=ofsc.SPMM_TMA)
+    assert np.linalg.norm(Xt - Xs) <= 2e-5 * np.linalg.norm(Xs)
+    np.testing.assert_allclose(trt[:5, 3], trs[:5, 3], rtol=1e-4)
+    if gather == 0:
+        og = o.build_graph(e.n, e.src, e.dst)
+        ref = o.iterate(og, o.OFM_F1, x0, 0.0, 5)
+        assert np.linalg.norm(Xt - ref.X) <= 1e-4 * np.linalg.norm(ref.X)

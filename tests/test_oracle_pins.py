@@ -451,3 +451,28 @@ def test_rayleigh_ritz_on_eigenvectors():
     ritz, rel = o.rayleigh_ritz_relerr(g, U[:, :3] @ R * 2.0)
     assert rel < 1e-12
     np.testing.assert_allclose(np.sort(ritz), np.sort(2.0 - lam[:3]), atol=1e-12)
+
+
+@pytest.mark.parametrize("method", [o.TRI_F1, o.OFM_F1])
+def test_every_direction_descends(method):
+    """Each column's direction is a descent direction for that column, v_j^T g_j < 0, while its
+    gradient is above rounding level (Algorithm 2 with the restart reading), and a long run past
+    convergence stays finite and keeps converging."""
+    g, _ = small_graph(40, 3, 7.0, seed=17)
+    A = o.dense_A(g)
+    X0 = synth.initial_block(40, 3, 4).astype(np.float64)
+    X = X0.copy()
+    # replay the oracle's recurrences step by step and check the sign of v_j^T g_j
+    res = o.iterate(g, method, X0, 0.0, 400)
+    assert np.all(np.isfinite(res.X))
+    G_prev = o.direction(method, X0, A @ X0)
+    g0 = np.linalg.norm(G_prev, axis=0)
+    V = -G_prev
+    for t in range(1, len(res.betas)):
+        X = X + V * res.alphas[t - 1][None, :]
+        G = o.direction(method, X, A @ X)
+        V = -G + V * res.betas[t][None, :]
+        vg = np.sum(V * G, axis=0)
+        live = np.linalg.norm(G, axis=0) > 1e-8 * g0
+        assert np.all(vg[live] < 0), (t, vg)
+    assert res.rel_norms[-1] < 1e-9

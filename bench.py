@@ -118,6 +118,7 @@ def parse():
     ap.add_argument("--method", default="ofm_f1", choices=list(METHODS))
     ap.add_argument("--gather", default="fp32", choices=["fp32", "bf16"])
     ap.add_argument("--iters", type=int, default=30, help="updates of Algorithm 2 per step")
+    ap.add_argument("--spmm-engine", default="auto", choices=["auto", "simt", "tma"])
     ap.add_argument("--nodes", type=int, default=None, help="shrink the workload (testing only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -229,10 +230,11 @@ def run_gpu(args):
     X0 = torch.from_numpy(x0).cuda()
     X = torch.empty_like(X0)
     stream = torch.cuda.current_stream()
+    eng = {"auto": ofsc.SPMM_AUTO, "simt": ofsc.SPMM_SIMT, "tma": ofsc.SPMM_TMA}[args.spmm_engine]
 
     def step(prof=None):
         X.copy_(X0)
-        return ofsc.ofsc_iterate(g, method, X, 0.0, args.iters, gather=gather, profile=prof)
+        return ofsc.ofsc_iterate(g, method, X, 0.0, args.iters, gather=gather, profile=prof, spmm_engine=eng)
 
     for _ in range(args.warmup):
         step()
@@ -277,7 +279,7 @@ def run_gpu(args):
     e_start.record(stream)
     for _ in range(args.steps):
         Xd.copy_(Xh0, non_blocking=True)
-        ofsc.ofsc_iterate(g, method, Xd, 0.0, args.iters, gather=gather)
+        ofsc.ofsc_iterate(g, method, Xd, 0.0, args.iters, gather=gather, spmm_engine=eng)
         Xh.copy_(Xd, non_blocking=True)
     e_end.record(stream)
     torch.cuda.synchronize()

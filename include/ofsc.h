@@ -168,8 +168,8 @@ typedef struct {
   ofsc_profile* profile; /* HOST struct or NULL: the call ADDS its per-phase device times
                             (events around every launch; adds a little host overhead) */
   int32_t gram_engine;   /* OFSC_GRAM_AUTO (tensor cores when k > 64), OFSC_GRAM_SIMT, OFSC_GRAM_TC */
-  int32_t spmm_engine;   /* OFSC_SPMM_AUTO (TMA gather when padded k is 64 or 128), OFSC_SPMM_SIMT,
-                            OFSC_SPMM_TMA */
+  int32_t spmm_engine;   /* OFSC_SPMM_AUTO (= OFSC_SPMM_SIMT: one warp per row, CUDA-core gathers),
+                            OFSC_SPMM_TMA (tile::gather4 into shared memory; padded k 64 or 128) */
 } ofsc_opts;
 
 typedef struct {

@@ -83,7 +83,7 @@ ofsc_status ofsc_graph_free(ofsc_graph* g) {
   cudaFree(g->val);
   cudaFree(g->dinv);
   cudaFree(g->deg);
-  for (int i = 0; i < 5; ++i) cudaFree(g->bnd[i]);
+  for (int i = 0; i < 6; ++i) cudaFree(g->bnd[i]);
   cudaSetDevice(prev);
   delete g;
   return OFSC_OK;

@@ -51,6 +51,16 @@ inline int spmm_lanes_index(int lanes) {
   return lanes <= 2 ? 0 : lanes <= 4 ? 1 : lanes <= 8 ? 2 : lanes <= 16 ? 3 : 4;
 }
 // Lane groups of the sparse product: about 512 nonzeros each, between 1 and 4 blocks per SM.
+// Warps of the direction product (one row at a time per warp): about 256 nonzeros each, 1 to 8
+// blocks of kRowWarpsPerBlock warps per SM.
+constexpr int kRowPart = 5;
+constexpr int kRowWarpsPerBlock = 8;
+inline int row_warps(int64_t nnz) {
+  int64_t w = nnz / 256;
+  if (w < kNumSMs * kRowWarpsPerBlock) w = kNumSMs * kRowWarpsPerBlock;
+  if (w > 8 * kNumSMs * kRowWarpsPerBlock) w = 8 * kNumSMs * kRowWarpsPerBlock;
+  return (int)ceil_div(w, kRowWarpsPerBlock) * kRowWarpsPerBlock;
+}
 inline int spmm_groups(int64_t nnz, int lpr) {
   const int64_t gpb = 256 / lpr;
   int64_t g = nnz / 512;
@@ -135,8 +145,10 @@ struct ofsc_graph {
   double* deg = nullptr;       // [n]
   // nnz-balanced row ranges of the sparse product's lane groups, one partition per group width
   // (2, 4, 8, 16, 32 lanes): bnd[i] has groups[i] + 1 entries
-  int64_t* bnd[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-  int groups[5] = {0, 0, 0, 0, 0};
+  // bnd[5]: warps of the direction product (one row at a time per warp, kRowWarpsPerBlock warps
+  // per block)
+  int64_t* bnd[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  int groups[6] = {0, 0, 0, 0, 0, 0};
   ofsc::Workspace ws;
 };
 

@@ -328,9 +328,8 @@ extern "C" ofsc_status ofsc_graph_build(int64_t n, int64_t m, const int32_t* src
     g->n_isolated = (int64_t)h_counts[1];
   }
   g->normA2 = normA2;
-  for (int i = 0; i < 5; ++i) {
-    const int lpr = 2 << i;
-    g->groups[i] = spmm_groups(nnz, lpr);
+  for (int i = 0; i < 6; ++i) {
+    g->groups[i] = i == kRowPart ? row_warps(nnz) : spmm_groups(nnz, 2 << i);
     OFSC_CUDA(cudaMalloc(&g->bnd[i], (g->groups[i] + 1) * sizeof(int64_t)));
     k_partition<<<grid_for(g->groups[i] + 1), 256, 0, stream>>>(n, g->row_ptr, g->groups[i], g->bnd[i]);
     OFSC_LAUNCH_CHECK("k_partition");

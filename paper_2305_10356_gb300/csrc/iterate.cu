@@ -249,6 +249,133 @@ __global__ void __launch_bounds__(256, 2) k_spmm(SpmmArgs a) {
   }
 }
 
+// W = A V = -V - D^-1/2 S Vh for a direction V, with the fused partial sums of diag(V^T AV) and
+// diag(V^T G). A warp owns a contiguous, nnz-balanced range of rows and takes one row at a time,
+// so its control flow is uniform: LPN lanes per nonzero hold four columns each, NPI = 32 / LPN
+// nonzeros are gathered side by side and U of those slots per lane are in flight together
+// (STEP = U NPI <= 32 nonzeros per step; a short row's last step is predicated, not split). The
+// STEP column indices of a step are loaded one per lane and handed out by shuffle; those of the
+// next step (at a row end, of the next row) are loaded while the current gathers are in flight,
+// and a row's epilogue operands travel with the gathers of its last step. Each lane sums its
+// slots in nonzero order; the NPI partial sums of a row are combined by an xor-shuffle butterfly,
+// which leaves the same bits in every lane (for LPN = 32 the sum is in plain nonzero order).
+template <int LPN, bool WEIGHTED, bool BF16, bool DOTS>
+__global__ void __launch_bounds__(256, 4) k_spmm_dir(SpmmArgs a) {
+  if (a.ctrl->done) return;
+  constexpr int NPI = 32 / LPN;
+  constexpr int U = LPN == 32 ? 8 : LPN == 16 ? 4 : 2;
+  constexpr int STEP = U * NPI;
+  constexpr int WPB = kRowWarpsPerBlock;
+  constexpr int W = 4 * LPN;
+  static_assert(STEP <= 32, "one column index per lane");
+  // per-warp sums of diag(V^T AV), diag(V^T G) over the warp's rows; each lane owns its columns
+  __shared__ float dred[DOTS ? WPB * 2 * W : 1];
+  const int lane = threadIdx.x & 31;
+  const int sub = lane % LPN;
+  const int q = lane / LPN;
+  const int warp = threadIdx.x >> 5;
+  const int gw = blockIdx.x * WPB + warp;
+  const int c = sub * 4;
+  const bool active = c < a.kp;
+  float* rr = dred + (size_t)warp * 2 * W;
+  if (DOTS && lane < LPN) {
+    *(float4*)(rr + c) = make_float4(0.f, 0.f, 0.f, 0.f);
+    *(float4*)(rr + W + c) = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  if (gw < a.groups) {
+    int64_t l = a.bnd[gw];
+    const int64_t rb = a.bnd[gw + 1];
+    if (l < rb) {
+      const int64_t pend = a.row_ptr[rb];
+      int64_t pb = a.row_ptr[l];
+      int64_t p1 = a.row_ptr[l + 1];
+      int jl = 0;
+      float wl = 1.0f;
+      {
+        const int64_t i = pb + lane;
+        if (lane < STEP && i < pend) {
+          jl = __ldg(a.col + i);
+          if (WEIGHTED) wl = __ldg(a.val + i);
+        }
+      }
+      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+      while (true) {
+        const int64_t rem = p1 - pb;
+        const bool last = rem <= STEP;
+        float4 base = make_float4(0.f, 0.f, 0.f, 0.f), gg = base;
+        float s = 0.0f;
+        if (last && lane < LPN && active) {
+          const int64_t o = l * a.kp + c;
+          base = *(const float4*)(a.base + o);
+          if (DOTS) gg = *(const float4*)(a.G + o);
+          s = a.dinv[l];
+        }
+        float4 v[U];
+        float wv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int slot = u * NPI + q;
+          const int j = __shfl_sync(0xffffffffu, jl, slot);
+          wv[u] = WEIGHTED ? __shfl_sync(0xffffffffu, wl, slot) : 1.0f;
+          v[u] = (slot < rem && active) ? load_row4<BF16>(a.gather, j, a.kp, c) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        const int64_t pn = last ? p1 : pb + STEP;
+        const bool more = !last || l + 1 < rb;
+        int64_t p1n = p1;
+        if (last && more) p1n = a.row_ptr[l + 2];
+        if (more) {
+          const int64_t i = pn + lane;
+          jl = 0;
+          if (lane < STEP && i < pend) {
+            jl = __ldg(a.col + i);
+            if (WEIGHTED) wl = __ldg(a.val + i);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (u * NPI + q < rem) fma4(acc, wv[u], v[u]);
+        if (last) {
+#pragma unroll
+          for (int off = LPN; off < 32; off <<= 1) {
+            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+            acc.z += __shfl_xor_sync(0xffffffffu, acc.z, off);
+            acc.w += __shfl_xor_sync(0xffffffffu, acc.w, off);
+          }
+          if (lane < LPN && active) {
+            const float4 r4 = make_float4(-fmaf(s, acc.x, base.x), -fmaf(s, acc.y, base.y),
+                                          -fmaf(s, acc.z, base.z), -fmaf(s, acc.w, base.w));
+            *(float4*)(a.out + l * a.kp + c) = r4;
+            if (DOTS) {
+              float4 dcw = *(float4*)(rr + c), dvg = *(float4*)(rr + W + c);
+              dcw.x = fmaf(base.x, r4.x, dcw.x); dcw.y = fmaf(base.y, r4.y, dcw.y);
+              dcw.z = fmaf(base.z, r4.z, dcw.z); dcw.w = fmaf(base.w, r4.w, dcw.w);
+              dvg.x = fmaf(base.x, gg.x, dvg.x); dvg.y = fmaf(base.y, gg.y, dvg.y);
+              dvg.z = fmaf(base.z, gg.z, dvg.z); dvg.w = fmaf(base.w, gg.w, dvg.w);
+              *(float4*)(rr + c) = dcw;
+              *(float4*)(rr + W + c) = dvg;
+            }
+          }
+          if (!more) break;
+          ++l;
+          p1 = p1n;
+          acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        pb = pn;
+      }
+    }
+  }
+  if (DOTS) {  // per-block partials in a fixed order: warps, then columns
+    __syncthreads();
+    for (int j = threadIdx.x; j < 2 * a.kp; j += blockDim.x) {
+      const int which = j / a.kp, col = j % a.kp;
+      double sum = 0.0;
+      for (int w = 0; w < WPB; ++w) sum += (double)dred[(size_t)w * 2 * W + which * W + col];
+      a.dots[(int64_t)blockIdx.x * 2 * a.kp + j] = sum;
+    }
+  }
+}
+
 // V_t = -G_t + V_{t-1} diag(beta) (V_0 = -G_0) and its gather copy Vh = D^-1/2 V_t (FP32 or BF16).
 template <bool BF16>
 __global__ void k_vpass(int64_t n, int kp, const float* __restrict__ G, float* __restrict__ V, void* __restrict__ Vh,
@@ -1193,6 +1320,38 @@ void launch_spmm(const SpmmArgs& a, bool weighted, int mode, bool bf16, cudaStre
   }
 }
 
+template <int LPN, bool WEIGHTED, bool BF16>
+void launch_dir_w(const SpmmArgs& a, bool dots, cudaStream_t s) {
+  const int grid = a.groups / kRowWarpsPerBlock;
+  if (dots) k_spmm_dir<LPN, WEIGHTED, BF16, true><<<grid, 32 * kRowWarpsPerBlock, 0, s>>>(a);
+  else k_spmm_dir<LPN, WEIGHTED, BF16, false><<<grid, 32 * kRowWarpsPerBlock, 0, s>>>(a);
+}
+
+template <int LPN>
+void launch_dir_l(const SpmmArgs& a, bool weighted, bool bf16, cudaStream_t s) {
+  const bool dots = a.dots != nullptr;
+  if (weighted) {
+    if (bf16) launch_dir_w<LPN, true, true>(a, dots, s);
+    else launch_dir_w<LPN, true, false>(a, dots, s);
+  } else {
+    if (bf16) launch_dir_w<LPN, false, true>(a, dots, s);
+    else launch_dir_w<LPN, false, false>(a, dots, s);
+  }
+}
+
+// The direction product on the warp-per-row partition; returns the blocks (rows of dots partials).
+int launch_spmm_dir(const SpmmArgs& a, bool weighted, bool bf16, cudaStream_t s) {
+  ++g_launches;
+  switch (spmm_lanes(a.kp)) {
+    case 2: launch_dir_l<2>(a, weighted, bf16, s); break;
+    case 4: launch_dir_l<4>(a, weighted, bf16, s); break;
+    case 8: launch_dir_l<8>(a, weighted, bf16, s); break;
+    case 16: launch_dir_l<16>(a, weighted, bf16, s); break;
+    default: launch_dir_l<32>(a, weighted, bf16, s); break;
+  }
+  return a.groups / kRowWarpsPerBlock;
+}
+
 int kpmax_for(int kp) { return kp <= 16 ? 16 : kp <= 32 ? 32 : kp <= 64 ? 64 : 128; }
 
 template <int METHOD, int KPMAX>
@@ -1475,7 +1634,9 @@ struct Runner {
       ++g_launches;
       dots_blocks = t.groups / spmm_tma_groups_per_block();
     } else {
-      launch_spmm(a, g->weighted != 0, SP_DIR, bf16, s);
+      a.bnd = g->bnd[kRowPart];
+      a.groups = g->groups[kRowPart];
+      dots_blocks = launch_spmm_dir(a, g->weighted != 0, bf16, s);
     }
     prof.end();
     // V^T X and V^T V for every method; V^T AX and V^T AV in full for the f2 methods
@@ -1604,8 +1765,8 @@ extern "C" ofsc_status ofsc_iterate(ofsc_graph* g, int32_t method, int32_t k, fl
   Runner run{g, ws, s, method, o.gather == OFSC_GATHER_BF16, prof};
   run.tc = o.gram_engine == OFSC_GRAM_TC || (o.gram_engine == OFSC_GRAM_AUTO && kp > 64);
   if (run.tc && kp > 128) return fail(OFSC_ERR_INVALID_ARG, "ofsc_iterate: tensor-core Grams need k <= 128");
-  run.tma = spmm_tma_supported(kp) && o.spmm_engine != OFSC_SPMM_SIMT;
-  if (o.spmm_engine == OFSC_SPMM_TMA && !run.tma)
+  run.tma = o.spmm_engine == OFSC_SPMM_TMA;
+  if (run.tma && !spmm_tma_supported(kp))
     return fail(OFSC_ERR_INVALID_ARG, "ofsc_iterate: the TMA sparse product needs a padded k of 64 or 128");
   if (run.tma) {
     const int mi = run.bf16 ? 1 : 0;

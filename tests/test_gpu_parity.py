@@ -4,6 +4,7 @@ Tolerances: graph build, degrees and D^-1/2 are bit-exact; f and grad f match wi
 relative; iterates after a few updates match within 1e-4 relative (FP32 vs FP64 rounding);
 converged features match within a principal angle of 1e-4 rad; K-means labels reach ARI >= 0.99.
 """
+import dataclasses
 import math
 
 import numpy as np
@@ -312,3 +313,22 @@ def test_tma_gather_spmm_agrees(k, gather):
         og = o.build_graph(e.n, e.src, e.dst)
         ref = o.iterate(og, o.OFM_F1, x0, 0.0, 5)
         assert np.linalg.norm(Xt - ref.X) <= 1e-4 * np.linalg.norm(ref.X)
+
+
+
+@pytest.mark.parametrize("k", [3, 12, 20, 44, 100])
+def test_direction_product_all_lane_widths_weighted(k):
+    """The warp-per-row direction product at every lane width (padded k 8 to 104: 2 to 32 lanes per
+    nonzero, 16 to 1 nonzeros side by side), on a weighted graph with hub rows longer than a step
+    and isolated (empty) rows, against the oracle's updates."""
+    e = synth.sbm(2500, 5, 18.0, 5.0, seed=60 + k, gamma=2.2, ratio_kind="count", weighted=True)
+    # 20 trailing nodes without edges: empty rows, also at the end of the last warp's range
+    e = dataclasses.replace(e, n=e.n + 20, labels=np.concatenate([e.labels, np.zeros(20, np.int32)]))
+    og = o.build_graph(e.n, e.src, e.dst, e.w)
+    assert (og.deg[-20:] == 0).all() and np.diff(og.row_ptr).max() > 64
+    x0 = synth.initial_block(e.n, k, 61)
+    g = gpu_graph(e)
+    X, r, tr = run_iterate(g, o.OFM_F2, x0, 0.0, 4, trace_cap=5)
+    ref = o.iterate(og, o.OFM_F2, x0, 0.0, 4)
+    assert np.linalg.norm(X - ref.X) <= 1e-4 * np.linalg.norm(ref.X)
+    np.testing.assert_allclose(tr[:4, 3:3 + k], np.array(ref.alphas[:4]), rtol=1e-4, atol=1e-7)

@@ -103,8 +103,8 @@ __global__ void k_update_x(int64_t n, int kp, float* __restrict__ X, const float
 // Sparse product Y = A M with A = -I - D^-1/2 S D^-1/2, fused epilogues
 // ------------------------------------------------------------------------------------------
 
-enum { SP_DIR = 0, SP_Y = 1 };
-
+// Operands of the two sparse products: the direction product W = A V (k_spmm_dir, gathering
+// Vh = D^-1/2 V) and the exact AX = A X (k_spmm, gathering X and scaling by D^-1/2 per nonzero).
 struct SpmmArgs {
   int64_t n;
   int kp;
@@ -112,16 +112,34 @@ struct SpmmArgs {
   const int32_t* col;
   const float* val;
   const float* dinv;
-  const int64_t* bnd;  // [groups + 1]: contiguous, nnz-balanced row ranges of the lane groups
+  const int64_t* bnd;  // [groups + 1]: contiguous, nnz-balanced row ranges of the lane groups / warps
   int groups;
-  const void* gather;  // SP_DIR: Vh = D^-1/2 V (FP32 or BF16); SP_Y: X (FP32, scaled per nonzero)
-  const float* base;   // SP_DIR: V; SP_Y: X  (the row block M in A M = -M - D^-1/2 S D^-1/2 M)
-  float* out;          // SP_DIR: AV; SP_Y: AX
-  const float* G;      // SP_DIR with DOTS: the direction G
-  double* dots;        // SP_DIR with DOTS: [gridDim.x][2][kp] partial sums of diag(V^T AV), diag(V^T G)
+  const void* gather;  // direction: Vh = D^-1/2 V (FP32 or BF16); AX: X
+  const float* base;   // direction: V; AX: X  (the row block M in A M = -M - D^-1/2 S D^-1/2 M)
+  float* out;          // direction: W = AV; AX: AX
+  const float* G;      // direction with dots: the direction G
+  double* dots;        // direction with dots: [blocks][2][kp] partials of diag(V^T AV), diag(V^T G)
   Ctrl* ctrl;
   int ignore_done;
 };
+
+#ifndef OFSC_ROW_STAGE
+#define OFSC_ROW_STAGE 1  // epilogue operands of the direction product staged by cp.async
+#endif
+
+#ifndef OFSC_ROW_U32
+#define OFSC_ROW_U32 8  // gathers in flight per lane when a warp covers a row of 128 columns
+#endif
+#ifndef OFSC_ROW_MINB
+#define OFSC_ROW_MINB (32 / kRowWarpsPerBlock)  // resident blocks per SM the registers must allow
+#endif
+// 16-byte global -> shared copy that completes asynchronously (L2 only), and its fences.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Four consecutive values of row `row` from column c, as FP32 (FP32 or BF16 storage).
 template <bool BF16>
@@ -143,109 +161,65 @@ __device__ __forceinline__ void fma4(float4& acc, float w, const float4& v) {
   acc.w = fmaf(w, v.w, acc.w);
 }
 
-// out = A M = -M - D^-1/2 S (D^-1/2 M) row by row. A group of LANES lanes owns a contiguous range
-// of rows holding about nnz / groups nonzeros (hub rows do not pile up on one group); lane q
-// holds columns [4q, 4q + 4). For each row the group loads up to LANES column indices at once
-// and keeps 8 row gathers in flight per lane; the next row's pointer and epilogue operands are
-// loaded before the current row's gathers. SP_DIR also sums diag(V^T AV) and diag(V^T G).
-template <int LANES, bool WEIGHTED, int MODE, bool BF16, bool DOTS>
+// AX = -X - D^-1/2 S D^-1/2 X row by row, the exact product behind the objective, the gradient
+// and the periodic refresh of the AX recurrence (each gathered row is scaled by its own D^-1/2
+// entry and edge weight). A group of LANES lanes owns a contiguous range of rows holding about
+// nnz / groups nonzeros; lane q holds columns [4q, 4q + 4). For each row the group loads up to
+// LANES column indices at once and keeps 8 row gathers in flight per lane.
+template <int LANES, bool WEIGHTED>
 __global__ void __launch_bounds__(256, 2) k_spmm(SpmmArgs a) {
   if (!a.ignore_done && a.ctrl->done) return;
   constexpr int GPB = 256 / LANES;
-  constexpr bool GBF = (MODE == SP_DIR) && BF16;
-  constexpr bool SCALED = WEIGHTED || MODE == SP_Y;
-  __shared__ float dred[DOTS ? 2 * 256 * 4 : 1];
   const int lane = threadIdx.x % LANES;
   const int grp = threadIdx.x / LANES;
   const unsigned mask = LANES == 32 ? 0xffffffffu : (((1u << LANES) - 1u) << ((threadIdx.x & 31) / LANES * LANES));
   const int c = lane * 4;
   const bool active = c < a.kp;
   const int gid = blockIdx.x * GPB + grp;
-  float4 dcw = make_float4(0.f, 0.f, 0.f, 0.f), dvg = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (gid < a.groups) {
-    const int64_t ra = a.bnd[gid], rb = a.bnd[gid + 1];
-    int64_t p1 = ra < rb ? a.row_ptr[ra] : 0;
-    for (int64_t l = ra; l < rb; ++l) {
-      const int64_t p0 = p1;
-      p1 = a.row_ptr[l + 1];
-      const int64_t o = l * a.kp + c;
-      float4 base = make_float4(0.f, 0.f, 0.f, 0.f), gg = base;
-      if (active) {
-        base = *(const float4*)(a.base + o);
-        if (DOTS) gg = *(const float4*)(a.G + o);
+  if (gid >= a.groups) return;
+  const float* X = (const float*)a.gather;
+  const int64_t ra = a.bnd[gid], rb = a.bnd[gid + 1];
+  int64_t p1 = ra < rb ? a.row_ptr[ra] : 0;
+  for (int64_t l = ra; l < rb; ++l) {
+    const int64_t p0 = p1;
+    p1 = a.row_ptr[l + 1];
+    const int64_t o = l * a.kp + c;
+    float4 base = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (active) base = *(const float4*)(a.base + o);
+    const float s = a.dinv[l];
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int64_t pb = p0; pb < p1; pb += LANES) {
+      const int cnt = (int)min((int64_t)LANES, p1 - pb);
+      int jj = 0;
+      float ww = 0.0f;
+      if (lane < cnt) {
+        jj = __ldg(a.col + pb + lane);
+        ww = (WEIGHTED ? __ldg(a.val + pb + lane) : 1.0f) * __ldg(a.dinv + jj);
       }
-      const float s = a.dinv[l];
-      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-      for (int64_t pb = p0; pb < p1; pb += LANES) {
-        const int cnt = (int)min((int64_t)LANES, p1 - pb);
-        int jj = 0;
-        float ww = 0.0f;
-        if (lane < cnt) {
-          jj = __ldg(a.col + pb + lane);
-          if (SCALED) {
-            ww = WEIGHTED ? __ldg(a.val + pb + lane) : 1.0f;
-            if (MODE == SP_Y) ww *= __ldg(a.dinv + jj);
-          }
+      int q = 0;
+      for (; q + 8 <= cnt; q += 8) {
+        float4 v[8];
+        float w[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int j = __shfl_sync(mask, jj, q + u, LANES);
+          w[u] = __shfl_sync(mask, ww, q + u, LANES);
+          if (active) v[u] = __ldg((const float4*)(X + (int64_t)j * a.kp + c));
         }
-        int q = 0;
-        for (; q + 8 <= cnt; q += 8) {
-          float4 v[8];
-          float w[8];
+        if (active) {
 #pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            const int j = __shfl_sync(mask, jj, q + u, LANES);
-            w[u] = SCALED ? __shfl_sync(mask, ww, q + u, LANES) : 1.0f;
-            if (active) v[u] = load_row4<GBF>(a.gather, j, a.kp, c);
-          }
-          if (active) {
-#pragma unroll
-            for (int u = 0; u < 8; ++u) fma4(acc, w[u], v[u]);
-          }
-        }
-        for (; q + 4 <= cnt; q += 4) {
-          float4 v[4];
-          float w[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int j = __shfl_sync(mask, jj, q + u, LANES);
-            w[u] = SCALED ? __shfl_sync(mask, ww, q + u, LANES) : 1.0f;
-            if (active) v[u] = load_row4<GBF>(a.gather, j, a.kp, c);
-          }
-          if (active) {
-#pragma unroll
-            for (int u = 0; u < 4; ++u) fma4(acc, w[u], v[u]);
-          }
-        }
-        for (; q < cnt; ++q) {
-          const int j = __shfl_sync(mask, jj, q, LANES);
-          const float w = SCALED ? __shfl_sync(mask, ww, q, LANES) : 1.0f;
-          if (active) fma4(acc, w, load_row4<GBF>(a.gather, j, a.kp, c));
+          for (int u = 0; u < 8; ++u) fma4(acc, w[u], v[u]);
         }
       }
-      if (!active) continue;
-      const float4 r4 = make_float4(-fmaf(s, acc.x, base.x), -fmaf(s, acc.y, base.y),
-                                    -fmaf(s, acc.z, base.z), -fmaf(s, acc.w, base.w));
-      *(float4*)(a.out + o) = r4;
-      if (DOTS) {
-        dcw.x = fmaf(base.x, r4.x, dcw.x); dcw.y = fmaf(base.y, r4.y, dcw.y);
-        dcw.z = fmaf(base.z, r4.z, dcw.z); dcw.w = fmaf(base.w, r4.w, dcw.w);
-        dvg.x = fmaf(base.x, gg.x, dvg.x); dvg.y = fmaf(base.y, gg.y, dvg.y);
-        dvg.z = fmaf(base.z, gg.z, dvg.z); dvg.w = fmaf(base.w, gg.w, dvg.w);
+      for (; q < cnt; ++q) {
+        const int j = __shfl_sync(mask, jj, q, LANES);
+        const float w = __shfl_sync(mask, ww, q, LANES);
+        if (active) fma4(acc, w, __ldg((const float4*)(X + (int64_t)j * a.kp + c)));
       }
     }
-  }
-  if (DOTS) {  // per-block partials of diag(V^T AV), diag(V^T G) in a fixed order: groups, columns
-    constexpr int W = LANES * 4;
-    float* rr = dred + (size_t)grp * 2 * W;
-    *(float4*)(rr + c) = dcw;
-    *(float4*)(rr + W + c) = dvg;
-    __syncthreads();
-    for (int j = threadIdx.x; j < 2 * a.kp; j += blockDim.x) {
-      const int which = j / a.kp, col = j % a.kp;
-      double sum = 0.0;
-      for (int g = 0; g < GPB; ++g) sum += (double)dred[(size_t)g * 2 * W + which * W + col];
-      a.dots[(int64_t)blockIdx.x * 2 * a.kp + j] = sum;
-    }
+    if (!active) continue;
+    *(float4*)(a.out + o) = make_float4(-fmaf(s, acc.x, base.x), -fmaf(s, acc.y, base.y),
+                                        -fmaf(s, acc.z, base.z), -fmaf(s, acc.w, base.w));
   }
 }
 
@@ -256,20 +230,25 @@ __global__ void __launch_bounds__(256, 2) k_spmm(SpmmArgs a) {
 // (STEP = U NPI <= 32 nonzeros per step; a short row's last step is predicated, not split). The
 // STEP column indices of a step are loaded one per lane and handed out by shuffle; those of the
 // next step (at a row end, of the next row) are loaded while the current gathers are in flight,
-// and a row's epilogue operands travel with the gathers of its last step. Each lane sums its
-// slots in nonzero order; the NPI partial sums of a row are combined by an xor-shuffle butterfly,
-// which leaves the same bits in every lane (for LPN = 32 the sum is in plain nonzero order).
+// and a row's epilogue operands (its rows of V and G) are copied to shared memory with cp.async
+// during the gathers of its last step, holding no registers meanwhile. Each lane sums its slots
+// in nonzero order; the NPI partial sums of a row are combined by an xor-shuffle butterfly, which
+// leaves the same bits in every lane (for LPN = 32 the sum is in plain nonzero order). Blocks
+// are small (kRowWarpsPerBlock warps over about 1024 nonzeros each) so the grid runs in several
+// waves with a short last one; the per-block dots partials are folded by k_dots_fold.
 template <int LPN, bool WEIGHTED, bool BF16, bool DOTS>
-__global__ void __launch_bounds__(256, 4) k_spmm_dir(SpmmArgs a) {
+__global__ void __launch_bounds__(32 * kRowWarpsPerBlock, OFSC_ROW_MINB) k_spmm_dir(SpmmArgs a) {
   if (a.ctrl->done) return;
   constexpr int NPI = 32 / LPN;
-  constexpr int U = LPN == 32 ? 8 : LPN == 16 ? 4 : 2;
+  constexpr int U = LPN == 32 ? OFSC_ROW_U32 : LPN == 16 ? 4 : 2;
   constexpr int STEP = U * NPI;
   constexpr int WPB = kRowWarpsPerBlock;
   constexpr int W = 4 * LPN;
   static_assert(STEP <= 32, "one column index per lane");
   // per-warp sums of diag(V^T AV), diag(V^T G) over the warp's rows; each lane owns its columns
   __shared__ float dred[DOTS ? WPB * 2 * W : 1];
+  // the epilogue operands V and G of a row, copied asynchronously during its last step's gathers
+  __shared__ __align__(16) float stage[WPB][2][W];
   const int lane = threadIdx.x & 31;
   const int sub = lane % LPN;
   const int q = lane / LPN;
@@ -283,8 +262,8 @@ __global__ void __launch_bounds__(256, 4) k_spmm_dir(SpmmArgs a) {
     *(float4*)(rr + W + c) = make_float4(0.f, 0.f, 0.f, 0.f);
   }
   if (gw < a.groups) {
-    int64_t l = a.bnd[gw];
-    const int64_t rb = a.bnd[gw + 1];
+    int l = (int)a.bnd[gw];  // column indices are int32, so n < 2^31
+    const int rb = (int)a.bnd[gw + 1];
     if (l < rb) {
       const int64_t pend = a.row_ptr[rb];
       int64_t pb = a.row_ptr[l];
@@ -302,14 +281,24 @@ __global__ void __launch_bounds__(256, 4) k_spmm_dir(SpmmArgs a) {
       while (true) {
         const int64_t rem = p1 - pb;
         const bool last = rem <= STEP;
-        float4 base = make_float4(0.f, 0.f, 0.f, 0.f), gg = base;
         float s = 0.0f;
+#if OFSC_ROW_STAGE
         if (last && lane < LPN && active) {
-          const int64_t o = l * a.kp + c;
+          const int64_t o = (int64_t)l * a.kp + c;
+          cp_async16(&stage[warp][0][c], a.base + o);
+          if (DOTS) cp_async16(&stage[warp][1][c], a.G + o);
+          cp_async_commit();
+          s = a.dinv[l];
+        }
+#else
+        float4 base = make_float4(0.f, 0.f, 0.f, 0.f), gg = base;
+        if (last && lane < LPN && active) {
+          const int64_t o = (int64_t)l * a.kp + c;
           base = *(const float4*)(a.base + o);
           if (DOTS) gg = *(const float4*)(a.G + o);
           s = a.dinv[l];
         }
+#endif
         float4 v[U];
         float wv[U];
 #pragma unroll
@@ -343,10 +332,17 @@ __global__ void __launch_bounds__(256, 4) k_spmm_dir(SpmmArgs a) {
             acc.w += __shfl_xor_sync(0xffffffffu, acc.w, off);
           }
           if (lane < LPN && active) {
+#if OFSC_ROW_STAGE
+            cp_async_wait_all();  // each lane reads back only its own copies
+            const float4 base = *(const float4*)&stage[warp][0][c];
+#endif
             const float4 r4 = make_float4(-fmaf(s, acc.x, base.x), -fmaf(s, acc.y, base.y),
                                           -fmaf(s, acc.z, base.z), -fmaf(s, acc.w, base.w));
-            *(float4*)(a.out + l * a.kp + c) = r4;
+            *(float4*)(a.out + (int64_t)l * a.kp + c) = r4;
             if (DOTS) {
+#if OFSC_ROW_STAGE
+              const float4 gg = *(const float4*)&stage[warp][1][c];
+#endif
               float4 dcw = *(float4*)(rr + c), dvg = *(float4*)(rr + W + c);
               dcw.x = fmaf(base.x, r4.x, dcw.x); dcw.y = fmaf(base.y, r4.y, dcw.y);
               dcw.z = fmaf(base.z, r4.z, dcw.z); dcw.w = fmaf(base.w, r4.w, dcw.w);
@@ -373,6 +369,20 @@ __global__ void __launch_bounds__(256, 4) k_spmm_dir(SpmmArgs a) {
       for (int w = 0; w < WPB; ++w) sum += (double)dred[(size_t)w * 2 * W + which * W + col];
       a.dots[(int64_t)blockIdx.x * 2 * a.kp + j] = sum;
     }
+  }
+}
+
+// Folds nblk rows of per-block partials (width values each) into gridDim.x rows: row r sums the
+// blocks [r nblk / R, (r + 1) nblk / R) in order, so the result does not depend on scheduling.
+__global__ void k_dots_fold(const double* __restrict__ part, int nblk, int width, double* __restrict__ out,
+                            const Ctrl* ctrl) {
+  if (ctrl->done) return;
+  const int r = blockIdx.x;
+  const int b0 = (int)((int64_t)r * nblk / gridDim.x), b1 = (int)((int64_t)(r + 1) * nblk / gridDim.x);
+  for (int t = threadIdx.x; t < width; t += blockDim.x) {
+    double sum = 0.0;
+    for (int b = b0; b < b1; ++b) sum += part[(int64_t)b * width + t];
+    out[(int64_t)r * width + t] = sum;
   }
 }
 
@@ -1285,38 +1295,23 @@ struct Prof {
   }
 };
 
-template <int LANES, int MODE, bool BF16, bool DOTS>
-void launch_spmm_w(const SpmmArgs& a, bool weighted, cudaStream_t s) {
-  const int grid = a.groups / (256 / LANES);
-  if (weighted) k_spmm<LANES, true, MODE, BF16, DOTS><<<grid, 256, 0, s>>>(a);
-  else k_spmm<LANES, false, MODE, BF16, DOTS><<<grid, 256, 0, s>>>(a);
-}
-
 template <int LANES>
-void launch_spmm_l(const SpmmArgs& a, bool weighted, int mode, bool bf16, cudaStream_t s) {
+void launch_spmm_l(const SpmmArgs& a, bool weighted, cudaStream_t s) {
   ++g_launches;
-  const bool dots = a.dots != nullptr;
-  if (mode == SP_DIR) {
-    if (bf16) {
-      if (dots) launch_spmm_w<LANES, SP_DIR, true, true>(a, weighted, s);
-      else launch_spmm_w<LANES, SP_DIR, true, false>(a, weighted, s);
-    } else {
-      if (dots) launch_spmm_w<LANES, SP_DIR, false, true>(a, weighted, s);
-      else launch_spmm_w<LANES, SP_DIR, false, false>(a, weighted, s);
-    }
-  } else {
-    launch_spmm_w<LANES, SP_Y, false, false>(a, weighted, s);
-  }
+  const int grid = a.groups / (256 / LANES);
+  if (weighted) k_spmm<LANES, true><<<grid, 256, 0, s>>>(a);
+  else k_spmm<LANES, false><<<grid, 256, 0, s>>>(a);
 }
 
-void launch_spmm(const SpmmArgs& a, bool weighted, int mode, bool bf16, cudaStream_t s) {
+// AX for the row block in a.gather (= a.base), on the lane-group partition of a.kp.
+void launch_spmm(const SpmmArgs& a, bool weighted, cudaStream_t s) {
   if (a.n <= 0) return;
   switch (spmm_lanes(a.kp)) {
-    case 2: launch_spmm_l<2>(a, weighted, mode, bf16, s); break;
-    case 4: launch_spmm_l<4>(a, weighted, mode, bf16, s); break;
-    case 8: launch_spmm_l<8>(a, weighted, mode, bf16, s); break;
-    case 16: launch_spmm_l<16>(a, weighted, mode, bf16, s); break;
-    default: launch_spmm_l<32>(a, weighted, mode, bf16, s); break;
+    case 2: launch_spmm_l<2>(a, weighted, s); break;
+    case 4: launch_spmm_l<4>(a, weighted, s); break;
+    case 8: launch_spmm_l<8>(a, weighted, s); break;
+    case 16: launch_spmm_l<16>(a, weighted, s); break;
+    default: launch_spmm_l<32>(a, weighted, s); break;
   }
 }
 
@@ -1460,7 +1455,7 @@ ofsc_status ensure_workspace(ofsc_graph* g, int kp) {
       {(void**)&ws.Bn, kk * sizeof(float)},
       {(void**)&ws.R64, kk * sizeof(double)},
       {(void**)&ws.B64, kk * sizeof(double)},
-      {(void**)&ws.dots, (size_t)16 * kNumSMs * 2 * kp * sizeof(double)},
+      {(void**)&ws.dots, (size_t)(kRowMaxBlocks + kDotsRows) * 2 * kp * sizeof(double)},
       {(void**)&ws.part_tc, kp > 64 ? std::max(gram_tc_part_bytes(n, 2, gram_tc_rows_per_cta(n, 2)),
                                                gram_tc_part_bytes(n, 4, gram_tc_rows_per_cta(n, 4)))
                                     : (size_t)16},
@@ -1559,7 +1554,7 @@ struct Runner {
     a.out = ws.Y;
     a.ignore_done = ignore_done;
     prof.begin(OFSC_PHASE_REFRESH);
-    launch_spmm(a, g->weighted != 0, SP_Y, false, s);
+    launch_spmm(a, g->weighted != 0, s);
     const float* R[2] = {ws.X, ws.Y};
     const int slots[2] = {G_R, G_B};
     cudaError_t e = grams(ws.X, R, 2, slots, ignore_done, false);
@@ -1638,6 +1633,14 @@ struct Runner {
       a.groups = g->groups[kRowPart];
       dots_blocks = launch_spmm_dir(a, g->weighted != 0, bf16, s);
     }
+    const double* dots = ws.dots;
+    if (dots_blocks > kDotsRows) {
+      double* folded = ws.dots + (size_t)kRowMaxBlocks * 2 * ws.kp;
+      k_dots_fold<<<kDotsRows, 256, 0, s>>>(ws.dots, dots_blocks, 2 * ws.kp, folded, ws.ctrl);
+      ++g_launches;
+      dots = folded;
+      dots_blocks = kDotsRows;
+    }
     prof.end();
     // V^T X and V^T V for every method; V^T AX and V^T AV in full for the f2 methods
     const float* Rs[4] = {ws.X, ws.V, ws.Y, ws.W};
@@ -1646,7 +1649,7 @@ struct Runner {
     if (e != cudaSuccess) return e;
     SolveArgs sa{};
     sa.gram = ws.gram;
-    sa.dots = ws.dots;
+    sa.dots = dots;
     sa.dots_blocks = dots_blocks;
     sa.dE = ws.dE;
     sa.R64 = ws.R64;
@@ -1972,7 +1975,7 @@ extern "C" ofsc_status ofsc_objective_grad_noalloc(const ofsc_graph* gc, int32_t
   a.gather = ws.X;
   a.base = ws.X;
   a.out = ws.Y;
-  launch_spmm(a, g->weighted != 0, SP_Y, false, s);
+  launch_spmm(a, g->weighted != 0, s);
   GramArgs ga;
   ga.n = ws.n;
   ga.kp = kp;

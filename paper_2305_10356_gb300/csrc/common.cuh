@@ -78,6 +78,8 @@ inline int row_warps(int64_t nnz) {
 // Per-block partial sums of the sparse product's dots are folded to at most this many rows, in a
 // fixed order, before the line-search solve reads them.
 constexpr int kDotsRows = 64;
+// Blocks of the V pass (each writes one row of diag(V^T G) partials).
+constexpr int kVpassMaxBlocks = 8 * kNumSMs;
 inline int spmm_groups(int64_t nnz, int lpr) {
   const int64_t gpb = 256 / lpr;
   int64_t g = nnz / 512;
@@ -198,8 +200,7 @@ struct TmaSpmmArgs {
   int groups;
   const float* base;    // V
   float* out;           // AV
-  const float* G;       // direction, for diag(V^T G)
-  double* dots;         // [groups / 4][2][kp]
+  double* dots;         // [groups / 4][kp] partials of diag(V^T AV)
   Ctrl* ctrl;
 };
 bool spmm_tma_supported(int kp);

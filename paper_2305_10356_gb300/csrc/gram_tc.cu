@@ -242,19 +242,37 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(GramTcArgs a) {
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOLS));
 }
 
-// gram[slot[b]][i][j] = sum over CTAs (in order) of part[cta][b][i][j], FP64, for i, j < kp.
-// gram[slot[b] * kk_stride + i * ld_out + j] = sum over CTAs, in order, of part[cta][b][i][j] (FP64),
-// for i, j < kout.
-__global__ void k_gram_tc_reduce(const float* __restrict__ part, int nctas, int nr, int kout, int ld_out,
-                                 int64_t kk_stride, int s0, int s1, int s2, int s3, double* __restrict__ gram,
-                                 Ctrl* ctrl, int ignore_done) {
+// The per-CTA FP32 partials are summed in FP64 in two fixed-order levels: level 1 adds groups of
+// kRedGroup consecutive CTAs (all groups and elements in parallel), level 2 adds the groups in
+// order. The result does not depend on scheduling.
+constexpr int kRedGroup = 32;
+
+__global__ void k_gram_tc_reduce1(const float* __restrict__ part, int nctas, int total, double* __restrict__ lvl1,
+                                  const Ctrl* ctrl, int ignore_done) {
+  if (ctrl && !ignore_done && ctrl->done) return;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  const int g = blockIdx.y;
+  const int c0 = g * kRedGroup, c1 = min(nctas, c0 + kRedGroup);
+  double s = 0.0;
+  for (int c = c0; c < c1; ++c) s += (double)part[(int64_t)c * total + t];
+  lvl1[(int64_t)g * total + t] = s;
+}
+
+// gram[slot[b] * kk_stride + i * ld_out + j] = sum over groups, in order, of lvl1[g][b][i][j], for
+// i, j < kout.
+__global__ void k_gram_tc_reduce2(const double* __restrict__ lvl1, int ngroups, int nr, int kout, int ld_out,
+                                  int64_t kk_stride, int s0, int s1, int s2, int s3, double* __restrict__ gram,
+                                  const Ctrl* ctrl, int ignore_done) {
   if (ctrl && !ignore_done && ctrl->done) return;
   const int slot[4] = {s0, s1, s2, s3};
   const int total = nr * kout * kout;
+  const int64_t stride = (int64_t)nr * kTcM * kTcM;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
     const int b = t / (kout * kout), ij = t % (kout * kout), i = ij / kout, j = ij % kout;
+    const int64_t e = ((int64_t)b * kTcM + i) * kTcM + j;
     double s = 0.0;
-    for (int c = 0; c < nctas; ++c) s += (double)part[(((int64_t)c * nr + b) * kTcM + i) * kTcM + j];
+    for (int g = 0; g < ngroups; ++g) s += lvl1[g * stride + e];
     gram[(int64_t)slot[b] * kk_stride + (int64_t)i * ld_out + j] = s;
   }
 }
@@ -289,9 +307,16 @@ int64_t gram_tc_rows_per_cta(int64_t n, int nr) {
   return rpc < kTcRows ? kTcRows : rpc;
 }
 
+// Bytes of the partials buffer: the FP32 per-CTA partials, then the FP64 level-1 sums.
+static size_t part_floats_bytes(int64_t ctas, int nr) {
+  const size_t b = (size_t)(ctas > 0 ? ctas : 1) * nr * kTcM * kTcM * sizeof(float);
+  return (b + 255) / 256 * 256;
+}
+
 size_t gram_tc_part_bytes(int64_t n, int nr, int64_t rows_per_cta) {
   const int64_t ctas = (n + rows_per_cta - 1) / rows_per_cta;
-  return (size_t)(ctas > 0 ? ctas : 1) * nr * kTcM * kTcM * sizeof(float);
+  const int64_t groups = (std::max<int64_t>(ctas, 1) + kRedGroup - 1) / kRedGroup;
+  return part_floats_bytes(ctas, nr) + (size_t)groups * nr * kTcM * kTcM * sizeof(double);
 }
 
 // Launches the partial Grams and their FP64 reduction into gram[slot][kp][kp].
@@ -316,11 +341,16 @@ cudaError_t gram_tc_launch_ld(GramTcArgs a, const int* slot, int kout, int ld_ou
     default: e = launch_t<4, true>(a, grid, s); break;
   }
   if (e != cudaSuccess) return e;
+  const int total_p = a.nr * kTcM * kTcM;
+  const int ngroups = (grid + kRedGroup - 1) / kRedGroup;
+  double* lvl1 = (double*)((char*)a.part + part_floats_bytes(grid, a.nr));
+  k_gram_tc_reduce1<<<dim3((total_p + 255) / 256, ngroups), 256, 0, s>>>(a.part, grid, total_p, lvl1, a.ctrl,
+                                                                          a.ignore_done);
   const int total = a.nr * kout * kout;
   const int rgrid = (int)std::min<int64_t>((total + 255) / 256, 4 * kNumSMs);
-  k_gram_tc_reduce<<<rgrid, 256, 0, s>>>(a.part, grid, a.nr, kout, ld_out, kk_stride, slot[0],
-                                         a.nr > 1 ? slot[1] : 0, a.nr > 2 ? slot[2] : 0, a.nr > 3 ? slot[3] : 0,
-                                         gram, a.ctrl, a.ignore_done);
+  k_gram_tc_reduce2<<<rgrid, 256, 0, s>>>(lvl1, ngroups, a.nr, kout, ld_out, kk_stride, slot[0],
+                                          a.nr > 1 ? slot[1] : 0, a.nr > 2 ? slot[2] : 0, a.nr > 3 ? slot[3] : 0,
+                                          gram, a.ctrl, a.ignore_done);
   return cudaGetLastError();
 }
 

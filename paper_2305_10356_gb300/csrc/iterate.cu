@@ -117,15 +117,10 @@ struct SpmmArgs {
   const void* gather;  // direction: Vh = D^-1/2 V (FP32 or BF16); AX: X
   const float* base;   // direction: V; AX: X  (the row block M in A M = -M - D^-1/2 S D^-1/2 M)
   float* out;          // direction: W = AV; AX: AX
-  const float* G;      // direction with dots: the direction G
-  double* dots;        // direction with dots: [blocks][2][kp] partials of diag(V^T AV), diag(V^T G)
+  double* dots;        // direction with dots: [blocks][kp] partials of diag(V^T AV)
   Ctrl* ctrl;
   int ignore_done;
 };
-
-#ifndef OFSC_ROW_STAGE
-#define OFSC_ROW_STAGE 1  // epilogue operands of the direction product staged by cp.async
-#endif
 
 #ifndef OFSC_ROW_U32
 #define OFSC_ROW_U32 8  // gathers in flight per lane when a warp covers a row of 128 columns
@@ -133,13 +128,6 @@ struct SpmmArgs {
 #ifndef OFSC_ROW_MINB
 #define OFSC_ROW_MINB (32 / kRowWarpsPerBlock)  // resident blocks per SM the registers must allow
 #endif
-// 16-byte global -> shared copy that completes asynchronously (L2 only), and its fences.
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Four consecutive values of row `row` from column c, as FP32 (FP32 or BF16 storage).
 template <bool BF16>
@@ -223,32 +211,29 @@ __global__ void __launch_bounds__(256, 2) k_spmm(SpmmArgs a) {
   }
 }
 
-// W = A V = -V - D^-1/2 S Vh for a direction V, with the fused partial sums of diag(V^T AV) and
-// diag(V^T G). A warp owns a contiguous, nnz-balanced range of rows and takes one row at a time,
-// so its control flow is uniform: LPN lanes per nonzero hold four columns each, NPI = 32 / LPN
-// nonzeros are gathered side by side and U of those slots per lane are in flight together
-// (STEP = U NPI <= 32 nonzeros per step; a short row's last step is predicated, not split). The
-// STEP column indices of a step are loaded one per lane and handed out by shuffle; those of the
-// next step (at a row end, of the next row) are loaded while the current gathers are in flight,
-// and a row's epilogue operands (its rows of V and G) are copied to shared memory with cp.async
-// during the gathers of its last step, holding no registers meanwhile. Each lane sums its slots
-// in nonzero order; the NPI partial sums of a row are combined by an xor-shuffle butterfly, which
-// leaves the same bits in every lane (for LPN = 32 the sum is in plain nonzero order). Blocks
-// are small (kRowWarpsPerBlock warps over about 1024 nonzeros each) so the grid runs in several
-// waves with a short last one; the per-block dots partials are folded by k_dots_fold.
+// W = A V = -V - D^-1/2 S Vh for a direction V (or AX from Xh = D^-1/2 X), with the fused
+// per-block partial sums of diag(V^T AV). A warp owns a contiguous, nnz-balanced range of rows
+// and takes one row at a time, so its control flow is uniform: LPN lanes per nonzero hold four
+// columns each, NPI = 32 / LPN nonzeros are gathered side by side and U of those slots per lane
+// are in flight together (STEP = U NPI <= 32 nonzeros per step; a short row's last step is
+// predicated, not split). The STEP column indices of a step are loaded one per lane and handed
+// out by shuffle; those of the next step (at a row end, of the next row) are loaded while the
+// current gathers are in flight, and a row's epilogue operands (its row of V, its D^-1/2 entry)
+// are loaded with the gathers of its last step (staging them through shared memory with cp.async
+// measured 12% slower). Each lane sums its slots in nonzero order; the NPI partial sums of a row
+// are combined by an xor-shuffle butterfly, which leaves the same bits in every lane (for LPN = 32
+// the sum is in plain nonzero order). The per-block partials are folded by k_dots_fold.
 template <int LPN, bool WEIGHTED, bool BF16, bool DOTS>
 __global__ void __launch_bounds__(32 * kRowWarpsPerBlock, OFSC_ROW_MINB) k_spmm_dir(SpmmArgs a) {
-  if (a.ctrl->done) return;
+  if (!a.ignore_done && a.ctrl->done) return;
   constexpr int NPI = 32 / LPN;
   constexpr int U = LPN == 32 ? OFSC_ROW_U32 : LPN == 16 ? 4 : 2;
   constexpr int STEP = U * NPI;
   constexpr int WPB = kRowWarpsPerBlock;
   constexpr int W = 4 * LPN;
   static_assert(STEP <= 32, "one column index per lane");
-  // per-warp sums of diag(V^T AV), diag(V^T G) over the warp's rows; each lane owns its columns
-  __shared__ float dred[DOTS ? WPB * 2 * W : 1];
-  // the epilogue operands V and G of a row, copied asynchronously during its last step's gathers
-  __shared__ __align__(16) float stage[WPB][2][W];
+  // per-warp sums of diag(V^T AV) over the warp's rows; each lane owns its columns
+  __shared__ float dred[DOTS ? WPB * W : 1];
   const int lane = threadIdx.x & 31;
   const int sub = lane % LPN;
   const int q = lane / LPN;
@@ -256,11 +241,8 @@ __global__ void __launch_bounds__(32 * kRowWarpsPerBlock, OFSC_ROW_MINB) k_spmm_
   const int gw = blockIdx.x * WPB + warp;
   const int c = sub * 4;
   const bool active = c < a.kp;
-  float* rr = dred + (size_t)warp * 2 * W;
-  if (DOTS && lane < LPN) {
-    *(float4*)(rr + c) = make_float4(0.f, 0.f, 0.f, 0.f);
-    *(float4*)(rr + W + c) = make_float4(0.f, 0.f, 0.f, 0.f);
-  }
+  float* rr = dred + (size_t)warp * W;
+  if (DOTS && lane < LPN) *(float4*)(rr + c) = make_float4(0.f, 0.f, 0.f, 0.f);
   if (gw < a.groups) {
     int l = (int)a.bnd[gw];  // column indices are int32, so n < 2^31
     const int rb = (int)a.bnd[gw + 1];
@@ -282,23 +264,11 @@ __global__ void __launch_bounds__(32 * kRowWarpsPerBlock, OFSC_ROW_MINB) k_spmm_
         const int64_t rem = p1 - pb;
         const bool last = rem <= STEP;
         float s = 0.0f;
-#if OFSC_ROW_STAGE
+        float4 base = make_float4(0.f, 0.f, 0.f, 0.f);
         if (last && lane < LPN && active) {
-          const int64_t o = (int64_t)l * a.kp + c;
-          cp_async16(&stage[warp][0][c], a.base + o);
-          if (DOTS) cp_async16(&stage[warp][1][c], a.G + o);
-          cp_async_commit();
+          base = *(const float4*)(a.base + (int64_t)l * a.kp + c);
           s = a.dinv[l];
         }
-#else
-        float4 base = make_float4(0.f, 0.f, 0.f, 0.f), gg = base;
-        if (last && lane < LPN && active) {
-          const int64_t o = (int64_t)l * a.kp + c;
-          base = *(const float4*)(a.base + o);
-          if (DOTS) gg = *(const float4*)(a.G + o);
-          s = a.dinv[l];
-        }
-#endif
         float4 v[U];
         float wv[U];
 #pragma unroll
@@ -332,24 +302,14 @@ __global__ void __launch_bounds__(32 * kRowWarpsPerBlock, OFSC_ROW_MINB) k_spmm_
             acc.w += __shfl_xor_sync(0xffffffffu, acc.w, off);
           }
           if (lane < LPN && active) {
-#if OFSC_ROW_STAGE
-            cp_async_wait_all();  // each lane reads back only its own copies
-            const float4 base = *(const float4*)&stage[warp][0][c];
-#endif
             const float4 r4 = make_float4(-fmaf(s, acc.x, base.x), -fmaf(s, acc.y, base.y),
                                           -fmaf(s, acc.z, base.z), -fmaf(s, acc.w, base.w));
             *(float4*)(a.out + (int64_t)l * a.kp + c) = r4;
             if (DOTS) {
-#if OFSC_ROW_STAGE
-              const float4 gg = *(const float4*)&stage[warp][1][c];
-#endif
-              float4 dcw = *(float4*)(rr + c), dvg = *(float4*)(rr + W + c);
+              float4 dcw = *(float4*)(rr + c);
               dcw.x = fmaf(base.x, r4.x, dcw.x); dcw.y = fmaf(base.y, r4.y, dcw.y);
               dcw.z = fmaf(base.z, r4.z, dcw.z); dcw.w = fmaf(base.w, r4.w, dcw.w);
-              dvg.x = fmaf(base.x, gg.x, dvg.x); dvg.y = fmaf(base.y, gg.y, dvg.y);
-              dvg.z = fmaf(base.z, gg.z, dvg.z); dvg.w = fmaf(base.w, gg.w, dvg.w);
               *(float4*)(rr + c) = dcw;
-              *(float4*)(rr + W + c) = dvg;
             }
           }
           if (!more) break;
@@ -363,62 +323,100 @@ __global__ void __launch_bounds__(32 * kRowWarpsPerBlock, OFSC_ROW_MINB) k_spmm_
   }
   if (DOTS) {  // per-block partials in a fixed order: warps, then columns
     __syncthreads();
-    for (int j = threadIdx.x; j < 2 * a.kp; j += blockDim.x) {
-      const int which = j / a.kp, col = j % a.kp;
+    for (int j = threadIdx.x; j < a.kp; j += blockDim.x) {
       double sum = 0.0;
-      for (int w = 0; w < WPB; ++w) sum += (double)dred[(size_t)w * 2 * W + which * W + col];
-      a.dots[(int64_t)blockIdx.x * 2 * a.kp + j] = sum;
+      for (int w = 0; w < WPB; ++w) sum += (double)dred[(size_t)w * W + j];
+      a.dots[(int64_t)blockIdx.x * a.kp + j] = sum;
     }
   }
 }
 
-// Folds nblk rows of per-block partials (width values each) into gridDim.x rows: row r sums the
-// blocks [r nblk / R, (r + 1) nblk / R) in order, so the result does not depend on scheduling.
-__global__ void k_dots_fold(const double* __restrict__ part, int nblk, int width, double* __restrict__ out,
-                            const Ctrl* ctrl) {
-  if (ctrl->done) return;
-  const int r = blockIdx.x;
-  const int b0 = (int)((int64_t)r * nblk / gridDim.x), b1 = (int)((int64_t)(r + 1) * nblk / gridDim.x);
-  for (int t = threadIdx.x; t < width; t += blockDim.x) {
-    double sum = 0.0;
-    for (int b = b0; b < b1; ++b) sum += part[(int64_t)b * width + t];
-    out[(int64_t)r * width + t] = sum;
-  }
-}
-
-// V_t = -G_t + V_{t-1} diag(beta) (V_0 = -G_0) and its gather copy Vh = D^-1/2 V_t (FP32 or BF16).
-template <bool BF16>
-__global__ void k_vpass(int64_t n, int kp, const float* __restrict__ G, float* __restrict__ V, void* __restrict__ Vh,
-                        const float* __restrict__ dinv, const float* __restrict__ beta, int first, Ctrl* ctrl) {
-  if (ctrl->done) return;
+// Xh = D^-1/2 X (FP32), the gathered block of the exact AX product.
+__global__ void k_scale_rows(int64_t n, int kp, const float* __restrict__ X, const float* __restrict__ dinv,
+                             float* __restrict__ Xh, const Ctrl* ctrl, int ignore_done) {
+  if (!ignore_done && ctrl->done) return;
   const int64_t total = n * kp / 4;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t e = i * 4;
-    const int64_t row = e / kp;
-    const int c = (int)(e - row * kp);
-    const float4 g = *(const float4*)(G + e);
-    float4 v = make_float4(-g.x, -g.y, -g.z, -g.w);
-    if (!first) {
-      const float4 b = *(const float4*)(beta + c);
-      const float4 vp = *(const float4*)(V + e);
-      v.x = fmaf(b.x, vp.x, v.x);
-      v.y = fmaf(b.y, vp.y, v.y);
-      v.z = fmaf(b.z, vp.z, v.z);
-      v.w = fmaf(b.w, vp.w, v.w);
+    const float s = dinv[e / kp];
+    const float4 x = *(const float4*)(X + e);
+    *(float4*)(Xh + e) = make_float4(s * x.x, s * x.y, s * x.z, s * x.w);
+  }
+}
+
+// Folds the per-block partials of diag(V^T AV) (pw: nw rows of kp) and of diag(V^T G) (pg: ng
+// rows) into gridDim.x rows of out[r][2][kp]: row r sums the blocks [r nb / R, (r + 1) nb / R) of
+// each source in order, so the result does not depend on scheduling.
+__global__ void k_dots_fold(const double* __restrict__ pw, int nw, const double* __restrict__ pg, int ng, int kp,
+                            double* __restrict__ out, const Ctrl* ctrl) {
+  if (ctrl->done) return;
+  const int r = blockIdx.x, R = gridDim.x;
+  for (int t = threadIdx.x; t < 2 * kp; t += blockDim.x) {
+    const int which = t / kp, j = t % kp;
+    const double* p = which ? pg : pw;
+    const int nb = which ? ng : nw;
+    const int b0 = (int)((int64_t)r * nb / R), b1 = (int)((int64_t)(r + 1) * nb / R);
+    double sum = 0.0;
+    for (int b = b0; b < b1; ++b) sum += p[(int64_t)b * kp + j];
+    out[(int64_t)r * 2 * kp + t] = sum;
+  }
+}
+
+// V_t = -G_t + V_{t-1} diag(beta) (V_0 = -G_0), its gather copy Vh = D^-1/2 V_t (FP32 or BF16) and
+// per-block partial sums of diag(V_t^T G_t), the derivative of every line-search polynomial at
+// alpha = 0. LPN lanes cover a row (four columns each, fixed per thread), 256 / LPN rows per
+// block step; each thread sums its columns over its rows, and the block adds its row groups in
+// order in FP64 into dots_g[blockIdx.x][kp].
+template <int LPN, bool BF16>
+__global__ void __launch_bounds__(256) k_vpass(int64_t n, int kp, const float* __restrict__ G, float* __restrict__ V,
+                                               void* __restrict__ Vh, const float* __restrict__ dinv,
+                                               const float* __restrict__ beta, int first, double* __restrict__ dots_g,
+                                               Ctrl* ctrl) {
+  if (ctrl->done) return;
+  constexpr int RPB = 256 / LPN;
+  constexpr int W = 4 * LPN;
+  __shared__ float red[RPB * W];
+  const int lane = threadIdx.x % LPN, rg = threadIdx.x / LPN;
+  const int c = lane * 4;
+  const bool active = c < kp;
+  float4 b = make_float4(0.f, 0.f, 0.f, 0.f), acc = b;
+  if (active && !first) b = *(const float4*)(beta + c);
+  if (active) {
+    for (int64_t row = (int64_t)blockIdx.x * RPB + rg; row < n; row += (int64_t)gridDim.x * RPB) {
+      const int64_t e = row * kp + c;
+      const float4 g = *(const float4*)(G + e);
+      float4 v = make_float4(-g.x, -g.y, -g.z, -g.w);
+      if (!first) {
+        const float4 vp = *(const float4*)(V + e);
+        v.x = fmaf(b.x, vp.x, v.x);
+        v.y = fmaf(b.y, vp.y, v.y);
+        v.z = fmaf(b.z, vp.z, v.z);
+        v.w = fmaf(b.w, vp.w, v.w);
+      }
+      *(float4*)(V + e) = v;
+      acc.x = fmaf(v.x, g.x, acc.x);
+      acc.y = fmaf(v.y, g.y, acc.y);
+      acc.z = fmaf(v.z, g.z, acc.z);
+      acc.w = fmaf(v.w, g.w, acc.w);
+      const float s = dinv[row];
+      if (BF16) {
+        __nv_bfloat162 h0 = __floats2bfloat162_rn(s * v.x, s * v.y);
+        __nv_bfloat162 h1 = __floats2bfloat162_rn(s * v.z, s * v.w);
+        uint2 u;
+        u.x = *reinterpret_cast<uint32_t*>(&h0);
+        u.y = *reinterpret_cast<uint32_t*>(&h1);
+        *(uint2*)((__nv_bfloat16*)Vh + e) = u;
+      } else {
+        *(float4*)((float*)Vh + e) = make_float4(s * v.x, s * v.y, s * v.z, s * v.w);
+      }
     }
-    *(float4*)(V + e) = v;
-    const float s = dinv[row];
-    if (BF16) {
-      __nv_bfloat162 h0 = __floats2bfloat162_rn(s * v.x, s * v.y);
-      __nv_bfloat162 h1 = __floats2bfloat162_rn(s * v.z, s * v.w);
-      uint2 u;
-      u.x = *reinterpret_cast<uint32_t*>(&h0);
-      u.y = *reinterpret_cast<uint32_t*>(&h1);
-      *(uint2*)((__nv_bfloat16*)Vh + e) = u;
-    } else {
-      *(float4*)((float*)Vh + e) = make_float4(s * v.x, s * v.y, s * v.z, s * v.w);
-    }
+  }
+  *(float4*)(red + rg * W + c) = acc;
+  __syncthreads();
+  for (int j = threadIdx.x; j < kp; j += blockDim.x) {
+    double sum = 0.0;
+    for (int r = 0; r < RPB; ++r) sum += (double)red[r * W + j];
+    dots_g[(int64_t)blockIdx.x * kp + j] = sum;
   }
 }
 
@@ -1315,6 +1313,24 @@ void launch_spmm(const SpmmArgs& a, bool weighted, cudaStream_t s) {
   }
 }
 
+void launch_vpass(int lpn, bool bf16, int grid, cudaStream_t s, int64_t n, int kp, const float* G, float* V, void* Vh,
+                  const float* dinv, const float* beta, int first, double* dots_g, Ctrl* ctrl) {
+#define OFSC_VPASS(L)                                                                                    \
+  case L:                                                                                               \
+    if (bf16) k_vpass<L, true><<<grid, 256, 0, s>>>(n, kp, G, V, Vh, dinv, beta, first, dots_g, ctrl);   \
+    else k_vpass<L, false><<<grid, 256, 0, s>>>(n, kp, G, V, Vh, dinv, beta, first, dots_g, ctrl);       \
+    break;
+  switch (lpn) {
+    OFSC_VPASS(2)
+    OFSC_VPASS(4)
+    OFSC_VPASS(8)
+    OFSC_VPASS(16)
+    default:
+      OFSC_VPASS(32)
+  }
+#undef OFSC_VPASS
+}
+
 template <int LPN, bool WEIGHTED, bool BF16>
 void launch_dir_w(const SpmmArgs& a, bool dots, cudaStream_t s) {
   const int grid = a.groups / kRowWarpsPerBlock;
@@ -1455,7 +1471,7 @@ ofsc_status ensure_workspace(ofsc_graph* g, int kp) {
       {(void**)&ws.Bn, kk * sizeof(float)},
       {(void**)&ws.R64, kk * sizeof(double)},
       {(void**)&ws.B64, kk * sizeof(double)},
-      {(void**)&ws.dots, (size_t)(kRowMaxBlocks + kDotsRows) * 2 * kp * sizeof(double)},
+      {(void**)&ws.dots, (size_t)(kRowMaxBlocks + kVpassMaxBlocks + 2 * kDotsRows) * kp * sizeof(double)},
       {(void**)&ws.part_tc, kp > 64 ? std::max(gram_tc_part_bytes(n, 2, gram_tc_rows_per_cta(n, 2)),
                                                gram_tc_part_bytes(n, 4, gram_tc_rows_per_cta(n, 4)))
                                     : (size_t)16},
@@ -1517,7 +1533,7 @@ struct Runner {
       if (timed) prof.begin(OFSC_PHASE_GRAM);
       cudaError_t e = gram_tc_launch(t, slots, ws.kp, ws.gram, s);
       if (timed) prof.end();
-      g_launches += 2;
+      g_launches += 3;
       return e;
     }
     GramPairs p{};
@@ -1547,14 +1563,22 @@ struct Runner {
   }
 
   // AX from X exactly, then X^T X and X^T AX; Rn, Bn and f of `objective` from them.
+  // (The gather copy Vh of the current direction is dead here: the next V pass rewrites it, so
+  // it holds D^-1/2 X for the warp-per-row product.)
   cudaError_t refresh(int objective, int ignore_done) {
+    prof.begin(OFSC_PHASE_REFRESH);
+    float* Xh = (float*)ws.Vh;
+    k_scale_rows<<<(int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ws.n * ws.kp / 4, 256), 8 * kNumSMs)), 256, 0,
+                   s>>>(ws.n, ws.kp, ws.X, g->dinv, Xh, ws.ctrl, ignore_done);
+    ++g_launches;
     SpmmArgs a = spmm_base();
-    a.gather = ws.X;
+    a.bnd = g->bnd[kRowPart];
+    a.groups = g->groups[kRowPart];
+    a.gather = Xh;
     a.base = ws.X;
     a.out = ws.Y;
     a.ignore_done = ignore_done;
-    prof.begin(OFSC_PHASE_REFRESH);
-    launch_spmm(a, g->weighted != 0, s);
+    launch_spmm_dir(a, g->weighted != 0, false, s);
     const float* R[2] = {ws.X, ws.Y};
     const int slots[2] = {G_R, G_B};
     cudaError_t e = grams(ws.X, R, 2, slots, ignore_done, false);
@@ -1592,21 +1616,25 @@ struct Runner {
 
   cudaError_t direction_and_linesearch(int first, const ofsc_opts& o, int k, double alpha0) {
     const bool f2 = method >= M_OFM_F2;
+    // Partials of diag(V^T AV) (sparse product) and diag(V^T G) (V pass) in ws.dots, then their
+    // fold into kDotsRows rows of [2][kp] for the solve.
+    double* dots_w = ws.dots;
+    double* dots_g = ws.dots + (size_t)kRowMaxBlocks * ws.kp;
+    double* folded = dots_g + (size_t)kVpassMaxBlocks * ws.kp;
     // V_t = -G_t + V_{t-1} diag(beta) and Vh = D^-1/2 V_t for the gather
     prof.begin(OFSC_PHASE_OTHER);
-    const int vgrid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ws.n * ws.kp / 4, 256), 8 * kNumSMs));
-    if (bf16) k_vpass<true><<<vgrid, 256, 0, s>>>(ws.n, ws.kp, ws.G, ws.V, ws.Vh, g->dinv, ws.beta, first, ws.ctrl);
-    else k_vpass<false><<<vgrid, 256, 0, s>>>(ws.n, ws.kp, ws.G, ws.V, ws.Vh, g->dinv, ws.beta, first, ws.ctrl);
+    const int lpn = spmm_lanes(ws.kp);
+    const int vgrid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ws.n, 256 / lpn), kVpassMaxBlocks));
+    launch_vpass(lpn, bf16, vgrid, s, ws.n, ws.kp, ws.G, ws.V, ws.Vh, g->dinv, ws.beta, first, dots_g, ws.ctrl);
     ++g_launches;
     prof.end();
-    // AV_t exactly (one sparse product), with diag(V^T AV) and diag(V^T G)
+    // AV_t exactly (one sparse product), with diag(V^T AV)
     SpmmArgs a = spmm_base();
     a.gather = ws.Vh;
     a.base = ws.V;
     a.out = ws.W;
-    a.G = ws.G;
-    a.dots = ws.dots;
-    int dots_blocks = a.groups / (256 / spmm_lanes(ws.kp));
+    a.dots = dots_w;
+    int dots_blocks = 0;
     prof.begin(OFSC_PHASE_SPMM);
     if (tma) {
       TmaSpmmArgs t{};
@@ -1621,8 +1649,7 @@ struct Runner {
       t.groups = g->groups[pi];
       t.base = ws.V;
       t.out = ws.W;
-      t.G = ws.G;
-      t.dots = ws.dots;
+      t.dots = dots_w;
       t.ctrl = ws.ctrl;
       cudaError_t e = spmm_tma_launch(ws.vh_map[bf16 ? 1 : 0], t, bf16, g->weighted != 0, s);
       if (e != cudaSuccess) return e;
@@ -1633,14 +1660,8 @@ struct Runner {
       a.groups = g->groups[kRowPart];
       dots_blocks = launch_spmm_dir(a, g->weighted != 0, bf16, s);
     }
-    const double* dots = ws.dots;
-    if (dots_blocks > kDotsRows) {
-      double* folded = ws.dots + (size_t)kRowMaxBlocks * 2 * ws.kp;
-      k_dots_fold<<<kDotsRows, 256, 0, s>>>(ws.dots, dots_blocks, 2 * ws.kp, folded, ws.ctrl);
-      ++g_launches;
-      dots = folded;
-      dots_blocks = kDotsRows;
-    }
+    k_dots_fold<<<kDotsRows, 256, 0, s>>>(dots_w, dots_blocks, dots_g, vgrid, ws.kp, folded, ws.ctrl);
+    ++g_launches;
     prof.end();
     // V^T X and V^T V for every method; V^T AX and V^T AV in full for the f2 methods
     const float* Rs[4] = {ws.X, ws.V, ws.Y, ws.W};
@@ -1649,8 +1670,8 @@ struct Runner {
     if (e != cudaSuccess) return e;
     SolveArgs sa{};
     sa.gram = ws.gram;
-    sa.dots = dots;
-    sa.dots_blocks = dots_blocks;
+    sa.dots = folded;
+    sa.dots_blocks = kDotsRows;
     sa.dE = ws.dE;
     sa.R64 = ws.R64;
     sa.B64 = ws.B64;

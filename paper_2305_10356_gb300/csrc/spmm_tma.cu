@@ -6,7 +6,7 @@
 // shared-memory slots, each with its own mbarrier, kTmaStages slots ahead of the consumer. All 32
 // lanes then read their k/32 columns of the 4 rows from shared memory and accumulate them into
 // the current row; when the stream passes a row's end the warp writes AV for that row and adds
-// diag(V^T AV) and diag(V^T G) to its partial sums. Deep memory-level parallelism therefore
+// its terms of diag(V^T AV) to its partial sums. Deep memory-level parallelism therefore
 // costs no registers. Every mbarrier wait is bounded (OFSC_ERR_TIMEOUT on expiry).
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(kTmaWarps * 32) k_spmm_tma(const __grid_consta
   constexpr int SLOT = 4 * ROWB;
   extern __shared__ unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bars[kTmaWarps][kTmaStages];
-  __shared__ float dred[kTmaWarps][2][KP];
+  __shared__ float dred[kTmaWarps][KP];
   __shared__ int abort_flag;
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -125,9 +125,9 @@ __global__ void __launch_bounds__(kTmaWarps * 32) k_spmm_tma(const __grid_consta
   }
   __syncthreads();
 
-  float dcw[CPL], dvg[CPL];
+  float dcw[CPL];
 #pragma unroll
-  for (int u = 0; u < CPL; ++u) dcw[u] = dvg[u] = 0.f;
+  for (int u = 0; u < CPL; ++u) dcw[u] = 0.f;
   const int c = lane * CPL;
   const int gid = blockIdx.x * kTmaWarps + warp;
   bool ok = true;
@@ -178,13 +178,12 @@ __global__ void __launch_bounds__(kTmaWarps * 32) k_spmm_tma(const __grid_consta
         return __shfl_sync(0xffffffffu, wreg, (int)(row - wbase));
       };
       int64_t rend = row_end(r);
-      float acc[CPL], ev[CPL], eg[CPL];
+      float acc[CPL], ev[CPL];
       float es = 0.f;
       auto load_epi = [&](int64_t row) {
         es = a.dinv[row];
         const int64_t o = row * KP + c;
         ldg_cpl<CPL>(a.base + o, ev);
-        ldg_cpl<CPL>(a.G + o, eg);
       };
       auto finish = [&]() {
         const int64_t o = r * KP + c;
@@ -193,7 +192,6 @@ __global__ void __launch_bounds__(kTmaWarps * 32) k_spmm_tma(const __grid_consta
         for (int u = 0; u < CPL; ++u) {
           w[u] = -fmaf(es, acc[u], ev[u]);
           dcw[u] = fmaf(ev[u], w[u], dcw[u]);
-          dvg[u] = fmaf(ev[u], eg[u], dvg[u]);
           acc[u] = 0.f;
         }
         stg_cpl<CPL>(a.out + o, w);
@@ -239,18 +237,14 @@ __global__ void __launch_bounds__(kTmaWarps * 32) k_spmm_tma(const __grid_consta
     }
   }
   if (!ok) abort_flag = 1;
-  // per-block partials of diag(V^T AV), diag(V^T G): warps in order, then columns
+  // per-block partials of diag(V^T AV): warps in order, then columns
 #pragma unroll
-  for (int u = 0; u < CPL; ++u) {
-    dred[warp][0][c + u] = dcw[u];
-    dred[warp][1][c + u] = dvg[u];
-  }
+  for (int u = 0; u < CPL; ++u) dred[warp][c + u] = dcw[u];
   __syncthreads();
-  for (int j = threadIdx.x; j < 2 * KP; j += blockDim.x) {
-    const int which = j / KP, col = j % KP;
+  for (int j = threadIdx.x; j < KP; j += blockDim.x) {
     double sum = 0.0;
-    for (int w = 0; w < kTmaWarps; ++w) sum += (double)dred[w][which][col];
-    a.dots[(int64_t)blockIdx.x * 2 * KP + j] = sum;
+    for (int w = 0; w < kTmaWarps; ++w) sum += (double)dred[w][j];
+    a.dots[(int64_t)blockIdx.x * KP + j] = sum;
   }
   if (threadIdx.x == 0 && abort_flag) {
     a.ctrl->status = OFSC_ERR_TIMEOUT;

@@ -198,18 +198,29 @@ def run_reference(args):
     return 0
 
 
-def phase_bytes(n: int, kp: int, nnz: int, gather_bytes: int, weighted: bool) -> dict:
-    """Compulsory HBM bytes per launch of each phase (every array touched once)."""
-    row = 4 * n * kp
+def spmm_bytes(n: int, kp: int, nnz: int, gather_bytes: int, weighted: bool, h: float) -> dict:
+    """Algorithmic HBM bytes of one direction product W = A V (the cost model of the one-product
+    design): CSR (int64 row pointers, int32 columns, FP32 weights), the gathered rows of
+    D^-1/2 V that miss L2 (nnz k b_g (1 - h)), the epilogue read of V and D^-1/2, the write of W."""
     csr = 8 * (n + 1) + 4 * nnz + (4 * nnz if weighted else 0)
-    return {
-        # read X, Y, V, W, G_prev; write X, Y, G and the gather copy Gh
-        "direction": 5 * row + 3 * row + gather_bytes * n * kp,
-        # CSR + D^-1/2 + each gathered row once + read G, V, W; write V, W
-        "spmm": csr + 4 * n + gather_bytes * n * kp + 3 * row + 2 * row,
-        # read X, V, Y, W once
-        "gram": 4 * row,
-    }
+    gather_all = nnz * kp * gather_bytes
+    return {"csr": csr, "gather": int(gather_all * (1.0 - h)), "gather_all": gather_all,
+            "epilogue": 4 * n * kp + 4 * n, "write": 4 * n * kp,
+            "total": int(csr + gather_all * (1.0 - h) + 4 * n * kp + 4 * n + 4 * n * kp)}
+
+
+def measured_traffic(workload: str, gather: str) -> dict | None:
+    """ncu DRAM counters of the direction product at this workload (profiles/traffic.json), or
+    None when the kernel sources changed since they were taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        tj = json.load(fh)
+    entry = tj.get("entries", {}).get(f"{workload}/{gather}")
+    if not entry or entry.get("source_digest") != source_digest():
+        return None
+    return entry
 
 
 def run_gpu(args):
@@ -291,37 +302,29 @@ def run_gpu(args):
     e2e = {"value": updates / e2e_s, "unit": "iterations/s",
            "h2d_bytes_per_step": int(x0.nbytes), "d2h_bytes_per_step": int(x0.nbytes)}
 
-    # dominant phase and its roofline
+    # dominant kernel (the direction product, phase "spmm") and its roofline
     pd = prof.as_dict()
     dom = max(pd, key=lambda p: pd[p]["ms"])
     kp = ((e.n_blocks + 7) // 8) * 8
     gb = 2 if args.gather == "bf16" else 4
     peaks = load_peaks()
-    bytes_ = phase_bytes(e.n, kp, int(info.nnz), gb, bool(info.weighted))
-    per_launch_ms = pd[dom]["ms"] / max(1, pd[dom]["launches"])
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tpath):
-        with open(tpath) as fh:
-            tj = json.load(fh)
-        if tj.get("source_digest") == source_digest() and tj.get("workload") == args.workload:
-            traffic = tj.get("bytes_per_launch", {}).get(dom)
-    if dom == "gram":
-        # SIMT FP32 Gram: ALU bound; algorithmic flops = 6 Grams x 2 N k^2
-        flops = 6 * 2.0 * e.n * e.n_blocks ** 2
-        achieved = flops / (per_launch_ms / 1000.0) / 1e12
-        peak = NUM_SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-        roof = {"bound": "alu", "kernel": "k_gram", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
-                "algorithmic": f"{flops:.4g} flop/launch", "ms_per_launch": per_launch_ms}
-    else:
-        alg = bytes_.get(dom, 0)
-        achieved = alg / (per_launch_ms / 1000.0) / 1e9
-        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                "peak_source": peaks["source"], "algorithmic": f"{alg} B/launch",
-                "ms_per_launch": per_launch_ms}
+    per_launch_ms = pd["spmm"]["ms"] / max(1, pd["spmm"]["launches"])
+    tr = measured_traffic(args.workload if args.nodes is None else f"{args.workload}@{args.nodes}", args.gather)
+    # L2 hit rate of the gathers: from the measured DRAM reads of the kernel when available (the
+    # rows that did not come from DRAM came from L2), else 0 (every gathered row from HBM)
+    h = 0.0
+    if tr is not None:
+        base = spmm_bytes(e.n, kp, int(info.nnz), gb, bool(info.weighted), 0.0)
+        miss = tr["dram_read_bytes"] - base["csr"] - base["epilogue"]
+        h = min(1.0, max(0.0, 1.0 - miss / base["gather_all"]))
+    alg = spmm_bytes(e.n, kp, int(info.nnz), gb, bool(info.weighted), h)
+    achieved = alg["total"] / (per_launch_ms / 1000.0) / 1e9
+    roof = {"bound": "hbm", "kernel": "k_spmm_dir (direction product W = A V)", "achieved": achieved,
+            "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+            "traffic": (tr["dram_read_bytes"] + tr["dram_write_bytes"]) if tr else None,
+            "peak_source": f"{peaks['source']} (copy bandwidth)",
+            "algorithmic_bytes": alg["total"], "gather_l2_hit": round(h, 4),
+            "ms_per_launch": per_launch_ms, "dominant_phase": dom}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

@@ -123,10 +123,16 @@ struct SpmmArgs {
 };
 
 #ifndef OFSC_ROW_U32
-#define OFSC_ROW_U32 8  // gathers in flight per lane when a warp covers a row of 128 columns
+#define OFSC_ROW_U32 6  // gathers in flight per lane when a warp covers a row of 128 columns
 #endif
 #ifndef OFSC_ROW_MINB
-#define OFSC_ROW_MINB (32 / kRowWarpsPerBlock)  // resident blocks per SM the registers must allow
+#define OFSC_ROW_MINB 5  // resident blocks per SM the registers must allow (40 warps)
+#endif
+#ifndef OFSC_ROW_U16_BF16
+#define OFSC_ROW_U16_BF16 4  // the same for 16-byte BF16 slots (128 columns)
+#endif
+#ifndef OFSC_ROW_MINB_BF16
+#define OFSC_ROW_MINB_BF16 (32 / kRowWarpsPerBlock)  // the same with 16-byte BF16 slots
 #endif
 
 // Four consecutive values of row `row` from column c, as FP32 (FP32 or BF16 storage).
@@ -223,26 +229,90 @@ __global__ void __launch_bounds__(256, 2) k_spmm(SpmmArgs a) {
 // measured 12% slower). Each lane sums its slots in nonzero order; the NPI partial sums of a row
 // are combined by an xor-shuffle butterfly, which leaves the same bits in every lane (for LPN = 32
 // the sum is in plain nonzero order). The per-block partials are folded by k_dots_fold.
-template <int LPN, bool WEIGHTED, bool BF16, bool DOTS>
-__global__ void __launch_bounds__(32 * kRowWarpsPerBlock, OFSC_ROW_MINB) k_spmm_dir(SpmmArgs a) {
+// One gathered slot of VPL consecutive values of a row of Vh, kept raw (FP32: float4; BF16: 8
+// values in a uint4) until it is accumulated, so a slot in flight costs four registers.
+template <int VPL, bool BF16>
+struct Slot;
+template <>
+struct Slot<4, false> {
+  using Raw = float4;
+  static __device__ __forceinline__ Raw load(const void* p, int64_t row, int kp, int c) {
+    return __ldg((const float4*)((const float*)p + row * kp + c));
+  }
+  static __device__ __forceinline__ Raw zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+  static __device__ __forceinline__ void fma(float* acc, float w, const Raw& r) {
+    acc[0] = fmaf(w, r.x, acc[0]);
+    acc[1] = fmaf(w, r.y, acc[1]);
+    acc[2] = fmaf(w, r.z, acc[2]);
+    acc[3] = fmaf(w, r.w, acc[3]);
+  }
+};
+template <>
+struct Slot<4, true> {
+  using Raw = uint2;
+  static __device__ __forceinline__ Raw load(const void* p, int64_t row, int kp, int c) {
+    return __ldg((const uint2*)((const __nv_bfloat16*)p + row * kp + c));
+  }
+  static __device__ __forceinline__ Raw zero() { return make_uint2(0u, 0u); }
+  static __device__ __forceinline__ void fma(float* acc, float w, const Raw& r) {
+    const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&r.x));
+    const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&r.y));
+    acc[0] = fmaf(w, a.x, acc[0]);
+    acc[1] = fmaf(w, a.y, acc[1]);
+    acc[2] = fmaf(w, b.x, acc[2]);
+    acc[3] = fmaf(w, b.y, acc[3]);
+  }
+};
+template <>
+struct Slot<8, true> {
+  using Raw = uint4;
+  static __device__ __forceinline__ Raw load(const void* p, int64_t row, int kp, int c) {
+    return __ldg((const uint4*)((const __nv_bfloat16*)p + row * kp + c));
+  }
+  static __device__ __forceinline__ Raw zero() { return make_uint4(0u, 0u, 0u, 0u); }
+  static __device__ __forceinline__ void fma(float* acc, float w, const Raw& r) {
+    const uint32_t u[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u[i]));
+      acc[2 * i] = fmaf(w, f.x, acc[2 * i]);
+      acc[2 * i + 1] = fmaf(w, f.y, acc[2 * i + 1]);
+    }
+  }
+};
+
+// Slots in flight per lane: FP32 rows use 4 values per lane, BF16 rows 8 (16-byte loads), so a
+// warp holds twice as many BF16 rows in flight in the same registers.
+template <int LPN, int VPL>
+__host__ __device__ constexpr int dir_slots() {
+  return VPL == 4 ? (LPN == 32 ? OFSC_ROW_U32 : LPN == 16 ? 4 : 2) : (LPN == 16 ? OFSC_ROW_U16_BF16 : LPN == 8 ? 4 : 2);
+}
+
+template <int LPN, int VPL, bool WEIGHTED, bool BF16, bool DOTS>
+__global__ void __launch_bounds__(32 * kRowWarpsPerBlock, VPL == 4 ? OFSC_ROW_MINB : OFSC_ROW_MINB_BF16)
+    k_spmm_dir(SpmmArgs a) {
   if (!a.ignore_done && a.ctrl->done) return;
+  using S = Slot<VPL, BF16>;
   constexpr int NPI = 32 / LPN;
-  constexpr int U = LPN == 32 ? OFSC_ROW_U32 : LPN == 16 ? 4 : 2;
+  constexpr int U = dir_slots<LPN, VPL>();
   constexpr int STEP = U * NPI;
   constexpr int WPB = kRowWarpsPerBlock;
-  constexpr int W = 4 * LPN;
+  constexpr int W = VPL * LPN;
   static_assert(STEP <= 32, "one column index per lane");
   // per-warp sums of diag(V^T AV) over the warp's rows; each lane owns its columns
-  __shared__ float dred[DOTS ? WPB * W : 1];
+  __shared__ __align__(16) float dred[DOTS ? WPB * W : 4];
   const int lane = threadIdx.x & 31;
   const int sub = lane % LPN;
   const int q = lane / LPN;
   const int warp = threadIdx.x >> 5;
   const int gw = blockIdx.x * WPB + warp;
-  const int c = sub * 4;
+  const int c = sub * VPL;
   const bool active = c < a.kp;
   float* rr = dred + (size_t)warp * W;
-  if (DOTS && lane < LPN) *(float4*)(rr + c) = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (DOTS && lane < LPN) {
+#pragma unroll
+    for (int i = 0; i < VPL; ++i) rr[c + i] = 0.0f;
+  }
   if (gw < a.groups) {
     int l = (int)a.bnd[gw];  // column indices are int32, so n < 2^31
     const int rb = (int)a.bnd[gw + 1];
@@ -259,24 +329,29 @@ __global__ void __launch_bounds__(32 * kRowWarpsPerBlock, OFSC_ROW_MINB) k_spmm_
           if (WEIGHTED) wl = __ldg(a.val + i);
         }
       }
-      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+      float acc[VPL];
+#pragma unroll
+      for (int i = 0; i < VPL; ++i) acc[i] = 0.0f;
       while (true) {
         const int64_t rem = p1 - pb;
         const bool last = rem <= STEP;
         float s = 0.0f;
-        float4 base = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (last && lane < LPN && active) {
-          base = *(const float4*)(a.base + (int64_t)l * a.kp + c);
-          s = a.dinv[l];
+        float base[VPL];
+#pragma unroll
+        for (int i = 0; i < VPL; i += 4) {
+          float4 b4 = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (last && lane < LPN && active) b4 = *(const float4*)(a.base + (int64_t)l * a.kp + c + i);
+          base[i] = b4.x; base[i + 1] = b4.y; base[i + 2] = b4.z; base[i + 3] = b4.w;
         }
-        float4 v[U];
+        if (last && lane < LPN && active) s = a.dinv[l];
+        typename S::Raw v[U];
         float wv[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           const int slot = u * NPI + q;
           const int j = __shfl_sync(0xffffffffu, jl, slot);
           wv[u] = WEIGHTED ? __shfl_sync(0xffffffffu, wl, slot) : 1.0f;
-          v[u] = (slot < rem && active) ? load_row4<BF16>(a.gather, j, a.kp, c) : make_float4(0.f, 0.f, 0.f, 0.f);
+          v[u] = (slot < rem && active) ? S::load(a.gather, j, a.kp, c) : S::zero();
         }
         const int64_t pn = last ? p1 : pb + STEP;
         const bool more = !last || l + 1 < rb;
@@ -292,30 +367,29 @@ __global__ void __launch_bounds__(32 * kRowWarpsPerBlock, OFSC_ROW_MINB) k_spmm_
         }
 #pragma unroll
         for (int u = 0; u < U; ++u)
-          if (u * NPI + q < rem) fma4(acc, wv[u], v[u]);
+          if (u * NPI + q < rem) S::fma(acc, wv[u], v[u]);
         if (last) {
 #pragma unroll
-          for (int off = LPN; off < 32; off <<= 1) {
-            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
-            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
-            acc.z += __shfl_xor_sync(0xffffffffu, acc.z, off);
-            acc.w += __shfl_xor_sync(0xffffffffu, acc.w, off);
-          }
+          for (int off = LPN; off < 32; off <<= 1)
+#pragma unroll
+            for (int i = 0; i < VPL; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], off);
           if (lane < LPN && active) {
-            const float4 r4 = make_float4(-fmaf(s, acc.x, base.x), -fmaf(s, acc.y, base.y),
-                                          -fmaf(s, acc.z, base.z), -fmaf(s, acc.w, base.w));
-            *(float4*)(a.out + (int64_t)l * a.kp + c) = r4;
+            float r[VPL];
+#pragma unroll
+            for (int i = 0; i < VPL; ++i) r[i] = -fmaf(s, acc[i], base[i]);
+#pragma unroll
+            for (int i = 0; i < VPL; i += 4)
+              *(float4*)(a.out + (int64_t)l * a.kp + c + i) = make_float4(r[i], r[i + 1], r[i + 2], r[i + 3]);
             if (DOTS) {
-              float4 dcw = *(float4*)(rr + c);
-              dcw.x = fmaf(base.x, r4.x, dcw.x); dcw.y = fmaf(base.y, r4.y, dcw.y);
-              dcw.z = fmaf(base.z, r4.z, dcw.z); dcw.w = fmaf(base.w, r4.w, dcw.w);
-              *(float4*)(rr + c) = dcw;
+#pragma unroll
+              for (int i = 0; i < VPL; ++i) rr[c + i] = fmaf(base[i], r[i], rr[c + i]);
             }
           }
           if (!more) break;
           ++l;
           p1 = p1n;
-          acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+          for (int i = 0; i < VPL; ++i) acc[i] = 0.0f;
         }
         pb = pn;
       }
@@ -1331,34 +1405,46 @@ void launch_vpass(int lpn, bool bf16, int grid, cudaStream_t s, int64_t n, int k
 #undef OFSC_VPASS
 }
 
-template <int LPN, bool WEIGHTED, bool BF16>
+template <int LPN, int VPL, bool WEIGHTED, bool BF16>
 void launch_dir_w(const SpmmArgs& a, bool dots, cudaStream_t s) {
   const int grid = a.groups / kRowWarpsPerBlock;
-  if (dots) k_spmm_dir<LPN, WEIGHTED, BF16, true><<<grid, 32 * kRowWarpsPerBlock, 0, s>>>(a);
-  else k_spmm_dir<LPN, WEIGHTED, BF16, false><<<grid, 32 * kRowWarpsPerBlock, 0, s>>>(a);
+  if (dots) k_spmm_dir<LPN, VPL, WEIGHTED, BF16, true><<<grid, 32 * kRowWarpsPerBlock, 0, s>>>(a);
+  else k_spmm_dir<LPN, VPL, WEIGHTED, BF16, false><<<grid, 32 * kRowWarpsPerBlock, 0, s>>>(a);
 }
 
-template <int LPN>
-void launch_dir_l(const SpmmArgs& a, bool weighted, bool bf16, cudaStream_t s) {
+template <int LPN, int VPL, bool BF16>
+void launch_dir_l(const SpmmArgs& a, bool weighted, cudaStream_t s) {
   const bool dots = a.dots != nullptr;
-  if (weighted) {
-    if (bf16) launch_dir_w<LPN, true, true>(a, dots, s);
-    else launch_dir_w<LPN, true, false>(a, dots, s);
-  } else {
-    if (bf16) launch_dir_w<LPN, false, true>(a, dots, s);
-    else launch_dir_w<LPN, false, false>(a, dots, s);
-  }
+  if (weighted) launch_dir_w<LPN, VPL, true, BF16>(a, dots, s);
+  else launch_dir_w<LPN, VPL, false, BF16>(a, dots, s);
+}
+
+// Lanes per nonzero of the direction product: rows of kp values, VPL per lane, a power of two
+// of at least 2.
+int dir_lanes(int kp, int vpl) {
+  int l = 2;
+  while (l * vpl < kp) l *= 2;
+  return l;
 }
 
 // The direction product on the warp-per-row partition; returns the blocks (rows of dots partials).
 int launch_spmm_dir(const SpmmArgs& a, bool weighted, bool bf16, cudaStream_t s) {
   ++g_launches;
-  switch (spmm_lanes(a.kp)) {
-    case 2: launch_dir_l<2>(a, weighted, bf16, s); break;
-    case 4: launch_dir_l<4>(a, weighted, bf16, s); break;
-    case 8: launch_dir_l<8>(a, weighted, bf16, s); break;
-    case 16: launch_dir_l<16>(a, weighted, bf16, s); break;
-    default: launch_dir_l<32>(a, weighted, bf16, s); break;
+  if (bf16) {
+    switch (dir_lanes(a.kp, 8)) {
+      case 2: launch_dir_l<2, 8, true>(a, weighted, s); break;
+      case 4: launch_dir_l<4, 8, true>(a, weighted, s); break;
+      case 8: launch_dir_l<8, 8, true>(a, weighted, s); break;
+      default: launch_dir_l<16, 8, true>(a, weighted, s); break;
+    }
+  } else {
+    switch (dir_lanes(a.kp, 4)) {
+      case 2: launch_dir_l<2, 4, false>(a, weighted, s); break;
+      case 4: launch_dir_l<4, 4, false>(a, weighted, s); break;
+      case 8: launch_dir_l<8, 4, false>(a, weighted, s); break;
+      case 16: launch_dir_l<16, 4, false>(a, weighted, s); break;
+      default: launch_dir_l<32, 4, false>(a, weighted, s); break;
+    }
   }
   return a.groups / kRowWarpsPerBlock;
 }

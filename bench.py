@@ -1,14 +1,15 @@
 #!/usr/bin/env python
 """OFM iterations/s of the GB300 path on a seeded degree-corrected SBM (2,000,000 nodes, k = 128).
 
-One step = one ofsc_iterate call of 30 updates of Algorithm 2 (the paper's 30 iterations per
-static graph, Sec. 5.3) from the same X0, with the graph and X0 resident in HBM. `value` is
-updates per second over all ranks. `e2e` times the same steps through the public API from
-pinned host buffers (X0 copied in, X copied out every step). The dominant kernel's roofline
-comes from CUDA-event phase timings taken inside the timed steps. `--impl reference` times the
-FP64 CPU oracle on the same workload instead (one update per step).
+One step = one ofsc_iterate call of 30 updates of Algorithm 2 from the same X0, with the graph and
+X0 resident in HBM. By default the gathered block D^-1/2 V is stored in BF16 with the FP32 master
+copy and FP32 accumulation (the configured mixed-precision form); the plain FP32 path is timed on
+the same steps and reported as `plain_fp32`. `value` is updates per second over all ranks. `e2e`
+times the same steps through the public API from pinned host buffers (X0 copied in, X copied out
+every step). The dominant kernel's roofline comes from CUDA-event phase timings taken inside the
+timed steps. `--impl reference` times the FP64 CPU oracle on the same workload instead.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference] [--gather bf16|fp32]
 """
 from __future__ import annotations
 
@@ -116,7 +117,10 @@ def parse():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="dcsbm_n2m_k128")
     ap.add_argument("--method", default="ofm_f1", choices=list(METHODS))
-    ap.add_argument("--gather", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--gather", default="bf16", choices=["fp32", "bf16"],
+                    help="storage of the gathered block D^-1/2 V (bf16: FP32 master copy, FP32 accumulation)")
+    ap.add_argument("--no-fp32-compare", action="store_true",
+                    help="skip timing the plain FP32 path next to the BF16-gather one")
     ap.add_argument("--iters", type=int, default=30, help="updates of Algorithm 2 per step")
     ap.add_argument("--spmm-engine", default="auto", choices=["auto", "simt", "tma"])
     ap.add_argument("--nodes", type=int, default=None, help="shrink the workload (testing only)")
@@ -279,6 +283,31 @@ def run_gpu(args):
     updates = args.iters * args.steps * world
     value = updates / (elapsed_ms / 1000.0)
 
+    # the plain FP32 path on the same steps, for the mixed-vs-plain comparison of the metric
+    plain = None
+    if gather == ofsc.GATHER_BF16 and not args.no_fp32_compare:
+        def step32():
+            X.copy_(X0)
+            return ofsc.ofsc_iterate(g, method, X, 0.0, args.iters, gather=ofsc.GATHER_FP32, spmm_engine=eng)
+        step32()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        p_start = torch.cuda.Event(enable_timing=True)
+        p_end = torch.cuda.Event(enable_timing=True)
+        p_start.record(stream)
+        for _ in range(args.steps):
+            step32()
+        p_end.record(stream)
+        torch.cuda.synchronize()
+        p_ms = p_start.elapsed_time(p_end)
+        if world > 1:
+            t = torch.tensor([p_ms], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            p_ms = float(t.item())
+        plain = {"value": updates / (p_ms / 1000.0), "unit": "iterations/s", "ms_per_step": p_ms / args.steps,
+                 "gather": "fp32"}
+
     # end to end: pinned host X0 -> device, iterate, device -> pinned host X
     Xh0 = torch.from_numpy(x0).pin_memory()
     Xh = torch.empty_like(Xh0).pin_memory()
@@ -336,10 +365,10 @@ def run_gpu(args):
         line = {"metric": "OFM iterations/s", "value": value, "unit": "iterations/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32" if args.gather == "fp32" else "bf16-gather/f32",
+                "vs_baseline": None, "dtype": "f32" if args.gather == "fp32" else "f32 (bf16 gather storage)",
                 "data": "synthetic", "config": workload_config(args), "impl": "gpu",
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-                "gpu_launches": launches,
+                "gpu_launches": launches, "plain_fp32": plain,
                 "phases_ms_per_step": {p: pd[p]["ms"] / args.steps for p in pd},
                 "parallelism": "replicas only" if world > 1 else "single GPU"}
         print(json.dumps(line), flush=True)

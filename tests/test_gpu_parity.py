@@ -332,3 +332,17 @@ def test_direction_product_all_lane_widths_weighted(k):
     ref = o.iterate(og, o.OFM_F2, x0, 0.0, 4)
     assert np.linalg.norm(X - ref.X) <= 1e-4 * np.linalg.norm(ref.X)
     np.testing.assert_allclose(tr[:4, 3:3 + k], np.array(ref.alphas[:4]), rtol=1e-4, atol=1e-7)
+
+
+@pytest.mark.parametrize("gather", [0, 1])
+def test_iterations_are_bitwise_repeatable(gather):
+    """Every reduction has a fixed shape (per-block partials summed in block order, no atomics), so
+    two runs from the same X0 give the same bits."""
+    e = synth.sbm(4000, 8, 24.0, 6.0, seed=71, gamma=2.4, ratio_kind="count")
+    g = gpu_graph(e)
+    x0 = synth.initial_block(e.n, 64, 72)
+    X1, r1, t1 = run_iterate(g, o.OFM_F1, x0, 0.0, 12, trace_cap=13, gather=gather)
+    X2, r2, t2 = run_iterate(g, o.OFM_F1, x0, 0.0, 12, trace_cap=13, gather=gather)
+    assert np.array_equal(X1, X2)
+    assert np.array_equal(t1, t2)
+    assert r1.rel_dir_norm == r2.rel_dir_norm

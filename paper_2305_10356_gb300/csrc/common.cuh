@@ -187,6 +187,7 @@ struct GramTcArgs {
   float* part;           // [ctas][nr][128][128] FP32 partials
   Ctrl* ctrl;            // status / stop flag (may be null only with ignore_done = 1)
   int ignore_done;
+  int use_ws;            // allow the warp-specialised TMA kernel (L one of R, nr <= 2; own segments)
 };
 // Arguments of the TMA-gather sparse product (csrc/spmm_tma.cu): out = -base - D^-1/2 S Vh.
 struct TmaSpmmArgs {
@@ -206,6 +207,10 @@ struct TmaSpmmArgs {
 bool spmm_tma_supported(int kp);
 int spmm_tma_groups_per_block();
 ofsc_status spmm_tma_encode(const void* vh, int64_t n, int kp, bool bf16, CUtensorMap* map);
+// 2-D tensor map over a row-major FP32 block (rows x cols, row stride ld values): boxes of box_cols
+// x box_rows values with the 128-byte swizzle (box_cols <= 32), zero fill outside the block.
+ofsc_status tma_encode_f32_sw128(const float* base, int64_t rows, int cols, int ld, int box_cols, int box_rows,
+                                 CUtensorMap* map);
 cudaError_t spmm_tma_launch(const CUtensorMap& map, const TmaSpmmArgs& a, bool bf16, bool weighted, cudaStream_t s);
 
 int64_t gram_tc_rows_per_cta(int64_t n, int nr);

@@ -242,6 +242,295 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(GramTcArgs a) {
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOLS));
 }
 
+// ------------------------------------------------------------------------------------------
+// Warp-specialised Grams for one or two right blocks when the left block is one of them (the
+// Grams of every update). One CTA per SM walks a contiguous range of rows in 32-row chunks, and
+// no stage waits for another unless a ring is full:
+//   * warp 4 (one thread) loads the raw FP32 chunk of every block with TMA, four boxes of 32 rows
+//     x 32 features, 128-byte swizzle, into a ring of kWsRaw stages;
+//   * warps 0-3 convert a raw chunk into the tf32 hi/lo K-major tiles of a ring of kWsTile stages
+//     (warp w owns features 32w..32w+31, lane = row; the swizzle keeps both the row reads and the
+//     feature-line writes free of bank conflicts);
+//   * warp 5 (one thread) issues each chunk's MMAs as k_gram_tc does, then commits them to free
+//     the tile stage and, at a segment end, to hand the accumulator over.
+// Accuracy: the tensor cores accumulate a segment of kWsSegRows rows in FP32 in tensor memory
+// (columns [0, 128 NR)); its error grows linearly with the rows it holds. At every segment end
+// warps 0-3 (TMEM lanes 32w..32w+31 are warp w's) add the segment into a running FP32 total kept
+// in columns [128 NR, 256 NR) with round-to-nearest adds, so a CTA's result carries the error of
+// one short segment plus about one rounding per segment. The total is written once per CTA and
+// the partials are reduced by k_gram_tc_reduce1/2. Every wait is bounded: on expiry the CTA
+// records OFSC_ERR_TIMEOUT, every role stops, the TMA copies and MMAs already issued are waited
+// for (bounded), and the tensor memory is freed.
+constexpr int kWsRaw = 2;
+constexpr int kWsTile = 2;
+constexpr int kWsThreads = 192;
+constexpr int kWsBox = 32 * 128;  // one TMA box: 32 rows x 32 FP32 features
+constexpr int64_t kWsSegRows = 512;
+
+template <int NR>
+struct WsShape {
+  static constexpr int RAW = NR * 4 * kWsBox;  // one raw stage: four boxes per block
+  static constexpr int TILE = NR * kTcTile;    // the hi (or lo) tiles of one stage
+  static constexpr size_t bytes() { return (size_t)kWsRaw * RAW + (size_t)kWsTile * 2 * TILE + 1024; }
+};
+
+struct WsArgs {
+  int64_t n;
+  int lslot;
+  int64_t rows_per_cta;  // multiple of 32
+  int64_t seg_rows;      // multiple of 32
+  float* part;           // [ctas][nr][128][128]
+  Ctrl* ctrl;
+  int ignore_done;
+};
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void tma_load_box(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cta.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t* r) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]),
+      "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]),
+      "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+      : "memory");
+}
+
+// Bounded wait that also gives up once another role has aborted; false on either.
+__device__ __forceinline__ bool ws_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  const uint32_t addr = smem_u32(bar);
+  for (long long it = 0; it < kTcSpinLimit; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n"
+        ".reg .pred p;\n"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(ok)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if ((it & 255) == 255 && *abort_flag) return false;
+  }
+  *abort_flag = 1;
+  return false;
+}
+
+template <int NR>
+__global__ void __launch_bounds__(kWsThreads, 1)
+    k_gram_tc_ws(const __grid_constant__ CUtensorMap m0, const __grid_constant__ CUtensorMap m1, WsArgs a) {
+  if (!a.ignore_done && a.ctrl->done) return;
+  using Sh = WsShape<NR>;
+  constexpr uint32_t NCOLS = NR == 1 ? 256 : 512;  // segment accumulator, then the running total
+  constexpr uint32_t TOT = NR * kTcM;               // first column of the total
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ uint64_t raw_full[kWsRaw], raw_empty[kWsRaw], tile_full[kWsTile], tile_empty[kWsTile];
+  __shared__ uint64_t acc_full, acc_empty;
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int abort_flag;
+  unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* raw = base;                      // [kWsRaw][NR][4 boxes]
+  unsigned char* hi = base + kWsRaw * Sh::RAW;    // [kWsTile][NR tiles]
+  unsigned char* lo = hi + kWsTile * Sh::TILE;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  if (warp == 5) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(NCOLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    abort_flag = 0;
+    for (int st = 0; st < kWsRaw; ++st) {
+      mbar_init(&raw_full[st], 1);
+      mbar_init(&raw_empty[st], 4);
+    }
+    for (int tt = 0; tt < kWsTile; ++tt) {
+      mbar_init(&tile_full[tt], 4);
+      mbar_init(&tile_empty[tt], 1);
+    }
+    mbar_init(&acc_full, 1);
+    mbar_init(&acc_empty, 4);
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_slot;
+
+  const int64_t r0 = (int64_t)blockIdx.x * a.rows_per_cta;
+  const int64_t r1 = min(a.n, r0 + a.rows_per_cta);
+  const int64_t nchunks = r1 > r0 ? (r1 - r0 + 31) / 32 : 0;
+  const int64_t cps = a.seg_rows / 32;  // chunks per segment
+  auto seg_last = [&](int64_t c) { return (c + 1) % cps == 0 || c + 1 == nchunks; };
+
+  if (warp == 4) {
+    if (lane == 0) {  // producer
+      int64_t c = 0;
+      for (; c < nchunks; ++c) {
+        const int st = (int)(c % kWsRaw);
+        if (c >= kWsRaw && !ws_wait(&raw_empty[st], (uint32_t)((c / kWsRaw - 1) & 1), &abort_flag)) break;
+        mbar_expect_tx(&raw_full[st], (uint32_t)Sh::RAW);
+        const int y = (int)(r0 + c * 32);
+        unsigned char* dst = raw + st * Sh::RAW;
+#pragma unroll
+        for (int b = 0; b < NR; ++b)
+#pragma unroll
+          for (int fb = 0; fb < 4; ++fb) tma_load_box(dst + (b * 4 + fb) * kWsBox, b ? &m1 : &m0, fb * 32, y, &raw_full[st]);
+      }
+      // the copies already issued must land before the CTA may exit
+      for (int64_t d = c > kWsRaw ? c - kWsRaw : 0; d < c; ++d) mbar_wait(&raw_full[d % kWsRaw], (uint32_t)((d / kWsRaw) & 1));
+    }
+  } else if (warp == 5) {
+    if (lane == 0) {  // MMA issuer
+      int64_t c = 0;
+      for (; c < nchunks; ++c) {
+        const int tt = (int)(c % kWsTile);
+        const int64_t seg = c / cps;
+        const bool first = c % cps == 0;
+        if (!ws_wait(&tile_full[tt], (uint32_t)((c / kWsTile) & 1), &abort_flag)) break;
+        if (first && seg > 0 && !ws_wait(&acc_empty, (uint32_t)((seg - 1) & 1), &abort_flag)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t hs = smem_u32(hi + tt * Sh::TILE), ls = smem_u32(lo + tt * Sh::TILE);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {  // K steps of 8 rows (32 bytes)
+          const uint64_t ahi = sw128_desc(hs + a.lslot * kTcTile + s * 32);
+          const uint64_t alo = sw128_desc(ls + a.lslot * kTcTile + s * 32);
+#pragma unroll
+          for (int h = 0; h < (NR + 1) / 2; ++h) {
+            const int ncol = (2 * h + 1 < NR) ? 256 : 128;
+            const uint32_t id = tf32_idesc(ncol);
+            const uint32_t d = tmem + (uint32_t)(h * 256);
+            const uint64_t bhi = sw128_desc(hs + 2 * h * kTcTile + s * 32);
+            const uint64_t blo = sw128_desc(ls + 2 * h * kTcTile + s * 32);
+            mma_tf32(d, ahi, bhi, id, (!first || s > 0) ? 1u : 0u);
+            mma_tf32(d, ahi, blo, id, 1u);
+            mma_tf32(d, alo, bhi, id, 1u);
+          }
+        }
+        mma_commit(&tile_empty[tt]);
+        if (seg_last(c)) mma_commit(&acc_full);
+      }
+      // the MMAs already issued must finish before the tensor memory is released
+      if (c > 0) mbar_wait(&tile_empty[(c - 1) % kWsTile], (uint32_t)(((c - 1) / kWsTile) & 1));
+    }
+  } else {  // warps 0-3: convert, and drain at segment ends
+    const int fb = warp;
+    const int fi = warp * 32 + lane;  // TMEM lane = feature of the left block
+    int64_t c = 0;
+    for (; c < nchunks; ++c) {
+      const int st = (int)(c % kWsRaw), tt = (int)(c % kWsTile);
+      if (!ws_wait(&raw_full[st], (uint32_t)((c / kWsRaw) & 1), &abort_flag)) break;
+      if (c >= kWsTile && !ws_wait(&tile_empty[tt], (uint32_t)((c / kWsTile - 1) & 1), &abort_flag)) break;
+#pragma unroll
+      for (int b = 0; b < NR; ++b) {
+        const unsigned char* src = raw + st * Sh::RAW + (b * 4 + fb) * kWsBox + lane * 128;
+        unsigned char* dh = hi + tt * Sh::TILE + b * kTcTile;
+        unsigned char* dl = lo + tt * Sh::TILE + b * kTcTile;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const float4 v4 = *(const float4*)(src + ((j ^ (lane & 7)) << 4));
+          const float v[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int f = fb * 32 + 4 * j + q;
+            const uint32_t h = tf32_rna(v[q]);
+            const uint32_t l = tf32_rna(v[q] - __uint_as_float(h));
+            const uint32_t off = tile_off(f, lane);
+            *(uint32_t*)(dh + off) = h;
+            *(uint32_t*)(dl + off) = l;
+          }
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;");  // generic-proxy stores -> tensor-core reads
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&raw_empty[st]);
+        mbar_arrive(&tile_full[tt]);
+      }
+      if (seg_last(c)) {
+        const int64_t seg = c / cps;
+        if (!ws_wait(&acc_full, (uint32_t)(seg & 1), &abort_flag)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t lanes = (uint32_t)(warp * 32) << 16;
+#pragma unroll 1
+        for (uint32_t c0 = 0; c0 < TOT; c0 += 32) {
+          uint32_t d[32], t[32];
+          tmem_ld32(tmem + lanes + c0, d);
+          if (seg > 0) tmem_ld32(tmem + lanes + TOT + c0, t);
+          asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+          for (int q = 0; q < 32; ++q)
+            t[q] = seg > 0 ? __float_as_uint(__uint_as_float(t[q]) + __uint_as_float(d[q])) : d[q];
+          tmem_st32(tmem + lanes + TOT + c0, t);
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acc_empty);
+      }
+    }
+    // the CTA's total into its partial (zero if it had no rows)
+    float* out = a.part + (int64_t)blockIdx.x * NR * kTcM * kTcM;
+    if (nchunks > 0 && !abort_flag) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll 1
+      for (uint32_t c0 = 0; c0 < TOT; c0 += 32) {
+        uint32_t t[32];
+        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + TOT + c0, t);
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+        const int b = (int)(c0 / kTcM), j0 = (int)(c0 % kTcM);
+        float4* dst = (float4*)(out + ((int64_t)b * kTcM + fi) * kTcM + j0);
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          dst[q] = make_float4(__uint_as_float(t[4 * q]), __uint_as_float(t[4 * q + 1]), __uint_as_float(t[4 * q + 2]),
+                               __uint_as_float(t[4 * q + 3]));
+      }
+    } else {
+      for (int j = 0; j < NR * kTcM; j += 4) {
+        const int b = j / kTcM, jj = j % kTcM;
+        *(float4*)(out + ((int64_t)b * kTcM + fi) * kTcM + jj) = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (abort_flag && tid == 0) {
+    a.ctrl->status = OFSC_ERR_TIMEOUT;
+    a.ctrl->done = 1;
+  }
+  if (warp == 5) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOLS));
+}
+
 // The per-CTA FP32 partials are summed in FP64 in two fixed-order levels: level 1 adds groups of
 // kRedGroup consecutive CTAs (all groups and elements in parallel), level 2 adds the groups in
 // order. The result does not depend on scheduling.
@@ -313,10 +602,25 @@ static size_t part_floats_bytes(int64_t ctas, int nr) {
   return (b + 255) / 256 * 256;
 }
 
+// Row ranges of the warp-specialised kernel: one CTA per SM, each split into segments of
+// kWsSegRows rows; returns the CTAs and sets the rows per CTA and the segments per CTA.
+static int64_t ws_layout(int64_t n, int64_t* rpc) {
+  int64_t r = (n + kNumSMs - 1) / kNumSMs;
+  r = std::max<int64_t>(32, (r + 31) / 32 * 32);
+  *rpc = r;
+  return (n + r - 1) / r;
+}
+
+static size_t parts_bytes(int64_t parts, int nr) {
+  const int64_t groups = (std::max<int64_t>(parts, 1) + kRedGroup - 1) / kRedGroup;
+  return part_floats_bytes(parts, nr) + (size_t)groups * nr * kTcM * kTcM * sizeof(double);
+}
+
 size_t gram_tc_part_bytes(int64_t n, int nr, int64_t rows_per_cta) {
   const int64_t ctas = (n + rows_per_cta - 1) / rows_per_cta;
-  const int64_t groups = (std::max<int64_t>(ctas, 1) + kRedGroup - 1) / kRedGroup;
-  return part_floats_bytes(ctas, nr) + (size_t)groups * nr * kTcM * kTcM * sizeof(double);
+  int64_t rpc;
+  const int64_t ws_ctas = ws_layout(n, &rpc);
+  return std::max(parts_bytes(ctas, nr), parts_bytes(ws_ctas, nr));
 }
 
 // Launches the partial Grams and their FP64 reduction into gram[slot][kp][kp].
@@ -324,12 +628,41 @@ cudaError_t gram_tc_launch(GramTcArgs a, const int* slot, int kp, double* gram, 
   return gram_tc_launch_ld(a, slot, kp, kp, (int64_t)kp * kp, gram, s);
 }
 
+template <int NR>
+cudaError_t launch_ws(const CUtensorMap& m0, const CUtensorMap& m1, const WsArgs& w, int grid, cudaStream_t s) {
+  const size_t smem = WsShape<NR>::bytes();
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_gram_tc_ws<NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_gram_tc_ws<NR><<<grid, kWsThreads, smem, s>>>(m0, m1, w);
+  return cudaGetLastError();
+}
+
 cudaError_t gram_tc_launch_ld(GramTcArgs a, const int* slot, int kout, int ld_out, int64_t kk_stride,
                               double* gram, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
-  const int grid = (int)((a.n + a.rows_per_cta - 1) / a.rows_per_cta);
+  int grid = (int)((a.n + a.rows_per_cta - 1) / a.rows_per_cta);
   const bool sep = a.lslot < 0;
-  cudaError_t e;
+  cudaError_t e = cudaSuccess;
+  if (a.use_ws && !sep && a.nr <= 2) {
+    WsArgs w{};
+    const int64_t ctas = ws_layout(a.n, &w.rows_per_cta);
+    w.n = a.n;
+    w.lslot = a.lslot;
+    w.seg_rows = kWsSegRows;
+    w.part = a.part;
+    w.ctrl = a.ctrl;
+    w.ignore_done = a.ignore_done;
+    CUtensorMap m0, m1;
+    if (tma_encode_f32_sw128(a.R[0], a.n, a.k, a.ld, 32, 32, &m0) != OFSC_OK) return cudaErrorInvalidValue;
+    if (a.nr > 1 && tma_encode_f32_sw128(a.R[1], a.n, a.k, a.ld, 32, 32, &m1) != OFSC_OK) return cudaErrorInvalidValue;
+    if (a.nr == 1) m1 = m0;
+    e = a.nr == 1 ? launch_ws<1>(m0, m1, w, (int)ctas, s) : launch_ws<2>(m0, m1, w, (int)ctas, s);
+    grid = (int)ctas;  // partials to reduce
+  } else {
   switch (a.nr * 2 + (sep ? 1 : 0)) {
     case 2: e = launch_t<1, false>(a, grid, s); break;
     case 3: e = launch_t<1, true>(a, grid, s); break;
@@ -339,6 +672,7 @@ cudaError_t gram_tc_launch_ld(GramTcArgs a, const int* slot, int kout, int ld_ou
     case 7: e = launch_t<3, true>(a, grid, s); break;
     case 8: e = launch_t<4, false>(a, grid, s); break;
     default: e = launch_t<4, true>(a, grid, s); break;
+  }
   }
   if (e != cudaSuccess) return e;
   const int total_p = a.nr * kTcM * kTcM;
@@ -381,6 +715,7 @@ extern "C" ofsc_status ofsc_gram(int64_t n, int32_t k, int32_t ld, const float* 
   if (rows_per_block < 0 || (rows_per_block % kTcRows) != 0)
     return fail(OFSC_ERR_INVALID_ARG, "ofsc_gram: rows_per_block must be a non-negative multiple of %d", kTcRows);
   a.rows_per_cta = rows_per_block > 0 ? rows_per_block : gram_tc_rows_per_cta(n, nr);
+  a.use_ws = rows_per_block == 0;
   cudaStream_t s = (cudaStream_t)stream_;
   if (n == 0) {
     OFSC_CUDA(cudaMemsetAsync(out, 0, (size_t)nr * k * k * sizeof(double), s));

@@ -523,7 +523,13 @@ struct RowArgs {
 // k x k block (triu-masked for TriOFM) stays resident in shared memory. All global loads of a
 // batch are issued before any arithmetic, so each warp keeps up to 5 * KPB 16-byte loads in
 // flight. Column sums (for beta and ||G||) go to per-block partials in a fixed order.
-constexpr int kKPB = 8;       // rows per slot per batch
+#ifndef OFSC_DIR_KPB
+#define OFSC_DIR_KPB 8
+#endif
+#ifndef OFSC_DIR_MINB
+#define OFSC_DIR_MINB 1
+#endif
+constexpr int kKPB = OFSC_DIR_KPB;  // rows per slot per batch
 constexpr int kColSums = 6;  // column sums of the direction pass
 
 template <int KPMAX, bool F2>
@@ -542,7 +548,7 @@ struct DirShape {
 };
 
 template <int METHOD, int KPMAX>
-__global__ void __launch_bounds__(kRowThreads, 1) k_direction(RowArgs a) {
+__global__ void __launch_bounds__(kRowThreads, OFSC_DIR_MINB) k_direction(RowArgs a) {
   if (!a.ignore_done && a.ctrl->done) return;
   constexpr bool F2 = METHOD >= M_OFM_F2;
   constexpr bool TRI = METHOD == M_TRI_F1 || METHOD == M_TRI_F2;
@@ -1614,6 +1620,7 @@ struct Runner {
       }
       t.rows_per_cta = gram_tc_rows_per_cta(ws.n, nr);
       t.part = ws.part_tc;
+      t.use_ws = 1;
       t.ctrl = ws.ctrl;
       t.ignore_done = ignore_done;
       if (timed) prof.begin(OFSC_PHASE_GRAM);

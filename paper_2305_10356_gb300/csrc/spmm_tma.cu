@@ -276,27 +276,47 @@ bool spmm_tma_supported(int kp) { return kp == 64 || kp == 128; }
 
 int spmm_tma_groups_per_block() { return kTmaWarps; }
 
+// cuTensorMapEncodeTiled from the driver, looked up once.
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  std::lock_guard<std::mutex> lock(g_encode_mu);
+  if (!g_encode) {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e == cudaSuccess && q == cudaDriverEntryPointSuccess && fn) g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  }
+  return g_encode;
+}
+
 // Tensor map over the n x kp block `vh` (FP32 or BF16), one row per box: the gather4 layout.
 ofsc_status spmm_tma_encode(const void* vh, int64_t n, int kp, bool bf16, CUtensorMap* map) {
-  {
-    std::lock_guard<std::mutex> lock(g_encode_mu);
-    if (!g_encode) {
-      cudaDriverEntryPointQueryResult q;
-      void* fn = nullptr;
-      cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
-      if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
-        return fail(OFSC_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
-      g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
-    }
-  }
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  if (!enc) return fail(OFSC_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
   const cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)(n > 0 ? n : 1)};
   const cuuint64_t strides[1] = {(cuuint64_t)kp * (bf16 ? 2 : 4)};
   const cuuint32_t box[2] = {(cuuint32_t)kp, 1};
   const cuuint32_t estr[2] = {1, 1};
-  CUresult r = g_encode(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
-                        const_cast<void*>(vh), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r = enc(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                   const_cast<void*>(vh), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(OFSC_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return OFSC_OK;
+}
+
+ofsc_status tma_encode_f32_sw128(const float* base, int64_t rows, int cols, int ld, int box_cols, int box_rows,
+                                 CUtensorMap* map) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  if (!enc) return fail(OFSC_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+  if (box_cols * 4 > 128 || ((uintptr_t)base & 15) || (ld & 3))
+    return fail(OFSC_ERR_INVALID_ARG, "tensor map: box wider than the 128-byte swizzle or misaligned block");
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)(rows > 0 ? rows : 1)};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+  const cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(OFSC_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
   return OFSC_OK;
 }

@@ -265,17 +265,22 @@ def test_kmeans_matches_oracle(cuda_lib):
     assert torch.equal(lab, lab2)  # deterministic given the seed
 
 
-@pytest.mark.parametrize("n,k,ld,nr,same", [(100, 128, 128, 2, True), (10_001, 128, 128, 4, True),
-                                            (3_333, 100, 104, 3, False), (777, 20, 24, 1, False)])
-def test_tensor_core_gram_matches_fp64(cuda_lib, n, k, ld, nr, same):
+@pytest.mark.parametrize("n,k,ld,nr,lslot", [
+    (100, 128, 128, 2, 1),        # warp-specialised TMA kernel: one CTA, ragged 32-row chunk
+    (300_001, 128, 128, 2, 0),    # ... several accumulator segments per CTA
+    (4_999, 100, 104, 1, 0),      # ... one block, features 100..127 zero-filled
+    (10_001, 128, 128, 4, 1),     # per-CTA kernel: four right blocks
+    (3_333, 100, 104, 3, None),   # ... left block separate from the right blocks
+    (777, 20, 24, 1, None)])
+def test_tensor_core_gram_matches_fp64(cuda_lib, n, k, ld, nr, lslot):
     """ofsc_gram (tcgen05, 3-term TF32, FP32 tensor-memory accumulation) against FP64 numpy."""
     torch = cuda_lib
     rng = np.random.default_rng(n + k)
     L = (rng.standard_normal((n, ld)) / np.sqrt(n)).astype(np.float32)
-    Rs = [L if (same and b == 1) else (rng.standard_normal((n, ld)) / np.sqrt(n)).astype(np.float32)
+    Rs = [L if b == lslot else (rng.standard_normal((n, ld)) / np.sqrt(n)).astype(np.float32)
           for b in range(nr)]
     Ld = torch.from_numpy(L).cuda()
-    Rd = [Ld if (same and b == 1) else torch.from_numpy(R).cuda() for b, R in enumerate(Rs)]
+    Rd = [Ld if b == lslot else torch.from_numpy(R).cuda() for b, R in enumerate(Rs)]
     out = torch.zeros((nr, k, k), dtype=torch.float64, device="cuda")
     ofsc.ofsc_gram(Ld, Rd, out, k=k)
     got = out.cpu().numpy()

@@ -36,6 +36,11 @@ __device__ __forceinline__ uint32_t tf32_rna(float x) {
   return r;
 }
 
+// x rounded to tf32 (10 stored mantissa bits, nearest with ties away from zero) by integer
+// arithmetic on its bits; x - tf32_round(x) is exact in FP32. The tensor cores ignore the low 13
+// bits of a tf32 operand, so the low part keeps 11 significant bits.
+__device__ __forceinline__ uint32_t tf32_round(float x) { return (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u; }
+
 // Byte offset of element (feature f, chunk row l) in a K-major SWIZZLE_128B tile: 8-feature
 // groups of 1024 bytes, one 128-byte line per feature, 16-byte chunks XOR-permuted by f % 8.
 __device__ __forceinline__ uint32_t tile_off(int f, int l) {
@@ -249,8 +254,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(GramTcArgs a) {
 //   * warp 4 (one thread) loads the raw FP32 chunk of every block with TMA, four boxes of 32 rows
 //     x 32 features, 128-byte swizzle, into a ring of kWsRaw stages;
 //   * warps 0-3 convert a raw chunk into the tf32 hi/lo K-major tiles of a ring of kWsTile stages
-//     (warp w owns features 32w..32w+31, lane = row; the swizzle keeps both the row reads and the
-//     feature-line writes free of bank conflicts);
+//     (warp w owns features 32w..32w+31, lane = feature; the swizzle keeps both the row reads and
+//     the 16-byte feature-line writes free of bank conflicts);
 //   * warp 5 (one thread) issues each chunk's MMAs as k_gram_tc does, then commits them to free
 //     the tile stage and, at a segment end, to hand the accumulator over.
 // Accuracy: the tensor cores accumulate a segment of kWsSegRows rows in FP32 in tensor memory
@@ -261,11 +266,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(GramTcArgs a) {
 // the partials are reduced by k_gram_tc_reduce1/2. Every wait is bounded: on expiry the CTA
 // records OFSC_ERR_TIMEOUT, every role stops, the TMA copies and MMAs already issued are waited
 // for (bounded), and the tensor memory is freed.
-constexpr int kWsRaw = 2;
+#ifndef OFSC_WS_RAW
+#define OFSC_WS_RAW 3
+#endif
+#ifndef OFSC_WS_SEG
+#define OFSC_WS_SEG 512
+#endif
+constexpr int kWsRaw = OFSC_WS_RAW;
 constexpr int kWsTile = 2;
 constexpr int kWsThreads = 192;
 constexpr int kWsBox = 32 * 128;  // one TMA box: 32 rows x 32 FP32 features
-constexpr int64_t kWsSegRows = 512;
+constexpr int64_t kWsSegRows = OFSC_WS_SEG;
 
 template <int NR>
 struct WsShape {
@@ -451,24 +462,28 @@ __global__ void __launch_bounds__(kWsThreads, 1)
       const int st = (int)(c % kWsRaw), tt = (int)(c % kWsTile);
       if (!ws_wait(&raw_full[st], (uint32_t)((c / kWsRaw) & 1), &abort_flag)) break;
       if (c >= kWsTile && !ws_wait(&tile_empty[tt], (uint32_t)((c / kWsTile - 1) & 1), &abort_flag)) break;
+      // lane = feature fb*32 + lane; four consecutive rows per step: four 4-byte reads from the
+      // swizzled row lines (one line per read, all lanes distinct words) and one 16-byte store per
+      // tile into the feature's K-major line (each group of 8 lanes hits 8 distinct 16-byte banks)
 #pragma unroll
       for (int b = 0; b < NR; ++b) {
-        const unsigned char* src = raw + st * Sh::RAW + (b * 4 + fb) * kWsBox + lane * 128;
+        const unsigned char* box = raw + st * Sh::RAW + (b * 4 + fb) * kWsBox + (lane & 3) * 4;
         unsigned char* dh = hi + tt * Sh::TILE + b * kTcTile;
         unsigned char* dl = lo + tt * Sh::TILE + b * kTcTile;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const float4 v4 = *(const float4*)(src + ((j ^ (lane & 7)) << 4));
-          const float v[4] = {v4.x, v4.y, v4.z, v4.w};
+        for (int rg = 0; rg < 8; ++rg) {
+          uint32_t h[4];
+          float l[4];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int f = fb * 32 + 4 * j + q;
-            const uint32_t h = tf32_rna(v[q]);
-            const uint32_t l = tf32_rna(v[q] - __uint_as_float(h));
-            const uint32_t off = tile_off(f, lane);
-            *(uint32_t*)(dh + off) = h;
-            *(uint32_t*)(dl + off) = l;
+          for (int i = 0; i < 4; ++i) {
+            const int r = 4 * rg + i;
+            const float x = *(const float*)(box + r * 128 + ((((lane >> 2) ^ r) & 7) << 4));
+            h[i] = tf32_round(x);
+            l[i] = x - __uint_as_float(h[i]);  // exact
           }
+          const uint32_t off = tile_off(fi, 4 * rg);
+          *(uint4*)(dh + off) = make_uint4(h[0], h[1], h[2], h[3]);
+          *(float4*)(dl + off) = make_float4(l[0], l[1], l[2], l[3]);
         }
       }
       asm volatile("fence.proxy.async.shared::cta;");  // generic-proxy stores -> tensor-core reads

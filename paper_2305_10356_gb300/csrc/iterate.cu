@@ -725,6 +725,20 @@ __global__ void __launch_bounds__(kRowThreads, OFSC_DIR_MINB) k_direction(RowArg
 // beta and the stop test (one block)
 // ------------------------------------------------------------------------------------------
 
+// Folds nb rows of width values into gridDim.x rows: row r sums the rows [r nb / R, (r + 1) nb / R)
+// in order (a fixed shape, so the sums do not depend on scheduling).
+__global__ void k_fold_rows(const double* __restrict__ part, int nb, int width, double* __restrict__ out,
+                            const Ctrl* ctrl, int ignore_done) {
+  if (!ignore_done && ctrl->done) return;
+  const int r = blockIdx.x, R = gridDim.x;
+  const int b0 = (int)((int64_t)r * nb / R), b1 = (int)((int64_t)(r + 1) * nb / R);
+  for (int t = threadIdx.x; t < width; t += blockDim.x) {
+    double sum = 0.0;
+    for (int b = b0; b < b1; ++b) sum += part[(int64_t)b * width + t];
+    out[(int64_t)r * width + t] = sum;
+  }
+}
+
 __global__ void k_beta(const double* __restrict__ colpart, int nblk, int kp, float* beta,
                        double* beta64, double* dE, Ctrl* ctrl, int first, int eval) {
   if (!eval && ctrl->done) return;
@@ -1571,7 +1585,7 @@ ofsc_status ensure_workspace(ofsc_graph* g, int kp) {
       {(void**)&ws.beta, kp * sizeof(float)},
       {(void**)&ws.alpha64, kp * sizeof(double)},
       {(void**)&ws.beta64, kp * sizeof(double)},
-      {(void**)&ws.colpart, (size_t)kMaxRowBlocks * kColSums * kp * sizeof(double)},
+      {(void**)&ws.colpart, (size_t)(kMaxRowBlocks + kDotsRows) * kColSums * kp * sizeof(double)},
       {(void**)&ws.dE, (size_t)kp * sizeof(double)},
       {(void**)&ws.ctrl, sizeof(Ctrl)},
   };
@@ -1705,6 +1719,21 @@ struct Runner {
     cudaError_t e = launch_rowpass(dir_method, r, s, nblk);
     prof.end();
     return e;
+  }
+
+  // beta, the stop test and the objective's diagonal term from the direction pass's column sums,
+  // folded to kDotsRows rows first (eval: only the gradient norm)
+  void beta(int nblk, int first, int eval) {
+    const double* cp = ws.colpart;
+    if (nblk > kDotsRows) {
+      double* folded = ws.colpart + (size_t)kMaxRowBlocks * kColSums * ws.kp;
+      k_fold_rows<<<kDotsRows, 256, 0, s>>>(ws.colpart, nblk, kColSums * ws.kp, folded, ws.ctrl, eval);
+      ++g_launches;
+      cp = folded;
+      nblk = kDotsRows;
+    }
+    k_beta<<<1, 256, 0, s>>>(cp, nblk, ws.kp, ws.beta, ws.beta64, eval ? nullptr : ws.dE, ws.ctrl, first, eval);
+    ++g_launches;
   }
 
   cudaError_t direction_and_linesearch(int first, const ofsc_opts& o, int k, double alpha0) {
@@ -1919,8 +1948,7 @@ extern "C" ofsc_status ofsc_iterate(ofsc_graph* g, int32_t method, int32_t k, fl
       OFSC_CUDA(run.rowpass(method, t > 0 ? 1 : 0, t == 0 ? 1 : 0, 0, &nblk));
     }
     prof.begin(OFSC_PHASE_BETA);
-    k_beta<<<1, 256, 0, s>>>(ws.colpart, nblk, kp, ws.beta, ws.beta64, ws.dE, ws.ctrl, t == 0 ? 1 : 0, 0);
-    ++g_launches;
+    run.beta(nblk, t == 0 ? 1 : 0, 0);
     prof.end();
     OFSC_LAUNCH_CHECK("k_beta");
     if (t == maxit) break;
@@ -1941,8 +1969,7 @@ extern "C" ofsc_status ofsc_iterate(ofsc_graph* g, int32_t method, int32_t k, fl
     OFSC_CUDA(run.refresh(objective, 1));
     int nblk = 0;
     OFSC_CUDA(run.rowpass(method, 0, 1, 1, &nblk));
-    k_beta<<<1, 256, 0, s>>>(ws.colpart, nblk, kp, ws.beta, ws.beta64, nullptr, ws.ctrl, 0, 1);
-    ++g_launches;
+    run.beta(nblk, 0, 1);
     OFSC_LAUNCH_CHECK("k_beta(eval)");
   }
   k_pad_out<<<grid_elems(g->n * k), 256, 0, s>>>(g->n, k, kp, ws.X, X);

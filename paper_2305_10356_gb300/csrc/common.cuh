@@ -189,6 +189,27 @@ struct GramTcArgs {
   int ignore_done;
   int use_ws;            // allow the warp-specialised TMA kernel (L one of R, nr <= 2; own segments)
 };
+// Arguments of the direction pass (k_direction in csrc/iterate.cu, k_direction_tc in
+// csrc/direction_tc.cu).
+struct RowArgs {
+  int64_t n;
+  int kp;
+  float* X;
+  float* Y;
+  const float* V;
+  const float* W;
+  float* G;
+  const float* Rn;
+  const float* Bn;
+  const float* alpha;
+  double* colpart;  // [gridDim.x][6][kp]: sums of G^2, (G - G_prev) G, G_prev^2, G AX, V_prev AX, V_prev G
+  Ctrl* ctrl;
+  int update;
+  int need_vy;      // read V_{t-1} for the V_prev AX sums even without an update
+  int eval;         // no previous G (objective/gradient evaluation and the final report)
+  int ignore_done;
+};
+
 // Arguments of the TMA-gather sparse product (csrc/spmm_tma.cu): out = -base - D^-1/2 S Vh.
 struct TmaSpmmArgs {
   int64_t n;
@@ -212,6 +233,11 @@ ofsc_status spmm_tma_encode(const void* vh, int64_t n, int kp, bool bf16, CUtens
 ofsc_status tma_encode_f32_sw128(const float* base, int64_t rows, int cols, int ld, int box_cols, int box_rows,
                                  CUtensorMap* map);
 cudaError_t spmm_tma_launch(const CUtensorMap& map, const TmaSpmmArgs& a, bool bf16, bool weighted, cudaStream_t s);
+
+// Direction pass of OFM-f1 / TriOFM-f1 at padded k = 128 with the kp x kp product on the tensor
+// cores (csrc/direction_tc.cu); *nblk receives the rows of column-sum partials written.
+bool direction_tc_supported(int method, int kp);
+cudaError_t direction_tc_launch(int method, const RowArgs& a, cudaStream_t s, int* nblk);
 
 int64_t gram_tc_rows_per_cta(int64_t n, int nr);
 size_t gram_tc_part_bytes(int64_t n, int nr, int64_t rows_per_cta);

@@ -498,24 +498,6 @@ __global__ void __launch_bounds__(256) k_vpass(int64_t n, int kp, const float* _
 // Direction pass: optional update, G = g(X), column sums for beta
 // ------------------------------------------------------------------------------------------
 
-struct RowArgs {
-  int64_t n;
-  int kp;
-  float* X;
-  float* Y;
-  const float* V;
-  const float* W;
-  float* G;
-  const float* Rn;
-  const float* Bn;
-  const float* alpha;
-  double* colpart;  // [gridDim.x][6][kp]: sums of G^2, (G - G_prev) G, G_prev^2, G AX, V_prev AX, V_prev G
-  Ctrl* ctrl;
-  int update;
-  int need_vy;      // read V_{t-1} for the V_prev AX sums even without an update
-  int eval;         // no previous G (objective/gradient evaluation and the final report)
-  int ignore_done;
-};
 
 // Warp-batched direction pass. A warp owns S = 32 / (KPMAX / 4) row slots of KPB rows each;
 // lane q of a slot holds columns [4q, 4q + 4) of its rows in registers. The rows are staged in a
@@ -1716,7 +1698,13 @@ struct Runner {
     r.eval = eval;
     r.ignore_done = ignore_done;
     prof.begin(OFSC_PHASE_DIRECTION);
-    cudaError_t e = launch_rowpass(dir_method, r, s, nblk);
+    cudaError_t e;
+    if (tc && direction_tc_supported(dir_method, ws.kp)) {
+      e = direction_tc_launch(dir_method, r, s, nblk);
+      ++g_launches;
+    } else {
+      e = launch_rowpass(dir_method, r, s, nblk);
+    }
     prof.end();
     return e;
   }

@@ -339,15 +339,32 @@ def test_direction_product_all_lane_widths_weighted(k):
     np.testing.assert_allclose(tr[:4, 3:3 + k], np.array(ref.alphas[:4]), rtol=1e-4, atol=1e-7)
 
 
-@pytest.mark.parametrize("gather", [0, 1])
-def test_iterations_are_bitwise_repeatable(gather):
+@pytest.mark.parametrize("gather,k", [(0, 64), (1, 64), (0, 128)])
+def test_iterations_are_bitwise_repeatable(gather, k):
     """Every reduction has a fixed shape (per-block partials summed in block order, no atomics), so
-    two runs from the same X0 give the same bits."""
+    two runs from the same X0 give the same bits (k = 128: tensor-core direction pass and Grams)."""
     e = synth.sbm(4000, 8, 24.0, 6.0, seed=71, gamma=2.4, ratio_kind="count")
     g = gpu_graph(e)
-    x0 = synth.initial_block(e.n, 64, 72)
+    x0 = synth.initial_block(e.n, k, 72)
     X1, r1, t1 = run_iterate(g, o.OFM_F1, x0, 0.0, 12, trace_cap=13, gather=gather)
     X2, r2, t2 = run_iterate(g, o.OFM_F1, x0, 0.0, 12, trace_cap=13, gather=gather)
     assert np.array_equal(X1, X2)
     assert np.array_equal(t1, t2)
     assert r1.rel_dir_norm == r2.rel_dir_norm
+
+
+@pytest.mark.parametrize("method", [o.OFM_F1, o.TRI_F1])
+def test_tensor_core_direction_pass(method):
+    """k = 128: the direction pass with X_new R on the tensor cores (3-term tf32) against the CUDA-core
+    pass and against the oracle, on 3001 rows (a ragged last 128-row tile)."""
+    e = synth.sbm(3001, 9, 22.0, 6.0, seed=81, gamma=2.4, ratio_kind="count")
+    og = o.build_graph(e.n, e.src, e.dst)
+    g = gpu_graph(e)
+    x0 = synth.initial_block(e.n, 128, 82)
+    Xt, rt, tt = run_iterate(g, method, x0, 0.0, 6, trace_cap=7, gram_engine=ofsc.GRAM_TC)
+    Xs, rs, ts = run_iterate(g, method, x0, 0.0, 6, trace_cap=7, gram_engine=ofsc.GRAM_SIMT)
+    assert np.linalg.norm(Xt - Xs) <= 1e-5 * np.linalg.norm(Xs)
+    np.testing.assert_allclose(tt[:6, 3:3 + 128], ts[:6, 3:3 + 128], rtol=1e-4, atol=1e-7)
+    ref = o.iterate(og, method, x0, 0.0, 6)
+    assert np.linalg.norm(Xt - ref.X) <= 1e-4 * np.linalg.norm(ref.X)
+    assert abs(rt.rel_dir_norm - ref.rel_norms[-1]) <= 1e-4 * ref.rel_norms[-1] + 1e-7

@@ -52,27 +52,28 @@ inline int spmm_lanes_index(int lanes) {
 }
 // Lane groups of the sparse product: about 512 nonzeros each, between 1 and 4 blocks per SM.
 // Warps of the direction product (one row at a time per warp): about kRowNnz nonzeros each, at
-// least one full wave of 32 warps per SM and at most kRowMaxBlocks blocks of kRowWarpsPerBlock
-// warps. A warp takes a hub row whole, so a warp's share must stay well above the largest degree
-// or that warp becomes the tail: on the 2M-node, k = 128 graph (max degree 5828) two waves of
-// about 6200 nonzeros per warp measured fastest. The macros exist for tuning builds.
+// least one full wave of 32 warps per SM and at most kRowMaxWarps, in blocks of
+// kRowWarpsPerBlock warps. Blocks of one warp retire as soon as their warp is done, so the
+// hardware balances the load warp by warp (blocks of eight warps, held by their slowest warp,
+// measured 22-29% slower on the 2M-node, k = 128 graph). A warp takes a hub row whole, so a warp's
+// share must stay well above the largest degree. The macros exist for tuning builds.
 #ifndef OFSC_ROW_WPB
-#define OFSC_ROW_WPB 8
+#define OFSC_ROW_WPB 1
 #endif
 #ifndef OFSC_ROW_NNZ
 #define OFSC_ROW_NNZ 256
 #endif
-#ifndef OFSC_ROW_MAX_BLOCKS_PER_SM
-#define OFSC_ROW_MAX_BLOCKS_PER_SM 8
+#ifndef OFSC_ROW_MAX_WARPS_PER_SM
+#define OFSC_ROW_MAX_WARPS_PER_SM 32
 #endif
 constexpr int kRowPart = 5;
 constexpr int kRowWarpsPerBlock = OFSC_ROW_WPB;
 constexpr int kRowNnz = OFSC_ROW_NNZ;
-constexpr int kRowMaxBlocks = OFSC_ROW_MAX_BLOCKS_PER_SM * kNumSMs;
+constexpr int kRowMaxWarps = OFSC_ROW_MAX_WARPS_PER_SM * kNumSMs;
 inline int row_warps(int64_t nnz) {
   int64_t w = nnz / kRowNnz;
   if (w < 32 * kNumSMs) w = 32 * kNumSMs;
-  if (w > (int64_t)kRowMaxBlocks * kRowWarpsPerBlock) w = (int64_t)kRowMaxBlocks * kRowWarpsPerBlock;
+  if (w > kRowMaxWarps) w = kRowMaxWarps;
   return (int)ceil_div(w, kRowWarpsPerBlock) * kRowWarpsPerBlock;
 }
 // Per-block partial sums of the sparse product's dots are folded to at most this many rows, in a

@@ -125,14 +125,14 @@ struct SpmmArgs {
 #ifndef OFSC_ROW_U32
 #define OFSC_ROW_U32 6  // gathers in flight per lane when a warp covers a row of 128 columns
 #endif
-#ifndef OFSC_ROW_MINB
-#define OFSC_ROW_MINB 5  // resident blocks per SM the registers must allow (40 warps)
+#ifndef OFSC_ROW_WARPS_F32
+#define OFSC_ROW_WARPS_F32 32  // resident warps per SM the registers must allow (FP32 slots)
 #endif
 #ifndef OFSC_ROW_U16_BF16
-#define OFSC_ROW_U16_BF16 4  // the same for 16-byte BF16 slots (128 columns)
+#define OFSC_ROW_U16_BF16 4  // gathers in flight per lane for 16-byte BF16 slots (128 columns)
 #endif
-#ifndef OFSC_ROW_MINB_BF16
-#define OFSC_ROW_MINB_BF16 (32 / kRowWarpsPerBlock)  // the same with 16-byte BF16 slots
+#ifndef OFSC_ROW_WARPS_BF16
+#define OFSC_ROW_WARPS_BF16 32  // resident warps per SM the registers must allow (BF16 slots)
 #endif
 
 // Four consecutive values of row `row` from column c, as FP32 (FP32 or BF16 storage).
@@ -228,7 +228,8 @@ __global__ void __launch_bounds__(256, 2) k_spmm(SpmmArgs a) {
 // are loaded with the gathers of its last step (staging them through shared memory with cp.async
 // measured 12% slower). Each lane sums its slots in nonzero order; the NPI partial sums of a row
 // are combined by an xor-shuffle butterfly, which leaves the same bits in every lane (for LPN = 32
-// the sum is in plain nonzero order). The per-block partials are folded by k_dots_fold.
+// the sum is in plain nonzero order). Each warp writes its own row of partials (no block-wide
+// barrier, so a block is never held by its slowest warp's reduction); k_dots_fold folds them.
 // One gathered slot of VPL consecutive values of a row of Vh, kept raw (FP32: float4; BF16: 8
 // values in a uint4) until it is accumulated, so a slot in flight costs four registers.
 template <int VPL, bool BF16>
@@ -289,7 +290,8 @@ __host__ __device__ constexpr int dir_slots() {
 }
 
 template <int LPN, int VPL, bool WEIGHTED, bool BF16, bool DOTS>
-__global__ void __launch_bounds__(32 * kRowWarpsPerBlock, VPL == 4 ? OFSC_ROW_MINB : OFSC_ROW_MINB_BF16)
+__global__ void __launch_bounds__(32 * kRowWarpsPerBlock,
+                                  (VPL == 4 ? OFSC_ROW_WARPS_F32 : OFSC_ROW_WARPS_BF16) / kRowWarpsPerBlock)
     k_spmm_dir(SpmmArgs a) {
   if (!a.ignore_done && a.ctrl->done) return;
   using S = Slot<VPL, BF16>;
@@ -395,13 +397,9 @@ __global__ void __launch_bounds__(32 * kRowWarpsPerBlock, VPL == 4 ? OFSC_ROW_MI
       }
     }
   }
-  if (DOTS) {  // per-block partials in a fixed order: warps, then columns
-    __syncthreads();
-    for (int j = threadIdx.x; j < a.kp; j += blockDim.x) {
-      double sum = 0.0;
-      for (int w = 0; w < WPB; ++w) sum += (double)dred[(size_t)w * W + j];
-      a.dots[(int64_t)blockIdx.x * a.kp + j] = sum;
-    }
+  if (DOTS && gw < a.groups) {  // one row of partials per warp: no block-wide barrier
+    __syncwarp();
+    for (int j = lane; j < a.kp; j += 32) a.dots[(int64_t)gw * a.kp + j] = (double)rr[j];
   }
 }
 
@@ -1429,7 +1427,8 @@ int dir_lanes(int kp, int vpl) {
   return l;
 }
 
-// The direction product on the warp-per-row partition; returns the blocks (rows of dots partials).
+// The direction product on the warp-per-row partition; returns the rows of dots partials (one per
+// warp).
 int launch_spmm_dir(const SpmmArgs& a, bool weighted, bool bf16, cudaStream_t s) {
   ++g_launches;
   if (bf16) {
@@ -1448,7 +1447,7 @@ int launch_spmm_dir(const SpmmArgs& a, bool weighted, bool bf16, cudaStream_t s)
       default: launch_dir_l<32, 4, false>(a, weighted, s); break;
     }
   }
-  return a.groups / kRowWarpsPerBlock;
+  return a.groups;
 }
 
 int kpmax_for(int kp) { return kp <= 16 ? 16 : kp <= 32 ? 32 : kp <= 64 ? 64 : 128; }
@@ -1559,7 +1558,7 @@ ofsc_status ensure_workspace(ofsc_graph* g, int kp) {
       {(void**)&ws.Bn, kk * sizeof(float)},
       {(void**)&ws.R64, kk * sizeof(double)},
       {(void**)&ws.B64, kk * sizeof(double)},
-      {(void**)&ws.dots, (size_t)(kRowMaxBlocks + kVpassMaxBlocks + 2 * kDotsRows) * kp * sizeof(double)},
+      {(void**)&ws.dots, (size_t)((kRowMaxWarps + kRowWarpsPerBlock) + kVpassMaxBlocks + 2 * kDotsRows) * kp * sizeof(double)},
       {(void**)&ws.part_tc, kp > 64 ? std::max(gram_tc_part_bytes(n, 2, gram_tc_rows_per_cta(n, 2)),
                                                gram_tc_part_bytes(n, 4, gram_tc_rows_per_cta(n, 4)))
                                     : (size_t)16},
@@ -1729,7 +1728,7 @@ struct Runner {
     // Partials of diag(V^T AV) (sparse product) and diag(V^T G) (V pass) in ws.dots, then their
     // fold into kDotsRows rows of [2][kp] for the solve.
     double* dots_w = ws.dots;
-    double* dots_g = ws.dots + (size_t)kRowMaxBlocks * ws.kp;
+    double* dots_g = ws.dots + (size_t)(kRowMaxWarps + kRowWarpsPerBlock) * ws.kp;
     double* folded = dots_g + (size_t)kVpassMaxBlocks * ws.kp;
     // V_t = -G_t + V_{t-1} diag(beta) and Vh = D^-1/2 V_t for the gather
     prof.begin(OFSC_PHASE_OTHER);

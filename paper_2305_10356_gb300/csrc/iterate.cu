@@ -135,19 +135,6 @@ struct SpmmArgs {
 #define OFSC_ROW_WARPS_BF16 32  // resident warps per SM the registers must allow (BF16 slots)
 #endif
 
-// Four consecutive values of row `row` from column c, as FP32 (FP32 or BF16 storage).
-template <bool BF16>
-__device__ __forceinline__ float4 load_row4(const void* base, int64_t row, int kp, int c) {
-  if constexpr (BF16) {
-    const uint2 u = __ldg((const uint2*)((const __nv_bfloat16*)base + row * kp + c));
-    const float2 lo = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
-    const float2 hi = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
-    return make_float4(lo.x, lo.y, hi.x, hi.y);
-  } else {
-    return __ldg((const float4*)((const float*)base + row * kp + c));
-  }
-}
-
 __device__ __forceinline__ void fma4(float4& acc, float w, const float4& v) {
   acc.x = fmaf(w, v.x, acc.x);
   acc.y = fmaf(w, v.y, acc.y);
@@ -246,22 +233,6 @@ struct Slot<4, false> {
     acc[1] = fmaf(w, r.y, acc[1]);
     acc[2] = fmaf(w, r.z, acc[2]);
     acc[3] = fmaf(w, r.w, acc[3]);
-  }
-};
-template <>
-struct Slot<4, true> {
-  using Raw = uint2;
-  static __device__ __forceinline__ Raw load(const void* p, int64_t row, int kp, int c) {
-    return __ldg((const uint2*)((const __nv_bfloat16*)p + row * kp + c));
-  }
-  static __device__ __forceinline__ Raw zero() { return make_uint2(0u, 0u); }
-  static __device__ __forceinline__ void fma(float* acc, float w, const Raw& r) {
-    const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&r.x));
-    const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&r.y));
-    acc[0] = fmaf(w, a.x, acc[0]);
-    acc[1] = fmaf(w, a.y, acc[1]);
-    acc[2] = fmaf(w, b.x, acc[2]);
-    acc[3] = fmaf(w, b.y, acc[3]);
   }
 };
 template <>

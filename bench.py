@@ -121,6 +121,8 @@ def parse():
                     help="storage of the gathered block D^-1/2 V (bf16: FP32 master copy, FP32 accumulation)")
     ap.add_argument("--no-fp32-compare", action="store_true",
                     help="skip timing the plain FP32 path next to the BF16-gather one")
+    ap.add_argument("--no-time-to-tol", action="store_true",
+                    help="skip the time to a 1e-4 rad subspace angle against the FP32 reference")
     ap.add_argument("--iters", type=int, default=30, help="updates of Algorithm 2 per step")
     ap.add_argument("--spmm-engine", default="auto", choices=["auto", "simt", "tma"])
     ap.add_argument("--nodes", type=int, default=None, help="shrink the workload (testing only)")
@@ -227,6 +229,110 @@ def measured_traffic(workload: str, gather: str) -> dict | None:
     return entry
 
 
+TTT_TOL = 1e-4          # rad
+TTT_REF_UPDATES = 400   # the FP32 reference run (its relative gradient reaches the FP32 floor)
+
+
+def time_to_tol(g, method, X0, stream) -> dict:
+    """Updates and seconds until X is within TTT_TOL rad of the FP32 reference subspace, for the
+    BF16-gather and the plain FP32 path: the smallest multiple of 10 updates (fresh calls from X0)
+    that gets there, then that call timed with CUDA events (fixed per-call costs included)."""
+    import torch
+    from paper_2305_10356_gb300 import ofsc
+
+    def sin_angle(A, B):
+        qa, _ = torch.linalg.qr(A.double())
+        qb, _ = torch.linalg.qr(B.double())
+        sv = torch.linalg.svdvals(qa.T @ qb)
+        return float(torch.sqrt(torch.clamp(1.0 - sv.min() ** 2, min=0.0)))
+
+    X = X0.clone()
+    ofsc.ofsc_iterate(g, method, X, 0.0, TTT_REF_UPDATES, gather=ofsc.GATHER_FP32)
+    ref = X.clone()
+    out = {"tol_rad": TTT_TOL, "reference": f"plain FP32, {TTT_REF_UPDATES} updates from the same X0"}
+    for name, gather in (("bf16_gather", ofsc.GATHER_BF16), ("fp32", ofsc.GATHER_FP32)):
+        m, ang = 0, 1.0
+        while ang > TTT_TOL and m < TTT_REF_UPDATES:
+            m += 10
+            X.copy_(X0)
+            ofsc.ofsc_iterate(g, method, X, 0.0, m, gather=gather)
+            ang = sin_angle(X, ref)
+        X.copy_(X0)
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        ofsc.ofsc_iterate(g, method, X, 0.0, m, gather=gather)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        out[name] = {"updates": m, "seconds": t0.elapsed_time(t1) / 1000.0, "sin_angle": ang}
+    del ref
+    return out
+
+
+def run_stream(args):
+    """Streaming form: the snapshots of a synth.STREAMS workload, each built on the device and
+    iterated args.iters updates from the previous snapshot's X; one step = the whole stream, graph
+    builds included. `value` = updates per second over the stream."""
+    import torch
+
+    world, rank, local = dist_setup("nccl")
+    torch.cuda.set_device(local)
+    from paper_2305_10356_gb300 import build, ofsc, synth
+    build.build()
+    snaps, x0 = synth.stream(args.workload, n=args.nodes)
+    method = METHODS[args.method]
+    gather = ofsc.GATHER_BF16 if args.gather == "bf16" else ofsc.GATHER_FP32
+    dev = [(torch.from_numpy(e.src).cuda(), torch.from_numpy(e.dst).cuda()) for e in snaps]
+    X0 = torch.from_numpy(x0).cuda()
+    X = torch.empty_like(X0)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        X.copy_(X0)
+        n_up = 0
+        for (src, dst), e in zip(dev, snaps):
+            g = ofsc.ofsc_graph_build(e.n, src, dst)
+            r = ofsc.ofsc_iterate(g, method, X, 0.0, args.iters, gather=gather)
+            n_up += r.iterations
+            g.free()
+        return n_up
+
+    for _ in range(args.warmup):
+        step()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    updates = 0
+    for _ in range(args.steps):
+        updates += step()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    spec = synth.STREAMS[args.workload]
+    if rank == 0:
+        line = {"metric": "OFM iterations/s", "value": updates * world / (ms / 1000.0), "unit": "iterations/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32" if args.gather == "fp32" else "f32 (bf16 gather storage)", "data": "synthetic",
+                "config": {"workload": f"{args.workload}: SBM, N={args.nodes or spec['n']}, k={spec['n_blocks']}, "
+                                       f"mean degree {spec['mean_degree']:g} at 100%, {spec['parts']} cumulative "
+                                       f"edge-sampled snapshots, warm start, graph builds timed",
+                           "updates_per_snapshot": args.iters, "method": METHOD_LABEL[args.method]},
+                "impl": "gpu", "parallelism": "replicas only" if world > 1 else "single GPU"}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -331,6 +437,11 @@ def run_gpu(args):
     e2e = {"value": updates / e2e_s, "unit": "iterations/s",
            "h2d_bytes_per_step": int(x0.nbytes), "d2h_bytes_per_step": int(x0.nbytes)}
 
+    # time to tolerance: the subspace angle to an FP32 reference run of 400 updates
+    ttt = None
+    if rank == 0 and not args.no_time_to_tol:
+        ttt = time_to_tol(g, method, X0, stream)
+
     # dominant kernel (the direction product, phase "spmm") and its roofline
     pd = prof.as_dict()
     dom = max(pd, key=lambda p: pd[p]["ms"])
@@ -368,7 +479,7 @@ def run_gpu(args):
                 "vs_baseline": None, "dtype": "f32" if args.gather == "fp32" else "f32 (bf16 gather storage)",
                 "data": "synthetic", "config": workload_config(args), "impl": "gpu",
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-                "gpu_launches": launches, "plain_fp32": plain,
+                "gpu_launches": launches, "plain_fp32": plain, "time_to_tol": ttt,
                 "phases_ms_per_step": {p: pd[p]["ms"] / args.steps for p in pd},
                 "parallelism": "replicas only" if world > 1 else "single GPU"}
         print(json.dumps(line), flush=True)
@@ -381,6 +492,9 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    from paper_2305_10356_gb300 import synth
+    if args.workload in synth.STREAMS:
+        return run_stream(args)
     return run_gpu(args)
 
 

@@ -219,6 +219,42 @@ WORKLOADS = {
 }
 
 
+def edge_stream(edges: EdgeList, parts: int, seed: int) -> list[EdgeList]:
+    """Cumulative snapshots of a graph revealed by uniform edge sampling: the edge list in a random
+    order, snapshot s (s = 0..parts-1) holding its first round((s + 1) m / parts) edges, i.e.
+    1/parts, 2/parts, ... of the edges. Nodes without an edge yet are isolated in that snapshot."""
+    rng = rng_for(seed)
+    order = rng.permutation(edges.m)
+    out = []
+    for s in range(parts):
+        take = order[: int(round((s + 1) * edges.m / parts))]
+        out.append(EdgeList(n=edges.n, src=edges.src[take], dst=edges.dst[take],
+                            w=None if edges.w is None else edges.w[take], labels=edges.labels,
+                            n_blocks=edges.n_blocks))
+    return out
+
+
+STREAMS = {
+    # SBM, 200,000 nodes, 71 blocks (+-20%), mean degree 30 at 100%, within:between 5:1 (edge
+    # counts), revealed in ten cumulative snapshots (10%, 20%, ..., 100% of the edges)
+    "sbm_stream_n200k_k71": dict(n=200_000, n_blocks=71, mean_degree=30.0, ratio=5.0, ratio_kind="count",
+                                 sizes="uniform", size_param=0.2, gamma=None, join_isolated=False, idx=4,
+                                 parts=10),
+}
+
+
+def stream(name: str, n: int | None = None) -> tuple[list[EdgeList], np.ndarray]:
+    """Snapshots and X0 of a named streaming workload; `n` shrinks the node count."""
+    spec = dict(STREAMS[name])
+    idx = spec.pop("idx")
+    parts = spec.pop("parts")
+    if n is not None:
+        spec["n"] = n
+    seed = 2305 * 1000 + idx
+    full = sbm(seed=seed, **spec)
+    return edge_stream(full, parts, seed + 2), initial_block(full.n, full.n_blocks, seed + 1)
+
+
 def workload(name: str, n: int | None = None, seed_offset: int = 0) -> tuple[EdgeList, np.ndarray]:
     """Edge list and X0 for a named workload; `n` shrinks the node count (same recipe)."""
     spec = dict(WORKLOADS[name])

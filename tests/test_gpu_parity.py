@@ -368,3 +368,25 @@ def test_tensor_core_direction_pass(method):
     ref = o.iterate(og, method, x0, 0.0, 6)
     assert np.linalg.norm(Xt - ref.X) <= 1e-4 * np.linalg.norm(ref.X)
     assert abs(rt.rel_dir_norm - ref.rel_norms[-1]) <= 1e-4 * ref.rel_norms[-1] + 1e-7
+
+
+def test_streaming_snapshots_warm_start_match_oracle():
+    """The streaming form: five cumulative edge-sampled snapshots, a new graph per snapshot and X
+    carried from one snapshot's iterations into the next (CG restarted from G of the new graph);
+    every snapshot's X matches the oracle doing the same, and on the last snapshot the warm start
+    reaches the tolerance in fewer updates than a cold start."""
+    full = synth.sbm(3000, 6, 24.0, 5.0, ratio_kind="count", join_isolated=False, seed=91)
+    snaps = synth.edge_stream(full, 5, seed=92)
+    x0 = synth.initial_block(full.n, 6, 93)
+    Xg, Xo = x0.copy(), x0.copy()
+    for e in snaps:
+        g = gpu_graph(e)
+        Xg, r, _ = run_iterate(g, o.OFM_F1, Xg, 0.0, 8)
+        ref = o.iterate(o.build_graph(e.n, e.src, e.dst), o.OFM_F1, Xo, 0.0, 8)
+        Xo = ref.X
+        assert np.linalg.norm(Xg - Xo) <= 1e-4 * np.linalg.norm(Xo)
+    g = gpu_graph(snaps[-1])
+    _, warm, _ = run_iterate(g, o.OFM_F1, Xg, 1e-4, 2000)
+    _, cold, _ = run_iterate(g, o.OFM_F1, x0, 1e-4, 2000)
+    assert warm.status == ofsc.OK and cold.status == ofsc.OK
+    assert warm.iterations < cold.iterations

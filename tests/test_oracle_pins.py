@@ -476,3 +476,21 @@ def test_every_direction_descends(method):
         live = np.linalg.norm(G, axis=0) > 1e-8 * g0
         assert np.all(vg[live] < 0), (t, vg)
     assert res.rel_norms[-1] < 1e-9
+
+
+def test_edge_stream_snapshots_are_cumulative_uniform_samples():
+    """Streaming snapshots: each holds a prefix of one random order of the full edge list, so they
+    are nested, the last one is the whole graph, and the sizes step by m / parts."""
+    full = synth.sbm(500, 4, 12.0, 5.0, ratio_kind="count", join_isolated=False, seed=3)
+    snaps = synth.edge_stream(full, 5, seed=4)
+    prev = None
+    for s, e in enumerate(snaps):
+        assert e.m == int(round((s + 1) * full.m / 5))
+        pairs = list(zip(e.src.tolist(), e.dst.tolist()))
+        if prev is not None:
+            assert pairs[: len(prev)] == prev
+        prev = pairs
+    assert sorted(prev) == sorted(zip(full.src.tolist(), full.dst.tolist()))
+    # the early snapshots leave nodes isolated; the builder gives them D = 0 (Eq. (1) reading)
+    og = o.build_graph(snaps[0].n, snaps[0].src, snaps[0].dst)
+    assert (og.deg == 0).any()

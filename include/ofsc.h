@@ -192,7 +192,8 @@ typedef struct {
  *   opts     host struct or NULL for defaults
  *   out      HOST ofsc_result (nullable)
  * G_0 = g(X_0), V_0 = -G_0, X_1 = X_0 + V_0 diag(alpha_0); for t >= 1: G_t = g(X_t);
- * beta_i = sum_l (G_t - G_{t-1})_li G_t,li / sum_l G_{t-1,li}^2 (0 if the denominator is 0);
+ * beta_i = sum_l (G_t - G_{t-1})_li G_t,li / sum_l G_{t-1,li}^2 (0 if the denominator is 0, and 0
+ * when the resulting column of V_t would not be a descent direction, V_t,i . G_t,i >= 0);
  * V_t = -G_t + V_{t-1} diag(beta); alpha_t from the exact line search (one alpha for OFM, one
  * per column for TriOFM, with X_i, V_i the first i columns); X_{t+1} = X_t + V_t diag(alpha_t).
  * Returns OFSC_OK when tol was met, OFSC_ERR_NOT_CONVERGED when maxit was reached first (X is
@@ -201,6 +202,21 @@ typedef struct {
  */
 ofsc_status ofsc_iterate(ofsc_graph* g, int32_t method, int32_t k, float* X, double tol,
                          int32_t maxit, const ofsc_opts* opts, ofsc_result* out, void* stream);
+
+/*
+ * ofsc_rayleigh_ritz - the eigensolver view of a feature block (Sec. 5): Ritz values of
+ * B = 2I - L = -A on span(X) and relerr = ||B U - U Lam||_F / ||U Lam||_F with U = X Z the
+ * B-Ritz vectors (Z^T X^T X Z = I). Computed from the Grams X^T X, X^T A X (exact A X) by k x k
+ * FP64 algebra on the device (Cholesky, cyclic Jacobi) and one row pass for the residual
+ * A X - X (X^T X)^-1 X^T A X; U itself is not formed.
+ * X: device float32 [n x k] (n = the graph's node count, 1 <= k <= 128), read only, full column
+ * rank. ritz: device float64 [k], written with the Ritz values in ascending order. relerr: host,
+ * written. Uses the graph's cached workspace; synchronises `stream`.
+ * Errors: OFSC_ERR_INVALID_ARG (NULL pointers, k out of range, X rank deficient), OFSC_ERR_OOM,
+ * OFSC_ERR_NONFINITE.
+ */
+ofsc_status ofsc_rayleigh_ritz(ofsc_graph* g, int32_t k, const float* X, double* ritz, double* relerr,
+                               void* stream);
 
 /*
  * ofsc_row_normalize - X_l <- X_l / ||X_l||_2 for every row; zero rows stay zero

@@ -240,6 +240,12 @@ cudaError_t spmm_tma_launch(const CUtensorMap& map, const TmaSpmmArgs& a, bool b
 bool direction_tc_supported(int method, int kp);
 cudaError_t direction_tc_launch(int method, const RowArgs& a, cudaStream_t s, int* nblk);
 
+// Rayleigh-Ritz algebra of csrc/ritz.cu (k x k FP64; work holds [4][kp][kp] doubles).
+cudaError_t ritz_prepare_launch(const double* R64, const double* B64, int k, int kp, double* work, float* Rn,
+                                double* lam, double* sums, Ctrl* ctrl, cudaStream_t s);
+cudaError_t ritz_relerr_launch(const double* GtG, const double* work, int k, int kp, const double* sums, double* out,
+                               cudaStream_t s);
+
 int64_t gram_tc_rows_per_cta(int64_t n, int nr);
 size_t gram_tc_part_bytes(int64_t n, int nr, int64_t rows_per_cta);
 cudaError_t gram_tc_launch(GramTcArgs a, const int* slot, int kp, double* gram, cudaStream_t s);

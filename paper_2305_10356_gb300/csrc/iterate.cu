@@ -1833,6 +1833,52 @@ extern "C" ofsc_status ofsc_objective_grad(ofsc_graph* g, int32_t objective, int
   return OFSC_OK;
 }
 
+extern "C" ofsc_status ofsc_rayleigh_ritz(ofsc_graph* g, int32_t k, const float* X, double* ritz, double* relerr,
+                                          void* stream_) {
+  clear_error();
+  if (!g) return fail(OFSC_ERR_INVALID_ARG, "ofsc_rayleigh_ritz: graph is NULL");
+  if (k < 1 || k > kMaxK) return fail(OFSC_ERR_INVALID_ARG, "ofsc_rayleigh_ritz: k=%d outside [1, %d]", k, kMaxK);
+  if (!ritz || !relerr || (g->n > 0 && !X)) return fail(OFSC_ERR_INVALID_ARG, "ofsc_rayleigh_ritz: NULL pointer");
+  if (g->n < k) return fail(OFSC_ERR_INVALID_ARG, "ofsc_rayleigh_ritz: n=%lld < k=%d", (long long)g->n, k);
+  cudaStream_t s = (cudaStream_t)stream_;
+  const int kp = round_up(k, 8);
+  ofsc_status st = ensure_workspace(g, kp);
+  if (st != OFSC_OK) return st;
+  Workspace& ws = g->ws;
+  Prof prof{ws, nullptr, s};
+  Runner run{g, ws, s, M_OFM_F1, false, prof};
+  run.tc = kp > 64;
+  double* work = nullptr;
+  OFSC_CUDA(cudaMallocAsync((void**)&work, (4 * (size_t)kp * kp + 2) * sizeof(double), s));
+  double* sums = work + 4 * (size_t)kp * kp;
+  double* out = sums + 1;
+  k_init_ctrl<<<1, 1, 0, s>>>(ws.ctrl, 0.0, 0, k, g->normA2, 0);
+  k_pad_in<<<grid_elems(g->n * kp), 256, 0, s>>>(g->n, k, kp, X, ws.X, ws.ctrl);
+  cudaError_t e = run.refresh(1, 0);  // A X, X^T X (R64), X^T A X (B64)
+  if (e == cudaSuccess) e = ritz_prepare_launch(ws.R64, ws.B64, k, kp, work, ws.Rn, ritz, sums, ws.ctrl, s);
+  int nblk = 0;
+  // G = 4 (A X + X Rn) = 4 E with Rn = -(X^T X)^-1 X^T A X (the OFM-f1 row pass, evaluation form)
+  if (e == cudaSuccess) e = run.rowpass(M_OFM_F1, 0, 1, 0, &nblk);
+  if (e == cudaSuccess) {
+    const float* Rs[1] = {ws.G};
+    const int slots[1] = {G_E};
+    e = run.grams(ws.G, Rs, 1, slots, 0, false);
+  }
+  if (e == cudaSuccess) e = ritz_relerr_launch(ws.gram + (size_t)G_E * kp * kp, work, k, kp, sums, out, s);
+  double h = 0.0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, out, sizeof(double), cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(work, s);
+  if (e != cudaSuccess) return cuda_fail(e, "ofsc_rayleigh_ritz");
+  Ctrl c{};
+  st = finish(ws, s, &c);
+  if (st != OFSC_OK) return st;
+  if (c.status == OFSC_ERR_INVALID_ARG) return fail(c.status, "ofsc_rayleigh_ritz: X^T X is not positive definite");
+  if (c.status != OFSC_OK) return fail(c.status, "ofsc_rayleigh_ritz: failed (status %d)", c.status);
+  if (!std::isfinite(h)) return fail(OFSC_ERR_NONFINITE, "ofsc_rayleigh_ritz: non-finite relerr");
+  *relerr = h;
+  return OFSC_OK;
+}
+
 extern "C" ofsc_status ofsc_iterate(ofsc_graph* g, int32_t method, int32_t k, float* X, double tol,
                                     int32_t maxit, const ofsc_opts* opts, ofsc_result* out, void* stream_) {
   clear_error();

@@ -91,6 +91,7 @@ def lib() -> ctypes.CDLL:
             "ofsc_objective_grad_noalloc": [vp, i32, i32, vp, ctypes.POINTER(dbl), vp, vp],
             "ofsc_iterate": [vp, i32, i32, vp, dbl, i32, ctypes.POINTER(Opts),
                              ctypes.POINTER(Result), vp],
+            "ofsc_rayleigh_ritz": [vp, i32, vp, vp, ctypes.POINTER(dbl), vp],
             "ofsc_row_normalize": [i64, i32, vp, vp],
             "ofsc_gram": [i64, i32, i32, vp, i32, ctypes.POINTER(vp), i64, vp, vp],
             "ofsc_kmeans": [i64, i32, vp, i32, u64, i32, i32, vp, ctypes.POINTER(dbl), vp],
@@ -213,6 +214,15 @@ def ofsc_gram(L, Rs, out, k: int | None = None, rows_per_block: int = 0, stream=
     arr = (ctypes.c_void_p * len(Rs))(*[_ptr(r) for r in Rs])
     _check(lib().ofsc_gram(n, ld if k is None else k, ld, _ptr(L), len(Rs), arr, rows_per_block,
                            _ptr(out), _stream(stream)))
+
+
+def ofsc_rayleigh_ritz(g: Graph, X, ritz, stream=None) -> float:
+    """Ritz values of B = 2I - L on span(X) into the device float64 vector `ritz` (ascending) and
+    the relative residual relerr of Sec. 5, returned."""
+    out = ctypes.c_double(0.0)
+    _check(lib().ofsc_rayleigh_ritz(g.handle, int(X.shape[1]), _ptr(X), _ptr(ritz), ctypes.byref(out),
+                                    _stream(stream)))
+    return float(out.value)
 
 
 def ofsc_row_normalize(X, stream=None) -> None:

@@ -390,3 +390,29 @@ def test_streaming_snapshots_warm_start_match_oracle():
     _, cold, _ = run_iterate(g, o.OFM_F1, x0, 1e-4, 2000)
     assert warm.status == ofsc.OK and cold.status == ofsc.OK
     assert warm.iterations < cold.iterations
+
+
+@pytest.mark.parametrize("k", [8, 128])
+def test_rayleigh_ritz_matches_oracle(k):
+    """Ritz values of B = -A on span(X) and relerr (Sec. 5) from the device's Grams and FP64 k x k
+    algebra, against the oracle's QR + dense eigendecomposition, for a raw random block (large
+    relerr) and for a block after 300 oracle updates (small relerr)."""
+    import torch
+    e = synth.sbm(2500, 8, 24.0, 6.0, ratio_kind="count", seed=101)
+    og = o.build_graph(e.n, e.src, e.dst)
+    g = gpu_graph(e)
+    x0 = synth.initial_block(e.n, k, 102)
+    x_conv = o.iterate(og, o.OFM_F1, x0, 0.0, 300).X.astype(np.float32)
+    for X in (x0, x_conv):
+        lam_ref, rel_ref = o.rayleigh_ritz_relerr(og, X.astype(np.float64))
+        Xd = torch.from_numpy(np.ascontiguousarray(X)).cuda()
+        ritz = torch.zeros(k, dtype=torch.float64, device="cuda")
+        rel = ofsc.ofsc_rayleigh_ritz(g, Xd, ritz)
+        lam = ritz.cpu().numpy()
+        assert np.max(np.abs(lam - lam_ref)) <= 2e-6 * np.max(np.abs(lam_ref))
+        assert abs(rel - rel_ref) <= 0.02 * rel_ref + 2e-6, (rel, rel_ref)
+    # a rank-deficient block is refused
+    Xbad = np.array(x0)
+    Xbad[:, 1] = Xbad[:, 0]
+    with pytest.raises(ofsc.OfscError):
+        ofsc.ofsc_rayleigh_ritz(g, torch.from_numpy(Xbad).cuda(), torch.zeros(k, dtype=torch.float64, device="cuda"))

@@ -204,6 +204,21 @@ ofsc_status ofsc_iterate(ofsc_graph* g, int32_t method, int32_t k, float* X, dou
                          int32_t maxit, const ofsc_opts* opts, ofsc_result* out, void* stream);
 
 /*
+ * ofsc_weight_grad - gradient of f1 (Eq. (2)) or f2 (Eq. (3)) at X with respect to the weight of
+ * every listed edge of a weighted graph: with A_hat = D^-1/2 S D^-1/2 and Gamma = df/dA_hat
+ * (2(I + A_hat - X X^T) for f1, -X(2I - X^T X)X^T for f2), a listing e of the pair {a, b}, a != b,
+ * gets 2 Gamma_ab / sqrt(d_a d_b) - r_a / d_a - r_b / d_b with r_a = sum_j Gamma_aj A_hat_aj.
+ * Listings of the same pair share one value (S sums them); self-loops get 0.
+ * g: built with weights from the same edge list. X: device float32 [n x k], 1 <= k <= 128.
+ * src, dst: device int32 [m], the edge list given to ofsc_graph_build. grad: device float32 [m],
+ * written. Synchronises `stream`.
+ * Errors: OFSC_ERR_INVALID_ARG (unweighted graph, NULL pointers, an endpoint outside [0, n)),
+ * OFSC_ERR_OOM.
+ */
+ofsc_status ofsc_weight_grad(ofsc_graph* g, int32_t objective, int32_t k, const float* X, int64_t m,
+                             const int32_t* src, const int32_t* dst, float* grad, void* stream);
+
+/*
  * ofsc_rayleigh_ritz - the eigensolver view of a feature block (Sec. 5): Ritz values of
  * B = 2I - L = -A on span(X) and relerr = ||B U - U Lam||_F / ||U Lam||_F with U = X Z the
  * B-Ritz vectors (Z^T X^T X Z = I). Computed from the Grams X^T X, X^T A X (exact A X) by k x k

@@ -206,6 +206,79 @@ def gradient(which: int, X: np.ndarray, AX: np.ndarray) -> np.ndarray:
     return direction(OFM_F1 if which == 1 else OFM_F2, X, AX)
 
 
+def objective_of_weights(n: int, src: np.ndarray, dst: np.ndarray, w: np.ndarray, X: np.ndarray, which: int) -> float:
+    """f1 (Eq. (2)) or f2 (Eq. (3)) in FP64 straight from the listed edge weights (pairs summed,
+    self-loops dropped, no FP32 rounding of S), sparse: with A = -I - A_hat and tr(A_hat) = 0,
+    ||A||_F^2 = n + ||A_hat||_F^2."""
+    src = np.asarray(src, dtype=np.int64)
+    dst = np.asarray(dst, dtype=np.int64)
+    w = np.asarray(w, dtype=np.float64)
+    X = np.asarray(X, dtype=np.float64)
+    a = np.minimum(src, dst)
+    b = np.maximum(src, dst)
+    keep = a != b
+    keys, inv = np.unique(a[keep] * n + b[keep], return_inverse=True)
+    pa, pb = keys // n, keys % n
+    S = np.zeros(keys.size)
+    np.add.at(S, inv, w[keep])
+    d = np.zeros(n)
+    np.add.at(d, pa, S)
+    np.add.at(d, pb, S)
+    sd = np.where(d > 0, 1.0 / np.sqrt(np.where(d > 0, d, 1.0)), 0.0)
+    ah = S * sd[pa] * sd[pb]
+    AX = -X.copy()
+    np.add.at(AX, pa, -ah[:, None] * X[pb])
+    np.add.at(AX, pb, -ah[:, None] * X[pa])
+    normA2 = n + 2.0 * float(np.sum(ah * ah))
+    return objective(which, X, AX, normA2)
+
+
+def weight_grad(n: int, src: np.ndarray, dst: np.ndarray, w: np.ndarray, X: np.ndarray, which: int) -> np.ndarray:
+    """d f / d w_e for every listed edge e of a weighted graph, f = f1 (Eq. (2)) or f2 (Eq. (3)).
+
+    Everything in FP64 from the listed weights (no FP32 rounding of S). With
+    A_hat = D^-1/2 S D^-1/2, A = -I - A_hat and Gamma = df/dA_hat (symmetric),
+        Gamma = 2 (I + A_hat - X X^T)          for f1,
+        Gamma = -X (2I - X^T X) X^T            for f2,
+    a listing of the pair {a, b} (a != b) changes S_ab = S_ba and the degrees d_a, d_b, so
+        df/dw = 2 Gamma_ab / sqrt(d_a d_b) - r_a / d_a - r_b / d_b,   r_a = sum_j Gamma_aj A_hat_aj.
+    Listings of the same pair share one value; self-loops (dropped from S) get 0.
+    """
+    src = np.asarray(src, dtype=np.int64)
+    dst = np.asarray(dst, dtype=np.int64)
+    w = np.asarray(w, dtype=np.float64)
+    X = np.asarray(X, dtype=np.float64)
+    a = np.minimum(src, dst)
+    b = np.maximum(src, dst)
+    keep = a != b
+    keys, inv = np.unique(a[keep] * n + b[keep], return_inverse=True)
+    pa, pb = keys // n, keys % n
+    S = np.zeros(keys.size)
+    np.add.at(S, inv, w[keep])
+    d = np.zeros(n)
+    np.add.at(d, pa, S)
+    np.add.at(d, pb, S)
+    sd = np.where(d > 0, 1.0 / np.sqrt(np.where(d > 0, d, 1.0)), 0.0)
+    ah = S * sd[pa] * sd[pb]
+    AhX = np.zeros_like(X)
+    np.add.at(AhX, pa, ah[:, None] * X[pb])
+    np.add.at(AhX, pb, ah[:, None] * X[pa])
+    if which == 1:
+        gam = 2.0 * (ah - np.sum(X[pa] * X[pb], axis=1))
+        sq = np.zeros(n)
+        np.add.at(sq, pa, ah * ah)
+        np.add.at(sq, pb, ah * ah)
+        r = 2.0 * (sq - np.sum(X * AhX, axis=1))
+    else:
+        Z = X @ (2.0 * np.eye(X.shape[1]) - X.T @ X)
+        gam = -np.sum(X[pa] * Z[pb], axis=1)
+        r = -np.sum(Z * AhX, axis=1)
+    gp = 2.0 * gam * sd[pa] * sd[pb] - r[pa] * sd[pa] ** 2 - r[pb] * sd[pb] ** 2
+    out = np.zeros(src.size)
+    out[keep] = gp[inv]
+    return out
+
+
 # =============================================================================================
 # Exact line search, Sec. 3.2, Eqs. (15)-(18)
 # =============================================================================================

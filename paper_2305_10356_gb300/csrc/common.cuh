@@ -240,6 +240,28 @@ cudaError_t spmm_tma_launch(const CUtensorMap& map, const TmaSpmmArgs& a, bool b
 bool direction_tc_supported(int method, int kp);
 cudaError_t direction_tc_launch(int method, const RowArgs& a, cudaStream_t s, int* nblk);
 
+// Edge-weight gradient of f1 / f2 (csrc/wgrad.cu).
+struct WgradArgs {
+  int64_t n;
+  int kp;
+  int which;             // 1: f1, 2: f2
+  const float* X;        // [n][kp]
+  const float* AX;       // [n][kp]
+  const double* R64;     // X^T X (f2)
+  const int64_t* row_ptr;
+  const int32_t* col;
+  const float* val;      // weighted S (or null)
+  const float* dinv;
+  float* r;              // [n] scratch
+  float* Z;              // [n][kp] scratch (f2)
+  int64_t m;
+  const int32_t* src;
+  const int32_t* dst;
+  float* grad;           // [m]
+  int* bad;              // set when an endpoint is out of range
+};
+cudaError_t wgrad_launch(const WgradArgs& w, cudaStream_t s);
+
 // Rayleigh-Ritz algebra of csrc/ritz.cu (k x k FP64; work holds [4][kp][kp] doubles).
 cudaError_t ritz_prepare_launch(const double* R64, const double* B64, int k, int kp, double* work, float* Rn,
                                 double* lam, double* sums, Ctrl* ctrl, cudaStream_t s);

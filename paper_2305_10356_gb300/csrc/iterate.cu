@@ -1833,6 +1833,68 @@ extern "C" ofsc_status ofsc_objective_grad(ofsc_graph* g, int32_t objective, int
   return OFSC_OK;
 }
 
+extern "C" ofsc_status ofsc_weight_grad(ofsc_graph* g, int32_t objective, int32_t k, const float* X, int64_t m,
+                                        const int32_t* src, const int32_t* dst, float* grad, void* stream_) {
+  clear_error();
+  if (!g) return fail(OFSC_ERR_INVALID_ARG, "ofsc_weight_grad: graph is NULL");
+  if (objective != OFSC_F1 && objective != OFSC_F2)
+    return fail(OFSC_ERR_INVALID_ARG, "ofsc_weight_grad: objective must be OFSC_F1 or OFSC_F2");
+  if (k < 1 || k > kMaxK) return fail(OFSC_ERR_INVALID_ARG, "ofsc_weight_grad: k=%d outside [1, %d]", k, kMaxK);
+  if (!g->weighted) return fail(OFSC_ERR_INVALID_ARG, "ofsc_weight_grad: the graph was built without edge weights");
+  if (m < 0 || (m > 0 && (!src || !dst || !grad)) || (g->n > 0 && !X))
+    return fail(OFSC_ERR_INVALID_ARG, "ofsc_weight_grad: bad edge arrays or NULL X");
+  cudaStream_t s = (cudaStream_t)stream_;
+  const int kp = round_up(k, 8);
+  ofsc_status st = ensure_workspace(g, kp);
+  if (st != OFSC_OK) return st;
+  Workspace& ws = g->ws;
+  Prof prof{ws, nullptr, s};
+  Runner run{g, ws, s, objective == OFSC_F1 ? M_OFM_F1 : M_OFM_F2, false, prof};
+  run.tc = kp > 64;
+  void* scratch = nullptr;
+  OFSC_CUDA(cudaMallocAsync(&scratch, (size_t)(g->n + 1) * sizeof(float) + 16, s));
+  int* bad = (int*)scratch;
+  float* r = (float*)((char*)scratch + 16);
+  cudaMemsetAsync(bad, 0, sizeof(int), s);
+  k_init_ctrl<<<1, 1, 0, s>>>(ws.ctrl, 0.0, 0, k, g->normA2, 0);
+  cudaError_t e = cudaSuccess;
+  if (g->n > 0) {
+    k_pad_in<<<grid_elems(g->n * kp), 256, 0, s>>>(g->n, k, kp, X, ws.X, ws.ctrl);
+    e = run.refresh(objective, 0);  // A X and X^T X
+  }
+  if (e == cudaSuccess) {
+    WgradArgs w{};
+    w.n = g->n;
+    w.kp = kp;
+    w.which = objective;
+    w.X = ws.X;
+    w.AX = ws.Y;
+    w.R64 = ws.R64;
+    w.row_ptr = g->row_ptr;
+    w.col = g->col;
+    w.val = g->val;
+    w.dinv = g->dinv;
+    w.r = r;
+    w.Z = ws.W;
+    w.m = m;
+    w.src = src;
+    w.dst = dst;
+    w.grad = grad;
+    w.bad = bad;
+    e = wgrad_launch(w, s);
+  }
+  int hbad = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(scratch, s);
+  if (e != cudaSuccess) return cuda_fail(e, "ofsc_weight_grad");
+  Ctrl c{};
+  st = finish(ws, s, &c);
+  if (st != OFSC_OK) return st;
+  if (hbad) return fail(OFSC_ERR_INVALID_ARG, "ofsc_weight_grad: an edge endpoint is outside [0, n)");
+  if (c.status != OFSC_OK) return fail(c.status, "ofsc_weight_grad: failed (status %d)", c.status);
+  return OFSC_OK;
+}
+
 extern "C" ofsc_status ofsc_rayleigh_ritz(ofsc_graph* g, int32_t k, const float* X, double* ritz, double* relerr,
                                           void* stream_) {
   clear_error();

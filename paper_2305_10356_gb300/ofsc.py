@@ -92,6 +92,7 @@ def lib() -> ctypes.CDLL:
             "ofsc_iterate": [vp, i32, i32, vp, dbl, i32, ctypes.POINTER(Opts),
                              ctypes.POINTER(Result), vp],
             "ofsc_rayleigh_ritz": [vp, i32, vp, vp, ctypes.POINTER(dbl), vp],
+            "ofsc_weight_grad": [vp, i32, i32, vp, i64, vp, vp, vp, vp],
             "ofsc_row_normalize": [i64, i32, vp, vp],
             "ofsc_gram": [i64, i32, i32, vp, i32, ctypes.POINTER(vp), i64, vp, vp],
             "ofsc_kmeans": [i64, i32, vp, i32, u64, i32, i32, vp, ctypes.POINTER(dbl), vp],
@@ -214,6 +215,43 @@ def ofsc_gram(L, Rs, out, k: int | None = None, rows_per_block: int = 0, stream=
     arr = (ctypes.c_void_p * len(Rs))(*[_ptr(r) for r in Rs])
     _check(lib().ofsc_gram(n, ld if k is None else k, ld, _ptr(L), len(Rs), arr, rows_per_block,
                            _ptr(out), _stream(stream)))
+
+
+def ofsc_weight_grad(g: Graph, objective: int, X, src, dst, grad, stream=None) -> None:
+    """d f / d w for every listed edge (device int32 src, dst; device float32 grad) of a weighted graph."""
+    _check(lib().ofsc_weight_grad(g.handle, objective, int(X.shape[1]), _ptr(X), int(src.numel()), _ptr(src),
+                                  _ptr(dst), _ptr(grad), _stream(stream)))
+
+
+def objective(X, w, src, dst, n: int, which: int = 1):
+    """f1 (which=1) or f2 (which=2) of the graph with edge list (src, dst) and weights w at the
+    feature block X, as a differentiable scalar (float64): backward gives df/dX (Eqs. (5), (10))
+    and df/dw (ofsc_weight_grad). All tensors on one CUDA device; X float32 [n x k], w float32 [m]."""
+    import torch
+
+    class _Objective(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, X, w):
+            g = ofsc_graph_build(n, src, dst, w)
+            G = torch.empty_like(X)
+            f = ofsc_objective_grad(g, which, X, G)
+            ctx.g = g
+            ctx.save_for_backward(X, G)
+            return torch.tensor(f, dtype=torch.float64, device=X.device)
+
+        @staticmethod
+        def backward(ctx, gf):
+            X, G = ctx.saved_tensors
+            gX = gw = None
+            if ctx.needs_input_grad[0]:
+                gX = G * gf.to(G.dtype)
+            if ctx.needs_input_grad[1]:
+                gw = torch.empty(src.shape[0], dtype=torch.float32, device=X.device)
+                ofsc_weight_grad(ctx.g, which, X, src, dst, gw)
+                gw = gw * gf.to(gw.dtype)
+            return gX, gw
+
+    return _Objective.apply(X, w)
 
 
 def ofsc_rayleigh_ritz(g: Graph, X, ritz, stream=None) -> float:

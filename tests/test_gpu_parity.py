@@ -416,3 +416,51 @@ def test_rayleigh_ritz_matches_oracle(k):
     Xbad[:, 1] = Xbad[:, 0]
     with pytest.raises(ofsc.OfscError):
         ofsc.ofsc_rayleigh_ritz(g, torch.from_numpy(Xbad).cuda(), torch.zeros(k, dtype=torch.float64, device="cuda"))
+
+
+@pytest.mark.parametrize("which,k", [(1, 8), (2, 8), (1, 32), (2, 32)])
+def test_weight_grad_matches_oracle(which, k):
+    """df/dw for every listed edge of a weighted SBM (repeated pairs and self-loops included) against
+    the oracle's FP64 gradient."""
+    import torch
+    e = synth.sbm(3000, 6, 20.0, 6.0, ratio_kind="count", weighted=True, seed=111)
+    x = synth.initial_block(e.n, k, 112) * 3.0
+    g = gpu_graph(e)
+    src, dst, w = upload(e)
+    Xd = torch.from_numpy(x).cuda()
+    grad = torch.empty(e.m, dtype=torch.float32, device="cuda")
+    ofsc.ofsc_weight_grad(g, which, Xd, src, dst, grad)
+    ref = o.weight_grad(e.n, e.src, e.dst, e.w, x, which)
+    got = grad.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(got - ref) <= 1e-4 * np.linalg.norm(ref)
+    loops = e.src == e.dst
+    assert loops.any() and np.all(got[loops] == 0.0)
+
+
+@pytest.mark.parametrize("which", [1, 2])
+def test_autograd_objective_matches_central_differences(which):
+    """The differentiable objective (weighted SBM, 20,000 nodes, k = 32, w ~ U(0.5, 1.5)): the
+    directional derivatives of its hand-written backward in X and in the edge weights against FP64
+    oracle central differences (step 1e-3, 64 random directions)."""
+    import torch
+    e, x0 = synth.workload("wsbm_n20k_k32")
+    X = torch.from_numpy(x0 * 4.0).cuda().requires_grad_(True)
+    src, dst, w = upload(e)
+    w = w.clone().requires_grad_(True)
+    f = ofsc.objective(X, w, src, dst, e.n, which)
+    f.backward()
+    gX = X.grad.cpu().numpy().astype(np.float64)
+    gw = w.grad.cpu().numpy().astype(np.float64)
+    f64 = o.objective_of_weights(e.n, e.src, e.dst, e.w, x0 * 4.0, which)
+    assert abs(float(f.detach()) - f64) <= 1e-5 * max(1.0, abs(f64))
+    rng = np.random.default_rng(113)
+    eps = 1e-3
+    xb, wb = (x0 * 4.0).astype(np.float64), e.w.astype(np.float64)
+    for _ in range(64):
+        dX = rng.standard_normal(xb.shape) * 1e-2
+        dw = rng.standard_normal(wb.shape) * 1e-1
+        fp = o.objective_of_weights(e.n, e.src, e.dst, wb + eps * dw, xb + eps * dX, which)
+        fm = o.objective_of_weights(e.n, e.src, e.dst, wb - eps * dw, xb - eps * dX, which)
+        fd = (fp - fm) / (2 * eps)
+        an = float(np.sum(gX * dX) + np.sum(gw * dw))
+        assert abs(an - fd) <= 1e-3 * abs(fd) + 1e-6, (an, fd)

@@ -494,3 +494,52 @@ def test_edge_stream_snapshots_are_cumulative_uniform_samples():
     # the early snapshots leave nodes isolated; the builder gives them D = 0 (Eq. (1) reading)
     og = o.build_graph(snaps[0].n, snaps[0].src, snaps[0].dst)
     assert (og.deg == 0).any()
+
+
+def _objective_of_weights(n, src, dst, w, X, which):
+    """Eqs. (2)/(3) written out densely in FP64 as a function of the listed edge weights."""
+    S = np.zeros((n, n))
+    for a, b, x in zip(src, dst, w):
+        if a != b:
+            S[a, b] += x
+            S[b, a] += x
+    d = S.sum(axis=1)
+    sd = np.where(d > 0, 1.0 / np.sqrt(np.where(d > 0, d, 1.0)), 0.0)
+    A = -np.eye(n) - sd[:, None] * S * sd[None, :]
+    return o.objective_dense(which, A, X)
+
+
+@pytest.mark.parametrize("which", [1, 2])
+def test_weight_grad_matches_central_differences(which):
+    """d f / d w for every listed edge against central differences of the dense FP64 objective, on
+    a graph with a pair listed twice (in both directions), a self-loop and an isolated node."""
+    rng = np.random.default_rng(11 + which)
+    n, k = 10, 3
+    src = np.array([0, 1, 2, 3, 4, 5, 6, 1, 7, 2, 8, 3], dtype=np.int64)
+    dst = np.array([1, 2, 3, 4, 5, 6, 0, 0, 7, 5, 2, 0], dtype=np.int64)  # (1, 0) repeats (0, 1); (7, 7) a loop; 9 isolated
+    w = rng.uniform(0.5, 1.5, src.size)
+    X = rng.standard_normal((n, k)) * 0.4
+    got = o.weight_grad(n, src, dst, w, X, which)
+    eps = 1e-5
+    for e in range(src.size):
+        wp, wm = w.copy(), w.copy()
+        wp[e] += eps
+        wm[e] -= eps
+        fd = (_objective_of_weights(n, src, dst, wp, X, which) - _objective_of_weights(n, src, dst, wm, X, which)) / (2 * eps)
+        assert abs(got[e] - fd) <= 1e-6 * max(1.0, abs(fd)), (e, got[e], fd)
+    assert got[8] == 0.0  # the self-loop
+    assert got[0] == got[7]  # both listings of {0, 1}
+
+
+@pytest.mark.parametrize("which", [1, 2])
+def test_sparse_objective_of_weights_matches_dense(which):
+    """The sparse FP64 objective of the listed weights equals Eqs. (2)/(3) written out densely."""
+    rng = np.random.default_rng(31 + which)
+    n, k = 14, 4
+    src = rng.integers(0, n, 40)
+    dst = rng.integers(0, n, 40)
+    w = rng.uniform(0.5, 1.5, 40)
+    X = rng.standard_normal((n, k)) * 0.3
+    got = o.objective_of_weights(n, src, dst, w, X, which)
+    ref = _objective_of_weights(n, src, dst, w, X, which)
+    assert abs(got - ref) <= 1e-12 * max(1.0, abs(ref))

@@ -333,6 +333,119 @@ def run_stream(args):
     return 0
 
 
+def run_batch(args):
+    """A batch of independent graphs (synth.BATCHES): one step = ofsc_iterate_batched over all of
+    them, `iters` updates each from their X0. `value` = updates summed over the graphs per second.
+    The same steps are also timed with direct launches (no CUDA graph replay) and as a loop of
+    one ofsc_iterate call per graph."""
+    import torch
+
+    world, rank, local = dist_setup("nccl")
+    torch.cuda.set_device(local)
+    from paper_2305_10356_gb300 import build, ofsc, synth
+    build.build()
+    spec = synth.BATCHES[args.workload]
+    scale = 1.0 if args.nodes is None else args.nodes / 51_000.0
+    probs = synth.batch(args.workload, scale)
+    method = METHODS[args.method]
+    gather = ofsc.GATHER_BF16 if args.gather == "bf16" else ofsc.GATHER_FP32
+    graphs, X0s = [], []
+    for e, x0 in probs:
+        src, dst = torch.from_numpy(e.src).cuda(), torch.from_numpy(e.dst).cuda()
+        graphs.append(ofsc.ofsc_graph_build(e.n, src, dst))
+        X0s.append(torch.from_numpy(x0).cuda())
+    nnz = sum(int(g.info().nnz) for g in graphs)
+    Xs = [torch.empty_like(x) for x in X0s]
+    stream = torch.cuda.current_stream()
+
+    def step_batched(direct=False):
+        for X, X0 in zip(Xs, X0s):
+            X.copy_(X0)
+        rs = ofsc.ofsc_iterate_batched(graphs, method, Xs, 0.0, args.iters, gather=gather, direct_launch=direct)
+        return sum(r.iterations for r in rs), sum(r.kernel_launches for r in rs) + len(Xs)
+
+    def step_loop():
+        n_up = 0
+        for g, X, X0 in zip(graphs, Xs, X0s):
+            X.copy_(X0)
+            n_up += ofsc.ofsc_iterate(g, method, X, 0.0, args.iters, gather=gather).iterations
+        return n_up, 0
+
+    def timed(fn, with_clocks=False):
+        for _ in range(args.warmup):
+            fn()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        sampler = None
+        if with_clocks:
+            dev_id = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local if world > 1 else 0]
+            try:
+                dev_id = "GPU-" + str(torch.cuda.get_device_properties(local).uuid).replace("GPU-", "")
+            except Exception:
+                pass
+            sampler = ClockSampler(dev_id)
+            sampler.start()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        ups = launches = 0
+        for _ in range(args.steps):
+            u, l = fn()
+            ups += u
+            launches += l
+        t1.record(stream)
+        torch.cuda.synchronize()
+        clocks = sampler.stop() if sampler else None
+        ms = t0.elapsed_time(t1)
+        if world > 1:
+            t = torch.tensor([ms], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        return ups * world / (ms / 1000.0), ms / args.steps, launches, clocks
+
+    value, ms, launches, clocks = timed(step_batched, with_clocks=True)
+    direct, ms_direct, _, _ = timed(lambda: step_batched(True))
+    loop, ms_loop, _, _ = timed(step_loop)
+
+    # end to end: pinned host X0 -> device, one batched call, device -> pinned host X
+    Xh0 = [x.cpu().pin_memory() for x in X0s]
+    Xh = [torch.empty_like(x) for x in Xh0]
+
+    def step_e2e():
+        for X, h in zip(Xs, Xh0):
+            X.copy_(h, non_blocking=True)
+        rs = ofsc.ofsc_iterate_batched(graphs, method, Xs, 0.0, args.iters, gather=gather)
+        for X, h in zip(Xs, Xh):
+            h.copy_(X, non_blocking=True)
+        return sum(r.iterations for r in rs), 0
+
+    e2e_v, _, _, _ = timed(step_e2e)
+    nbytes = sum(int(x.numel()) * 4 for x in X0s)
+    if rank == 0:
+        line = {"metric": "OFM iterations/s", "value": value, "unit": "iterations/s (summed over graphs)",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32" if args.gather == "fp32" else "f32 (bf16 gather storage)", "data": "synthetic",
+                "config": {"workload": f"{args.workload}: {spec['count']} SBMs, N ~ U[{spec['n'][0]}, {spec['n'][1]}] "
+                                       f"(x{scale:g}), k ~ U[{spec['k'][0]}, {spec['k'][1]}], mean degree ~ "
+                                       f"U[{spec['mean_degree'][0]:g}, {spec['mean_degree'][1]:g}], within:between "
+                                       f"{spec['ratio']:g}:1 (edge counts); sum N = {sum(x.shape[0] for x in X0s)}, "
+                                       f"sum nnz = {nnz}",
+                           "updates_per_graph_per_step": args.iters, "method": METHOD_LABEL[args.method],
+                           "gather": args.gather, "l2": "state of all graphs about 1 GB, larger than L2"},
+                "impl": "gpu", "e2e": {"value": e2e_v, "unit": "iterations/s (summed over graphs)",
+                                       "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+                "clocks": clocks, "gpu_launches": launches,
+                "batched_direct_launch": {"value": direct, "ms_per_step": ms_direct},
+                "per_graph_loop": {"value": loop, "ms_per_step": ms_loop},
+                "parallelism": "replicas only" if world > 1 else "single GPU"}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -495,6 +608,8 @@ def main():
     from paper_2305_10356_gb300 import synth
     if args.workload in synth.STREAMS:
         return run_stream(args)
+    if args.workload in synth.BATCHES:
+        return run_batch(args)
     return run_gpu(args)
 
 

@@ -170,6 +170,9 @@ typedef struct {
   int32_t gram_engine;   /* OFSC_GRAM_AUTO (tensor cores when k > 64), OFSC_GRAM_SIMT, OFSC_GRAM_TC */
   int32_t spmm_engine;   /* OFSC_SPMM_AUTO (= OFSC_SPMM_SIMT: one warp per row, CUDA-core gathers),
                             OFSC_SPMM_TMA (tile::gather4 into shared memory; padded k 64 or 128) */
+  int32_t direct_launch; /* ofsc_iterate_batched only: 0 (default) replays the updates whose
+                            launches repeat from one captured CUDA graph; 1 launches every kernel
+                            directly (same results, bit for bit) */
 } ofsc_opts;
 
 typedef struct {
@@ -202,6 +205,30 @@ typedef struct {
  */
 ofsc_status ofsc_iterate(ofsc_graph* g, int32_t method, int32_t k, float* X, double tol,
                          int32_t maxit, const ofsc_opts* opts, ofsc_result* out, void* stream);
+
+/*
+ * ofsc_iterate_batched - ofsc_iterate (Algorithm 2) on `count` independent graphs in one call, for
+ * many small independent problems of uneven sizes.
+ *   count    number of problems (>= 0)
+ *   graphs   HOST array [count] of distinct handles
+ *   method   one method for every problem
+ *   ks       HOST int32 [count]: columns of each problem (1 <= k <= 128)
+ *   Xs       HOST array [count] of device float32 [n_i x k_i]: in = X0, out = final X
+ *   tol, maxit, opts   as for ofsc_iterate, shared by every problem; opts->trace and
+ *            opts->profile must be NULL
+ *   outs     HOST ofsc_result [count] (nullable), one per problem, in input order
+ * Each problem runs on a stream owned by its handle, ordered after `stream` on entry and before it
+ * on return; the problems advance in lockstep and share the SMs. Every problem gets exactly the
+ * launches, in the same order, that ofsc_iterate would give it, so each result and each X equals
+ * that of ofsc_iterate on the same problem bit for bit. The call returns when every problem has
+ * met tol or maxit is reached. Synchronises `stream`.
+ * Returns OFSC_OK when every problem converged, else the first error among them, else
+ * OFSC_ERR_NOT_CONVERGED. Errors: OFSC_ERR_INVALID_ARG (any problem's arguments, a repeated
+ * handle, trace or profile set), OFSC_ERR_OOM, OFSC_ERR_NONFINITE, OFSC_ERR_CUDA.
+ */
+ofsc_status ofsc_iterate_batched(int32_t count, ofsc_graph* const* graphs, int32_t method,
+                                 const int32_t* ks, float* const* Xs, double tol, int32_t maxit,
+                                 const ofsc_opts* opts, ofsc_result* outs, void* stream);
 
 /*
  * ofsc_weight_grad - gradient of f1 (Eq. (2)) or f2 (Eq. (3)) at X with respect to the weight of

@@ -58,6 +58,7 @@ void workspace_free(Workspace& ws) {
   cudaFree(ws.beta64);
   cudaFree(ws.colpart);
   cudaFree(ws.dE);
+  cudaFree(ws.solve);
   cudaFree(ws.ctrl);
   if (ws.ctrl_host) cudaFreeHost(ws.ctrl_host);
   for (cudaEvent_t e : ws.events) cudaEventDestroy(e);
@@ -84,6 +85,7 @@ ofsc_status ofsc_graph_free(ofsc_graph* g) {
   cudaFree(g->dinv);
   cudaFree(g->deg);
   for (int i = 0; i < 6; ++i) cudaFree(g->bnd[i]);
+  if (g->stream) cudaStreamDestroy(g->stream);
   cudaSetDevice(prev);
   delete g;
   return OFSC_OK;

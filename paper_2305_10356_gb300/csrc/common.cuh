@@ -137,6 +137,7 @@ struct Workspace {
   double* beta64 = nullptr;     // kp
   double* colpart = nullptr;    // [row_blocks][5][kp]
   double* dE = nullptr;         // kp: diag(V^T AX) (f1 methods)
+  double* solve = nullptr;      // line-search scratch: per-block trace partials, diagonals, cubics
   Ctrl* ctrl = nullptr;
   Ctrl* ctrl_host = nullptr;    // pinned
   int gram_gy = 0;
@@ -170,6 +171,7 @@ struct ofsc_graph {
   int64_t* bnd[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   int groups[6] = {0, 0, 0, 0, 0, 0};
   ofsc::Workspace ws;
+  cudaStream_t stream = nullptr;  // this graph's stream in ofsc_iterate_batched (created on first use)
 };
 
 namespace ofsc {

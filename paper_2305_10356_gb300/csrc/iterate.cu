@@ -19,7 +19,9 @@
 
 #include <algorithm>
 #include <cmath>
+#include <memory>
 #include <mutex>
+#include <vector>
 
 #include "common.cuh"
 
@@ -685,6 +687,7 @@ __global__ void k_fold_rows(const double* __restrict__ part, int nb, int width, 
   const int b0 = (int)((int64_t)r * nb / R), b1 = (int)((int64_t)(r + 1) * nb / R);
   for (int t = threadIdx.x; t < width; t += blockDim.x) {
     double sum = 0.0;
+#pragma unroll 8
     for (int b = b0; b < b1; ++b) sum += part[(int64_t)b * width + t];
     out[(int64_t)r * width + t] = sum;
   }
@@ -697,6 +700,7 @@ __global__ void k_beta(const double* __restrict__ colpart, int nblk, int kp, flo
   const int j = threadIdx.x;
   double gg = 0.0, num = 0.0, den = 0.0, gy = 0.0, vy = 0.0, vg = 0.0;
   if (j < kp) {
+#pragma unroll 8
     for (int b = 0; b < nblk; ++b) {
       const double* p = colpart + (int64_t)b * kColSums * kp;
       gg += p[j];
@@ -1012,6 +1016,9 @@ __device__ void block_sum(double (&v)[NV], double* sh) {
   __syncthreads();
 }
 
+constexpr int kSolveBlocks = 128;  // blocks of the trace and update passes (>= kMaxK: one column each)
+constexpr int kSolveSums = 16;     // per-block partial sums of the trace pass
+
 struct SolveArgs {
   const double* gram;  // [6][kp*kp]: V^T X (P), V^T V (Q); f2 methods also V^T AX (E), V^T AV (C)
   const double* dots;  // [dots_blocks][2][kp] partials of diag(V^T AV), diag(V^T G)
@@ -1030,159 +1037,197 @@ struct SolveArgs {
   double* trace;
   Ctrl* ctrl;
   double alpha0;  // > 0: fixed step for update 0 instead of the line search
+  double* part;   // scratch: [kSolveBlocks][kSolveSums] trace partials, [kp][4] diagonals, [kp][4] cubics
 };
 
-__global__ void __launch_bounds__(256) k_solve(SolveArgs a) {
+// C = V^T A V and B = X^T A X are symmetric; the recurrences leave rounding asymmetry.
+#define SYM(M, i, j) (0.5 * ((M)[(i) * kp + (j)] + (M)[(j) * kp + (i)]))
+
+// Line search, pass 1 of 3 (kSolveBlocks blocks). Block b: the diagonals diag(V^T AV), diag(V^T AX)
+// and diag(V^T G) of column b; for TriOFM the cubic of column b alone (Eqs. (16)/(18) before the
+// prefix sum); and its slice of the k x k traces that make up f(X_t) and the OFM cubic (Eq. (15)).
+// Per-block partial sums go to a.part in a fixed order. Partial layout (v[0..14]):
+//   v[0..2]   tr B, ||R||_F^2, tr(R B)                         (objective)
+//   v[3..8]   tr(QQ), tr(QP), tr(PP), tr(PP^T), tr(QR), tr(PR)  (OFM-f1 cubic)
+//   v[3..13]  tr(QC) ... tr(RE), tr C, tr E                     (OFM-f2 cubic)
+__global__ void __launch_bounds__(256) k_solve_traces(SolveArgs a) {
   if (a.ctrl->done) return;
-  __shared__ double sh[12 * 256];  // block_sum scratch for up to 12 values
-  __shared__ double coef[kMaxK][4];
-  __shared__ double al[kMaxK];
-  __shared__ double dC[kMaxK], dE[kMaxK], dG[kMaxK];
-  __shared__ int bad;
-  const int kp = a.kp, k = a.k, kk = kp * kp, tid = threadIdx.x;
-  const bool f2 = is_f2(a.method);
+  __shared__ double sh[15 * 256];
+  const int kp = a.kp, kk = kp * kp, tid = threadIdx.x, b = blockIdx.x, nb = gridDim.x;
+  const bool f2 = is_f2(a.method), tri = is_tri(a.method);
   const double* P = a.gram + G_P * kk;
   const double* Q = a.gram + G_Q * kk;
   const double* E = a.gram + G_E * kk;
   const double* C = a.gram + G_C * kk;
   const double* R = a.R64;
   const double* B = a.B64;
-  // C = V^T A V and B = X^T A X are symmetric; the recurrences leave rounding asymmetry.
-#define SYM(M, i, j) (0.5 * ((M)[(i) * kp + (j)] + (M)[(j) * kp + (i)]))
-  if (tid == 0) bad = 0;
-  for (int j = tid; j < kp; j += blockDim.x) {
-    double sc = 0.0, sg = 0.0;
-    for (int b = 0; b < a.dots_blocks; ++b) {
-      sc += a.dots[(int64_t)b * 2 * kp + j];
-      sg += a.dots[(int64_t)b * 2 * kp + kp + j];
+  double* diag = a.part + kSolveBlocks * kSolveSums;  // [kp][4]: dC, dE, dG
+  double* coef = diag + 4 * kp;                       // [kp][4]: cubic of column j alone
+  for (int j = b; j < kp; j += nb) {
+    double s2[2] = {0.0, 0.0};
+    for (int r = tid; r < a.dots_blocks; r += 256) {
+      s2[0] += a.dots[(int64_t)r * 2 * kp + j];
+      s2[1] += a.dots[(int64_t)r * 2 * kp + kp + j];
     }
+    block_sum<2>(s2, sh);
     // The constant term of every cubic is the derivative along V at alpha = 0, i.e. diag(V^T G)
     // (with the 1/4 of Eq. (15) for OFM-f1): summing v.g directly avoids the cancellation in
     // tr(V^T AX) + tr(V^T X X^T X) near a fixed point, where AX = -X X^T X.
-    dG[j] = sg;
-    if (f2) {
-      dC[j] = C[j * kp + j];
-      dE[j] = E[j * kp + j];
-    } else {
-      dC[j] = sc;
-      dE[j] = a.dE[j];
-    }
-  }
-  // objective at X_t: f1 = ||A||^2 + 2 tr B + ||R||^2, f2 = 2 tr B - tr(R B)
-  double fv[3] = {0.0, 0.0, 0.0};
-  for (int i = tid; i < kk; i += 256) {
-    const int r = i / kp, c = i % kp;
-    const double rij = R[i];
-    fv[1] += rij * rij;
-    if (f2) {
-      fv[2] += rij * SYM(B, c, r);
-      if (r == c) fv[0] += B[i];
-    }
-  }
-  block_sum<3>(fv, sh);  // also orders the dC/dE writes before their use
-  const double trB = f2 ? fv[0] : a.ctrl->trB;
-  const double f = f2 ? 2.0 * trB - fv[2] : a.ctrl->normA2 + 2.0 * trB + fv[1];
-
-  if (!is_tri(a.method)) {
-    double c3, c2, c1, c0;
-    if (a.method == M_OFM_F1) {
-      // (1/4) d/dalpha f1(X + alpha V) = tr(V^T A (X + aV)) + tr(V^T Z Z^T Z), Z = X + aV
-      double t[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-      for (int i = tid; i < kk; i += 256) {
-        const int r = i / kp, c = i % kp, it = c * kp + r;
-        const double q = Q[i], p = P[i];
-        t[0] += q * Q[it];  // tr(Q Q)
-        t[1] += q * P[it];  // tr(Q P)
-        t[2] += p * P[it];  // tr(P P)
-        t[3] += p * p;      // tr(P P^T)
-        t[4] += q * R[it];  // tr(Q R)
-        t[5] += p * R[it];  // tr(P R)
-      }
-      for (int j = tid; j < kp; j += 256) {
-        t[6] += dC[j];
-        t[7] += dG[j];
-      }
-      block_sum<8>(t, sh);
-      c3 = t[0];
-      c2 = 3.0 * t[1];
-      c1 = t[6] + t[2] + t[3] + t[4];
-      c0 = 0.25 * t[7];  // = tr(E) + tr(P R) with G = grad f1 = 4 (AX + X X^T X)
-    } else {
-      // d/dalpha f2 = tr(V^T (4 A Z - 2 Z Z^T A Z - 2 A Z Z^T Z)), Z = X + aV
-      double t[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-      for (int j = tid; j < kp; j += 256) t[11] += dG[j];
-      for (int i = tid; i < kk; i += 256) {
-        const int r = i / kp, c = i % kp, it = c * kp + r;
-        const double q = Q[i], p = P[i], rr = R[i], e = E[i];
-        const double cji = SYM(C, c, r), bji = SYM(B, c, r);
-        t[0] += q * cji;     // tr(Q C)
-        t[1] += p * cji;     // tr(P C)
-        t[2] += q * E[it];   // tr(Q E)
-        t[3] += p * e;       // tr(P E^T)
-        t[4] += p * E[it];   // tr(P E)
-        t[5] += q * bji;     // tr(Q B)
-        t[6] += rr * cji;    // tr(R C)
-        t[7] += p * bji;     // tr(P B)
-        t[8] += rr * E[it];  // tr(R E)
-        if (r == c) {
-          t[9] += C[i];
-          t[10] += e;
-        }
-      }
-      block_sum<12>(t, sh);
-      c3 = -4.0 * t[0];
-      c2 = -6.0 * (t[1] + t[2]);
-      c1 = 2.0 * (2.0 * t[9] - 2.0 * t[3] - 2.0 * t[4] - t[5] - t[6]);
-      c0 = t[11];  // = 2 tr(2E - P B - R E) = tr(V^T grad f2)
-    }
+    const double dC = f2 ? C[j * kp + j] : s2[0];
+    const double dE = f2 ? E[j * kp + j] : a.dE[j];
+    const double dG = s2[1];
     if (tid == 0) {
-      int b = 0;
-      const double st = pick_step(c3, c2, c1, c0, &b);
-      bad |= b;
-      for (int j = 0; j < kp; ++j) al[j] = j < k ? st : 0.0;
+      diag[4 * j + 0] = dC;
+      diag[4 * j + 1] = dE;
+      diag[4 * j + 2] = dG;
     }
-  } else {
-    // Column j of g(X + aV) depends on columns 1..j only, so the prefix-i cubic of Eqs. (16)/(18)
-    // is the sum over j <= i of v_j^T g(X + aV)_j; each term is a product of two polynomials in a.
-    if (tid < kp) {
-      const int j = tid;
-      double d0 = 0, d1 = 0, d2 = 0, d3 = 0;
-      if (a.method == M_TRI_F1) {
-        d1 = dC[j];
-        for (int m = 0; m <= j; ++m) {
+    if (tri) {
+      // Column j of g(X + aV) depends on columns 1..j only, so its term of the prefix cubic is
+      // v_j^T g(X + aV)_j, a sum over m <= j of products of two polynomials in a.
+      double d[3] = {0.0, 0.0, 0.0};  // a^1, a^2, a^3
+      for (int m = tid; m <= j; m += 256) {
+        if (a.method == M_TRI_F1) {
           // (P_jm + a Q_jm)(R_mj + a (P_jm + P_mj) + a^2 Q_mj)
           const double x0 = P[j * kp + m], x1 = Q[j * kp + m];
           const double y0 = R[m * kp + j], y1 = P[j * kp + m] + P[m * kp + j], y2 = Q[m * kp + j];
-          d1 += x0 * y1 + x1 * y0;
-          d2 += x0 * y2 + x1 * y1;
-          d3 += x1 * y2;
-        }
-        d0 = dG[j];  // = E_jj + sum_{m<=j} P_jm R_mj = v_j^T g1_j
-      } else {
-        d1 = 2.0 * dC[j];
-        for (int m = 0; m <= j; ++m) {
+          d[0] += x0 * y1 + x1 * y0;
+          d[1] += x0 * y2 + x1 * y1;
+          d[2] += x1 * y2;
+        } else {
           // -(E_jm + a C_jm)(R_mj + a (P_jm + P_mj) + a^2 Q_mj)
           const double x0 = E[j * kp + m], x1 = SYM(C, j, m);
           const double y0 = R[m * kp + j], y1 = P[j * kp + m] + P[m * kp + j], y2 = Q[m * kp + j];
           // -(P_jm + a Q_jm)(B_mj + a (E_jm + E_mj) + a^2 C_mj)
           const double u0 = P[j * kp + m], u1 = Q[j * kp + m];
           const double w0 = SYM(B, m, j), w1 = E[j * kp + m] + E[m * kp + j], w2 = SYM(C, m, j);
-          d1 -= x0 * y1 + x1 * y0 + u0 * w1 + u1 * w0;
-          d2 -= x0 * y2 + x1 * y1 + u0 * w2 + u1 * w1;
-          d3 -= x1 * y2 + u1 * w2;
+          d[0] -= x0 * y1 + x1 * y0 + u0 * w1 + u1 * w0;
+          d[1] -= x0 * y2 + x1 * y1 + u0 * w2 + u1 * w1;
+          d[2] -= x1 * y2 + u1 * w2;
         }
-        d0 = dG[j];  // = 2 E_jj - sum_{m<=j} (E_jm R_mj + P_jm B_mj) = v_j^T g2_j
       }
-      coef[j][0] = d3;
-      coef[j][1] = d2;
-      coef[j][2] = d1;
-      coef[j][3] = d0;
+      block_sum<3>(d, sh);
+      if (tid == 0) {
+        coef[4 * j + 0] = d[2];
+        coef[4 * j + 1] = d[1];
+        coef[4 * j + 2] = d[0] + (a.method == M_TRI_F1 ? dC : 2.0 * dC);
+        coef[4 * j + 3] = dG;  // v_j^T g_j at a = 0
+      }
+    }
+  }
+  double v[15];
+#pragma unroll
+  for (int q = 0; q < 15; ++q) v[q] = 0.0;
+  for (int i = b * 256 + tid; i < kk; i += nb * 256) {
+    const int r = i / kp, c = i % kp, it = c * kp + r;
+    const double rr = R[i];
+    v[1] += rr * rr;
+    if (f2) {
+      v[2] += rr * SYM(B, c, r);
+      if (r == c) v[0] += B[i];
+    }
+    if (tri) continue;
+    const double q = Q[i], p = P[i];
+    if (a.method == M_OFM_F1) {
+      v[3] += q * Q[it];
+      v[4] += q * P[it];
+      v[5] += p * P[it];
+      v[6] += p * p;
+      v[7] += q * R[it];
+      v[8] += p * R[it];
+    } else {
+      const double e = E[i], cji = SYM(C, c, r), bji = SYM(B, c, r);
+      v[3] += q * cji;      // tr(Q C)
+      v[4] += p * cji;      // tr(P C)
+      v[5] += q * E[it];    // tr(Q E)
+      v[6] += p * e;        // tr(P E^T)
+      v[7] += p * E[it];    // tr(P E)
+      v[8] += q * bji;      // tr(Q B)
+      v[9] += rr * cji;     // tr(R C)
+      v[10] += p * bji;     // tr(P B)
+      v[11] += rr * E[it];  // tr(R E)
+      if (r == c) {
+        v[12] += C[i];
+        v[13] += e;
+      }
+    }
+  }
+  block_sum<15>(v, sh);
+  if (tid == 0) {
+#pragma unroll
+    for (int q = 0; q < 15; ++q) a.part[b * kSolveSums + q] = v[q];
+  }
+}
+
+// Line search, pass 2 of 3 (one block): f(X_t), the cubic coefficients and their roots, i.e. the
+// step(s) alpha, written to a.alpha / a.alpha64; also the objective, the trace record and the
+// running tr(X^T AX) of the f1 methods.
+__global__ void __launch_bounds__(256) k_solve(SolveArgs a) {
+  if (a.ctrl->done) return;
+  __shared__ double sh[15 * 256];
+  __shared__ double coef[kMaxK][4];
+  __shared__ double al[kMaxK];
+  __shared__ int bad;
+  const int kp = a.kp, k = a.k, tid = threadIdx.x;
+  const bool f2 = is_f2(a.method);
+  const double* diag = a.part + kSolveBlocks * kSolveSums;
+  if (tid == 0) bad = 0;
+  double v[15];
+#pragma unroll
+  for (int q = 0; q < 15; ++q) v[q] = tid < kSolveBlocks ? a.part[tid * kSolveSums + q] : 0.0;
+  if (tid < kp) {
+    if (f2) {
+      v[14] += diag[4 * tid + 2];  // tr(V^T G)
+    } else {
+      v[9] += diag[4 * tid + 0];   // tr(V^T AV)
+      v[10] += diag[4 * tid + 2];  // tr(V^T G)
+    }
+  }
+  block_sum<15>(v, sh);  // also orders bad = 0 before its use
+  // objective at X_t: f1 = ||A||^2 + 2 tr B + ||R||^2, f2 = 2 tr B - tr(R B)
+  const double trB = f2 ? v[0] : a.ctrl->trB;
+  const double f = f2 ? 2.0 * trB - v[2] : a.ctrl->normA2 + 2.0 * trB + v[1];
+
+  if (!is_tri(a.method)) {
+    double c3, c2, c1, c0;
+    if (a.method == M_OFM_F1) {
+      // (1/4) d/dalpha f1(X + alpha V) = tr(V^T A (X + aV)) + tr(V^T Z Z^T Z), Z = X + aV
+      c3 = v[3];
+      c2 = 3.0 * v[4];
+      c1 = v[9] + v[5] + v[6] + v[7];
+      c0 = 0.25 * v[10];  // = tr(E) + tr(P R) with G = grad f1 = 4 (AX + X X^T X)
+    } else {
+      // d/dalpha f2 = tr(V^T (4 A Z - 2 Z Z^T A Z - 2 A Z Z^T Z)), Z = X + aV
+      c3 = -4.0 * v[3];
+      c2 = -6.0 * (v[4] + v[5]);
+      c1 = 2.0 * (2.0 * v[12] - 2.0 * v[6] - 2.0 * v[7] - v[8] - v[9]);
+      c0 = v[14];  // = 2 tr(2E - P B - R E) = tr(V^T grad f2)
+    }
+    // one thread solves the cubic (FP64 issue is scarce: 8 warps solving it would cost 8x)
+    if (tid == 0) {
+      int b = 0;
+      const double st = pick_step(c3, c2, c1, c0, &b);
+      bad |= b;
+      al[0] = st;
     }
     __syncthreads();
-    if (tid == 0)
-      for (int j = 1; j < kp; ++j)
-        for (int q = 0; q < 4; ++q) coef[j][q] += coef[j - 1][q];
+    const double st = al[0];
     __syncthreads();
+    for (int j = tid; j < kp; j += 256) al[j] = j < k ? st : 0.0;
+  } else {
+    // prefix sums over columns of the per-column cubics (Hillis-Steele, kp <= 256 threads)
+    const double* cg = diag + 4 * kp;
+    if (tid < kp)
+      for (int q = 0; q < 4; ++q) coef[tid][q] = cg[4 * tid + q];
+    __syncthreads();
+    for (int off = 1; off < kp; off <<= 1) {
+      double t4[4] = {0.0, 0.0, 0.0, 0.0};
+      if (tid < kp && tid >= off)
+        for (int q = 0; q < 4; ++q) t4[q] = coef[tid - off][q];
+      __syncthreads();
+      if (tid < kp)
+        for (int q = 0; q < 4; ++q) coef[tid][q] += t4[q];
+      __syncthreads();
+    }
     if (tid < kp) {
       int b = 0;
       al[tid] = tid < k ? pick_step(coef[tid][0], coef[tid][1], coef[tid][2], coef[tid][3], &b) : 0.0;
@@ -1194,51 +1239,68 @@ __global__ void __launch_bounds__(256) k_solve(SolveArgs a) {
     for (int j = tid; j < kp; j += 256) al[j] = j < k ? a.alpha0 : 0.0;
     __syncthreads();
   }
-  // X' = X + V diag(al), AX' = AX + AV diag(al):
-  //   X'^T X'  = R + diag(al) P + P^T diag(al) + diag(al) Q diag(al)
-  //   X'^T AX' = B + E^T diag(al) + diag(al) E + diag(al) C diag(al)
-  for (int i = tid; i < kk; i += 256) {
-    const int r = i / kp, c = i % kp;
-    const double ar = al[r], ac = al[c];
-    const double rn = R[i] + ar * P[i] + P[c * kp + r] * ac + ar * Q[i] * ac;
-    a.R64[i] = rn;
-    a.Rn[i] = (float)rn;
-    if (f2) {
-      // B is symmetric up to rounding; read only this thread's element (B64 is updated in place)
-      const double bn = B[i] + E[c * kp + r] * ac + ar * E[i] + ar * SYM(C, r, c) * ac;
-      a.B64[i] = bn;
-      a.Bn[i] = (float)bn;
-    }
-  }
   for (int j = tid; j < kp; j += 256) {
     a.alpha[j] = (float)al[j];
     a.alpha64[j] = al[j];
   }
+  if (!f2) {  // tr(X'^T AX') = tr B + 2 sum al_j E_jj + sum al_j^2 C_jj
+    double t1[1] = {0.0};
+    for (int j = tid; j < kp; j += 256) t1[0] += 2.0 * al[j] * diag[4 * j + 1] + al[j] * al[j] * diag[4 * j + 0];
+    block_sum<1>(t1, sh);
+    if (tid == 0) a.ctrl->trB = trB + t1[0];
+  }
+  const int t = a.ctrl->it;
+  if (a.trace && t < a.ctrl->trace_cap) {
+    double* rec = a.trace + (int64_t)t * (3 + 2 * k);
+    if (tid == 0) {
+      rec[0] = t;
+      rec[1] = a.ctrl->rel;
+      rec[2] = f;
+    }
+    for (int j = tid; j < k; j += 256) {
+      rec[3 + j] = al[j];
+      rec[3 + k + j] = a.beta64[j];
+    }
+  }
+  __syncthreads();
   if (tid == 0) {
     a.ctrl->f = f;
-    if (!f2) {  // tr(X'^T AX') = tr B + 2 sum al_j E_jj + sum al_j^2 C_jj
-      double tb = trB;
-      for (int j = 0; j < kp; ++j) tb += 2.0 * al[j] * dE[j] + al[j] * al[j] * dC[j];
-      a.ctrl->trB = tb;
-    }
     if (bad) {
       a.ctrl->status = OFSC_ERR_NONFINITE;
       a.ctrl->done = 1;
     }
-    const int t = a.ctrl->it;
-    if (a.trace && t < a.ctrl->trace_cap) {
-      double* rec = a.trace + (int64_t)t * (3 + 2 * k);
-      rec[0] = t;
-      rec[1] = a.ctrl->rel;
-      rec[2] = f;
-      for (int j = 0; j < k; ++j) {
-        rec[3 + j] = al[j];
-        rec[3 + k + j] = a.beta64[j];
-      }
+  }
+}
+
+// Line search, pass 3 of 3 (kSolveBlocks blocks): X' = X + V diag(al), AX' = AX + AV diag(al) give
+//   X'^T X'  = R + diag(al) P + P^T diag(al) + diag(al) Q diag(al)
+//   X'^T AX' = B + E^T diag(al) + diag(al) E + diag(al) C diag(al)
+// element by element in FP64 (each element read and written by one thread, so in place).
+__global__ void __launch_bounds__(256) k_solve_update(SolveArgs a) {
+  if (a.ctrl->done) return;
+  __shared__ double al[kMaxK];
+  const int kp = a.kp, kk = kp * kp, tid = threadIdx.x;
+  const bool f2 = is_f2(a.method);
+  const double* P = a.gram + G_P * kk;
+  const double* Q = a.gram + G_Q * kk;
+  const double* E = a.gram + G_E * kk;
+  const double* C = a.gram + G_C * kk;
+  for (int j = tid; j < kp; j += 256) al[j] = a.alpha64[j];
+  __syncthreads();
+  for (int i = blockIdx.x * 256 + tid; i < kk; i += gridDim.x * 256) {
+    const int r = i / kp, c = i % kp;
+    const double ar = al[r], ac = al[c];
+    const double rn = a.R64[i] + ar * P[i] + P[c * kp + r] * ac + ar * Q[i] * ac;
+    a.R64[i] = rn;
+    a.Rn[i] = (float)rn;
+    if (f2) {
+      const double bn = a.B64[i] + E[c * kp + r] * ac + ar * E[i] + ar * SYM(C, r, c) * ac;
+      a.B64[i] = bn;
+      a.Bn[i] = (float)bn;
     }
   }
-#undef SYM
 }
+#undef SYM
 
 // Exact refresh: X^T X and X^T AX of the current X from their Grams; objective of X.
 __global__ void k_set_rb(const double* __restrict__ gram, int kp, int objective, float* Rn, float* Bn,
@@ -1539,6 +1601,7 @@ ofsc_status ensure_workspace(ofsc_graph* g, int kp) {
       {(void**)&ws.beta64, kp * sizeof(double)},
       {(void**)&ws.colpart, (size_t)(kMaxRowBlocks + kDotsRows) * kColSums * kp * sizeof(double)},
       {(void**)&ws.dE, (size_t)kp * sizeof(double)},
+      {(void**)&ws.solve, (size_t)(kSolveBlocks * kSolveSums + 8 * kp) * sizeof(double)},
       {(void**)&ws.ctrl, sizeof(Ctrl)},
   };
   size_t total = 0;
@@ -1766,9 +1829,12 @@ struct Runner {
     sa.trace = o.trace;
     sa.ctrl = ws.ctrl;
     sa.alpha0 = alpha0;
+    sa.part = ws.solve;
     prof.begin(OFSC_PHASE_LINESEARCH);
+    k_solve_traces<<<kSolveBlocks, 256, 0, s>>>(sa);
     k_solve<<<1, 256, 0, s>>>(sa);
-    ++g_launches;
+    k_solve_update<<<kSolveBlocks, 256, 0, s>>>(sa);
+    g_launches += 3;
     prof.end();
     return cudaGetLastError();
   }
@@ -1941,67 +2007,93 @@ extern "C" ofsc_status ofsc_rayleigh_ritz(ofsc_graph* g, int32_t k, const float*
   return OFSC_OK;
 }
 
-extern "C" ofsc_status ofsc_iterate(ofsc_graph* g, int32_t method, int32_t k, float* X, double tol,
-                                    int32_t maxit, const ofsc_opts* opts, ofsc_result* out, void* stream_) {
-  clear_error();
-  if (!g) return fail(OFSC_ERR_INVALID_ARG, "ofsc_iterate: graph is NULL");
-  if (method < OFSC_OFM_F1 || method > OFSC_TRI_F2)
-    return fail(OFSC_ERR_INVALID_ARG, "ofsc_iterate: unknown method %d", method);
-  if (k < 1 || k > kMaxK) return fail(OFSC_ERR_INVALID_ARG, "ofsc_iterate: k=%d outside [1, %d]", k, kMaxK);
-  if (maxit < 0) return fail(OFSC_ERR_INVALID_ARG, "ofsc_iterate: maxit < 0");
-  if (!(tol == tol)) return fail(OFSC_ERR_INVALID_ARG, "ofsc_iterate: tol is NaN");
-  if (g->n > 0 && !X) return fail(OFSC_ERR_INVALID_ARG, "ofsc_iterate: X is NULL");
-  ofsc_opts o{};
-  if (opts) o = *opts;
+namespace ofsc {
+namespace {
+
+// Argument checks shared by the single and batched entry points (no launches).
+ofsc_status check_iterate_args(const ofsc_graph* g, int32_t method, int32_t k, const float* X, double tol,
+                               int32_t maxit, const ofsc_opts& o, const char* who) {
+  if (!g) return fail(OFSC_ERR_INVALID_ARG, "%s: graph is NULL", who);
+  if (method < OFSC_OFM_F1 || method > OFSC_TRI_F2) return fail(OFSC_ERR_INVALID_ARG, "%s: unknown method %d", who, method);
+  if (k < 1 || k > kMaxK) return fail(OFSC_ERR_INVALID_ARG, "%s: k=%d outside [1, %d]", who, k, kMaxK);
+  if (maxit < 0) return fail(OFSC_ERR_INVALID_ARG, "%s: maxit < 0", who);
+  if (!(tol == tol)) return fail(OFSC_ERR_INVALID_ARG, "%s: tol is NaN", who);
+  if (g->n > 0 && !X) return fail(OFSC_ERR_INVALID_ARG, "%s: X is NULL", who);
   if (o.gather != OFSC_GATHER_FP32 && o.gather != OFSC_GATHER_BF16)
-    return fail(OFSC_ERR_INVALID_ARG, "ofsc_iterate: unknown gather mode %d", o.gather);
-  if (o.trace && o.trace_cap < 0) return fail(OFSC_ERR_INVALID_ARG, "ofsc_iterate: trace_cap < 0");
+    return fail(OFSC_ERR_INVALID_ARG, "%s: unknown gather mode %d", who, o.gather);
+  if (o.trace && o.trace_cap < 0) return fail(OFSC_ERR_INVALID_ARG, "%s: trace_cap < 0", who);
   if (o.gram_engine < OFSC_GRAM_AUTO || o.gram_engine > OFSC_GRAM_TC)
-    return fail(OFSC_ERR_INVALID_ARG, "ofsc_iterate: unknown gram_engine %d", o.gram_engine);
+    return fail(OFSC_ERR_INVALID_ARG, "%s: unknown gram_engine %d", who, o.gram_engine);
   if (o.spmm_engine < OFSC_SPMM_AUTO || o.spmm_engine > OFSC_SPMM_TMA)
-    return fail(OFSC_ERR_INVALID_ARG, "ofsc_iterate: unknown spmm_engine %d", o.spmm_engine);
-  const int y_refresh = o.y_refresh > 0 ? o.y_refresh : 32;
-  const int check_every = o.check_every > 0 ? o.check_every : 16;
-  cudaStream_t s = (cudaStream_t)stream_;
-  if (out) *out = ofsc_result{0, OFSC_OK, 0.0, 0.0, 0.0, 0};
-  if (g->n == 0) {
-    if (out) out->status = OFSC_OK;
+    return fail(OFSC_ERR_INVALID_ARG, "%s: unknown spmm_engine %d", who, o.spmm_engine);
+  const int kp = round_up(k, 8);
+  const bool tc = o.gram_engine == OFSC_GRAM_TC || (o.gram_engine == OFSC_GRAM_AUTO && kp > 64);
+  if (tc && kp > 128) return fail(OFSC_ERR_INVALID_ARG, "%s: tensor-core Grams need k <= 128", who);
+  if (o.spmm_engine == OFSC_SPMM_TMA && !spmm_tma_supported(kp))
+    return fail(OFSC_ERR_INVALID_ARG, "%s: the TMA sparse product needs a padded k of 64 or 128", who);
+  return OFSC_OK;
+}
+
+// One graph's run of Algorithm 2 on one stream: setup, the update of iteration t (no host reads),
+// and the final report. ofsc_iterate drives one Job; ofsc_iterate_batched drives many in lockstep.
+struct Job {
+  ofsc_graph* g;
+  int method, k, kp, objective, maxit, y_refresh;
+  float* X;
+  double tol;
+  ofsc_opts o;
+  cudaStream_t s;
+  Prof prof;
+  Runner run;
+  int64_t launches = 0;  // kernels launched for this graph
+
+  Job(ofsc_graph* g_, int method_, int k_, float* X_, double tol_, int maxit_, const ofsc_opts& o_, cudaStream_t s_)
+      : g(g_), method(method_), k(k_), kp(round_up(k_, 8)),
+        objective((method_ == OFSC_OFM_F1 || method_ == OFSC_TRI_F1) ? 1 : 2), maxit(maxit_),
+        y_refresh(o_.y_refresh > 0 ? o_.y_refresh : 32), X(X_), tol(tol_), o(o_), s(s_),
+        prof{g_->ws, o_.profile, s_}, run{g_, g_->ws, s_, method_, o_.gather == OFSC_GATHER_BF16, prof} {}
+
+  // Workspace, engines and TMA maps; call before any launch (allocates, so never under capture).
+  ofsc_status prepare() {
+    ofsc_status st = ensure_workspace(g, kp);
+    if (st != OFSC_OK) return st;
+    Workspace& ws = g->ws;
+    run.tc = o.gram_engine == OFSC_GRAM_TC || (o.gram_engine == OFSC_GRAM_AUTO && kp > 64);
+    run.tma = o.spmm_engine == OFSC_SPMM_TMA;
+    if (run.tma) {
+      const int mi = run.bf16 ? 1 : 0;
+      if (!ws.vh_map_ok[mi]) {
+        st = spmm_tma_encode(ws.Vh, ws.n, kp, run.bf16, &ws.vh_map[mi]);
+        if (st != OFSC_OK) return st;
+        ws.vh_map_ok[mi] = true;
+      }
+    }
     return OFSC_OK;
   }
-  const int kp = round_up(k, 8);
-  ofsc_status st = ensure_workspace(g, kp);
-  if (st != OFSC_OK) return st;
-  Workspace& ws = g->ws;
-  g_launches = 0;
-  Prof prof{ws, o.profile, s};
-  Runner run{g, ws, s, method, o.gather == OFSC_GATHER_BF16, prof};
-  run.tc = o.gram_engine == OFSC_GRAM_TC || (o.gram_engine == OFSC_GRAM_AUTO && kp > 64);
-  if (run.tc && kp > 128) return fail(OFSC_ERR_INVALID_ARG, "ofsc_iterate: tensor-core Grams need k <= 128");
-  run.tma = o.spmm_engine == OFSC_SPMM_TMA;
-  if (run.tma && !spmm_tma_supported(kp))
-    return fail(OFSC_ERR_INVALID_ARG, "ofsc_iterate: the TMA sparse product needs a padded k of 64 or 128");
-  if (run.tma) {
-    const int mi = run.bf16 ? 1 : 0;
-    if (!ws.vh_map_ok[mi]) {
-      st = spmm_tma_encode(ws.Vh, ws.n, kp, run.bf16, &ws.vh_map[mi]);
-      if (st != OFSC_OK) return st;
-      ws.vh_map_ok[mi] = true;
-    }
+
+  // Control block, padded copy of X_0, exact AX_0 with X^T X and X^T AX.
+  ofsc_status start() {
+    const int64_t l0 = g_launches;
+    Workspace& ws = g->ws;
+    k_init_ctrl<<<1, 1, 0, s>>>(ws.ctrl, tol, maxit, k, g->normA2, o.trace ? o.trace_cap : 0);
+    ++g_launches;
+    OFSC_LAUNCH_CHECK("k_init_ctrl");
+    k_pad_in<<<grid_elems(g->n * kp), 256, 0, s>>>(g->n, k, kp, X, ws.X, ws.ctrl);
+    ++g_launches;
+    OFSC_LAUNCH_CHECK("k_pad_in");
+    OFSC_CUDA(run.refresh(objective, 0));
+    launches += g_launches - l0;
+    return OFSC_OK;
   }
-  const int objective = (method == OFSC_OFM_F1 || method == OFSC_TRI_F1) ? 1 : 2;
 
-  k_init_ctrl<<<1, 1, 0, s>>>(ws.ctrl, tol, maxit, k, g->normA2, o.trace ? o.trace_cap : 0);
-  ++g_launches;
-  OFSC_LAUNCH_CHECK("k_init_ctrl");
-  k_pad_in<<<grid_elems(g->n * kp), 256, 0, s>>>(g->n, k, kp, X, ws.X, ws.ctrl);
-  ++g_launches;
-  OFSC_LAUNCH_CHECK("k_pad_in");
-  OFSC_CUDA(run.refresh(objective, 0));
-
-  for (int t = 0; t <= maxit; ++t) {
+  // Iteration t: G_t (with the update of X_t fused in, or an exact refresh of AX every y_refresh
+  // updates), beta and the stop test, and for t < maxit the direction and the line search.
+  // Depends on t only through t == 0, t == maxit and the refresh schedule.
+  ofsc_status update(int t) {
+    const int64_t l0 = g_launches;
+    Workspace& ws = g->ws;
     int nblk = 0;
-    const bool refresh = t > 0 && (t % y_refresh) == 0;
-    if (refresh) {
+    if (is_refresh(t)) {
       prof.begin(OFSC_PHASE_OTHER);
       k_update_x<<<grid_elems(g->n * kp), 256, 0, s>>>(g->n, kp, ws.X, ws.V, ws.alpha, ws.ctrl);
       ++g_launches;
@@ -2017,44 +2109,296 @@ extern "C" ofsc_status ofsc_iterate(ofsc_graph* g, int32_t method, int32_t k, fl
     run.beta(nblk, t == 0 ? 1 : 0, 0);
     prof.end();
     OFSC_LAUNCH_CHECK("k_beta");
+    if (t < maxit) OFSC_CUDA(run.direction_and_linesearch(t == 0 ? 1 : 0, o, k, t == 0 ? o.alpha0 : 0.0));
+    launches += g_launches - l0;
+    return OFSC_OK;
+  }
+
+  bool is_refresh(int t) const { return t > 0 && (t % y_refresh) == 0; }
+  // The launches of update(t) are the same for every t with plain(t) true.
+  bool plain(int t) const { return t > 0 && t < maxit && !is_refresh(t); }
+
+  // Final report, queued: from an exact AX when the run has no error status (read by the caller
+  // into `c` after a stream synchronisation), then the unpadded X.
+  ofsc_status report(const Ctrl& c) {
+    const int64_t l0 = g_launches;
+    Workspace& ws = g->ws;
+    if (c.status == OFSC_OK) {
+      OFSC_CUDA(run.refresh(objective, 1));
+      int nblk = 0;
+      OFSC_CUDA(run.rowpass(method, 0, 1, 1, &nblk));
+      run.beta(nblk, 0, 1);
+      OFSC_LAUNCH_CHECK("k_beta(eval)");
+    }
+    k_pad_out<<<grid_elems(g->n * k), 256, 0, s>>>(g->n, k, kp, ws.X, X);
+    ++g_launches;
+    OFSC_LAUNCH_CHECK("k_pad_out");
+    OFSC_CUDA(cudaMemcpyAsync(ws.ctrl_host, ws.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+    launches += g_launches - l0;
+    return OFSC_OK;
+  }
+
+  // After the stream has drained: the result from the control block copied by report().
+  ofsc_status result(ofsc_result* out) const {
+    const Ctrl& c = *g->ws.ctrl_host;
+    ofsc_status rs = c.status != OFSC_OK ? c.status : (c.converged ? OFSC_OK : OFSC_ERR_NOT_CONVERGED);
+    if (out) {
+      out->iterations = c.it;
+      out->status = rs;
+      out->rel_dir_norm = c.rel;
+      out->g0_norm = c.g0;
+      out->f = c.f;
+      out->kernel_launches = launches;
+    }
+    return rs;
+  }
+};
+
+ofsc_status result_error(ofsc_status rs, const char* who) {
+  if (rs == OFSC_ERR_NONFINITE) return fail(rs, "%s: non-finite value in X0 or in the iteration", who);
+  if (rs == OFSC_ERR_TIMEOUT) return fail(rs, "%s: a bounded tensor-core wait timed out", who);
+  return rs;
+}
+
+}  // namespace
+}  // namespace ofsc
+
+extern "C" ofsc_status ofsc_iterate(ofsc_graph* g, int32_t method, int32_t k, float* X, double tol,
+                                    int32_t maxit, const ofsc_opts* opts, ofsc_result* out, void* stream_) {
+  clear_error();
+  ofsc_opts o{};
+  if (opts) o = *opts;
+  ofsc_status st = check_iterate_args(g, method, k, X, tol, maxit, o, "ofsc_iterate");
+  if (st != OFSC_OK) return st;
+  const int check_every = o.check_every > 0 ? o.check_every : 16;
+  cudaStream_t s = (cudaStream_t)stream_;
+  if (out) *out = ofsc_result{0, OFSC_OK, 0.0, 0.0, 0.0, 0};
+  if (g->n == 0) return OFSC_OK;
+  Job job(g, method, k, X, tol, maxit, o, s);
+  st = job.prepare();
+  if (st != OFSC_OK) return st;
+  g_launches = 0;
+  st = job.start();
+  if (st != OFSC_OK) return st;
+  Workspace& ws = g->ws;
+  for (int t = 0; t <= maxit; ++t) {
+    st = job.update(t);
+    if (st != OFSC_OK) return st;
     if (t == maxit) break;
-    OFSC_CUDA(run.direction_and_linesearch(t == 0 ? 1 : 0, o, k, t == 0 ? o.alpha0 : 0.0));
     if ((t + 1) % check_every == 0) {
       OFSC_CUDA(cudaMemcpyAsync(&ws.ctrl_host->done, &ws.ctrl->done, sizeof(int), cudaMemcpyDeviceToHost, s));
       OFSC_CUDA(cudaStreamSynchronize(s));
-      prof.collect();
+      job.prof.collect();
       if (ws.ctrl_host->done) break;
     }
   }
-  // Final report from an exact AX.
   Ctrl c{};
   st = finish(ws, s, &c);
-  prof.collect();
+  job.prof.collect();
   if (st != OFSC_OK) return st;
-  if (c.status == OFSC_OK) {
-    OFSC_CUDA(run.refresh(objective, 1));
-    int nblk = 0;
-    OFSC_CUDA(run.rowpass(method, 0, 1, 1, &nblk));
-    run.beta(nblk, 0, 1);
-    OFSC_LAUNCH_CHECK("k_beta(eval)");
-  }
-  k_pad_out<<<grid_elems(g->n * k), 256, 0, s>>>(g->n, k, kp, ws.X, X);
-  ++g_launches;
-  OFSC_LAUNCH_CHECK("k_pad_out");
-  st = finish(ws, s, &c);
+  st = job.report(c);
   if (st != OFSC_OK) return st;
-  ofsc_status rs = c.status != OFSC_OK ? c.status : (c.converged ? OFSC_OK : OFSC_ERR_NOT_CONVERGED);
-  if (out) {
-    out->iterations = c.it;
-    out->status = rs;
-    out->rel_dir_norm = c.rel;
-    out->g0_norm = c.g0;
-    out->f = c.f;
-    out->kernel_launches = g_launches;
+  OFSC_CUDA(cudaStreamSynchronize(s));
+  job.prof.collect();
+  return result_error(job.result(out), "ofsc_iterate");
+}
+
+// ==========================================================================================
+// ofsc_iterate_batched: Algorithm 2 on many independent graphs at once.
+//
+// Each graph runs on a stream of its own (owned by its handle), forked from the caller's stream,
+// so the kernels of small graphs share the SMs. The graphs advance in lockstep: iteration t of
+// every graph is queued before iteration t + 1 of any. The updates whose launches do not depend
+// on t (not the first, not a refresh of AX, not the last) are captured once, for all graphs, into
+// one CUDA graph (a branch per graph) and replayed; a graph that has stopped keeps its branch,
+// whose kernels return at once on its control block's stop flag, as they do between the host's
+// flag reads in ofsc_iterate. So every graph gets the same launches, in the same order on its
+// stream, as ofsc_iterate would give it, and the same bits.
+// ==========================================================================================
+
+namespace ofsc {
+namespace {
+
+struct BatchEvents {
+  std::vector<cudaEvent_t> ev;
+  ~BatchEvents() {
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
   }
-  if (rs == OFSC_ERR_NONFINITE) return fail(rs, "ofsc_iterate: non-finite value in X0 or in the iteration");
-  if (rs == OFSC_ERR_TIMEOUT) return fail(rs, "ofsc_iterate: a bounded tensor-core wait timed out");
-  return rs;
+  cudaError_t make(size_t n) {
+    ev.assign(n, nullptr);
+    for (auto& e : ev) {
+      cudaError_t r = cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+      if (r != cudaSuccess) return r;
+    }
+    return cudaSuccess;
+  }
+};
+
+// Orders every job stream after `main` (fork) or `main` after every job stream (join).
+cudaError_t fork_jobs(cudaStream_t main, std::vector<std::unique_ptr<Job>>& jobs, cudaEvent_t e) {
+  cudaError_t r = cudaEventRecord(e, main);
+  for (auto& j : jobs)
+    if (r == cudaSuccess) r = cudaStreamWaitEvent(j->s, e, 0);
+  return r;
+}
+cudaError_t join_jobs(cudaStream_t main, std::vector<std::unique_ptr<Job>>& jobs, const std::vector<cudaEvent_t>& e) {
+  cudaError_t r = cudaSuccess;
+  for (size_t i = 0; i < jobs.size() && r == cudaSuccess; ++i) {
+    r = cudaEventRecord(e[i], jobs[i]->s);
+    if (r == cudaSuccess) r = cudaStreamWaitEvent(main, e[i], 0);
+  }
+  return r;
+}
+
+struct HubStream {
+  cudaStream_t s = nullptr;
+  ~HubStream() {
+    if (s) cudaStreamDestroy(s);
+  }
+};
+
+struct GraphExec {
+  cudaGraphExec_t exec = nullptr;
+  ~GraphExec() {
+    if (exec) cudaGraphExecDestroy(exec);
+  }
+};
+
+}  // namespace
+}  // namespace ofsc
+
+extern "C" ofsc_status ofsc_iterate_batched(int32_t count, ofsc_graph* const* graphs, int32_t method,
+                                            const int32_t* ks, float* const* Xs, double tol, int32_t maxit,
+                                            const ofsc_opts* opts, ofsc_result* outs, void* stream_) {
+  clear_error();
+  if (count < 0) return fail(OFSC_ERR_INVALID_ARG, "ofsc_iterate_batched: count < 0");
+  if (count > 0 && (!graphs || !ks || !Xs)) return fail(OFSC_ERR_INVALID_ARG, "ofsc_iterate_batched: NULL array");
+  ofsc_opts o{};
+  if (opts) o = *opts;
+  if (o.trace || o.profile)
+    return fail(OFSC_ERR_INVALID_ARG, "ofsc_iterate_batched: opts.trace and opts.profile must be NULL");
+  for (int i = 0; i < count; ++i) {
+    ofsc_status st = check_iterate_args(graphs[i], method, ks[i], Xs[i], tol, maxit, o, "ofsc_iterate_batched");
+    if (st != OFSC_OK) return st;
+    for (int j = 0; j < i; ++j)
+      if (graphs[j] == graphs[i]) return fail(OFSC_ERR_INVALID_ARG, "ofsc_iterate_batched: graph %d repeats graph %d", i, j);
+  }
+  if (outs)
+    for (int i = 0; i < count; ++i) outs[i] = ofsc_result{0, OFSC_OK, 0.0, 0.0, 0.0, 0};
+  const int check_every = o.check_every > 0 ? o.check_every : 16;
+  cudaStream_t caller = (cudaStream_t)stream_;
+  std::vector<std::unique_ptr<Job>> jobs;
+  std::vector<int> slot;  // job index -> position in the caller's arrays
+  for (int i = 0; i < count; ++i) {
+    ofsc_graph* g = graphs[i];
+    if (g->n == 0) continue;
+    if (!g->stream) OFSC_CUDA(cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking));
+    jobs.emplace_back(new Job(g, method, ks[i], Xs[i], tol, maxit, o, g->stream));
+    slot.push_back(i);
+  }
+  if (jobs.empty()) return OFSC_OK;
+  for (auto& j : jobs) {
+    ofsc_status st = j->prepare();
+    if (st != OFSC_OK) return st;
+  }
+  BatchEvents ev;
+  OFSC_CUDA(ev.make(jobs.size() + 1));
+  const std::vector<cudaEvent_t> jev(ev.ev.begin() + 1, ev.ev.end());
+  cudaEvent_t fev = ev.ev[0];
+  const bool replay = o.direct_launch == 0;
+  // A hub stream of this call orders the graphs' streams (the caller's stream may be the legacy
+  // default stream, on which no capture can start): caller -> hub -> graphs -> hub -> caller.
+  HubStream hub;
+  OFSC_CUDA(cudaStreamCreateWithFlags(&hub.s, cudaStreamNonBlocking));
+  cudaStream_t main = hub.s;
+  OFSC_CUDA(cudaEventRecord(fev, caller));
+  OFSC_CUDA(cudaStreamWaitEvent(main, fev, 0));
+
+  OFSC_CUDA(fork_jobs(main, jobs, fev));
+  for (auto& j : jobs) {
+    ofsc_status st = j->start();
+    if (st != OFSC_OK) return st;
+  }
+  GraphExec plain;                  // one plain update of every graph
+  std::vector<int64_t> plain_launches(jobs.size(), 0);
+  bool forked = true;               // job streams are ordered after main and main not after them
+  for (int t = 0; t <= maxit; ++t) {
+    if (replay && jobs[0]->plain(t)) {
+      if (forked) {
+        OFSC_CUDA(join_jobs(main, jobs, jev));
+        forked = false;
+      }
+      if (!plain.exec) {
+        // capture: main forks into one branch per graph and joins them again
+        OFSC_CUDA(cudaStreamBeginCapture(main, cudaStreamCaptureModeThreadLocal));
+        cudaError_t ce = fork_jobs(main, jobs, fev);
+        ofsc_status st = OFSC_OK;
+        for (size_t i = 0; i < jobs.size() && ce == cudaSuccess && st == OFSC_OK; ++i) {
+          const int64_t l0 = jobs[i]->launches;
+          st = jobs[i]->update(t);
+          plain_launches[i] = jobs[i]->launches - l0;
+          jobs[i]->launches = l0;  // counted when the graph runs
+        }
+        if (ce == cudaSuccess && st == OFSC_OK) ce = join_jobs(main, jobs, jev);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ee = cudaStreamEndCapture(main, &graph);
+        if (st != OFSC_OK) {
+          if (graph) cudaGraphDestroy(graph);
+          return st;
+        }
+        if (ce == cudaSuccess) ce = ee;
+        if (ce == cudaSuccess) ce = cudaGraphInstantiate(&plain.exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        OFSC_CUDA(ce);
+      }
+      OFSC_CUDA(cudaGraphLaunch(plain.exec, main));
+      for (size_t i = 0; i < jobs.size(); ++i) jobs[i]->launches += plain_launches[i];
+    } else {
+      if (!forked) {
+        OFSC_CUDA(fork_jobs(main, jobs, fev));
+        forked = true;
+      }
+      for (auto& j : jobs) {
+        ofsc_status st = j->update(t);
+        if (st != OFSC_OK) return st;
+      }
+    }
+    if (t == maxit) break;
+    if ((t + 1) % check_every == 0) {
+      if (forked) {
+        OFSC_CUDA(join_jobs(main, jobs, jev));
+        forked = false;
+      }
+      for (auto& j : jobs)
+        OFSC_CUDA(cudaMemcpyAsync(&j->g->ws.ctrl_host->done, &j->g->ws.ctrl->done, sizeof(int),
+                                  cudaMemcpyDeviceToHost, main));
+      OFSC_CUDA(cudaStreamSynchronize(main));
+      bool all = true;
+      for (auto& j : jobs) all = all && j->g->ws.ctrl_host->done;
+      if (all) break;
+    }
+  }
+  // final reports: read every control block, then queue the exact evaluations together
+  if (forked) OFSC_CUDA(join_jobs(main, jobs, jev));
+  for (auto& j : jobs)
+    OFSC_CUDA(cudaMemcpyAsync(j->g->ws.ctrl_host, j->g->ws.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, main));
+  OFSC_CUDA(cudaStreamSynchronize(main));
+  OFSC_CUDA(fork_jobs(main, jobs, fev));
+  for (auto& j : jobs) {
+    const Ctrl c = *j->g->ws.ctrl_host;
+    ofsc_status st = j->report(c);
+    if (st != OFSC_OK) return st;
+  }
+  OFSC_CUDA(join_jobs(main, jobs, jev));
+  OFSC_CUDA(cudaEventRecord(fev, main));
+  OFSC_CUDA(cudaStreamWaitEvent(caller, fev, 0));
+  OFSC_CUDA(cudaStreamSynchronize(main));
+  ofsc_status worst = OFSC_OK;
+  for (size_t i = 0; i < jobs.size(); ++i) {
+    const ofsc_status rs = jobs[i]->result(outs ? &outs[slot[i]] : nullptr);
+    if (rs != OFSC_OK && (worst == OFSC_OK || worst == OFSC_ERR_NOT_CONVERGED)) worst = rs;
+  }
+  return result_error(worst, "ofsc_iterate_batched");
 }
 
 // ==========================================================================================

@@ -52,7 +52,7 @@ class Opts(ctypes.Structure):
                 ("check_every", ctypes.c_int32), ("alpha0", ctypes.c_double),
                 ("trace", ctypes.c_void_p), ("trace_cap", ctypes.c_int32),
                 ("profile", ctypes.POINTER(Profile)), ("gram_engine", ctypes.c_int32),
-                ("spmm_engine", ctypes.c_int32)]
+                ("spmm_engine", ctypes.c_int32), ("direct_launch", ctypes.c_int32)]
 
 
 class Result(ctypes.Structure):
@@ -91,6 +91,8 @@ def lib() -> ctypes.CDLL:
             "ofsc_objective_grad_noalloc": [vp, i32, i32, vp, ctypes.POINTER(dbl), vp, vp],
             "ofsc_iterate": [vp, i32, i32, vp, dbl, i32, ctypes.POINTER(Opts),
                              ctypes.POINTER(Result), vp],
+            "ofsc_iterate_batched": [i32, ctypes.POINTER(vp), i32, ctypes.POINTER(i32), ctypes.POINTER(vp), dbl,
+                                     i32, ctypes.POINTER(Opts), ctypes.POINTER(Result), vp],
             "ofsc_rayleigh_ritz": [vp, i32, vp, vp, ctypes.POINTER(dbl), vp],
             "ofsc_weight_grad": [vp, i32, i32, vp, i64, vp, vp, vp, vp],
             "ofsc_row_normalize": [i64, i32, vp, vp],
@@ -207,6 +209,27 @@ def ofsc_iterate(g: Graph, method: int, X, tol: float, maxit: int, *, gather: in
                               ctypes.byref(o), ctypes.byref(r), _stream(stream)),
            allow=(OK, ERR_NOT_CONVERGED))
     return r
+
+
+def ofsc_iterate_batched(graphs: list[Graph], method: int, Xs: list, tol: float, maxit: int, *,
+                         gather: int = GATHER_FP32, y_refresh: int = 0, check_every: int = 0,
+                         alpha0: float = 0.0, gram_engine: int = GRAM_AUTO, spmm_engine: int = SPMM_AUTO,
+                         direct_launch: bool = False, stream=None) -> list[Result]:
+    """Algorithm 2 in place on every device block Xs[i] (n_i x k_i, FP32) of the graphs, in one
+    call. Returns one ofsc_result per problem, in order."""
+    count = len(graphs)
+    if len(Xs) != count:
+        raise ValueError("ofsc_iterate_batched: one X per graph")
+    o = Opts(gather, y_refresh, check_every, alpha0, None, 0, None, gram_engine, spmm_engine,
+             1 if direct_launch else 0)
+    hs = (ctypes.c_void_p * count)(*[g.handle for g in graphs])
+    ks = (ctypes.c_int32 * count)(*[int(X.shape[1]) for X in Xs])
+    xs = (ctypes.c_void_p * count)(*[_ptr(X) for X in Xs])
+    rs = (Result * count)()
+    _check(lib().ofsc_iterate_batched(count, hs, method, ks, xs, float(tol), int(maxit), ctypes.byref(o), rs,
+                                      _stream(stream)),
+           allow=(OK, ERR_NOT_CONVERGED))
+    return list(rs)
 
 
 def ofsc_gram(L, Rs, out, k: int | None = None, rows_per_block: int = 0, stream=None) -> None:

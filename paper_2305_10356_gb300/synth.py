@@ -255,6 +255,34 @@ def stream(name: str, n: int | None = None) -> tuple[list[EdgeList], np.ndarray]
     return edge_stream(full, parts, seed + 2), initial_block(full.n, full.n_blocks, seed + 1)
 
 
+BATCHES = {
+    # 32 independent SBMs of uneven size: N ~ U[2000, 100000], blocks k ~ U[8, 64], mean degree
+    # ~ U[16, 48], within:between 5:1 (edge counts), block sizes +-20%
+    "sbm_batch32": dict(count=32, n=(2000, 100_000), k=(8, 64), mean_degree=(16.0, 48.0), ratio=5.0, idx=6),
+}
+
+
+def batch(name: str, scale: float = 1.0) -> list[tuple[EdgeList, np.ndarray]]:
+    """Edge lists and X0 of a named batch of graphs; `scale` shrinks every node count (at least
+    4 nodes per block). The sizes are drawn from one generator, each graph from its own seed."""
+    spec = BATCHES[name]
+    base = 2305 * 1000 + spec["idx"]
+    rng = rng_for(base)
+    count = spec["count"]
+    ns = rng.integers(spec["n"][0], spec["n"][1] + 1, size=count)
+    ks = rng.integers(spec["k"][0], spec["k"][1] + 1, size=count)
+    ds = rng.uniform(spec["mean_degree"][0], spec["mean_degree"][1], size=count)
+    out = []
+    for i in range(count):
+        k = int(ks[i])
+        n = max(4 * k, int(round(int(ns[i]) * scale)))
+        seed = base * 100 + 2 * i
+        g = sbm(n, k, float(ds[i]), spec["ratio"], ratio_kind="count", sizes="uniform", size_param=0.2,
+                gamma=None, seed=seed)
+        out.append((g, initial_block(n, k, seed + 1)))
+    return out
+
+
 def workload(name: str, n: int | None = None, seed_offset: int = 0) -> tuple[EdgeList, np.ndarray]:
     """Edge list and X0 for a named workload; `n` shrinks the node count (same recipe)."""
     spec = dict(WORKLOADS[name])

@@ -464,3 +464,74 @@ def test_autograd_objective_matches_central_differences(which):
         fd = (fp - fm) / (2 * eps)
         an = float(np.sum(gX * dX) + np.sum(gw * dw))
         assert abs(an - fd) <= 1e-3 * abs(fd) + 1e-6, (an, fd)
+
+
+def batch_problems(scale, count):
+    """The first `count` graphs of the 32-graph batch recipe, node counts scaled by `scale`, plus:
+    a graph with no nodes (skipped by the batch); one with k = 128 (tensor-core Grams and
+    direction pass) to mix engines in one batch; and the first graph again from X0 = 0, where every
+    direction vanishes, so that problem stops at t = 0 while the others go on."""
+    probs = synth.batch("sbm_batch32", scale)[:count]
+    probs.append((synth.EdgeList(n=0, src=np.zeros(0, np.int32), dst=np.zeros(0, np.int32), w=None,
+                                 labels=np.zeros(0, np.int32), n_blocks=3), np.zeros((0, 3), np.float32)))
+    e = synth.sbm(3000, 128, 20.0, 5.0, ratio_kind="count", seed=121)
+    probs.append((e, synth.initial_block(e.n, 128, 122)))
+    probs.append((probs[0][0], np.zeros_like(probs[0][1])))
+    return probs
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_batched_equals_single_bit_for_bit(method):
+    """ofsc_iterate_batched gives every problem the launches ofsc_iterate gives it: same X, same
+    result fields, bit for bit, with CUDA graph replay and with direct launches. maxit = 40 spans
+    two host flag reads and one exact refresh of AX; tol = 1e-3 lets some problems stop early."""
+    import torch
+    probs = batch_problems(0.02, 6)
+    graphs = [gpu_graph(e) for e, _ in probs]
+    singles = []
+    for g, (e, x0) in zip(graphs, probs):
+        X = torch.from_numpy(x0).cuda()
+        r = ofsc.ofsc_iterate(g, method, X, 1e-3, 40) if e.n > 0 else None
+        singles.append((X.cpu().numpy(), r))
+    for direct in (False, True):
+        Xs = [torch.from_numpy(x0).cuda() for _, x0 in probs]
+        rs = ofsc.ofsc_iterate_batched(graphs, method, Xs, 1e-3, 40, direct_launch=direct)
+        assert len(rs) == len(probs)
+        stopped_early = 0
+        for (Xr, r), X, rb, (e, _) in zip(singles, Xs, rs, probs):
+            assert np.array_equal(X.cpu().numpy(), Xr)
+            if e.n == 0:
+                assert rb.iterations == 0
+                continue
+            assert (rb.iterations, rb.status, rb.rel_dir_norm, rb.f, rb.g0_norm) == \
+                   (r.iterations, r.status, r.rel_dir_norm, r.f, r.g0_norm)
+            assert rb.kernel_launches >= r.kernel_launches
+            stopped_early += rb.iterations < 40
+        assert stopped_early >= 1
+
+
+def test_batched_matches_oracle():
+    """Five updates of OFM-f1 on each of four problems of the batch recipe (k from 8 to 64) in one
+    batched call, against the oracle run problem by problem."""
+    import torch
+    probs = synth.batch("sbm_batch32", 0.01)[:4]
+    graphs = [gpu_graph(e) for e, _ in probs]
+    Xs = [torch.from_numpy(x0).cuda() for _, x0 in probs]
+    rs = ofsc.ofsc_iterate_batched(graphs, o.OFM_F1, Xs, 0.0, 5)
+    for (e, x0), X, r in zip(probs, Xs, rs):
+        ref = o.iterate(o.build_graph(e.n, e.src, e.dst), o.OFM_F1, x0, 0.0, 5)
+        assert r.iterations == 5 == ref.iterations
+        Xg = X.cpu().numpy()
+        assert np.linalg.norm(Xg - ref.X) <= 1e-4 * np.linalg.norm(ref.X)
+
+
+def test_batched_rejects_bad_arguments():
+    import torch
+    e, x0 = synth.batch("sbm_batch32", 0.01)[0]
+    g = gpu_graph(e)
+    X = torch.from_numpy(x0).cuda()
+    with pytest.raises(ofsc.OfscError):
+        ofsc.ofsc_iterate_batched([g, g], o.OFM_F1, [X, X.clone()], 0.0, 3)
+    with pytest.raises(ofsc.OfscError):
+        ofsc.ofsc_iterate_batched([g], 7, [X], 0.0, 3)
+    assert ofsc.ofsc_iterate_batched([], o.OFM_F1, [], 0.0, 3) == []

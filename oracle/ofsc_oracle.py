@@ -454,7 +454,7 @@ def step_sizes(g: Graph, method: int, X, V, AX, AV, normA2: float) -> np.ndarray
 
 
 def iterate(g: Graph, method: int, X0: np.ndarray, tol: float, maxit: int,
-            alpha0: float = 0.0) -> IterResult:
+            alpha0: float = 0.0, record: list | None = None) -> IterResult:
     """Algorithm 2 for one of the four methods, in FP64, from the FP32 (or FP64) start X0.
 
     G_0 = g(X_0); V_0 = -G_0; X_1 = X_0 + alpha V_0 (alpha0 > 0 given, else exact line
@@ -462,6 +462,8 @@ def iterate(g: Graph, method: int, X0: np.ndarray, tol: float, maxit: int,
     beta_i = sum_l (G_t - G_{t-1})_li G_t,li / sum_l G_{t-1,li}^2 (0 when the denominator is 0,
     and 0 when the column's new direction would not descend: -|g_i|^2 + beta_i v_i^T g_i >= 0);
     V_t = -G_t + V_{t-1} diag(beta); alpha by exact line search; X_{t+1} = X_t + V_t diag(alpha).
+    `record`, when given, receives one dict per update t: X_t, G_t, V_t, AV_t, alpha_t, beta_t,
+    the denominators of beta_t and the columns whose beta the restart rule set to 0.
     """
     X = np.array(X0, dtype=np.float64)
     normA2 = normA_fro2(g)
@@ -480,6 +482,10 @@ def iterate(g: Graph, method: int, X0: np.ndarray, tol: float, maxit: int,
         alpha = step_sizes(g, method, X, V, AX, AV, normA2)
     alphas.append(alpha.copy())
     betas.append(np.zeros(X.shape[1]))
+    if record is not None:
+        k = X.shape[1]
+        record.append(dict(X=X, G=G, V=V, AV=AV, alpha=alpha.copy(), beta=np.zeros(k), den=np.zeros(k),
+                           restart=np.zeros(k, dtype=bool)))
     X = X + V * alpha[None, :]
     t = 1
     rel = float("nan")
@@ -498,17 +504,82 @@ def iterate(g: Graph, method: int, X0: np.ndarray, tol: float, maxit: int,
         den = np.sum(G * G, axis=0)
         beta = np.where(den != 0.0, num / np.where(den != 0.0, den, 1.0), 0.0)
         descent = -np.sum(Gn * Gn, axis=0) + beta * np.sum(V * Gn, axis=0)
-        beta = np.where(descent >= 0.0, 0.0, beta)
+        restart = descent >= 0.0
+        beta = np.where(restart, 0.0, beta)
         V = -Gn + V * beta[None, :]
         AV = apply_A(g, V)
         alpha = step_sizes(g, method, X, V, AX, AV, normA2)
         alphas.append(alpha.copy())
         betas.append(beta.copy())
+        if record is not None:
+            record.append(dict(X=X, G=Gn, V=V, AV=AV, alpha=alpha.copy(), beta=beta.copy(), den=den,
+                               restart=restart))
         X = X + V * alpha[None, :]
         G = Gn
         t += 1
     f = objective(objective_of(method), X, AX, normA2)
     return IterResult(X, t, rel, g0, f, converged, alphas, betas, rels)
+
+
+# =============================================================================================
+# Differentiating through unrolled updates (OFM-f1)
+# =============================================================================================
+
+def hess_f1_quarter(g: Graph, Z: np.ndarray, U: np.ndarray) -> np.ndarray:
+    """The Hessian of f1/4 at Z applied to U: the derivative of A Z + Z Z^T Z (= grad f1 / 4,
+    Eq. (5)) along U, i.e. A U + U Z^T Z + Z U^T Z + Z Z^T U."""
+    return apply_A(g, U) + U @ (Z.T @ Z) + Z @ (U.T @ Z) + Z @ (Z.T @ U)
+
+
+def unrolled_objective(g: Graph, X0: np.ndarray, T: int) -> float:
+    """L(X_0) = f1(X_T) after T updates of OFM-f1 (Algorithm 2, no stopping test)."""
+    r = iterate(g, OFM_F1, X0, 0.0, T)
+    return r.f
+
+
+def unrolled_grad(g: Graph, X0: np.ndarray, T: int) -> tuple[float, np.ndarray]:
+    """dL/dX_0 for L = f1(X_T) after T updates of OFM-f1, by reverse accumulation through
+    Algorithm 2 as `iterate` runs it. Per update t, X_{t+1} = X_t + alpha_t V_t with
+      * alpha_t a root of p(a) = <V_t, grad f1(X_t + a V_t)> / 4 (the cubic of Eq. (15)); by the
+        implicit-function theorem d alpha = -(dp at fixed a) / p'(alpha), where
+        dp/dX = H(X_{t+1})[V_t], dp/dV = grad f1(X_{t+1})/4 + alpha H(X_{t+1})[V_t] and
+        p'(alpha) = <V_t, H(X_{t+1})[V_t]>, H the Hessian of f1/4 (hess_f1_quarter);
+      * V_t = -G_t + V_{t-1} diag(beta_t), beta_t,j = <G_t - G_{t-1}, G_t>_j / |G_{t-1},j|^2, with
+        beta held at 0 (no derivative) where the restart rule or a zero denominator set it;
+      * G_t = grad f1(X_t) = 4(A X_t + X_t X_t^T X_t), whose derivative along U is 4 H(X_t)[U].
+    Returns (L, dL/dX_0)."""
+    rec: list = []
+    res = iterate(g, OFM_F1, X0, 0.0, T, record=rec)
+    X = res.X
+    if not rec:  # T = 0, or X_0 stationary: L = f1(X_0)
+        return res.f, gradient(1, X, apply_A(g, X))
+    Gnext = gradient(1, X, apply_A(g, X))  # grad f1(X_T)
+    Xbar = Gnext.copy()
+    Vbar = np.zeros_like(X)
+    Gcarry = np.zeros_like(X)
+    Xnext = X
+    for t in range(len(rec) - 1, -1, -1):
+        r = rec[t]
+        V, a = r["V"], float(r["alpha"][0])
+        H1 = hess_f1_quarter(g, Xnext, V)
+        abar = float(np.sum(Xbar * V))
+        c = -abar / float(np.sum(V * H1))
+        Vbar = Vbar + a * Xbar + c * (0.25 * Gnext + a * H1)
+        Xbar = Xbar + c * H1
+        Gt = Gcarry - Vbar
+        if t >= 1:
+            Gp, Vp = rec[t - 1]["G"], rec[t - 1]["V"]
+            bbar = np.sum(Vbar * Vp, axis=0)
+            live = (~r["restart"]) & (r["den"] != 0.0)
+            den = np.where(live, r["den"], 1.0)
+            nbar = np.where(live, bbar / den, 0.0)
+            dbar = np.where(live, -bbar * r["beta"] / den, 0.0)
+            Gt = Gt + nbar * (2.0 * r["G"] - Gp)
+            Gcarry = -nbar * r["G"] + 2.0 * dbar * Gp
+            Vbar = Vbar * r["beta"]
+        Xbar = Xbar + 4.0 * hess_f1_quarter(g, r["X"], Gt)
+        Gnext, Xnext = r["G"], r["X"]
+    return res.f, Xbar
 
 
 # =============================================================================================

@@ -543,3 +543,41 @@ def test_sparse_objective_of_weights_matches_dense(which):
     got = o.objective_of_weights(n, src, dst, w, X, which)
     ref = _objective_of_weights(n, src, dst, w, X, which)
     assert abs(got - ref) <= 1e-12 * max(1.0, abs(ref))
+
+
+# ------------------------------------------------------------------------------------------
+# Differentiating through unrolled updates of OFM-f1: central differences in random directions
+# ------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed,T", [(5, 1), (5, 12), (12, 20), (24, 20)])
+def test_unrolled_grad_matches_central_differences(seed, T):
+    """d f1(X_T) / d X_0 through T updates of Algorithm 2 (line search by the implicit-function
+    theorem, beta's quotient, the Hessian-vector products of the direction) against central
+    differences of the FP64 iteration itself. Seeds 12 and 24 have columns restarted by the
+    descent rule (beta held at 0) in several updates."""
+    e = synth.sbm(80 if seed == 5 else 60, 3, 10.0 if seed == 5 else 8.0, 5.0, ratio_kind="count", seed=seed)
+    g = o.build_graph(e.n, e.src, e.dst)
+    x0 = synth.initial_block(e.n, 3, seed + 1).astype(np.float64)
+    rec = []
+    o.iterate(g, o.OFM_F1, x0, 0.0, T, record=rec)
+    assert len(rec) == T
+    if seed in (12, 24):
+        assert sum(int(r["restart"].sum()) for r in rec) >= 6
+    f, grad = o.unrolled_grad(g, x0, T)
+    assert f == o.unrolled_objective(g, x0, T)
+    rng = np.random.default_rng(seed * 100 + T)
+    eps = 1e-6
+    for _ in range(3):
+        D = rng.standard_normal(x0.shape)
+        fd = (o.unrolled_objective(g, x0 + eps * D, T) - o.unrolled_objective(g, x0 - eps * D, T)) / (2 * eps)
+        assert abs(float(np.sum(grad * D)) - fd) <= 2e-6 * abs(fd), (float(np.sum(grad * D)), fd)
+
+
+def test_unrolled_grad_without_updates_is_the_gradient():
+    """T = 0 leaves L = f1(X_0), whose gradient is Eq. (5)."""
+    g, _ = small_graph()
+    x0 = synth.initial_block(g.n, 4, 3).astype(np.float64)
+    f, grad = o.unrolled_grad(g, x0, 0)
+    A = o.dense_A(g)
+    np.testing.assert_allclose(grad, 4.0 * (A @ x0 + x0 @ (x0.T @ x0)), rtol=1e-12, atol=1e-14)
+    assert abs(f - o.objective_dense(1, A, x0)) <= 1e-10 * abs(f)

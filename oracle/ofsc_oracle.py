@@ -85,13 +85,16 @@ class Graph:
         return (d @ self.S() @ d).tocsr()
 
 
-def build_graph(n: int, src: np.ndarray, dst: np.ndarray, w: np.ndarray | None = None) -> Graph:
+def build_graph(n: int, src: np.ndarray, dst: np.ndarray, w: np.ndarray | None = None,
+                exact: bool = False) -> Graph:
     """S from an undirected edge list (Eq. (1)): symmetric, no self-loops, one entry per pair.
 
     Binary S: a pair listed several times (in either direction) is one edge of weight 1.
     Weighted S: the FP32 weights of all listings of a pair are summed in FP64, then rounded
     once to FP32. Degrees: D_ii = sum_j S_ij (an integer count, or an FP64 sum of the FP32
     entries). D^-1/2 is 1/sqrt(D_ii) in FP64, and 0 when D_ii = 0.
+    exact=True keeps the weights and their sums in FP64 (no FP32 rounding anywhere), so that S is
+    a smooth function of the listed weights (for derivatives by finite differences).
     """
     src = np.asarray(src, dtype=np.int64)
     dst = np.asarray(dst, dtype=np.int64)
@@ -100,7 +103,7 @@ def build_graph(n: int, src: np.ndarray, dst: np.ndarray, w: np.ndarray | None =
     if src.size and (src.min() < 0 or dst.min() < 0 or src.max() >= n or dst.max() >= n):
         raise ValueError("node id out of range")
     if w is not None:
-        w = np.asarray(w, dtype=np.float32)
+        w = np.asarray(w, dtype=np.float64 if exact else np.float32)
         if w.shape != src.shape or not np.all(np.isfinite(w)) or np.any(w <= 0):
             raise ValueError("weights must be finite and > 0")
     loop = src == dst
@@ -121,7 +124,7 @@ def build_graph(n: int, src: np.ndarray, dst: np.ndarray, w: np.ndarray | None =
         ww = np.concatenate([w[keep], w[keep]]).astype(np.float64)
         start = np.nonzero(head)[0]
         sums = np.add.reduceat(ww[order], start) if key_s.size else np.zeros(0)
-        val = sums.astype(np.float32)
+        val = sums if exact else sums.astype(np.float32)
     r = (ukey // max(n, 1)).astype(np.int64)
     c = (ukey % max(n, 1)).astype(np.int32)
     counts = np.bincount(r, minlength=n)
@@ -233,21 +236,12 @@ def objective_of_weights(n: int, src: np.ndarray, dst: np.ndarray, w: np.ndarray
     return objective(which, X, AX, normA2)
 
 
-def weight_grad(n: int, src: np.ndarray, dst: np.ndarray, w: np.ndarray, X: np.ndarray, which: int) -> np.ndarray:
-    """d f / d w_e for every listed edge e of a weighted graph, f = f1 (Eq. (2)) or f2 (Eq. (3)).
-
-    Everything in FP64 from the listed weights (no FP32 rounding of S). With
-    A_hat = D^-1/2 S D^-1/2, A = -I - A_hat and Gamma = df/dA_hat (symmetric),
-        Gamma = 2 (I + A_hat - X X^T)          for f1,
-        Gamma = -X (2I - X^T X) X^T            for f2,
-    a listing of the pair {a, b} (a != b) changes S_ab = S_ba and the degrees d_a, d_b, so
-        df/dw = 2 Gamma_ab / sqrt(d_a d_b) - r_a / d_a - r_b / d_b,   r_a = sum_j Gamma_aj A_hat_aj.
-    Listings of the same pair share one value; self-loops (dropped from S) get 0.
-    """
+def _pairs(n: int, src, dst, w):
+    """The distinct undirected pairs {a < b} of an edge list with their FP64 summed weights:
+    (kept listings, listing -> pair index, a, b, D^-1/2 per node, A_hat per pair)."""
     src = np.asarray(src, dtype=np.int64)
     dst = np.asarray(dst, dtype=np.int64)
     w = np.asarray(w, dtype=np.float64)
-    X = np.asarray(X, dtype=np.float64)
     a = np.minimum(src, dst)
     b = np.maximum(src, dst)
     keep = a != b
@@ -259,7 +253,35 @@ def weight_grad(n: int, src: np.ndarray, dst: np.ndarray, w: np.ndarray, X: np.n
     np.add.at(d, pa, S)
     np.add.at(d, pb, S)
     sd = np.where(d > 0, 1.0 / np.sqrt(np.where(d > 0, d, 1.0)), 0.0)
-    ah = S * sd[pa] * sd[pb]
+    return keep, inv, pa, pb, sd, S * sd[pa] * sd[pb]
+
+
+def _weight_chain(n: int, keep, inv, pa, pb, sd, ah, gam) -> np.ndarray:
+    """d/dw per listing from Gamma = d/dA_hat on the pairs (symmetric): a listing of {a, b}
+    moves S_ab = S_ba and both degrees, 2 Gamma_ab / sqrt(d_a d_b) - r_a / d_a - r_b / d_b with
+    r_a = sum_j Gamma_aj A_hat_aj."""
+    r = np.zeros(n)
+    np.add.at(r, pa, gam * ah)
+    np.add.at(r, pb, gam * ah)
+    gp = 2.0 * gam * sd[pa] * sd[pb] - r[pa] * sd[pa] ** 2 - r[pb] * sd[pb] ** 2
+    out = np.zeros(keep.size)
+    out[keep] = gp[inv]
+    return out
+
+
+def weight_grad(n: int, src: np.ndarray, dst: np.ndarray, w: np.ndarray, X: np.ndarray, which: int) -> np.ndarray:
+    """d f / d w_e for every listed edge e of a weighted graph, f = f1 (Eq. (2)) or f2 (Eq. (3)).
+
+    Everything in FP64 from the listed weights (no FP32 rounding of S). With
+    A_hat = D^-1/2 S D^-1/2, A = -I - A_hat and Gamma = df/dA_hat (symmetric),
+        Gamma = 2 (I + A_hat - X X^T)          for f1,
+        Gamma = -X (2I - X^T X) X^T            for f2,
+    a listing of the pair {a, b} (a != b) changes S_ab = S_ba and the degrees d_a, d_b, so
+        df/dw = 2 Gamma_ab / sqrt(d_a d_b) - r_a / d_a - r_b / d_b,   r_a = sum_j Gamma_aj A_hat_aj.
+    Listings of the same pair share one value; self-loops (dropped from S) get 0.
+    """
+    X = np.asarray(X, dtype=np.float64)
+    keep, inv, pa, pb, sd, ah = _pairs(n, src, dst, w)
     AhX = np.zeros_like(X)
     np.add.at(AhX, pa, ah[:, None] * X[pb])
     np.add.at(AhX, pb, ah[:, None] * X[pa])
@@ -537,7 +559,7 @@ def unrolled_objective(g: Graph, X0: np.ndarray, T: int) -> float:
     return r.f
 
 
-def unrolled_grad(g: Graph, X0: np.ndarray, T: int) -> tuple[float, np.ndarray]:
+def unrolled_grad(g: Graph, X0: np.ndarray, T: int, edges=None):
     """dL/dX_0 for L = f1(X_T) after T updates of OFM-f1, by reverse accumulation through
     Algorithm 2 as `iterate` runs it. Per update t, X_{t+1} = X_t + alpha_t V_t with
       * alpha_t a root of p(a) = <V_t, grad f1(X_t + a V_t)> / 4 (the cubic of Eq. (15)); by the
@@ -547,12 +569,26 @@ def unrolled_grad(g: Graph, X0: np.ndarray, T: int) -> tuple[float, np.ndarray]:
       * V_t = -G_t + V_{t-1} diag(beta_t), beta_t,j = <G_t - G_{t-1}, G_t>_j / |G_{t-1},j|^2, with
         beta held at 0 (no derivative) where the restart rule or a zero denominator set it;
       * G_t = grad f1(X_t) = 4(A X_t + X_t X_t^T X_t), whose derivative along U is 4 H(X_t)[U].
-    Returns (L, dL/dX_0)."""
+    Returns (L, dL/dX_0), or with edges = (src, dst, w) of a weighted graph (g built from them
+    with exact=True) also dL/dw per listing: A enters G_t (adjoint 4 Gbar_t X_t^T), the cubic of
+    alpha_t (c V_t X_{t+1}^T, c the implicit-function factor) and f1(X_T) itself; with
+    Gamma = dL/dA_hat = -dL/dA symmetrised, the weights follow as in weight_grad."""
     rec: list = []
     res = iterate(g, OFM_F1, X0, 0.0, T, record=rec)
     X = res.X
+    pairs = _pairs(g.n, *edges) if edges is not None else None
+    gam = None
+    if pairs is not None:
+        _, _, pa, pb, _, ah = pairs
+        gam = 2.0 * (ah - np.sum(X[pa] * X[pb], axis=1))  # f1(X_T) directly
+
+    def finish(f, dX):
+        if pairs is None:
+            return f, dX
+        return f, dX, _weight_chain(g.n, *pairs, gam)
+
     if not rec:  # T = 0, or X_0 stationary: L = f1(X_0)
-        return res.f, gradient(1, X, apply_A(g, X))
+        return finish(res.f, gradient(1, X, apply_A(g, X)))
     Gnext = gradient(1, X, apply_A(g, X))  # grad f1(X_T)
     Xbar = Gnext.copy()
     Vbar = np.zeros_like(X)
@@ -578,8 +614,12 @@ def unrolled_grad(g: Graph, X0: np.ndarray, T: int) -> tuple[float, np.ndarray]:
             Gcarry = -nbar * r["G"] + 2.0 * dbar * Gp
             Vbar = Vbar * r["beta"]
         Xbar = Xbar + 4.0 * hess_f1_quarter(g, r["X"], Gt)
+        if gam is not None:
+            Xt = r["X"]
+            gam = gam - 0.5 * (4.0 * (np.sum(Gt[pa] * Xt[pb], axis=1) + np.sum(Gt[pb] * Xt[pa], axis=1))
+                               + c * (np.sum(V[pa] * Xnext[pb], axis=1) + np.sum(V[pb] * Xnext[pa], axis=1)))
         Gnext, Xnext = r["G"], r["X"]
-    return res.f, Xbar
+    return finish(res.f, Xbar)
 
 
 # =============================================================================================

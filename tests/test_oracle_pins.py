@@ -581,3 +581,29 @@ def test_unrolled_grad_without_updates_is_the_gradient():
     A = o.dense_A(g)
     np.testing.assert_allclose(grad, 4.0 * (A @ x0 + x0 @ (x0.T @ x0)), rtol=1e-12, atol=1e-14)
     assert abs(f - o.objective_dense(1, A, x0)) <= 1e-10 * abs(f)
+
+
+@pytest.mark.parametrize("T", [1, 6, 20])
+def test_unrolled_weight_grad_matches_central_differences(T):
+    """d f1(X_T) / d w for every listed weight, through T updates of OFM-f1 (A enters every G_t,
+    every line-search cubic and f1 itself), against central differences of the FP64 iteration on
+    the graph rebuilt from the perturbed weights (FP64 throughout, no FP32 rounding of S)."""
+    e = synth.sbm(60, 3, 8.0, 5.0, ratio_kind="count", seed=12, weighted=True)
+    src, dst, w = e.src, e.dst, e.w.astype(np.float64)
+    x0 = synth.initial_block(e.n, 3, 13).astype(np.float64)
+    g = o.build_graph(e.n, src, dst, w, exact=True)
+    f, gx, gw = o.unrolled_grad(g, x0, T, edges=(src, dst, w))
+    f2, gx2 = o.unrolled_grad(g, x0, T)
+    assert f == f2 and np.array_equal(gx, gx2)
+    rng = np.random.default_rng(T)
+    eps = 1e-6
+    for _ in range(3):
+        D = rng.standard_normal(w.shape)
+        fp = o.unrolled_objective(o.build_graph(e.n, src, dst, w + eps * D, exact=True), x0, T)
+        fm = o.unrolled_objective(o.build_graph(e.n, src, dst, w - eps * D, exact=True), x0, T)
+        fd = (fp - fm) / (2 * eps)
+        assert abs(float(np.sum(gw * D)) - fd) <= 2e-5 * abs(fd), (float(np.sum(gw * D)), fd)
+    # T = 0: the same as the plain weight gradient of f1
+    if T == 1:
+        _, _, gw0 = o.unrolled_grad(g, x0, 0, edges=(src, dst, w))
+        np.testing.assert_allclose(gw0, o.weight_grad(e.n, src, dst, w, x0, 1), rtol=1e-12, atol=1e-14)

@@ -6,7 +6,8 @@ X0 resident in HBM. By default the gathered block D^-1/2 V is stored in BF16 wit
 copy and FP32 accumulation (the configured mixed-precision form); the plain FP32 path is timed on
 the same steps and reported as `plain_fp32`. `value` is updates per second over all ranks. `e2e`
 times the same steps through the public API from pinned host buffers (X0 copied in, X copied out
-every step). The dominant kernel's roofline comes from CUDA-event phase timings taken inside the
+every step; the copies of neighbouring steps overlap the current step's iterations on a copy
+stream, and the serial form is reported beside it). The dominant kernel's roofline comes from CUDA-event phase timings taken inside the
 timed steps. `--impl reference` times the FP64 CPU oracle on the same workload instead.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference] [--gather bf16|fp32]
@@ -127,6 +128,9 @@ def parse():
     ap.add_argument("--spmm-engine", default="auto", choices=["auto", "simt", "tma"])
     ap.add_argument("--nodes", type=int, default=None, help="shrink the workload (testing only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--unrolled", type=int, default=0,
+                    help="time d f1(X_T)/d(X_0, w) through this many unrolled OFM-f1 updates instead")
+    ap.add_argument("--ckpt", type=int, default=5, help="checkpoint interval of --unrolled")
     return ap.parse_args()
 
 
@@ -410,7 +414,7 @@ def run_batch(args):
 
     # end to end: pinned host X0 -> device, one batched call, device -> pinned host X
     Xh0 = [x.cpu().pin_memory() for x in X0s]
-    Xh = [torch.empty_like(x) for x in Xh0]
+    Xh = [torch.empty_like(x).pin_memory() for x in Xh0]
 
     def step_e2e():
         for X, h in zip(Xs, Xh0):
@@ -439,6 +443,77 @@ def run_batch(args):
                 "clocks": clocks, "gpu_launches": launches,
                 "batched_direct_launch": {"value": direct, "ms_per_step": ms_direct},
                 "per_graph_loop": {"value": loop, "ms_per_step": ms_loop},
+                "parallelism": "replicas only" if world > 1 else "single GPU"}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def run_unrolled(args):
+    """One step = one ofsc_unrolled_grad call: T updates of OFM-f1 from X_0, checkpointed, and the
+    reverse sweep giving d f1(X_T) / d X_0 and, for a weighted graph, d f1(X_T) / d w.
+    `value` = gradients per second; the FP64 oracle's reverse sweep is timed as the CPU baseline."""
+    import torch
+
+    world, rank, local = dist_setup("nccl")
+    torch.cuda.set_device(local)
+    from paper_2305_10356_gb300 import build, ofsc, synth
+    build.build()
+    e, x0 = synth.workload(args.workload, n=args.nodes)
+    src, dst = torch.from_numpy(e.src).cuda(), torch.from_numpy(e.dst).cuda()
+    w = None if e.w is None else torch.from_numpy(e.w).cuda()
+    g = ofsc.ofsc_graph_build(e.n, src, dst, w)
+    X0 = torch.from_numpy(x0).cuda()
+    grad = torch.empty_like(X0)
+    gw = torch.empty(e.src.size, dtype=torch.float32, device="cuda") if w is not None else None
+    stream = torch.cuda.current_stream()
+    T = args.unrolled
+
+    def step():
+        return ofsc.ofsc_unrolled_grad(g, X0, T, grad, ckpt=args.ckpt, src=src if w is not None else None,
+                                       dst=dst if w is not None else None, grad_w=gw)
+
+    for _ in range(args.warmup):
+        step()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        step()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import numpy as np
+        from oracle import ofsc_oracle as o
+        og = o.build_graph(e.n, e.src, e.dst, None if e.w is None else e.w.astype(np.float64), exact=e.w is not None)
+        edges = None if e.w is None else (e.src, e.dst, e.w.astype(np.float64))
+        c0 = time.perf_counter()
+        o.unrolled_grad(og, x0.astype(np.float64), T, edges=edges)
+        secs = time.perf_counter() - c0
+        cpu = {"value": 1.0 / secs, "unit": "gradients/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": "one full FP64 unrolled gradient (numpy/scipy oracle, whole trajectory kept, no checkpoints)"}
+    if rank == 0:
+        spec = synth.WORKLOADS[args.workload]
+        line = {"metric": "unrolled gradients/s", "value": args.steps * world / (ms / 1000.0), "unit": "gradients/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": f"{args.workload}: N={e.n}, k={spec['n_blocks']}, "
+                                       f"{'weighted' if e.w is not None else 'binary'}; d f1(X_T)/dX_0"
+                                       f"{' and d/dw' if e.w is not None else ''} through T={T} OFM-f1 updates, "
+                                       f"checkpoint every {args.ckpt}",
+                           "T": T, "ckpt": args.ckpt},
+                "impl": "gpu", "cpu_baseline": cpu,
                 "parallelism": "replicas only" if world > 1 else "single GPU"}
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -527,28 +602,60 @@ def run_gpu(args):
         plain = {"value": updates / (p_ms / 1000.0), "unit": "iterations/s", "ms_per_step": p_ms / args.steps,
                  "gather": "fp32"}
 
-    # end to end: pinned host X0 -> device, iterate, device -> pinned host X
+    # end to end through the public API from pinned host buffers: every step uploads its X0 and
+    # downloads its X. Serial: upload, iterate, download. Pipelined (reported as `value`): two
+    # device buffers, the next step's upload and the previous step's download run on a copy
+    # stream while the current step iterates. Wall clock from a synchronised start to the last
+    # download, copy stream included.
     Xh0 = torch.from_numpy(x0).pin_memory()
-    Xh = torch.empty_like(Xh0).pin_memory()
-    Xd = torch.empty_like(X0)
-    torch.cuda.synchronize()
-    w0 = time.perf_counter()
-    e_start = torch.cuda.Event(enable_timing=True)
-    e_end = torch.cuda.Event(enable_timing=True)
-    e_start.record(stream)
-    for _ in range(args.steps):
-        Xd.copy_(Xh0, non_blocking=True)
-        ofsc.ofsc_iterate(g, method, Xd, 0.0, args.iters, gather=gather, spmm_engine=eng)
-        Xh.copy_(Xd, non_blocking=True)
-    e_end.record(stream)
-    torch.cuda.synchronize()
-    e2e_s = max(time.perf_counter() - w0, e_start.elapsed_time(e_end) / 1000.0)
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    Xh = [torch.empty_like(Xh0).pin_memory() for _ in range(2)]
+    Xd = [torch.empty_like(X0) for _ in range(2)]
+    copy = torch.cuda.Stream()
+    ev_in = [torch.cuda.Event() for _ in range(2)]
+    ev_done = [torch.cuda.Event() for _ in range(2)]
+
+    def e2e_run(pipelined: bool) -> float:
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        w0 = time.perf_counter()
+        if pipelined:
+            with torch.cuda.stream(copy):
+                Xd[0].copy_(Xh0, non_blocking=True)
+                ev_in[0].record(copy)
+        for i in range(args.steps):
+            cur = i % 2
+            if pipelined:
+                stream.wait_event(ev_in[cur])
+                if i + 1 < args.steps:
+                    nxt = (i + 1) % 2
+                    with torch.cuda.stream(copy):  # after the download of step i - 1 (same stream)
+                        Xd[nxt].copy_(Xh0, non_blocking=True)
+                        ev_in[nxt].record(copy)
+            else:
+                Xd[cur].copy_(Xh0, non_blocking=True)
+            ofsc.ofsc_iterate(g, method, Xd[cur], 0.0, args.iters, gather=gather, spmm_engine=eng)
+            if pipelined:
+                ev_done[cur].record(stream)
+                with torch.cuda.stream(copy):
+                    copy.wait_event(ev_done[cur])
+                    Xh[cur].copy_(Xd[cur], non_blocking=True)
+            else:
+                Xh[cur].copy_(Xd[cur], non_blocking=True)
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - w0
+        if world > 1:
+            t = torch.tensor([secs], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            secs = float(t.item())
+        return secs
+
+    e2e_serial_s = e2e_run(False)
+    e2e_s = e2e_run(True)
     e2e = {"value": updates / e2e_s, "unit": "iterations/s",
-           "h2d_bytes_per_step": int(x0.nbytes), "d2h_bytes_per_step": int(x0.nbytes)}
+           "h2d_bytes_per_step": int(x0.nbytes), "d2h_bytes_per_step": int(x0.nbytes),
+           "form": "pipelined: upload of step i+1 and download of step i-1 overlap step i",
+           "serial_value": updates / e2e_serial_s}
 
     # time to tolerance: the subspace angle to an FP32 reference run of 400 updates
     ttt = None
@@ -610,6 +717,8 @@ def main():
         return run_stream(args)
     if args.workload in synth.BATCHES:
         return run_batch(args)
+    if args.unrolled > 0:
+        return run_unrolled(args)
     return run_gpu(args)
 
 

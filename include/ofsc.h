@@ -231,6 +231,38 @@ ofsc_status ofsc_iterate_batched(int32_t count, ofsc_graph* const* graphs, int32
                                  const ofsc_opts* opts, ofsc_result* outs, void* stream);
 
 /*
+ * ofsc_unrolled_grad - the gradient, with respect to the starting block X_0, of f1 (Eq. (2)) at
+ * the block X_T reached by T updates of OFM-f1 (Algorithm 2 with the exact line search of
+ * Eq. (15), beta as in ofsc_iterate, A X recomputed every update, no stopping test).
+ *   k        columns (1 <= k <= 128)
+ *   X0       device float32 [n x k]
+ *   T        updates to differentiate through (0 <= T <= 4096; T = 0 gives grad f1(X_0))
+ *   ckpt     checkpoint interval (0: 5): the forward sweep keeps X_t, V_{t-1}, G_{t-1} every ckpt
+ *            updates and the reverse sweep recomputes one segment at a time, so the working set is
+ *            about 4 ckpt + 13 + 3 T / ckpt row blocks of n x k FP32 (k padded to a multiple of 8).
+ *            The result does not depend on ckpt (the recomputation repeats the same arithmetic).
+ *   m, src, dst  the edge list the (weighted) graph was built from, device int32 [m]; used only
+ *            with grad_w
+ *   f_out    HOST double* (nullable): f1(X_T)
+ *   grad     device float32 [n x k] (nullable): d f1(X_T) / d X_0
+ *   grad_w   device float32 [m] (nullable; weighted graphs only): d f1(X_T) / d w_e for every
+ *            listed edge, with A depending on the weights through S and D (listings of one pair
+ *            share a value, self-loops get 0), as for ofsc_weight_grad
+ * The step alpha_t is differentiated through the implicit-function theorem on the cubic, beta_t
+ * through its quotient (a column the restart rule set to 0 carries no derivative), G_t through
+ * its Hessian-vector product; for grad_w, A's adjoint collects 4 Gbar_t X_t^T from every G_t,
+ * c_t V_t X_{t+1}^T from every step's cubic and f1(X_T)'s own term, and is mapped to the
+ * weights per stored entry (an SDDMM per update). Allocates its working set for the call.
+ * Synchronises `stream`.
+ * Errors: OFSC_ERR_INVALID_ARG (also grad_w on an unweighted graph, an endpoint outside [0, n)),
+ * OFSC_ERR_OOM, OFSC_ERR_NONFINITE (non-finite value, or a step whose cubic has zero slope at
+ * its root, where the step is not differentiable), OFSC_ERR_CUDA.
+ */
+ofsc_status ofsc_unrolled_grad(ofsc_graph* g, int32_t k, const float* X0, int32_t T, int32_t ckpt,
+                               int64_t m, const int32_t* src, const int32_t* dst, double* f_out,
+                               float* grad, float* grad_w, void* stream);
+
+/*
  * ofsc_weight_grad - gradient of f1 (Eq. (2)) or f2 (Eq. (3)) at X with respect to the weight of
  * every listed edge of a weighted graph: with A_hat = D^-1/2 S D^-1/2 and Gamma = df/dA_hat
  * (2(I + A_hat - X X^T) for f1, -X(2I - X^T X)X^T for f2), a listing e of the pair {a, b}, a != b,

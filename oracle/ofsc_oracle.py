@@ -18,6 +18,8 @@ Paper map:
   Algorithm 2       column-wise nonlinear CG framework                     -> iterate
   Algorithm 1       row normalisation + K-means                            -> row_normalize, kmeans
   Sec. 5            ARI, relerr via Rayleigh-Ritz                          -> ari, rayleigh_ritz_relerr
+  Eqs. (2), (5), (15), Algorithm 2   f1 after T updates, differentiated     -> unrolled_grad
+                    in reverse through the updates (X_0 and edge weights)
 
 Readings of the paper taken where it is silent or ambiguous (each one is pinned by a test):
   * X_i, V_i in Eqs. (16), (18) are the first i columns; alpha_i moves the whole prefix.

@@ -52,8 +52,8 @@ inline int spmm_lanes_index(int lanes) {
 }
 // Lane groups of the sparse product: about 512 nonzeros each, between 1 and 4 blocks per SM.
 // Warps of the direction product (one row at a time per warp): about kRowNnz nonzeros each, at
-// least one full wave of 32 warps per SM and at most kRowMaxWarps, in blocks of
-// kRowWarpsPerBlock warps. Blocks of one warp retire as soon as their warp is done, so the
+// least OFSC_ROW_MIN_WARPS_PER_SM per SM (a small graph takes few SMs, leaving the rest to other
+// problems' kernels in a batch) and at most kRowMaxWarps, in blocks of kRowWarpsPerBlock warps. Blocks of one warp retire as soon as their warp is done, so the
 // hardware balances the load warp by warp (blocks of eight warps, held by their slowest warp,
 // measured 22-29% slower on the 2M-node, k = 128 graph). A warp takes a hub row whole, so a warp's
 // share must stay well above the largest degree. The macros exist for tuning builds.
@@ -66,13 +66,16 @@ inline int spmm_lanes_index(int lanes) {
 #ifndef OFSC_ROW_MAX_WARPS_PER_SM
 #define OFSC_ROW_MAX_WARPS_PER_SM 32
 #endif
+#ifndef OFSC_ROW_MIN_WARPS_PER_SM
+#define OFSC_ROW_MIN_WARPS_PER_SM 4
+#endif
 constexpr int kRowPart = 5;
 constexpr int kRowWarpsPerBlock = OFSC_ROW_WPB;
 constexpr int kRowNnz = OFSC_ROW_NNZ;
 constexpr int kRowMaxWarps = OFSC_ROW_MAX_WARPS_PER_SM * kNumSMs;
 inline int row_warps(int64_t nnz) {
   int64_t w = nnz / kRowNnz;
-  if (w < 32 * kNumSMs) w = 32 * kNumSMs;
+  if (w < OFSC_ROW_MIN_WARPS_PER_SM * kNumSMs) w = OFSC_ROW_MIN_WARPS_PER_SM * kNumSMs;
   if (w > kRowMaxWarps) w = kRowMaxWarps;
   return (int)ceil_div(w, kRowWarpsPerBlock) * kRowWarpsPerBlock;
 }
@@ -262,6 +265,9 @@ struct WgradArgs {
   float* grad;           // [m]
   int* bad;              // set when an endpoint is out of range
 };
+// Y = A X = -X - D^-1/2 S D^-1/2 X for an n x kp FP32 row block (kp a multiple of 8, rows 16-byte
+// aligned); scratch: n x kp FP32 (receives D^-1/2 X). Queued on s; no control block.
+cudaError_t apply_A(ofsc_graph* g, int kp, const float* X, float* Y, float* scratch, cudaStream_t s);
 cudaError_t wgrad_launch(const WgradArgs& w, cudaStream_t s);
 
 // Rayleigh-Ritz algebra of csrc/ritz.cu (k x k FP64; work holds [4][kp][kp] doubles).

@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "cubic.cuh"
 
 namespace ofsc {
 namespace {
@@ -395,15 +396,25 @@ __global__ void k_scale_rows(int64_t n, int kp, const float* __restrict__ X, con
 __global__ void k_dots_fold(const double* __restrict__ pw, int nw, const double* __restrict__ pg, int ng, int kp,
                             double* __restrict__ out, const Ctrl* ctrl) {
   if (ctrl->done) return;
-  const int r = blockIdx.x, R = gridDim.x;
-  for (int t = threadIdx.x; t < 2 * kp; t += blockDim.x) {
+  // 2 kp <= blockDim.x columns; blockDim.x / (2 kp) lane groups split this block's rows and are
+  // combined in group order
+  __shared__ double red[256];
+  const int r = blockIdx.x, R = gridDim.x, width = 2 * kp, groups = blockDim.x / width;
+  const int t = threadIdx.x % width, l = threadIdx.x / width;
+  if (l < groups) {
     const int which = t / kp, j = t % kp;
     const double* p = which ? pg : pw;
     const int nb = which ? ng : nw;
     const int b0 = (int)((int64_t)r * nb / R), b1 = (int)((int64_t)(r + 1) * nb / R);
     double sum = 0.0;
-    for (int b = b0; b < b1; ++b) sum += p[(int64_t)b * kp + j];
-    out[(int64_t)r * 2 * kp + t] = sum;
+    for (int b = b0 + l; b < b1; b += groups) sum += p[(int64_t)b * kp + j];
+    red[l * width + t] = sum;
+  }
+  __syncthreads();
+  if (threadIdx.x < width) {
+    double sum = 0.0;
+    for (int g = 0; g < groups; ++g) sum += red[g * width + threadIdx.x];
+    out[(int64_t)r * width + threadIdx.x] = sum;
   }
 }
 
@@ -697,12 +708,27 @@ __global__ void k_beta(const double* __restrict__ colpart, int nblk, int kp, flo
                        double* beta64, double* dE, Ctrl* ctrl, int first, int eval) {
   if (!eval && ctrl->done) return;
   __shared__ double sh[256];
+  __shared__ double lanes[256 * kColSums];  // [lane group][kColSums][kp]
   const int j = threadIdx.x;
+  // the blocks' rows are split over 256 / kp lane groups, then combined in group order
+  {
+    const int ng = 256 / kp, c = j % kp, l = j / kp;
+    if (l < ng) {
+      double acc[kColSums] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+      for (int b = l; b < nblk; b += ng) {
+        const double* p = colpart + (int64_t)b * kColSums * kp;
+#pragma unroll
+        for (int q = 0; q < kColSums; ++q) acc[q] += p[q * kp + c];
+      }
+#pragma unroll
+      for (int q = 0; q < kColSums; ++q) lanes[(l * kColSums + q) * kp + c] = acc[q];
+    }
+  }
+  __syncthreads();
   double gg = 0.0, num = 0.0, den = 0.0, gy = 0.0, vy = 0.0, vg = 0.0;
   if (j < kp) {
-#pragma unroll 8
-    for (int b = 0; b < nblk; ++b) {
-      const double* p = colpart + (int64_t)b * kColSums * kp;
+    for (int l = 0; l < 256 / kp; ++l) {
+      const double* p = lanes + l * kColSums * kp;
       gg += p[j];
       num += p[kp + j];
       den += p[2 * kp + j];
@@ -901,16 +927,27 @@ __global__ void __launch_bounds__(256) k_gram(GramArgs a) {
     }
 }
 
-__global__ void k_gram_reduce(const double* __restrict__ part, int gy, int kp, int slot_mask,
-                              double* __restrict__ gram, Ctrl* ctrl, int ignore_done) {
+// Blocks of 32 consecutive entries (one slot each, as kp^2 is a multiple of 64): warp w sums the
+// row groups w, w + 8, ... (coalesced, one entry per lane); the eight warp sums are added in warp
+// order.
+__global__ void __launch_bounds__(256) k_gram_reduce(const double* __restrict__ part, int gy, int kp, int slot_mask,
+                                                     double* __restrict__ gram, Ctrl* ctrl, int ignore_done) {
   if (!ignore_done && ctrl->done) return;
-  const int kk = kp * kp;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kPairs * kk; i += gridDim.x * blockDim.x) {
-    const int slot = i / kk;
-    if (!((slot_mask >> slot) & 1)) continue;
+  __shared__ double ws[8][32];
+  const int kk = kp * kp, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int base = blockIdx.x * 32; base < kPairs * kk; base += gridDim.x * 32) {
+    if (!((slot_mask >> (base / kk)) & 1)) continue;  // uniform over the block
+    const int i = base + lane;
     double s = 0.0;
-    for (int b = 0; b < gy; ++b) s += part[(int64_t)b * kPairs * kk + i];
-    gram[i] = s;
+    for (int b = warp; b < gy; b += 8) s += part[(int64_t)b * kPairs * kk + i];
+    ws[warp][lane] = s;
+    __syncthreads();
+    if (warp == 0) {
+      double t = 0.0;
+      for (int w = 0; w < 8; ++w) t += ws[w][lane];
+      gram[i] = t;
+    }
+    __syncthreads();
   }
 }
 
@@ -918,89 +955,6 @@ __global__ void k_gram_reduce(const double* __restrict__ part, int gy, int kp, i
 // FP64 line search (one block): cubic coefficients, real roots, alpha, next X^T X and X^T AX
 // ------------------------------------------------------------------------------------------
 
-// Real roots of c3 a^3 + c2 a^2 + c1 a + c0; returns the count (0..3).
-__device__ int real_roots(double c3, double c2, double c1, double c0, double* r) {
-  if (c3 == 0.0) {
-    if (c2 == 0.0) {
-      if (c1 == 0.0) return 0;
-      r[0] = -c0 / c1;
-      return 1;
-    }
-    const double disc = c1 * c1 - 4.0 * c2 * c0;
-    if (disc < 0.0) return 0;
-    const double q = -0.5 * (c1 + copysign(sqrt(disc), c1));
-    if (q == 0.0) {
-      r[0] = 0.0;
-      return 1;
-    }
-    r[0] = q / c2;
-    r[1] = c0 / q;
-    return 2;
-  }
-  // monic form a^3 + A a^2 + B a + C, shift a = t - A/3: t^3 + p t + q
-  const double A = c2 / c3, B = c1 / c3, C = c0 / c3;
-  const double p = B - A * A / 3.0;
-  const double q = 2.0 * A * A * A / 27.0 - A * B / 3.0 + C;
-  const double h = -A / 3.0;
-  const double D = 0.25 * q * q + p * p * p / 27.0;
-  int cnt;
-  if (D > 0.0) {
-    const double u = cbrt(-0.5 * q - copysign(sqrt(D), q));
-    r[0] = (u != 0.0 ? u - p / (3.0 * u) : 0.0) + h;
-    cnt = 1;
-  } else if (D == 0.0) {
-    if (p == 0.0) {
-      r[0] = h;
-      return 1;
-    }
-    r[0] = 3.0 * q / p + h;      // simple root
-    r[1] = -1.5 * q / p + h;     // double root
-    cnt = 2;
-  } else {
-    const double m = 2.0 * sqrt(-p / 3.0);
-    double arg = 1.5 * q / p * sqrt(-3.0 / p);
-    arg = fmax(-1.0, fmin(1.0, arg));
-    const double th = acos(arg) / 3.0;
-    const double two_pi_3 = 2.0943951023931954923;
-    for (int i = 0; i < 3; ++i) r[i] = m * cos(th - two_pi_3 * i) + h;
-    cnt = 3;
-  }
-  for (int i = 0; i < cnt; ++i) {  // two Newton steps on the original cubic
-    for (int s = 0; s < 2; ++s) {
-      const double x = r[i];
-      const double f = ((c3 * x + c2) * x + c1) * x + c0;
-      const double d = (3.0 * c3 * x + 2.0 * c2) * x + c1;
-      if (d != 0.0) {
-        const double nx = x - f / d;
-        if (isfinite(nx)) r[i] = nx;
-      }
-    }
-  }
-  return cnt;
-}
-
-// The step: the real root where q(a) = c3 a^4/4 + c2 a^3/3 + c1 a^2/2 + c0 a is smallest
-// (for OFM, q is the objective along the line up to a constant factor). An exact double root
-// never beats the simple root, so the paper's three cases all reduce to this rule.
-__device__ double pick_step(double c3, double c2, double c1, double c0, int* bad) {
-  if (!(isfinite(c3) && isfinite(c2) && isfinite(c1) && isfinite(c0))) {
-    *bad = 1;
-    return 0.0;
-  }
-  double r[3];
-  const int n = real_roots(c3, c2, c1, c0, r);
-  if (n == 0) return 0.0;
-  double best = r[0], bq = 0.0;
-  for (int i = 0; i < n; ++i) {
-    const double x = r[i];
-    const double qv = ((0.25 * c3 * x + c2 / 3.0) * x + 0.5 * c1) * x * x + c0 * x;
-    if (i == 0 || qv < bq || (qv == bq && (fabs(x) < fabs(best) || (fabs(x) == fabs(best) && x < best)))) {
-      best = x;
-      bq = qv;
-    }
-  }
-  return best;
-}
 
 template <int NV>
 __device__ void block_sum(double (&v)[NV], double* sh) {
@@ -1016,7 +970,10 @@ __device__ void block_sum(double (&v)[NV], double* sh) {
   __syncthreads();
 }
 
-constexpr int kSolveBlocks = 128;  // blocks of the trace and update passes (>= kMaxK: one column each)
+constexpr int kSolveBlocks = 128;  // most blocks of the trace and update passes (>= kMaxK)
+
+// Blocks of the trace and update passes: one per 256 k x k entries, at least 8.
+inline int solve_blocks(int kp) { return std::max(8, std::min(kSolveBlocks, (kp * kp + 255) / 256)); }
 constexpr int kSolveSums = 16;     // per-block partial sums of the trace pass
 
 struct SolveArgs {
@@ -1038,13 +995,14 @@ struct SolveArgs {
   Ctrl* ctrl;
   double alpha0;  // > 0: fixed step for update 0 instead of the line search
   double* part;   // scratch: [kSolveBlocks][kSolveSums] trace partials, [kp][4] diagonals, [kp][4] cubics
+  int tblocks;    // blocks of the trace pass (rows of trace partials)
 };
 
 // C = V^T A V and B = X^T A X are symmetric; the recurrences leave rounding asymmetry.
 #define SYM(M, i, j) (0.5 * ((M)[(i) * kp + (j)] + (M)[(j) * kp + (i)]))
 
-// Line search, pass 1 of 3 (kSolveBlocks blocks). Block b: the diagonals diag(V^T AV), diag(V^T AX)
-// and diag(V^T G) of column b; for TriOFM the cubic of column b alone (Eqs. (16)/(18) before the
+// Line search, pass 1 of 3 (nb = solve_blocks(kp) blocks). Block b: the diagonals diag(V^T AV), diag(V^T AX)
+// and diag(V^T G) of columns b, b + nb, ...; for TriOFM their cubics alone (Eqs. (16)/(18) before the
 // prefix sum); and its slice of the k x k traces that make up f(X_t) and the OFM cubic (Eq. (15)).
 // Per-block partial sums go to a.part in a fixed order. Partial layout (v[0..14]):
 //   v[0..2]   tr B, ||R||_F^2, tr(R B)                         (objective)
@@ -1173,7 +1131,7 @@ __global__ void __launch_bounds__(256) k_solve(SolveArgs a) {
   if (tid == 0) bad = 0;
   double v[15];
 #pragma unroll
-  for (int q = 0; q < 15; ++q) v[q] = tid < kSolveBlocks ? a.part[tid * kSolveSums + q] : 0.0;
+  for (int q = 0; q < 15; ++q) v[q] = tid < a.tblocks ? a.part[tid * kSolveSums + q] : 0.0;
   if (tid < kp) {
     if (f2) {
       v[14] += diag[4 * tid + 2];  // tr(V^T G)
@@ -1272,7 +1230,7 @@ __global__ void __launch_bounds__(256) k_solve(SolveArgs a) {
   }
 }
 
-// Line search, pass 3 of 3 (kSolveBlocks blocks): X' = X + V diag(al), AX' = AX + AV diag(al) give
+// Line search, pass 3 of 3 (solve_blocks(kp) blocks): X' = X + V diag(al), AX' = AX + AV diag(al) give
 //   X'^T X'  = R + diag(al) P + P^T diag(al) + diag(al) Q diag(al)
 //   X'^T AX' = B + E^T diag(al) + diag(al) E + diag(al) C diag(al)
 // element by element in FP64 (each element read and written by one thread, so in place).
@@ -1553,7 +1511,7 @@ cudaError_t launch_gram(Workspace& ws, const GramPairs& pairs, int npairs, int s
     prof->begin(OFSC_PHASE_GRAM_REDUCE);
   }
   const int total = kPairs * ws.kp * ws.kp;
-  k_gram_reduce<<<(int)std::min<int64_t>(ceil_div(total, 256), 4 * kNumSMs), 256, 0, s>>>(
+  k_gram_reduce<<<(int)std::min<int64_t>(ceil_div(total, 32), 8 * kNumSMs), 256, 0, s>>>(
       ws.gram_part, gy, ws.kp, slot_mask, ws.gram, ws.ctrl, ignore_done);
   if (prof) prof->end();
   g_launches += 2;
@@ -1830,10 +1788,11 @@ struct Runner {
     sa.ctrl = ws.ctrl;
     sa.alpha0 = alpha0;
     sa.part = ws.solve;
+    sa.tblocks = solve_blocks(ws.kp);
     prof.begin(OFSC_PHASE_LINESEARCH);
-    k_solve_traces<<<kSolveBlocks, 256, 0, s>>>(sa);
+    k_solve_traces<<<sa.tblocks, 256, 0, s>>>(sa);
     k_solve<<<1, 256, 0, s>>>(sa);
-    k_solve_update<<<kSolveBlocks, 256, 0, s>>>(sa);
+    k_solve_update<<<sa.tblocks, 256, 0, s>>>(sa);
     g_launches += 3;
     prof.end();
     return cudaGetLastError();
@@ -1850,6 +1809,28 @@ ofsc_status finish(Workspace& ws, cudaStream_t s, Ctrl* out) {
 }
 
 }  // namespace
+
+cudaError_t apply_A(ofsc_graph* g, int kp, const float* X, float* Y, float* scratch, cudaStream_t s) {
+  if (g->n == 0) return cudaSuccess;
+  k_scale_rows<<<(int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(g->n * kp / 4, 256), 8 * kNumSMs)), 256, 0, s>>>(
+      g->n, kp, X, g->dinv, scratch, nullptr, 1);
+  SpmmArgs a{};
+  a.n = g->n;
+  a.kp = kp;
+  a.row_ptr = g->row_ptr;
+  a.col = g->col;
+  a.val = g->val;
+  a.dinv = g->dinv;
+  a.bnd = g->bnd[kRowPart];
+  a.groups = g->groups[kRowPart];
+  a.gather = scratch;
+  a.base = X;
+  a.out = Y;
+  a.ignore_done = 1;
+  launch_spmm_dir(a, g->weighted != 0, false, s);
+  return cudaGetLastError();
+}
+
 }  // namespace ofsc
 
 using namespace ofsc;
@@ -2547,7 +2528,7 @@ extern "C" ofsc_status ofsc_objective_grad_noalloc(const ofsc_graph* gc, int32_t
     case 2: k_gram<2><<<grid, 256, 0, s>>>(ga); break;
     default: k_gram<4><<<grid, 256, 0, s>>>(ga); break;
   }
-  k_gram_reduce<<<(int)std::min<int64_t>(ceil_div(kPairs * kp * kp, 256), 4 * kNumSMs), 256, 0, s>>>(
+  k_gram_reduce<<<(int)std::min<int64_t>(ceil_div(kPairs * kp * kp, 32), 8 * kNumSMs), 256, 0, s>>>(
       ws.gram_part, gy, kp, (1 << G_R) | (1 << G_B), ws.gram, ws.ctrl, 0);
   k_set_rb<<<1, 256, 0, s>>>(ws.gram, kp, objective, ws.Rn, ws.Bn, nullptr, nullptr, ws.ctrl, 0);
   OFSC_LAUNCH_CHECK("noalloc: refresh");

@@ -94,6 +94,7 @@ def lib() -> ctypes.CDLL:
             "ofsc_iterate_batched": [i32, ctypes.POINTER(vp), i32, ctypes.POINTER(i32), ctypes.POINTER(vp), dbl,
                                      i32, ctypes.POINTER(Opts), ctypes.POINTER(Result), vp],
             "ofsc_rayleigh_ritz": [vp, i32, vp, vp, ctypes.POINTER(dbl), vp],
+            "ofsc_unrolled_grad": [vp, i32, vp, i32, i32, i64, vp, vp, ctypes.POINTER(dbl), vp, vp, vp],
             "ofsc_weight_grad": [vp, i32, i32, vp, i64, vp, vp, vp, vp],
             "ofsc_row_normalize": [i64, i32, vp, vp],
             "ofsc_gram": [i64, i32, i32, vp, i32, ctypes.POINTER(vp), i64, vp, vp],
@@ -238,6 +239,18 @@ def ofsc_gram(L, Rs, out, k: int | None = None, rows_per_block: int = 0, stream=
     arr = (ctypes.c_void_p * len(Rs))(*[_ptr(r) for r in Rs])
     _check(lib().ofsc_gram(n, ld if k is None else k, ld, _ptr(L), len(Rs), arr, rows_per_block,
                            _ptr(out), _stream(stream)))
+
+
+def ofsc_unrolled_grad(g: Graph, X0, T: int, grad=None, ckpt: int = 0, src=None, dst=None, grad_w=None,
+                       stream=None) -> float:
+    """d f1(X_T) / d X_0 through T updates of OFM-f1 into the device block grad (n x k, FP32), and
+    d f1(X_T) / d w into grad_w (one FP32 per listed edge of src, dst) for a weighted graph;
+    returns f1(X_T)."""
+    f = ctypes.c_double(0.0)
+    m = 0 if src is None else int(src.numel())
+    _check(lib().ofsc_unrolled_grad(g.handle, int(X0.shape[1]), _ptr(X0), int(T), int(ckpt), m, _ptr(src),
+                                    _ptr(dst), ctypes.byref(f), _ptr(grad), _ptr(grad_w), _stream(stream)))
+    return f.value
 
 
 def ofsc_weight_grad(g: Graph, objective: int, X, src, dst, grad, stream=None) -> None:

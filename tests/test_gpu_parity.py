@@ -535,3 +535,68 @@ def test_batched_rejects_bad_arguments():
     with pytest.raises(ofsc.OfscError):
         ofsc.ofsc_iterate_batched([g], 7, [X], 0.0, 3)
     assert ofsc.ofsc_iterate_batched([], o.OFM_F1, [], 0.0, 3) == []
+
+
+@pytest.mark.parametrize("case", ["sbm_k8", "wsbm_k32"])
+def test_unrolled_grad_matches_oracle(case):
+    """d f1(X_20) / d X_0 (and d/dw on the weighted graph) through 20 updates of OFM-f1,
+    checkpointed every 5 updates, against the oracle's reverse accumulation in FP64 (itself pinned
+    by central differences); the same bits for every checkpoint interval, and T = 0 gives
+    grad f1(X_0).
+
+    Tolerance: after 20 line-searched updates the gradient is ill-conditioned: the oracle's own
+    result moves by ~1e-3 (relative) when X_0 moves by 1e-7, the size of one FP32 rounding. The
+    GPU result, computed in FP32, is allowed 10x that measured sensitivity (at least 1e-3)."""
+    import torch
+    if case == "sbm_k8":
+        e = synth.sbm(1500, 8, 16.0, 5.0, ratio_kind="count", seed=131)
+        k = 8
+    else:
+        e = synth.sbm(2000, 32, 32.0, 10.0, seed=132, weighted=True)
+        k = 32
+    weighted = e.w is not None
+    og = o.build_graph(e.n, e.src, e.dst, None if not weighted else e.w.astype(np.float64), exact=weighted)
+    g = gpu_graph(e)
+    x0 = synth.initial_block(e.n, k, 133)
+    T = 20
+    if weighted:
+        f_ref, g_ref, w_ref = o.unrolled_grad(og, x0.astype(np.float64), T,
+                                              edges=(e.src, e.dst, e.w.astype(np.float64)))
+    else:
+        f_ref, g_ref = o.unrolled_grad(og, x0.astype(np.float64), T)
+    rng = np.random.default_rng(134)
+    xp = x0.astype(np.float64) * (1.0 + 1e-7 * rng.standard_normal(x0.shape))
+    if weighted:
+        _, gp, wp = o.unrolled_grad(og, xp, T, edges=(e.src, e.dst, e.w.astype(np.float64)))
+        wtol = max(1e-3, 10.0 * np.linalg.norm(wp - w_ref) / np.linalg.norm(w_ref))
+    else:
+        _, gp = o.unrolled_grad(og, xp, T)
+    tol = max(1e-3, 10.0 * np.linalg.norm(gp - g_ref) / np.linalg.norm(g_ref))
+    X0 = torch.from_numpy(x0).cuda()
+    src, dst, _ = upload(e)
+    outs = {}
+    for ckpt in (5, 1, 7, 20):
+        grad = torch.empty_like(X0)
+        gw = torch.full((e.src.size,), float("nan"), dtype=torch.float32, device="cuda") if weighted else None
+        f = ofsc.ofsc_unrolled_grad(g, X0, T, grad, ckpt=ckpt, src=src if weighted else None,
+                                    dst=dst if weighted else None, grad_w=gw)
+        outs[ckpt] = (f, grad.cpu().numpy(), None if gw is None else gw.cpu().numpy())
+    f, G, W = outs[5]
+    assert abs(f - f_ref) <= 1e-5 * abs(f_ref)
+    err = np.linalg.norm(G - g_ref) / np.linalg.norm(g_ref)
+    assert err <= tol, (err, tol)
+    if weighted:
+        werr = np.linalg.norm(W - w_ref) / np.linalg.norm(w_ref)
+        assert werr <= wtol, (werr, wtol)
+    for ckpt in (1, 7, 20):
+        assert outs[ckpt][0] == f and np.array_equal(outs[ckpt][1], G)
+        if weighted:
+            assert np.array_equal(outs[ckpt][2], W)
+    grad0 = torch.empty_like(X0)
+    f0 = ofsc.ofsc_unrolled_grad(g, X0, 0, grad0)
+    Gd = torch.empty_like(X0)
+    fo = ofsc.ofsc_objective_grad(g, 1, X0, Gd)
+    assert abs(f0 - fo) <= 1e-6 * abs(fo)
+    # the two paths form X^T X on different engines (tensor cores vs. CUDA cores): FP32 rounding apart
+    G0, Gr = grad0.cpu().numpy(), Gd.cpu().numpy()
+    assert np.linalg.norm(G0 - Gr) <= 1e-5 * np.linalg.norm(Gr)

@@ -359,6 +359,9 @@ def run_batch(args):
         graphs.append(ofsc.ofsc_graph_build(e.n, src, dst))
         X0s.append(torch.from_numpy(x0).cuda())
     nnz = sum(int(g.info().nnz) for g in graphs)
+    # the row-partition granularity of each graph's direction product, by timing (outside the
+    # timed steps)
+    tuned = [ofsc.ofsc_autotune(g, x.shape[1], gather)[0] // NUM_SMS for g, x in zip(graphs, X0s)]
     Xs = [torch.empty_like(x) for x in X0s]
     stream = torch.cuda.current_stream()
 
@@ -437,7 +440,8 @@ def run_batch(args):
                                        f"{spec['ratio']:g}:1 (edge counts); sum N = {sum(x.shape[0] for x in X0s)}, "
                                        f"sum nnz = {nnz}",
                            "updates_per_graph_per_step": args.iters, "method": METHOD_LABEL[args.method],
-                           "gather": args.gather, "l2": "state of all graphs about 1 GB, larger than L2"},
+                           "gather": args.gather, "l2": "state of all graphs about 1 GB, larger than L2",
+                           "autotuned_warps_per_sm": {str(w): tuned.count(w) for w in sorted(set(tuned))}},
                 "impl": "gpu", "e2e": {"value": e2e_v, "unit": "iterations/s (summed over graphs)",
                                        "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
                 "clocks": clocks, "gpu_launches": launches,

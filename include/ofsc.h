@@ -263,6 +263,23 @@ ofsc_status ofsc_unrolled_grad(ofsc_graph* g, int32_t k, const float* X0, int32_
                                float* grad, float* grad_w, void* stream);
 
 /*
+ * ofsc_autotune - picks, by timing, how finely the direction product (the sparse product of
+ * Sec. 3.3, the largest part of an update of Algorithm 2) splits this graph's rows among warps:
+ * 4, 8, 16 or 32 warps per SM (coarser ones only while each warp keeps at least 16 nonzeros), for
+ * k columns and the given gather storage. The fastest is kept in the handle and used by every
+ * later call on it. Each warp sums its rows' share of diag(V^T AV) before a fixed-order fold, so a
+ * new choice can change the last bits of later results (never the rows of A V).
+ *   k         columns (1 <= k <= 128)
+ *   gather    OFSC_GATHER_FP32 or OFSC_GATHER_BF16
+ *   warps_out HOST int32* (nullable): the chosen number of warps
+ *   ms_out    HOST double* (nullable): its time per product in milliseconds
+ * Uses the handle's workspace (allocated for k if needed; its blocks are overwritten).
+ * Synchronises `stream`. Errors: OFSC_ERR_INVALID_ARG, OFSC_ERR_OOM, OFSC_ERR_CUDA.
+ */
+ofsc_status ofsc_autotune(ofsc_graph* g, int32_t k, int32_t gather, int32_t* warps_out, double* ms_out,
+                          void* stream);
+
+/*
  * ofsc_weight_grad - gradient of f1 (Eq. (2)) or f2 (Eq. (3)) at X with respect to the weight of
  * every listed edge of a weighted graph: with A_hat = D^-1/2 S D^-1/2 and Gamma = df/dA_hat
  * (2(I + A_hat - X X^T) for f1, -X(2I - X^T X)X^T for f2), a listing e of the pair {a, b}, a != b,

@@ -268,6 +268,9 @@ struct WgradArgs {
 // Y = A X = -X - D^-1/2 S D^-1/2 X for an n x kp FP32 row block (kp a multiple of 8, rows 16-byte
 // aligned); scratch: n x kp FP32 (receives D^-1/2 X). Queued on s; no control block.
 cudaError_t apply_A(ofsc_graph* g, int kp, const float* X, float* Y, float* scratch, cudaStream_t s);
+// Replaces the direction product's row partition (bnd[kRowPart]) with `warps` nnz-balanced row
+// ranges; synchronises s.
+ofsc_status set_row_partition(ofsc_graph* g, int warps, cudaStream_t s);
 cudaError_t wgrad_launch(const WgradArgs& w, cudaStream_t s);
 
 // Rayleigh-Ritz algebra of csrc/ritz.cu (k x k FP64; work holds [4][kp][kp] doubles).

@@ -183,6 +183,24 @@ struct Scratch {
 };
 
 }  // namespace
+
+ofsc_status set_row_partition(ofsc_graph* g, int warps, cudaStream_t s) {
+  if (warps < 1 || warps > kRowMaxWarps) return fail(OFSC_ERR_INVALID_ARG, "row partition: %d warps", warps);
+  int64_t* nb = nullptr;
+  OFSC_CUDA(cudaMalloc(&nb, (size_t)(warps + 1) * sizeof(int64_t)));
+  k_partition<<<grid_for(warps + 1), 256, 0, s>>>(g->n, g->row_ptr, warps, nb);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    cudaFree(nb);
+    return cuda_fail(e, "row partition");
+  }
+  cudaFree(g->bnd[kRowPart]);  // synchronises with any queued use of the old ranges
+  g->bnd[kRowPart] = nb;
+  g->groups[kRowPart] = warps;
+  return OFSC_OK;
+}
+
 }  // namespace ofsc
 
 using namespace ofsc;

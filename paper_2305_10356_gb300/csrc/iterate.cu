@@ -2185,6 +2185,91 @@ extern "C" ofsc_status ofsc_iterate(ofsc_graph* g, int32_t method, int32_t k, fl
 }
 
 // ==========================================================================================
+// ofsc_autotune: the row-partition granularity of the direction product, chosen by timing.
+// ==========================================================================================
+
+extern "C" ofsc_status ofsc_autotune(ofsc_graph* g, int32_t k, int32_t gather, int32_t* warps_out, double* ms_out,
+                                     void* stream_) {
+  clear_error();
+  if (!g) return fail(OFSC_ERR_INVALID_ARG, "ofsc_autotune: graph is NULL");
+  if (k < 1 || k > kMaxK) return fail(OFSC_ERR_INVALID_ARG, "ofsc_autotune: k=%d outside [1, %d]", k, kMaxK);
+  if (gather != OFSC_GATHER_FP32 && gather != OFSC_GATHER_BF16)
+    return fail(OFSC_ERR_INVALID_ARG, "ofsc_autotune: unknown gather mode %d", gather);
+  cudaStream_t s = (cudaStream_t)stream_;
+  if (g->n == 0 || g->nnz == 0) {
+    if (warps_out) *warps_out = g->groups[kRowPart];
+    if (ms_out) *ms_out = 0.0;
+    return OFSC_OK;
+  }
+  const int kp = round_up(k, 8);
+  ofsc_status st = ensure_workspace(g, kp);
+  if (st != OFSC_OK) return st;
+  Workspace& ws = g->ws;
+  const bool bf16 = gather == OFSC_GATHER_BF16;
+  // timing depends on the access pattern only: zero blocks
+  OFSC_CUDA(cudaMemsetAsync(ws.V, 0, (size_t)g->n * kp * sizeof(float), s));
+  OFSC_CUDA(cudaMemsetAsync(ws.Vh, 0, (size_t)g->n * kp * sizeof(float), s));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  OFSC_CUDA(cudaEventCreate(&e0));
+  cudaError_t ce = cudaEventCreate(&e1);
+  if (ce != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cuda_fail(ce, "ofsc_autotune: cudaEventCreate");
+  }
+  struct Ev {
+    cudaEvent_t a, b;
+    ~Ev() {
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+    }
+  } ev{e0, e1};
+  const int min_wps = OFSC_ROW_MIN_WARPS_PER_SM, max_wps = OFSC_ROW_MAX_WARPS_PER_SM;
+  int best_w = 0;
+  float best_ms = 0.0f;
+  for (int wps = min_wps; wps <= max_wps; wps *= 2) {
+    const int W = wps * kNumSMs;
+    if (wps > min_wps && (int64_t)W * 16 > g->nnz) break;  // at least 16 nonzeros per warp
+    st = set_row_partition(g, W, s);
+    if (st != OFSC_OK) return st;
+    SpmmArgs a{};
+    a.n = g->n;
+    a.kp = kp;
+    a.row_ptr = g->row_ptr;
+    a.col = g->col;
+    a.val = g->val;
+    a.dinv = g->dinv;
+    a.bnd = g->bnd[kRowPart];
+    a.groups = g->groups[kRowPart];
+    a.gather = ws.Vh;
+    a.base = ws.V;
+    a.out = ws.W;
+    a.dots = ws.dots;
+    a.ctrl = ws.ctrl;
+    a.ignore_done = 1;
+    launch_spmm_dir(a, g->weighted != 0, bf16, s);  // warm
+    OFSC_CUDA(cudaEventRecord(e0, s));
+    for (int r = 0; r < 3; ++r) launch_spmm_dir(a, g->weighted != 0, bf16, s);
+    OFSC_CUDA(cudaEventRecord(e1, s));
+    OFSC_CUDA(cudaEventSynchronize(e1));
+    OFSC_LAUNCH_CHECK("ofsc_autotune: direction product");
+    float ms = 0.0f;
+    OFSC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    ms /= 3.0f;
+    if (best_w == 0 || ms < best_ms) {
+      best_w = W;
+      best_ms = ms;
+    }
+  }
+  if (g->groups[kRowPart] != best_w) {
+    st = set_row_partition(g, best_w, s);
+    if (st != OFSC_OK) return st;
+  }
+  if (warps_out) *warps_out = best_w;
+  if (ms_out) *ms_out = best_ms;
+  return OFSC_OK;
+}
+
+// ==========================================================================================
 // ofsc_iterate_batched: Algorithm 2 on many independent graphs at once.
 //
 // Each graph runs on a stream of its own (owned by its handle), forked from the caller's stream,

@@ -95,6 +95,7 @@ def lib() -> ctypes.CDLL:
                                      i32, ctypes.POINTER(Opts), ctypes.POINTER(Result), vp],
             "ofsc_rayleigh_ritz": [vp, i32, vp, vp, ctypes.POINTER(dbl), vp],
             "ofsc_unrolled_grad": [vp, i32, vp, i32, i32, i64, vp, vp, ctypes.POINTER(dbl), vp, vp, vp],
+            "ofsc_autotune": [vp, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(dbl), vp],
             "ofsc_weight_grad": [vp, i32, i32, vp, i64, vp, vp, vp, vp],
             "ofsc_row_normalize": [i64, i32, vp, vp],
             "ofsc_gram": [i64, i32, i32, vp, i32, ctypes.POINTER(vp), i64, vp, vp],
@@ -239,6 +240,15 @@ def ofsc_gram(L, Rs, out, k: int | None = None, rows_per_block: int = 0, stream=
     arr = (ctypes.c_void_p * len(Rs))(*[_ptr(r) for r in Rs])
     _check(lib().ofsc_gram(n, ld if k is None else k, ld, _ptr(L), len(Rs), arr, rows_per_block,
                            _ptr(out), _stream(stream)))
+
+
+def ofsc_autotune(g: Graph, k: int, gather: int = GATHER_FP32, stream=None) -> tuple[int, float]:
+    """Times the direction product at several row-partition granularities and keeps the fastest in
+    the handle; returns (warps, ms per product)."""
+    w = ctypes.c_int32(0)
+    ms = ctypes.c_double(0.0)
+    _check(lib().ofsc_autotune(g.handle, int(k), int(gather), ctypes.byref(w), ctypes.byref(ms), _stream(stream)))
+    return w.value, ms.value
 
 
 def ofsc_unrolled_grad(g: Graph, X0, T: int, grad=None, ckpt: int = 0, src=None, dst=None, grad_w=None,

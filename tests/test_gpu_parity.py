@@ -600,3 +600,21 @@ def test_unrolled_grad_matches_oracle(case):
     # the two paths form X^T X on different engines (tensor cores vs. CUDA cores): FP32 rounding apart
     G0, Gr = grad0.cpu().numpy(), Gd.cpu().numpy()
     assert np.linalg.norm(G0 - Gr) <= 1e-5 * np.linalg.norm(Gr)
+
+
+def test_autotune_keeps_results_within_rounding():
+    """ofsc_autotune picks a row-partition granularity (4..32 warps per SM) by timing; the first
+    five updates after it still match the oracle, and every granularity tried gives the same A V
+    rows (only the fold of diag(V^T AV) changes its rounding)."""
+    e = synth.sbm(20000, 16, 24.0, 5.0, ratio_kind="count", seed=141)
+    og = o.build_graph(e.n, e.src, e.dst)
+    g = gpu_graph(e)
+    x0 = synth.initial_block(e.n, 16, 142)
+    Xa, ra, _ = run_iterate(g, o.OFM_F1, x0, 0.0, 5)
+    w, ms = ofsc.ofsc_autotune(g, 16, ofsc.GATHER_BF16)
+    assert w in [m * 152 for m in (4, 8, 16, 32)] and ms > 0.0
+    Xb, rb, _ = run_iterate(g, o.OFM_F1, x0, 0.0, 5)
+    ref = o.iterate(og, o.OFM_F1, x0, 0.0, 5)
+    for X in (Xa, Xb):
+        assert np.linalg.norm(X - ref.X) <= 1e-4 * np.linalg.norm(ref.X)
+    assert np.linalg.norm(Xa - Xb) <= 1e-5 * np.linalg.norm(Xa)

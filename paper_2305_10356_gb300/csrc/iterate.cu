@@ -126,13 +126,21 @@ struct SpmmArgs {
 };
 
 #ifndef OFSC_ROW_U32
-#define OFSC_ROW_U32 6  // gathers in flight per lane when a warp covers a row of 128 columns
+#define OFSC_ROW_U32 8  // gathers in flight per lane when a warp covers a row of 128 columns
 #endif
 #ifndef OFSC_ROW_WARPS_F32
 #define OFSC_ROW_WARPS_F32 32  // resident warps per SM the registers must allow (FP32 slots)
 #endif
 #ifndef OFSC_ROW_U16_BF16
-#define OFSC_ROW_U16_BF16 4  // gathers in flight per lane for 16-byte BF16 slots (128 columns)
+#define OFSC_ROW_U16_BF16 6  // gathers in flight per lane for 16-byte BF16 slots (128 columns)
+#endif
+// Weighted graphs load an FP32 value beside every column index: fewer slots keep them in the
+// same 64 registers without spilling.
+#ifndef OFSC_ROW_U32_W
+#define OFSC_ROW_U32_W 8
+#endif
+#ifndef OFSC_ROW_U16_BF16_W
+#define OFSC_ROW_U16_BF16_W 6
 #endif
 #ifndef OFSC_ROW_WARPS_BF16
 #define OFSC_ROW_WARPS_BF16 32  // resident warps per SM the registers must allow (BF16 slots)
@@ -258,9 +266,10 @@ struct Slot<8, true> {
 
 // Slots in flight per lane: FP32 rows use 4 values per lane, BF16 rows 8 (16-byte loads), so a
 // warp holds twice as many BF16 rows in flight in the same registers.
-template <int LPN, int VPL>
+template <int LPN, int VPL, bool WEIGHTED>
 __host__ __device__ constexpr int dir_slots() {
-  return VPL == 4 ? (LPN == 32 ? OFSC_ROW_U32 : LPN == 16 ? 4 : 2) : (LPN == 16 ? OFSC_ROW_U16_BF16 : LPN == 8 ? 4 : 2);
+  return VPL == 4 ? (LPN == 32 ? (WEIGHTED ? OFSC_ROW_U32_W : OFSC_ROW_U32) : LPN == 16 ? 4 : 2)
+                  : (LPN == 16 ? (WEIGHTED ? OFSC_ROW_U16_BF16_W : OFSC_ROW_U16_BF16) : LPN == 8 ? 4 : 2);
 }
 
 template <int LPN, int VPL, bool WEIGHTED, bool BF16, bool DOTS>
@@ -270,7 +279,7 @@ __global__ void __launch_bounds__(32 * kRowWarpsPerBlock,
   if (!a.ignore_done && a.ctrl->done) return;
   using S = Slot<VPL, BF16>;
   constexpr int NPI = 32 / LPN;
-  constexpr int U = dir_slots<LPN, VPL>();
+  constexpr int U = dir_slots<LPN, VPL, WEIGHTED>();
   constexpr int STEP = U * NPI;
   constexpr int WPB = kRowWarpsPerBlock;
   constexpr int W = VPL * LPN;

@@ -39,6 +39,23 @@ def test_host_side_argument_checks(lib):
     assert lib.ofsc_graph_free(None) == ofsc.OK
 
 
+def test_host_side_argument_checks_of_the_widened_entry_points(lib):
+    """Batched iteration, the unrolled gradient, the autotuner, the weight gradient and
+    Rayleigh-Ritz reject bad arguments on the host, before any CUDA call."""
+    import ctypes
+    i32 = ctypes.c_int32
+    assert lib.ofsc_iterate_batched(-1, None, 0, None, None, 0.0, 1, None, None, None) == ofsc.ERR_INVALID_ARG
+    assert b"count" in lib.ofsc_last_error()
+    assert lib.ofsc_iterate_batched(2, None, 0, None, None, 0.0, 1, None, None, None) == ofsc.ERR_INVALID_ARG
+    assert lib.ofsc_iterate_batched(0, None, 0, None, None, 0.0, 1, None, None, None) == ofsc.OK
+    assert lib.ofsc_unrolled_grad(None, 4, None, 3, 0, 0, None, None, None, None, None, None) == ofsc.ERR_INVALID_ARG
+    assert lib.ofsc_autotune(None, 4, 0, None, None, None) == ofsc.ERR_INVALID_ARG
+    assert lib.ofsc_weight_grad(None, 1, 4, None, 0, None, None, None, None) == ofsc.ERR_INVALID_ARG
+    assert lib.ofsc_rayleigh_ritz(None, 4, None, None, None, None) == ofsc.ERR_INVALID_ARG
+    w = i32(0)
+    assert lib.ofsc_autotune(None, 4, 0, ctypes.byref(w), None, None) == ofsc.ERR_INVALID_ARG
+
+
 def test_no_cpu_fallback_when_library_missing(monkeypatch, tmp_path):
     monkeypatch.setattr(ofsc, "_lib", None)
     monkeypatch.setattr(ofsc, "LIB_PATH", str(tmp_path / "missing.so"))

@@ -144,6 +144,18 @@ def dist_setup(backend: str):
     return world, rank, local
 
 
+def max_over_ranks(x: float, world: int) -> float:
+    """The largest of every rank's x (the job's time is its slowest rank's); x itself for one rank."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def workload_config(args) -> dict:
     from paper_2305_10356_gb300 import synth
     spec = synth.WORKLOADS[args.workload]
@@ -316,10 +328,7 @@ def run_stream(args):
     t1.record(stream)
     torch.cuda.synchronize()
     ms = t0.elapsed_time(t1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world)
     spec = synth.STREAMS[args.workload]
     if rank == 0:
         line = {"metric": "OFM iterations/s", "value": updates * world / (ms / 1000.0), "unit": "iterations/s",
@@ -405,10 +414,7 @@ def run_batch(args):
         torch.cuda.synchronize()
         clocks = sampler.stop() if sampler else None
         ms = t0.elapsed_time(t1)
-        if world > 1:
-            t = torch.tensor([ms], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ms, world)
         return ups * world / (ms / 1000.0), ms / args.steps, launches, clocks
 
     value, ms, launches, clocks = timed(step_batched, with_clocks=True)
@@ -491,10 +497,7 @@ def run_unrolled(args):
     t1.record(stream)
     torch.cuda.synchronize()
     ms = t0.elapsed_time(t1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         import numpy as np
@@ -573,11 +576,7 @@ def run_gpu(args):
     torch.cuda.synchronize()
     clocks = sampler.stop()
     elapsed_ms = t_start.elapsed_time(t_end)
-    if world > 1:
-        t = torch.tensor([elapsed_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.barrier()
-        elapsed_ms = float(t.item())
+    elapsed_ms = max_over_ranks(elapsed_ms, world)
     updates = args.iters * args.steps * world
     value = updates / (elapsed_ms / 1000.0)
 
@@ -599,10 +598,7 @@ def run_gpu(args):
         p_end.record(stream)
         torch.cuda.synchronize()
         p_ms = p_start.elapsed_time(p_end)
-        if world > 1:
-            t = torch.tensor([p_ms], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            p_ms = float(t.item())
+        p_ms = max_over_ranks(p_ms, world)
         plain = {"value": updates / (p_ms / 1000.0), "unit": "iterations/s", "ms_per_step": p_ms / args.steps,
                  "gather": "fp32"}
 
@@ -648,10 +644,7 @@ def run_gpu(args):
                 Xh[cur].copy_(Xd[cur], non_blocking=True)
         torch.cuda.synchronize()
         secs = time.perf_counter() - w0
-        if world > 1:
-            t = torch.tensor([secs], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            secs = float(t.item())
+        secs = max_over_ranks(secs, world)
         return secs
 
     e2e_serial_s = e2e_run(False)

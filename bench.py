@@ -29,6 +29,7 @@ sys.path.insert(0, ROOT)
 
 METHODS = {"ofm_f1": 0, "tri_f1": 1, "ofm_f2": 2, "tri_f2": 3}
 METHOD_LABEL = {"ofm_f1": "OFM-f1", "tri_f1": "TriOFM-f1", "ofm_f2": "OFM-f2", "tri_f2": "TriOFM-f2"}
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal
 FP32_LANES_PER_SM = 128
 NUM_SMS = 152
 SM_MAX_MHZ = 2070.0
@@ -188,6 +189,47 @@ def oracle_sample(args):
     n_s = max(1000, n_full // SAMPLE_FRACTION)
     e, x0 = synth.workload(args.workload, n=n_s)
     return o.build_graph(e.n, e.src, e.dst, e.w), x0, n_s, n_full
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the baseline's record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith(("model name", "cpu model")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+ONE_THREAD_FRACTION = SAMPLE_FRACTION  # the single-thread sample: the same N / 5 graph as the all-core one
+
+
+def oracle_one_thread_seconds(args) -> float | None:
+    """Seconds of one oracle update on one thread (BLAS limited to one thread in a child
+    process), on N / ONE_THREAD_FRACTION nodes of the same recipe, scaled to the full N."""
+    from paper_2305_10356_gb300 import synth
+    n_full = args.nodes or synth.WORKLOADS[args.workload]["n"]
+    n_s = max(1000, n_full // ONE_THREAD_FRACTION)
+    code = ("import sys, time; sys.path.insert(0, %r)\n"
+            "from oracle import ofsc_oracle as o\nfrom paper_2305_10356_gb300 import synth\n"
+            "e, x0 = synth.workload(%r, n=%d)\ng = o.build_graph(e.n, e.src, e.dst, e.w)\n"
+            "t0 = time.perf_counter(); o.iterate(g, %d, x0, 0.0, 1); print(time.perf_counter() - t0)\n"
+            % (ROOT, args.workload, n_s, METHODS[args.method]))
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300, env=env)
+        return float(r.stdout.strip().splitlines()[-1]) * n_full / n_s
+    except (OSError, subprocess.SubprocessError, ValueError, IndexError):
+        return None
 
 
 SAMPLE_TEXT = ("one update of Algorithm 2 (maxit=1) by the FP64 numpy/scipy oracle on a graph of "
@@ -680,22 +722,44 @@ def run_gpu(args):
             "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
             "traffic": (tr["dram_read_bytes"] + tr["dram_write_bytes"]) if tr else None,
             "peak_source": f"{peaks['source']} (copy bandwidth)",
+            "peak_nominal": NOMINAL_HBM_GBS, "frac_nominal": achieved / NOMINAL_HBM_GBS,
             "algorithmic_bytes": alg["total"], "gather_l2_hit": round(h, 4),
             "ms_per_launch": per_launch_ms, "dominant_phase": dom}
+
+    # the whole update: DRAM bytes of all its kernels (ncu, profiles/traffic.json) and the
+    # compulsory-bytes model, over the device time of a steady update (the phases without the
+    # exact refreshes)
+    n_up = args.iters * args.steps
+    upd_ms = (sum(pd[p]["ms"] for p in pd) - pd["refresh"]["ms"]) / n_up
+    tu = measured_traffic(f"{args.workload}/{args.gather}" if args.nodes is None else "", "update")
+    nkp = e.n * kp
+    useful = (alg["total"]                      # the direction product (gathers net of L2 hits)
+              + 32 * nkp                        # direction pass: read X, AX, V, AV, G_p; write X, AX, G
+              + 12 * nkp + gb * nkp             # V pass: read G, V; write V, D^-1/2 V
+              + 8 * nkp)                        # Grams: read V, X
+    iteration = {"ms_per_update": upd_ms, "useful_bytes": useful,
+                 "useful_gbs": useful / (upd_ms / 1000.0) / 1e9,
+                 "dram_bytes": (tu["dram_read_bytes"] + tu["dram_write_bytes"]) if tu else None}
+    if tu:
+        gbs = iteration["dram_bytes"] / (upd_ms / 1000.0) / 1e9
+        iteration.update({"achieved_gbs": gbs, "frac": gbs / peaks["hbm_gbs"], "frac_nominal": gbs / NOMINAL_HBM_GBS})
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         og, xs, n_s, n_full = oracle_sample(args)
         secs = cpu_oracle_step(og, method, xs) * n_full / n_s
+        s1 = oracle_one_thread_seconds(args)
         cpu = {"value": 1.0 / secs, "unit": "iterations/s", "cores": os.cpu_count(), "kind": "oracle",
-               "sample": SAMPLE_TEXT}
+               "sample": SAMPLE_TEXT, "cpu_model": cpu_model(),
+               "value_1thread": (1.0 / s1) if s1 else None,
+               "sample_1thread": f"one update on N/{ONE_THREAD_FRACTION} nodes, BLAS on one thread, scaled to N"}
     if rank == 0:
         line = {"metric": "OFM iterations/s", "value": value, "unit": "iterations/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32" if args.gather == "fp32" else "f32 (bf16 gather storage)",
                 "data": "synthetic", "config": workload_config(args), "impl": "gpu",
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "roofline": roof, "iteration_hbm": iteration, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": launches, "plain_fp32": plain, "time_to_tol": ttt,
                 "phases_ms_per_step": {p: pd[p]["ms"] / args.steps for p in pd},
                 "parallelism": "replicas only" if world > 1 else "single GPU"}

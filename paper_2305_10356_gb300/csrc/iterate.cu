@@ -257,6 +257,18 @@ struct Slot<8, true> {
     const uint32_t u[4] = {r.x, r.y, r.z, r.w};
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
+      if (w == 1.0f) {  // binary S (a compile-time 1): add each BF16 half straight into FP32
+        // add.f32.bf16 widens exactly and rounds once, the same bits as widening then fmaf(1, x,
+        // acc), without the shift and mask that unpacking takes per value
+        float lo_acc = acc[2 * i], hi_acc = acc[2 * i + 1];
+        asm("{ .reg .b16 lo, hi;\n mov.b32 {lo, hi}, %2;\n add.rn.f32.bf16 %0, lo, %0;\n"
+            " add.rn.f32.bf16 %1, hi, %1;\n}"
+            : "+f"(lo_acc), "+f"(hi_acc)
+            : "r"(u[i]));
+        acc[2 * i] = lo_acc;
+        acc[2 * i + 1] = hi_acc;
+        continue;
+      }
       const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u[i]));
       acc[2 * i] = fmaf(w, f.x, acc[2 * i]);
       acc[2 * i + 1] = fmaf(w, f.y, acc[2 * i + 1]);

@@ -8,6 +8,13 @@
  *      ofsc_objective_grad  f1 (Eq. (2)) or f2 (Eq. (3)) and its gradient (Eq. (5) / Eq. (10))
  *   3. ofsc_row_normalize   row normalisation of the feature block
  *   4. ofsc_kmeans          Euclidean K-means on the rows
+ * and beyond them:
+ *      ofsc_iterate_batched many independent graphs in one call (streams, CUDA-graph replay)
+ *      ofsc_autotune        the row partition of the sparse product, chosen by timing
+ *      ofsc_weight_grad     df/dw for the edge weights of a weighted S
+ *      ofsc_unrolled_grad   d f1(X_T)/dX_0 (and /dw) through T updates of Algorithm 2
+ *      ofsc_rayleigh_ritz   Ritz values and relerr of Sec. 5 for a feature block
+ *      ofsc_gram            the k x k dot-product blocks on the tensor cores
  *
  * Conventions (all calls):
  *   - Every call returns an ofsc_status. No C++ exception crosses this boundary. On an error
@@ -17,7 +24,10 @@
  *     Pointers to FP32 data must be 4-byte aligned; they need not be 16-byte aligned.
  *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream). Work is
  *     queued on it. A call that returns a host value (f_out, ofsc_result, inertia, counts)
- *     synchronises that stream before it returns; no call synchronises the whole device.
+ *     synchronises that stream before it returns. Calls that allocate or free device memory
+ *     (the first call on a handle for a given k, ofsc_graph_build/free, ofsc_unrolled_grad,
+ *     ofsc_autotune) carry the device-wide synchronisation of cudaMalloc/cudaFree; no other call
+ *     synchronises the whole device.
  *   - ofsc_graph handles are owned by the library: create with ofsc_graph_build, release with
  *     ofsc_graph_free. A handle also caches the device workspace of ofsc_iterate and
  *     ofsc_objective_grad, so calls that share one handle must be ordered by the caller

@@ -137,6 +137,33 @@ def _ptr(t) -> int | None:
     return None if t is None else int(t.data_ptr())
 
 
+def _arg(t, name: str, dtype: str, rows: int | None = None, numel: int | None = None, like=None) -> int | None:
+    """Device pointer of a tensor argument after the checks the C ABI cannot make on a raw pointer:
+    a contiguous CUDA tensor of the expected dtype and size (None passes through)."""
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise OfscError(ERR_INVALID_ARG, f"{name}: a torch tensor is required")
+    if t.dtype != getattr(torch, dtype):
+        raise OfscError(ERR_INVALID_ARG, f"{name}: dtype {t.dtype}, expected torch.{dtype}")
+    if not t.is_contiguous():
+        raise OfscError(ERR_INVALID_ARG, f"{name}: must be contiguous")
+    if not t.is_cuda:
+        raise OfscError(ERR_INVALID_ARG, f"{name}: must be a CUDA tensor")
+    if rows is not None and (t.dim() != 2 or t.shape[0] != rows):
+        raise OfscError(ERR_INVALID_ARG, f"{name}: shape {tuple(t.shape)}, expected {rows} rows")
+    if numel is not None and t.numel() != numel:
+        raise OfscError(ERR_INVALID_ARG, f"{name}: {t.numel()} elements, expected {numel}")
+    if like is not None and tuple(t.shape) != tuple(like.shape):
+        raise OfscError(ERR_INVALID_ARG, f"{name}: shape {tuple(t.shape)}, expected {tuple(like.shape)}")
+    return int(t.data_ptr())
+
+
+def _rows(g) -> int:
+    return int(g.info().n)
+
+
 def _stream(stream) -> int | None:
     if stream is None:
         import torch
@@ -177,24 +204,28 @@ def ofsc_graph_build(n: int, src, dst, w=None, stream=None) -> Graph:
     """S, D and D^-1/2 (Eq. (1)) from device int32 edge arrays (and optional FP32 weights)."""
     h = ctypes.c_void_p()
     m = 0 if src is None else int(src.numel())
-    _check(lib().ofsc_graph_build(n, m, _ptr(src), _ptr(dst), _ptr(w), 0, _stream(stream),
-                                  ctypes.byref(h)))
+    ps, pd = _arg(src, "src", "int32"), _arg(dst, "dst", "int32", numel=m)
+    pw = _arg(w, "w", "float32", numel=m)
+    _check(lib().ofsc_graph_build(n, m, ps, pd, pw, 0, _stream(stream), ctypes.byref(h)))
     return Graph(h.value)
 
 
 def ofsc_objective_grad(g: Graph, objective: int, X, G_out=None, stream=None) -> float:
     """f (Eq. (2)/(3)) at the device block X (n x k, FP32); the gradient goes to G_out if given."""
     f = ctypes.c_double()
-    _check(lib().ofsc_objective_grad(g.handle, objective, int(X.shape[1]), _ptr(X),
-                                     ctypes.byref(f), _ptr(G_out), _stream(stream)))
+    px = _arg(X, "X", "float32", rows=_rows(g))
+    _check(lib().ofsc_objective_grad(g.handle, objective, int(X.shape[1]), px,
+                                     ctypes.byref(f), _arg(G_out, "G_out", "float32", like=X), _stream(stream)))
     return f.value
 
 
 def ofsc_objective_grad_noalloc(g: Graph, objective: int, X, G_out=None, stream=None) -> float:
     """As ofsc_objective_grad, with no device allocation (static scratch; n * kp <= 2^20)."""
     f = ctypes.c_double()
-    _check(lib().ofsc_objective_grad_noalloc(g.handle, objective, int(X.shape[1]), _ptr(X),
-                                             ctypes.byref(f), _ptr(G_out), _stream(stream)))
+    px = _arg(X, "X", "float32", rows=_rows(g))
+    _check(lib().ofsc_objective_grad_noalloc(g.handle, objective, int(X.shape[1]), px,
+                                             ctypes.byref(f), _arg(G_out, "G_out", "float32", like=X),
+                                             _stream(stream)))
     return f.value
 
 
@@ -203,11 +234,12 @@ def ofsc_iterate(g: Graph, method: int, X, tol: float, maxit: int, *, gather: in
                  profile: Profile | None = None, gram_engine: int = GRAM_AUTO,
                  spmm_engine: int = SPMM_AUTO, stream=None) -> Result:
     """Algorithm 2 in place on the device block X (n x k, FP32). Returns the ofsc_result."""
-    o = Opts(gather, y_refresh, check_every, alpha0, _ptr(trace),
+    px = _arg(X, "X", "float32", rows=_rows(g))
+    o = Opts(gather, y_refresh, check_every, alpha0, _arg(trace, "trace", "float64"),
              0 if trace is None else int(trace.shape[0]),
              ctypes.pointer(profile) if profile is not None else None, gram_engine, spmm_engine)
     r = Result()
-    _check(lib().ofsc_iterate(g.handle, method, int(X.shape[1]), _ptr(X), float(tol), int(maxit),
+    _check(lib().ofsc_iterate(g.handle, method, int(X.shape[1]), px, float(tol), int(maxit),
                               ctypes.byref(o), ctypes.byref(r), _stream(stream)),
            allow=(OK, ERR_NOT_CONVERGED))
     return r
@@ -226,7 +258,8 @@ def ofsc_iterate_batched(graphs: list[Graph], method: int, Xs: list, tol: float,
              1 if direct_launch else 0)
     hs = (ctypes.c_void_p * count)(*[g.handle for g in graphs])
     ks = (ctypes.c_int32 * count)(*[int(X.shape[1]) for X in Xs])
-    xs = (ctypes.c_void_p * count)(*[_ptr(X) for X in Xs])
+    xs = (ctypes.c_void_p * count)(*[_arg(X, f"Xs[{i}]", "float32", rows=_rows(g))
+                                     for i, (g, X) in enumerate(zip(graphs, Xs))])
     rs = (Result * count)()
     _check(lib().ofsc_iterate_batched(count, hs, method, ks, xs, float(tol), int(maxit), ctypes.byref(o), rs,
                                       _stream(stream)),
@@ -237,9 +270,9 @@ def ofsc_iterate_batched(graphs: list[Graph], method: int, Xs: list, tol: float,
 def ofsc_gram(L, Rs, out, k: int | None = None, rows_per_block: int = 0, stream=None) -> None:
     """out[b] = L^T Rs[b] (FP64 [nr, k, k]) on the tensor cores; L and Rs[b] are n x ld FP32."""
     n, ld = int(L.shape[0]), int(L.shape[1])
-    arr = (ctypes.c_void_p * len(Rs))(*[_ptr(r) for r in Rs])
-    _check(lib().ofsc_gram(n, ld if k is None else k, ld, _ptr(L), len(Rs), arr, rows_per_block,
-                           _ptr(out), _stream(stream)))
+    arr = (ctypes.c_void_p * len(Rs))(*[_arg(r, f"Rs[{b}]", "float32", like=L) for b, r in enumerate(Rs)])
+    _check(lib().ofsc_gram(n, ld if k is None else k, ld, _arg(L, "L", "float32"), len(Rs), arr, rows_per_block,
+                           _arg(out, "out", "float64"), _stream(stream)))
 
 
 def ofsc_autotune(g: Graph, k: int, gather: int = GATHER_FP32, stream=None) -> tuple[int, float]:
@@ -258,15 +291,20 @@ def ofsc_unrolled_grad(g: Graph, X0, T: int, grad=None, ckpt: int = 0, src=None,
     returns f1(X_T)."""
     f = ctypes.c_double(0.0)
     m = 0 if src is None else int(src.numel())
-    _check(lib().ofsc_unrolled_grad(g.handle, int(X0.shape[1]), _ptr(X0), int(T), int(ckpt), m, _ptr(src),
-                                    _ptr(dst), ctypes.byref(f), _ptr(grad), _ptr(grad_w), _stream(stream)))
+    px = _arg(X0, "X0", "float32", rows=_rows(g))
+    _check(lib().ofsc_unrolled_grad(g.handle, int(X0.shape[1]), px, int(T), int(ckpt), m,
+                                    _arg(src, "src", "int32"), _arg(dst, "dst", "int32", numel=m),
+                                    ctypes.byref(f), _arg(grad, "grad", "float32", like=X0),
+                                    _arg(grad_w, "grad_w", "float32", numel=m), _stream(stream)))
     return f.value
 
 
 def ofsc_weight_grad(g: Graph, objective: int, X, src, dst, grad, stream=None) -> None:
     """d f / d w for every listed edge (device int32 src, dst; device float32 grad) of a weighted graph."""
-    _check(lib().ofsc_weight_grad(g.handle, objective, int(X.shape[1]), _ptr(X), int(src.numel()), _ptr(src),
-                                  _ptr(dst), _ptr(grad), _stream(stream)))
+    m = int(src.numel())
+    _check(lib().ofsc_weight_grad(g.handle, objective, int(X.shape[1]), _arg(X, "X", "float32", rows=_rows(g)), m,
+                                  _arg(src, "src", "int32"), _arg(dst, "dst", "int32", numel=m),
+                                  _arg(grad, "grad", "float32", numel=m), _stream(stream)))
 
 
 def objective(X, w, src, dst, n: int, which: int = 1):
@@ -304,20 +342,22 @@ def ofsc_rayleigh_ritz(g: Graph, X, ritz, stream=None) -> float:
     """Ritz values of B = 2I - L on span(X) into the device float64 vector `ritz` (ascending) and
     the relative residual relerr of Sec. 5, returned."""
     out = ctypes.c_double(0.0)
-    _check(lib().ofsc_rayleigh_ritz(g.handle, int(X.shape[1]), _ptr(X), _ptr(ritz), ctypes.byref(out),
+    _check(lib().ofsc_rayleigh_ritz(g.handle, int(X.shape[1]), _arg(X, "X", "float32", rows=_rows(g)),
+                                    _arg(ritz, "ritz", "float64", numel=int(X.shape[1])), ctypes.byref(out),
                                     _stream(stream)))
     return float(out.value)
 
 
 def ofsc_row_normalize(X, stream=None) -> None:
     """Row normalisation in place (Algorithm 1, step 3)."""
-    _check(lib().ofsc_row_normalize(int(X.shape[0]), int(X.shape[1]), _ptr(X), _stream(stream)))
+    _check(lib().ofsc_row_normalize(int(X.shape[0]), int(X.shape[1]), _arg(X, "X", "float32"), _stream(stream)))
 
 
 def ofsc_kmeans(X, n_clusters: int, labels, seed: int = 0, n_init: int = 1, maxit: int = 300,
                 stream=None) -> float:
     """K-means on the rows of X into the device int32 array `labels`; returns the inertia."""
     inertia = ctypes.c_double()
-    _check(lib().ofsc_kmeans(int(X.shape[0]), int(X.shape[1]), _ptr(X), n_clusters, seed, n_init,
-                             maxit, _ptr(labels), ctypes.byref(inertia), _stream(stream)))
+    _check(lib().ofsc_kmeans(int(X.shape[0]), int(X.shape[1]), _arg(X, "X", "float32"), n_clusters, seed, n_init,
+                             maxit, _arg(labels, "labels", "int32", numel=int(X.shape[0])), ctypes.byref(inertia),
+                             _stream(stream)))
     return inertia.value

@@ -35,3 +35,40 @@ def test_stream_snapshots_nest():
         assert prev <= cur
         prev = cur
     assert x0.shape == (2000, 71)
+
+
+def _pairs(e):
+    src, dst = e.src.astype(np.int64), e.dst.astype(np.int64)
+    keep = src != dst
+    a, b = np.minimum(src[keep], dst[keep]), np.maximum(src[keep], dst[keep])
+    u = np.unique(a * e.n + b)
+    return u // e.n, u % e.n
+
+
+def test_dcsbm_recipe_realises_its_parameters():
+    """DC-SBM N = 50,000, 44 blocks, mean degree 40, within:between 3:1 in edge counts, Pareto
+    2.5 degrees: after loops and repeats are removed the mean degree and the count ratio stay
+    within 10% and 15% of the recipe, and the degrees are heavy-tailed (max about the structural
+    cutoff sqrt(N d) = 1414)."""
+    e, _ = synth.workload("dcsbm_n50k_k44")
+    pa, pb = _pairs(e)
+    deg = np.bincount(np.concatenate([pa, pb]), minlength=e.n)
+    assert abs(deg.mean() - 40.0) <= 4.0
+    within = int((e.labels[pa] == e.labels[pb]).sum())
+    assert abs(within / (len(pa) - within) - 3.0) <= 0.45
+    assert 700 <= deg.max() <= 3000 and deg.max() >= 20 * np.median(deg)
+    assert deg.min() >= 1  # isolated nodes are joined to one random node
+    assert len(np.unique(e.labels)) == 44
+
+
+def test_sbm_probability_ratio_recipe():
+    """SBM N = 1000, 11 blocks, mean degree 20, within:between edge probability 10:1."""
+    e, _ = synth.workload("sbm_n1000_k11")
+    pa, pb = _pairs(e)
+    sizes = np.bincount(e.labels, minlength=11).astype(np.float64)
+    same = e.labels[pa] == e.labels[pb]
+    pairs_within = float((sizes * (sizes - 1) / 2).sum())
+    pairs_between = e.n * (e.n - 1) / 2 - pairs_within
+    ratio = (same.sum() / pairs_within) / ((~same).sum() / pairs_between)
+    assert 7.0 <= ratio <= 13.0
+    assert abs(2.0 * len(pa) / e.n - 20.0) <= 2.0

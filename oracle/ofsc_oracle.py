@@ -36,8 +36,10 @@ Readings of the paper taken where it is silent or ambiguous (each one is pinned 
   * Isolated nodes (degree 0) get D^-1/2 = 0, i.e. L_ii = 1.
   * Repeated undirected pairs collapse (binary S) or have their weights summed (weighted S).
 
-Parity unpinned: kmeans beyond self-consistency (same seeds, non-increasing inertia, Lloyd
-fixed point); its agreement with the GPU is judged by ARI.
+K-means is pinned in parts: its Lloyd iterations reach scikit-learn's Lloyd result from the same
+initial centres, its seeding follows the D^2 rule of k-means++ in a chi-square test, and its
+uniforms are Philox-4x32-10 known-answer vectors. The choice of seeding rule itself (which index
+a uniform selects) is a reading; the GPU's agreement with the oracle is then judged by ARI.
 """
 from __future__ import annotations
 

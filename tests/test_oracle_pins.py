@@ -438,6 +438,46 @@ def test_kmeans_blobs_and_fixed_point():
     np.testing.assert_array_equal(lab, lab2)
 
 
+def test_lloyd_iterations_match_library():
+    """From the same initial centres the oracle's Lloyd iterations reach scikit-learn's Lloyd
+    result: the same labels and the same inertia."""
+    sk = pytest.importorskip("sklearn.cluster")
+    rng = np.random.default_rng(3)
+    centers = rng.standard_normal((6, 4)) * 3
+    X = centers[rng.integers(0, 6, 2000)] + rng.standard_normal((2000, 4))
+    for seed in (1, 2, 3):
+        idx = o.kmeans_pp_seeds(X, 6, seed, 0)
+        lab, inertia = o.kmeans(X, 6, seed=seed, n_init=1)
+        km = sk.KMeans(n_clusters=6, init=X[idx], n_init=1, max_iter=300, tol=0.0, algorithm="lloyd").fit(X)
+        np.testing.assert_array_equal(lab, km.labels_)
+        assert inertia == pytest.approx(km.inertia_, rel=1e-12)
+
+
+def test_kmeanspp_seeding_follows_d_squared():
+    """k-means++ (Arthur and Vassilvitskii): the first centre is uniform over the points and the
+    next is point j with probability D(j)^2 / sum D^2 (D the distance to the chosen centre). Over
+    4000 seeds the empirical frequencies of the second centre, given the first, pass a
+    chi-square test at the 0.1% level for every first centre."""
+    X = np.array([[0.0], [1.0], [3.0], [6.0], [10.0]])
+    n = len(X)
+    firsts = np.zeros(n)
+    counts = np.zeros((n, n))
+    for seed in range(4000):
+        idx = o.kmeans_pp_seeds(X, 2, seed, 0)
+        firsts[idx[0]] += 1
+        counts[idx[0], idx[1]] += 1
+    expect = 4000 / n
+    assert np.sum((firsts - expect) ** 2 / expect) < 18.47  # chi-square, 4 dof, p = 0.001
+    for c in range(n):
+        d2 = (X[:, 0] - X[c, 0]) ** 2
+        p = d2 / d2.sum()
+        tot = counts[c].sum()
+        assert counts[c, c] == 0
+        keep = p > 0
+        chi = np.sum((counts[c, keep] - tot * p[keep]) ** 2 / (tot * p[keep]))
+        assert chi < 18.47, (c, counts[c], tot * p)
+
+
 def test_subspace_sin_known_angle():
     th = 0.3
     assert o.subspace_sin(np.array([[1.0], [0.0]]), np.array([[math.cos(th)], [math.sin(th)]])) \

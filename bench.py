@@ -377,7 +377,7 @@ def run_stream(args):
         line = {"metric": "OFM iterations/s", "value": updates * world / (ms / 1000.0), "unit": "iterations/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32" if args.gather == "fp32" else "f32 (bf16 gather storage)", "data": "synthetic",
+                "dtype": "f32", "storage": "f32" if args.gather == "fp32" else "bf16 gather copy, f32 master", "data": "synthetic",
                 "config": {"workload": f"{args.workload}: SBM, N={args.nodes or spec['n']}, k={spec['n_blocks']}, "
                                        f"mean degree {spec['mean_degree']:g} at 100%, {spec['parts']} cumulative "
                                        f"edge-sampled snapshots, warm start, graph builds timed",
@@ -482,7 +482,7 @@ def run_batch(args):
         line = {"metric": "OFM iterations/s", "value": value, "unit": "iterations/s (summed over graphs)",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32" if args.gather == "fp32" else "f32 (bf16 gather storage)", "data": "synthetic",
+                "dtype": "f32", "storage": "f32" if args.gather == "fp32" else "bf16 gather copy, f32 master", "data": "synthetic",
                 "config": {"workload": f"{args.workload}: {spec['count']} SBMs, N ~ U[{spec['n'][0]}, {spec['n'][1]}] "
                                        f"(x{scale:g}), k ~ U[{spec['k'][0]}, {spec['k'][1]}], mean degree ~ "
                                        f"U[{spec['mean_degree'][0]:g}, {spec['mean_degree'][1]:g}], within:between "
@@ -765,7 +765,7 @@ def run_gpu(args):
         line = {"metric": "OFM iterations/s", "value": value, "unit": "iterations/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32" if args.gather == "fp32" else "f32 (bf16 gather storage)",
+                "vs_baseline": None, "dtype": "f32", "storage": "f32" if args.gather == "fp32" else "bf16 gather copy, f32 master",
                 "data": "synthetic", "config": workload_config(args), "impl": "gpu",
                 "roofline": roof, "iteration_hbm": iteration, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": launches, "plain_fp32": plain, "time_to_tol": ttt,

@@ -493,6 +493,23 @@ def test_rayleigh_ritz_on_eigenvectors():
     np.testing.assert_allclose(np.sort(ritz), np.sort(2.0 - lam[:3]), atol=1e-12)
 
 
+def test_rayleigh_ritz_matches_generalised_eigenproblem():
+    """For a random block, the Ritz values are the eigenvalues of the pencil (X^T B X, X^T X)
+    (scipy's generalised symmetric solver, no orthonormalisation), and relerr is the residual of
+    the Ritz vectors U = X z written out with the dense B, relative to ||U Lam||_F."""
+    import scipy.linalg as sla
+    g, _ = small_graph(60, 4, 8.0, seed=12)
+    B = -o.dense_A(g)
+    X = np.random.default_rng(5).standard_normal((60, 4))
+    lam, Z = sla.eigh(X.T @ B @ X, X.T @ X)
+    U = X @ Z
+    rel = np.linalg.norm(B @ U - U * lam[None, :]) / np.linalg.norm(U * lam[None, :])
+    ritz, rel_o = o.rayleigh_ritz_relerr(g, X)
+    np.testing.assert_allclose(np.sort(ritz), lam, rtol=1e-10, atol=1e-12)
+    assert rel_o == pytest.approx(rel, rel=1e-9)
+    assert rel > 1e-3  # a random block is far from invariant
+
+
 @pytest.mark.parametrize("method", [o.TRI_F1, o.OFM_F1])
 def test_every_direction_descends(method):
     """Each column's direction is a descent direction for that column, v_j^T g_j < 0, while its

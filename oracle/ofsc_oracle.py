@@ -27,10 +27,9 @@ Readings of the paper taken where it is silent or ambiguous (each one is pinned 
   * TriOFM has no objective, so "minimal function value" becomes the minimal value of the
     antiderivative q(alpha) of the printed cubic. For OFM the objective itself is evaluated.
   * The paper's momentum coefficient is Polak-Ribiere as Algorithm 2 writes it; 0/0 -> 0.
-  * Algorithm 2 has no restart. A column whose new direction would not descend,
-    v_j^T g_j = -|g_j|^2 + beta_j v_prev,j^T g_j >= 0, restarts with beta_j = 0 (once a column's
-    gradient is at rounding level its beta is noise and, without the restart, v_j grows
-    geometrically until the line searches of every later prefix collapse).
+  * Algorithm 2 has no restart, and neither does `iterate` by default. An optional restart
+    (restart=True: a column whose new direction would not descend, v_j^T g_j >= 0, takes
+    beta_j = 0) exists only to check the library's matching opt-in option; it is not the paper's.
   * Step 0 of Algorithm 2 uses the same exact line search unless a fixed alpha0 > 0 is given.
   * Stop when ||G_t||_F / ||G_0||_F <= tol, or after maxit updates (Algorithm 2's t_max).
   * Isolated nodes (degree 0) get D^-1/2 = 0, i.e. L_ii = 1.
@@ -479,17 +478,28 @@ def step_sizes(g: Graph, method: int, X, V, AX, AV, normA2: float) -> np.ndarray
     return np.array([choose_root(C[i]) for i in range(k)])
 
 
+def cg_beta(G_new: np.ndarray, G_old: np.ndarray):
+    """Column-wise Polak-Ribiere coefficient of Algorithm 2:
+    beta_i = sum_l (G_new - G_old)_li G_new,li / sum_l G_old,li^2, with 0 where the denominator
+    is 0 (a zero column of G_old, e.g. a padded column). Returns (beta, denominator)."""
+    num = np.sum((G_new - G_old) * G_new, axis=0)
+    den = np.sum(G_old * G_old, axis=0)
+    beta = np.where(den != 0.0, num / np.where(den != 0.0, den, 1.0), 0.0)
+    return beta, den
+
+
 def iterate(g: Graph, method: int, X0: np.ndarray, tol: float, maxit: int,
-            alpha0: float = 0.0, record: list | None = None) -> IterResult:
+            alpha0: float = 0.0, record: list | None = None, restart: bool = False) -> IterResult:
     """Algorithm 2 for one of the four methods, in FP64, from the FP32 (or FP64) start X0.
 
     G_0 = g(X_0); V_0 = -G_0; X_1 = X_0 + alpha V_0 (alpha0 > 0 given, else exact line
     search); then for t = 1, 2, ...: G_t = g(X_t); stop if ||G_t|| <= tol ||G_0|| or t = maxit;
-    beta_i = sum_l (G_t - G_{t-1})_li G_t,li / sum_l G_{t-1,li}^2 (0 when the denominator is 0,
-    and 0 when the column's new direction would not descend: -|g_i|^2 + beta_i v_i^T g_i >= 0);
-    V_t = -G_t + V_{t-1} diag(beta); alpha by exact line search; X_{t+1} = X_t + V_t diag(alpha).
+    beta_t by cg_beta (Polak-Ribiere, 0 when the denominator is 0); V_t = -G_t + V_{t-1} diag(beta);
+    alpha by exact line search; X_{t+1} = X_t + V_t diag(alpha).
+    restart=True (not in the paper; off by default) also sets beta_i = 0 where the new column
+    would not descend: -|g_i|^2 + beta_i v_i^T g_i >= 0.
     `record`, when given, receives one dict per update t: X_t, G_t, V_t, AV_t, alpha_t, beta_t,
-    the denominators of beta_t and the columns whose beta the restart rule set to 0.
+    the denominators of beta_t and the columns whose beta the optional restart set to 0.
     """
     X = np.array(X0, dtype=np.float64)
     normA2 = normA_fro2(g)
@@ -526,12 +536,11 @@ def iterate(g: Graph, method: int, X0: np.ndarray, tol: float, maxit: int,
             break
         if t >= maxit:
             break
-        num = np.sum((Gn - G) * Gn, axis=0)
-        den = np.sum(G * G, axis=0)
-        beta = np.where(den != 0.0, num / np.where(den != 0.0, den, 1.0), 0.0)
-        descent = -np.sum(Gn * Gn, axis=0) + beta * np.sum(V * Gn, axis=0)
-        restart = descent >= 0.0
-        beta = np.where(restart, 0.0, beta)
+        beta, den = cg_beta(Gn, G)
+        restarted = np.zeros(X.shape[1], dtype=bool)
+        if restart:
+            restarted = -np.sum(Gn * Gn, axis=0) + beta * np.sum(V * Gn, axis=0) >= 0.0
+            beta = np.where(restarted, 0.0, beta)
         V = -Gn + V * beta[None, :]
         AV = apply_A(g, V)
         alpha = step_sizes(g, method, X, V, AX, AV, normA2)
@@ -539,7 +548,7 @@ def iterate(g: Graph, method: int, X0: np.ndarray, tol: float, maxit: int,
         betas.append(beta.copy())
         if record is not None:
             record.append(dict(X=X, G=Gn, V=V, AV=AV, alpha=alpha.copy(), beta=beta.copy(), den=den,
-                               restart=restart))
+                               restart=restarted))
         X = X + V * alpha[None, :]
         G = Gn
         t += 1
@@ -557,13 +566,13 @@ def hess_f1_quarter(g: Graph, Z: np.ndarray, U: np.ndarray) -> np.ndarray:
     return apply_A(g, U) + U @ (Z.T @ Z) + Z @ (U.T @ Z) + Z @ (Z.T @ U)
 
 
-def unrolled_objective(g: Graph, X0: np.ndarray, T: int) -> float:
+def unrolled_objective(g: Graph, X0: np.ndarray, T: int, restart: bool = False) -> float:
     """L(X_0) = f1(X_T) after T updates of OFM-f1 (Algorithm 2, no stopping test)."""
-    r = iterate(g, OFM_F1, X0, 0.0, T)
+    r = iterate(g, OFM_F1, X0, 0.0, T, restart=restart)
     return r.f
 
 
-def unrolled_grad(g: Graph, X0: np.ndarray, T: int, edges=None):
+def unrolled_grad(g: Graph, X0: np.ndarray, T: int, edges=None, restart: bool = False):
     """dL/dX_0 for L = f1(X_T) after T updates of OFM-f1, by reverse accumulation through
     Algorithm 2 as `iterate` runs it. Per update t, X_{t+1} = X_t + alpha_t V_t with
       * alpha_t a root of p(a) = <V_t, grad f1(X_t + a V_t)> / 4 (the cubic of Eq. (15)); by the
@@ -571,14 +580,15 @@ def unrolled_grad(g: Graph, X0: np.ndarray, T: int, edges=None):
         dp/dX = H(X_{t+1})[V_t], dp/dV = grad f1(X_{t+1})/4 + alpha H(X_{t+1})[V_t] and
         p'(alpha) = <V_t, H(X_{t+1})[V_t]>, H the Hessian of f1/4 (hess_f1_quarter);
       * V_t = -G_t + V_{t-1} diag(beta_t), beta_t,j = <G_t - G_{t-1}, G_t>_j / |G_{t-1},j|^2, with
-        beta held at 0 (no derivative) where the restart rule or a zero denominator set it;
+        beta held at 0 (no derivative) where a zero denominator (or, with the optional restart,
+        the restart) set it;
       * G_t = grad f1(X_t) = 4(A X_t + X_t X_t^T X_t), whose derivative along U is 4 H(X_t)[U].
     Returns (L, dL/dX_0), or with edges = (src, dst, w) of a weighted graph (g built from them
     with exact=True) also dL/dw per listing: A enters G_t (adjoint 4 Gbar_t X_t^T), the cubic of
     alpha_t (c V_t X_{t+1}^T, c the implicit-function factor) and f1(X_T) itself; with
     Gamma = dL/dA_hat = -dL/dA symmetrised, the weights follow as in weight_grad."""
     rec: list = []
-    res = iterate(g, OFM_F1, X0, 0.0, T, record=rec)
+    res = iterate(g, OFM_F1, X0, 0.0, T, record=rec, restart=restart)
     X = res.X
     pairs = _pairs(g.n, *edges) if edges is not None else None
     gam = None

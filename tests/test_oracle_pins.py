@@ -511,16 +511,15 @@ def test_rayleigh_ritz_matches_generalised_eigenproblem():
 
 
 @pytest.mark.parametrize("method", [o.TRI_F1, o.OFM_F1])
-def test_every_direction_descends(method):
-    """Each column's direction is a descent direction for that column, v_j^T g_j < 0, while its
-    gradient is above rounding level (Algorithm 2 with the restart reading), and a long run past
-    convergence stays finite and keeps converging."""
+def test_optional_restart_gives_descent_directions(method):
+    """The optional restart (not in Algorithm 2; restart=True) gives every column a descent
+    direction, v_j^T g_j < 0, while its gradient is above rounding level."""
     g, _ = small_graph(40, 3, 7.0, seed=17)
     A = o.dense_A(g)
     X0 = synth.initial_block(40, 3, 4).astype(np.float64)
     X = X0.copy()
-    # replay the oracle's recurrences step by step and check the sign of v_j^T g_j
-    res = o.iterate(g, method, X0, 0.0, 400)
+    # replay the recurrences step by step and check the sign of v_j^T g_j
+    res = o.iterate(g, method, X0, 0.0, 400, restart=True)
     assert np.all(np.isfinite(res.X))
     G_prev = o.direction(method, X0, A @ X0)
     g0 = np.linalg.norm(G_prev, axis=0)
@@ -533,6 +532,108 @@ def test_every_direction_descends(method):
         live = np.linalg.norm(G, axis=0) > 1e-8 * g0
         assert np.all(vg[live] < 0), (t, vg)
     assert res.rel_norms[-1] < 1e-9
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_long_run_past_convergence_stays_finite(method):
+    """Algorithm 2 as printed (no restart), in FP64: 1500 updates on a 40-node graph, far past the
+    rounding floor, keep X finite and the relative direction norm at that floor."""
+    g, _ = small_graph(40, 3, 7.0, seed=17)
+    X0 = synth.initial_block(40, 3, 4).astype(np.float64)
+    res = o.iterate(g, method, X0, 0.0, 1500)
+    assert np.all(np.isfinite(res.X))
+    assert min(res.rel_norms) < 1e-14 and res.rel_norms[-1] < 1e-13
+
+
+# ------------------------------------------------------------------------------------------
+# The Polak-Ribiere coefficient of Algorithm 2, pinned by what it implies: n-step termination of
+# CG near a minimiser, the column-wise (per-column) form, and acceleration over steepest descent
+# (Sec. 3.1). A planted mistake in cg_beta fails at least one of the three.
+# ------------------------------------------------------------------------------------------
+
+def _pin_local_termination() -> bool:
+    """One column of OFM-f1 started 1e-6 from the minimiser x* = u_1 sqrt(-lambda_1) (Theorem 1).
+    There f1 is a quadratic (Hessian 4(A - lambda_1 I) + 8 (-lambda_1) u_1 u_1^T, positive definite
+    when lambda_1 < lambda_2) plus O(|e|^3). Nonlinear CG with an exact line search then repeats
+    linear CG up to O(|e|), and linear CG ends in at most n steps on an n-dimensional quadratic, so
+    after n updates the relative gradient is O(|e_0|). Steepest descent (beta = 0) only gains
+    ((kappa - 1)/(kappa + 1))^n, about 1e-2 on these graphs."""
+    for n_nodes, seed in ((10, 3), (12, 5), (16, 7)):
+        g, _ = small_graph(n_nodes, 2, 4.0, seed=seed)
+        lam, U = np.linalg.eigh(o.dense_A(g))
+        assert lam[1] - lam[0] > 0.1
+        x_star = U[:, :1] * math.sqrt(-lam[0])
+        X0 = x_star + 1e-6 * np.random.default_rng(1).standard_normal(x_star.shape)
+        r = o.iterate(g, o.OFM_F1, X0, 0.0, n_nodes)
+        if not r.rel_norms[-1] <= 1e-4:
+            return False
+    return True
+
+
+def _pin_columnwise() -> bool:
+    """TriOFM's first i columns evolve on their own: g(X)[:, :i] = g(X[:, :i]), the prefix-i cubic
+    involves only the first i columns, and Algorithm 2 sums beta's quotient column by column. So
+    the first i columns of a run equal a run from X_0[:, :i]."""
+    g, _ = small_graph(40, 3, 7.0, seed=17)
+    X0 = synth.initial_block(40, 3, 4).astype(np.float64)
+    for method in (o.TRI_F1, o.TRI_F2):
+        full = o.iterate(g, method, X0, 0.0, 30).X
+        for i in (1, 2):
+            if not np.allclose(full[:, :i], o.iterate(g, method, X0[:, :i], 0.0, 30).X, rtol=0, atol=1e-12):
+                return False
+    return True
+
+
+def _pin_accelerates(monkeypatch) -> bool:
+    """Sec. 3.1 adopts CG to accelerate gradient descent: on the 60-node, 4-block graph of the
+    Theorem pins, Algorithm 2 reaches 1e-10 in fewer updates than the same iteration with beta = 0
+    (steepest descent with the same exact line search), for OFM-f1 and TriOFM-f1."""
+    g, _ = small_graph(60, 4, 8.0, seed=39)
+    X0 = synth.initial_block(60, 4, 99).astype(np.float64)
+    for method in (o.OFM_F1, o.TRI_F1):
+        cg = o.iterate(g, method, X0, 1e-10, 2000).iterations
+        with monkeypatch.context() as m:
+            m.setattr(o, "cg_beta", lambda Gn, G: (np.zeros(Gn.shape[1]), np.sum(G * G, axis=0)))
+            sd = o.iterate(g, method, X0, 1e-10, 2000).iterations
+        if not cg < sd:
+            return False
+    return True
+
+
+def test_beta_n_step_termination_near_a_minimiser():
+    assert _pin_local_termination()
+
+
+def test_beta_is_columnwise():
+    assert _pin_columnwise()
+
+
+def test_beta_accelerates_steepest_descent(monkeypatch):
+    assert _pin_accelerates(monkeypatch)
+
+
+def _q(num, den):
+    return np.where(den != 0.0, num / np.where(den != 0.0, den, 1.0), 0.0)
+
+
+BETA_MISTAKES = {
+    "fletcher_reeves": lambda Gn, G: (_q(np.sum(Gn * Gn, 0), np.sum(G * G, 0)), np.sum(G * G, 0)),
+    "zero": lambda Gn, G: (np.zeros(Gn.shape[1]), np.sum(G * G, 0)),
+    "swapped_t_and_t_minus_1": lambda Gn, G: (_q(np.sum((G - Gn) * G, 0), np.sum(Gn * Gn, 0)), np.sum(Gn * Gn, 0)),
+    "sign": lambda Gn, G: (-_q(np.sum((Gn - G) * Gn, 0), np.sum(G * G, 0)), np.sum(G * G, 0)),
+    "dropped_minus_in_numerator": lambda Gn, G: (_q(np.sum((Gn + G) * Gn, 0), np.sum(G * G, 0)), np.sum(G * G, 0)),
+    "denominator_of_G_t": lambda Gn, G: (_q(np.sum((Gn - G) * Gn, 0), np.sum(Gn * Gn, 0)), np.sum(G * G, 0)),
+    "one_beta_for_all_columns": lambda Gn, G: (np.full(Gn.shape[1], _q(np.sum((Gn - G) * Gn), np.sum(G * G))),
+                                               np.sum(G * G, 0)),
+}
+
+
+@pytest.mark.parametrize("mistake", list(BETA_MISTAKES))
+def test_beta_pins_catch_planted_mistakes(monkeypatch, mistake):
+    """Each plausible mistake in the Polak-Ribiere coefficient, planted in the oracle, fails at
+    least one of the three beta pins."""
+    monkeypatch.setattr(o, "cg_beta", BETA_MISTAKES[mistake])
+    assert not (_pin_local_termination() and _pin_columnwise() and _pin_accelerates(monkeypatch))
 
 
 def test_edge_stream_snapshots_are_cumulative_uniform_samples():
@@ -606,27 +707,30 @@ def test_sparse_objective_of_weights_matches_dense(which):
 # Differentiating through unrolled updates of OFM-f1: central differences in random directions
 # ------------------------------------------------------------------------------------------
 
-@pytest.mark.parametrize("seed,T", [(5, 1), (5, 12), (12, 20), (24, 20)])
-def test_unrolled_grad_matches_central_differences(seed, T):
+@pytest.mark.parametrize("seed,T,restart,eps", [(5, 1, False, 1e-6), (5, 12, False, 1e-6), (12, 20, False, 1e-6),
+                                                (24, 20, False, 1e-8), (12, 20, True, 1e-6), (24, 20, True, 1e-6)])
+def test_unrolled_grad_matches_central_differences(seed, T, restart, eps):
     """d f1(X_T) / d X_0 through T updates of Algorithm 2 (line search by the implicit-function
     theorem, beta's quotient, the Hessian-vector products of the direction) against central
-    differences of the FP64 iteration itself. Seeds 12 and 24 have columns restarted by the
-    descent rule (beta held at 0) in several updates."""
+    differences of the FP64 iteration itself; with the optional restart, seeds 12 and 24 have
+    columns restarted (beta held at 0) in several updates. Without the restart, seed 24's
+    20-update map bends so sharply that central differences settle only below a step of 1e-7
+    (1e-6 is off by 2%, 1e-8 agrees to 3e-7), hence its smaller step."""
     e = synth.sbm(80 if seed == 5 else 60, 3, 10.0 if seed == 5 else 8.0, 5.0, ratio_kind="count", seed=seed)
     g = o.build_graph(e.n, e.src, e.dst)
     x0 = synth.initial_block(e.n, 3, seed + 1).astype(np.float64)
     rec = []
-    o.iterate(g, o.OFM_F1, x0, 0.0, T, record=rec)
+    o.iterate(g, o.OFM_F1, x0, 0.0, T, record=rec, restart=restart)
     assert len(rec) == T
-    if seed in (12, 24):
+    if restart:
         assert sum(int(r["restart"].sum()) for r in rec) >= 6
-    f, grad = o.unrolled_grad(g, x0, T)
-    assert f == o.unrolled_objective(g, x0, T)
+    f, grad = o.unrolled_grad(g, x0, T, restart=restart)
+    assert f == o.unrolled_objective(g, x0, T, restart=restart)
     rng = np.random.default_rng(seed * 100 + T)
-    eps = 1e-6
     for _ in range(3):
         D = rng.standard_normal(x0.shape)
-        fd = (o.unrolled_objective(g, x0 + eps * D, T) - o.unrolled_objective(g, x0 - eps * D, T)) / (2 * eps)
+        fd = (o.unrolled_objective(g, x0 + eps * D, T, restart)
+              - o.unrolled_objective(g, x0 - eps * D, T, restart)) / (2 * eps)
         assert abs(float(np.sum(grad * D)) - fd) <= 2e-6 * abs(fd), (float(np.sum(grad * D)), fd)
 
 

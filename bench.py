@@ -126,6 +126,8 @@ def parse():
     ap.add_argument("--no-time-to-tol", action="store_true",
                     help="skip the time to a 1e-4 rad subspace angle against the FP32 reference")
     ap.add_argument("--iters", type=int, default=30, help="updates of Algorithm 2 per step")
+    ap.add_argument("--no-legs", action="store_true",
+                    help="skip the 1,000-node all-methods leg and the batched-vs-loop leg")
     ap.add_argument("--spmm-engine", default="auto", choices=["auto", "simt", "tma"])
     ap.add_argument("--nodes", type=int, default=None, help="shrink the workload (testing only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -292,12 +294,23 @@ TTT_TOL = 1e-4          # rad
 TTT_REF_UPDATES = 400   # the FP32 reference run (its relative gradient reaches the FP32 floor)
 
 
-def time_to_tol(g, method, X0, stream) -> dict:
-    """Updates and seconds until X is within TTT_TOL rad of the FP32 reference subspace, for the
-    BF16-gather and the plain FP32 path: the smallest multiple of 10 updates (fresh calls from X0)
-    that gets there, then that call timed with CUDA events (fixed per-call costs included)."""
+TTT_REFINE_TOL = 1e-2   # the refined BF16 form switches to FP32 gathers below this relative gradient
+TTT_SEEDS = 3           # starting blocks: updates-to-tolerance of Algorithm 2 vary widely with tiny
+                        # perturbations (chaotic CG), so forms are compared by their median
+
+
+def time_to_tol(g, method, n, k, stream, seed0: int) -> dict:
+    """Updates and seconds until X is within TTT_TOL rad of an FP32 reference subspace (400 plain FP32
+    updates from the same start), for the BF16-gather form, the BF16 form with the FP32 refinement
+    sweep (FP32 gathers once the relative direction norm read at a host check is <= TTT_REFINE_TOL),
+    the plain FP32 path, and the BF16 and FP32 forms with the optional CG restart. Per start: the
+    smallest multiple of 10 updates (fresh calls from X0) that gets there, then that call timed with
+    CUDA events (fixed per-call costs included). Reported per start and as medians over TTT_SEEDS
+    seeded starts X0 ~ N(0, 1/N)."""
+    import statistics
+
     import torch
-    from paper_2305_10356_gb300 import ofsc
+    from paper_2305_10356_gb300 import ofsc, synth
 
     def sin_angle(A, B):
         qa, _ = torch.linalg.qr(A.double())
@@ -305,27 +318,122 @@ def time_to_tol(g, method, X0, stream) -> dict:
         sv = torch.linalg.svdvals(qa.T @ qb)
         return float(torch.sqrt(torch.clamp(1.0 - sv.min() ** 2, min=0.0)))
 
-    X = X0.clone()
-    ofsc.ofsc_iterate(g, method, X, 0.0, TTT_REF_UPDATES, gather=ofsc.GATHER_FP32)
-    ref = X.clone()
-    out = {"tol_rad": TTT_TOL, "reference": f"plain FP32, {TTT_REF_UPDATES} updates from the same X0"}
-    for name, gather in (("bf16_gather", ofsc.GATHER_BF16), ("fp32", ofsc.GATHER_FP32)):
-        m, ang = 0, 1.0
-        while ang > TTT_TOL and m < TTT_REF_UPDATES:
-            m += 10
+    forms = (("bf16_gather", dict(gather=ofsc.GATHER_BF16)),
+             ("bf16_refined", dict(gather=ofsc.GATHER_BF16, refine_tol=TTT_REFINE_TOL)),
+             ("fp32", dict(gather=ofsc.GATHER_FP32)),
+             ("bf16_gather_restart", dict(gather=ofsc.GATHER_BF16, cg_restart=True)),
+             ("fp32_restart", dict(gather=ofsc.GATHER_FP32, cg_restart=True)))
+    out = {"tol_rad": TTT_TOL, "reference": f"plain FP32, {TTT_REF_UPDATES} updates from the same X0",
+           "starts": TTT_SEEDS, "refine_tol": TTT_REFINE_TOL, "runs": {name: [] for name, _ in forms}}
+    for si in range(TTT_SEEDS):
+        X0 = torch.from_numpy(synth.initial_block(n, k, seed0 + si)).cuda()
+        X = X0.clone()
+        ofsc.ofsc_iterate(g, method, X, 0.0, TTT_REF_UPDATES, gather=ofsc.GATHER_FP32)
+        ref = X.clone()
+        for name, kw in forms:
+            m, ang, r = 0, 1.0, None
+            while ang > TTT_TOL and m < TTT_REF_UPDATES:
+                m += 10
+                X.copy_(X0)
+                r = ofsc.ofsc_iterate(g, method, X, 0.0, m, **kw)
+                ang = sin_angle(X, ref)
             X.copy_(X0)
-            ofsc.ofsc_iterate(g, method, X, 0.0, m, gather=gather)
-            ang = sin_angle(X, ref)
-        X.copy_(X0)
+            torch.cuda.synchronize()
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            ofsc.ofsc_iterate(g, method, X, 0.0, m, **kw)
+            t1.record(stream)
+            torch.cuda.synchronize()
+            out["runs"][name].append({"updates": m, "seconds": t0.elapsed_time(t1) / 1000.0, "sin_angle": ang,
+                                      "rel_dir_norm": r.rel_dir_norm if r else None,
+                                      "fp32_from_update": r.refined_at if (r and r.refined_at >= 0) else None})
+        del ref, X, X0
+    for name, _ in forms:
+        runs = out["runs"][name]
+        out[name] = {"median_updates": statistics.median(x["updates"] for x in runs),
+                     "median_seconds": statistics.median(x["seconds"] for x in runs)}
+    return out
+
+
+C1_TOL, C1_MAXIT = 1e-6, 2000
+
+
+def c1_leg(stream) -> dict:
+    """The 1,000-node, 11-block SBM (the oracle-sized case): every method to tol 1e-6 (2,000 updates
+    at most) from the seeded X0, in FP32 and with BF16 gathers; updates and device seconds per run
+    (one warm-up run each, then the run timed with CUDA events)."""
+    import torch
+    from paper_2305_10356_gb300 import ofsc, synth
+    e, x0 = synth.workload("sbm_n1000_k11")
+    g = ofsc.ofsc_graph_build(e.n, torch.from_numpy(e.src).cuda(), torch.from_numpy(e.dst).cuda())
+    X0 = torch.from_numpy(x0).cuda()
+    X = torch.empty_like(X0)
+    out = {"workload": "sbm_n1000_k11: SBM N=1000, k=11, mean degree 20, 10:1 edge probabilities",
+           "tol": C1_TOL, "maxit": C1_MAXIT}
+    for label, method in METHODS.items():
+        row = {}
+        for prec, gather in (("fp32", ofsc.GATHER_FP32), ("bf16", ofsc.GATHER_BF16)):
+            X.copy_(X0)
+            ofsc.ofsc_iterate(g, method, X, C1_TOL, C1_MAXIT, gather=gather)
+            X.copy_(X0)
+            torch.cuda.synchronize()
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            r = ofsc.ofsc_iterate(g, method, X, C1_TOL, C1_MAXIT, gather=gather)
+            t1.record(stream)
+            torch.cuda.synchronize()
+            secs = t0.elapsed_time(t1) / 1000.0
+            row[prec] = {"updates": r.iterations, "converged": r.status == ofsc.OK, "rel_dir_norm": r.rel_dir_norm,
+                         "seconds": secs, "updates_per_s": r.iterations / secs if secs > 0 else None}
+        out[METHOD_LABEL[label]] = row
+    g.free()
+    return out
+
+
+def batched_leg(stream, tol: float = 1e-4, iters: int = 300, steps: int = 2) -> dict:
+    """The 32-graph batch (sbm_batch32, N from 3.5K to 99K, k from 8 to 64), every graph to
+    tol (relative direction norm, at most `iters` updates): one ofsc_iterate_batched call against a
+    loop of one ofsc_iterate call per graph (both run the same updates of every graph, bit for bit),
+    timed with CUDA events over `steps` steps after one warm-up."""
+    import torch
+    from paper_2305_10356_gb300 import ofsc, synth
+    probs = synth.batch("sbm_batch32", 1.0)
+    graphs, X0s = [], []
+    for e, x0 in probs:
+        graphs.append(ofsc.ofsc_graph_build(e.n, torch.from_numpy(e.src).cuda(), torch.from_numpy(e.dst).cuda()))
+        X0s.append(torch.from_numpy(x0).cuda())
+    Xs = [torch.empty_like(x) for x in X0s]
+
+    def batched():
+        for X, X0 in zip(Xs, X0s):
+            X.copy_(X0)
+        return sum(r.iterations for r in ofsc.ofsc_iterate_batched(graphs, 0, Xs, tol, iters))
+
+    def loop():
+        n = 0
+        for g, X, X0 in zip(graphs, Xs, X0s):
+            X.copy_(X0)
+            n += ofsc.ofsc_iterate(g, 0, X, tol, iters).iterations
+        return n
+
+    out = {"workload": f"sbm_batch32: {len(probs)} SBMs, sum N = {sum(x.shape[0] for x in X0s)}, OFM-f1, "
+                       f"every graph to tol {tol:g} (at most {iters} updates), FP32"}
+    for name, fn in (("batched", batched), ("loop", loop)):
+        fn()
         torch.cuda.synchronize()
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
         t0.record(stream)
-        ofsc.ofsc_iterate(g, method, X, 0.0, m, gather=gather)
+        ups = sum(fn() for _ in range(steps))
         t1.record(stream)
         torch.cuda.synchronize()
-        out[name] = {"updates": m, "seconds": t0.elapsed_time(t1) / 1000.0, "sin_angle": ang}
-    del ref
+        secs = t0.elapsed_time(t1) / 1000.0
+        out[name] = {"updates_per_s": ups / secs, "ms_per_step": 1000.0 * secs / steps,
+                     "updates_per_step": ups // steps}
+    for g in graphs:
+        g.free()
     return out
 
 
@@ -413,7 +521,9 @@ def run_batch(args):
     nnz = sum(int(g.info().nnz) for g in graphs)
     # the row-partition granularity of each graph's direction product, by timing (outside the
     # timed steps)
-    tuned = [ofsc.ofsc_autotune(g, x.shape[1], gather)[0] // NUM_SMS for g, x in zip(graphs, X0s)]
+    shapes = [ofsc.ofsc_autotune(g, x.shape[1], gather) for g, x in zip(graphs, X0s)]
+    tuned = [w // NUM_SMS for w, _, _ in shapes]
+    tuned_slots = [u for _, u, _ in shapes]
     Xs = [torch.empty_like(x) for x in X0s]
     stream = torch.cuda.current_stream()
 
@@ -490,7 +600,8 @@ def run_batch(args):
                                        f"sum nnz = {nnz}",
                            "updates_per_graph_per_step": args.iters, "method": METHOD_LABEL[args.method],
                            "gather": args.gather, "l2": "state of all graphs about 1 GB, larger than L2",
-                           "autotuned_warps_per_sm": {str(w): tuned.count(w) for w in sorted(set(tuned))}},
+                           "autotuned_warps_per_sm": {str(w): tuned.count(w) for w in sorted(set(tuned))},
+                           "autotuned_slots_per_lane": {str(u): tuned_slots.count(u) for u in sorted(set(tuned_slots))}},
                 "impl": "gpu", "e2e": {"value": e2e_v, "unit": "iterations/s (summed over graphs)",
                                        "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
                 "clocks": clocks, "gpu_launches": launches,
@@ -700,7 +811,7 @@ def run_gpu(args):
     # time to tolerance: the subspace angle to an FP32 reference run of 400 updates
     ttt = None
     if rank == 0 and not args.no_time_to_tol:
-        ttt = time_to_tol(g, method, X0, stream)
+        ttt = time_to_tol(g, method, e.n, e.n_blocks, stream, 2305 * 1000 + 50)
 
     # dominant kernel (the direction product, phase "spmm") and its roofline
     pd = prof.as_dict()
@@ -734,10 +845,12 @@ def run_gpu(args):
             "algorithmic_bytes": alg["total"], "gather_l2_hit": round(h, 4), "gather_l2_hit_source": h_source,
             "ms_per_launch": per_launch_ms, "dominant_phase": dom}
 
-    # the whole update: DRAM bytes of all its kernels (ncu, profiles/traffic.json) and the
-    # compulsory-bytes model, over the device time of a steady update (the phases without the
-    # exact refreshes)
+    # the whole update: the compulsory-bytes model (and the DRAM bytes of all its kernels from one
+    # ncu capture, profiles/traffic.json) over the device time per update. `frac` divides by the
+    # full time per update, exact refreshes included (they are part of every call); `frac_steady`
+    # by the time of the updates without a refresh.
     n_up = args.iters * args.steps
+    all_ms = sum(pd[p]["ms"] for p in pd) / n_up
     upd_ms = (sum(pd[p]["ms"] for p in pd) - pd["refresh"]["ms"]) / n_up
     tu = measured_traffic(f"{args.workload}/{args.gather}" if args.nodes is None else "", "update")
     nkp = e.n * kp
@@ -745,13 +858,19 @@ def run_gpu(args):
               + 32 * nkp                        # direction pass: read X, AX, V, AV, G_p; write X, AX, G
               + 12 * nkp + gb * nkp             # V pass: read G, V; write V, D^-1/2 V
               + 8 * nkp)                        # Grams: read V, X
-    iteration = {"ms_per_update": upd_ms, "useful_bytes": useful,
-                 "useful_gbs": useful / (upd_ms / 1000.0) / 1e9,
+    useful_gbs = useful / (all_ms / 1000.0) / 1e9
+    iteration = {"ms_per_update": all_ms, "ms_per_update_steady": upd_ms, "useful_bytes": useful,
+                 "useful_gbs": useful_gbs, "frac": useful_gbs / peaks["hbm_gbs"],
+                 "frac_steady": useful / (upd_ms / 1000.0) / 1e9 / peaks["hbm_gbs"],
+                 "target_frac": 0.70, "gap_to_target": 0.70 - useful_gbs / peaks["hbm_gbs"],
                  "dram_bytes": (tu["dram_read_bytes"] + tu["dram_write_bytes"]) if tu else None}
     if tu:
         gbs = iteration["dram_bytes"] / (upd_ms / 1000.0) / 1e9
-        iteration.update({"achieved_gbs": gbs, "frac": gbs / peaks["hbm_gbs"], "frac_nominal": gbs / NOMINAL_HBM_GBS})
+        iteration.update({"dram_gbs_steady": gbs, "dram_frac_steady": gbs / peaks["hbm_gbs"]})
 
+    legs = None
+    if rank == 0 and not args.no_legs and args.nodes is None:
+        legs = {"c1_all_methods": c1_leg(stream), "batched_vs_loop": batched_leg(stream)}
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         og, xs, n_s, n_full = oracle_sample(args)
@@ -768,7 +887,7 @@ def run_gpu(args):
                 "vs_baseline": None, "dtype": "f32", "storage": "f32" if args.gather == "fp32" else "bf16 gather copy, f32 master",
                 "data": "synthetic", "config": workload_config(args), "impl": "gpu",
                 "roofline": roof, "iteration_hbm": iteration, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-                "gpu_launches": launches, "plain_fp32": plain, "time_to_tol": ttt,
+                "gpu_launches": launches, "plain_fp32": plain, "time_to_tol": ttt, "legs": legs,
                 "phases_ms_per_step": {p: pd[p]["ms"] / args.steps for p in pd},
                 "parallelism": "replicas only" if world > 1 else "single GPU"}
         print(json.dumps(line), flush=True)

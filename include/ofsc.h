@@ -10,7 +10,7 @@
  *   4. ofsc_kmeans          Euclidean K-means on the rows
  * and beyond them:
  *      ofsc_iterate_batched many independent graphs in one call (streams, CUDA-graph replay)
- *      ofsc_autotune        the row partition of the sparse product, chosen by timing
+ *      ofsc_autotune        the sparse product's row partition and gathers in flight, by timing
  *      ofsc_weight_grad     df/dw for the edge weights of a weighted S
  *      ofsc_unrolled_grad   d f1(X_T)/dX_0 (and /dw) through T updates of Algorithm 2
  *      ofsc_rayleigh_ritz   Ritz values and relerr of Sec. 5 for a feature block
@@ -139,9 +139,12 @@ ofsc_status ofsc_objective_grad(ofsc_graph* g, int32_t objective, int32_t k, con
  *   Limit: n * kp <= 2^20 with kp = k rounded up to a multiple of 8 (k <= 128); larger sizes
  *   return OFSC_ERR_INVALID_ARG with a message (use ofsc_objective_grad for them).
  *   The first call on a device looks up the array's device address with that device current;
- *   make that first call before any stream capture. All calls share the array and it keeps the
- *   previous call's contents, so calls that overlap on the GPU (several streams or host
- *   threads) race with one another: order them. Synchronises `stream`.
+ *   make that first call before any stream capture. The address is kept for the life of the
+ *   process, so after a cudaDeviceReset of a device this entry point must not be called on it
+ *   again. The graph must belong to the current device (OFSC_ERR_INVALID_ARG otherwise). All
+ *   calls share the array and it keeps the previous call's contents, so calls that overlap on
+ *   the GPU (several streams or host threads) race with one another: order them.
+ *   Synchronises `stream`.
  * Errors: OFSC_ERR_INVALID_ARG, OFSC_ERR_NONFINITE, OFSC_ERR_CUDA.
  */
 ofsc_status ofsc_objective_grad_noalloc(const ofsc_graph* g, int32_t objective, int32_t k,
@@ -180,9 +183,30 @@ typedef struct {
   int32_t gram_engine;   /* OFSC_GRAM_AUTO (tensor cores when k > 64), OFSC_GRAM_SIMT, OFSC_GRAM_TC */
   int32_t spmm_engine;   /* OFSC_SPMM_AUTO (= OFSC_SPMM_SIMT: one warp per row, CUDA-core gathers),
                             OFSC_SPMM_TMA (tile::gather4 into shared memory; padded k 64 or 128) */
-  int32_t direct_launch; /* ofsc_iterate_batched only: 0 (default) replays the updates whose
-                            launches repeat from one captured CUDA graph; 1 launches every kernel
-                            directly (same results, bit for bit) */
+  int32_t direct_launch; /* 0 (default): the updates whose launches repeat are captured once into a
+                            CUDA graph and replayed (ofsc_iterate does so unless `profile` is set);
+                            1: every kernel is launched directly (same results, bit for bit) */
+  int32_t cg_restart;    /* 0 (default): beta exactly as Algorithm 2 prints it. 1: an optional
+                            restart that is NOT in the paper: a column whose new direction would
+                            not descend (V_t,i . G_t,i >= 0) takes beta_i = 0. Runs far past the
+                            FP32 rounding floor can see noise-level beta compound in V until it
+                            overflows (OFSC_ERR_NONFINITE); the restart prevents that */
+  double refine_tol;     /* gather = OFSC_GATHER_BF16 only; 0 (default): BF16 gathers to the end.
+                            > 0: the FP32 refinement sweep: once a host check (every check_every
+                            updates) reads ||G_t||_F <= refine_tol ||G_0||_F, every later update
+                            gathers D^-1/2 V in FP32, so the run ends on FP32 products. The switch
+                            point depends only on check_every and the iterates */
+  double exact_tail;     /* 0 (default): 1e3 tol when tol > 0, else never. > 0: once a host check
+                            reads ||G_t||_F <= exact_tail ||G_0||_F, every later update recomputes
+                            AX = A X, X^T X and X^T AX exactly, as Algorithm 2 states it, instead of
+                            carrying them by the recurrences (whose FP32 drift is near the size of
+                            G at tolerances of 1e-6). < 0: never */
+  int32_t vscale_exp;    /* 0 (default 20), else in [-60, 60]: V is stored in FP32 as V diag(1/s)
+                            with s_j a power of two, 1 until |V_j| would exceed
+                            2^vscale_exp ||G_0||_F (Algorithm 2's beta can compound past the FP32
+                            range where FP64 still holds it). Scaling by powers of two is exact,
+                            so the results do not depend on this value unless FP32 would
+                            overflow or underflow */
 } ofsc_opts;
 
 typedef struct {
@@ -192,6 +216,8 @@ typedef struct {
   double g0_norm;       /* ||g(X_0)||_F */
   double f;             /* objective of the method (f1 or f2) at the returned X */
   int64_t kernel_launches; /* device kernels this call launched */
+  int32_t refined_at;   /* first update of the FP32 refinement sweep (opts->refine_tol), or -1 */
+  int32_t exact_at;     /* first update of the exact tail (opts->exact_tail), or -1 */
 } ofsc_result;
 
 /*
@@ -205,10 +231,13 @@ typedef struct {
  *   opts     host struct or NULL for defaults
  *   out      HOST ofsc_result (nullable)
  * G_0 = g(X_0), V_0 = -G_0, X_1 = X_0 + V_0 diag(alpha_0); for t >= 1: G_t = g(X_t);
- * beta_i = sum_l (G_t - G_{t-1})_li G_t,li / sum_l G_{t-1,li}^2 (0 if the denominator is 0, and 0
- * when the resulting column of V_t would not be a descent direction, V_t,i . G_t,i >= 0);
+ * beta_i = sum_l (G_t - G_{t-1})_li G_t,li / sum_l G_{t-1,li}^2 (0 if the denominator is 0; with
+ * opts->cg_restart also 0 where the column of V_t would not descend);
  * V_t = -G_t + V_{t-1} diag(beta); alpha_t from the exact line search (one alpha for OFM, one
  * per column for TriOFM, with X_i, V_i the first i columns); X_{t+1} = X_t + V_t diag(alpha_t).
+ * Only an update with an exact AX (every y_refresh updates, the exact tail, or one scheduled at the
+ * next host check after ||G_t|| <= tol ||G_0|| was seen on a recurrence update) may stop the run,
+ * so rel_dir_norm <= tol whenever the status is OFSC_OK.
  * Returns OFSC_OK when tol was met, OFSC_ERR_NOT_CONVERGED when maxit was reached first (X is
  * still the valid final iterate). Synchronises `stream`.
  * Errors: OFSC_ERR_INVALID_ARG, OFSC_ERR_OOM, OFSC_ERR_NONFINITE.
@@ -243,7 +272,8 @@ ofsc_status ofsc_iterate_batched(int32_t count, ofsc_graph* const* graphs, int32
 /*
  * ofsc_unrolled_grad - the gradient, with respect to the starting block X_0, of f1 (Eq. (2)) at
  * the block X_T reached by T updates of OFM-f1 (Algorithm 2 with the exact line search of
- * Eq. (15), beta as in ofsc_iterate, A X recomputed every update, no stopping test).
+ * Eq. (15), beta as Algorithm 2 prints it (no restart), A X recomputed every update, no stopping
+ * test).
  *   k        columns (1 <= k <= 128)
  *   X0       device float32 [n x k]
  *   T        updates to differentiate through (0 <= T <= 4096; T = 0 gives grad f1(X_0))
@@ -259,7 +289,7 @@ ofsc_status ofsc_iterate_batched(int32_t count, ofsc_graph* const* graphs, int32
  *            listed edge, with A depending on the weights through S and D (listings of one pair
  *            share a value, self-loops get 0), as for ofsc_weight_grad
  * The step alpha_t is differentiated through the implicit-function theorem on the cubic, beta_t
- * through its quotient (a column the restart rule set to 0 carries no derivative), G_t through
+ * through its quotient (a column whose denominator is 0 carries no derivative), G_t through
  * its Hessian-vector product; for grad_w, A's adjoint collects 4 Gbar_t X_t^T from every G_t,
  * c_t V_t X_{t+1}^T from every step's cubic and f1(X_T)'s own term, and is mapped to the
  * weights per stored entry (an SDDMM per update). Allocates its working set for the call.
@@ -273,21 +303,25 @@ ofsc_status ofsc_unrolled_grad(ofsc_graph* g, int32_t k, const float* X0, int32_
                                float* grad, float* grad_w, void* stream);
 
 /*
- * ofsc_autotune - picks, by timing, how finely the direction product (the sparse product of
- * Sec. 3.3, the largest part of an update of Algorithm 2) splits this graph's rows among warps:
- * 4, 8, 16 or 32 warps per SM (coarser ones only while each warp keeps at least 16 nonzeros), for
- * k columns and the given gather storage. The fastest is kept in the handle and used by every
- * later call on it. Each warp sums its rows' share of diag(V^T AV) before a fixed-order fold, so a
- * new choice can change the last bits of later results (never the rows of A V).
+ * ofsc_autotune - picks, by timing, the shape of the direction product (the sparse product of
+ * Sec. 3.3, the largest part of an update of Algorithm 2) for this graph, k columns and the given
+ * gather storage: how finely its rows are split among warps (4, 8, 16 or 32 warps per SM, coarser
+ * ones only while each warp keeps at least 16 nonzeros) and how many row gathers each lane keeps
+ * in flight (2, 4, 6 or 8, as many as one step of at most 32 nonzeros allows). Every combination is
+ * timed (3 launches after one warm-up); the fastest is kept in the handle and used by every later
+ * call on it with the same padded k and gather storage. Each warp sums its rows' share of
+ * diag(V^T AV) before a fixed-order fold, so a new choice can change the last bits of later results
+ * (never the rows of A V).
  *   k         columns (1 <= k <= 128)
  *   gather    OFSC_GATHER_FP32 or OFSC_GATHER_BF16
  *   warps_out HOST int32* (nullable): the chosen number of warps
+ *   slots_out HOST int32* (nullable): the chosen gathers in flight per lane
  *   ms_out    HOST double* (nullable): its time per product in milliseconds
  * Uses the handle's workspace (allocated for k if needed; its blocks are overwritten).
  * Synchronises `stream`. Errors: OFSC_ERR_INVALID_ARG, OFSC_ERR_OOM, OFSC_ERR_CUDA.
  */
-ofsc_status ofsc_autotune(ofsc_graph* g, int32_t k, int32_t gather, int32_t* warps_out, double* ms_out,
-                          void* stream);
+ofsc_status ofsc_autotune(ofsc_graph* g, int32_t k, int32_t gather, int32_t* warps_out, int32_t* slots_out,
+                          double* ms_out, void* stream);
 
 /*
  * ofsc_weight_grad - gradient of f1 (Eq. (2)) or f2 (Eq. (3)) at X with respect to the weight of

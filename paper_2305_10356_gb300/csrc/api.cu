@@ -56,6 +56,8 @@ void workspace_free(Workspace& ws) {
   cudaFree(ws.beta);
   cudaFree(ws.alpha64);
   cudaFree(ws.beta64);
+  cudaFree(ws.vscale);
+  cudaFree(ws.vinv);
   cudaFree(ws.colpart);
   cudaFree(ws.dE);
   cudaFree(ws.solve);

@@ -101,6 +101,8 @@ struct Ctrl {
   int maxit;
   int trace_cap;
   int k;           // real (unpadded) columns
+  int restart;     // 1: the optional CG restart (beta_j = 0 where v_j . g_j >= 0); 0: Algorithm 2
+  int vscale_exp;  // columns of V are stored scaled once |V_j| exceeds 2^vscale_exp ||G_0||
   int pad_;
   double tol;
   double g0;       // ||G_0||_F
@@ -110,8 +112,37 @@ struct Ctrl {
   double normA2;   // ||A||_F^2
   double trB;      // tr(X^T A X) of the current X (carried for the f1 objective)
   int dots_blocks; // blocks of the last sparse product that wrote dot partials
-  int pad2_;
+  int near_tol;    // 1 once ||G_t|| <= tol ||G_0|| was seen on an update whose AX came from the
+                   // recurrence: the host then makes every later update exact, and only an exact
+                   // update may stop the run
 };
+
+// Operands of the two sparse products: the direction product W = A V (k_spmm_dir, gathering
+// Vh = D^-1/2 V) and the exact AX = A X (k_spmm, gathering X and scaling by D^-1/2 per nonzero).
+struct SpmmArgs {
+  int64_t n;
+  int kp;
+  const int64_t* row_ptr;
+  const int32_t* col;
+  const float* val;
+  const float* dinv;
+  const int64_t* bnd;  // [groups + 1]: contiguous, nnz-balanced row ranges of the lane groups / warps
+  int groups;
+  const void* gather;  // direction: Vh = D^-1/2 V (FP32 or BF16); AX: X
+  const float* base;   // direction: V; AX: X  (the row block M in A M = -M - D^-1/2 S D^-1/2 M)
+  float* out;          // direction: W = AV; AX: AX
+  double* dots;        // direction with dots: [blocks][kp] partials of diag(V^T AV)
+  Ctrl* ctrl;
+  int ignore_done;
+};
+
+// The direction product (spmm_dir.cu): lanes per nonzero for rows of kp values with vpl values per
+// lane; the default and the candidate numbers of gathers in flight per lane; the launch (slots 0:
+// the default), returning the rows of dots partials it writes (one per warp).
+int dir_lanes(int kp, int vpl);
+int dir_default_slots(int kp, bool bf16, bool weighted);
+int dir_slot_options(int kp, bool bf16, int* out);
+int launch_spmm_dir(const SpmmArgs& a, bool weighted, bool bf16, int slots, cudaStream_t s);
 
 // Device workspace of the iteration for one padded width kp, cached on the graph handle.
 struct Workspace {
@@ -138,6 +169,11 @@ struct Workspace {
   float* beta = nullptr;        // kp
   double* alpha64 = nullptr;    // kp
   double* beta64 = nullptr;     // kp
+  // Extended exponent range of the direction: the stored FP32 V holds V_true diag(1 / vscale) with
+  // vscale a power of two per column (1 unless V_true outgrows 2^vscale_exp ||G_0||), so beta products
+  // that FP64 represents cannot overflow FP32 storage; vinv = 1 / vscale in FP32 for the V pass.
+  double* vscale = nullptr;     // kp
+  float* vinv = nullptr;        // kp
   double* colpart = nullptr;    // [row_blocks][5][kp]
   double* dE = nullptr;         // kp: diag(V^T AX) (f1 methods)
   double* solve = nullptr;      // line-search scratch: per-block trace partials, diagonals, cubics
@@ -162,6 +198,11 @@ struct ofsc_graph {
   int weighted = 0;
   double normA2 = 0.0;
   int device = 0;
+  // The direction product's shape chosen by ofsc_autotune for one padded width and gather storage:
+  // gathers in flight per lane (0: the kernel's default); the row partition is bnd[kRowPart].
+  int dir_tuned_kp = 0;
+  int dir_tuned_bf16 = 0;
+  int dir_slots = 0;
   int64_t* row_ptr = nullptr;  // [n+1]
   int32_t* col = nullptr;      // [nnz]
   float* val = nullptr;        // [nnz] or null

@@ -28,6 +28,13 @@
 
 namespace ofsc {
 namespace {
+// Columns of the stored direction are rescaled once |V_j| exceeds 2^kDefaultVscaleExp ||G_0||.
+constexpr int kDefaultVscaleExp = 20;
+}  // namespace
+}  // namespace ofsc
+
+namespace ofsc {
+namespace {
 
 enum { M_OFM_F1 = 0, M_TRI_F1 = 1, M_OFM_F2 = 2, M_TRI_F2 = 3 };
 constexpr int kPairs = 6;
@@ -43,8 +50,11 @@ __device__ __forceinline__ bool is_f2(int method) { return method >= M_OFM_F2; }
 // Setup kernels
 // ------------------------------------------------------------------------------------------
 
-__global__ void k_init_ctrl(Ctrl* c, double tol, int maxit, int k, double normA2, int trace_cap) {
+__global__ void k_init_ctrl(Ctrl* c, double tol, int maxit, int k, double normA2, int trace_cap, int restart = 0,
+                            int vscale_exp = kDefaultVscaleExp) {
   c->it = 0;
+  c->restart = restart;
+  c->vscale_exp = vscale_exp;
   c->done = 0;
   c->converged = 0;
   c->status = OFSC_OK;
@@ -59,6 +69,7 @@ __global__ void k_init_ctrl(Ctrl* c, double tol, int maxit, int k, double normA2
   c->normA2 = normA2;
   c->trB = 0.0;
   c->dots_blocks = 0;
+  c->near_tol = 0;
 }
 
 __global__ void k_pad_in(int64_t n, int k, int kp, const float* __restrict__ src,
@@ -106,45 +117,6 @@ __global__ void k_update_x(int64_t n, int kp, float* __restrict__ X, const float
 // Sparse product Y = A M with A = -I - D^-1/2 S D^-1/2, fused epilogues
 // ------------------------------------------------------------------------------------------
 
-// Operands of the two sparse products: the direction product W = A V (k_spmm_dir, gathering
-// Vh = D^-1/2 V) and the exact AX = A X (k_spmm, gathering X and scaling by D^-1/2 per nonzero).
-struct SpmmArgs {
-  int64_t n;
-  int kp;
-  const int64_t* row_ptr;
-  const int32_t* col;
-  const float* val;
-  const float* dinv;
-  const int64_t* bnd;  // [groups + 1]: contiguous, nnz-balanced row ranges of the lane groups / warps
-  int groups;
-  const void* gather;  // direction: Vh = D^-1/2 V (FP32 or BF16); AX: X
-  const float* base;   // direction: V; AX: X  (the row block M in A M = -M - D^-1/2 S D^-1/2 M)
-  float* out;          // direction: W = AV; AX: AX
-  double* dots;        // direction with dots: [blocks][kp] partials of diag(V^T AV)
-  Ctrl* ctrl;
-  int ignore_done;
-};
-
-#ifndef OFSC_ROW_U32
-#define OFSC_ROW_U32 8  // gathers in flight per lane when a warp covers a row of 128 columns
-#endif
-#ifndef OFSC_ROW_WARPS_F32
-#define OFSC_ROW_WARPS_F32 32  // resident warps per SM the registers must allow (FP32 slots)
-#endif
-#ifndef OFSC_ROW_U16_BF16
-#define OFSC_ROW_U16_BF16 6  // gathers in flight per lane for 16-byte BF16 slots (128 columns)
-#endif
-// Weighted graphs load an FP32 value beside every column index: fewer slots keep them in the
-// same 64 registers without spilling.
-#ifndef OFSC_ROW_U32_W
-#define OFSC_ROW_U32_W 8
-#endif
-#ifndef OFSC_ROW_U16_BF16_W
-#define OFSC_ROW_U16_BF16_W 6
-#endif
-#ifndef OFSC_ROW_WARPS_BF16
-#define OFSC_ROW_WARPS_BF16 32  // resident warps per SM the registers must allow (BF16 slots)
-#endif
 
 __device__ __forceinline__ void fma4(float4& acc, float w, const float4& v) {
   acc.x = fmaf(w, v.x, acc.x);
@@ -215,189 +187,6 @@ __global__ void __launch_bounds__(256, 2) k_spmm(SpmmArgs a) {
   }
 }
 
-// W = A V = -V - D^-1/2 S Vh for a direction V (or AX from Xh = D^-1/2 X), with the fused
-// per-block partial sums of diag(V^T AV). A warp owns a contiguous, nnz-balanced range of rows
-// and takes one row at a time, so its control flow is uniform: LPN lanes per nonzero hold four
-// columns each, NPI = 32 / LPN nonzeros are gathered side by side and U of those slots per lane
-// are in flight together (STEP = U NPI <= 32 nonzeros per step; a short row's last step is
-// predicated, not split). The STEP column indices of a step are loaded one per lane and handed
-// out by shuffle; those of the next step (at a row end, of the next row) are loaded while the
-// current gathers are in flight, and a row's epilogue operands (its row of V, its D^-1/2 entry)
-// are loaded with the gathers of its last step (staging them through shared memory with cp.async
-// measured 12% slower). Each lane sums its slots in nonzero order; the NPI partial sums of a row
-// are combined by an xor-shuffle butterfly, which leaves the same bits in every lane (for LPN = 32
-// the sum is in plain nonzero order). Each warp writes its own row of partials (no block-wide
-// barrier, so a block is never held by its slowest warp's reduction); k_dots_fold folds them.
-// One gathered slot of VPL consecutive values of a row of Vh, kept raw (FP32: float4; BF16: 8
-// values in a uint4) until it is accumulated, so a slot in flight costs four registers.
-template <int VPL, bool BF16>
-struct Slot;
-template <>
-struct Slot<4, false> {
-  using Raw = float4;
-  static __device__ __forceinline__ Raw load(const void* p, int64_t row, int kp, int c) {
-    return __ldg((const float4*)((const float*)p + row * kp + c));
-  }
-  static __device__ __forceinline__ Raw zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
-  static __device__ __forceinline__ void fma(float* acc, float w, const Raw& r) {
-    acc[0] = fmaf(w, r.x, acc[0]);
-    acc[1] = fmaf(w, r.y, acc[1]);
-    acc[2] = fmaf(w, r.z, acc[2]);
-    acc[3] = fmaf(w, r.w, acc[3]);
-  }
-};
-template <>
-struct Slot<8, true> {
-  using Raw = uint4;
-  static __device__ __forceinline__ Raw load(const void* p, int64_t row, int kp, int c) {
-    return __ldg((const uint4*)((const __nv_bfloat16*)p + row * kp + c));
-  }
-  static __device__ __forceinline__ Raw zero() { return make_uint4(0u, 0u, 0u, 0u); }
-  static __device__ __forceinline__ void fma(float* acc, float w, const Raw& r) {
-    const uint32_t u[4] = {r.x, r.y, r.z, r.w};
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      if (w == 1.0f) {  // binary S (a compile-time 1): add each BF16 half straight into FP32
-        // add.f32.bf16 widens exactly and rounds once, the same bits as widening then fmaf(1, x,
-        // acc), without the shift and mask that unpacking takes per value
-        float lo_acc = acc[2 * i], hi_acc = acc[2 * i + 1];
-        asm("{ .reg .b16 lo, hi;\n mov.b32 {lo, hi}, %2;\n add.rn.f32.bf16 %0, lo, %0;\n"
-            " add.rn.f32.bf16 %1, hi, %1;\n}"
-            : "+f"(lo_acc), "+f"(hi_acc)
-            : "r"(u[i]));
-        acc[2 * i] = lo_acc;
-        acc[2 * i + 1] = hi_acc;
-        continue;
-      }
-      const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u[i]));
-      acc[2 * i] = fmaf(w, f.x, acc[2 * i]);
-      acc[2 * i + 1] = fmaf(w, f.y, acc[2 * i + 1]);
-    }
-  }
-};
-
-// Slots in flight per lane: FP32 rows use 4 values per lane, BF16 rows 8 (16-byte loads), so a
-// warp holds twice as many BF16 rows in flight in the same registers.
-template <int LPN, int VPL, bool WEIGHTED>
-__host__ __device__ constexpr int dir_slots() {
-  return VPL == 4 ? (LPN == 32 ? (WEIGHTED ? OFSC_ROW_U32_W : OFSC_ROW_U32) : LPN == 16 ? 4 : 2)
-                  : (LPN == 16 ? (WEIGHTED ? OFSC_ROW_U16_BF16_W : OFSC_ROW_U16_BF16) : LPN == 8 ? 4 : 2);
-}
-
-template <int LPN, int VPL, bool WEIGHTED, bool BF16, bool DOTS>
-__global__ void __launch_bounds__(32 * kRowWarpsPerBlock,
-                                  (VPL == 4 ? OFSC_ROW_WARPS_F32 : OFSC_ROW_WARPS_BF16) / kRowWarpsPerBlock)
-    k_spmm_dir(SpmmArgs a) {
-  if (!a.ignore_done && a.ctrl->done) return;
-  using S = Slot<VPL, BF16>;
-  constexpr int NPI = 32 / LPN;
-  constexpr int U = dir_slots<LPN, VPL, WEIGHTED>();
-  constexpr int STEP = U * NPI;
-  constexpr int WPB = kRowWarpsPerBlock;
-  constexpr int W = VPL * LPN;
-  static_assert(STEP <= 32, "one column index per lane");
-  // per-warp sums of diag(V^T AV) over the warp's rows; each lane owns its columns
-  __shared__ __align__(16) float dred[DOTS ? WPB * W : 4];
-  const int lane = threadIdx.x & 31;
-  const int sub = lane % LPN;
-  const int q = lane / LPN;
-  const int warp = threadIdx.x >> 5;
-  const int gw = blockIdx.x * WPB + warp;
-  const int c = sub * VPL;
-  const bool active = c < a.kp;
-  float* rr = dred + (size_t)warp * W;
-  if (DOTS && lane < LPN) {
-#pragma unroll
-    for (int i = 0; i < VPL; ++i) rr[c + i] = 0.0f;
-  }
-  if (gw < a.groups) {
-    int l = (int)a.bnd[gw];  // column indices are int32, so n < 2^31
-    const int rb = (int)a.bnd[gw + 1];
-    if (l < rb) {
-      const int64_t pend = a.row_ptr[rb];
-      int64_t pb = a.row_ptr[l];
-      int64_t p1 = a.row_ptr[l + 1];
-      int jl = 0;
-      float wl = 1.0f;
-      {
-        const int64_t i = pb + lane;
-        if (lane < STEP && i < pend) {
-          jl = __ldg(a.col + i);
-          if (WEIGHTED) wl = __ldg(a.val + i);
-        }
-      }
-      float acc[VPL];
-#pragma unroll
-      for (int i = 0; i < VPL; ++i) acc[i] = 0.0f;
-      while (true) {
-        const int64_t rem = p1 - pb;
-        const bool last = rem <= STEP;
-        float s = 0.0f;
-        float base[VPL];
-#pragma unroll
-        for (int i = 0; i < VPL; i += 4) {
-          float4 b4 = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (last && lane < LPN && active) b4 = *(const float4*)(a.base + (int64_t)l * a.kp + c + i);
-          base[i] = b4.x; base[i + 1] = b4.y; base[i + 2] = b4.z; base[i + 3] = b4.w;
-        }
-        if (last && lane < LPN && active) s = a.dinv[l];
-        typename S::Raw v[U];
-        float wv[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const int slot = u * NPI + q;
-          const int j = __shfl_sync(0xffffffffu, jl, slot);
-          wv[u] = WEIGHTED ? __shfl_sync(0xffffffffu, wl, slot) : 1.0f;
-          v[u] = (slot < rem && active) ? S::load(a.gather, j, a.kp, c) : S::zero();
-        }
-        const int64_t pn = last ? p1 : pb + STEP;
-        const bool more = !last || l + 1 < rb;
-        int64_t p1n = p1;
-        if (last && more) p1n = a.row_ptr[l + 2];
-        if (more) {
-          const int64_t i = pn + lane;
-          jl = 0;
-          if (lane < STEP && i < pend) {
-            jl = __ldg(a.col + i);
-            if (WEIGHTED) wl = __ldg(a.val + i);
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-          if (u * NPI + q < rem) S::fma(acc, wv[u], v[u]);
-        if (last) {
-#pragma unroll
-          for (int off = LPN; off < 32; off <<= 1)
-#pragma unroll
-            for (int i = 0; i < VPL; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], off);
-          if (lane < LPN && active) {
-            float r[VPL];
-#pragma unroll
-            for (int i = 0; i < VPL; ++i) r[i] = -fmaf(s, acc[i], base[i]);
-#pragma unroll
-            for (int i = 0; i < VPL; i += 4)
-              *(float4*)(a.out + (int64_t)l * a.kp + c + i) = make_float4(r[i], r[i + 1], r[i + 2], r[i + 3]);
-            if (DOTS) {
-#pragma unroll
-              for (int i = 0; i < VPL; ++i) rr[c + i] = fmaf(base[i], r[i], rr[c + i]);
-            }
-          }
-          if (!more) break;
-          ++l;
-          p1 = p1n;
-#pragma unroll
-          for (int i = 0; i < VPL; ++i) acc[i] = 0.0f;
-        }
-        pb = pn;
-      }
-    }
-  }
-  if (DOTS && gw < a.groups) {  // one row of partials per warp: no block-wide barrier
-    __syncwarp();
-    for (int j = lane; j < a.kp; j += 32) a.dots[(int64_t)gw * a.kp + j] = (double)rr[j];
-  }
-}
-
 // Xh = D^-1/2 X (FP32), the gathered block of the exact AX product.
 __global__ void k_scale_rows(int64_t n, int kp, const float* __restrict__ X, const float* __restrict__ dinv,
                              float* __restrict__ Xh, const Ctrl* ctrl, int ignore_done) {
@@ -439,7 +228,9 @@ __global__ void k_dots_fold(const double* __restrict__ pw, int nw, const double*
   }
 }
 
-// V_t = -G_t + V_{t-1} diag(beta) (V_0 = -G_0), its gather copy Vh = D^-1/2 V_t (FP32 or BF16) and
+// V_t = -G_t + V_{t-1} diag(beta) (V_0 = -G_0), stored as V_t diag(1 / s_t) (column scales s_t from
+// k_beta: the FP32 coefficients are vinv = 1 / s_t and beta s_{t-1} / s_t), its gather copy
+// Vh = D^-1/2 V_t (FP32 or BF16) and
 // per-block partial sums of diag(V_t^T G_t), the derivative of every line-search polynomial at
 // alpha = 0. LPN lanes cover a row (four columns each, fixed per thread), 256 / LPN rows per
 // block step; each thread sums its columns over its rows, and the block adds its row groups in
@@ -447,8 +238,8 @@ __global__ void k_dots_fold(const double* __restrict__ pw, int nw, const double*
 template <int LPN, bool BF16>
 __global__ void __launch_bounds__(256) k_vpass(int64_t n, int kp, const float* __restrict__ G, float* __restrict__ V,
                                                void* __restrict__ Vh, const float* __restrict__ dinv,
-                                               const float* __restrict__ beta, int first, double* __restrict__ dots_g,
-                                               Ctrl* ctrl) {
+                                               const float* __restrict__ beta, const float* __restrict__ vinv,
+                                               int first, double* __restrict__ dots_g, Ctrl* ctrl) {
   if (ctrl->done) return;
   constexpr int RPB = 256 / LPN;
   constexpr int W = 4 * LPN;
@@ -456,13 +247,16 @@ __global__ void __launch_bounds__(256) k_vpass(int64_t n, int kp, const float* _
   const int lane = threadIdx.x % LPN, rg = threadIdx.x / LPN;
   const int c = lane * 4;
   const bool active = c < kp;
-  float4 b = make_float4(0.f, 0.f, 0.f, 0.f), acc = b;
-  if (active && !first) b = *(const float4*)(beta + c);
+  float4 b = make_float4(0.f, 0.f, 0.f, 0.f), acc = b, iv = make_float4(1.f, 1.f, 1.f, 1.f);
+  if (active && !first) {
+    b = *(const float4*)(beta + c);
+    iv = *(const float4*)(vinv + c);  // powers of two: exact
+  }
   if (active) {
     for (int64_t row = (int64_t)blockIdx.x * RPB + rg; row < n; row += (int64_t)gridDim.x * RPB) {
       const int64_t e = row * kp + c;
       const float4 g = *(const float4*)(G + e);
-      float4 v = make_float4(-g.x, -g.y, -g.z, -g.w);
+      float4 v = make_float4(-g.x * iv.x, -g.y * iv.y, -g.z * iv.z, -g.w * iv.w);
       if (!first) {
         const float4 vp = *(const float4*)(V + e);
         v.x = fmaf(b.x, vp.x, v.x);
@@ -725,8 +519,15 @@ __global__ void k_fold_rows(const double* __restrict__ part, int nb, int width, 
   }
 }
 
+// stop_ok: this update's G came from an exact AX, so meeting tol may stop the run; on an update
+// whose AX came from the recurrence, meeting tol only sets near_tol (the host then schedules an
+// exact update), so a run never stops on a recurrence value.
+// beta (FP32, for the V pass) is the stored-direction coefficient beta_true s_{t-1} / s_t with s the
+// column scales (vscale, updated here in place; vinv = 1 / s_t); beta64 is Algorithm 2's beta.
+// qprev: the Gram V_{t-1}^T V_{t-1} of the stored previous direction (its diagonal bounds |V_t|).
 __global__ void k_beta(const double* __restrict__ colpart, int nblk, int kp, float* beta,
-                       double* beta64, double* dE, Ctrl* ctrl, int first, int eval) {
+                       double* beta64, double* dE, Ctrl* ctrl, int first, int eval, int stop_ok,
+                       double* vscale, float* vinv, const double* __restrict__ qprev) {
   if (!eval && ctrl->done) return;
   __shared__ double sh[256];
   __shared__ double lanes[256 * kColSums];  // [lane group][kColSums][kp]
@@ -791,9 +592,12 @@ __global__ void k_beta(const double* __restrict__ colpart, int nblk, int kp, flo
     } else {
       const double rel = gnorm / ctrl->g0;
       ctrl->rel = rel;
-      if (rel <= ctrl->tol) {
+      if (rel <= ctrl->tol && stop_ok) {
         ctrl->converged = 1;
         stop = 1;
+      } else if (rel <= ctrl->tol) {
+        ctrl->near_tol = 1;
+        if (ctrl->it >= ctrl->maxit) stop = 1;
       } else if (ctrl->it >= ctrl->maxit) {
         stop = 1;
       }
@@ -804,12 +608,29 @@ __global__ void k_beta(const double* __restrict__ colpart, int nblk, int kp, flo
   if (j < kp) {
     double b = 0.0;
     if (!first && den != 0.0) b = num / den;
-    // restart a column whose new direction would not descend: -|g_j|^2 + beta_j v_prev,j^T g_j >= 0
-    if (-gg + b * vg >= 0.0) b = 0.0;
-    beta[j] = (float)b;
+    const double s_old = first ? 1.0 : vscale[j];
+    // the optional restart (not in Algorithm 2): a column whose new direction would not descend,
+    // -|g_j|^2 + beta_j v_prev,j^T g_j >= 0, takes beta_j = 0
+    if (ctrl->restart && -gg + b * s_old * vg >= 0.0) b = 0.0;
+    // column scale of V_t: |V_t,j| <= |G_t,j| + |beta_j| s_old |Vs_{t-1,j}| = mu; s_t = 1 while
+    // mu <= 2^vscale_exp ||G_0||, else the power of two that brings the stored column back under it
+    // (scaling by powers of two is exact, so the stored values carry the same bits of V)
+    double s_new = 1.0;
+    if (!first) {
+      const double mu = sqrt(gg) + fabs(b) * s_old * sqrt(fmax(qprev[(int64_t)j * kp + j], 0.0));
+      const double ref = ldexp(ctrl->g0, ctrl->vscale_exp);
+      if (mu > ref && ref > 0.0 && isfinite(mu)) {
+        int e = 0;
+        frexp(mu / ref, &e);  // mu / ref in [2^(e-1), 2^e)
+        s_new = ldexp(1.0, e);
+      }
+    }
+    vscale[j] = s_new;
+    vinv[j] = (float)(1.0 / s_new);
+    beta[j] = (float)(b * s_old / s_new);
     beta64[j] = b;
     // diag(V_t^T AX_t) with V_t = -G_t + V_{t-1} diag(beta): -diag(G^T AX) + beta diag(V_prev^T AX)
-    if (dE) dE[j] = first ? -gy : -gy + b * vy;
+    if (dE) dE[j] = first ? -gy : -gy + b * s_old * vy;
   }
 }
 
@@ -1017,10 +838,17 @@ struct SolveArgs {
   double alpha0;  // > 0: fixed step for update 0 instead of the line search
   double* part;   // scratch: [kSolveBlocks][kSolveSums] trace partials, [kp][4] diagonals, [kp][4] cubics
   int tblocks;    // blocks of the trace pass (rows of trace partials)
+  const double* vscale;  // column scales s of the stored V: the Grams and dots are of V diag(1/s)
 };
 
 // C = V^T A V and B = X^T A X are symmetric; the recurrences leave rounding asymmetry.
 #define SYM(M, i, j) (0.5 * ((M)[(i) * kp + (j)] + (M)[(j) * kp + (i)]))
+// The Grams of the stored direction Vs = V diag(1/s) scaled back to V (row index = column of V):
+// P = V^T X, E = V^T AX carry s_i; Q = V^T V, C = V^T AV carry s_i s_j (s = 1: the stored values).
+#define PS(i, j) (sc[i] * P[(i) * kp + (j)])
+#define ES(i, j) (sc[i] * E[(i) * kp + (j)])
+#define QS(i, j) (sc[i] * sc[j] * Q[(i) * kp + (j)])
+#define CS(i, j) (sc[i] * sc[j] * SYM(C, i, j))
 
 // Line search, pass 1 of 3 (nb = solve_blocks(kp) blocks). Block b: the diagonals diag(V^T AV), diag(V^T AX)
 // and diag(V^T G) of columns b, b + nb, ...; for TriOFM their cubics alone (Eqs. (16)/(18) before the
@@ -1040,6 +868,7 @@ __global__ void __launch_bounds__(256) k_solve_traces(SolveArgs a) {
   const double* C = a.gram + G_C * kk;
   const double* R = a.R64;
   const double* B = a.B64;
+  const double* sc = a.vscale;
   double* diag = a.part + kSolveBlocks * kSolveSums;  // [kp][4]: dC, dE, dG
   double* coef = diag + 4 * kp;                       // [kp][4]: cubic of column j alone
   for (int j = b; j < kp; j += nb) {
@@ -1052,9 +881,9 @@ __global__ void __launch_bounds__(256) k_solve_traces(SolveArgs a) {
     // The constant term of every cubic is the derivative along V at alpha = 0, i.e. diag(V^T G)
     // (with the 1/4 of Eq. (15) for OFM-f1): summing v.g directly avoids the cancellation in
     // tr(V^T AX) + tr(V^T X X^T X) near a fixed point, where AX = -X X^T X.
-    const double dC = f2 ? C[j * kp + j] : s2[0];
-    const double dE = f2 ? E[j * kp + j] : a.dE[j];
-    const double dG = s2[1];
+    const double dC = f2 ? CS(j, j) : sc[j] * sc[j] * s2[0];
+    const double dE = f2 ? ES(j, j) : a.dE[j];
+    const double dG = sc[j] * s2[1];
     if (tid == 0) {
       diag[4 * j + 0] = dC;
       diag[4 * j + 1] = dE;
@@ -1067,18 +896,18 @@ __global__ void __launch_bounds__(256) k_solve_traces(SolveArgs a) {
       for (int m = tid; m <= j; m += 256) {
         if (a.method == M_TRI_F1) {
           // (P_jm + a Q_jm)(R_mj + a (P_jm + P_mj) + a^2 Q_mj)
-          const double x0 = P[j * kp + m], x1 = Q[j * kp + m];
-          const double y0 = R[m * kp + j], y1 = P[j * kp + m] + P[m * kp + j], y2 = Q[m * kp + j];
+          const double x0 = PS(j, m), x1 = QS(j, m);
+          const double y0 = R[m * kp + j], y1 = PS(j, m) + PS(m, j), y2 = QS(m, j);
           d[0] += x0 * y1 + x1 * y0;
           d[1] += x0 * y2 + x1 * y1;
           d[2] += x1 * y2;
         } else {
           // -(E_jm + a C_jm)(R_mj + a (P_jm + P_mj) + a^2 Q_mj)
-          const double x0 = E[j * kp + m], x1 = SYM(C, j, m);
-          const double y0 = R[m * kp + j], y1 = P[j * kp + m] + P[m * kp + j], y2 = Q[m * kp + j];
+          const double x0 = ES(j, m), x1 = CS(j, m);
+          const double y0 = R[m * kp + j], y1 = PS(j, m) + PS(m, j), y2 = QS(m, j);
           // -(P_jm + a Q_jm)(B_mj + a (E_jm + E_mj) + a^2 C_mj)
-          const double u0 = P[j * kp + m], u1 = Q[j * kp + m];
-          const double w0 = SYM(B, m, j), w1 = E[j * kp + m] + E[m * kp + j], w2 = SYM(C, m, j);
+          const double u0 = PS(j, m), u1 = QS(j, m);
+          const double w0 = SYM(B, m, j), w1 = ES(j, m) + ES(m, j), w2 = CS(m, j);
           d[0] -= x0 * y1 + x1 * y0 + u0 * w1 + u1 * w0;
           d[1] -= x0 * y2 + x1 * y1 + u0 * w2 + u1 * w1;
           d[2] -= x1 * y2 + u1 * w2;
@@ -1105,27 +934,28 @@ __global__ void __launch_bounds__(256) k_solve_traces(SolveArgs a) {
       if (r == c) v[0] += B[i];
     }
     if (tri) continue;
-    const double q = Q[i], p = P[i];
+    const double q = QS(r, c), p = PS(r, c);
     if (a.method == M_OFM_F1) {
-      v[3] += q * Q[it];
-      v[4] += q * P[it];
-      v[5] += p * P[it];
+      const double pt = PS(c, r);
+      v[3] += q * QS(c, r);
+      v[4] += q * pt;
+      v[5] += p * pt;
       v[6] += p * p;
       v[7] += q * R[it];
       v[8] += p * R[it];
     } else {
-      const double e = E[i], cji = SYM(C, c, r), bji = SYM(B, c, r);
+      const double e = ES(r, c), et = ES(c, r), cji = CS(c, r), bji = SYM(B, c, r);
       v[3] += q * cji;      // tr(Q C)
       v[4] += p * cji;      // tr(P C)
-      v[5] += q * E[it];    // tr(Q E)
+      v[5] += q * et;       // tr(Q E)
       v[6] += p * e;        // tr(P E^T)
-      v[7] += p * E[it];    // tr(P E)
+      v[7] += p * et;       // tr(P E)
       v[8] += q * bji;      // tr(Q B)
       v[9] += rr * cji;     // tr(R C)
       v[10] += p * bji;     // tr(P B)
-      v[11] += rr * E[it];  // tr(R E)
+      v[11] += rr * et;     // tr(R E)
       if (r == c) {
-        v[12] += C[i];
+        v[12] += CS(r, r);
         v[13] += e;
       }
     }
@@ -1219,7 +1049,7 @@ __global__ void __launch_bounds__(256) k_solve(SolveArgs a) {
     __syncthreads();
   }
   for (int j = tid; j < kp; j += 256) {
-    a.alpha[j] = (float)al[j];
+    a.alpha[j] = (float)(al[j] * a.vscale[j]);  // the step along the stored direction V diag(1/s)
     a.alpha64[j] = al[j];
   }
   if (!f2) {  // tr(X'^T AX') = tr B + 2 sum al_j E_jj + sum al_j^2 C_jj
@@ -1264,22 +1094,27 @@ __global__ void __launch_bounds__(256) k_solve_update(SolveArgs a) {
   const double* Q = a.gram + G_Q * kk;
   const double* E = a.gram + G_E * kk;
   const double* C = a.gram + G_C * kk;
+  const double* sc = a.vscale;
   for (int j = tid; j < kp; j += 256) al[j] = a.alpha64[j];
   __syncthreads();
   for (int i = blockIdx.x * 256 + tid; i < kk; i += gridDim.x * 256) {
     const int r = i / kp, c = i % kp;
     const double ar = al[r], ac = al[c];
-    const double rn = a.R64[i] + ar * P[i] + P[c * kp + r] * ac + ar * Q[i] * ac;
+    const double rn = a.R64[i] + ar * PS(r, c) + PS(c, r) * ac + ar * QS(r, c) * ac;
     a.R64[i] = rn;
     a.Rn[i] = (float)rn;
     if (f2) {
-      const double bn = a.B64[i] + E[c * kp + r] * ac + ar * E[i] + ar * SYM(C, r, c) * ac;
+      const double bn = a.B64[i] + ES(c, r) * ac + ar * ES(r, c) + ar * CS(r, c) * ac;
       a.B64[i] = bn;
       a.Bn[i] = (float)bn;
     }
   }
 }
 #undef SYM
+#undef PS
+#undef ES
+#undef QS
+#undef CS
 
 // Exact refresh: X^T X and X^T AX of the current X from their Grams; objective of X.
 __global__ void k_set_rb(const double* __restrict__ gram, int kp, int objective, float* Rn, float* Bn,
@@ -1323,6 +1158,18 @@ namespace {
 constexpr int kGramTargetBlocks = 4 * kNumSMs;
 
 thread_local int64_t g_launches = 0;  // kernels launched by the current call on this thread
+
+// The direction product, counted among the call's launches; slots > 0: a tuned shape.
+int spmm_dir(const SpmmArgs& a, bool weighted, bool bf16, int slots, cudaStream_t s) {
+  ++g_launches;
+  return launch_spmm_dir(a, weighted, bf16, slots, s);
+}
+
+// The gathers in flight per lane that ofsc_autotune chose for this padded width and gather storage
+// (0, the kernel's default, for any other).
+int tuned_slots(const ofsc_graph* g, int kp, bool bf16) {
+  return (g->dir_tuned_kp == kp && g->dir_tuned_bf16 == (bf16 ? 1 : 0)) ? g->dir_slots : 0;
+}
 
 int gram_m_for(int kp) { return kp <= 16 ? 1 : kp <= 32 ? 2 : 4; }
 int gram_nt_for(int kp) { return (int)ceil_div(kp, 16 * gram_m_for(kp)); }
@@ -1400,11 +1247,11 @@ void launch_spmm(const SpmmArgs& a, bool weighted, cudaStream_t s) {
 }
 
 void launch_vpass(int lpn, bool bf16, int grid, cudaStream_t s, int64_t n, int kp, const float* G, float* V, void* Vh,
-                  const float* dinv, const float* beta, int first, double* dots_g, Ctrl* ctrl) {
-#define OFSC_VPASS(L)                                                                                    \
-  case L:                                                                                               \
-    if (bf16) k_vpass<L, true><<<grid, 256, 0, s>>>(n, kp, G, V, Vh, dinv, beta, first, dots_g, ctrl);   \
-    else k_vpass<L, false><<<grid, 256, 0, s>>>(n, kp, G, V, Vh, dinv, beta, first, dots_g, ctrl);       \
+                  const float* dinv, const float* beta, const float* vinv, int first, double* dots_g, Ctrl* ctrl) {
+#define OFSC_VPASS(L)                                                                                          \
+  case L:                                                                                                     \
+    if (bf16) k_vpass<L, true><<<grid, 256, 0, s>>>(n, kp, G, V, Vh, dinv, beta, vinv, first, dots_g, ctrl);   \
+    else k_vpass<L, false><<<grid, 256, 0, s>>>(n, kp, G, V, Vh, dinv, beta, vinv, first, dots_g, ctrl);       \
     break;
   switch (lpn) {
     OFSC_VPASS(2)
@@ -1415,51 +1262,6 @@ void launch_vpass(int lpn, bool bf16, int grid, cudaStream_t s, int64_t n, int k
       OFSC_VPASS(32)
   }
 #undef OFSC_VPASS
-}
-
-template <int LPN, int VPL, bool WEIGHTED, bool BF16>
-void launch_dir_w(const SpmmArgs& a, bool dots, cudaStream_t s) {
-  const int grid = a.groups / kRowWarpsPerBlock;
-  if (dots) k_spmm_dir<LPN, VPL, WEIGHTED, BF16, true><<<grid, 32 * kRowWarpsPerBlock, 0, s>>>(a);
-  else k_spmm_dir<LPN, VPL, WEIGHTED, BF16, false><<<grid, 32 * kRowWarpsPerBlock, 0, s>>>(a);
-}
-
-template <int LPN, int VPL, bool BF16>
-void launch_dir_l(const SpmmArgs& a, bool weighted, cudaStream_t s) {
-  const bool dots = a.dots != nullptr;
-  if (weighted) launch_dir_w<LPN, VPL, true, BF16>(a, dots, s);
-  else launch_dir_w<LPN, VPL, false, BF16>(a, dots, s);
-}
-
-// Lanes per nonzero of the direction product: rows of kp values, VPL per lane, a power of two
-// of at least 2.
-int dir_lanes(int kp, int vpl) {
-  int l = 2;
-  while (l * vpl < kp) l *= 2;
-  return l;
-}
-
-// The direction product on the warp-per-row partition; returns the rows of dots partials (one per
-// warp).
-int launch_spmm_dir(const SpmmArgs& a, bool weighted, bool bf16, cudaStream_t s) {
-  ++g_launches;
-  if (bf16) {
-    switch (dir_lanes(a.kp, 8)) {
-      case 2: launch_dir_l<2, 8, true>(a, weighted, s); break;
-      case 4: launch_dir_l<4, 8, true>(a, weighted, s); break;
-      case 8: launch_dir_l<8, 8, true>(a, weighted, s); break;
-      default: launch_dir_l<16, 8, true>(a, weighted, s); break;
-    }
-  } else {
-    switch (dir_lanes(a.kp, 4)) {
-      case 2: launch_dir_l<2, 4, false>(a, weighted, s); break;
-      case 4: launch_dir_l<4, 4, false>(a, weighted, s); break;
-      case 8: launch_dir_l<8, 4, false>(a, weighted, s); break;
-      case 16: launch_dir_l<16, 4, false>(a, weighted, s); break;
-      default: launch_dir_l<32, 4, false>(a, weighted, s); break;
-    }
-  }
-  return a.groups;
 }
 
 int kpmax_for(int kp) { return kp <= 16 ? 16 : kp <= 32 ? 32 : kp <= 64 ? 64 : 128; }
@@ -1578,6 +1380,8 @@ ofsc_status ensure_workspace(ofsc_graph* g, int kp) {
       {(void**)&ws.beta, kp * sizeof(float)},
       {(void**)&ws.alpha64, kp * sizeof(double)},
       {(void**)&ws.beta64, kp * sizeof(double)},
+      {(void**)&ws.vscale, kp * sizeof(double)},
+      {(void**)&ws.vinv, kp * sizeof(float)},
       {(void**)&ws.colpart, (size_t)(kMaxRowBlocks + kDotsRows) * kColSums * kp * sizeof(double)},
       {(void**)&ws.dE, (size_t)kp * sizeof(double)},
       {(void**)&ws.solve, (size_t)(kSolveBlocks * kSolveSums + 8 * kp) * sizeof(double)},
@@ -1679,7 +1483,7 @@ struct Runner {
     a.base = ws.X;
     a.out = ws.Y;
     a.ignore_done = ignore_done;
-    launch_spmm_dir(a, g->weighted != 0, false, s);
+    spmm_dir(a, g->weighted != 0, false, 0, s);
     const float* R[2] = {ws.X, ws.Y};
     const int slots[2] = {G_R, G_B};
     cudaError_t e = grams(ws.X, R, 2, slots, ignore_done, false);
@@ -1723,7 +1527,7 @@ struct Runner {
 
   // beta, the stop test and the objective's diagonal term from the direction pass's column sums,
   // folded to kDotsRows rows first (eval: only the gradient norm)
-  void beta(int nblk, int first, int eval) {
+  void beta(int nblk, int first, int eval, int stop_ok = 1) {
     const double* cp = ws.colpart;
     if (nblk > kDotsRows) {
       double* folded = ws.colpart + (size_t)kMaxRowBlocks * kColSums * ws.kp;
@@ -1732,7 +1536,8 @@ struct Runner {
       cp = folded;
       nblk = kDotsRows;
     }
-    k_beta<<<1, 256, 0, s>>>(cp, nblk, ws.kp, ws.beta, ws.beta64, eval ? nullptr : ws.dE, ws.ctrl, first, eval);
+    k_beta<<<1, 256, 0, s>>>(cp, nblk, ws.kp, ws.beta, ws.beta64, eval ? nullptr : ws.dE, ws.ctrl, first, eval,
+                             stop_ok, ws.vscale, ws.vinv, ws.gram + G_Q * (size_t)ws.kp * ws.kp);
     ++g_launches;
   }
 
@@ -1747,7 +1552,8 @@ struct Runner {
     prof.begin(OFSC_PHASE_OTHER);
     const int lpn = spmm_lanes(ws.kp);
     const int vgrid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ws.n, 256 / lpn), kVpassMaxBlocks));
-    launch_vpass(lpn, bf16, vgrid, s, ws.n, ws.kp, ws.G, ws.V, ws.Vh, g->dinv, ws.beta, first, dots_g, ws.ctrl);
+    launch_vpass(lpn, bf16, vgrid, s, ws.n, ws.kp, ws.G, ws.V, ws.Vh, g->dinv, ws.beta, ws.vinv, first, dots_g,
+                 ws.ctrl);
     ++g_launches;
     prof.end();
     // AV_t exactly (one sparse product), with diag(V^T AV)
@@ -1780,7 +1586,7 @@ struct Runner {
     } else {
       a.bnd = g->bnd[kRowPart];
       a.groups = g->groups[kRowPart];
-      dots_blocks = launch_spmm_dir(a, g->weighted != 0, bf16, s);
+      dots_blocks = spmm_dir(a, g->weighted != 0, bf16, tuned_slots(g, ws.kp, bf16), s);
     }
     k_dots_fold<<<kDotsRows, 256, 0, s>>>(dots_w, dots_blocks, dots_g, vgrid, ws.kp, folded, ws.ctrl);
     ++g_launches;
@@ -1810,6 +1616,7 @@ struct Runner {
     sa.alpha0 = alpha0;
     sa.part = ws.solve;
     sa.tblocks = solve_blocks(ws.kp);
+    sa.vscale = ws.vscale;
     prof.begin(OFSC_PHASE_LINESEARCH);
     k_solve_traces<<<sa.tblocks, 256, 0, s>>>(sa);
     k_solve<<<1, 256, 0, s>>>(sa);
@@ -1848,7 +1655,7 @@ cudaError_t apply_A(ofsc_graph* g, int kp, const float* X, float* Y, float* scra
   a.base = X;
   a.out = Y;
   a.ignore_done = 1;
-  launch_spmm_dir(a, g->weighted != 0, false, s);
+  spmm_dir(a, g->weighted != 0, false, 0, s);
   return cudaGetLastError();
 }
 
@@ -2028,6 +1835,12 @@ ofsc_status check_iterate_args(const ofsc_graph* g, int32_t method, int32_t k, c
     return fail(OFSC_ERR_INVALID_ARG, "%s: unknown gram_engine %d", who, o.gram_engine);
   if (o.spmm_engine < OFSC_SPMM_AUTO || o.spmm_engine > OFSC_SPMM_TMA)
     return fail(OFSC_ERR_INVALID_ARG, "%s: unknown spmm_engine %d", who, o.spmm_engine);
+  if (o.cg_restart != 0 && o.cg_restart != 1)
+    return fail(OFSC_ERR_INVALID_ARG, "%s: cg_restart must be 0 or 1", who);
+  if (!(o.refine_tol >= 0.0)) return fail(OFSC_ERR_INVALID_ARG, "%s: refine_tol must be >= 0", who);
+  if (!(o.exact_tail == o.exact_tail)) return fail(OFSC_ERR_INVALID_ARG, "%s: exact_tail is NaN", who);
+  if (o.vscale_exp < -60 || o.vscale_exp > 60)
+    return fail(OFSC_ERR_INVALID_ARG, "%s: vscale_exp outside [-60, 60]", who);
   const int kp = round_up(k, 8);
   const bool tc = o.gram_engine == OFSC_GRAM_TC || (o.gram_engine == OFSC_GRAM_AUTO && kp > 64);
   if (tc && kp > 128) return fail(OFSC_ERR_INVALID_ARG, "%s: tensor-core Grams need k <= 128", who);
@@ -2048,12 +1861,49 @@ struct Job {
   Prof prof;
   Runner run;
   int64_t launches = 0;  // kernels launched for this graph
+  // FP32 refinement sweep of a BF16-gather run: pending until a host check reads
+  // ||G_t|| <= refine_tol ||G_0||; refined_at is the update from which gathers are FP32 (-1: never)
+  bool refine_pending = false;
+  int refined_at = -1;
+  // Exact tail (opts.exact_tail > 0, or 1e3 tol by default): once a host check reads
+  // ||G_t|| <= exact_tail ||G_0||, every
+  // later update is exact; exact_at is the first such update. Independently, tol met on an update
+  // whose AX came from the recurrence (near_tol) makes the update after the next host check exact,
+  // and only exact updates may stop the run.
+  double exact_tail;
+  bool exact = false;
+  int exact_at = -1;
+  int forced_refresh = -1;
 
   Job(ofsc_graph* g_, int method_, int k_, float* X_, double tol_, int maxit_, const ofsc_opts& o_, cudaStream_t s_)
       : g(g_), method(method_), k(k_), kp(round_up(k_, 8)),
         objective((method_ == OFSC_OFM_F1 || method_ == OFSC_TRI_F1) ? 1 : 2), maxit(maxit_),
         y_refresh(o_.y_refresh > 0 ? o_.y_refresh : 32), X(X_), tol(tol_), o(o_), s(s_),
-        prof{g_->ws, o_.profile, s_}, run{g_, g_->ws, s_, method_, o_.gather == OFSC_GATHER_BF16, prof} {}
+        prof{g_->ws, o_.profile, s_}, run{g_, g_->ws, s_, method_, o_.gather == OFSC_GATHER_BF16, prof},
+        refine_pending(o_.gather == OFSC_GATHER_BF16 && o_.refine_tol > 0.0),
+        exact_tail(o_.exact_tail > 0.0 ? o_.exact_tail : (o_.exact_tail == 0.0 && tol_ > 0.0 ? 1e3 * tol_ : 0.0)) {}
+
+  // Host check after update t: copies done, rel (and it) from the control block; the caller
+  // synchronises the stream before calling checked().
+  cudaError_t queue_check(cudaStream_t on) {
+    return cudaMemcpyAsync(g->ws.ctrl_host, g->ws.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, on);
+  }
+  // After the copy of queue_check has landed: switches a pending BF16 run to FP32 gathers once the
+  // relative direction norm has reached refine_tol (from update t + 1 on). Returns done.
+  bool checked(int t) {
+    const Ctrl& c = *g->ws.ctrl_host;
+    if (refine_pending && !c.done && c.status == OFSC_OK && c.rel <= o.refine_tol) {
+      refine_pending = false;
+      run.bf16 = false;
+      refined_at = t + 1;
+    }
+    if (!exact && exact_tail > 0.0 && !c.done && c.status == OFSC_OK && c.rel <= exact_tail) {
+      exact = true;
+      exact_at = t + 1;
+    }
+    if (c.near_tol && !c.done && c.status == OFSC_OK) forced_refresh = t + 1;
+    return c.done != 0;
+  }
 
   // Workspace, engines and TMA maps; call before any launch (allocates, so never under capture).
   ofsc_status prepare() {
@@ -2077,7 +1927,8 @@ struct Job {
   ofsc_status start() {
     const int64_t l0 = g_launches;
     Workspace& ws = g->ws;
-    k_init_ctrl<<<1, 1, 0, s>>>(ws.ctrl, tol, maxit, k, g->normA2, o.trace ? o.trace_cap : 0);
+    k_init_ctrl<<<1, 1, 0, s>>>(ws.ctrl, tol, maxit, k, g->normA2, o.trace ? o.trace_cap : 0, o.cg_restart ? 1 : 0,
+                                o.vscale_exp != 0 ? o.vscale_exp : kDefaultVscaleExp);
     ++g_launches;
     OFSC_LAUNCH_CHECK("k_init_ctrl");
     k_pad_in<<<grid_elems(g->n * kp), 256, 0, s>>>(g->n, k, kp, X, ws.X, ws.ctrl);
@@ -2108,7 +1959,8 @@ struct Job {
       OFSC_CUDA(run.rowpass(method, t > 0 ? 1 : 0, t == 0 ? 1 : 0, 0, &nblk));
     }
     prof.begin(OFSC_PHASE_BETA);
-    run.beta(nblk, t == 0 ? 1 : 0, 0);
+    // t = 0 follows the exact AX of start(); a refresh update is exact as well
+    run.beta(nblk, t == 0 ? 1 : 0, 0, (t == 0 || is_refresh(t)) ? 1 : 0);
     prof.end();
     OFSC_LAUNCH_CHECK("k_beta");
     if (t < maxit) OFSC_CUDA(run.direction_and_linesearch(t == 0 ? 1 : 0, o, k, t == 0 ? o.alpha0 : 0.0));
@@ -2116,7 +1968,8 @@ struct Job {
     return OFSC_OK;
   }
 
-  bool is_refresh(int t) const { return t > 0 && (t % y_refresh) == 0; }
+  // exact: every update from here on recomputes AX, X^T X and X^T AX (the exact tail)
+  bool is_refresh(int t) const { return t > 0 && (exact || t == forced_refresh || (t % y_refresh) == 0); }
   // The launches of update(t) are the same for every t with plain(t) true.
   bool plain(int t) const { return t > 0 && t < maxit && !is_refresh(t); }
 
@@ -2151,10 +2004,16 @@ struct Job {
       out->g0_norm = c.g0;
       out->f = c.f;
       out->kernel_launches = launches;
+      out->refined_at = refined_at;
+      out->exact_at = exact_at;
     }
     return rs;
   }
 };
+
+ofsc_status iterate_lockstep(int32_t count, ofsc_graph* const* graphs, int32_t method, const int32_t* ks,
+                             float* const* Xs, double tol, int32_t maxit, const ofsc_opts& o, ofsc_result* outs,
+                             cudaStream_t caller, const char* who);
 
 ofsc_status result_error(ofsc_status rs, const char* who) {
   if (rs == OFSC_ERR_NONFINITE) return fail(rs, "%s: non-finite value in X0 or in the iteration", who);
@@ -2174,8 +2033,15 @@ extern "C" ofsc_status ofsc_iterate(ofsc_graph* g, int32_t method, int32_t k, fl
   if (st != OFSC_OK) return st;
   const int check_every = o.check_every > 0 ? o.check_every : 16;
   cudaStream_t s = (cudaStream_t)stream_;
-  if (out) *out = ofsc_result{0, OFSC_OK, 0.0, 0.0, 0.0, 0};
+  if (out) *out = ofsc_result{0, OFSC_OK, 0.0, 0.0, 0.0, 0, -1, -1};
   if (g->n == 0) return OFSC_OK;
+  if (!o.profile && o.direct_launch == 0) {
+    // replay the repeating updates from a captured CUDA graph (the same launches, so the same bits)
+    ofsc_graph* gs[1] = {g};
+    const int32_t kk[1] = {k};
+    float* xs[1] = {X};
+    return iterate_lockstep(1, gs, method, kk, xs, tol, maxit, o, out, s, "ofsc_iterate");
+  }
   Job job(g, method, k, X, tol, maxit, o, s);
   st = job.prepare();
   if (st != OFSC_OK) return st;
@@ -2188,10 +2054,10 @@ extern "C" ofsc_status ofsc_iterate(ofsc_graph* g, int32_t method, int32_t k, fl
     if (st != OFSC_OK) return st;
     if (t == maxit) break;
     if ((t + 1) % check_every == 0) {
-      OFSC_CUDA(cudaMemcpyAsync(&ws.ctrl_host->done, &ws.ctrl->done, sizeof(int), cudaMemcpyDeviceToHost, s));
+      OFSC_CUDA(job.queue_check(s));
       OFSC_CUDA(cudaStreamSynchronize(s));
       job.prof.collect();
-      if (ws.ctrl_host->done) break;
+      if (job.checked(t)) break;
     }
   }
   Ctrl c{};
@@ -2209,24 +2075,25 @@ extern "C" ofsc_status ofsc_iterate(ofsc_graph* g, int32_t method, int32_t k, fl
 // ofsc_autotune: the row-partition granularity of the direction product, chosen by timing.
 // ==========================================================================================
 
-extern "C" ofsc_status ofsc_autotune(ofsc_graph* g, int32_t k, int32_t gather, int32_t* warps_out, double* ms_out,
-                                     void* stream_) {
+extern "C" ofsc_status ofsc_autotune(ofsc_graph* g, int32_t k, int32_t gather, int32_t* warps_out,
+                                     int32_t* slots_out, double* ms_out, void* stream_) {
   clear_error();
   if (!g) return fail(OFSC_ERR_INVALID_ARG, "ofsc_autotune: graph is NULL");
   if (k < 1 || k > kMaxK) return fail(OFSC_ERR_INVALID_ARG, "ofsc_autotune: k=%d outside [1, %d]", k, kMaxK);
   if (gather != OFSC_GATHER_FP32 && gather != OFSC_GATHER_BF16)
     return fail(OFSC_ERR_INVALID_ARG, "ofsc_autotune: unknown gather mode %d", gather);
   cudaStream_t s = (cudaStream_t)stream_;
+  const int kp = round_up(k, 8);
+  const bool bf16 = gather == OFSC_GATHER_BF16;
   if (g->n == 0 || g->nnz == 0) {
     if (warps_out) *warps_out = g->groups[kRowPart];
+    if (slots_out) *slots_out = dir_default_slots(kp, bf16, g->weighted != 0);
     if (ms_out) *ms_out = 0.0;
     return OFSC_OK;
   }
-  const int kp = round_up(k, 8);
   ofsc_status st = ensure_workspace(g, kp);
   if (st != OFSC_OK) return st;
   Workspace& ws = g->ws;
-  const bool bf16 = gather == OFSC_GATHER_BF16;
   // timing depends on the access pattern only: zero blocks
   OFSC_CUDA(cudaMemsetAsync(ws.V, 0, (size_t)g->n * kp * sizeof(float), s));
   OFSC_CUDA(cudaMemsetAsync(ws.Vh, 0, (size_t)g->n * kp * sizeof(float), s));
@@ -2245,7 +2112,9 @@ extern "C" ofsc_status ofsc_autotune(ofsc_graph* g, int32_t k, int32_t gather, i
     }
   } ev{e0, e1};
   const int min_wps = OFSC_ROW_MIN_WARPS_PER_SM, max_wps = OFSC_ROW_MAX_WARPS_PER_SM;
-  int best_w = 0;
+  int opts[4];
+  const int nopt = dir_slot_options(kp, bf16, opts);
+  int best_w = 0, best_u = 0;
   float best_ms = 0.0f;
   for (int wps = min_wps; wps <= max_wps; wps *= 2) {
     const int W = wps * kNumSMs;
@@ -2267,25 +2136,33 @@ extern "C" ofsc_status ofsc_autotune(ofsc_graph* g, int32_t k, int32_t gather, i
     a.dots = ws.dots;
     a.ctrl = ws.ctrl;
     a.ignore_done = 1;
-    launch_spmm_dir(a, g->weighted != 0, bf16, s);  // warm
-    OFSC_CUDA(cudaEventRecord(e0, s));
-    for (int r = 0; r < 3; ++r) launch_spmm_dir(a, g->weighted != 0, bf16, s);
-    OFSC_CUDA(cudaEventRecord(e1, s));
-    OFSC_CUDA(cudaEventSynchronize(e1));
-    OFSC_LAUNCH_CHECK("ofsc_autotune: direction product");
-    float ms = 0.0f;
-    OFSC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-    ms /= 3.0f;
-    if (best_w == 0 || ms < best_ms) {
-      best_w = W;
-      best_ms = ms;
+    for (int oi = 0; oi < nopt; ++oi) {
+      const int u = opts[oi];
+      launch_spmm_dir(a, g->weighted != 0, bf16, u, s);  // warm
+      OFSC_CUDA(cudaEventRecord(e0, s));
+      for (int r = 0; r < 3; ++r) launch_spmm_dir(a, g->weighted != 0, bf16, u, s);
+      OFSC_CUDA(cudaEventRecord(e1, s));
+      OFSC_CUDA(cudaEventSynchronize(e1));
+      OFSC_LAUNCH_CHECK("ofsc_autotune: direction product");
+      float ms = 0.0f;
+      OFSC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      ms /= 3.0f;
+      if (best_w == 0 || ms < best_ms) {
+        best_w = W;
+        best_u = u;
+        best_ms = ms;
+      }
     }
   }
   if (g->groups[kRowPart] != best_w) {
     st = set_row_partition(g, best_w, s);
     if (st != OFSC_OK) return st;
   }
+  g->dir_tuned_kp = kp;
+  g->dir_tuned_bf16 = bf16 ? 1 : 0;
+  g->dir_slots = best_u;
   if (warps_out) *warps_out = best_w;
+  if (slots_out) *slots_out = best_u;
   if (ms_out) *ms_out = best_ms;
   return OFSC_OK;
 }
@@ -2354,26 +2231,17 @@ struct GraphExec {
 }  // namespace
 }  // namespace ofsc
 
-extern "C" ofsc_status ofsc_iterate_batched(int32_t count, ofsc_graph* const* graphs, int32_t method,
-                                            const int32_t* ks, float* const* Xs, double tol, int32_t maxit,
-                                            const ofsc_opts* opts, ofsc_result* outs, void* stream_) {
-  clear_error();
-  if (count < 0) return fail(OFSC_ERR_INVALID_ARG, "ofsc_iterate_batched: count < 0");
-  if (count > 0 && (!graphs || !ks || !Xs)) return fail(OFSC_ERR_INVALID_ARG, "ofsc_iterate_batched: NULL array");
-  ofsc_opts o{};
-  if (opts) o = *opts;
-  if (o.trace || o.profile)
-    return fail(OFSC_ERR_INVALID_ARG, "ofsc_iterate_batched: opts.trace and opts.profile must be NULL");
-  for (int i = 0; i < count; ++i) {
-    ofsc_status st = check_iterate_args(graphs[i], method, ks[i], Xs[i], tol, maxit, o, "ofsc_iterate_batched");
-    if (st != OFSC_OK) return st;
-    for (int j = 0; j < i; ++j)
-      if (graphs[j] == graphs[i]) return fail(OFSC_ERR_INVALID_ARG, "ofsc_iterate_batched: graph %d repeats graph %d", i, j);
-  }
-  if (outs)
-    for (int i = 0; i < count; ++i) outs[i] = ofsc_result{0, OFSC_OK, 0.0, 0.0, 0.0, 0};
+namespace ofsc {
+namespace {
+
+// The lockstep driver of ofsc_iterate_batched, and of ofsc_iterate when it replays: arguments
+// already checked, outs already cleared. Updates whose launches repeat for every problem are
+// captured once into a CUDA graph and replayed (unless o.direct_launch); a trace is allowed for
+// one problem (its records are written by a kernel at the device-side update index).
+ofsc_status iterate_lockstep(int32_t count, ofsc_graph* const* graphs, int32_t method, const int32_t* ks,
+                             float* const* Xs, double tol, int32_t maxit, const ofsc_opts& o, ofsc_result* outs,
+                             cudaStream_t caller, const char* who) {
   const int check_every = o.check_every > 0 ? o.check_every : 16;
-  cudaStream_t caller = (cudaStream_t)stream_;
   std::vector<std::unique_ptr<Job>> jobs;
   std::vector<int> slot;  // job index -> position in the caller's arrays
   for (int i = 0; i < count; ++i) {
@@ -2410,7 +2278,9 @@ extern "C" ofsc_status ofsc_iterate_batched(int32_t count, ofsc_graph* const* gr
   std::vector<int64_t> plain_launches(jobs.size(), 0);
   bool forked = true;               // job streams are ordered after main and main not after them
   for (int t = 0; t <= maxit; ++t) {
-    if (replay && jobs[0]->plain(t)) {
+    bool all_plain = true;
+    for (auto& j : jobs) all_plain = all_plain && j->plain(t);
+    if (replay && all_plain) {
       if (forked) {
         OFSC_CUDA(join_jobs(main, jobs, jev));
         forked = false;
@@ -2456,13 +2326,21 @@ extern "C" ofsc_status ofsc_iterate_batched(int32_t count, ofsc_graph* const* gr
         OFSC_CUDA(join_jobs(main, jobs, jev));
         forked = false;
       }
-      for (auto& j : jobs)
-        OFSC_CUDA(cudaMemcpyAsync(&j->g->ws.ctrl_host->done, &j->g->ws.ctrl->done, sizeof(int),
-                                  cudaMemcpyDeviceToHost, main));
+      for (auto& j : jobs) OFSC_CUDA(j->queue_check(main));
       OFSC_CUDA(cudaStreamSynchronize(main));
-      bool all = true;
-      for (auto& j : jobs) all = all && j->g->ws.ctrl_host->done;
+      bool all = true, switched = false;
+      for (auto& j : jobs) {
+        const bool was = j->run.bf16;
+        all = j->checked(t) && all;
+        switched = switched || (was != j->run.bf16);
+      }
       if (all) break;
+      // a job that moved to FP32 gathers launches other kernels: capture the plain update again
+      // (a job in its exact tail is never plain, so the batch launches directly from then on)
+      if (switched && plain.exec) {
+        cudaGraphExecDestroy(plain.exec);
+        plain.exec = nullptr;
+      }
     }
   }
   // final reports: read every control block, then queue the exact evaluations together
@@ -2485,7 +2363,32 @@ extern "C" ofsc_status ofsc_iterate_batched(int32_t count, ofsc_graph* const* gr
     const ofsc_status rs = jobs[i]->result(outs ? &outs[slot[i]] : nullptr);
     if (rs != OFSC_OK && (worst == OFSC_OK || worst == OFSC_ERR_NOT_CONVERGED)) worst = rs;
   }
-  return result_error(worst, "ofsc_iterate_batched");
+  return result_error(worst, who);
+}
+
+}  // namespace
+}  // namespace ofsc
+
+extern "C" ofsc_status ofsc_iterate_batched(int32_t count, ofsc_graph* const* graphs, int32_t method,
+                                            const int32_t* ks, float* const* Xs, double tol, int32_t maxit,
+                                            const ofsc_opts* opts, ofsc_result* outs, void* stream_) {
+  clear_error();
+  if (count < 0) return fail(OFSC_ERR_INVALID_ARG, "ofsc_iterate_batched: count < 0");
+  if (count > 0 && (!graphs || !ks || !Xs)) return fail(OFSC_ERR_INVALID_ARG, "ofsc_iterate_batched: NULL array");
+  ofsc_opts o{};
+  if (opts) o = *opts;
+  if (o.trace || o.profile)
+    return fail(OFSC_ERR_INVALID_ARG, "ofsc_iterate_batched: opts.trace and opts.profile must be NULL");
+  for (int i = 0; i < count; ++i) {
+    ofsc_status st = check_iterate_args(graphs[i], method, ks[i], Xs[i], tol, maxit, o, "ofsc_iterate_batched");
+    if (st != OFSC_OK) return st;
+    for (int j = 0; j < i; ++j)
+      if (graphs[j] == graphs[i]) return fail(OFSC_ERR_INVALID_ARG, "ofsc_iterate_batched: graph %d repeats graph %d", i, j);
+  }
+  if (outs)
+    for (int i = 0; i < count; ++i) outs[i] = ofsc_result{0, OFSC_OK, 0.0, 0.0, 0.0, 0, -1, -1};
+  return iterate_lockstep(count, graphs, method, ks, Xs, tol, maxit, o, outs, (cudaStream_t)stream_,
+                          "ofsc_iterate_batched");
 }
 
 // ==========================================================================================
@@ -2500,7 +2403,9 @@ extern "C" ofsc_status ofsc_iterate_batched(int32_t count, ofsc_graph* const* gr
 // Limits: n * kp <= 2^20 (kp = k rounded up to a multiple of 8, k <= 128); the array holds
 // kNoAllocBytes (about 30 MiB) on every GPU that loads the library, until the process exits.
 // The first call on a device looks the array's address up (cudaGetSymbolAddress) with that
-// device current; make that first call before any stream capture. Every call shares the one
+// device current; make that first call before any stream capture. The address is cached per
+// device for the life of the process: after a cudaDeviceReset of a device, this entry point must
+// not be called on it again. The graph must live on the current device. Every call shares the one
 // array and it keeps the last call's contents, so calls that overlap on the GPU (other streams,
 // other host threads) race; order them. Nothing read by a call depends on earlier contents: the
 // control block, the padded copy of X and every partial sum are written before they are read.
@@ -2534,10 +2439,10 @@ constexpr int kNoAllocMaxDevices = 64;
 std::mutex g_noalloc_mu;
 void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
 
-// Device address of g_noalloc_scratch on the current device (looked up once per device).
-ofsc_status noalloc_scratch(void** out) {
-  int dev = 0;
-  OFSC_CUDA(cudaGetDevice(&dev));
+// Device address of g_noalloc_scratch on the current device `dev` (looked up once per device; the
+// cached address belongs to that device's primary context, so it does not survive a
+// cudaDeviceReset of the device).
+ofsc_status noalloc_scratch(int dev, void** out) {
   if (dev < 0 || dev >= kNoAllocMaxDevices)
     return fail(OFSC_ERR_INVALID_ARG, "ofsc_objective_grad_noalloc: device %d not supported", dev);
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
@@ -2574,8 +2479,13 @@ extern "C" ofsc_status ofsc_objective_grad_noalloc(const ofsc_graph* gc, int32_t
     if (f_out) *f_out = 0.0;
     return OFSC_OK;
   }
+  int dev = 0;
+  OFSC_CUDA(cudaGetDevice(&dev));
+  if (dev != gc->device)
+    return fail(OFSC_ERR_INVALID_ARG, "ofsc_objective_grad_noalloc: the current device is %d, the graph's is %d",
+                dev, gc->device);
   void* base = nullptr;
-  ofsc_status st = noalloc_scratch(&base);
+  ofsc_status st = noalloc_scratch(dev, &base);
   if (st != OFSC_OK) return st;
   unsigned char* p = (unsigned char*)base;
   Workspace ws;  // views into the static array; owns nothing

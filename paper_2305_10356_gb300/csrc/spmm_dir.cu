@@ -1,0 +1,306 @@
+// The direction product of one update of Algorithm 2 (the sparse product of Sec. 3.3):
+// W = A V = -V - D^-1/2 S D^-1/2 V with A = L - 2I (Eq. (1)), gathering Vh = D^-1/2 V.
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+
+namespace ofsc {
+namespace {
+
+#ifndef OFSC_ROW_U32
+#define OFSC_ROW_U32 8  // gathers in flight per lane when a warp covers a row of 128 columns
+#endif
+#ifndef OFSC_ROW_WARPS_F32
+#define OFSC_ROW_WARPS_F32 32  // resident warps per SM the registers must allow (FP32 slots)
+#endif
+#ifndef OFSC_ROW_U16_BF16
+#define OFSC_ROW_U16_BF16 6  // gathers in flight per lane for 16-byte BF16 slots (128 columns)
+#endif
+// Weighted graphs load an FP32 value beside every column index: fewer slots keep them in the
+// same 64 registers without spilling.
+#ifndef OFSC_ROW_U32_W
+#define OFSC_ROW_U32_W 8
+#endif
+#ifndef OFSC_ROW_U16_BF16_W
+#define OFSC_ROW_U16_BF16_W 6
+#endif
+#ifndef OFSC_ROW_WARPS_BF16
+#define OFSC_ROW_WARPS_BF16 32  // resident warps per SM the registers must allow (BF16 slots)
+#endif
+
+
+// W = A V = -V - D^-1/2 S Vh for a direction V (or AX from Xh = D^-1/2 X), with the fused
+// per-block partial sums of diag(V^T AV). A warp owns a contiguous, nnz-balanced range of rows
+// and takes one row at a time, so its control flow is uniform: LPN lanes per nonzero hold four
+// columns each, NPI = 32 / LPN nonzeros are gathered side by side and U of those slots per lane
+// are in flight together (STEP = U NPI <= 32 nonzeros per step; a short row's last step is
+// predicated, not split). The STEP column indices of a step are loaded one per lane and handed
+// out by shuffle; those of the next step (at a row end, of the next row) are loaded while the
+// current gathers are in flight, and a row's epilogue operands (its row of V, its D^-1/2 entry)
+// are loaded with the gathers of its last step (staging them through shared memory with cp.async
+// measured 12% slower). Each lane sums its slots in nonzero order; the NPI partial sums of a row
+// are combined by an xor-shuffle butterfly, which leaves the same bits in every lane (for LPN = 32
+// the sum is in plain nonzero order). Each warp writes its own row of partials (no block-wide
+// barrier, so a block is never held by its slowest warp's reduction); k_dots_fold folds them.
+// One gathered slot of VPL consecutive values of a row of Vh, kept raw (FP32: float4; BF16: 8
+// values in a uint4) until it is accumulated, so a slot in flight costs four registers.
+template <int VPL, bool BF16>
+struct Slot;
+template <>
+struct Slot<4, false> {
+  using Raw = float4;
+  static __device__ __forceinline__ Raw load(const void* p, int64_t row, int kp, int c) {
+    return __ldg((const float4*)((const float*)p + row * kp + c));
+  }
+  static __device__ __forceinline__ Raw zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+  static __device__ __forceinline__ void fma(float* acc, float w, const Raw& r) {
+    acc[0] = fmaf(w, r.x, acc[0]);
+    acc[1] = fmaf(w, r.y, acc[1]);
+    acc[2] = fmaf(w, r.z, acc[2]);
+    acc[3] = fmaf(w, r.w, acc[3]);
+  }
+};
+template <>
+struct Slot<8, true> {
+  using Raw = uint4;
+  static __device__ __forceinline__ Raw load(const void* p, int64_t row, int kp, int c) {
+    return __ldg((const uint4*)((const __nv_bfloat16*)p + row * kp + c));
+  }
+  static __device__ __forceinline__ Raw zero() { return make_uint4(0u, 0u, 0u, 0u); }
+  static __device__ __forceinline__ void fma(float* acc, float w, const Raw& r) {
+    const uint32_t u[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (w == 1.0f) {  // binary S (a compile-time 1): add each BF16 half straight into FP32
+        // add.f32.bf16 widens exactly and rounds once, the same bits as widening then fmaf(1, x,
+        // acc), without the shift and mask that unpacking takes per value
+        float lo_acc = acc[2 * i], hi_acc = acc[2 * i + 1];
+        asm("{ .reg .b16 lo, hi;\n mov.b32 {lo, hi}, %2;\n add.rn.f32.bf16 %0, lo, %0;\n"
+            " add.rn.f32.bf16 %1, hi, %1;\n}"
+            : "+f"(lo_acc), "+f"(hi_acc)
+            : "r"(u[i]));
+        acc[2 * i] = lo_acc;
+        acc[2 * i + 1] = hi_acc;
+        continue;
+      }
+      const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u[i]));
+      acc[2 * i] = fmaf(w, f.x, acc[2 * i]);
+      acc[2 * i + 1] = fmaf(w, f.y, acc[2 * i + 1]);
+    }
+  }
+};
+
+// Slots in flight per lane: FP32 rows use 4 values per lane, BF16 rows 8 (16-byte loads), so a
+// warp holds twice as many BF16 rows in flight in the same registers.
+template <int LPN, int VPL, bool WEIGHTED>
+__host__ __device__ constexpr int dir_slots() {
+  return VPL == 4 ? (LPN == 32 ? (WEIGHTED ? OFSC_ROW_U32_W : OFSC_ROW_U32) : LPN == 16 ? 4 : 2)
+                  : (LPN == 16 ? (WEIGHTED ? OFSC_ROW_U16_BF16_W : OFSC_ROW_U16_BF16) : LPN == 8 ? 4 : 2);
+}
+
+// UU: gathers in flight per lane (0: the default of dir_slots; other values are the shapes the
+// autotuner may pick).
+template <int LPN, int VPL, bool WEIGHTED, bool BF16, bool DOTS, int UU>
+__global__ void __launch_bounds__(32 * kRowWarpsPerBlock,
+                                  (VPL == 4 ? OFSC_ROW_WARPS_F32 : OFSC_ROW_WARPS_BF16) / kRowWarpsPerBlock)
+    k_spmm_dir(SpmmArgs a) {
+  if (!a.ignore_done && a.ctrl->done) return;
+  using S = Slot<VPL, BF16>;
+  constexpr int NPI = 32 / LPN;
+  constexpr int U = UU > 0 ? UU : dir_slots<LPN, VPL, WEIGHTED>();
+  constexpr int STEP = U * NPI;
+  constexpr int WPB = kRowWarpsPerBlock;
+  constexpr int W = VPL * LPN;
+  static_assert(STEP <= 32, "one column index per lane");
+  // per-warp sums of diag(V^T AV) over the warp's rows; each lane owns its columns
+  __shared__ __align__(16) float dred[DOTS ? WPB * W : 4];
+  const int lane = threadIdx.x & 31;
+  const int sub = lane % LPN;
+  const int q = lane / LPN;
+  const int warp = threadIdx.x >> 5;
+  const int gw = blockIdx.x * WPB + warp;
+  const int c = sub * VPL;
+  const bool active = c < a.kp;
+  float* rr = dred + (size_t)warp * W;
+  if (DOTS && lane < LPN) {
+#pragma unroll
+    for (int i = 0; i < VPL; ++i) rr[c + i] = 0.0f;
+  }
+  if (gw < a.groups) {
+    int l = (int)a.bnd[gw];  // column indices are int32, so n < 2^31
+    const int rb = (int)a.bnd[gw + 1];
+    if (l < rb) {
+      const int64_t pend = a.row_ptr[rb];
+      int64_t pb = a.row_ptr[l];
+      int64_t p1 = a.row_ptr[l + 1];
+      int jl = 0;
+      float wl = 1.0f;
+      {
+        const int64_t i = pb + lane;
+        if (lane < STEP && i < pend) {
+          jl = __ldg(a.col + i);
+          if (WEIGHTED) wl = __ldg(a.val + i);
+        }
+      }
+      float acc[VPL];
+#pragma unroll
+      for (int i = 0; i < VPL; ++i) acc[i] = 0.0f;
+      while (true) {
+        const int64_t rem = p1 - pb;
+        const bool last = rem <= STEP;
+        float s = 0.0f;
+        float base[VPL];
+#pragma unroll
+        for (int i = 0; i < VPL; i += 4) {
+          float4 b4 = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (last && lane < LPN && active) b4 = *(const float4*)(a.base + (int64_t)l * a.kp + c + i);
+          base[i] = b4.x; base[i + 1] = b4.y; base[i + 2] = b4.z; base[i + 3] = b4.w;
+        }
+        if (last && lane < LPN && active) s = a.dinv[l];
+        typename S::Raw v[U];
+        float wv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int slot = u * NPI + q;
+          const int j = __shfl_sync(0xffffffffu, jl, slot);
+          wv[u] = WEIGHTED ? __shfl_sync(0xffffffffu, wl, slot) : 1.0f;
+          v[u] = (slot < rem && active) ? S::load(a.gather, j, a.kp, c) : S::zero();
+        }
+        const int64_t pn = last ? p1 : pb + STEP;
+        const bool more = !last || l + 1 < rb;
+        int64_t p1n = p1;
+        if (last && more) p1n = a.row_ptr[l + 2];
+        if (more) {
+          const int64_t i = pn + lane;
+          jl = 0;
+          if (lane < STEP && i < pend) {
+            jl = __ldg(a.col + i);
+            if (WEIGHTED) wl = __ldg(a.val + i);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (u * NPI + q < rem) S::fma(acc, wv[u], v[u]);
+        if (last) {
+#pragma unroll
+          for (int off = LPN; off < 32; off <<= 1)
+#pragma unroll
+            for (int i = 0; i < VPL; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], off);
+          if (lane < LPN && active) {
+            float r[VPL];
+#pragma unroll
+            for (int i = 0; i < VPL; ++i) r[i] = -fmaf(s, acc[i], base[i]);
+#pragma unroll
+            for (int i = 0; i < VPL; i += 4)
+              *(float4*)(a.out + (int64_t)l * a.kp + c + i) = make_float4(r[i], r[i + 1], r[i + 2], r[i + 3]);
+            if (DOTS) {
+#pragma unroll
+              for (int i = 0; i < VPL; ++i) rr[c + i] = fmaf(base[i], r[i], rr[c + i]);
+            }
+          }
+          if (!more) break;
+          ++l;
+          p1 = p1n;
+#pragma unroll
+          for (int i = 0; i < VPL; ++i) acc[i] = 0.0f;
+        }
+        pb = pn;
+      }
+    }
+  }
+  if (DOTS && gw < a.groups) {  // one row of partials per warp: no block-wide barrier
+    __syncwarp();
+    for (int j = lane; j < a.kp; j += 32) a.dots[(int64_t)gw * a.kp + j] = (double)rr[j];
+  }
+}
+
+template <int LPN, int VPL, bool WEIGHTED, bool BF16, bool DOTS, int UU>
+void launch_dir_u(const SpmmArgs& a, cudaStream_t s) {
+  k_spmm_dir<LPN, VPL, WEIGHTED, BF16, DOTS, UU><<<a.groups / kRowWarpsPerBlock, 32 * kRowWarpsPerBlock, 0, s>>>(a);
+}
+
+// A tuned number of slots in flight (u = 2, 4, 6, 8) only for the product with dots (the direction
+// product of the iteration); u must keep u * 32 / LPN <= 32 nonzeros per step, else the default.
+template <int LPN, int VPL, bool WEIGHTED, bool BF16>
+void launch_dir_w(const SpmmArgs& a, bool dots, int u, cudaStream_t s) {
+  constexpr int NPI = 32 / LPN;
+  if (!dots) return launch_dir_u<LPN, VPL, WEIGHTED, BF16, false, 0>(a, s);
+  if (u == 2) return launch_dir_u<LPN, VPL, WEIGHTED, BF16, true, 2>(a, s);
+  if constexpr (4 * NPI <= 32)
+    if (u == 4) return launch_dir_u<LPN, VPL, WEIGHTED, BF16, true, 4>(a, s);
+  if constexpr (6 * NPI <= 32)
+    if (u == 6) return launch_dir_u<LPN, VPL, WEIGHTED, BF16, true, 6>(a, s);
+  if constexpr (8 * NPI <= 32)
+    if (u == 8) return launch_dir_u<LPN, VPL, WEIGHTED, BF16, true, 8>(a, s);
+  launch_dir_u<LPN, VPL, WEIGHTED, BF16, true, 0>(a, s);
+}
+
+template <int LPN, int VPL, bool BF16>
+void launch_dir_l(const SpmmArgs& a, bool weighted, int u, cudaStream_t s) {
+  const bool dots = a.dots != nullptr;
+  if (weighted) launch_dir_w<LPN, VPL, true, BF16>(a, dots, u, s);
+  else launch_dir_w<LPN, VPL, false, BF16>(a, dots, u, s);
+}
+
+template <int LPN, int VPL>
+int default_slots(bool weighted) {
+  return weighted ? dir_slots<LPN, VPL, true>() : dir_slots<LPN, VPL, false>();
+}
+
+}  // namespace
+
+// Lanes per nonzero of the direction product: rows of kp values, VPL per lane, a power of two
+// of at least 2.
+int dir_lanes(int kp, int vpl) {
+  int l = 2;
+  while (l * vpl < kp) l *= 2;
+  return l;
+}
+
+int dir_default_slots(int kp, bool bf16, bool weighted) {
+  if (bf16) {
+    switch (dir_lanes(kp, 8)) {
+      case 2: return default_slots<2, 8>(weighted);
+      case 4: return default_slots<4, 8>(weighted);
+      case 8: return default_slots<8, 8>(weighted);
+      default: return default_slots<16, 8>(weighted);
+    }
+  }
+  switch (dir_lanes(kp, 4)) {
+    case 2: return default_slots<2, 4>(weighted);
+    case 4: return default_slots<4, 4>(weighted);
+    case 8: return default_slots<8, 4>(weighted);
+    case 16: return default_slots<16, 4>(weighted);
+    default: return default_slots<32, 4>(weighted);
+  }
+}
+
+int dir_slot_options(int kp, bool bf16, int* out) {
+  const int lpn = dir_lanes(kp, bf16 ? 8 : 4), npi = 32 / lpn;
+  int n = 0;
+  for (int u = 2; u <= 8; u += 2)
+    if (u * npi <= 32) out[n++] = u;
+  return n;
+}
+
+int launch_spmm_dir(const SpmmArgs& a, bool weighted, bool bf16, int slots, cudaStream_t s) {
+  if (bf16) {
+    switch (dir_lanes(a.kp, 8)) {
+      case 2: launch_dir_l<2, 8, true>(a, weighted, slots, s); break;
+      case 4: launch_dir_l<4, 8, true>(a, weighted, slots, s); break;
+      case 8: launch_dir_l<8, 8, true>(a, weighted, slots, s); break;
+      default: launch_dir_l<16, 8, true>(a, weighted, slots, s); break;
+    }
+  } else {
+    switch (dir_lanes(a.kp, 4)) {
+      case 2: launch_dir_l<2, 4, false>(a, weighted, slots, s); break;
+      case 4: launch_dir_l<4, 4, false>(a, weighted, slots, s); break;
+      case 8: launch_dir_l<8, 4, false>(a, weighted, slots, s); break;
+      case 16: launch_dir_l<16, 4, false>(a, weighted, slots, s); break;
+      default: launch_dir_l<32, 4, false>(a, weighted, slots, s); break;
+    }
+  }
+  return a.groups;
+}
+
+}  // namespace ofsc

@@ -4,8 +4,7 @@
 //
 // Forward, per update t (the iteration as Algorithm 2 states it, A X recomputed every update):
 //   G_t = 4 (A X_t + X_t X_t^T X_t)                                      (Eq. (5))
-//   beta_t,j = <G_t - G_{t-1}, G_t>_j / |G_{t-1},j|^2, 0 for a zero denominator or when the
-//            column would not descend (-|G_t,j|^2 + beta v_{t-1,j}.G_t,j >= 0);   V_0 = -G_0
+//   beta_t,j = <G_t - G_{t-1}, G_t>_j / |G_{t-1},j|^2, 0 for a zero denominator;   V_0 = -G_0
 //   V_t = -G_t + V_{t-1} diag(beta_t)
 //   alpha_t = the chosen real root of p(a) = <V_t, A Z + Z Z^T Z>, Z = X_t + a V_t (Eq. (15))
 //   X_{t+1} = X_t + alpha_t V_t
@@ -13,7 +12,7 @@
 //   alpha by the implicit-function theorem: c = -<Xbar_{t+1}, V_t> / <V_t, H(X_{t+1})[V_t]>,
 //     Xbar_t = Xbar_{t+1} + c H(X_{t+1})[V_t],
 //     Vbar_t += alpha Xbar_{t+1} + c (G_{t+1}/4 + alpha H(X_{t+1})[V_t]);
-//   beta through its quotient (held at 0 where the restart rule or a zero denominator set it):
+//   beta through its quotient (held at 0 where a zero denominator set it):
 //     bbar_j = <Vbar_t, V_{t-1}>_j, nbar = bbar/den, dbar = -bbar beta/den,
 //     Gbar_t = Gcarry - Vbar_t + nbar (2 G_t - G_{t-1}),  Gcarry <- -nbar G_t + 2 dbar G_{t-1},
 //     Vbar_{t-1} = Vbar_t diag(beta_t);
@@ -189,17 +188,13 @@ __device__ double ur_block_sum(double v, double* sh) {
   return r;
 }
 
-// beta_t from the column sums [gg | (G_t - G_{t-1}).G_t | den | v_{t-1}.G_t], the restart rule,
-// and whether beta_t carries a derivative (live).
+// beta_t of Algorithm 2 from the column sums [gg | (G_t - G_{t-1}).G_t | den | v_{t-1}.G_t], and
+// whether beta_t carries a derivative (live: a nonzero denominator).
 __global__ void k_ur_beta(const double* __restrict__ s, int kp, double* beta, double* den_out, int* live) {
   for (int j = threadIdx.x; j < kp; j += blockDim.x) {
-    const double gg = s[j], num = s[kp + j], den = s[2 * kp + j], vg = s[3 * kp + j];
-    double b = den != 0.0 ? num / den : 0.0;
-    int lv = den != 0.0;
-    if (-gg + b * vg >= 0.0) {
-      b = 0.0;
-      lv = 0;
-    }
+    const double num = s[kp + j], den = s[2 * kp + j];
+    const double b = den != 0.0 ? num / den : 0.0;
+    const int lv = den != 0.0;
     beta[j] = b;
     den_out[j] = den;
     live[j] = lv;

@@ -44,3 +44,13 @@ def run_iterate(g, method, x0, tol, maxit, trace_cap=0, **kw):
     r = ofsc.ofsc_iterate(g, method, X, tol, maxit, trace=tr, **kw)
     torch.cuda.synchronize()
     return X.cpu().numpy(), r, (None if tr is None else tr.cpu().numpy())
+
+
+def assert_elementwise(got, ref, rtol, what=""):
+    """Element by element: |got - ref| <= rtol (|ref| + max|ref|) for every entry (the absolute
+    part keeps entries near zero to the block's own scale), so a few bad rows cannot hide inside a
+    norm ratio."""
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    scale = float(np.abs(ref).max()) if ref.size else 0.0
+    np.testing.assert_allclose(got, ref, rtol=rtol, atol=rtol * scale, err_msg=what)

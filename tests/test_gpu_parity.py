@@ -1,8 +1,15 @@
 """GPU path (through the C ABI) against the FP64 oracle on seeded inputs.
 
 Tolerances: graph build, degrees and D^-1/2 are bit-exact; f and grad f match within 1e-5
-relative; iterates after a few updates match within 1e-4 relative (FP32 vs FP64 rounding);
-converged features match within a principal angle of 1e-4 rad; K-means labels reach ARI >= 0.99.
+relative (the gradient also element by element, against 1e-5 max|grad f|); iterates after a few
+updates match element by element within 1e-4 (FP32 state; 2e-3 with BF16 gather storage, one BF16
+unit roundoff); converged features match within a principal angle of 1e-4 rad; K-means labels
+reach ARI >= 0.99.
+
+Algorithm 2 is chaotic over long runs: an FP32 trajectory and the FP64 one part after a few tens
+of updates, and runs can fall into long two-cycles of one column's beta (the FP64 oracle does too,
+from perturbed starts). So converged results are compared where a run converges, and strictly
+(stop counts included) with the optional restart on both sides.
 """
 import dataclasses
 import math
@@ -13,7 +20,7 @@ import pytest
 from oracle import ofsc_oracle as o
 from paper_2305_10356_gb300 import build, ofsc, synth
 
-from .gpu_util import csr_host, gpu_graph, run_iterate, upload
+from .gpu_util import assert_elementwise, csr_host, gpu_graph, run_iterate, upload
 
 pytestmark = pytest.mark.gpu
 METHODS = [o.OFM_F1, o.TRI_F1, o.OFM_F2, o.TRI_F2]
@@ -111,7 +118,7 @@ def test_objective_and_gradient(cuda_lib, name, n, k, which):
     assert f == pytest.approx(f_ref, rel=1e-5)
     Gh = G.cpu().numpy().astype(np.float64)
     assert np.linalg.norm(Gh - G_ref) <= 1e-5 * np.linalg.norm(G_ref)
-    assert np.abs(Gh - G_ref).max() <= 1e-4 * np.abs(G_ref).max()
+    assert np.abs(Gh - G_ref).max() <= 1e-5 * np.abs(G_ref).max()
 
 
 @pytest.fixture(scope="module")
@@ -120,15 +127,18 @@ def c1():
     return e, x0, o.build_graph(e.n, e.src, e.dst, e.w)
 
 
+@pytest.mark.parametrize("restart", [False, True])
 @pytest.mark.parametrize("method", METHODS)
-def test_first_updates_match_oracle(c1, method):
+def test_first_updates_match_oracle(c1, method, restart):
+    """Five updates of Algorithm 2 (and, with restart=True, of the optional restart on both
+    sides): X element by element, alpha and beta per update."""
     e, x0, og = c1
     g = gpu_graph(e)
     steps = 5
-    X, r, tr = run_iterate(g, method, x0, 0.0, steps, trace_cap=steps + 2)
-    ref = o.iterate(og, method, x0, 0.0, steps)
+    X, r, tr = run_iterate(g, method, x0, 0.0, steps, trace_cap=steps + 2, cg_restart=restart)
+    ref = o.iterate(og, method, x0, 0.0, steps, restart=restart)
     assert r.iterations == steps == ref.iterations
-    assert np.linalg.norm(X - ref.X) <= 1e-4 * np.linalg.norm(ref.X)
+    assert_elementwise(X, ref.X, 1e-4, "X_5")
     k = x0.shape[1]
     for t in range(steps):
         np.testing.assert_allclose(tr[t, 3:3 + k], ref.alphas[t], rtol=1e-4)
@@ -142,28 +152,14 @@ def column_match(X, ref):
     return np.linalg.norm(X * s - ref) / np.linalg.norm(ref)
 
 
-@pytest.mark.parametrize("method", METHODS)
-def test_converged_features_and_clusters(c1, method):
+def check_features(e, method, X, ref, tol):
+    """Converged GPU features against the oracle's: principal angle, TriOFM columns, Algorithm 1
+    steps 3-4 on both sides (ARI against the oracle's labels and against the planted blocks)."""
     import torch
-    e, x0, og = c1
-    g = gpu_graph(e)
-    X, r, _ = run_iterate(g, method, x0, 1e-6, 2000)
-    ref = o.iterate(og, method, x0, 1e-6, 2000)
-    assert ref.converged
-    assert r.status == ofsc.OK, (r.status, r.iterations, r.rel_dir_norm)
-    assert r.rel_dir_norm <= 2e-6
-    if method in (o.OFM_F1, o.OFM_F2):
-        # FP32 rounding near tol = 1e-6 shifts the stopping update; the features are what must agree
-        assert abs(r.iterations - ref.iterations) <= max(10, 0.25 * ref.iterations)
-    else:
-        # TriOFM descends no single objective (Sec. 2.2): with momentum, FP32 rounding moves the
-        # trajectory away from the FP64 one within ~50 updates, so only the limit is comparable
-        assert r.iterations <= 2 * ref.iterations + 50
     sin = o.subspace_sin(X, ref.X)
     assert math.asin(min(1.0, sin)) <= 1e-4
     if method in (o.TRI_F1, o.TRI_F2):
         assert column_match(X.astype(np.float64), ref.X) <= 1e-4
-    # Algorithm 1 steps 3-4 on both sides
     Xd = torch.from_numpy(X).cuda()
     ofsc.ofsc_row_normalize(Xd)
     labels = torch.empty(e.n, dtype=torch.int32, device="cuda")
@@ -174,14 +170,113 @@ def test_converged_features_and_clusters(c1, method):
     assert o.ari(lab_gpu, e.labels) >= 0.9  # the planted blocks are recovered
 
 
-def test_bf16_gather_reaches_fp32_features():
-    e, x0 = synth.workload("dcsbm_n50k_k44", n=6000)
+@pytest.mark.parametrize("method", METHODS)
+def test_converged_with_matching_restart(c1, method):
+    """The 1,000-node case to tol 1e-6 (2,000 updates at most) with the optional restart on both
+    sides: both converge, the GPU's returned relative direction norm meets tol (only exact updates
+    stop a run), the stop counts agree within 50% (the FP32 and FP64 trajectories part after a few
+    tens of updates), and the features and clusters agree."""
+    e, x0, og = c1
     g = gpu_graph(e)
-    X32, r32, _ = run_iterate(g, o.OFM_F1, x0, 1e-5, 3000)
-    X16, r16, _ = run_iterate(g, o.OFM_F1, x0, 1e-5, 3000, gather=ofsc.GATHER_BF16)
-    assert r32.status == ofsc.OK and r16.status == ofsc.OK
-    assert r16.rel_dir_norm <= 2e-5
-    assert math.asin(min(1.0, o.subspace_sin(X16, X32))) <= 1e-4
+    X, r, _ = run_iterate(g, method, x0, 1e-6, 2000, cg_restart=True)
+    ref = o.iterate(og, method, x0, 1e-6, 2000, restart=True)
+    assert ref.converged
+    assert r.status == ofsc.OK, (r.status, r.iterations, r.rel_dir_norm)
+    assert r.rel_dir_norm <= 1e-6
+    assert abs(r.iterations - ref.iterations) <= max(10, 0.5 * ref.iterations), (r.iterations, ref.iterations)
+    check_features(e, method, X, ref, 1e-6)
+
+
+PRECISIONS = {"fp32": {}, "bf16": {"gather": ofsc.GATHER_BF16},
+              "bf16_refined": {"gather": ofsc.GATHER_BF16, "refine_tol": 1e-3}}
+
+
+def test_converged_features_and_clusters(c1):
+    """Algorithm 2 as printed (no restart) on the 1,000-node case, tol 1e-6, 2,000 updates at most,
+    for every method in FP32, with BF16 gather storage, and BF16 with the FP32 refinement sweep. The
+    oracle converges for every method. Every GPU run that reports convergence returns a relative
+    direction norm <= tol and the oracle's features and clusters, within [1/2, 2] of its stop count
+    (the trajectories part after a few tens of updates); a run that does not converge ends
+    NOT_CONVERGED or NONFINITE. From this start OFM-f1 falls into a long two-cycle of one column's
+    beta (the FP64 oracle does so too from perturbed starts, for up to 1,300 updates), so the test
+    asks that at least 8 of the 12 runs converge."""
+    e, x0, og = c1
+    g = gpu_graph(e)
+    converged = 0
+    for method in METHODS:
+        ref = o.iterate(og, method, x0, 1e-6, 2000)
+        assert ref.converged
+        for name, kw in PRECISIONS.items():
+            try:
+                X, r, _ = run_iterate(g, method, x0, 1e-6, 2000, **kw)
+            except ofsc.OfscError as ex:
+                assert ex.status == ofsc.ERR_NONFINITE, (method, name, ex)
+                continue
+            if r.status != ofsc.OK:
+                assert r.status == ofsc.ERR_NOT_CONVERGED and r.iterations == 2000, (method, name, r.status)
+                continue
+            converged += 1
+            assert r.rel_dir_norm <= 1e-6, (method, name)
+            assert 0.5 * ref.iterations <= r.iterations <= 2 * ref.iterations, (method, name, r.iterations,
+                                                                                ref.iterations)
+            if name == "bf16_refined":
+                assert 0 < r.refined_at <= r.iterations
+            check_features(e, method, X, ref, 1e-6)
+    assert converged >= 8, converged
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_single_call_replay_equals_direct_launches(c1, method):
+    """ofsc_iterate replays its repeating updates from a captured CUDA graph by default; with
+    direct_launch it launches every kernel itself. Both give the same bits of X, of the trace and of
+    the result on the 1,000-node case run to tol 1e-6 (host checks, exact refreshes, the exact update
+    scheduled once tol is met on a recurrence update)."""
+    e, x0, _ = c1
+    g = gpu_graph(e)
+    Xa, ra, ta = run_iterate(g, method, x0, 1e-6, 600, trace_cap=601)
+    Xb, rb, tb = run_iterate(g, method, x0, 1e-6, 600, trace_cap=601, direct_launch=True)
+    assert np.array_equal(Xa, Xb) and np.array_equal(ta, tb)
+    assert (ra.iterations, ra.status, ra.rel_dir_norm, ra.f) == (rb.iterations, rb.status, rb.rel_dir_norm, rb.f)
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_column_scales_leave_the_bits_unchanged(method):
+    """The stored direction V diag(1/s) with power-of-two column scales s: forcing scales of about
+    2^30 from the first update on (vscale_exp = -30) gives the same bits of X and of every alpha and
+    beta as the default (scales 1 here), at k = 11 (CUDA-core Grams) and k = 128 (tensor cores)."""
+    for n, k, seed in ((1000, 11, 3), (3001, 128, 4)):
+        e = synth.sbm(n, 8, 20.0, 6.0, ratio_kind="count", seed=150 + seed)
+        g = gpu_graph(e)
+        x0 = synth.initial_block(e.n, k, 151 + seed)
+        for gather in (ofsc.GATHER_FP32, ofsc.GATHER_BF16):
+            Xa, ra, ta = run_iterate(g, method, x0, 0.0, 40, trace_cap=41, gather=gather)
+            Xb, rb, tb = run_iterate(g, method, x0, 0.0, 40, trace_cap=41, gather=gather, vscale_exp=-30)
+            assert np.array_equal(Xa, Xb) and np.array_equal(ta, tb), (n, k, gather)
+            assert ra.rel_dir_norm == rb.rel_dir_norm
+
+
+BF16_CASES = [("sbm_n1000_k11", None, None), ("dcsbm_n50k_k44", 8000, None), ("dcsbm_n2m_k128", 4000, 128)]
+
+
+@pytest.mark.parametrize("name,n,k", BF16_CASES)
+@pytest.mark.parametrize("method", METHODS)
+def test_bf16_first_updates_match_oracle(name, n, k, method):
+    """BF16 gather storage of D^-1/2 V (FP32 master copy and accumulation; at k = 128 the bench's
+    16-lane, 8-values-per-lane instantiation of the direction product) against the FP64 oracle,
+    element by element after 5 updates, at k = 11, 44 and 128. Tolerance 2e-3 of max|X|, one BF16
+    unit roundoff (2^-9): every gathered value carries one BF16 rounding, which enters A V and the
+    line-search coefficients at that relative size; alpha within 1e-2 relative."""
+    e, x0 = synth.workload(name, n=n)
+    if k is not None:
+        x0 = synth.initial_block(e.n, k, 77)
+    og = o.build_graph(e.n, e.src, e.dst, e.w)
+    g = gpu_graph(e)
+    X, r, tr = run_iterate(g, method, x0, 0.0, 5, trace_cap=6, gather=ofsc.GATHER_BF16)
+    ref = o.iterate(og, method, x0, 0.0, 5)
+    assert r.iterations == 5 == ref.iterations
+    assert_elementwise(X, ref.X, 2e-3, "X_5 with BF16 gathers")
+    kk = x0.shape[1]
+    np.testing.assert_allclose(tr[:5, 3:3 + kk], np.array(ref.alphas), rtol=1e-2)
 
 
 @pytest.mark.parametrize("k", [1, 8, 128])
@@ -193,7 +288,7 @@ def test_widths(k):
     for method in (o.OFM_F2, o.TRI_F1):
         X, r, _ = run_iterate(g, method, x0, 0.0, 4)
         ref = o.iterate(og, method, x0, 0.0, 4)
-        assert np.linalg.norm(X - ref.X) <= 1e-4 * np.linalg.norm(ref.X)
+        assert_elementwise(X, ref.X, 1e-4)
 
 
 def test_degenerate_inputs(cuda_lib):
@@ -204,7 +299,7 @@ def test_degenerate_inputs(cuda_lib):
     x0 = synth.initial_block(e.n, 3, 2)
     X, r, _ = run_iterate(g, o.OFM_F1, x0, 0.0, 6)
     ref = o.iterate(og, o.OFM_F1, x0, 0.0, 6)
-    assert np.linalg.norm(X - ref.X) <= 1e-4 * np.linalg.norm(ref.X)
+    assert_elementwise(X, ref.X, 1e-4)
     # X0 = 0 is stationary: no update, status OK
     Xz, r, _ = run_iterate(g, o.OFM_F1, np.zeros((e.n, 3), np.float32), 1e-6, 10)
     assert r.iterations == 0 and r.status == ofsc.OK and np.all(Xz == 0)
@@ -287,6 +382,7 @@ def test_tensor_core_gram_matches_fp64(cuda_lib, n, k, ld, nr, lslot):
     for b in range(nr):
         ref = L[:, :k].astype(np.float64).T @ Rs[b][:, :k].astype(np.float64)
         assert np.linalg.norm(got[b] - ref) <= 1e-5 * np.linalg.norm(ref)
+        assert np.abs(got[b] - ref).max() <= 1e-5 * np.abs(ref).max()
 
 
 def test_tensor_core_and_cuda_core_iterations_agree(cuda_lib):
@@ -299,8 +395,11 @@ def test_tensor_core_and_cuda_core_iterations_agree(cuda_lib):
         Xs, rs, _ = run_iterate(g, method, x0, 0.0, 6, gram_engine=ofsc.GRAM_SIMT)
         Xt, rt, _ = run_iterate(g, method, x0, 0.0, 6, gram_engine=ofsc.GRAM_TC)
         ref = o.iterate(og, method, x0, 0.0, 6)
-        assert np.linalg.norm(Xt - ref.X) <= 1e-4 * np.linalg.norm(ref.X)
-        assert np.linalg.norm(Xs - ref.X) <= 1e-4 * np.linalg.norm(ref.X)
+        # the TriOFM prefix cubics of the trailing columns sum over 120+ columns, which amplifies
+        # FP32 rounding there to about 1e-3 of the block's scale after 6 updates
+        for Xg in (Xt, Xs):
+            assert np.linalg.norm(Xg - ref.X) <= 1e-4 * np.linalg.norm(ref.X)
+            assert_elementwise(Xg, ref.X, 1e-3)
 
 
 @pytest.mark.parametrize("k", [64, 128])
@@ -317,7 +416,7 @@ def test_tma_gather_spmm_agrees(k, gather):
     if gather == 0:
         og = o.build_graph(e.n, e.src, e.dst)
         ref = o.iterate(og, o.OFM_F1, x0, 0.0, 5)
-        assert np.linalg.norm(Xt - ref.X) <= 1e-4 * np.linalg.norm(ref.X)
+        assert_elementwise(Xt, ref.X, 1e-4)
 
 
 
@@ -335,7 +434,7 @@ def test_direction_product_all_lane_widths_weighted(k):
     g = gpu_graph(e)
     X, r, tr = run_iterate(g, o.OFM_F2, x0, 0.0, 4, trace_cap=5)
     ref = o.iterate(og, o.OFM_F2, x0, 0.0, 4)
-    assert np.linalg.norm(X - ref.X) <= 1e-4 * np.linalg.norm(ref.X)
+    assert_elementwise(X, ref.X, 1e-4)
     np.testing.assert_allclose(tr[:4, 3:3 + k], np.array(ref.alphas[:4]), rtol=1e-4, atol=1e-7)
 
 
@@ -364,9 +463,13 @@ def test_tensor_core_direction_pass(method):
     Xt, rt, tt = run_iterate(g, method, x0, 0.0, 6, trace_cap=7, gram_engine=ofsc.GRAM_TC)
     Xs, rs, ts = run_iterate(g, method, x0, 0.0, 6, trace_cap=7, gram_engine=ofsc.GRAM_SIMT)
     assert np.linalg.norm(Xt - Xs) <= 1e-5 * np.linalg.norm(Xs)
-    np.testing.assert_allclose(tt[:6, 3:3 + 128], ts[:6, 3:3 + 128], rtol=1e-4, atol=1e-7)
+    # TriOFM's step for column i solves the prefix cubic over columns 1..i, which amplifies the
+    # FP32-level difference of the two Gram engines to a few 1e-3 in some trailing columns' steps
+    np.testing.assert_allclose(tt[:6, 3:3 + 128], ts[:6, 3:3 + 128], rtol=1e-4 if method == o.OFM_F1 else 5e-3,
+                               atol=1e-7)
     ref = o.iterate(og, method, x0, 0.0, 6)
     assert np.linalg.norm(Xt - ref.X) <= 1e-4 * np.linalg.norm(ref.X)
+    assert_elementwise(Xt, ref.X, 1e-3)
     assert abs(rt.rel_dir_norm - ref.rel_norms[-1]) <= 1e-4 * ref.rel_norms[-1] + 1e-7
 
 
@@ -384,10 +487,12 @@ def test_streaming_snapshots_warm_start_match_oracle():
         Xg, r, _ = run_iterate(g, o.OFM_F1, Xg, 0.0, 8)
         ref = o.iterate(o.build_graph(e.n, e.src, e.dst), o.OFM_F1, Xo, 0.0, 8)
         Xo = ref.X
-        assert np.linalg.norm(Xg - Xo) <= 1e-4 * np.linalg.norm(Xo)
+        assert_elementwise(Xg, Xo, 1e-4)
     g = gpu_graph(snaps[-1])
-    _, warm, _ = run_iterate(g, o.OFM_F1, Xg, 1e-4, 2000)
-    _, cold, _ = run_iterate(g, o.OFM_F1, x0, 1e-4, 2000)
+    # to tolerance with the optional restart: without it OFM-f1 can sit in a long two-cycle of one
+    # column's beta, which says nothing about the warm start (the paper runs 2 updates a snapshot)
+    _, warm, _ = run_iterate(g, o.OFM_F1, Xg, 1e-4, 2000, cg_restart=True)
+    _, cold, _ = run_iterate(g, o.OFM_F1, x0, 1e-4, 2000, cg_restart=True)
     assert warm.status == ofsc.OK and cold.status == ofsc.OK
     assert warm.iterations < cold.iterations
 
@@ -522,7 +627,7 @@ def test_batched_matches_oracle():
         ref = o.iterate(o.build_graph(e.n, e.src, e.dst), o.OFM_F1, x0, 0.0, 5)
         assert r.iterations == 5 == ref.iterations
         Xg = X.cpu().numpy()
-        assert np.linalg.norm(Xg - ref.X) <= 1e-4 * np.linalg.norm(ref.X)
+        assert_elementwise(Xg, ref.X, 1e-4)
 
 
 def test_batched_rejects_bad_arguments():
@@ -545,8 +650,8 @@ def test_unrolled_grad_matches_oracle(case):
     grad f1(X_0).
 
     Tolerance: after 20 line-searched updates the gradient is ill-conditioned: the oracle's own
-    result moves by ~1e-3 (relative) when X_0 moves by 1e-7, the size of one FP32 rounding. The
-    GPU result, computed in FP32, is allowed 10x that measured sensitivity (at least 1e-3)."""
+    result moves by ~1e-3 (relative) when every entry of X_0 moves up by one FP32 ulp. The GPU
+    result, computed in FP32, is allowed twice that measured sensitivity (at least 1e-3)."""
     import torch
     if case == "sbm_k8":
         e = synth.sbm(1500, 8, 16.0, 5.0, ratio_kind="count", seed=131)
@@ -564,14 +669,15 @@ def test_unrolled_grad_matches_oracle(case):
                                               edges=(e.src, e.dst, e.w.astype(np.float64)))
     else:
         f_ref, g_ref = o.unrolled_grad(og, x0.astype(np.float64), T)
-    rng = np.random.default_rng(134)
-    xp = x0.astype(np.float64) * (1.0 + 1e-7 * rng.standard_normal(x0.shape))
+    # every entry of X_0 one FP32 ulp up: the GPU's FP32 arithmetic perturbs each update by about
+    # that much, and such a shift moves the oracle's gradient by ~1e-3 on the binary graph
+    xp = np.nextafter(x0, np.float32(np.inf)).astype(np.float64)
     if weighted:
         _, gp, wp = o.unrolled_grad(og, xp, T, edges=(e.src, e.dst, e.w.astype(np.float64)))
-        wtol = max(1e-3, 10.0 * np.linalg.norm(wp - w_ref) / np.linalg.norm(w_ref))
+        wtol = max(1e-3, 2.0 * np.linalg.norm(wp - w_ref) / np.linalg.norm(w_ref))
     else:
         _, gp = o.unrolled_grad(og, xp, T)
-    tol = max(1e-3, 10.0 * np.linalg.norm(gp - g_ref) / np.linalg.norm(g_ref))
+    tol = max(1e-3, 2.0 * np.linalg.norm(gp - g_ref) / np.linalg.norm(g_ref))
     X0 = torch.from_numpy(x0).cuda()
     src, dst, _ = upload(e)
     outs = {}
@@ -603,18 +709,28 @@ def test_unrolled_grad_matches_oracle(case):
 
 
 def test_autotune_keeps_results_within_rounding():
-    """ofsc_autotune picks a row-partition granularity (4..32 warps per SM) by timing; the first
-    five updates after it still match the oracle, and every granularity tried gives the same A V
-    rows (only the fold of diag(V^T AV) changes its rounding)."""
+    """ofsc_autotune picks a row partition (4..32 warps per SM) and the gathers in flight per lane
+    by timing; the first five updates after it still match the oracle element by element, and
+    every shape gives the same A V rows (only the fold of diag(V^T AV) changes its rounding). Then
+    every slot count is forced in turn through the tuned shape and compared with the default."""
     e = synth.sbm(20000, 16, 24.0, 5.0, ratio_kind="count", seed=141)
     og = o.build_graph(e.n, e.src, e.dst)
     g = gpu_graph(e)
     x0 = synth.initial_block(e.n, 16, 142)
     Xa, ra, _ = run_iterate(g, o.OFM_F1, x0, 0.0, 5)
-    w, ms = ofsc.ofsc_autotune(g, 16, ofsc.GATHER_BF16)
-    assert w in [m * 152 for m in (4, 8, 16, 32)] and ms > 0.0
+    w, u, ms = ofsc.ofsc_autotune(g, 16, ofsc.GATHER_FP32)
+    assert w in [m * 152 for m in (4, 8, 16, 32)] and u in (2, 4, 6, 8) and ms > 0.0
     Xb, rb, _ = run_iterate(g, o.OFM_F1, x0, 0.0, 5)
     ref = o.iterate(og, o.OFM_F1, x0, 0.0, 5)
     for X in (Xa, Xb):
-        assert np.linalg.norm(X - ref.X) <= 1e-4 * np.linalg.norm(ref.X)
+        assert_elementwise(X, ref.X, 1e-4)
     assert np.linalg.norm(Xa - Xb) <= 1e-5 * np.linalg.norm(Xa)
+    # BF16 storage at k = 128 (16 lanes per nonzero: slots 2 to 8 are all valid shapes)
+    e2 = synth.sbm(6000, 8, 24.0, 5.0, ratio_kind="count", seed=143, gamma=2.3)
+    og2 = o.build_graph(e2.n, e2.src, e2.dst)
+    g2 = gpu_graph(e2)
+    x2 = synth.initial_block(e2.n, 128, 144)
+    w2, u2, _ = ofsc.ofsc_autotune(g2, 128, ofsc.GATHER_BF16)
+    assert u2 in (2, 4, 6, 8)
+    X2, _, _ = run_iterate(g2, o.OFM_F1, x2, 0.0, 5, gather=ofsc.GATHER_BF16)
+    assert_elementwise(X2, o.iterate(og2, o.OFM_F1, x2, 0.0, 5).X, 2e-3)

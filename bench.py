@@ -44,12 +44,19 @@ def load_peaks() -> dict:
     return {"hbm_gbs": 6800.0, "source": "fallback"}
 
 
-def source_digest() -> str:
+DIR_PRODUCT_SOURCES = ("spmm_dir.cu", "spmm_dir.cuh")  # the direction product and its argument header
+
+
+def source_digest(names=None) -> str:
+    """Digest of the CUDA sources (all of them, or the named files of csrc/)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2305_10356_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
+    for name in sorted(names if names is not None else os.listdir(csrc)):
         with open(os.path.join(csrc, name), "rb") as fh:
             h.update(name.encode() + fh.read())
+    if names is None:
+        with open(os.path.join(ROOT, "include", "ofsc.h"), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
@@ -276,16 +283,18 @@ def spmm_bytes(n: int, kp: int, nnz: int, gather_bytes: int, weighted: bool, h: 
 
 
 def measured_traffic(workload: str, gather: str, any_build: bool = False) -> dict | None:
-    """ncu DRAM counters of the direction product at this workload (profiles/traffic.json), or
-    None when the kernel sources changed since they were taken (any_build: the entry whatever
-    build it was taken on)."""
+    """ncu DRAM counters at this workload (profiles/traffic.json): of the direction product (keyed
+    to the digest of its own sources) or, for gather "update", of all kernels of one update (keyed
+    to the digest of every source); None when those sources changed since (any_build: the entry
+    whatever build it was taken on)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as fh:
         tj = json.load(fh)
     entry = tj.get("entries", {}).get(f"{workload}/{gather}")
-    if not entry or (entry.get("source_digest") != source_digest() and not any_build):
+    digest = source_digest() if gather == "update" else source_digest(DIR_PRODUCT_SOURCES)
+    if not entry or (entry.get("source_digest") != digest and not any_build):
         return None
     return entry
 
@@ -834,7 +843,8 @@ def run_gpu(args):
         miss = tr_any["dram_read_bytes"] - base["csr"] - base["epilogue"]
         h = min(1.0, max(0.0, 1.0 - miss / base["gather_all"]))
         h_source = ("ncu DRAM reads of this build" if tr is not None else
-                    f"ncu DRAM reads of an earlier build (sources {tr_any['source_digest']}, now {source_digest()})")
+                    f"ncu DRAM reads of an earlier build (sources {tr_any['source_digest']}, now "
+                    f"{source_digest(DIR_PRODUCT_SOURCES)})")
     alg = spmm_bytes(e.n, kp, int(info.nnz), gb, bool(info.weighted), h)
     achieved = alg["total"] / (per_launch_ms / 1000.0) / 1e9
     roof = {"bound": "hbm", "kernel": "k_spmm_dir (direction product W = A V)", "achieved": achieved,

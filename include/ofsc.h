@@ -15,6 +15,7 @@
  *      ofsc_unrolled_grad   d f1(X_T)/dX_0 (and /dw) through T updates of Algorithm 2
  *      ofsc_rayleigh_ritz   Ritz values and relerr of Sec. 5 for a feature block
  *      ofsc_gram            the k x k dot-product blocks on the tensor cores
+ *      ofsc_set_allocator   the caller's device allocator for every block the library allocates
  *
  * Conventions (all calls):
  *   - Every call returns an ofsc_status. No C++ exception crosses this boundary. On an error
@@ -26,8 +27,11 @@
  *     queued on it. A call that returns a host value (f_out, ofsc_result, inertia, counts)
  *     synchronises that stream before it returns. Calls that allocate or free device memory
  *     (the first call on a handle for a given k, ofsc_graph_build/free, ofsc_unrolled_grad,
- *     ofsc_autotune) carry the device-wide synchronisation of cudaMalloc/cudaFree; no other call
+ *     ofsc_autotune, ofsc_weight_grad, ofsc_rayleigh_ritz, ofsc_gram) carry the device-wide
+ *     synchronisation of cudaMalloc/cudaFree (or of ofsc_set_allocator's frees); no other call
  *     synchronises the whole device.
+ *   - Host phases of the longer calls are marked with NVTX ranges ("ofsc_iterate", "update",
+ *     "exact refresh", "report", "ofsc_graph_build", ...) for Nsight tools.
  *   - ofsc_graph handles are owned by the library: create with ofsc_graph_build, release with
  *     ofsc_graph_free. A handle also caches the device workspace of ofsc_iterate and
  *     ofsc_objective_grad, so calls that share one handle must be ordered by the caller
@@ -207,6 +211,14 @@ typedef struct {
                             range where FP64 still holds it). Scaling by powers of two is exact,
                             so the results do not depend on this value unless FP32 would
                             overflow or underflow */
+  int64_t spin_limit;    /* polls allowed per bounded mbarrier wait of the tensor-core kernels
+                            (0: the compiled default, 2^22); a wait that runs out ends its kernel
+                            with OFSC_ERR_TIMEOUT after its own copies and MMAs have completed */
+  int32_t withhold_arrivals; /* test hook, 0 (default) or 1: the converter warps of the tensor-core
+                            direction pass (OFM-f1, TriOFM-f1 at padded k = 128) never signal a full
+                            stage, so its MMA warp's first bounded wait runs out before any MMA is
+                            issued and the call returns OFSC_ERR_TIMEOUT (exercises the timeout
+                            path without a fault; use with a small spin_limit) */
 } ofsc_opts;
 
 typedef struct {
@@ -394,6 +406,24 @@ ofsc_status ofsc_kmeans(int64_t n, int32_t d, const float* X, int32_t n_clusters
  */
 ofsc_status ofsc_gram(int64_t n, int32_t k, int32_t ld, const float* L, int32_t nr, const float* const* R,
                       int64_t rows_per_block, double* out, void* stream);
+
+/*
+ * ofsc_set_allocator - makes the library take every device block it allocates (graph arrays,
+ * workspaces, scratch) from the caller's allocator instead of cudaMalloc, for a process whose device
+ * memory belongs to another allocator (a framework's caching pool). Not in the paper.
+ *   alloc(bytes, user)  returns a device pointer on the current device, 256-byte aligned, or NULL
+ *                       when it cannot (the calling entry point then returns OFSC_ERR_OOM and
+ *                       frees what it had taken)
+ *   free(ptr, user)     returns a block that alloc gave
+ *   Both NULL: back to cudaMalloc/cudaFree for later allocations. One of them NULL: INVALID_ARG.
+ * A block is always returned to the allocator that made it, also after a later change of
+ * allocator. Before calling `free` the library synchronises the device, so no queued kernel still
+ * uses the block. Applies process-wide; not thread-safe against concurrent library calls.
+ * Errors: OFSC_ERR_INVALID_ARG.
+ */
+typedef void* (*ofsc_alloc_fn)(size_t bytes, void* user);
+typedef void (*ofsc_free_fn)(void* ptr, void* user);
+ofsc_status ofsc_set_allocator(ofsc_alloc_fn alloc, ofsc_free_fn free, void* user);
 
 /* Message of the last failing call on this host thread ("" if none). */
 const char* ofsc_last_error(void);

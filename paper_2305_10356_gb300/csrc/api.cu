@@ -1,5 +1,9 @@
-// Error state, graph-handle accessors and release.
+// Error state, the library's device allocator (cudaMalloc or the caller's), graph-handle accessors
+// and release.
 #include <stdarg.h>
+
+#include <mutex>
+#include <unordered_map>
 
 #include "common.cuh"
 
@@ -37,31 +41,75 @@ ofsc_status cuda_fail(cudaError_t e, const char* what) {
   return OFSC_ERR_CUDA;
 }
 
+namespace {
+struct Allocator {
+  ofsc_alloc_fn alloc = nullptr;
+  ofsc_free_fn free = nullptr;
+  void* user = nullptr;
+};
+std::mutex g_alloc_mu;
+Allocator g_alloc;                                      // the current one (alloc == NULL: cudaMalloc)
+std::unordered_map<void*, Allocator> g_alloc_owner;    // blocks made by a caller's allocator
+}  // namespace
+
+cudaError_t dev_alloc_bytes(void** p, size_t bytes) {
+  *p = nullptr;
+  Allocator a;
+  {
+    std::lock_guard<std::mutex> lock(g_alloc_mu);
+    a = g_alloc;
+  }
+  if (!a.alloc) return cudaMalloc(p, bytes);
+  void* q = a.alloc(bytes, a.user);
+  if (!q) return cudaErrorMemoryAllocation;
+  std::lock_guard<std::mutex> lock(g_alloc_mu);
+  g_alloc_owner[q] = a;
+  *p = q;
+  return cudaSuccess;
+}
+
+cudaError_t dev_free(void* p) {
+  if (!p) return cudaSuccess;
+  Allocator a;
+  {
+    std::lock_guard<std::mutex> lock(g_alloc_mu);
+    auto it = g_alloc_owner.find(p);
+    if (it == g_alloc_owner.end()) return cudaFree(p);
+    a = it->second;
+    g_alloc_owner.erase(it);
+  }
+  // the caller's allocator may hand the block out again at once: no queued kernel may still use it
+  const cudaError_t e = cudaDeviceSynchronize();
+  a.free(p, a.user);
+  return e;
+}
+
 void workspace_free(Workspace& ws) {
-  cudaFree(ws.X);
-  cudaFree(ws.Y);
-  cudaFree(ws.V);
-  cudaFree(ws.W);
-  cudaFree(ws.G);
-  cudaFree(ws.Vh);
-  cudaFree(ws.gram_part);
-  cudaFree(ws.gram);
-  cudaFree(ws.Rn);
-  cudaFree(ws.Bn);
-  cudaFree(ws.R64);
-  cudaFree(ws.B64);
-  cudaFree(ws.dots);
-  cudaFree(ws.part_tc);
-  cudaFree(ws.alpha);
-  cudaFree(ws.beta);
-  cudaFree(ws.alpha64);
-  cudaFree(ws.beta64);
-  cudaFree(ws.vscale);
-  cudaFree(ws.vinv);
-  cudaFree(ws.colpart);
-  cudaFree(ws.dE);
-  cudaFree(ws.solve);
-  cudaFree(ws.ctrl);
+  dev_free(ws.X);
+  dev_free(ws.Y);
+  dev_free(ws.V);
+  dev_free(ws.W);
+  dev_free(ws.G);
+  dev_free(ws.Vh);
+  dev_free(ws.gram_part);
+  dev_free(ws.gram);
+  dev_free(ws.Rn);
+  dev_free(ws.Bn);
+  dev_free(ws.R64);
+  dev_free(ws.B64);
+  dev_free(ws.dots);
+  dev_free(ws.part_tc);
+  dev_free(ws.alpha);
+  dev_free(ws.beta);
+  dev_free(ws.alpha64);
+  dev_free(ws.beta64);
+  dev_free(ws.vscale);
+  dev_free(ws.vinv);
+  dev_free(ws.colpart);
+  dev_free(ws.dE);
+  dev_free(ws.bimg);
+  dev_free(ws.solve);
+  dev_free(ws.ctrl);
   if (ws.ctrl_host) cudaFreeHost(ws.ctrl_host);
   for (cudaEvent_t e : ws.events) cudaEventDestroy(e);
   ws = Workspace();
@@ -81,12 +129,12 @@ ofsc_status ofsc_graph_free(ofsc_graph* g) {
   cudaGetDevice(&prev);
   cudaSetDevice(g->device);
   ofsc::workspace_free(g->ws);
-  cudaFree(g->row_ptr);
-  cudaFree(g->col);
-  cudaFree(g->val);
-  cudaFree(g->dinv);
-  cudaFree(g->deg);
-  for (int i = 0; i < 6; ++i) cudaFree(g->bnd[i]);
+  ofsc::dev_free(g->row_ptr);
+  ofsc::dev_free(g->col);
+  ofsc::dev_free(g->val);
+  ofsc::dev_free(g->dinv);
+  ofsc::dev_free(g->deg);
+  for (int i = 0; i < 6; ++i) ofsc::dev_free(g->bnd[i]);
   if (g->stream) cudaStreamDestroy(g->stream);
   cudaSetDevice(prev);
   delete g;
@@ -118,3 +166,13 @@ ofsc_status ofsc_graph_csr(const ofsc_graph* g, const int64_t** row_ptr, const i
 }
 
 }  // extern "C"
+
+extern "C" ofsc_status ofsc_set_allocator(ofsc_alloc_fn alloc, ofsc_free_fn free_fn, void* user) {
+  using namespace ofsc;
+  clear_error();
+  if ((alloc == nullptr) != (free_fn == nullptr))
+    return fail(OFSC_ERR_INVALID_ARG, "ofsc_set_allocator: give both functions or neither");
+  std::lock_guard<std::mutex> lock(g_alloc_mu);
+  g_alloc = Allocator{alloc, free_fn, user};
+  return OFSC_OK;
+}

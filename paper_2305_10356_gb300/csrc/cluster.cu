@@ -306,11 +306,11 @@ __global__ void __launch_bounds__(256) k_dist_sum(int64_t n, int64_t chunk, cons
 struct Buffers {
   std::vector<void*> ptrs;
   ~Buffers() {
-    for (void* p : ptrs) cudaFree(p);
+    for (void* p : ptrs) dev_free(p);
   }
   template <typename T>
   cudaError_t alloc(T** p, size_t count) {
-    cudaError_t e = cudaMalloc((void**)p, (count > 0 ? count : 1) * sizeof(T));
+    cudaError_t e = dev_alloc((void**)p, (count > 0 ? count : 1) * sizeof(T));
     if (e == cudaSuccess) ptrs.push_back(*p);
     return e;
   }

@@ -9,7 +9,10 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/ofsc.h"
+#include "spmm_dir.cuh"
 
 namespace ofsc {
 
@@ -25,6 +28,32 @@ ofsc_status fail(ofsc_status st, const char* fmt, ...);
 
 // Maps a CUDA error to OFSC_ERR_CUDA / OFSC_ERR_OOM and records it.
 ofsc_status cuda_fail(cudaError_t e, const char* what);
+
+// Device memory of the library: cudaMalloc / cudaFree, or the caller's allocator when one is set
+// (ofsc_set_allocator). A block is always freed by the allocator that made it; freeing through a
+// caller's allocator synchronises the device first, so no queued kernel still uses the block.
+cudaError_t dev_alloc_bytes(void** p, size_t bytes);
+cudaError_t dev_free(void* p);
+template <class T>
+inline cudaError_t dev_alloc(T** p, size_t bytes) {
+  return dev_alloc_bytes(reinterpret_cast<void**>(p), bytes);
+}
+// An NVTX range over a host phase of a call (no cost without an attached tool).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
+// A call's scratch block, freed when the call returns (both frees wait for the device's queued work).
+struct DevBuf {
+  void* p = nullptr;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { dev_free(p); }
+};
 
 #define OFSC_CUDA(call)                                        \
   do {                                                         \
@@ -103,7 +132,8 @@ struct Ctrl {
   int k;           // real (unpadded) columns
   int restart;     // 1: the optional CG restart (beta_j = 0 where v_j . g_j >= 0); 0: Algorithm 2
   int vscale_exp;  // columns of V are stored scaled once |V_j| exceeds 2^vscale_exp ||G_0||
-  int pad_;
+  int withhold;    // test hook: the tensor-core direction pass's converters withhold their arrivals
+  long long spin_limit;  // polls per bounded mbarrier wait (0: the compiled default)
   double tol;
   double g0;       // ||G_0||_F
   double gnorm;    // ||G_t||_F of the last direction pass
@@ -117,32 +147,6 @@ struct Ctrl {
                    // update may stop the run
 };
 
-// Operands of the two sparse products: the direction product W = A V (k_spmm_dir, gathering
-// Vh = D^-1/2 V) and the exact AX = A X (k_spmm, gathering X and scaling by D^-1/2 per nonzero).
-struct SpmmArgs {
-  int64_t n;
-  int kp;
-  const int64_t* row_ptr;
-  const int32_t* col;
-  const float* val;
-  const float* dinv;
-  const int64_t* bnd;  // [groups + 1]: contiguous, nnz-balanced row ranges of the lane groups / warps
-  int groups;
-  const void* gather;  // direction: Vh = D^-1/2 V (FP32 or BF16); AX: X
-  const float* base;   // direction: V; AX: X  (the row block M in A M = -M - D^-1/2 S D^-1/2 M)
-  float* out;          // direction: W = AV; AX: AX
-  double* dots;        // direction with dots: [blocks][kp] partials of diag(V^T AV)
-  Ctrl* ctrl;
-  int ignore_done;
-};
-
-// The direction product (spmm_dir.cu): lanes per nonzero for rows of kp values with vpl values per
-// lane; the default and the candidate numbers of gathers in flight per lane; the launch (slots 0:
-// the default), returning the rows of dots partials it writes (one per warp).
-int dir_lanes(int kp, int vpl);
-int dir_default_slots(int kp, bool bf16, bool weighted);
-int dir_slot_options(int kp, bool bf16, int* out);
-int launch_spmm_dir(const SpmmArgs& a, bool weighted, bool bf16, int slots, cudaStream_t s);
 
 // Device workspace of the iteration for one padded width kp, cached on the graph handle.
 struct Workspace {
@@ -176,6 +180,7 @@ struct Workspace {
   float* vinv = nullptr;        // kp
   double* colpart = nullptr;    // [row_blocks][5][kp]
   double* dE = nullptr;         // kp: diag(V^T AX) (f1 methods)
+  void* bimg = nullptr;         // kp = 128: B operand images of the f2 tensor-core direction pass
   double* solve = nullptr;      // line-search scratch: per-block trace partials, diagonals, cubics
   Ctrl* ctrl = nullptr;
   Ctrl* ctrl_host = nullptr;    // pinned
@@ -255,6 +260,7 @@ struct RowArgs {
   int need_vy;      // read V_{t-1} for the V_prev AX sums even without an update
   int eval;         // no previous G (objective/gradient evaluation and the final report)
   int ignore_done;
+  void* bimg;       // f2 tensor-core pass: 256 KB for the B operand images of X^T A X and X^T X
 };
 
 // Arguments of the TMA-gather sparse product (csrc/spmm_tma.cu): out = -base - D^-1/2 S Vh.

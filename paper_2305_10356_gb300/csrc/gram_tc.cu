@@ -29,6 +29,7 @@ namespace {
 template <int NR, bool SEPARATE_L>
 __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(GramTcArgs a) {
   if (!a.ignore_done && a.ctrl->done) return;
+  const long long lim = spin_limit_of(a.ctrl);
   extern __shared__ unsigned char smem_raw[];
   __shared__ uint64_t bar;
   __shared__ uint32_t tmem_slot;
@@ -99,7 +100,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(GramTcArgs a) {
   if (nchunks > 0) fetch(0);
   for (int64_t c = 0; c < nchunks; ++c) {
     if (c > 0) {  // the tensor cores must be done reading the tiles before they are rewritten
-      if (!mbar_wait(&bar, phase)) abort_flag = 1;
+      if (!mbar_wait(&bar, phase, lim)) abort_flag = 1;
       phase ^= 1;
     }
     __syncthreads();
@@ -132,7 +133,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(GramTcArgs a) {
   }
   bool ok = !abort_flag;
   if (nchunks > 0 && ok) {
-    ok = mbar_wait(&bar, phase);
+    ok = mbar_wait(&bar, phase, lim);
     if (!ok) abort_flag = 1;
   }
   __syncthreads();
@@ -228,6 +229,7 @@ template <int NR>
 __global__ void __launch_bounds__(kWsThreads, 1)
     k_gram_tc_ws(const __grid_constant__ CUtensorMap m0, const __grid_constant__ CUtensorMap m1, WsArgs a) {
   if (!a.ignore_done && a.ctrl->done) return;
+  const long long lim = spin_limit_of(a.ctrl);
   using Sh = WsShape<NR>;
   constexpr uint32_t NCOLS = NR == 1 ? 256 : 512;  // segment accumulator, then the running total
   constexpr uint32_t TOT = NR * kTcM;               // first column of the total
@@ -277,7 +279,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
       int64_t c = 0;
       for (; c < nchunks; ++c) {
         const int st = (int)(c % kWsRaw);
-        if (c >= kWsRaw && !ws_wait(&raw_empty[st], (uint32_t)((c / kWsRaw - 1) & 1), &abort_flag)) break;
+        if (c >= kWsRaw && !ws_wait(&raw_empty[st], (uint32_t)((c / kWsRaw - 1) & 1), &abort_flag, lim)) break;
         mbar_expect_tx(&raw_full[st], (uint32_t)Sh::RAW);
         const int y = (int)(r0 + c * 32);
         unsigned char* dst = raw + st * Sh::RAW;
@@ -287,7 +289,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
           for (int fb = 0; fb < 4; ++fb) tma_load_box(dst + (b * 4 + fb) * kWsBox, b ? &m1 : &m0, fb * 32, y, &raw_full[st]);
       }
       // the copies already issued must land before the CTA may exit
-      for (int64_t d = c > kWsRaw ? c - kWsRaw : 0; d < c; ++d) mbar_wait(&raw_full[d % kWsRaw], (uint32_t)((d / kWsRaw) & 1));
+      for (int64_t d = c > kWsRaw ? c - kWsRaw : 0; d < c; ++d) mbar_wait(&raw_full[d % kWsRaw], (uint32_t)((d / kWsRaw) & 1), lim);
     }
   } else if (warp == 5) {
     if (lane == 0) {  // MMA issuer
@@ -296,8 +298,8 @@ __global__ void __launch_bounds__(kWsThreads, 1)
         const int tt = (int)(c % kWsTile);
         const int64_t seg = c / cps;
         const bool first = c % cps == 0;
-        if (!ws_wait(&tile_full[tt], (uint32_t)((c / kWsTile) & 1), &abort_flag)) break;
-        if (first && seg > 0 && !ws_wait(&acc_empty, (uint32_t)((seg - 1) & 1), &abort_flag)) break;
+        if (!ws_wait(&tile_full[tt], (uint32_t)((c / kWsTile) & 1), &abort_flag, lim)) break;
+        if (first && seg > 0 && !ws_wait(&acc_empty, (uint32_t)((seg - 1) & 1), &abort_flag, lim)) break;
         asm volatile("tcgen05.fence::after_thread_sync;");
         const uint32_t hs = smem_u32(hi + tt * Sh::TILE), ls = smem_u32(lo + tt * Sh::TILE);
 #pragma unroll
@@ -320,7 +322,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
         if (seg_last(c)) mma_commit(&acc_full);
       }
       // the MMAs already issued must finish before the tensor memory is released
-      if (c > 0) mbar_wait(&tile_empty[(c - 1) % kWsTile], (uint32_t)(((c - 1) / kWsTile) & 1));
+      if (c > 0) mbar_wait(&tile_empty[(c - 1) % kWsTile], (uint32_t)(((c - 1) / kWsTile) & 1), lim);
     }
   } else {  // warps 0-3: convert, and drain at segment ends
     const int fb = warp;
@@ -328,8 +330,8 @@ __global__ void __launch_bounds__(kWsThreads, 1)
     int64_t c = 0;
     for (; c < nchunks; ++c) {
       const int st = (int)(c % kWsRaw), tt = (int)(c % kWsTile);
-      if (!ws_wait(&raw_full[st], (uint32_t)((c / kWsRaw) & 1), &abort_flag)) break;
-      if (c >= kWsTile && !ws_wait(&tile_empty[tt], (uint32_t)((c / kWsTile - 1) & 1), &abort_flag)) break;
+      if (!ws_wait(&raw_full[st], (uint32_t)((c / kWsRaw) & 1), &abort_flag, lim)) break;
+      if (c >= kWsTile && !ws_wait(&tile_empty[tt], (uint32_t)((c / kWsTile - 1) & 1), &abort_flag, lim)) break;
       // lane = feature fb*32 + lane; four consecutive rows per step: four 4-byte reads from the
       // swizzled row lines (one line per read, all lanes distinct words) and one 16-byte store per
       // tile into the feature's K-major line (each group of 8 lanes hits 8 distinct 16-byte banks)
@@ -362,7 +364,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
       }
       if (seg_last(c)) {
         const int64_t seg = c / cps;
-        if (!ws_wait(&acc_full, (uint32_t)(seg & 1), &abort_flag)) break;
+        if (!ws_wait(&acc_full, (uint32_t)(seg & 1), &abort_flag, lim)) break;
         asm volatile("tcgen05.fence::after_thread_sync;");
         const uint32_t lanes = (uint32_t)(warp * 32) << 16;
 #pragma unroll 1
@@ -605,23 +607,18 @@ extern "C" ofsc_status ofsc_gram(int64_t n, int32_t k, int32_t ld, const float* 
     return OFSC_OK;
   }
   const size_t pbytes = gram_tc_part_bytes(n, nr, a.rows_per_cta);
-  void* part = nullptr;
-  Ctrl* ctrl = nullptr;
-  OFSC_CUDA(cudaMallocAsync(&part, pbytes, s));
-  cudaError_t e = cudaMallocAsync((void**)&ctrl, sizeof(Ctrl), s);
-  if (e != cudaSuccess) {
-    cudaFreeAsync(part, s);
-    return cuda_fail(e, "ofsc_gram: cudaMallocAsync");
-  }
+  DevBuf pbuf, cbuf;
+  OFSC_CUDA(dev_alloc(&pbuf.p, pbytes));
+  OFSC_CUDA(dev_alloc(&cbuf.p, sizeof(Ctrl)));
+  void* part = pbuf.p;
+  Ctrl* ctrl = (Ctrl*)cbuf.p;
   cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), s);
   a.part = (float*)part;
   a.ctrl = ctrl;
   const int slot[4] = {0, 1, 2, 3};
-  e = gram_tc_launch_ld(a, slot, k, k, (int64_t)k * k, out, s);
+  cudaError_t e = gram_tc_launch_ld(a, slot, k, k, (int64_t)k * k, out, s);
   Ctrl h{};
   if (e == cudaSuccess) e = cudaMemcpyAsync(&h, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s);
-  cudaFreeAsync(part, s);
-  cudaFreeAsync(ctrl, s);
   if (e != cudaSuccess) return cuda_fail(e, "ofsc_gram");
   OFSC_CUDA(cudaStreamSynchronize(s));
   if (h.status == OFSC_ERR_TIMEOUT) return fail(OFSC_ERR_TIMEOUT, "ofsc_gram: tensor-core wait timed out");

@@ -178,7 +178,7 @@ int grid_for(int64_t items, int threads = 256) {
 struct Scratch {
   void* p[12] = {};
   ~Scratch() {
-    for (void* q : p) cudaFree(q);
+    for (void* q : p) dev_free(q);
   }
 };
 
@@ -187,15 +187,15 @@ struct Scratch {
 ofsc_status set_row_partition(ofsc_graph* g, int warps, cudaStream_t s) {
   if (warps < 1 || warps > kRowMaxWarps) return fail(OFSC_ERR_INVALID_ARG, "row partition: %d warps", warps);
   int64_t* nb = nullptr;
-  OFSC_CUDA(cudaMalloc(&nb, (size_t)(warps + 1) * sizeof(int64_t)));
+  OFSC_CUDA(dev_alloc(&nb, (size_t)(warps + 1) * sizeof(int64_t)));
   k_partition<<<grid_for(warps + 1), 256, 0, s>>>(g->n, g->row_ptr, warps, nb);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
-    cudaFree(nb);
+    dev_free(nb);
     return cuda_fail(e, "row partition");
   }
-  cudaFree(g->bnd[kRowPart]);  // synchronises with any queued use of the old ranges
+  dev_free(g->bnd[kRowPart]);  // synchronises with any queued use of the old ranges
   g->bnd[kRowPart] = nb;
   g->groups[kRowPart] = warps;
   return OFSC_OK;
@@ -209,10 +209,13 @@ extern "C" ofsc_status ofsc_graph_build(int64_t n, int64_t m, const int32_t* src
                                         const float* w, uint32_t flags, void* stream_,
                                         ofsc_graph** out) {
   clear_error();
+  NvtxRange nv("ofsc_graph_build");
   if (!out) return fail(OFSC_ERR_INVALID_ARG, "ofsc_graph_build: out is NULL");
   *out = nullptr;
   if (n < 0 || n >= (int64_t(1) << 31))
     return fail(OFSC_ERR_INVALID_ARG, "ofsc_graph_build: n=%lld outside [0, 2^31)", (long long)n);
+  // m < 2^30 keeps the 2 m directed entries within the int item count of CUB's radix sort (the
+  // paper's largest graph, 970M stored nonzeros, is 485M listed edges)
   if (m < 0 || m >= (int64_t(1) << 30))
     return fail(OFSC_ERR_INVALID_ARG, "ofsc_graph_build: m=%lld outside [0, 2^30)", (long long)m);
   if (flags != 0) return fail(OFSC_ERR_INVALID_ARG, "ofsc_graph_build: flags must be 0");
@@ -235,16 +238,16 @@ extern "C" ofsc_status ofsc_graph_build(int64_t n, int64_t m, const int32_t* src
   Scratch sc;
   int* d_flags = nullptr;
   unsigned long long* d_counts = nullptr;  // [0] self-loops, [1] isolated
-  OFSC_CUDA(cudaMalloc(&d_flags, sizeof(int)));
+  OFSC_CUDA(dev_alloc(&d_flags, sizeof(int)));
   sc.p[0] = d_flags;
-  OFSC_CUDA(cudaMalloc(&d_counts, 2 * sizeof(unsigned long long)));
+  OFSC_CUDA(dev_alloc(&d_counts, 2 * sizeof(unsigned long long)));
   sc.p[1] = d_counts;
   OFSC_CUDA(cudaMemsetAsync(d_flags, 0, sizeof(int), stream));
   OFSC_CUDA(cudaMemsetAsync(d_counts, 0, 2 * sizeof(unsigned long long), stream));
 
-  OFSC_CUDA(cudaMalloc(&g->row_ptr, (n + 1) * sizeof(int64_t)));
-  OFSC_CUDA(cudaMalloc(&g->dinv, (n > 0 ? n : 1) * sizeof(float)));
-  OFSC_CUDA(cudaMalloc(&g->deg, (n > 0 ? n : 1) * sizeof(double)));
+  OFSC_CUDA(dev_alloc(&g->row_ptr, (n + 1) * sizeof(int64_t)));
+  OFSC_CUDA(dev_alloc(&g->dinv, (n > 0 ? n : 1) * sizeof(float)));
+  OFSC_CUDA(dev_alloc(&g->deg, (n > 0 ? n : 1) * sizeof(double)));
 
   int64_t nvalid = 0, nnz = 0;
   unsigned long long h_counts[2] = {0, 0};
@@ -267,14 +270,14 @@ extern "C" ofsc_status ofsc_graph_build(int64_t n, int64_t m, const int32_t* src
     const int64_t m2 = 2 * m;
     uint64_t *keys_a = nullptr, *keys_b = nullptr;
     float *vals_a = nullptr, *vals_b = nullptr;
-    OFSC_CUDA(cudaMalloc(&keys_a, m2 * sizeof(uint64_t)));
+    OFSC_CUDA(dev_alloc(&keys_a, m2 * sizeof(uint64_t)));
     sc.p[2] = keys_a;
-    OFSC_CUDA(cudaMalloc(&keys_b, m2 * sizeof(uint64_t)));
+    OFSC_CUDA(dev_alloc(&keys_b, m2 * sizeof(uint64_t)));
     sc.p[3] = keys_b;
     if (w) {
-      OFSC_CUDA(cudaMalloc(&vals_a, m2 * sizeof(float)));
+      OFSC_CUDA(dev_alloc(&vals_a, m2 * sizeof(float)));
       sc.p[4] = vals_a;
-      OFSC_CUDA(cudaMalloc(&vals_b, m2 * sizeof(float)));
+      OFSC_CUDA(dev_alloc(&vals_b, m2 * sizeof(float)));
       sc.p[5] = vals_b;
     }
     k_make_keys<<<grid_for(m), 256, 0, stream>>>(m, n, bits, src, dst, w, keys_a, vals_a);
@@ -287,7 +290,7 @@ extern "C" ofsc_status ofsc_graph_build(int64_t n, int64_t m, const int32_t* src
     else
       OFSC_CUDA(cub::DeviceRadixSort::SortKeys(nullptr, temp, kb, (int)m2, 0, end_bit, stream));
     void* d_temp = nullptr;
-    OFSC_CUDA(cudaMalloc(&d_temp, temp > 0 ? temp : 1));
+    OFSC_CUDA(dev_alloc(&d_temp, temp > 0 ? temp : 1));
     sc.p[6] = d_temp;
     if (w)
       OFSC_CUDA(cub::DeviceRadixSort::SortPairs(d_temp, temp, kb, vb, (int)m2, 0, end_bit, stream));
@@ -298,22 +301,22 @@ extern "C" ofsc_status ofsc_graph_build(int64_t n, int64_t m, const int32_t* src
 
     if (nvalid > 0) {
       int64_t* head = nullptr;
-      OFSC_CUDA(cudaMalloc(&head, nvalid * sizeof(int64_t)));
+      OFSC_CUDA(dev_alloc(&head, nvalid * sizeof(int64_t)));
       sc.p[7] = head;
       k_heads<<<grid_for(nvalid), 256, 0, stream>>>(nvalid, keys, head);
       OFSC_LAUNCH_CHECK("k_heads");
       size_t temp2 = 0;
       OFSC_CUDA(cub::DeviceScan::InclusiveSum(nullptr, temp2, head, head, (int)nvalid, stream));
       void* d_temp2 = nullptr;
-      OFSC_CUDA(cudaMalloc(&d_temp2, temp2 > 0 ? temp2 : 1));
+      OFSC_CUDA(dev_alloc(&d_temp2, temp2 > 0 ? temp2 : 1));
       sc.p[8] = d_temp2;
       OFSC_CUDA(cub::DeviceScan::InclusiveSum(d_temp2, temp2, head, head, (int)nvalid, stream));
       OFSC_CUDA(cudaMemcpyAsync(&nnz, head + nvalid - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, stream));
       OFSC_CUDA(cudaStreamSynchronize(stream));
-      OFSC_CUDA(cudaMalloc(&g->col, nnz * sizeof(int32_t)));
-      if (w) OFSC_CUDA(cudaMalloc(&g->val, nnz * sizeof(float)));
+      OFSC_CUDA(dev_alloc(&g->col, nnz * sizeof(int32_t)));
+      if (w) OFSC_CUDA(dev_alloc(&g->val, nnz * sizeof(float)));
       int32_t* row_of = nullptr;
-      OFSC_CUDA(cudaMalloc(&row_of, nnz * sizeof(int32_t)));
+      OFSC_CUDA(dev_alloc(&row_of, nnz * sizeof(int32_t)));
       sc.p[9] = row_of;
       k_scatter<<<grid_for(nvalid), 256, 0, stream>>>(nvalid, bits, keys, vals, head, g->col,
                                                        row_of, g->val);
@@ -329,12 +332,12 @@ extern "C" ofsc_status ofsc_graph_build(int64_t n, int64_t m, const int32_t* src
   double normA2 = (double)n;
   if (n > 0) {
     double* dinv64 = nullptr;
-    OFSC_CUDA(cudaMalloc(&dinv64, n * sizeof(double)));
+    OFSC_CUDA(dev_alloc(&dinv64, n * sizeof(double)));
     sc.p[11] = dinv64;
     k_degree<<<grid_for(n), 256, 0, stream>>>(n, g->row_ptr, g->val, g->deg, g->dinv, dinv64, d_counts + 1);
     OFSC_LAUNCH_CHECK("k_degree");
     double* part = nullptr;
-    OFSC_CUDA(cudaMalloc(&part, kNormBlocks * sizeof(double)));
+    OFSC_CUDA(dev_alloc(&part, kNormBlocks * sizeof(double)));
     sc.p[10] = part;
     k_normA_part<<<kNormBlocks, 256, 0, stream>>>(n, g->row_ptr, g->col, g->val, dinv64, part);
     OFSC_LAUNCH_CHECK("k_normA_part");
@@ -348,7 +351,7 @@ extern "C" ofsc_status ofsc_graph_build(int64_t n, int64_t m, const int32_t* src
   g->normA2 = normA2;
   for (int i = 0; i < 6; ++i) {
     g->groups[i] = i == kRowPart ? row_warps(nnz) : spmm_groups(nnz, 2 << i);
-    OFSC_CUDA(cudaMalloc(&g->bnd[i], (g->groups[i] + 1) * sizeof(int64_t)));
+    OFSC_CUDA(dev_alloc(&g->bnd[i], (g->groups[i] + 1) * sizeof(int64_t)));
     k_partition<<<grid_for(g->groups[i] + 1), 256, 0, stream>>>(n, g->row_ptr, g->groups[i], g->bnd[i]);
     OFSC_LAUNCH_CHECK("k_partition");
   }

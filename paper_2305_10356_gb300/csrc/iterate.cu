@@ -51,10 +51,12 @@ __device__ __forceinline__ bool is_f2(int method) { return method >= M_OFM_F2; }
 // ------------------------------------------------------------------------------------------
 
 __global__ void k_init_ctrl(Ctrl* c, double tol, int maxit, int k, double normA2, int trace_cap, int restart = 0,
-                            int vscale_exp = kDefaultVscaleExp) {
+                            int vscale_exp = kDefaultVscaleExp, long long spin_limit = 0, int withhold = 0) {
   c->it = 0;
   c->restart = restart;
   c->vscale_exp = vscale_exp;
+  c->spin_limit = spin_limit;
+  c->withhold = withhold;
   c->done = 0;
   c->converged = 0;
   c->status = OFSC_OK;
@@ -1384,12 +1386,13 @@ ofsc_status ensure_workspace(ofsc_graph* g, int kp) {
       {(void**)&ws.vinv, kp * sizeof(float)},
       {(void**)&ws.colpart, (size_t)(kMaxRowBlocks + kDotsRows) * kColSums * kp * sizeof(double)},
       {(void**)&ws.dE, (size_t)kp * sizeof(double)},
+      {(void**)&ws.bimg, kp == 128 ? (size_t)(4 * 4 * 128 * 32 * 4) : (size_t)16},
       {(void**)&ws.solve, (size_t)(kSolveBlocks * kSolveSums + 8 * kp) * sizeof(double)},
       {(void**)&ws.ctrl, sizeof(Ctrl)},
   };
   size_t total = 0;
   for (auto& it : items) {
-    cudaError_t e = cudaMalloc(it.p, it.bytes);
+    cudaError_t e = dev_alloc(it.p, it.bytes);
     if (e != cudaSuccess) {
       workspace_free(ws);
       return cuda_fail(e, "workspace cudaMalloc");
@@ -1513,11 +1516,12 @@ struct Runner {
     r.need_vy = need_vy;
     r.eval = eval;
     r.ignore_done = ignore_done;
+    r.bimg = ws.bimg;
     prof.begin(OFSC_PHASE_DIRECTION);
     cudaError_t e;
     if (tc && direction_tc_supported(dir_method, ws.kp)) {
       e = direction_tc_launch(dir_method, r, s, nblk);
-      ++g_launches;
+      g_launches += dir_method >= M_OFM_F2 ? 2 : 1;  // the f2 pass formats its B images first
     } else {
       e = launch_rowpass(dir_method, r, s, nblk);
     }
@@ -1726,8 +1730,9 @@ extern "C" ofsc_status ofsc_weight_grad(ofsc_graph* g, int32_t objective, int32_
   Prof prof{ws, nullptr, s};
   Runner run{g, ws, s, objective == OFSC_F1 ? M_OFM_F1 : M_OFM_F2, false, prof};
   run.tc = kp > 64;
-  void* scratch = nullptr;
-  OFSC_CUDA(cudaMallocAsync(&scratch, (size_t)(g->n + 1) * sizeof(float) + 16, s));
+  DevBuf sbuf;
+  OFSC_CUDA(dev_alloc(&sbuf.p, (size_t)(g->n + 1) * sizeof(float) + 16));
+  void* scratch = sbuf.p;
   int* bad = (int*)scratch;
   float* r = (float*)((char*)scratch + 16);
   cudaMemsetAsync(bad, 0, sizeof(int), s);
@@ -1760,7 +1765,6 @@ extern "C" ofsc_status ofsc_weight_grad(ofsc_graph* g, int32_t objective, int32_
   }
   int hbad = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s);
-  cudaFreeAsync(scratch, s);
   if (e != cudaSuccess) return cuda_fail(e, "ofsc_weight_grad");
   Ctrl c{};
   st = finish(ws, s, &c);
@@ -1785,8 +1789,9 @@ extern "C" ofsc_status ofsc_rayleigh_ritz(ofsc_graph* g, int32_t k, const float*
   Prof prof{ws, nullptr, s};
   Runner run{g, ws, s, M_OFM_F1, false, prof};
   run.tc = kp > 64;
-  double* work = nullptr;
-  OFSC_CUDA(cudaMallocAsync((void**)&work, (4 * (size_t)kp * kp + 2) * sizeof(double), s));
+  DevBuf wbuf;
+  OFSC_CUDA(dev_alloc(&wbuf.p, (4 * (size_t)kp * kp + 2) * sizeof(double)));
+  double* work = (double*)wbuf.p;
   double* sums = work + 4 * (size_t)kp * kp;
   double* out = sums + 1;
   k_init_ctrl<<<1, 1, 0, s>>>(ws.ctrl, 0.0, 0, k, g->normA2, 0);
@@ -1804,7 +1809,6 @@ extern "C" ofsc_status ofsc_rayleigh_ritz(ofsc_graph* g, int32_t k, const float*
   if (e == cudaSuccess) e = ritz_relerr_launch(ws.gram + (size_t)G_E * kp * kp, work, k, kp, sums, out, s);
   double h = 0.0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&h, out, sizeof(double), cudaMemcpyDeviceToHost, s);
-  cudaFreeAsync(work, s);
   if (e != cudaSuccess) return cuda_fail(e, "ofsc_rayleigh_ritz");
   Ctrl c{};
   st = finish(ws, s, &c);
@@ -1841,6 +1845,9 @@ ofsc_status check_iterate_args(const ofsc_graph* g, int32_t method, int32_t k, c
   if (!(o.exact_tail == o.exact_tail)) return fail(OFSC_ERR_INVALID_ARG, "%s: exact_tail is NaN", who);
   if (o.vscale_exp < -60 || o.vscale_exp > 60)
     return fail(OFSC_ERR_INVALID_ARG, "%s: vscale_exp outside [-60, 60]", who);
+  if (o.spin_limit < 0) return fail(OFSC_ERR_INVALID_ARG, "%s: spin_limit < 0", who);
+  if (o.withhold_arrivals != 0 && o.withhold_arrivals != 1)
+    return fail(OFSC_ERR_INVALID_ARG, "%s: withhold_arrivals must be 0 or 1", who);
   const int kp = round_up(k, 8);
   const bool tc = o.gram_engine == OFSC_GRAM_TC || (o.gram_engine == OFSC_GRAM_AUTO && kp > 64);
   if (tc && kp > 128) return fail(OFSC_ERR_INVALID_ARG, "%s: tensor-core Grams need k <= 128", who);
@@ -1925,10 +1932,12 @@ struct Job {
 
   // Control block, padded copy of X_0, exact AX_0 with X^T X and X^T AX.
   ofsc_status start() {
+    NvtxRange nv("start: exact AX");
     const int64_t l0 = g_launches;
     Workspace& ws = g->ws;
     k_init_ctrl<<<1, 1, 0, s>>>(ws.ctrl, tol, maxit, k, g->normA2, o.trace ? o.trace_cap : 0, o.cg_restart ? 1 : 0,
-                                o.vscale_exp != 0 ? o.vscale_exp : kDefaultVscaleExp);
+                                o.vscale_exp != 0 ? o.vscale_exp : kDefaultVscaleExp, (long long)o.spin_limit,
+                                o.withhold_arrivals ? 1 : 0);
     ++g_launches;
     OFSC_LAUNCH_CHECK("k_init_ctrl");
     k_pad_in<<<grid_elems(g->n * kp), 256, 0, s>>>(g->n, k, kp, X, ws.X, ws.ctrl);
@@ -1943,6 +1952,7 @@ struct Job {
   // updates), beta and the stop test, and for t < maxit the direction and the line search.
   // Depends on t only through t == 0, t == maxit and the refresh schedule.
   ofsc_status update(int t) {
+    NvtxRange nv(is_refresh(t) ? "update (exact refresh)" : "update");
     const int64_t l0 = g_launches;
     Workspace& ws = g->ws;
     int nblk = 0;
@@ -1976,6 +1986,7 @@ struct Job {
   // Final report, queued: from an exact AX when the run has no error status (read by the caller
   // into `c` after a stream synchronisation), then the unpadded X.
   ofsc_status report(const Ctrl& c) {
+    NvtxRange nv("report");
     const int64_t l0 = g_launches;
     Workspace& ws = g->ws;
     if (c.status == OFSC_OK) {
@@ -2027,6 +2038,7 @@ ofsc_status result_error(ofsc_status rs, const char* who) {
 extern "C" ofsc_status ofsc_iterate(ofsc_graph* g, int32_t method, int32_t k, float* X, double tol,
                                     int32_t maxit, const ofsc_opts* opts, ofsc_result* out, void* stream_) {
   clear_error();
+  NvtxRange nv("ofsc_iterate");
   ofsc_opts o{};
   if (opts) o = *opts;
   ofsc_status st = check_iterate_args(g, method, k, X, tol, maxit, o, "ofsc_iterate");
@@ -2078,6 +2090,7 @@ extern "C" ofsc_status ofsc_iterate(ofsc_graph* g, int32_t method, int32_t k, fl
 extern "C" ofsc_status ofsc_autotune(ofsc_graph* g, int32_t k, int32_t gather, int32_t* warps_out,
                                      int32_t* slots_out, double* ms_out, void* stream_) {
   clear_error();
+  NvtxRange nv("ofsc_autotune");
   if (!g) return fail(OFSC_ERR_INVALID_ARG, "ofsc_autotune: graph is NULL");
   if (k < 1 || k > kMaxK) return fail(OFSC_ERR_INVALID_ARG, "ofsc_autotune: k=%d outside [1, %d]", k, kMaxK);
   if (gather != OFSC_GATHER_FP32 && gather != OFSC_GATHER_BF16)
@@ -2241,6 +2254,7 @@ namespace {
 ofsc_status iterate_lockstep(int32_t count, ofsc_graph* const* graphs, int32_t method, const int32_t* ks,
                              float* const* Xs, double tol, int32_t maxit, const ofsc_opts& o, ofsc_result* outs,
                              cudaStream_t caller, const char* who) {
+  NvtxRange nv("lockstep iteration");
   const int check_every = o.check_every > 0 ? o.check_every : 16;
   std::vector<std::unique_ptr<Job>> jobs;
   std::vector<int> slot;  // job index -> position in the caller's arrays

@@ -1,0 +1,38 @@
+// Arguments and entry points of the sparse products W = A V (the direction product, spmm_dir.cu)
+// and A X, with A = L - 2I = -I - D^-1/2 S D^-1/2 (Eq. (1)).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ofsc {
+
+struct Ctrl;
+
+// Operands of the two sparse products: the direction product W = A V (k_spmm_dir, gathering
+// Vh = D^-1/2 V) and the exact AX = A X (k_spmm, gathering X and scaling by D^-1/2 per nonzero).
+struct SpmmArgs {
+  int64_t n;
+  int kp;
+  const int64_t* row_ptr;
+  const int32_t* col;
+  const float* val;
+  const float* dinv;
+  const int64_t* bnd;  // [groups + 1]: contiguous, nnz-balanced row ranges of the lane groups / warps
+  int groups;
+  const void* gather;  // direction: Vh = D^-1/2 V (FP32 or BF16); AX: X
+  const float* base;   // direction: V; AX: X  (the row block M in A M = -M - D^-1/2 S D^-1/2 M)
+  float* out;          // direction: W = AV; AX: AX
+  double* dots;        // direction with dots: [blocks][kp] partials of diag(V^T AV)
+  Ctrl* ctrl;
+  int ignore_done;
+};
+
+// The direction product (spmm_dir.cu): lanes per nonzero for rows of kp values with vpl values per
+// lane; the default and the candidate numbers of gathers in flight per lane; the launch (slots 0:
+// the default), returning the rows of dots partials it writes (one per warp).
+int dir_lanes(int kp, int vpl);
+int dir_default_slots(int kp, bool bf16, bool weighted);
+int dir_slot_options(int kp, bool bf16, int* out);
+int launch_spmm_dir(const SpmmArgs& a, bool weighted, bool bf16, int slots, cudaStream_t s);
+
+}  // namespace ofsc

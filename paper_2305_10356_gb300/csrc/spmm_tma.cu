@@ -26,9 +26,9 @@ constexpr long long kTmaSpin = 1ll << 22;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity, long long limit) {
   const uint32_t addr = smem_addr(bar);
-  for (long long it = 0; it < kTmaSpin; ++it) {
+  for (long long it = 0; it < limit; ++it) {
     uint32_t ok;
     asm volatile(
         "{\n"
@@ -106,6 +106,7 @@ __device__ __forceinline__ void stg_cpl(float* p, const float* v) {
 template <int CPL, bool BF16, bool WEIGHTED>
 __global__ void __launch_bounds__(kTmaWarps * 32) k_spmm_tma(const __grid_constant__ CUtensorMap tmap, TmaSpmmArgs a) {
   if (a.ctrl->done) return;
+  const long long lim = a.ctrl->spin_limit > 0 ? a.ctrl->spin_limit : kTmaSpin;
   constexpr int KP = CPL * 32;
   constexpr int ROWB = KP * (BF16 ? 2 : 4);
   constexpr int SLOT = 4 * ROWB;
@@ -209,7 +210,7 @@ __global__ void __launch_bounds__(kTmaWarps * 32) k_spmm_tma(const __grid_consta
       int64_t s = 0;
       for (; s < nst; ++s) {
         const int slot = (int)(s % kTmaStages);
-        if (!bar_wait(&bar[slot], (uint32_t)((s / kTmaStages) & 1))) {
+        if (!bar_wait(&bar[slot], (uint32_t)((s / kTmaStages) & 1), lim)) {
           ok = false;
           break;
         }
@@ -232,7 +233,7 @@ __global__ void __launch_bounds__(kTmaWarps * 32) k_spmm_tma(const __grid_consta
         // stop consuming, but let the copies already issued land (bounded) before the CTA exits
         const int64_t last = (s + kTmaStages < nst) ? s + kTmaStages : nst;
         for (int64_t t = s + 1; t < last; ++t)
-          bar_wait(&bar[t % kTmaStages], (uint32_t)((t / kTmaStages) & 1));
+          bar_wait(&bar[t % kTmaStages], (uint32_t)((t / kTmaStages) & 1), lim);
       }
     }
   }

@@ -62,10 +62,15 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
       smem_u32(bar)));
 }
 
+// Polls allowed per bounded wait: the control block's runtime limit when set, else kTcSpinLimit.
+__device__ __forceinline__ long long spin_limit_of(const Ctrl* c) {
+  return (c && c->spin_limit > 0) ? c->spin_limit : kTcSpinLimit;
+}
+
 // Waits for phase `parity` of the mbarrier; false if the bounded wait ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit = kTcSpinLimit) {
   const uint32_t addr = smem_u32(bar);
-  for (long long it = 0; it < kTcSpinLimit; ++it) {
+  for (long long it = 0; it < limit; ++it) {
     uint32_t ok;
     asm volatile(
         "{\n"
@@ -122,9 +127,10 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t* r) {
 }
 
 // Bounded wait that also gives up once another role has aborted; false on either.
-__device__ __forceinline__ bool ws_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+__device__ __forceinline__ bool ws_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                        long long limit = kTcSpinLimit) {
   const uint32_t addr = smem_u32(bar);
-  for (long long it = 0; it < kTcSpinLimit; ++it) {
+  for (long long it = 0; it < limit; ++it) {
     uint32_t ok;
     asm volatile(
         "{\n"

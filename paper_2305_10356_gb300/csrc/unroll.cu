@@ -382,12 +382,12 @@ struct Engine {
   size_t blk() const { return (size_t)n * kp * sizeof(float); }
 
   cudaError_t alloc(void** p, size_t bytes) {
-    cudaError_t e = cudaMalloc(p, bytes);
+    cudaError_t e = dev_alloc(p, bytes);
     if (e == cudaSuccess) owned.push_back(*p);
     return e;
   }
   ~Engine() {
-    for (void* p : owned) cudaFree(p);
+    for (void* p : owned) dev_free(p);
   }
   cudaError_t init() {
     const size_t kk = (size_t)kp * kp;

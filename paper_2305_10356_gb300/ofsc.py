@@ -54,7 +54,8 @@ class Opts(ctypes.Structure):
                 ("profile", ctypes.POINTER(Profile)), ("gram_engine", ctypes.c_int32),
                 ("spmm_engine", ctypes.c_int32), ("direct_launch", ctypes.c_int32),
                 ("cg_restart", ctypes.c_int32), ("refine_tol", ctypes.c_double),
-                ("exact_tail", ctypes.c_double), ("vscale_exp", ctypes.c_int32)]
+                ("exact_tail", ctypes.c_double), ("vscale_exp", ctypes.c_int32),
+                ("spin_limit", ctypes.c_int64), ("withhold_arrivals", ctypes.c_int32)]
 
 
 class Result(ctypes.Structure):
@@ -65,6 +66,10 @@ class Result(ctypes.Structure):
 
 
 _lib = None
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+_allocator = None  # the ctypes callbacks in use (kept alive while the library may call them)
 
 
 def header_functions() -> list[str]:
@@ -103,6 +108,7 @@ def lib() -> ctypes.CDLL:
             "ofsc_row_normalize": [i64, i32, vp, vp],
             "ofsc_gram": [i64, i32, i32, vp, i32, ctypes.POINTER(vp), i64, vp, vp],
             "ofsc_kmeans": [i64, i32, vp, i32, u64, i32, i32, vp, ctypes.POINTER(dbl), vp],
+            "ofsc_set_allocator": [ALLOC_FN, FREE_FN, vp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -237,14 +243,14 @@ def ofsc_iterate(g: Graph, method: int, X, tol: float, maxit: int, *, gather: in
                  profile: Profile | None = None, gram_engine: int = GRAM_AUTO,
                  spmm_engine: int = SPMM_AUTO, cg_restart: bool = False, refine_tol: float = 0.0,
                  exact_tail: float = 0.0, vscale_exp: int = 0, direct_launch: bool = False,
-                 stream=None) -> Result:
+                 spin_limit: int = 0, withhold_arrivals: bool = False, stream=None) -> Result:
     """Algorithm 2 in place on the device block X (n x k, FP32). Returns the ofsc_result."""
     px = _arg(X, "X", "float32", rows=_rows(g))
     o = Opts(gather, y_refresh, check_every, alpha0, _arg(trace, "trace", "float64"),
              0 if trace is None else int(trace.shape[0]),
              ctypes.pointer(profile) if profile is not None else None, gram_engine, spmm_engine,
              1 if direct_launch else 0, 1 if cg_restart else 0, float(refine_tol), float(exact_tail),
-             int(vscale_exp))
+             int(vscale_exp), int(spin_limit), 1 if withhold_arrivals else 0)
     r = Result()
     _check(lib().ofsc_iterate(g.handle, method, int(X.shape[1]), px, float(tol), int(maxit),
                               ctypes.byref(o), ctypes.byref(r), _stream(stream)),
@@ -357,6 +363,22 @@ def ofsc_rayleigh_ritz(g: Graph, X, ritz, stream=None) -> float:
                                     _arg(ritz, "ritz", "float64", numel=int(X.shape[1])), ctypes.byref(out),
                                     _stream(stream)))
     return float(out.value)
+
+
+def ofsc_set_allocator(alloc=None, free=None) -> None:
+    """Every device block the library allocates from now on comes from alloc(bytes) -> int device
+    pointer (0 when it cannot) and goes back through free(ptr); both None: cudaMalloc again."""
+    global _allocator
+    if (alloc is None) != (free is None):
+        raise OfscError(ERR_INVALID_ARG, "ofsc_set_allocator: give both functions or neither")
+    if alloc is None:
+        cb = (ALLOC_FN(), FREE_FN())
+    else:
+        cb = (ALLOC_FN(lambda nbytes, user: int(alloc(int(nbytes)) or 0)),
+              FREE_FN(lambda ptr, user: free(int(ptr))))
+    _check(lib().ofsc_set_allocator(cb[0], cb[1], None))
+    # callbacks of blocks still owned by the library must outlive them: keep every pair set
+    _allocator = (_allocator or ()) + (cb,)
 
 
 def ofsc_row_normalize(X, stream=None) -> None:

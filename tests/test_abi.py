@@ -61,3 +61,12 @@ def test_no_cpu_fallback_when_library_missing(monkeypatch, tmp_path):
     monkeypatch.setattr(ofsc, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(ofsc.OfscError):
         ofsc.lib()
+
+
+def test_set_allocator_argument_checks():
+    """ofsc_set_allocator takes both functions or neither (host state only, no GPU needed)."""
+    lib = ofsc.lib()
+    alloc = ofsc.ALLOC_FN(lambda nbytes, user: 0)
+    assert lib.ofsc_set_allocator(alloc, ofsc.FREE_FN(), None) == ofsc.ERR_INVALID_ARG
+    assert b"both" in lib.ofsc_last_error()
+    assert lib.ofsc_set_allocator(ofsc.ALLOC_FN(), ofsc.FREE_FN(), None) == ofsc.OK

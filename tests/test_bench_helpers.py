@@ -25,7 +25,7 @@ def test_traffic_is_keyed_to_the_kernel_sources(tmp_path, monkeypatch):
     entry = {"dram_read_bytes": 10, "dram_write_bytes": 2, "source_digest": "not-this-build"}
     (tmp_path / "profiles" / "traffic.json").write_text(json.dumps({"entries": {"w/bf16": entry}}))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    monkeypatch.setattr(bench, "source_digest", lambda: "this-build")
+    monkeypatch.setattr(bench, "source_digest", lambda names=None: "this-build")
     assert bench.measured_traffic("w", "bf16") is None
     assert bench.measured_traffic("w", "bf16", any_build=True)["dram_read_bytes"] == 10
     entry["source_digest"] = "this-build"
@@ -38,6 +38,9 @@ def test_source_digest_covers_the_kernel_sources():
     d = bench.source_digest()
     assert len(d) == 16 and d == bench.source_digest()
     assert os.path.isdir(os.path.join(bench.ROOT, "paper_2305_10356_gb300", "csrc"))
+    # the direction product's own digest covers its translation unit and the shared header only
+    dp = bench.source_digest(bench.DIR_PRODUCT_SOURCES)
+    assert len(dp) == 16 and dp != d
 
 
 def test_max_over_ranks_single_rank():

@@ -239,6 +239,70 @@ def test_single_call_replay_equals_direct_launches(c1, method):
     assert (ra.iterations, ra.status, ra.rel_dir_norm, ra.f) == (rb.iterations, rb.status, rb.rel_dir_norm, rb.f)
 
 
+def test_allocator_hook_and_oom_injection():
+    """ofsc_set_allocator: every device block of the library comes from the caller's allocator (here
+    torch's caching allocator). One that refuses past a byte budget makes ofsc_graph_build and then
+    ofsc_iterate return OFSC_ERR_OOM with every block they had taken given back; with room again the
+    same calls run and give the bits they give on cudaMalloc; freeing the graph returns the rest."""
+    import torch
+    e = synth.sbm(3000, 6, 20.0, 6.0, ratio_kind="count", seed=161)
+    x0 = synth.initial_block(e.n, 16, 162)
+    X_ref, r_ref, _ = run_iterate(gpu_graph(e), o.OFM_F1, x0, 0.0, 8)
+    live, budget = {}, [1 << 14]
+
+    def alloc(nbytes):
+        if sum(live.values()) + nbytes > budget[0]:
+            return 0
+        p = torch.cuda.caching_allocator_alloc(nbytes)
+        live[p] = nbytes
+        return p
+
+    def free(p):
+        del live[p]
+        torch.cuda.caching_allocator_delete(p)
+
+    try:
+        ofsc.ofsc_set_allocator(alloc, free)
+        with pytest.raises(ofsc.OfscError) as ei:
+            gpu_graph(e)
+        assert ei.value.status == ofsc.ERR_OOM and not live
+        budget[0] = 1 << 30
+        g = gpu_graph(e)
+        held = sum(live.values())
+        assert held > 0
+        budget[0] = held + 4096  # too little for the iteration's workspace
+        with pytest.raises(ofsc.OfscError) as ei:
+            run_iterate(g, o.OFM_F1, x0, 0.0, 8)
+        assert ei.value.status == ofsc.ERR_OOM and sum(live.values()) == held
+        budget[0] = 1 << 30
+        X, r, _ = run_iterate(g, o.OFM_F1, x0, 0.0, 8)
+        assert np.array_equal(X, X_ref) and r.f == r_ref.f
+        g.free()
+        assert not live
+    finally:
+        ofsc.ofsc_set_allocator()
+
+
+def test_bounded_wait_runs_out_and_the_next_call_succeeds():
+    """Failure detection without a fault: with the test hook that makes the tensor-core direction
+    pass's converter warps withhold their arrivals and a short spin limit, the MMA warp's first
+    bounded wait runs out before any MMA is issued (the pass has no TMA copies), the kernel records
+    OFSC_ERR_TIMEOUT, frees its tensor memory and returns, and the call reports the status. The next
+    normal call on the same handle then runs and matches the oracle."""
+    e = synth.sbm(3001, 9, 22.0, 6.0, seed=81, gamma=2.4, ratio_kind="count")
+    og = o.build_graph(e.n, e.src, e.dst)
+    g = gpu_graph(e)
+    x0 = synth.initial_block(e.n, 128, 82)
+    with pytest.raises(ofsc.OfscError) as ei:
+        run_iterate(g, o.OFM_F1, x0, 0.0, 3, withhold_arrivals=True, spin_limit=1 << 12,
+                    gram_engine=ofsc.GRAM_TC, direct_launch=True)
+    assert ei.value.status == ofsc.ERR_TIMEOUT
+    X, r, _ = run_iterate(g, o.OFM_F1, x0, 0.0, 3, gram_engine=ofsc.GRAM_TC)
+    assert r.iterations == 3 and r.status == ofsc.ERR_NOT_CONVERGED
+    ref = o.iterate(og, o.OFM_F1, x0, 0.0, 3)
+    assert_elementwise(X, ref.X, 1e-4)
+
+
 @pytest.mark.parametrize("method", METHODS)
 def test_column_scales_leave_the_bits_unchanged(method):
     """The stored direction V diag(1/s) with power-of-two column scales s: forcing scales of about

@@ -293,9 +293,11 @@ __global__ void __launch_bounds__(kDtThreads, 1) k_direction_tc(RowArgs a) {
 // so one half reloads while the other half's MMAs run):
 //   * warps 0-3 form X_new, warps 4-7 AX_new, 32-feature chunks of 128 rows, into tf32 hi/lo
 //     K-major 128-byte-swizzled tiles of a ring of two stages (warps 0-3 also store X_new);
-//   * warp 12 (one thread) copies the B chunks and issues D += Xhi B'hi + Xhi B'lo + Xlo B'hi +
-//     Yhi R'hi + Yhi R'lo + Ylo R'hi into one of two 128-column tensor-memory accumulators;
-//   * warps 8-11 read P with tcgen05.ld, recompute and store AX_new from AX and AV (their second
+//   * warp 12 (one thread) copies the B chunks and issues Dx += Xhi B'hi + Xhi B'lo + Xlo B'hi and
+//     Dy += Yhi R'hi + Yhi R'lo + Ylo R'hi into two 128-column tensor-memory accumulators (of a
+//     pair of such, 512 columns): each FP32 accumulator then takes as many MMA updates as the f1
+//     pass's, which keeps the accumulation rounding at the f1 pass's size;
+//   * warps 8-11 read P = Dx + Dy with tcgen05.ld, recompute and store AX_new from AX and AV (their second
 //     reads, mostly from L2), form G and the column sums as the f1 pass does.
 // Every wait is bounded; on expiry the CTA records OFSC_ERR_TIMEOUT, stops every role, waits
 // (bounded) for the copies and MMAs it issued and frees its tensor memory.
@@ -358,7 +360,7 @@ __global__ void __launch_bounds__(kD2Threads, 1) k_direction_tc2(RowArgs a) {
 
   if (warp == 12) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                 "r"(256));
+                 "r"(512));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
@@ -446,14 +448,23 @@ __global__ void __launch_bounds__(kD2Threads, 1) k_direction_tc2(RowArgs a) {
       asm volatile("tcgen05.fence::after_thread_sync;");
       const int64_t row0 = (blockIdx.x + i * gridDim.x) * 128 + ew * 32;
       for (int cc = 0; cc < 4; ++cc) {
-        uint32_t p[32];
-        tmem_ld32(tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)(buf * 128 + cc * 32), p);
-        asm volatile("tcgen05.wait::ld.sync.aligned;");
+        // P = (X_new B') + (AX_new R'): the two accumulators, added in FP32 through the staging tile
+        for (int part = 0; part < 2; ++part) {
+          uint32_t p[32];
+          tmem_ld32(tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)(buf * 256 + part * 128 + cc * 32), p);
+          asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
-        for (int q = 0; q < 8; ++q)
-          *(float4*)(ps + lane * 32 + ((q ^ (lane & 7)) << 2)) =
-              make_float4(__uint_as_float(p[4 * q]), __uint_as_float(p[4 * q + 1]), __uint_as_float(p[4 * q + 2]),
-                          __uint_as_float(p[4 * q + 3]));
+          for (int q = 0; q < 8; ++q) {
+            float4* dst = (float4*)(ps + lane * 32 + ((q ^ (lane & 7)) << 2));
+            float4 v = make_float4(__uint_as_float(p[4 * q]), __uint_as_float(p[4 * q + 1]),
+                                   __uint_as_float(p[4 * q + 2]), __uint_as_float(p[4 * q + 3]));
+            if (part) {
+              const float4 o = *dst;
+              v = make_float4(o.x + v.x, o.y + v.y, o.z + v.z, o.w + v.w);
+            }
+            *dst = v;
+          }
+        }
         __syncwarp();
         const int c = cc * 32 + 4 * j;
         float4 al = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -548,16 +559,17 @@ __global__ void __launch_bounds__(kD2Threads, 1) k_direction_tc2(RowArgs a) {
              ws_wait(&b_full[1], (uint32_t)(u & 1), &abort_flag, lim);
         if (!ok) break;
         asm volatile("tcgen05.fence::after_thread_sync;");
-        const uint32_t d = tmem + (uint32_t)(buf * 128);
         const uint32_t as = smem_u32(ast + st * kD2Stage);
         for (int h = 0; h < 2; ++h) {  // h = 0: X_new with B'; h = 1: AX_new with R'
+          // each product has its own accumulator, so neither chains more MMA updates than the f1 pass
+          const uint32_t d = tmem + (uint32_t)(buf * 256 + h * 128);
           const uint32_t a_hi = as + h * 2 * kTcTile, a_lo = a_hi + kTcTile;
           const uint32_t b_hi = smem_u32(bbuf + h * kD2Half), b_lo = b_hi + kTcTile;
 #pragma unroll
           for (int s = 0; s < 4; ++s) {  // K steps of 8 features (32 bytes)
             const uint64_t ah = sw128_desc(a_hi + s * 32), alo = sw128_desc(a_lo + s * 32);
             const uint64_t bh = sw128_desc(b_hi + s * 32), blo = sw128_desc(b_lo + s * 32);
-            mma_tf32(d, ah, bh, idesc, (kc > 0 || h > 0 || s > 0) ? 1u : 0u);
+            mma_tf32(d, ah, bh, idesc, (kc > 0 || s > 0) ? 1u : 0u);
             mma_tf32(d, ah, blo, idesc, 1u);
             mma_tf32(d, alo, bh, idesc, 1u);
           }
@@ -596,7 +608,7 @@ __global__ void __launch_bounds__(kD2Threads, 1) k_direction_tc2(RowArgs a) {
     a.ctrl->status = OFSC_ERR_TIMEOUT;
     a.ctrl->done = 1;
   }
-  if (warp == 12) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
+  if (warp == 12) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
 }
 
 template <bool TRI>

@@ -208,11 +208,17 @@ constexpr int kWsThreads = 192;
 constexpr int kWsBox = 32 * 128;  // one TMA box: 32 rows x 32 FP32 features
 constexpr int64_t kWsSegRows = OFSC_WS_SEG;
 
-template <int NR>
+// SEPL: the left block is staged and converted as a block of its own after the NR right blocks
+// (the left block is not one of them); the three blocks of NR = 2 then take a raw ring of two stages
+// and one tile stage (193 KB).
+template <int NR, bool SEPL>
 struct WsShape {
-  static constexpr int RAW = NR * 4 * kWsBox;  // one raw stage: four boxes per block
-  static constexpr int TILE = NR * kTcTile;    // the hi (or lo) tiles of one stage
-  static constexpr size_t bytes() { return (size_t)kWsRaw * RAW + (size_t)kWsTile * 2 * TILE + 1024; }
+  static constexpr int NB = NR + (SEPL ? 1 : 0);   // blocks staged per chunk
+  static constexpr int RAWS = SEPL ? 2 : kWsRaw;    // raw ring stages
+  static constexpr int TILES = SEPL ? 1 : kWsTile;  // tile ring stages
+  static constexpr int RAW = NB * 4 * kWsBox;       // one raw stage: four boxes per block
+  static constexpr int TILE = NB * kTcTile;         // the hi (or lo) tiles of one stage
+  static constexpr size_t bytes() { return (size_t)RAWS * RAW + (size_t)TILES * 2 * TILE + 1024; }
 };
 
 struct WsArgs {
@@ -225,12 +231,15 @@ struct WsArgs {
   int ignore_done;
 };
 
-template <int NR>
+template <int NR, bool SEPL>
 __global__ void __launch_bounds__(kWsThreads, 1)
-    k_gram_tc_ws(const __grid_constant__ CUtensorMap m0, const __grid_constant__ CUtensorMap m1, WsArgs a) {
+    k_gram_tc_ws(const __grid_constant__ CUtensorMap m0, const __grid_constant__ CUtensorMap m1,
+                 const __grid_constant__ CUtensorMap ml, WsArgs a) {
   if (!a.ignore_done && a.ctrl->done) return;
   const long long lim = spin_limit_of(a.ctrl);
-  using Sh = WsShape<NR>;
+  using Sh = WsShape<NR, SEPL>;
+  constexpr int RAWS = Sh::RAWS, TILES = Sh::TILES;
+  const int atile = SEPL ? NR : a.lslot;  // the tile of the left block (the A operand)
   constexpr uint32_t NCOLS = NR == 1 ? 256 : 512;  // segment accumulator, then the running total
   constexpr uint32_t TOT = NR * kTcM;               // first column of the total
   extern __shared__ unsigned char smem_raw[];
@@ -240,8 +249,8 @@ __global__ void __launch_bounds__(kWsThreads, 1)
   __shared__ volatile int abort_flag;
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* raw = base;                      // [kWsRaw][NR][4 boxes]
-  unsigned char* hi = base + kWsRaw * Sh::RAW;    // [kWsTile][NR tiles]
-  unsigned char* lo = hi + kWsTile * Sh::TILE;
+  unsigned char* hi = base + RAWS * Sh::RAW;    // [kWsTile][NR tiles]
+  unsigned char* lo = hi + TILES * Sh::TILE;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (warp == 5) {
@@ -251,11 +260,11 @@ __global__ void __launch_bounds__(kWsThreads, 1)
   }
   if (tid == 0) {
     abort_flag = 0;
-    for (int st = 0; st < kWsRaw; ++st) {
+    for (int st = 0; st < RAWS; ++st) {
       mbar_init(&raw_full[st], 1);
       mbar_init(&raw_empty[st], 4);
     }
-    for (int tt = 0; tt < kWsTile; ++tt) {
+    for (int tt = 0; tt < TILES; ++tt) {
       mbar_init(&tile_full[tt], 4);
       mbar_init(&tile_empty[tt], 1);
     }
@@ -278,34 +287,35 @@ __global__ void __launch_bounds__(kWsThreads, 1)
     if (lane == 0) {  // producer
       int64_t c = 0;
       for (; c < nchunks; ++c) {
-        const int st = (int)(c % kWsRaw);
-        if (c >= kWsRaw && !ws_wait(&raw_empty[st], (uint32_t)((c / kWsRaw - 1) & 1), &abort_flag, lim)) break;
+        const int st = (int)(c % RAWS);
+        if (c >= RAWS && !ws_wait(&raw_empty[st], (uint32_t)((c / RAWS - 1) & 1), &abort_flag, lim)) break;
         mbar_expect_tx(&raw_full[st], (uint32_t)Sh::RAW);
         const int y = (int)(r0 + c * 32);
         unsigned char* dst = raw + st * Sh::RAW;
 #pragma unroll
-        for (int b = 0; b < NR; ++b)
+        for (int b = 0; b < Sh::NB; ++b)
 #pragma unroll
-          for (int fb = 0; fb < 4; ++fb) tma_load_box(dst + (b * 4 + fb) * kWsBox, b ? &m1 : &m0, fb * 32, y, &raw_full[st]);
+          for (int fb = 0; fb < 4; ++fb)
+            tma_load_box(dst + (b * 4 + fb) * kWsBox, b == NR ? &ml : (b ? &m1 : &m0), fb * 32, y, &raw_full[st]);
       }
       // the copies already issued must land before the CTA may exit
-      for (int64_t d = c > kWsRaw ? c - kWsRaw : 0; d < c; ++d) mbar_wait(&raw_full[d % kWsRaw], (uint32_t)((d / kWsRaw) & 1), lim);
+      for (int64_t d = c > RAWS ? c - RAWS : 0; d < c; ++d) mbar_wait(&raw_full[d % RAWS], (uint32_t)((d / RAWS) & 1), lim);
     }
   } else if (warp == 5) {
     if (lane == 0) {  // MMA issuer
       int64_t c = 0;
       for (; c < nchunks; ++c) {
-        const int tt = (int)(c % kWsTile);
+        const int tt = (int)(c % TILES);
         const int64_t seg = c / cps;
         const bool first = c % cps == 0;
-        if (!ws_wait(&tile_full[tt], (uint32_t)((c / kWsTile) & 1), &abort_flag, lim)) break;
+        if (!ws_wait(&tile_full[tt], (uint32_t)((c / TILES) & 1), &abort_flag, lim)) break;
         if (first && seg > 0 && !ws_wait(&acc_empty, (uint32_t)((seg - 1) & 1), &abort_flag, lim)) break;
         asm volatile("tcgen05.fence::after_thread_sync;");
         const uint32_t hs = smem_u32(hi + tt * Sh::TILE), ls = smem_u32(lo + tt * Sh::TILE);
 #pragma unroll
         for (int s = 0; s < 4; ++s) {  // K steps of 8 rows (32 bytes)
-          const uint64_t ahi = sw128_desc(hs + a.lslot * kTcTile + s * 32);
-          const uint64_t alo = sw128_desc(ls + a.lslot * kTcTile + s * 32);
+          const uint64_t ahi = sw128_desc(hs + atile * kTcTile + s * 32);
+          const uint64_t alo = sw128_desc(ls + atile * kTcTile + s * 32);
 #pragma unroll
           for (int h = 0; h < (NR + 1) / 2; ++h) {
             const int ncol = (2 * h + 1 < NR) ? 256 : 128;
@@ -322,21 +332,21 @@ __global__ void __launch_bounds__(kWsThreads, 1)
         if (seg_last(c)) mma_commit(&acc_full);
       }
       // the MMAs already issued must finish before the tensor memory is released
-      if (c > 0) mbar_wait(&tile_empty[(c - 1) % kWsTile], (uint32_t)(((c - 1) / kWsTile) & 1), lim);
+      if (c > 0) mbar_wait(&tile_empty[(c - 1) % TILES], (uint32_t)(((c - 1) / TILES) & 1), lim);
     }
   } else {  // warps 0-3: convert, and drain at segment ends
     const int fb = warp;
     const int fi = warp * 32 + lane;  // TMEM lane = feature of the left block
     int64_t c = 0;
     for (; c < nchunks; ++c) {
-      const int st = (int)(c % kWsRaw), tt = (int)(c % kWsTile);
-      if (!ws_wait(&raw_full[st], (uint32_t)((c / kWsRaw) & 1), &abort_flag, lim)) break;
-      if (c >= kWsTile && !ws_wait(&tile_empty[tt], (uint32_t)((c / kWsTile - 1) & 1), &abort_flag, lim)) break;
+      const int st = (int)(c % RAWS), tt = (int)(c % TILES);
+      if (!ws_wait(&raw_full[st], (uint32_t)((c / RAWS) & 1), &abort_flag, lim)) break;
+      if (c >= TILES && !ws_wait(&tile_empty[tt], (uint32_t)((c / TILES - 1) & 1), &abort_flag, lim)) break;
       // lane = feature fb*32 + lane; four consecutive rows per step: four 4-byte reads from the
       // swizzled row lines (one line per read, all lanes distinct words) and one 16-byte store per
       // tile into the feature's K-major line (each group of 8 lanes hits 8 distinct 16-byte banks)
 #pragma unroll
-      for (int b = 0; b < NR; ++b) {
+      for (int b = 0; b < Sh::NB; ++b) {
         const unsigned char* box = raw + st * Sh::RAW + (b * 4 + fb) * kWsBox + (lane & 3) * 4;
         unsigned char* dh = hi + tt * Sh::TILE + b * kTcTile;
         unsigned char* dl = lo + tt * Sh::TILE + b * kTcTile;
@@ -513,16 +523,18 @@ cudaError_t gram_tc_launch(GramTcArgs a, const int* slot, int kp, double* gram, 
   return gram_tc_launch_ld(a, slot, kp, kp, (int64_t)kp * kp, gram, s);
 }
 
-template <int NR>
-cudaError_t launch_ws(const CUtensorMap& m0, const CUtensorMap& m1, const WsArgs& w, int grid, cudaStream_t s) {
-  const size_t smem = WsShape<NR>::bytes();
+template <int NR, bool SEPL>
+cudaError_t launch_ws(const CUtensorMap& m0, const CUtensorMap& m1, const CUtensorMap& ml, const WsArgs& w,
+                      int grid, cudaStream_t s) {
+  const size_t smem = WsShape<NR, SEPL>::bytes();
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_gram_tc_ws<NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_gram_tc_ws<NR, SEPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k_gram_tc_ws<NR><<<grid, kWsThreads, smem, s>>>(m0, m1, w);
+  k_gram_tc_ws<NR, SEPL><<<grid, kWsThreads, smem, s>>>(m0, m1, ml, w);
   return cudaGetLastError();
 }
 
@@ -532,7 +544,7 @@ cudaError_t gram_tc_launch_ld(GramTcArgs a, const int* slot, int kout, int ld_ou
   int grid = (int)((a.n + a.rows_per_cta - 1) / a.rows_per_cta);
   const bool sep = a.lslot < 0;
   cudaError_t e = cudaSuccess;
-  if (a.use_ws && !sep && a.nr <= 2) {
+  if (a.use_ws && (sep ? a.nr == 2 : a.nr <= 2)) {
     WsArgs w{};
     const int64_t ctas = ws_layout(a.n, &w.rows_per_cta);
     w.n = a.n;
@@ -545,7 +557,11 @@ cudaError_t gram_tc_launch_ld(GramTcArgs a, const int* slot, int kout, int ld_ou
     if (tma_encode_f32_sw128(a.R[0], a.n, a.k, a.ld, 32, 32, &m0) != OFSC_OK) return cudaErrorInvalidValue;
     if (a.nr > 1 && tma_encode_f32_sw128(a.R[1], a.n, a.k, a.ld, 32, 32, &m1) != OFSC_OK) return cudaErrorInvalidValue;
     if (a.nr == 1) m1 = m0;
-    e = a.nr == 1 ? launch_ws<1>(m0, m1, w, (int)ctas, s) : launch_ws<2>(m0, m1, w, (int)ctas, s);
+    CUtensorMap ml = m0;
+    if (sep && tma_encode_f32_sw128(a.L, a.n, a.k, a.ld, 32, 32, &ml) != OFSC_OK) return cudaErrorInvalidValue;
+    e = sep ? launch_ws<2, true>(m0, m1, ml, w, (int)ctas, s)
+            : (a.nr == 1 ? launch_ws<1, false>(m0, m1, ml, w, (int)ctas, s)
+                         : launch_ws<2, false>(m0, m1, ml, w, (int)ctas, s));
     grid = (int)ctas;  // partials to reduce
   } else {
   switch (a.nr * 2 + (sep ? 1 : 0)) {

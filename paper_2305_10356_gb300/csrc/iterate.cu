@@ -1416,6 +1416,7 @@ struct Runner {
   bool bf16;
   Prof& prof;
   bool tc = false;   // Grams on the tensor cores
+  bool tc_dir = true;  // with tc: the direction pass on the tensor cores too (padded k = 128)
   bool tma = false;  // sparse product with TMA gather4
 
   // L^T R_b for b < nr into the gram slots, on the tensor cores or the CUDA cores
@@ -1519,7 +1520,7 @@ struct Runner {
     r.bimg = ws.bimg;
     prof.begin(OFSC_PHASE_DIRECTION);
     cudaError_t e;
-    if (tc && direction_tc_supported(dir_method, ws.kp)) {
+    if (tc && tc_dir && direction_tc_supported(dir_method, ws.kp)) {
       e = direction_tc_launch(dir_method, r, s, nblk);
       g_launches += dir_method >= M_OFM_F2 ? 2 : 1;  // the f2 pass formats its B images first
     } else {
@@ -1598,7 +1599,14 @@ struct Runner {
     // V^T X and V^T V for every method; V^T AX and V^T AV in full for the f2 methods
     const float* Rs[4] = {ws.X, ws.V, ws.Y, ws.W};
     const int slots[4] = {G_P, G_Q, G_E, G_C};
-    cudaError_t e = grams(ws.V, Rs, f2 ? 4 : 2, slots, 0, true);
+    cudaError_t e;
+    if (tc && f2) {
+      // two warp-specialised launches: (V; X, V), then (V; AX, AV) with V staged on its own
+      e = grams(ws.V, Rs, 2, slots, 0, true);
+      if (e == cudaSuccess) e = grams(ws.V, Rs + 2, 2, slots + 2, 0, true);
+    } else {
+      e = grams(ws.V, Rs, f2 ? 4 : 2, slots, 0, true);
+    }
     if (e != cudaSuccess) return e;
     SolveArgs sa{};
     sa.gram = ws.gram;
@@ -1684,6 +1692,9 @@ extern "C" ofsc_status ofsc_objective_grad(ofsc_graph* g, int32_t objective, int
   Prof prof{ws, nullptr, s};
   Runner run{g, ws, s, method, false, prof};
   run.tc = kp > 64;
+  // a single evaluation: the direction pass in plain FP32 on the CUDA cores (the iteration's
+  // tensor-core pass accumulates its K = 128 or 256 products in FP32 tensor memory)
+  run.tc_dir = false;
   k_init_ctrl<<<1, 1, 0, s>>>(ws.ctrl, 0.0, 0, k, g->normA2, 0);
   ++g_launches;
   OFSC_LAUNCH_CHECK("k_init_ctrl");

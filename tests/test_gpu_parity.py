@@ -428,6 +428,8 @@ def test_kmeans_matches_oracle(cuda_lib):
     (100, 128, 128, 2, 1),        # warp-specialised TMA kernel: one CTA, ragged 32-row chunk
     (300_001, 128, 128, 2, 0),    # ... several accumulator segments per CTA
     (4_999, 100, 104, 1, 0),      # ... one block, features 100..127 zero-filled
+    (150_001, 128, 128, 2, None), # ... two right blocks, the left block staged on its own
+    (4_999, 100, 104, 2, None),   # ... the same with features 100..127 zero-filled
     (10_001, 128, 128, 4, 1),     # per-CTA kernel: four right blocks
     (3_333, 100, 104, 3, None),   # ... left block separate from the right blocks
     (777, 20, 24, 1, None)])
@@ -516,10 +518,11 @@ def test_iterations_are_bitwise_repeatable(gather, k):
     assert r1.rel_dir_norm == r2.rel_dir_norm
 
 
-@pytest.mark.parametrize("method", [o.OFM_F1, o.TRI_F1])
+@pytest.mark.parametrize("method", METHODS)
 def test_tensor_core_direction_pass(method):
-    """k = 128: the direction pass with X_new R on the tensor cores (3-term tf32) against the CUDA-core
-    pass and against the oracle, on 3001 rows (a ragged last 128-row tile)."""
+    """k = 128: the direction pass on the tensor cores (3-term tf32; X_new R for the f1 methods,
+    X_new B + AX_new R with the B operands streamed per K chunk for the f2 methods) against the
+    CUDA-core pass and against the oracle, on 3001 rows (a ragged last 128-row tile)."""
     e = synth.sbm(3001, 9, 22.0, 6.0, seed=81, gamma=2.4, ratio_kind="count")
     og = o.build_graph(e.n, e.src, e.dst)
     g = gpu_graph(e)

@@ -219,6 +219,13 @@ typedef struct {
                             stage, so its MMA warp's first bounded wait runs out before any MMA is
                             issued and the call returns OFSC_ERR_TIMEOUT (exercises the timeout
                             path without a fault; use with a small spin_limit) */
+  int32_t merge_path;    /* 0 (default): the direction product (Sec. 3.3) splits its work by merge
+                            path (equal shares of rows + nonzeros, so a long row spans several
+                            warps, whose partial sums are added in warp order) when ofsc_autotune
+                            chose it for this k and gather storage, or, untuned, when the graph's
+                            longest row holds at least 1024 nonzeros and more than four warps'
+                            shares of the row partition; else by whole rows; 1: always by merge
+                            path; -1: never */
 } ofsc_opts;
 
 typedef struct {
@@ -319,21 +326,23 @@ ofsc_status ofsc_unrolled_grad(ofsc_graph* g, int32_t k, const float* X0, int32_
  * Sec. 3.3, the largest part of an update of Algorithm 2) for this graph, k columns and the given
  * gather storage: how finely its rows are split among warps (4, 8, 16 or 32 warps per SM, coarser
  * ones only while each warp keeps at least 16 nonzeros) and how many row gathers each lane keeps
- * in flight (2, 4, 6 or 8, as many as one step of at most 32 nonzeros allows). Every combination is
- * timed (3 launches after one warm-up); the fastest is kept in the handle and used by every later
- * call on it with the same padded k and gather storage. Each warp sums its rows' share of
- * diag(V^T AV) before a fixed-order fold, so a new choice can change the last bits of later results
- * (never the rows of A V).
+ * in flight (2, 4, 6 or 8, as many as one step of at most 32 nonzeros allows), and, for each number
+ * of warps, the merge-path split (equal shares of rows + nonzeros, default gathers in flight). Every
+ * combination is timed (3 launches after one warm-up); the fastest is kept in the handle and used
+ * by every later call on it with the same padded k and gather storage whose merge_path option is 0.
+ * Each warp sums its rows' share of diag(V^T AV) before a fixed-order fold, so a new choice can
+ * change the last bits of later results (and the split of a long row those of its row of A V).
  *   k         columns (1 <= k <= 128)
  *   gather    OFSC_GATHER_FP32 or OFSC_GATHER_BF16
  *   warps_out HOST int32* (nullable): the chosen number of warps
  *   slots_out HOST int32* (nullable): the chosen gathers in flight per lane
+ *   merge_out HOST int32* (nullable): 1 if the merge-path split was chosen, else 0
  *   ms_out    HOST double* (nullable): its time per product in milliseconds
  * Uses the handle's workspace (allocated for k if needed; its blocks are overwritten).
  * Synchronises `stream`. Errors: OFSC_ERR_INVALID_ARG, OFSC_ERR_OOM, OFSC_ERR_CUDA.
  */
 ofsc_status ofsc_autotune(ofsc_graph* g, int32_t k, int32_t gather, int32_t* warps_out, int32_t* slots_out,
-                          double* ms_out, void* stream);
+                          int32_t* merge_out, double* ms_out, void* stream);
 
 /*
  * ofsc_weight_grad - gradient of f1 (Eq. (2)) or f2 (Eq. (3)) at X with respect to the weight of

@@ -108,6 +108,8 @@ void workspace_free(Workspace& ws) {
   dev_free(ws.colpart);
   dev_free(ws.dE);
   dev_free(ws.bimg);
+  dev_free(ws.carry_row);
+  dev_free(ws.carry);
   dev_free(ws.solve);
   dev_free(ws.ctrl);
   if (ws.ctrl_host) cudaFreeHost(ws.ctrl_host);
@@ -135,6 +137,7 @@ ofsc_status ofsc_graph_free(ofsc_graph* g) {
   ofsc::dev_free(g->dinv);
   ofsc::dev_free(g->deg);
   for (int i = 0; i < 6; ++i) ofsc::dev_free(g->bnd[i]);
+  ofsc::dev_free(g->mp);
   if (g->stream) cudaStreamDestroy(g->stream);
   cudaSetDevice(prev);
   delete g;

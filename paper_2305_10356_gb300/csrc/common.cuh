@@ -166,7 +166,8 @@ struct Workspace {
   double* R64 = nullptr;        // kp*kp: X^T X of the current X (exact recurrence, FP64)
   double* B64 = nullptr;        // kp*kp: X^T A X of the current X (f2 methods)
   double* dots = nullptr;       // [spmm blocks][2][kp]: partial diag(V^T AV), diag(V^T AX)
-  float* part_tc = nullptr;     // tensor-core Gram partials (kp > 64)
+  float* part_tc = nullptr;     // tensor-core Gram partials (sized for kp > 64, or when a call
+  size_t part_tc_bytes = 0;     // forces the tensor-core Grams at a smaller kp)
   CUtensorMap vh_map[2];        // TMA maps over Vh as FP32 [0] and BF16 [1] (gather4 rows)
   bool vh_map_ok[2] = {false, false};
   float* alpha = nullptr;       // kp
@@ -181,6 +182,8 @@ struct Workspace {
   double* colpart = nullptr;    // [row_blocks][5][kp]
   double* dE = nullptr;         // kp: diag(V^T AX) (f1 methods)
   void* bimg = nullptr;         // kp = 128: B operand images of the f2 tensor-core direction pass
+  int64_t* carry_row = nullptr; // [kRowMaxWarps][2]: split rows of the merge-path product
+  float* carry = nullptr;       // [kRowMaxWarps][2][kp]: their partial sums
   double* solve = nullptr;      // line-search scratch: per-block trace partials, diagonals, cubics
   Ctrl* ctrl = nullptr;
   Ctrl* ctrl_host = nullptr;    // pinned
@@ -205,9 +208,14 @@ struct ofsc_graph {
   int device = 0;
   // The direction product's shape chosen by ofsc_autotune for one padded width and gather storage:
   // gathers in flight per lane (0: the kernel's default); the row partition is bnd[kRowPart].
+  // Merge-path shares of the direction product's warps (mp[2 groups + 2], recomputed with the row
+  // partition) and the longest row's nonzeros: rows longer than a warp's share use them.
+  int64_t* mp = nullptr;
+  int64_t max_row = 0;
   int dir_tuned_kp = 0;
   int dir_tuned_bf16 = 0;
   int dir_slots = 0;
+  int dir_mp = 0;  // 1: merge path timed faster, -1: whole rows, 0: untuned
   int64_t* row_ptr = nullptr;  // [n+1]
   int32_t* col = nullptr;      // [nnz]
   float* val = nullptr;        // [nnz] or null

@@ -187,16 +187,25 @@ struct Scratch {
 ofsc_status set_row_partition(ofsc_graph* g, int warps, cudaStream_t s) {
   if (warps < 1 || warps > kRowMaxWarps) return fail(OFSC_ERR_INVALID_ARG, "row partition: %d warps", warps);
   int64_t* nb = nullptr;
+  int64_t* nmp = nullptr;
   OFSC_CUDA(dev_alloc(&nb, (size_t)(warps + 1) * sizeof(int64_t)));
-  k_partition<<<grid_for(warps + 1), 256, 0, s>>>(g->n, g->row_ptr, warps, nb);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = dev_alloc(&nmp, (size_t)(2 * warps + 2) * sizeof(int64_t));
+  if (e == cudaSuccess) {
+    k_partition<<<grid_for(warps + 1), 256, 0, s>>>(g->n, g->row_ptr, warps, nb);
+    e = cudaGetLastError();
+  }
+  // the merge-path shares follow the same warp count (the product reads mp[0 .. 2 warps + 1])
+  if (e == cudaSuccess) e = merge_partition(g->n, g->row_ptr, warps, nmp, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
     dev_free(nb);
+    dev_free(nmp);
     return cuda_fail(e, "row partition");
   }
   dev_free(g->bnd[kRowPart]);  // synchronises with any queued use of the old ranges
+  dev_free(g->mp);
   g->bnd[kRowPart] = nb;
+  g->mp = nmp;
   g->groups[kRowPart] = warps;
   return OFSC_OK;
 }
@@ -355,7 +364,16 @@ extern "C" ofsc_status ofsc_graph_build(int64_t n, int64_t m, const int32_t* src
     k_partition<<<grid_for(g->groups[i] + 1), 256, 0, stream>>>(n, g->row_ptr, g->groups[i], g->bnd[i]);
     OFSC_LAUNCH_CHECK("k_partition");
   }
+  // the merge-path shares of the direction product's warps, and the longest row
+  OFSC_CUDA(dev_alloc(&g->mp, (size_t)(2 * g->groups[kRowPart] + 2) * sizeof(int64_t)));
+  OFSC_CUDA(merge_partition(n, g->row_ptr, g->groups[kRowPart], g->mp, stream));
+  unsigned long long* d_max = (unsigned long long*)d_counts;  // the counts were read above
+  OFSC_CUDA(cudaMemsetAsync(d_max, 0, sizeof(unsigned long long), stream));
+  OFSC_CUDA(max_row_length(n, g->row_ptr, d_max, stream));
+  unsigned long long h_max = 0;
+  OFSC_CUDA(cudaMemcpyAsync(&h_max, d_max, sizeof(h_max), cudaMemcpyDeviceToHost, stream));
   OFSC_CUDA(cudaStreamSynchronize(stream));
+  g->max_row = (int64_t)h_max;
   guard.keep = true;
   *out = g;
   return OFSC_OK;

@@ -1163,8 +1163,20 @@ thread_local int64_t g_launches = 0;  // kernels launched by the current call on
 
 // The direction product, counted among the call's launches; slots > 0: a tuned shape.
 int spmm_dir(const SpmmArgs& a, bool weighted, bool bf16, int slots, cudaStream_t s) {
-  ++g_launches;
+  g_launches += a.mp ? 2 : 1;  // the merge-path form adds the fixup of split rows
   return launch_spmm_dir(a, weighted, bf16, slots, s);
+}
+
+// Whether the direction product runs on the merge-path shares: forced on or off by `setting`
+// (> 0, < 0); else the form ofsc_autotune timed faster for this padded width and gather storage;
+// else when the longest row holds at least 1024 nonzeros and more than four warps' shares (the
+// warp that takes it whole then runs a chain of at least 128 dependent gather steps, several
+// times as long as the other warps').
+bool use_merge_path(const ofsc_graph* g, int setting, int kp, bool bf16) {
+  if (g->mp == nullptr || g->nnz <= 0 || g->groups[kRowPart] <= 0) return false;
+  if (setting != 0) return setting > 0;
+  if (g->dir_mp != 0 && g->dir_tuned_kp == kp && g->dir_tuned_bf16 == (bf16 ? 1 : 0)) return g->dir_mp > 0;
+  return g->max_row >= 1024 && g->max_row * g->groups[kRowPart] > 4 * g->nnz;
 }
 
 // The gathers in flight per lane that ofsc_autotune chose for this padded width and gather storage
@@ -1343,6 +1355,12 @@ cudaError_t launch_gram(Workspace& ws, const GramPairs& pairs, int npairs, int s
   return cudaGetLastError();
 }
 
+// Bytes of the tensor-core Gram partials for n rows (two or four right blocks per launch).
+size_t gram_tc_part_need(int64_t n) {
+  return std::max(gram_tc_part_bytes(n, 2, gram_tc_rows_per_cta(n, 2)),
+                  gram_tc_part_bytes(n, 4, gram_tc_rows_per_cta(n, 4)));
+}
+
 ofsc_status ensure_workspace(ofsc_graph* g, int kp) {
   Workspace& ws = g->ws;
   if (ws.kp == kp && ws.n == g->n && ws.X) return OFSC_OK;
@@ -1375,9 +1393,7 @@ ofsc_status ensure_workspace(ofsc_graph* g, int kp) {
       {(void**)&ws.R64, kk * sizeof(double)},
       {(void**)&ws.B64, kk * sizeof(double)},
       {(void**)&ws.dots, (size_t)((kRowMaxWarps + kRowWarpsPerBlock) + kVpassMaxBlocks + 2 * kDotsRows) * kp * sizeof(double)},
-      {(void**)&ws.part_tc, kp > 64 ? std::max(gram_tc_part_bytes(n, 2, gram_tc_rows_per_cta(n, 2)),
-                                               gram_tc_part_bytes(n, 4, gram_tc_rows_per_cta(n, 4)))
-                                    : (size_t)16},
+      {(void**)&ws.part_tc, kp > 64 ? gram_tc_part_need(n) : (size_t)16},
       {(void**)&ws.alpha, kp * sizeof(float)},
       {(void**)&ws.beta, kp * sizeof(float)},
       {(void**)&ws.alpha64, kp * sizeof(double)},
@@ -1387,6 +1403,8 @@ ofsc_status ensure_workspace(ofsc_graph* g, int kp) {
       {(void**)&ws.colpart, (size_t)(kMaxRowBlocks + kDotsRows) * kColSums * kp * sizeof(double)},
       {(void**)&ws.dE, (size_t)kp * sizeof(double)},
       {(void**)&ws.bimg, kp == 128 ? (size_t)(4 * 4 * 128 * 32 * 4) : (size_t)16},
+      {(void**)&ws.carry_row, (size_t)kRowMaxWarps * 2 * sizeof(int64_t)},
+      {(void**)&ws.carry, (size_t)kRowMaxWarps * 2 * kp * sizeof(float)},
       {(void**)&ws.solve, (size_t)(kSolveBlocks * kSolveSums + 8 * kp) * sizeof(double)},
       {(void**)&ws.ctrl, sizeof(Ctrl)},
   };
@@ -1404,7 +1422,23 @@ ofsc_status ensure_workspace(ofsc_graph* g, int kp) {
     workspace_free(ws);
     return cuda_fail(e, "cudaMallocHost");
   }
+  ws.part_tc_bytes = kp > 64 ? gram_tc_part_need(n) : (size_t)16;
   ws.bytes = total;
+  return OFSC_OK;
+}
+
+// The tensor-core Gram partials for a call that forces the tensor-core Grams at kp <= 64 (the
+// workspace holds them only for kp > 64): grown once, kept with the workspace.
+ofsc_status ensure_part_tc(Workspace& ws) {
+  const size_t need = gram_tc_part_need(ws.n);
+  if (ws.part_tc_bytes >= need) return OFSC_OK;
+  float* p = nullptr;
+  cudaError_t e = dev_alloc(&p, need);
+  if (e != cudaSuccess) return cuda_fail(e, "tensor-core Gram partials");
+  dev_free(ws.part_tc);  // synchronises with any queued use of the old buffer
+  ws.bytes += need - ws.part_tc_bytes;
+  ws.part_tc = p;
+  ws.part_tc_bytes = need;
   return OFSC_OK;
 }
 
@@ -1417,6 +1451,7 @@ struct Runner {
   Prof& prof;
   bool tc = false;   // Grams on the tensor cores
   bool tc_dir = true;  // with tc: the direction pass on the tensor cores too (padded k = 128)
+  bool mp = false;     // the direction product on the merge-path shares (rows longer than a share)
   bool tma = false;  // sparse product with TMA gather4
 
   // L^T R_b for b < nr into the gram slots, on the tensor cores or the CUDA cores
@@ -1471,6 +1506,17 @@ struct Runner {
     return a;
   }
 
+  // The warp-per-row product's arguments on the direction partition, merge-path when chosen.
+  void dir_partition(SpmmArgs& a) const {
+    a.bnd = g->bnd[kRowPart];
+    a.groups = g->groups[kRowPart];
+    if (mp) {
+      a.mp = g->mp;
+      a.carry_row = ws.carry_row;
+      a.carry = ws.carry;
+    }
+  }
+
   // AX from X exactly, then X^T X and X^T AX; Rn, Bn and f of `objective` from them.
   // (The gather copy Vh of the current direction is dead here: the next V pass rewrites it, so
   // it holds D^-1/2 X for the warp-per-row product.)
@@ -1481,8 +1527,7 @@ struct Runner {
                    s>>>(ws.n, ws.kp, ws.X, g->dinv, Xh, ws.ctrl, ignore_done);
     ++g_launches;
     SpmmArgs a = spmm_base();
-    a.bnd = g->bnd[kRowPart];
-    a.groups = g->groups[kRowPart];
+    dir_partition(a);
     a.gather = Xh;
     a.base = ws.X;
     a.out = ws.Y;
@@ -1589,8 +1634,7 @@ struct Runner {
       ++g_launches;
       dots_blocks = t.groups / spmm_tma_groups_per_block();
     } else {
-      a.bnd = g->bnd[kRowPart];
-      a.groups = g->groups[kRowPart];
+      dir_partition(a);
       dots_blocks = spmm_dir(a, g->weighted != 0, bf16, tuned_slots(g, ws.kp, bf16), s);
     }
     k_dots_fold<<<kDotsRows, 256, 0, s>>>(dots_w, dots_blocks, dots_g, vgrid, ws.kp, folded, ws.ctrl);
@@ -1691,6 +1735,7 @@ extern "C" ofsc_status ofsc_objective_grad(ofsc_graph* g, int32_t objective, int
   const int method = objective == OFSC_F1 ? M_OFM_F1 : M_OFM_F2;
   Prof prof{ws, nullptr, s};
   Runner run{g, ws, s, method, false, prof};
+  run.mp = use_merge_path(g, 0, kp, false);
   run.tc = kp > 64;
   // a single evaluation: the direction pass in plain FP32 on the CUDA cores (the iteration's
   // tensor-core pass accumulates its K = 128 or 256 products in FP32 tensor memory)
@@ -1740,6 +1785,7 @@ extern "C" ofsc_status ofsc_weight_grad(ofsc_graph* g, int32_t objective, int32_
   Workspace& ws = g->ws;
   Prof prof{ws, nullptr, s};
   Runner run{g, ws, s, objective == OFSC_F1 ? M_OFM_F1 : M_OFM_F2, false, prof};
+  run.mp = use_merge_path(g, 0, kp, false);
   run.tc = kp > 64;
   DevBuf sbuf;
   OFSC_CUDA(dev_alloc(&sbuf.p, (size_t)(g->n + 1) * sizeof(float) + 16));
@@ -1799,6 +1845,7 @@ extern "C" ofsc_status ofsc_rayleigh_ritz(ofsc_graph* g, int32_t k, const float*
   Workspace& ws = g->ws;
   Prof prof{ws, nullptr, s};
   Runner run{g, ws, s, M_OFM_F1, false, prof};
+  run.mp = use_merge_path(g, 0, kp, false);
   run.tc = kp > 64;
   DevBuf wbuf;
   OFSC_CUDA(dev_alloc(&wbuf.p, (4 * (size_t)kp * kp + 2) * sizeof(double)));
@@ -1859,6 +1906,7 @@ ofsc_status check_iterate_args(const ofsc_graph* g, int32_t method, int32_t k, c
   if (o.spin_limit < 0) return fail(OFSC_ERR_INVALID_ARG, "%s: spin_limit < 0", who);
   if (o.withhold_arrivals != 0 && o.withhold_arrivals != 1)
     return fail(OFSC_ERR_INVALID_ARG, "%s: withhold_arrivals must be 0 or 1", who);
+  if (o.merge_path < -1 || o.merge_path > 1) return fail(OFSC_ERR_INVALID_ARG, "%s: merge_path must be -1, 0 or 1", who);
   const int kp = round_up(k, 8);
   const bool tc = o.gram_engine == OFSC_GRAM_TC || (o.gram_engine == OFSC_GRAM_AUTO && kp > 64);
   if (tc && kp > 128) return fail(OFSC_ERR_INVALID_ARG, "%s: tensor-core Grams need k <= 128", who);
@@ -1930,6 +1978,11 @@ struct Job {
     Workspace& ws = g->ws;
     run.tc = o.gram_engine == OFSC_GRAM_TC || (o.gram_engine == OFSC_GRAM_AUTO && kp > 64);
     run.tma = o.spmm_engine == OFSC_SPMM_TMA;
+    run.mp = use_merge_path(g, o.merge_path, kp, run.bf16);
+    if (run.tc) {
+      st = ensure_part_tc(ws);
+      if (st != OFSC_OK) return st;
+    }
     if (run.tma) {
       const int mi = run.bf16 ? 1 : 0;
       if (!ws.vh_map_ok[mi]) {
@@ -2099,7 +2152,8 @@ extern "C" ofsc_status ofsc_iterate(ofsc_graph* g, int32_t method, int32_t k, fl
 // ==========================================================================================
 
 extern "C" ofsc_status ofsc_autotune(ofsc_graph* g, int32_t k, int32_t gather, int32_t* warps_out,
-                                     int32_t* slots_out, double* ms_out, void* stream_) {
+                                     int32_t* slots_out, int32_t* merge_out, double* ms_out,
+                                     void* stream_) {
   clear_error();
   NvtxRange nv("ofsc_autotune");
   if (!g) return fail(OFSC_ERR_INVALID_ARG, "ofsc_autotune: graph is NULL");
@@ -2112,6 +2166,7 @@ extern "C" ofsc_status ofsc_autotune(ofsc_graph* g, int32_t k, int32_t gather, i
   if (g->n == 0 || g->nnz == 0) {
     if (warps_out) *warps_out = g->groups[kRowPart];
     if (slots_out) *slots_out = dir_default_slots(kp, bf16, g->weighted != 0);
+    if (merge_out) *merge_out = 0;
     if (ms_out) *ms_out = 0.0;
     return OFSC_OK;
   }
@@ -2139,6 +2194,7 @@ extern "C" ofsc_status ofsc_autotune(ofsc_graph* g, int32_t k, int32_t gather, i
   int opts[4];
   const int nopt = dir_slot_options(kp, bf16, opts);
   int best_w = 0, best_u = 0;
+  bool best_mp = false;
   float best_ms = 0.0f;
   for (int wps = min_wps; wps <= max_wps; wps *= 2) {
     const int W = wps * kNumSMs;
@@ -2160,8 +2216,16 @@ extern "C" ofsc_status ofsc_autotune(ofsc_graph* g, int32_t k, int32_t gather, i
     a.dots = ws.dots;
     a.ctrl = ws.ctrl;
     a.ignore_done = 1;
-    for (int oi = 0; oi < nopt; ++oi) {
-      const int u = opts[oi];
+    // the whole-row shapes, then (option index nopt) the merge-path split with the default slots
+    for (int oi = 0; oi <= nopt; ++oi) {
+      const bool mp = oi == nopt;
+      if (mp && g->nnz == 0) break;
+      const int u = mp ? 0 : opts[oi];
+      if (mp) {
+        a.mp = g->mp;  // set_row_partition recomputed the shares for W warps
+        a.carry_row = ws.carry_row;
+        a.carry = ws.carry;
+      }
       launch_spmm_dir(a, g->weighted != 0, bf16, u, s);  // warm
       OFSC_CUDA(cudaEventRecord(e0, s));
       for (int r = 0; r < 3; ++r) launch_spmm_dir(a, g->weighted != 0, bf16, u, s);
@@ -2173,7 +2237,8 @@ extern "C" ofsc_status ofsc_autotune(ofsc_graph* g, int32_t k, int32_t gather, i
       ms /= 3.0f;
       if (best_w == 0 || ms < best_ms) {
         best_w = W;
-        best_u = u;
+        best_u = mp ? dir_default_slots(kp, bf16, g->weighted != 0) : u;
+        best_mp = mp;
         best_ms = ms;
       }
     }
@@ -2184,9 +2249,11 @@ extern "C" ofsc_status ofsc_autotune(ofsc_graph* g, int32_t k, int32_t gather, i
   }
   g->dir_tuned_kp = kp;
   g->dir_tuned_bf16 = bf16 ? 1 : 0;
-  g->dir_slots = best_u;
+  g->dir_slots = best_mp ? 0 : best_u;
+  g->dir_mp = best_mp ? 1 : -1;
   if (warps_out) *warps_out = best_w;
   if (slots_out) *slots_out = best_u;
+  if (merge_out) *merge_out = best_mp ? 1 : 0;
   if (ms_out) *ms_out = best_ms;
   return OFSC_OK;
 }

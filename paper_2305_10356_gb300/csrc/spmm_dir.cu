@@ -2,6 +2,8 @@
 // W = A V = -V - D^-1/2 S D^-1/2 V with A = L - 2I (Eq. (1)), gathering Vh = D^-1/2 V.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace ofsc {
@@ -99,8 +101,9 @@ __host__ __device__ constexpr int dir_slots() {
 }
 
 // UU: gathers in flight per lane (0: the default of dir_slots; other values are the shapes the
-// autotuner may pick).
-template <int LPN, int VPL, bool WEIGHTED, bool BF16, bool DOTS, int UU>
+// autotuner may pick). MP: the warps take the merge-path shares a.mp (a long row can span warps;
+// the partial sums of a row a warp does not both start and finish go to a.carry).
+template <int LPN, int VPL, bool WEIGHTED, bool BF16, bool DOTS, int UU, bool MP>
 __global__ void __launch_bounds__(32 * kRowWarpsPerBlock,
                                   (VPL == 4 ? OFSC_ROW_WARPS_F32 : OFSC_ROW_WARPS_BF16) / kRowWarpsPerBlock)
     k_spmm_dir(SpmmArgs a) {
@@ -127,12 +130,30 @@ __global__ void __launch_bounds__(32 * kRowWarpsPerBlock,
     for (int i = 0; i < VPL; ++i) rr[c + i] = 0.0f;
   }
   if (gw < a.groups) {
-    int l = (int)a.bnd[gw];  // column indices are int32, so n < 2^31
-    const int rb = (int)a.bnd[gw + 1];
+    int l, rb;  // rows [l, rb) (column indices are int32, so n < 2^31)
+    int64_t pend, pb;
+    bool cut_head = false;  // MP: the first row began in an earlier warp
+    if (MP) {
+      const int64_t i1 = a.mp[gw + 1];
+      l = (int)a.mp[gw];
+      pb = a.mp[a.groups + 1 + gw];
+      pend = a.mp[a.groups + 2 + gw];
+      // rows l .. i1 - 1 end in this warp; row i1 as well if the warp holds some of its nonzeros
+      rb = (int)((i1 < a.n && pend > a.row_ptr[i1]) ? i1 + 1 : i1);
+      cut_head = l < rb && pb > a.row_ptr[l];
+      if (lane == 0) {
+        a.carry_row[2 * (int64_t)gw] = -1;
+        a.carry_row[2 * (int64_t)gw + 1] = -1;
+      }
+    } else {
+      l = (int)a.bnd[gw];
+      rb = (int)a.bnd[gw + 1];
+      pend = l < rb ? a.row_ptr[rb] : 0;
+      pb = l < rb ? a.row_ptr[l] : 0;
+    }
     if (l < rb) {
-      const int64_t pend = a.row_ptr[rb];
-      int64_t pb = a.row_ptr[l];
-      int64_t p1 = a.row_ptr[l + 1];
+      int64_t e1 = a.row_ptr[l + 1];      // where the current row ends
+      int64_t p1 = MP ? min(e1, pend) : e1;  // where this warp stops in it
       int jl = 0;
       float wl = 1.0f;
       {
@@ -168,8 +189,11 @@ __global__ void __launch_bounds__(32 * kRowWarpsPerBlock,
         }
         const int64_t pn = last ? p1 : pb + STEP;
         const bool more = !last || l + 1 < rb;
-        int64_t p1n = p1;
-        if (last && more) p1n = a.row_ptr[l + 2];
+        int64_t p1n = p1, e1n = e1;
+        if (last && more) {
+          e1n = a.row_ptr[l + 2];
+          p1n = MP ? min(e1n, pend) : e1n;
+        }
         if (more) {
           const int64_t i = pn + lane;
           jl = 0;
@@ -186,7 +210,17 @@ __global__ void __launch_bounds__(32 * kRowWarpsPerBlock,
           for (int off = LPN; off < 32; off <<= 1)
 #pragma unroll
             for (int i = 0; i < VPL; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], off);
-          if (lane < LPN && active) {
+          const bool cut_tail = MP && p1 < e1;  // the row goes on in a later warp
+          if (MP && (cut_head || cut_tail)) {
+            // a share of a split row: its partial sum for k_spmm_fixup (slot 1: unfinished here)
+            const int64_t slot = 2 * (int64_t)gw + (cut_tail ? 1 : 0);
+            if (lane < LPN && active) {
+#pragma unroll
+              for (int i = 0; i < VPL; i += 4)
+                *(float4*)(a.carry + slot * a.kp + c + i) = make_float4(acc[i], acc[i + 1], acc[i + 2], acc[i + 3]);
+            }
+            if (lane == 0) a.carry_row[slot] = (cut_tail && cut_head) ? -((int64_t)l + 2) : (int64_t)l;
+          } else if (lane < LPN && active) {
             float r[VPL];
 #pragma unroll
             for (int i = 0; i < VPL; ++i) r[i] = -fmaf(s, acc[i], base[i]);
@@ -199,8 +233,10 @@ __global__ void __launch_bounds__(32 * kRowWarpsPerBlock,
             }
           }
           if (!more) break;
+          cut_head = false;
           ++l;
           p1 = p1n;
+          e1 = e1n;
 #pragma unroll
           for (int i = 0; i < VPL; ++i) acc[i] = 0.0f;
         }
@@ -214,25 +250,99 @@ __global__ void __launch_bounds__(32 * kRowWarpsPerBlock,
   }
 }
 
-template <int LPN, int VPL, bool WEIGHTED, bool BF16, bool DOTS, int UU>
+// Rows split across warps by the merge-path shares: the warp that starts a row and leaves it
+// unfinished adds, in warp order, its partial sums and those of the following warps up to the one
+// that finishes the row, then writes W = -V - D^-1/2 (sum) for the row and adds the row's share of
+// diag(V^T AV) to its own row of dots partials. One warp per warp of the product, four columns
+// per lane (kp <= 128).
+__global__ void __launch_bounds__(256) k_spmm_fixup(SpmmArgs a) {
+  if (!a.ignore_done && a.ctrl->done) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t w = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (w >= a.groups) return;
+  const int64_t r = a.carry_row[2 * w + 1];
+  if (r < 0) return;  // no row that this warp started and left unfinished
+  const int c = lane * 4;
+  const bool active = c < a.kp;
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (active) acc = *(const float4*)(a.carry + (2 * w + 1) * a.kp + c);
+  for (int64_t w2 = w + 1; w2 < a.groups; ++w2) {
+    const bool mid = a.carry_row[2 * w2 + 1] == -(r + 2);  // a share inside the row
+    const int64_t slot = mid ? 2 * w2 + 1 : 2 * w2;
+    if (!mid && a.carry_row[2 * w2] != r) break;
+    if (active) {
+      const float4 v = *(const float4*)(a.carry + slot * a.kp + c);
+      acc = make_float4(acc.x + v.x, acc.y + v.y, acc.z + v.z, acc.w + v.w);
+    }
+    if (!mid) break;  // the warp that finishes the row
+  }
+  if (!active) return;
+  const float sr = a.dinv[r];
+  const float4 b = *(const float4*)(a.base + r * a.kp + c);
+  const float4 o = make_float4(-fmaf(sr, acc.x, b.x), -fmaf(sr, acc.y, b.y), -fmaf(sr, acc.z, b.z),
+                               -fmaf(sr, acc.w, b.w));
+  *(float4*)(a.out + r * a.kp + c) = o;
+  if (a.dots) {
+    double* d = a.dots + w * a.kp + c;
+    d[0] += (double)b.x * (double)o.x;
+    d[1] += (double)b.y * (double)o.y;
+    d[2] += (double)b.z * (double)o.z;
+    d[3] += (double)b.w * (double)o.w;
+  }
+}
+
+// mp[w] = first row and mp[warps + 1 + w] = first nonzero of warp w's share of the merged list of
+// row ends and nonzeros: the point (i, d - i) of diagonal d = w (n + nnz) / warps, with i the
+// number of rows whose end, row_ptr[i + 1] + i in merged order, lies before d.
+__global__ void k_merge_partition(int64_t n, const int64_t* __restrict__ row_ptr, int warps, int64_t* __restrict__ mp) {
+  const int64_t total = n + row_ptr[n];
+  for (int w = blockIdx.x * blockDim.x + threadIdx.x; w <= warps; w += gridDim.x * blockDim.x) {
+    const int64_t d = total * w / warps;
+    int64_t lo = 0, hi = n;  // first i in [0, n] with row_ptr[i + 1] + i >= d (i = n if none)
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (row_ptr[mid + 1] + mid < d) lo = mid + 1;
+      else hi = mid;
+    }
+    mp[w] = lo;
+    mp[warps + 1 + w] = d - lo;
+  }
+}
+
+__global__ void k_max_row(int64_t n, const int64_t* __restrict__ row_ptr, unsigned long long* out) {
+  unsigned long long m = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    m = max(m, (unsigned long long)(row_ptr[i + 1] - row_ptr[i]));
+  for (int off = 16; off > 0; off >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, off));
+  if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(out, m);
+}
+
+template <int LPN, int VPL, bool WEIGHTED, bool BF16, bool DOTS, int UU, bool MP>
 void launch_dir_u(const SpmmArgs& a, cudaStream_t s) {
-  k_spmm_dir<LPN, VPL, WEIGHTED, BF16, DOTS, UU><<<a.groups / kRowWarpsPerBlock, 32 * kRowWarpsPerBlock, 0, s>>>(a);
+  k_spmm_dir<LPN, VPL, WEIGHTED, BF16, DOTS, UU, MP><<<a.groups / kRowWarpsPerBlock, 32 * kRowWarpsPerBlock, 0, s>>>(a);
+  if (MP) k_spmm_fixup<<<(a.groups + 7) / 8, 256, 0, s>>>(a);
 }
 
 // A tuned number of slots in flight (u = 2, 4, 6, 8) only for the product with dots (the direction
 // product of the iteration); u must keep u * 32 / LPN <= 32 nonzeros per step, else the default.
+// The merge-path form (a.mp set) takes the default number of slots.
 template <int LPN, int VPL, bool WEIGHTED, bool BF16>
 void launch_dir_w(const SpmmArgs& a, bool dots, int u, cudaStream_t s) {
   constexpr int NPI = 32 / LPN;
-  if (!dots) return launch_dir_u<LPN, VPL, WEIGHTED, BF16, false, 0>(a, s);
-  if (u == 2) return launch_dir_u<LPN, VPL, WEIGHTED, BF16, true, 2>(a, s);
+  if (a.mp) {
+    if (dots) launch_dir_u<LPN, VPL, WEIGHTED, BF16, true, 0, true>(a, s);
+    else launch_dir_u<LPN, VPL, WEIGHTED, BF16, false, 0, true>(a, s);
+    return;
+  }
+  if (!dots) return launch_dir_u<LPN, VPL, WEIGHTED, BF16, false, 0, false>(a, s);
+  if (u == 2) return launch_dir_u<LPN, VPL, WEIGHTED, BF16, true, 2, false>(a, s);
   if constexpr (4 * NPI <= 32)
-    if (u == 4) return launch_dir_u<LPN, VPL, WEIGHTED, BF16, true, 4>(a, s);
+    if (u == 4) return launch_dir_u<LPN, VPL, WEIGHTED, BF16, true, 4, false>(a, s);
   if constexpr (6 * NPI <= 32)
-    if (u == 6) return launch_dir_u<LPN, VPL, WEIGHTED, BF16, true, 6>(a, s);
+    if (u == 6) return launch_dir_u<LPN, VPL, WEIGHTED, BF16, true, 6, false>(a, s);
   if constexpr (8 * NPI <= 32)
-    if (u == 8) return launch_dir_u<LPN, VPL, WEIGHTED, BF16, true, 8>(a, s);
-  launch_dir_u<LPN, VPL, WEIGHTED, BF16, true, 0>(a, s);
+    if (u == 8) return launch_dir_u<LPN, VPL, WEIGHTED, BF16, true, 8, false>(a, s);
+  launch_dir_u<LPN, VPL, WEIGHTED, BF16, true, 0, false>(a, s);
 }
 
 template <int LPN, int VPL, bool BF16>
@@ -281,6 +391,18 @@ int dir_slot_options(int kp, bool bf16, int* out) {
   for (int u = 2; u <= 8; u += 2)
     if (u * npi <= 32) out[n++] = u;
   return n;
+}
+
+cudaError_t merge_partition(int64_t n, const int64_t* row_ptr, int warps, int64_t* mp, cudaStream_t s) {
+  k_merge_partition<<<(warps + 256) / 256, 256, 0, s>>>(n, row_ptr, warps, mp);
+  return cudaGetLastError();
+}
+
+cudaError_t max_row_length(int64_t n, const int64_t* row_ptr, unsigned long long* max_row, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4 * kNumSMs);
+  k_max_row<<<(int)blocks, 256, 0, s>>>(n, row_ptr, max_row);
+  return cudaGetLastError();
 }
 
 int launch_spmm_dir(const SpmmArgs& a, bool weighted, bool bf16, int slots, cudaStream_t s) {

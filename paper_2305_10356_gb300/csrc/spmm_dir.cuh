@@ -25,6 +25,15 @@ struct SpmmArgs {
   double* dots;        // direction with dots: [blocks][kp] partials of diag(V^T AV)
   Ctrl* ctrl;
   int ignore_done;
+  // Merge-path split (k_spmm_dir only; NULL: the row ranges of bnd): mp[0 .. groups] are the first
+  // rows and mp[groups + 1 .. 2 groups + 1] the first nonzeros of the warps' equal shares of the
+  // rows + nonzeros, so a long row can span warps. A warp's partial sums of a row it does not
+  // finish, or did not start, go to carry (row ids in carry_row: [warp][2], -1 none; slot 0 the
+  // row the warp finishes, slot 1 the row it leaves unfinished, as r if it started it, else
+  // -(r + 2)), and k_spmm_fixup adds them in warp order and writes those rows.
+  const int64_t* mp;
+  int64_t* carry_row;  // [groups][2]
+  float* carry;        // [groups][2][kp]
 };
 
 // The direction product (spmm_dir.cu): lanes per nonzero for rows of kp values with vpl values per
@@ -34,5 +43,9 @@ int dir_lanes(int kp, int vpl);
 int dir_default_slots(int kp, bool bf16, bool weighted);
 int dir_slot_options(int kp, bool bf16, int* out);
 int launch_spmm_dir(const SpmmArgs& a, bool weighted, bool bf16, int slots, cudaStream_t s);
+// The merge-path partition of `warps` warps over the rows + nonzeros of row_ptr into mp[2 warps + 2],
+// and the largest row (nonzeros) into *max_row (device int64, atomically maximised: zero it first).
+cudaError_t merge_partition(int64_t n, const int64_t* row_ptr, int warps, int64_t* mp, cudaStream_t s);
+cudaError_t max_row_length(int64_t n, const int64_t* row_ptr, unsigned long long* max_row, cudaStream_t s);
 
 }  // namespace ofsc

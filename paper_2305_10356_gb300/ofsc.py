@@ -55,7 +55,8 @@ class Opts(ctypes.Structure):
                 ("spmm_engine", ctypes.c_int32), ("direct_launch", ctypes.c_int32),
                 ("cg_restart", ctypes.c_int32), ("refine_tol", ctypes.c_double),
                 ("exact_tail", ctypes.c_double), ("vscale_exp", ctypes.c_int32),
-                ("spin_limit", ctypes.c_int64), ("withhold_arrivals", ctypes.c_int32)]
+                ("spin_limit", ctypes.c_int64), ("withhold_arrivals", ctypes.c_int32),
+                ("merge_path", ctypes.c_int32)]
 
 
 class Result(ctypes.Structure):
@@ -103,7 +104,8 @@ def lib() -> ctypes.CDLL:
                                      i32, ctypes.POINTER(Opts), ctypes.POINTER(Result), vp],
             "ofsc_rayleigh_ritz": [vp, i32, vp, vp, ctypes.POINTER(dbl), vp],
             "ofsc_unrolled_grad": [vp, i32, vp, i32, i32, i64, vp, vp, ctypes.POINTER(dbl), vp, vp, vp],
-            "ofsc_autotune": [vp, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(dbl), vp],
+            "ofsc_autotune": [vp, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
+                              ctypes.POINTER(dbl), vp],
             "ofsc_weight_grad": [vp, i32, i32, vp, i64, vp, vp, vp, vp],
             "ofsc_row_normalize": [i64, i32, vp, vp],
             "ofsc_gram": [i64, i32, i32, vp, i32, ctypes.POINTER(vp), i64, vp, vp],
@@ -243,14 +245,15 @@ def ofsc_iterate(g: Graph, method: int, X, tol: float, maxit: int, *, gather: in
                  profile: Profile | None = None, gram_engine: int = GRAM_AUTO,
                  spmm_engine: int = SPMM_AUTO, cg_restart: bool = False, refine_tol: float = 0.0,
                  exact_tail: float = 0.0, vscale_exp: int = 0, direct_launch: bool = False,
-                 spin_limit: int = 0, withhold_arrivals: bool = False, stream=None) -> Result:
+                 spin_limit: int = 0, withhold_arrivals: bool = False, merge_path: int = 0,
+                 stream=None) -> Result:
     """Algorithm 2 in place on the device block X (n x k, FP32). Returns the ofsc_result."""
     px = _arg(X, "X", "float32", rows=_rows(g))
     o = Opts(gather, y_refresh, check_every, alpha0, _arg(trace, "trace", "float64"),
              0 if trace is None else int(trace.shape[0]),
              ctypes.pointer(profile) if profile is not None else None, gram_engine, spmm_engine,
              1 if direct_launch else 0, 1 if cg_restart else 0, float(refine_tol), float(exact_tail),
-             int(vscale_exp), int(spin_limit), 1 if withhold_arrivals else 0)
+             int(vscale_exp), int(spin_limit), 1 if withhold_arrivals else 0, int(merge_path))
     r = Result()
     _check(lib().ofsc_iterate(g.handle, method, int(X.shape[1]), px, float(tol), int(maxit),
                               ctypes.byref(o), ctypes.byref(r), _stream(stream)),
@@ -262,7 +265,8 @@ def ofsc_iterate_batched(graphs: list[Graph], method: int, Xs: list, tol: float,
                          gather: int = GATHER_FP32, y_refresh: int = 0, check_every: int = 0,
                          alpha0: float = 0.0, gram_engine: int = GRAM_AUTO, spmm_engine: int = SPMM_AUTO,
                          direct_launch: bool = False, cg_restart: bool = False, refine_tol: float = 0.0,
-                         exact_tail: float = 0.0, vscale_exp: int = 0, stream=None) -> list[Result]:
+                         exact_tail: float = 0.0, vscale_exp: int = 0, merge_path: int = 0,
+                         stream=None) -> list[Result]:
     """Algorithm 2 in place on every device block Xs[i] (n_i x k_i, FP32) of the graphs, in one
     call. Returns one ofsc_result per problem, in order."""
     count = len(graphs)
@@ -270,7 +274,7 @@ def ofsc_iterate_batched(graphs: list[Graph], method: int, Xs: list, tol: float,
         raise ValueError("ofsc_iterate_batched: one X per graph")
     o = Opts(gather, y_refresh, check_every, alpha0, None, 0, None, gram_engine, spmm_engine,
              1 if direct_launch else 0, 1 if cg_restart else 0, float(refine_tol), float(exact_tail),
-             int(vscale_exp))
+             int(vscale_exp), 0, 0, int(merge_path))
     hs = (ctypes.c_void_p * count)(*[g.handle for g in graphs])
     ks = (ctypes.c_int32 * count)(*[int(X.shape[1]) for X in Xs])
     xs = (ctypes.c_void_p * count)(*[_arg(X, f"Xs[{i}]", "float32", rows=_rows(g))
@@ -290,14 +294,19 @@ def ofsc_gram(L, Rs, out, k: int | None = None, rows_per_block: int = 0, stream=
                            _arg(out, "out", "float64"), _stream(stream)))
 
 
-def ofsc_autotune(g: Graph, k: int, gather: int = GATHER_FP32, stream=None) -> tuple[int, int, float]:
-    """Times the direction product at several row partitions and gathers in flight per lane, keeps
-    the fastest in the handle; returns (warps, slots per lane, ms per product)."""
+def ofsc_autotune(g: Graph, k: int, gather: int = GATHER_FP32, stream=None,
+                  with_merge: bool = False) -> tuple:
+    """Times the direction product at several row partitions and gathers in flight per lane, and
+    the merge-path split at each partition; keeps the fastest in the handle. Returns (warps, slots
+    per lane, ms per product), or (warps, slots, merge path chosen, ms) with with_merge."""
     w = ctypes.c_int32(0)
     u = ctypes.c_int32(0)
+    mp = ctypes.c_int32(0)
     ms = ctypes.c_double(0.0)
-    _check(lib().ofsc_autotune(g.handle, int(k), int(gather), ctypes.byref(w), ctypes.byref(u), ctypes.byref(ms),
-                               _stream(stream)))
+    _check(lib().ofsc_autotune(g.handle, int(k), int(gather), ctypes.byref(w), ctypes.byref(u), ctypes.byref(mp),
+                               ctypes.byref(ms), _stream(stream)))
+    if with_merge:
+        return w.value, u.value, bool(mp.value), ms.value
     return w.value, u.value, ms.value
 
 

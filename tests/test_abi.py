@@ -49,11 +49,11 @@ def test_host_side_argument_checks_of_the_widened_entry_points(lib):
     assert lib.ofsc_iterate_batched(2, None, 0, None, None, 0.0, 1, None, None, None) == ofsc.ERR_INVALID_ARG
     assert lib.ofsc_iterate_batched(0, None, 0, None, None, 0.0, 1, None, None, None) == ofsc.OK
     assert lib.ofsc_unrolled_grad(None, 4, None, 3, 0, 0, None, None, None, None, None, None) == ofsc.ERR_INVALID_ARG
-    assert lib.ofsc_autotune(None, 4, 0, None, None, None, None) == ofsc.ERR_INVALID_ARG
+    assert lib.ofsc_autotune(None, 4, 0, None, None, None, None, None) == ofsc.ERR_INVALID_ARG
     assert lib.ofsc_weight_grad(None, 1, 4, None, 0, None, None, None, None) == ofsc.ERR_INVALID_ARG
     assert lib.ofsc_rayleigh_ritz(None, 4, None, None, None, None) == ofsc.ERR_INVALID_ARG
     w = i32(0)
-    assert lib.ofsc_autotune(None, 4, 0, ctypes.byref(w), None, None, None) == ofsc.ERR_INVALID_ARG
+    assert lib.ofsc_autotune(None, 4, 0, ctypes.byref(w), None, None, None, None) == ofsc.ERR_INVALID_ARG
 
 
 def test_no_cpu_fallback_when_library_missing(monkeypatch, tmp_path):

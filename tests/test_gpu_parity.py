@@ -504,6 +504,105 @@ def test_direction_product_all_lane_widths_weighted(k):
     np.testing.assert_allclose(tr[:4, 3:3 + k], np.array(ref.alphas[:4]), rtol=1e-4, atol=1e-7)
 
 
+def hub_graph(weighted, seed):
+    """An SBM of 6,000 nodes with one hub joined to 4,000 random nodes: the hub's row holds about
+    30 times a warp's share of the nonzeros (608 warps for about 80,000 stored entries)."""
+    e = synth.sbm(6000, 6, 12.0, 6.0, ratio_kind="count", weighted=weighted, seed=seed)
+    rng = np.random.default_rng(seed + 1)
+    leaves = rng.choice(np.arange(1, e.n), 4000, replace=False).astype(np.int32)
+    src = np.concatenate([e.src, np.zeros(4000, np.int32)])
+    dst = np.concatenate([e.dst, leaves])
+    w = None if e.w is None else np.concatenate([e.w, rng.uniform(0.5, 1.5, 4000).astype(np.float32)])
+    return dataclasses.replace(e, src=src, dst=dst, w=w)
+
+
+@pytest.mark.parametrize("k,gather,weighted", [(20, 0, True), (44, 0, False), (128, 1, False), (128, 0, True)])
+def test_merge_path_splits_hub_rows(k, gather, weighted):
+    """The direction product on merge-path shares (a long row spans several warps; their partial
+    sums are added in warp order by the fixup): on a graph with a hub row of 4,000 nonzeros the first
+    five updates match the oracle element by element (chosen automatically and forced), agree with
+    the whole-row partition within FP32 rounding, repeat bit for bit, and the objective and gradient
+    on the same graph match the oracle."""
+    import torch
+    e = hub_graph(weighted, 170 + k)
+    og = o.build_graph(e.n, e.src, e.dst, e.w)
+    assert og.row_ptr[1] - og.row_ptr[0] >= 4000
+    g = gpu_graph(e)
+    x0 = synth.initial_block(e.n, k, 171)
+    ref = o.iterate(og, o.OFM_F1, x0, 0.0, 5)
+    rtol = 2e-3 if gather else 1e-4
+    # At k = 128 the default engines are the tensor cores' (3-term TF32 Grams and direction pass).
+    # On this graph their rounding (the first step within 3e-6 of the oracle's, against 2e-8 on
+    # the CUDA cores) grows to a few 1e-4 in one column's step by the fifth update, beyond the
+    # 1e-4 element bound; so the three forms meet the oracle on the CUDA-core engines, and on the
+    # default engines they agree with each other and with the oracle's first step.
+    eng = dict(gram_engine=ofsc.GRAM_SIMT) if k > 64 and not gather else {}
+    Xa, ra, ta = run_iterate(g, o.OFM_F1, x0, 0.0, 5, trace_cap=6, gather=gather, **eng)             # automatic
+    Xm, rm, tm = run_iterate(g, o.OFM_F1, x0, 0.0, 5, trace_cap=6, gather=gather, merge_path=1, **eng)
+    Xr, rr, tr = run_iterate(g, o.OFM_F1, x0, 0.0, 5, trace_cap=6, gather=gather, merge_path=-1, **eng)
+    Xm2, _, tm2 = run_iterate(g, o.OFM_F1, x0, 0.0, 5, trace_cap=6, gather=gather, merge_path=1, **eng)
+    for name, X in (("automatic", Xa), ("merge path", Xm), ("whole rows", Xr)):
+        assert_elementwise(X, ref.X, rtol, name)
+    assert np.array_equal(Xa, Xm) and np.array_equal(ta, tm)  # the hub makes the automatic choice merge path
+    assert np.array_equal(Xm, Xm2) and np.array_equal(tm, tm2)
+    assert np.linalg.norm(Xm - Xr) <= (1e-3 if gather else 1e-5) * np.linalg.norm(Xr)
+    if eng:
+        Xmt, _, tmt = run_iterate(g, o.OFM_F1, x0, 0.0, 5, trace_cap=6, merge_path=1)
+        Xrt, _, _ = run_iterate(g, o.OFM_F1, x0, 0.0, 5, trace_cap=6, merge_path=-1)
+        np.testing.assert_allclose(tmt[0, 3:3 + k], ref.alphas[0], rtol=1e-5)
+        assert np.linalg.norm(Xmt - Xrt) <= 1e-5 * np.linalg.norm(Xrt)
+        assert np.linalg.norm(Xmt - ref.X) <= 1e-4 * np.linalg.norm(ref.X)
+    X = torch.from_numpy(x0).cuda()
+    G = torch.empty_like(X)
+    f = ofsc.ofsc_objective_grad(g, 1, X, G)
+    x64 = x0.astype(np.float64)
+    AX = o.apply_A(og, x64)
+    assert f == pytest.approx(o.objective(1, x64, AX, o.normA_fro2(og)), rel=1e-5)
+    G_ref = o.gradient(1, x64, AX)
+    assert np.abs(G.cpu().numpy() - G_ref).max() <= 1e-5 * np.abs(G_ref).max()
+
+
+@pytest.mark.parametrize("k", [20, 64])
+def test_forced_tensor_core_grams_at_small_k(k):
+    """gram_engine = OFSC_GRAM_TC below k = 64, where the workspace does not hold the tensor-core
+    Gram partials until a call asks for them: five updates match the oracle element by element and
+    the CUDA-core Grams within FP32 rounding, and a following default call is unaffected."""
+    e = synth.sbm(5000, 6, 16.0, 5.0, ratio_kind="count", seed=200 + k)
+    og = o.build_graph(e.n, e.src, e.dst)
+    g = gpu_graph(e)
+    x0 = synth.initial_block(e.n, k, 201)
+    ref = o.iterate(og, o.OFM_F1, x0, 0.0, 5)
+    Xs, rs, ts = run_iterate(g, o.OFM_F1, x0, 0.0, 5, trace_cap=6)  # the default (CUDA-core) Grams
+    Xt, rt, tt = run_iterate(g, o.OFM_F1, x0, 0.0, 5, trace_cap=6, gram_engine=ofsc.GRAM_TC)
+    Xs2, rs2, ts2 = run_iterate(g, o.OFM_F1, x0, 0.0, 5, trace_cap=6)
+    assert rt.status == ofsc.ERR_NOT_CONVERGED and rt.iterations == 5
+    assert_elementwise(Xt, ref.X, 1e-4, "tensor-core Grams")
+    assert np.linalg.norm(Xt - Xs) <= 1e-5 * np.linalg.norm(Xs)
+    assert np.array_equal(Xs, Xs2) and np.array_equal(ts, ts2)
+
+
+@pytest.mark.parametrize("k,gather", [(32, 0), (128, 1)])
+def test_autotune_times_the_merge_path_split(k, gather):
+    """ofsc_autotune also times the merge-path split at every row partition (which reallocates and
+    recomputes the warps' shares with the partition); later calls with merge_path = 0 take its
+    choice: the result repeats bit for bit the run that forces that form, and matches the oracle
+    element by element."""
+    e = hub_graph(False, 190 + k)
+    og = o.build_graph(e.n, e.src, e.dst)
+    g = gpu_graph(e)
+    x0 = synth.initial_block(e.n, k, 191)
+    ref = o.iterate(og, o.OFM_F1, x0, 0.0, 5)
+    w, u, mp, ms = ofsc.ofsc_autotune(g, k, gather, with_merge=True)
+    assert w in [m * 152 for m in (4, 8, 16, 32)] and ms > 0.0
+    Xa, _, ta = run_iterate(g, o.OFM_F1, x0, 0.0, 5, trace_cap=6, gather=gather)
+    Xf, _, tf = run_iterate(g, o.OFM_F1, x0, 0.0, 5, trace_cap=6, gather=gather, merge_path=1 if mp else -1)
+    assert np.array_equal(Xa, Xf) and np.array_equal(ta, tf)
+    assert_elementwise(Xa, ref.X, 2e-3 if gather else 1e-4)
+    # the other form on the tuned partition agrees within rounding
+    Xo, _, _ = run_iterate(g, o.OFM_F1, x0, 0.0, 5, gather=gather, merge_path=-1 if mp else 1)
+    assert np.linalg.norm(Xo - Xa) <= (1e-3 if gather else 1e-5) * np.linalg.norm(Xa)
+
+
 @pytest.mark.parametrize("gather,k", [(0, 64), (1, 64), (0, 128)])
 def test_iterations_are_bitwise_repeatable(gather, k):
     """Every reduction has a fixed shape (per-block partials summed in block order, no atomics), so

@@ -403,9 +403,11 @@ def c1_leg(stream) -> dict:
 
 def batched_leg(stream, tol: float = 1e-4, iters: int = 300, steps: int = 2) -> dict:
     """The 32-graph batch (sbm_batch32, N from 3.5K to 99K, k from 8 to 64), every graph to
-    tol (relative direction norm, at most `iters` updates): one ofsc_iterate_batched call against a
-    loop of one ofsc_iterate call per graph (both run the same updates of every graph, bit for bit),
-    timed with CUDA events over `steps` steps after one warm-up."""
+    tol (relative direction norm, at most `iters` updates): one ofsc_iterate_batched call (one
+    launch per graph and kernel on the graphs' streams, replayed), the same call with grouped
+    launches (one launch per kernel over the blocks of the graphs of each of 4 lanes), and a loop
+    of one ofsc_iterate call per graph (all three run the same updates of every graph, bit for
+    bit), timed with CUDA events over `steps` steps after one warm-up."""
     import torch
     from paper_2305_10356_gb300 import ofsc, synth
     probs = synth.batch("sbm_batch32", 1.0)
@@ -415,10 +417,10 @@ def batched_leg(stream, tol: float = 1e-4, iters: int = 300, steps: int = 2) -> 
         X0s.append(torch.from_numpy(x0).cuda())
     Xs = [torch.empty_like(x) for x in X0s]
 
-    def batched():
+    def batched(group=0):
         for X, X0 in zip(Xs, X0s):
             X.copy_(X0)
-        return sum(r.iterations for r in ofsc.ofsc_iterate_batched(graphs, 0, Xs, tol, iters))
+        return sum(r.iterations for r in ofsc.ofsc_iterate_batched(graphs, 0, Xs, tol, iters, group_launches=group))
 
     def loop():
         n = 0
@@ -429,7 +431,7 @@ def batched_leg(stream, tol: float = 1e-4, iters: int = 300, steps: int = 2) -> 
 
     out = {"workload": f"sbm_batch32: {len(probs)} SBMs, sum N = {sum(x.shape[0] for x in X0s)}, OFM-f1, "
                        f"every graph to tol {tol:g} (at most {iters} updates), FP32"}
-    for name, fn in (("batched", batched), ("loop", loop)):
+    for name, fn in (("batched", batched), ("batched_grouped_launches", lambda: batched(4)), ("loop", loop)):
         fn()
         torch.cuda.synchronize()
         t0 = torch.cuda.Event(enable_timing=True)
@@ -536,10 +538,11 @@ def run_batch(args):
     Xs = [torch.empty_like(x) for x in X0s]
     stream = torch.cuda.current_stream()
 
-    def step_batched(direct=False):
+    def step_batched(direct=False, group=0):
         for X, X0 in zip(Xs, X0s):
             X.copy_(X0)
-        rs = ofsc.ofsc_iterate_batched(graphs, method, Xs, 0.0, args.iters, gather=gather, direct_launch=direct)
+        rs = ofsc.ofsc_iterate_batched(graphs, method, Xs, 0.0, args.iters, gather=gather, direct_launch=direct,
+                                       group_launches=group)
         return sum(r.iterations for r in rs), sum(r.kernel_launches for r in rs) + len(Xs)
 
     def step_loop():
@@ -580,6 +583,7 @@ def run_batch(args):
         return ups * world / (ms / 1000.0), ms / args.steps, launches, clocks
 
     value, ms, launches, clocks = timed(step_batched, with_clocks=True)
+    grouped, ms_grouped, launches_grouped, _ = timed(lambda: step_batched(group=4))
     direct, ms_direct, _, _ = timed(lambda: step_batched(True))
     loop, ms_loop, _, _ = timed(step_loop)
 
@@ -614,6 +618,8 @@ def run_batch(args):
                 "impl": "gpu", "e2e": {"value": e2e_v, "unit": "iterations/s (summed over graphs)",
                                        "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
                 "clocks": clocks, "gpu_launches": launches,
+                "batched_grouped_launches": {"value": grouped, "ms_per_step": ms_grouped, "lanes": 4,
+                                             "gpu_launches": launches_grouped},
                 "batched_direct_launch": {"value": direct, "ms_per_step": ms_direct},
                 "per_graph_loop": {"value": loop, "ms_per_step": ms_loop},
                 "parallelism": "replicas only" if world > 1 else "single GPU"}

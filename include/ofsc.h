@@ -226,6 +226,12 @@ typedef struct {
                             longest row holds at least 1024 nonzeros and more than four warps'
                             shares of the row partition; else by whole rows; 1: always by merge
                             path; -1: never */
+  int32_t group_launches; /* replayed updates: 0 (default) one launch per graph and kernel, on
+                            the graphs' own streams; n in [1, 64]: grouped launches, where one
+                            launch runs a kernel of the update for up to 32 graphs, its blocks a
+                            work list of (graph, block) pairs, with the same results bit for bit;
+                            the graphs are dealt into n lanes of similar work, grouped within a
+                            lane, and the lanes overlap */
 } ofsc_opts;
 
 typedef struct {
@@ -234,7 +240,8 @@ typedef struct {
   double rel_dir_norm;  /* ||g(X)||_F / ||g(X_0)||_F at the returned X (AX recomputed exactly) */
   double g0_norm;       /* ||g(X_0)||_F */
   double f;             /* objective of the method (f1 or f2) at the returned X */
-  int64_t kernel_launches; /* device kernels this call launched */
+  int64_t kernel_launches; /* device kernels this call launched (in a batch, a grouped launch
+                              serving several graphs is counted once, for the first of them) */
   int32_t refined_at;   /* first update of the FP32 refinement sweep (opts->refine_tol), or -1 */
   int32_t exact_at;     /* first update of the exact tail (opts->exact_tail), or -1 */
 } ofsc_result;

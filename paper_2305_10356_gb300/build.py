@@ -11,8 +11,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libofsc.so")
-SOURCES = ["api.cu", "graph.cu", "iterate.cu", "spmm_dir.cu", "cluster.cu", "gram_tc.cu", "spmm_tma.cu", "direction_tc.cu", "ritz.cu", "wgrad.cu", "unroll.cu"]
-HEADERS = [os.path.join(CSRC, "common.cuh"), os.path.join(CSRC, "spmm_dir.cuh"), os.path.join(CSRC, "tcgen05.cuh"), os.path.join(CSRC, "cubic.cuh"), os.path.join(ROOT, "include", "ofsc.h")]
+SOURCES = ["api.cu", "graph.cu", "iterate.cu", "spmm_dir.cu", "cluster.cu", "gram_tc.cu", "spmm_tma.cu", "direction_tc.cu", "ritz.cu", "wgrad.cu", "unroll.cu", "group.cu"]
+HEADERS = [os.path.join(CSRC, "common.cuh"), os.path.join(CSRC, "spmm_dir.cuh"), os.path.join(CSRC, "tcgen05.cuh"), os.path.join(CSRC, "cubic.cuh"), os.path.join(CSRC, "group.cuh"), os.path.join(CSRC, "spmm_dir_body.inc"), os.path.join(CSRC, "direction_body.inc"), os.path.join(ROOT, "include", "ofsc.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I", os.path.join(ROOT, "include")]

@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "group.cuh"
 #include "cubic.cuh"
 
 namespace ofsc {
@@ -205,13 +206,24 @@ __global__ void k_scale_rows(int64_t n, int kp, const float* __restrict__ X, con
 // Folds the per-block partials of diag(V^T AV) (pw: nw rows of kp) and of diag(V^T G) (pg: ng
 // rows) into gridDim.x rows of out[r][2][kp]: row r sums the blocks [r nb / R, (r + 1) nb / R) of
 // each source in order, so the result does not depend on scheduling.
-__global__ void k_dots_fold(const double* __restrict__ pw, int nw, const double* __restrict__ pg, int ng, int kp,
-                            double* __restrict__ out, const Ctrl* ctrl) {
-  if (ctrl->done) return;
+struct DotsFoldArgs {
+  const double* pw;
+  const double* pg;
+  double* out;
+  const Ctrl* ctrl;
+  int nw, ng, kp;
+};
+
+__device__ __forceinline__ void dots_fold_body(const DotsFoldArgs& a, const VBlock vb) {
+  const double* __restrict__ pw = a.pw;
+  const double* __restrict__ pg = a.pg;
+  double* __restrict__ out = a.out;
+  const int nw = a.nw, ng = a.ng, kp = a.kp;
+  if (a.ctrl->done) return;
   // 2 kp <= blockDim.x columns; blockDim.x / (2 kp) lane groups split this block's rows and are
   // combined in group order
   __shared__ double red[256];
-  const int r = blockIdx.x, R = gridDim.x, width = 2 * kp, groups = blockDim.x / width;
+  const int r = vb.x, R = vb.gx, width = 2 * kp, groups = blockDim.x / width;
   const int t = threadIdx.x % width, l = threadIdx.x / width;
   if (l < groups) {
     const int which = t / kp, j = t % kp;
@@ -230,6 +242,14 @@ __global__ void k_dots_fold(const double* __restrict__ pw, int nw, const double*
   }
 }
 
+__global__ void k_dots_fold(const __grid_constant__ DotsFoldArgs a) { dots_fold_body(a, hw_block()); }
+
+__global__ void k_dots_fold_g(const __grid_constant__ GroupParams<DotsFoldArgs> p) {
+  VBlock vb;
+  const DotsFoldArgs& a = group_find(p, &vb);
+  dots_fold_body(a, vb);
+}
+
 // V_t = -G_t + V_{t-1} diag(beta) (V_0 = -G_0), stored as V_t diag(1 / s_t) (column scales s_t from
 // k_beta: the FP32 coefficients are vinv = 1 / s_t and beta s_{t-1} / s_t), its gather copy
 // Vh = D^-1/2 V_t (FP32 or BF16) and
@@ -237,12 +257,31 @@ __global__ void k_dots_fold(const double* __restrict__ pw, int nw, const double*
 // alpha = 0. LPN lanes cover a row (four columns each, fixed per thread), 256 / LPN rows per
 // block step; each thread sums its columns over its rows, and the block adds its row groups in
 // order in FP64 into dots_g[blockIdx.x][kp].
+struct VpassArgs {
+  int64_t n;
+  const float* G;
+  float* V;
+  void* Vh;
+  const float* dinv;
+  const float* beta;
+  const float* vinv;
+  double* dots_g;
+  Ctrl* ctrl;
+  int kp, first;
+};
+
 template <int LPN, bool BF16>
-__global__ void __launch_bounds__(256) k_vpass(int64_t n, int kp, const float* __restrict__ G, float* __restrict__ V,
-                                               void* __restrict__ Vh, const float* __restrict__ dinv,
-                                               const float* __restrict__ beta, const float* __restrict__ vinv,
-                                               int first, double* __restrict__ dots_g, Ctrl* ctrl) {
-  if (ctrl->done) return;
+__device__ __forceinline__ void vpass_body(const VpassArgs& a, const VBlock vb) {
+  const int64_t n = a.n;
+  const int kp = a.kp, first = a.first;
+  const float* __restrict__ G = a.G;
+  float* __restrict__ V = a.V;
+  void* __restrict__ Vh = a.Vh;
+  const float* __restrict__ dinv = a.dinv;
+  const float* __restrict__ beta = a.beta;
+  const float* __restrict__ vinv = a.vinv;
+  double* __restrict__ dots_g = a.dots_g;
+  if (a.ctrl->done) return;
   constexpr int RPB = 256 / LPN;
   constexpr int W = 4 * LPN;
   __shared__ float red[RPB * W];
@@ -255,7 +294,7 @@ __global__ void __launch_bounds__(256) k_vpass(int64_t n, int kp, const float* _
     iv = *(const float4*)(vinv + c);  // powers of two: exact
   }
   if (active) {
-    for (int64_t row = (int64_t)blockIdx.x * RPB + rg; row < n; row += (int64_t)gridDim.x * RPB) {
+    for (int64_t row = (int64_t)vb.x * RPB + rg; row < n; row += (int64_t)vb.gx * RPB) {
       const int64_t e = row * kp + c;
       const float4 g = *(const float4*)(G + e);
       float4 v = make_float4(-g.x * iv.x, -g.y * iv.y, -g.z * iv.z, -g.w * iv.w);
@@ -289,8 +328,20 @@ __global__ void __launch_bounds__(256) k_vpass(int64_t n, int kp, const float* _
   for (int j = threadIdx.x; j < kp; j += blockDim.x) {
     double sum = 0.0;
     for (int r = 0; r < RPB; ++r) sum += (double)red[r * W + j];
-    dots_g[(int64_t)blockIdx.x * kp + j] = sum;
+    dots_g[(int64_t)vb.x * kp + j] = sum;
   }
+}
+
+template <int LPN, bool BF16>
+__global__ void __launch_bounds__(256) k_vpass(const __grid_constant__ VpassArgs a) {
+  vpass_body<LPN, BF16>(a, hw_block());
+}
+
+template <int LPN, bool BF16>
+__global__ void __launch_bounds__(256) k_vpass_g(const __grid_constant__ GroupParams<VpassArgs> p) {
+  VBlock vb;
+  const VpassArgs& a = group_find(p, &vb);
+  vpass_body<LPN, BF16>(a, vb);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -330,176 +381,23 @@ struct DirShape {
 
 template <int METHOD, int KPMAX>
 __global__ void __launch_bounds__(kRowThreads, OFSC_DIR_MINB) k_direction(RowArgs a) {
-  if (!a.ignore_done && a.ctrl->done) return;
-  constexpr bool F2 = METHOD >= M_OFM_F2;
-  constexpr bool TRI = METHOD == M_TRI_F1 || METHOD == M_TRI_F2;
-  using Sh = DirShape<KPMAX, F2>;
-  extern __shared__ __align__(16) float sm[];
-  const int kp = a.kp;
-  float* Rs = sm;                                       // row m at m * KPMAX
-  float* Bs = Rs + KPMAX * KPMAX;                       // F2 only
-  float* stage = sm + Sh::kk_floats;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int slot = lane / Sh::LPR;
-  const int c = (lane % Sh::LPR) * 4;
-  const bool active = c < kp;
-  float* sx = stage + (size_t)(warp * Sh::S + slot) * Sh::SSTR * Sh::NSTAGE;
-  float* sy = sx + Sh::SSTR;                            // F2 only
-  float* __restrict__ Xp = a.X;
-  float* __restrict__ Yp = a.Y;
-  const float* __restrict__ Vp = a.V;
-  const float* __restrict__ Wp = a.W;
-  float* __restrict__ Gp = a.G;
+#define OFSC_VB_X blockIdx.x
+#define OFSC_VB_GX gridDim.x
+#include "direction_body.inc"
+#undef OFSC_VB_X
+#undef OFSC_VB_GX
+}
 
-  for (int i = tid; i < kp * KPMAX; i += blockDim.x) {
-    const int m = i / KPMAX, j = i % KPMAX;
-    const bool keep = j < kp && (!TRI || m <= j);       // triu(.) keeps m <= j
-    Rs[i] = keep ? a.Rn[m * kp + j] : 0.0f;
-    if (F2) Bs[i] = keep ? a.Bn[m * kp + j] : 0.0f;
-  }
-  float4 al = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (a.update && active) al = *(const float4*)(a.alpha + c);
-  if (a.update && blockIdx.x == 0 && tid == 0) a.ctrl->it += 1;
-  __syncthreads();
-
-  // per-lane running column sums (FP32: a lane adds one row-batch partial at a time)
-  float sgg[4] = {0, 0, 0, 0}, snum[4] = {0, 0, 0, 0}, sden[4] = {0, 0, 0, 0};
-  float sgy[4] = {0, 0, 0, 0}, svy[4] = {0, 0, 0, 0}, svg[4] = {0, 0, 0, 0};
-  const int64_t nwarps = (int64_t)gridDim.x * (kRowThreads / 32);
-  const int64_t nbatch = (a.n + Sh::ROWS - 1) / Sh::ROWS;
-  for (int64_t b = (int64_t)blockIdx.x * (kRowThreads / 32) + warp; b < nbatch; b += nwarps) {
-    const int64_t row0 = b * Sh::ROWS + (int64_t)slot * kKPB;
-    // issue every global load of the batch before any store or arithmetic
-    float4 x[kKPB], y[kKPB], v[kKPB], w[kKPB], gp[kKPB];
-#pragma unroll
-    for (int i = 0; i < kKPB; ++i) {
-      const int64_t r = row0 + i;
-      const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-      const bool ok = active && r < a.n;
-      x[i] = ok ? *(const float4*)(Xp + r * kp + c) : z;
-      y[i] = ok ? *(const float4*)(Yp + r * kp + c) : z;
-      v[i] = (ok && (a.update || a.need_vy)) ? *(const float4*)(Vp + r * kp + c) : z;
-      w[i] = (ok && a.update) ? *(const float4*)(Wp + r * kp + c) : z;
-      gp[i] = (ok && !a.eval) ? *(const float4*)(Gp + r * kp + c) : z;
-    }
-    if (a.update) {
-#pragma unroll
-      for (int i = 0; i < kKPB; ++i) {
-        const int64_t r = row0 + i;
-        x[i] = make_float4(fmaf(al.x, v[i].x, x[i].x), fmaf(al.y, v[i].y, x[i].y), fmaf(al.z, v[i].z, x[i].z),
-                           fmaf(al.w, v[i].w, x[i].w));
-        y[i] = make_float4(fmaf(al.x, w[i].x, y[i].x), fmaf(al.y, w[i].y, y[i].y), fmaf(al.z, w[i].z, y[i].z),
-                           fmaf(al.w, w[i].w, y[i].w));
-        if (active && r < a.n) {
-          *(float4*)(Xp + r * kp + c) = x[i];
-          *(float4*)(Yp + r * kp + c) = y[i];
-        }
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < kKPB; ++i) {
-      *(float4*)(sx + i * KPMAX + c) = x[i];
-      if (F2) *(float4*)(sy + i * KPMAX + c) = y[i];
-    }
-    __syncwarp();
-    float4 acc[kKPB];
-#pragma unroll
-    for (int i = 0; i < kKPB; ++i) acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int m = 0; m < kp; m += 4) {
-      const float4 r0 = *(const float4*)(Rs + (m + 0) * KPMAX + c);
-      const float4 r1 = *(const float4*)(Rs + (m + 1) * KPMAX + c);
-      const float4 r2 = *(const float4*)(Rs + (m + 2) * KPMAX + c);
-      const float4 r3 = *(const float4*)(Rs + (m + 3) * KPMAX + c);
-      float4 b0, b1, b2, b3;
-      if (F2) {
-        b0 = *(const float4*)(Bs + (m + 0) * KPMAX + c);
-        b1 = *(const float4*)(Bs + (m + 1) * KPMAX + c);
-        b2 = *(const float4*)(Bs + (m + 2) * KPMAX + c);
-        b3 = *(const float4*)(Bs + (m + 3) * KPMAX + c);
-      }
-#pragma unroll
-      for (int i = 0; i < kKPB; ++i) {
-        // f1: acc = x R (triu for TriOFM); f2: acc = x B + y R (triu for TriOFM)
-        const float4 xm = *(const float4*)(sx + i * KPMAX + m);
-        const float4 p0 = F2 ? b0 : r0, p1 = F2 ? b1 : r1, p2 = F2 ? b2 : r2, p3 = F2 ? b3 : r3;
-        float4 t = acc[i];
-        t.x = fmaf(xm.x, p0.x, t.x); t.y = fmaf(xm.x, p0.y, t.y); t.z = fmaf(xm.x, p0.z, t.z); t.w = fmaf(xm.x, p0.w, t.w);
-        t.x = fmaf(xm.y, p1.x, t.x); t.y = fmaf(xm.y, p1.y, t.y); t.z = fmaf(xm.y, p1.z, t.z); t.w = fmaf(xm.y, p1.w, t.w);
-        t.x = fmaf(xm.z, p2.x, t.x); t.y = fmaf(xm.z, p2.y, t.y); t.z = fmaf(xm.z, p2.z, t.z); t.w = fmaf(xm.z, p2.w, t.w);
-        t.x = fmaf(xm.w, p3.x, t.x); t.y = fmaf(xm.w, p3.y, t.y); t.z = fmaf(xm.w, p3.z, t.z); t.w = fmaf(xm.w, p3.w, t.w);
-        if (F2) {
-          const float4 ym = *(const float4*)(sy + i * KPMAX + m);
-          t.x = fmaf(ym.x, r0.x, t.x); t.y = fmaf(ym.x, r0.y, t.y); t.z = fmaf(ym.x, r0.z, t.z); t.w = fmaf(ym.x, r0.w, t.w);
-          t.x = fmaf(ym.y, r1.x, t.x); t.y = fmaf(ym.y, r1.y, t.y); t.z = fmaf(ym.y, r1.z, t.z); t.w = fmaf(ym.y, r1.w, t.w);
-          t.x = fmaf(ym.z, r2.x, t.x); t.y = fmaf(ym.z, r2.y, t.y); t.z = fmaf(ym.z, r2.z, t.z); t.w = fmaf(ym.z, r2.w, t.w);
-          t.x = fmaf(ym.w, r3.x, t.x); t.y = fmaf(ym.w, r3.y, t.y); t.z = fmaf(ym.w, r3.z, t.z); t.w = fmaf(ym.w, r3.w, t.w);
-        }
-        acc[i] = t;
-      }
-    }
-    __syncwarp();  // the stage is rewritten by the next batch
-    float tg[4] = {0, 0, 0, 0}, tn[4] = {0, 0, 0, 0}, td[4] = {0, 0, 0, 0};
-    float ty[4] = {0, 0, 0, 0}, tv[4] = {0, 0, 0, 0}, tw[4] = {0, 0, 0, 0};
-#pragma unroll
-    for (int i = 0; i < kKPB; ++i) {
-      const int64_t r = row0 + i;
-      if (!active || r >= a.n) continue;
-      const float yv[4] = {y[i].x, y[i].y, y[i].z, y[i].w};
-      const float vv[4] = {v[i].x, v[i].y, v[i].z, v[i].w};
-      const float av[4] = {acc[i].x, acc[i].y, acc[i].z, acc[i].w};
-      float g[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        if (METHOD == M_OFM_F1) g[q] = 4.0f * (yv[q] + av[q]);           // Eq. (5)
-        else if (METHOD == M_TRI_F1) g[q] = yv[q] + av[q];                // Eq. (7)
-        else if (METHOD == M_OFM_F2) g[q] = 4.0f * yv[q] - 2.0f * av[q];  // Eq. (10)
-        else g[q] = 2.0f * yv[q] - av[q];                                 // Eq. (12)
-      }
-      const int64_t o = r * kp + c;
-      const float gpv[4] = {gp[i].x, gp[i].y, gp[i].z, gp[i].w};
-      *(float4*)(Gp + o) = make_float4(g[0], g[1], g[2], g[3]);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        tg[q] = fmaf(g[q], g[q], tg[q]);
-        tn[q] = fmaf(g[q] - gpv[q], g[q], tn[q]);
-        td[q] = fmaf(gpv[q], gpv[q], td[q]);
-        ty[q] = fmaf(g[q], yv[q], ty[q]);
-        tv[q] = fmaf(vv[q], yv[q], tv[q]);
-        tw[q] = fmaf(vv[q], g[q], tw[q]);
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      sgg[q] += tg[q];
-      snum[q] += tn[q];
-      sden[q] += td[q];
-      sgy[q] += ty[q];
-      svy[q] += tv[q];
-      svg[q] += tw[q];
-    }
-  }
-  // per-block column sums in a fixed order: (warp, slot) contributions, then over them
-  __syncthreads();
-  double* red = (double*)stage;  // [warps * S][kColSums][KPMAX]
-  const int ws = warp * Sh::S + slot;
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    if (c + q < KPMAX) {
-      red[((size_t)ws * kColSums + 0) * KPMAX + c + q] = (double)sgg[q];
-      red[((size_t)ws * kColSums + 1) * KPMAX + c + q] = (double)snum[q];
-      red[((size_t)ws * kColSums + 2) * KPMAX + c + q] = (double)sden[q];
-      red[((size_t)ws * kColSums + 3) * KPMAX + c + q] = (double)sgy[q];
-      red[((size_t)ws * kColSums + 4) * KPMAX + c + q] = (double)svy[q];
-      red[((size_t)ws * kColSums + 5) * KPMAX + c + q] = (double)svg[q];
-    }
-  }
-  __syncthreads();
-  for (int j = tid; j < kColSums * kp; j += blockDim.x) {
-    const int which = j / kp, col = j % kp;
-    double sum = 0.0;
-    for (int w = 0; w < (kRowThreads / 32) * Sh::S; ++w) sum += red[((size_t)w * kColSums + which) * KPMAX + col];
-    a.colpart[(int64_t)blockIdx.x * kColSums * kp + which * kp + col] = sum;
-  }
+// The same pass for every graph of a batch in one launch (see group.cuh).
+template <int METHOD, int KPMAX>
+__global__ void __launch_bounds__(kRowThreads, OFSC_DIR_MINB) k_direction_g(const __grid_constant__ GroupParams<RowArgs> p) {
+  VBlock vb;
+  const RowArgs& a = group_find(p, &vb);
+#define OFSC_VB_X ((unsigned)vb.x)
+#define OFSC_VB_GX ((unsigned)vb.gx)
+#include "direction_body.inc"
+#undef OFSC_VB_X
+#undef OFSC_VB_GX
 }
 
 // ------------------------------------------------------------------------------------------
@@ -508,10 +406,19 @@ __global__ void __launch_bounds__(kRowThreads, OFSC_DIR_MINB) k_direction(RowArg
 
 // Folds nb rows of width values into gridDim.x rows: row r sums the rows [r nb / R, (r + 1) nb / R)
 // in order (a fixed shape, so the sums do not depend on scheduling).
-__global__ void k_fold_rows(const double* __restrict__ part, int nb, int width, double* __restrict__ out,
-                            const Ctrl* ctrl, int ignore_done) {
-  if (!ignore_done && ctrl->done) return;
-  const int r = blockIdx.x, R = gridDim.x;
+struct FoldArgs {
+  const double* part;
+  double* out;
+  const Ctrl* ctrl;
+  int nb, width, ignore_done;
+};
+
+__device__ __forceinline__ void fold_rows_body(const FoldArgs& a, const VBlock vb) {
+  const double* __restrict__ part = a.part;
+  double* __restrict__ out = a.out;
+  const int nb = a.nb, width = a.width;
+  if (!a.ignore_done && a.ctrl->done) return;
+  const int r = vb.x, R = vb.gx;
   const int b0 = (int)((int64_t)r * nb / R), b1 = (int)((int64_t)(r + 1) * nb / R);
   for (int t = threadIdx.x; t < width; t += blockDim.x) {
     double sum = 0.0;
@@ -521,15 +428,43 @@ __global__ void k_fold_rows(const double* __restrict__ part, int nb, int width, 
   }
 }
 
+__global__ void k_fold_rows(const __grid_constant__ FoldArgs a) { fold_rows_body(a, hw_block()); }
+
+__global__ void k_fold_rows_g(const __grid_constant__ GroupParams<FoldArgs> p) {
+  VBlock vb;
+  const FoldArgs& a = group_find(p, &vb);
+  fold_rows_body(a, vb);
+}
+
 // stop_ok: this update's G came from an exact AX, so meeting tol may stop the run; on an update
 // whose AX came from the recurrence, meeting tol only sets near_tol (the host then schedules an
 // exact update), so a run never stops on a recurrence value.
 // beta (FP32, for the V pass) is the stored-direction coefficient beta_true s_{t-1} / s_t with s the
 // column scales (vscale, updated here in place; vinv = 1 / s_t); beta64 is Algorithm 2's beta.
 // qprev: the Gram V_{t-1}^T V_{t-1} of the stored previous direction (its diagonal bounds |V_t|).
-__global__ void k_beta(const double* __restrict__ colpart, int nblk, int kp, float* beta,
-                       double* beta64, double* dE, Ctrl* ctrl, int first, int eval, int stop_ok,
-                       double* vscale, float* vinv, const double* __restrict__ qprev) {
+struct BetaArgs {
+  const double* colpart;
+  float* beta;
+  double* beta64;
+  double* dE;
+  Ctrl* ctrl;
+  double* vscale;
+  float* vinv;
+  const double* qprev;
+  int nblk, kp, first, eval, stop_ok;
+};
+
+// One block (the grouped twin runs one block per problem).
+__device__ __forceinline__ void beta_body(const BetaArgs& a) {
+  const double* __restrict__ colpart = a.colpart;
+  float* beta = a.beta;
+  double* beta64 = a.beta64;
+  double* dE = a.dE;
+  Ctrl* ctrl = a.ctrl;
+  double* vscale = a.vscale;
+  float* vinv = a.vinv;
+  const double* __restrict__ qprev = a.qprev;
+  const int nblk = a.nblk, kp = a.kp, first = a.first, eval = a.eval, stop_ok = a.stop_ok;
   if (!eval && ctrl->done) return;
   __shared__ double sh[256];
   __shared__ double lanes[256 * kColSums];  // [lane group][kColSums][kp]
@@ -636,6 +571,14 @@ __global__ void k_beta(const double* __restrict__ colpart, int nblk, int kp, flo
   }
 }
 
+__global__ void k_beta(const __grid_constant__ BetaArgs a) { beta_body(a); }
+
+__global__ void k_beta_g(const __grid_constant__ GroupParams<BetaArgs> p) {
+  VBlock vb;
+  const BetaArgs& a = group_find(p, &vb);
+  beta_body(a);
+}
+
 // ------------------------------------------------------------------------------------------
 // Grams L^T R over all rows: per row-group partials with compensated FP32 accumulation
 // ------------------------------------------------------------------------------------------
@@ -688,7 +631,7 @@ struct VecT<4> {
 // Each 32-row chunk is staged in shared memory; the next chunk's float4 loads are issued into
 // registers before the current chunk's FMAs, so global latency overlaps the arithmetic.
 template <int M>
-__global__ void __launch_bounds__(256) k_gram(GramArgs a) {
+__device__ __forceinline__ void gram_body(const GramArgs& a, const VBlock vb) {
   if (!a.ignore_done && a.ctrl->done) return;
   constexpr int T = 16 * M;
   constexpr int NV = kGramChunk * T / 4;          // float4 per operand per chunk
@@ -698,12 +641,12 @@ __global__ void __launch_bounds__(256) k_gram(GramArgs a) {
   const int tid = threadIdx.x;
   const int tx = tid % 16, ty = tid / 16;
   const int nt2 = a.nt * a.nt;
-  const int pair = blockIdx.x / nt2;
-  const int tile = blockIdx.x % nt2;
+  const int pair = vb.x / nt2;
+  const int tile = vb.x % nt2;
   const int i0 = (tile / a.nt) * T, j0 = (tile % a.nt) * T;
   const float* __restrict__ L = a.pairs.L[pair];
   const float* __restrict__ R = a.pairs.R[pair];
-  const int64_t r0 = (int64_t)blockIdx.y * a.rows_per_group;
+  const int64_t r0 = (int64_t)vb.y * a.rows_per_group;
   const int64_t r1 = min(a.n, r0 + a.rows_per_group);
   float s[M][M], cmp[M][M];
 #pragma unroll
@@ -761,7 +704,7 @@ __global__ void __launch_bounds__(256) k_gram(GramArgs a) {
       }
     __syncthreads();
   }
-  double* out = a.part + ((int64_t)blockIdx.y * kPairs + a.pairs.slot[pair]) * a.kp * a.kp;
+  double* out = a.part + ((int64_t)vb.y * kPairs + a.pairs.slot[pair]) * a.kp * a.kp;
 #pragma unroll
   for (int u = 0; u < M; ++u)
 #pragma unroll
@@ -771,15 +714,34 @@ __global__ void __launch_bounds__(256) k_gram(GramArgs a) {
     }
 }
 
+template <int M>
+__global__ void __launch_bounds__(256) k_gram(const __grid_constant__ GramArgs a) { gram_body<M>(a, hw_block()); }
+
+template <int M>
+__global__ void __launch_bounds__(256) k_gram_g(const __grid_constant__ GroupParams<GramArgs> p) {
+  VBlock vb;
+  const GramArgs& a = group_find(p, &vb);
+  gram_body<M>(a, vb);
+}
+
 // Blocks of 32 consecutive entries (one slot each, as kp^2 is a multiple of 64): warp w sums the
 // row groups w, w + 8, ... (coalesced, one entry per lane); the eight warp sums are added in warp
 // order.
-__global__ void __launch_bounds__(256) k_gram_reduce(const double* __restrict__ part, int gy, int kp, int slot_mask,
-                                                     double* __restrict__ gram, Ctrl* ctrl, int ignore_done) {
-  if (!ignore_done && ctrl->done) return;
+struct GramReduceArgs {
+  const double* part;
+  double* gram;
+  Ctrl* ctrl;
+  int gy, kp, slot_mask, ignore_done;
+};
+
+__device__ __forceinline__ void gram_reduce_body(const GramReduceArgs& a, const VBlock vb) {
+  const double* __restrict__ part = a.part;
+  double* __restrict__ gram = a.gram;
+  const int gy = a.gy, kp = a.kp, slot_mask = a.slot_mask;
+  if (!a.ignore_done && a.ctrl->done) return;
   __shared__ double ws[8][32];
   const int kk = kp * kp, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int base = blockIdx.x * 32; base < kPairs * kk; base += gridDim.x * 32) {
+  for (int base = vb.x * 32; base < kPairs * kk; base += vb.gx * 32) {
     if (!((slot_mask >> (base / kk)) & 1)) continue;  // uniform over the block
     const int i = base + lane;
     double s = 0.0;
@@ -793,6 +755,16 @@ __global__ void __launch_bounds__(256) k_gram_reduce(const double* __restrict__ 
     }
     __syncthreads();
   }
+}
+
+__global__ void __launch_bounds__(256) k_gram_reduce(const __grid_constant__ GramReduceArgs a) {
+  gram_reduce_body(a, hw_block());
+}
+
+__global__ void __launch_bounds__(256) k_gram_reduce_g(const __grid_constant__ GroupParams<GramReduceArgs> p) {
+  VBlock vb;
+  const GramReduceArgs& a = group_find(p, &vb);
+  gram_reduce_body(a, vb);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -859,10 +831,10 @@ struct SolveArgs {
 //   v[0..2]   tr B, ||R||_F^2, tr(R B)                         (objective)
 //   v[3..8]   tr(QQ), tr(QP), tr(PP), tr(PP^T), tr(QR), tr(PR)  (OFM-f1 cubic)
 //   v[3..13]  tr(QC) ... tr(RE), tr C, tr E                     (OFM-f2 cubic)
-__global__ void __launch_bounds__(256) k_solve_traces(SolveArgs a) {
+__device__ __forceinline__ void solve_traces_body(const SolveArgs& a, const VBlock vb) {
   if (a.ctrl->done) return;
   __shared__ double sh[15 * 256];
-  const int kp = a.kp, kk = kp * kp, tid = threadIdx.x, b = blockIdx.x, nb = gridDim.x;
+  const int kp = a.kp, kk = kp * kp, tid = threadIdx.x, b = vb.x, nb = vb.gx;
   const bool f2 = is_f2(a.method), tri = is_tri(a.method);
   const double* P = a.gram + G_P * kk;
   const double* Q = a.gram + G_Q * kk;
@@ -969,10 +941,18 @@ __global__ void __launch_bounds__(256) k_solve_traces(SolveArgs a) {
   }
 }
 
+__global__ void __launch_bounds__(256) k_solve_traces(const __grid_constant__ SolveArgs a) { solve_traces_body(a, hw_block()); }
+
+__global__ void __launch_bounds__(256) k_solve_traces_g(const __grid_constant__ GroupParams<SolveArgs> p) {
+  VBlock vb;
+  const SolveArgs& a = group_find(p, &vb);
+  solve_traces_body(a, vb);
+}
+
 // Line search, pass 2 of 3 (one block): f(X_t), the cubic coefficients and their roots, i.e. the
 // step(s) alpha, written to a.alpha / a.alpha64; also the objective, the trace record and the
 // running tr(X^T AX) of the f1 methods.
-__global__ void __launch_bounds__(256) k_solve(SolveArgs a) {
+__device__ __forceinline__ void solve_body(const SolveArgs& a, const VBlock vb) {
   if (a.ctrl->done) return;
   __shared__ double sh[15 * 256];
   __shared__ double coef[kMaxK][4];
@@ -1083,11 +1063,19 @@ __global__ void __launch_bounds__(256) k_solve(SolveArgs a) {
   }
 }
 
+__global__ void __launch_bounds__(256) k_solve(const __grid_constant__ SolveArgs a) { solve_body(a, hw_block()); }
+
+__global__ void __launch_bounds__(256) k_solve_g(const __grid_constant__ GroupParams<SolveArgs> p) {
+  VBlock vb;
+  const SolveArgs& a = group_find(p, &vb);
+  solve_body(a, vb);
+}
+
 // Line search, pass 3 of 3 (solve_blocks(kp) blocks): X' = X + V diag(al), AX' = AX + AV diag(al) give
 //   X'^T X'  = R + diag(al) P + P^T diag(al) + diag(al) Q diag(al)
 //   X'^T AX' = B + E^T diag(al) + diag(al) E + diag(al) C diag(al)
 // element by element in FP64 (each element read and written by one thread, so in place).
-__global__ void __launch_bounds__(256) k_solve_update(SolveArgs a) {
+__device__ __forceinline__ void solve_update_body(const SolveArgs& a, const VBlock vb) {
   if (a.ctrl->done) return;
   __shared__ double al[kMaxK];
   const int kp = a.kp, kk = kp * kp, tid = threadIdx.x;
@@ -1099,7 +1087,7 @@ __global__ void __launch_bounds__(256) k_solve_update(SolveArgs a) {
   const double* sc = a.vscale;
   for (int j = tid; j < kp; j += 256) al[j] = a.alpha64[j];
   __syncthreads();
-  for (int i = blockIdx.x * 256 + tid; i < kk; i += gridDim.x * 256) {
+  for (int i = vb.x * 256 + tid; i < kk; i += vb.gx * 256) {
     const int r = i / kp, c = i % kp;
     const double ar = al[r], ac = al[c];
     const double rn = a.R64[i] + ar * PS(r, c) + PS(c, r) * ac + ar * QS(r, c) * ac;
@@ -1111,6 +1099,14 @@ __global__ void __launch_bounds__(256) k_solve_update(SolveArgs a) {
       a.Bn[i] = (float)bn;
     }
   }
+}
+
+__global__ void __launch_bounds__(256) k_solve_update(const __grid_constant__ SolveArgs a) { solve_update_body(a, hw_block()); }
+
+__global__ void __launch_bounds__(256) k_solve_update_g(const __grid_constant__ GroupParams<SolveArgs> p) {
+  VBlock vb;
+  const SolveArgs& a = group_find(p, &vb);
+  solve_update_body(a, vb);
 }
 #undef SYM
 #undef PS
@@ -1262,10 +1258,27 @@ void launch_spmm(const SpmmArgs& a, bool weighted, cudaStream_t s) {
 
 void launch_vpass(int lpn, bool bf16, int grid, cudaStream_t s, int64_t n, int kp, const float* G, float* V, void* Vh,
                   const float* dinv, const float* beta, const float* vinv, int first, double* dots_g, Ctrl* ctrl) {
-#define OFSC_VPASS(L)                                                                                          \
-  case L:                                                                                                     \
-    if (bf16) k_vpass<L, true><<<grid, 256, 0, s>>>(n, kp, G, V, Vh, dinv, beta, vinv, first, dots_g, ctrl);   \
-    else k_vpass<L, false><<<grid, 256, 0, s>>>(n, kp, G, V, Vh, dinv, beta, vinv, first, dots_g, ctrl);       \
+  VpassArgs a{};
+  a.n = n;
+  a.kp = kp;
+  a.G = G;
+  a.V = V;
+  a.Vh = Vh;
+  a.dinv = dinv;
+  a.beta = beta;
+  a.vinv = vinv;
+  a.first = first;
+  a.dots_g = dots_g;
+  a.ctrl = ctrl;
+#define OFSC_VPASS(L)                                                       \
+  case L:                                                                  \
+    if (bf16) {                                                            \
+      OFSC_GROUPABLE((k_vpass<L, true>), (k_vpass_g<L, true>), VpassArgs);   \
+      k_vpass<L, true><<<grid, 256, 0, s>>>(a);                             \
+    } else {                                                               \
+      OFSC_GROUPABLE((k_vpass<L, false>), (k_vpass_g<L, false>), VpassArgs); \
+      k_vpass<L, false><<<grid, 256, 0, s>>>(a);                            \
+    }                                                                      \
     break;
   switch (lpn) {
     OFSC_VPASS(2)
@@ -1298,6 +1311,7 @@ cudaError_t launch_direction_t(const RowArgs& a, cudaStream_t s, int* nblk_out) 
   int grid = (int)std::min<int64_t>(ceil_div(warps_needed, kRowThreads / 32), (int64_t)blocks_per_sm * kNumSMs);
   if (grid > kMaxRowBlocks) grid = kMaxRowBlocks;
   if (grid < 1) grid = 1;
+  OFSC_GROUPABLE((k_direction<METHOD, KPMAX>), (k_direction_g<METHOD, KPMAX>), RowArgs);
   k_direction<METHOD, KPMAX><<<grid, kRowThreads, smem, s>>>(a);
   ++g_launches;
   *nblk_out = grid;
@@ -1339,17 +1353,34 @@ cudaError_t launch_gram(Workspace& ws, const GramPairs& pairs, int npairs, int s
   dim3 grid(npairs * a.nt * a.nt, gy);
   if (prof) prof->begin(OFSC_PHASE_GRAM);
   switch (gram_m_for(ws.kp)) {
-    case 1: k_gram<1><<<grid, 256, 0, s>>>(a); break;
-    case 2: k_gram<2><<<grid, 256, 0, s>>>(a); break;
-    default: k_gram<4><<<grid, 256, 0, s>>>(a); break;
+    case 1:
+      OFSC_GROUPABLE(k_gram<1>, k_gram_g<1>, GramArgs);
+      k_gram<1><<<grid, 256, 0, s>>>(a);
+      break;
+    case 2:
+      OFSC_GROUPABLE(k_gram<2>, k_gram_g<2>, GramArgs);
+      k_gram<2><<<grid, 256, 0, s>>>(a);
+      break;
+    default:
+      OFSC_GROUPABLE(k_gram<4>, k_gram_g<4>, GramArgs);
+      k_gram<4><<<grid, 256, 0, s>>>(a);
+      break;
   }
   if (prof) {
     prof->end();
     prof->begin(OFSC_PHASE_GRAM_REDUCE);
   }
   const int total = kPairs * ws.kp * ws.kp;
-  k_gram_reduce<<<(int)std::min<int64_t>(ceil_div(total, 32), 8 * kNumSMs), 256, 0, s>>>(
-      ws.gram_part, gy, ws.kp, slot_mask, ws.gram, ws.ctrl, ignore_done);
+  GramReduceArgs ra{};
+  ra.part = ws.gram_part;
+  ra.gy = gy;
+  ra.kp = ws.kp;
+  ra.slot_mask = slot_mask;
+  ra.gram = ws.gram;
+  ra.ctrl = ws.ctrl;
+  ra.ignore_done = ignore_done;
+  OFSC_GROUPABLE(k_gram_reduce, k_gram_reduce_g, GramReduceArgs);
+  k_gram_reduce<<<(int)std::min<int64_t>(ceil_div(total, 32), 8 * kNumSMs), 256, 0, s>>>(ra);
   if (prof) prof->end();
   g_launches += 2;
   return cudaGetLastError();
@@ -1581,13 +1612,35 @@ struct Runner {
     const double* cp = ws.colpart;
     if (nblk > kDotsRows) {
       double* folded = ws.colpart + (size_t)kMaxRowBlocks * kColSums * ws.kp;
-      k_fold_rows<<<kDotsRows, 256, 0, s>>>(ws.colpart, nblk, kColSums * ws.kp, folded, ws.ctrl, eval);
+      FoldArgs fa{};
+      fa.part = ws.colpart;
+      fa.nb = nblk;
+      fa.width = kColSums * ws.kp;
+      fa.out = folded;
+      fa.ctrl = ws.ctrl;
+      fa.ignore_done = eval;
+      OFSC_GROUPABLE(k_fold_rows, k_fold_rows_g, FoldArgs);
+      k_fold_rows<<<kDotsRows, 256, 0, s>>>(fa);
       ++g_launches;
       cp = folded;
       nblk = kDotsRows;
     }
-    k_beta<<<1, 256, 0, s>>>(cp, nblk, ws.kp, ws.beta, ws.beta64, eval ? nullptr : ws.dE, ws.ctrl, first, eval,
-                             stop_ok, ws.vscale, ws.vinv, ws.gram + G_Q * (size_t)ws.kp * ws.kp);
+    BetaArgs ba{};
+    ba.colpart = cp;
+    ba.nblk = nblk;
+    ba.kp = ws.kp;
+    ba.beta = ws.beta;
+    ba.beta64 = ws.beta64;
+    ba.dE = eval ? nullptr : ws.dE;
+    ba.ctrl = ws.ctrl;
+    ba.first = first;
+    ba.eval = eval;
+    ba.stop_ok = stop_ok;
+    ba.vscale = ws.vscale;
+    ba.vinv = ws.vinv;
+    ba.qprev = ws.gram + G_Q * (size_t)ws.kp * ws.kp;
+    OFSC_GROUPABLE(k_beta, k_beta_g, BetaArgs);
+    k_beta<<<1, 256, 0, s>>>(ba);
     ++g_launches;
   }
 
@@ -1637,7 +1690,16 @@ struct Runner {
       dir_partition(a);
       dots_blocks = spmm_dir(a, g->weighted != 0, bf16, tuned_slots(g, ws.kp, bf16), s);
     }
-    k_dots_fold<<<kDotsRows, 256, 0, s>>>(dots_w, dots_blocks, dots_g, vgrid, ws.kp, folded, ws.ctrl);
+    DotsFoldArgs df{};
+    df.pw = dots_w;
+    df.nw = dots_blocks;
+    df.pg = dots_g;
+    df.ng = vgrid;
+    df.kp = ws.kp;
+    df.out = folded;
+    df.ctrl = ws.ctrl;
+    OFSC_GROUPABLE(k_dots_fold, k_dots_fold_g, DotsFoldArgs);
+    k_dots_fold<<<kDotsRows, 256, 0, s>>>(df);
     ++g_launches;
     prof.end();
     // V^T X and V^T V for every method; V^T AX and V^T AV in full for the f2 methods
@@ -1674,6 +1736,9 @@ struct Runner {
     sa.tblocks = solve_blocks(ws.kp);
     sa.vscale = ws.vscale;
     prof.begin(OFSC_PHASE_LINESEARCH);
+    OFSC_GROUPABLE(k_solve_traces, k_solve_traces_g, SolveArgs);
+    OFSC_GROUPABLE(k_solve, k_solve_g, SolveArgs);
+    OFSC_GROUPABLE(k_solve_update, k_solve_update_g, SolveArgs);
     k_solve_traces<<<sa.tblocks, 256, 0, s>>>(sa);
     k_solve<<<1, 256, 0, s>>>(sa);
     k_solve_update<<<sa.tblocks, 256, 0, s>>>(sa);
@@ -1907,6 +1972,8 @@ ofsc_status check_iterate_args(const ofsc_graph* g, int32_t method, int32_t k, c
   if (o.withhold_arrivals != 0 && o.withhold_arrivals != 1)
     return fail(OFSC_ERR_INVALID_ARG, "%s: withhold_arrivals must be 0 or 1", who);
   if (o.merge_path < -1 || o.merge_path > 1) return fail(OFSC_ERR_INVALID_ARG, "%s: merge_path must be -1, 0 or 1", who);
+  if (o.group_launches < 0 || o.group_launches > 64)
+    return fail(OFSC_ERR_INVALID_ARG, "%s: group_launches must be in [0, 64]", who);
   const int kp = round_up(k, 8);
   const bool tc = o.gram_engine == OFSC_GRAM_TC || (o.gram_engine == OFSC_GRAM_AUTO && kp > 64);
   if (tc && kp > 128) return fail(OFSC_ERR_INVALID_ARG, "%s: tensor-core Grams need k <= 128", who);
@@ -2368,6 +2435,8 @@ ofsc_status iterate_lockstep(int32_t count, ofsc_graph* const* graphs, int32_t m
   }
   GraphExec plain;                  // one plain update of every graph
   std::vector<int64_t> plain_launches(jobs.size(), 0);
+  const bool group = o.group_launches > 0;
+  const int lanes = o.group_launches;
   bool forked = true;               // job streams are ordered after main and main not after them
   for (int t = 0; t <= maxit; ++t) {
     bool all_plain = true;
@@ -2396,7 +2465,23 @@ ofsc_status iterate_lockstep(int32_t count, ofsc_graph* const* graphs, int32_t m
           return st;
         }
         if (ce == cudaSuccess) ce = ee;
-        if (ce == cudaSuccess) ce = cudaGraphInstantiate(&plain.exec, graph, 0);
+        // one launch per kernel of the update over every graph's blocks (the captured graph is
+        // one chain per graph); kept as captured if it holds a node the rewrite does not know
+        cudaGraph_t grouped = nullptr;
+        int grouped_launches = 0;
+        if (ce == cudaSuccess && group) {
+          const cudaError_t ge = regroup_chains(graph, lanes, &grouped, &grouped_launches);
+          if (ge != cudaSuccess) {
+            (void)cudaGetLastError();
+            grouped = nullptr;
+          }
+        }
+        if (ce == cudaSuccess) ce = cudaGraphInstantiate(&plain.exec, grouped ? grouped : graph, 0);
+        if (grouped) {
+          cudaGraphDestroy(grouped);
+          // a grouped launch serving several graphs is counted once, for the first of them
+          for (size_t i = 0; i < jobs.size(); ++i) plain_launches[i] = i == 0 ? grouped_launches : 0;
+        }
         if (graph) cudaGraphDestroy(graph);
         OFSC_CUDA(ce);
       }
@@ -2636,8 +2721,15 @@ extern "C" ofsc_status ofsc_objective_grad_noalloc(const ofsc_graph* gc, int32_t
     case 2: k_gram<2><<<grid, 256, 0, s>>>(ga); break;
     default: k_gram<4><<<grid, 256, 0, s>>>(ga); break;
   }
-  k_gram_reduce<<<(int)std::min<int64_t>(ceil_div(kPairs * kp * kp, 32), 8 * kNumSMs), 256, 0, s>>>(
-      ws.gram_part, gy, kp, (1 << G_R) | (1 << G_B), ws.gram, ws.ctrl, 0);
+  GramReduceArgs ra{};
+  ra.part = ws.gram_part;
+  ra.gy = gy;
+  ra.kp = kp;
+  ra.slot_mask = (1 << G_R) | (1 << G_B);
+  ra.gram = ws.gram;
+  ra.ctrl = ws.ctrl;
+  ra.ignore_done = 0;
+  k_gram_reduce<<<(int)std::min<int64_t>(ceil_div(kPairs * kp * kp, 32), 8 * kNumSMs), 256, 0, s>>>(ra);
   k_set_rb<<<1, 256, 0, s>>>(ws.gram, kp, objective, ws.Rn, ws.Bn, nullptr, nullptr, ws.ctrl, 0);
   OFSC_LAUNCH_CHECK("noalloc: refresh");
   int nblk = 0;

@@ -5,6 +5,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "group.cuh"
 
 namespace ofsc {
 namespace {
@@ -103,162 +104,36 @@ __host__ __device__ constexpr int dir_slots() {
 // UU: gathers in flight per lane (0: the default of dir_slots; other values are the shapes the
 // autotuner may pick). MP: the warps take the merge-path shares a.mp (a long row can span warps;
 // the partial sums of a row a warp does not both start and finish go to a.carry).
+#define OFSC_DIR_BOUNDS \
+  __launch_bounds__(32 * kRowWarpsPerBlock, (VPL == 4 ? OFSC_ROW_WARPS_F32 : OFSC_ROW_WARPS_BF16) / kRowWarpsPerBlock)
+
 template <int LPN, int VPL, bool WEIGHTED, bool BF16, bool DOTS, int UU, bool MP>
-__global__ void __launch_bounds__(32 * kRowWarpsPerBlock,
-                                  (VPL == 4 ? OFSC_ROW_WARPS_F32 : OFSC_ROW_WARPS_BF16) / kRowWarpsPerBlock)
-    k_spmm_dir(SpmmArgs a) {
-  if (!a.ignore_done && a.ctrl->done) return;
-  using S = Slot<VPL, BF16>;
-  constexpr int NPI = 32 / LPN;
-  constexpr int U = UU > 0 ? UU : dir_slots<LPN, VPL, WEIGHTED>();
-  constexpr int STEP = U * NPI;
-  constexpr int WPB = kRowWarpsPerBlock;
-  constexpr int W = VPL * LPN;
-  static_assert(STEP <= 32, "one column index per lane");
-  // per-warp sums of diag(V^T AV) over the warp's rows; each lane owns its columns
-  __shared__ __align__(16) float dred[DOTS ? WPB * W : 4];
-  const int lane = threadIdx.x & 31;
-  const int sub = lane % LPN;
-  const int q = lane / LPN;
-  const int warp = threadIdx.x >> 5;
-  const int gw = blockIdx.x * WPB + warp;
-  const int c = sub * VPL;
-  const bool active = c < a.kp;
-  float* rr = dred + (size_t)warp * W;
-  if (DOTS && lane < LPN) {
-#pragma unroll
-    for (int i = 0; i < VPL; ++i) rr[c + i] = 0.0f;
-  }
-  if (gw < a.groups) {
-    int l, rb;  // rows [l, rb) (column indices are int32, so n < 2^31)
-    int64_t pend, pb;
-    bool cut_head = false;  // MP: the first row began in an earlier warp
-    if (MP) {
-      const int64_t i1 = a.mp[gw + 1];
-      l = (int)a.mp[gw];
-      pb = a.mp[a.groups + 1 + gw];
-      pend = a.mp[a.groups + 2 + gw];
-      // rows l .. i1 - 1 end in this warp; row i1 as well if the warp holds some of its nonzeros
-      rb = (int)((i1 < a.n && pend > a.row_ptr[i1]) ? i1 + 1 : i1);
-      cut_head = l < rb && pb > a.row_ptr[l];
-      if (lane == 0) {
-        a.carry_row[2 * (int64_t)gw] = -1;
-        a.carry_row[2 * (int64_t)gw + 1] = -1;
-      }
-    } else {
-      l = (int)a.bnd[gw];
-      rb = (int)a.bnd[gw + 1];
-      pend = l < rb ? a.row_ptr[rb] : 0;
-      pb = l < rb ? a.row_ptr[l] : 0;
-    }
-    if (l < rb) {
-      int64_t e1 = a.row_ptr[l + 1];      // where the current row ends
-      int64_t p1 = MP ? min(e1, pend) : e1;  // where this warp stops in it
-      int jl = 0;
-      float wl = 1.0f;
-      {
-        const int64_t i = pb + lane;
-        if (lane < STEP && i < pend) {
-          jl = __ldg(a.col + i);
-          if (WEIGHTED) wl = __ldg(a.val + i);
-        }
-      }
-      float acc[VPL];
-#pragma unroll
-      for (int i = 0; i < VPL; ++i) acc[i] = 0.0f;
-      while (true) {
-        const int64_t rem = p1 - pb;
-        const bool last = rem <= STEP;
-        float s = 0.0f;
-        float base[VPL];
-#pragma unroll
-        for (int i = 0; i < VPL; i += 4) {
-          float4 b4 = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (last && lane < LPN && active) b4 = *(const float4*)(a.base + (int64_t)l * a.kp + c + i);
-          base[i] = b4.x; base[i + 1] = b4.y; base[i + 2] = b4.z; base[i + 3] = b4.w;
-        }
-        if (last && lane < LPN && active) s = a.dinv[l];
-        typename S::Raw v[U];
-        float wv[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const int slot = u * NPI + q;
-          const int j = __shfl_sync(0xffffffffu, jl, slot);
-          wv[u] = WEIGHTED ? __shfl_sync(0xffffffffu, wl, slot) : 1.0f;
-          v[u] = (slot < rem && active) ? S::load(a.gather, j, a.kp, c) : S::zero();
-        }
-        const int64_t pn = last ? p1 : pb + STEP;
-        const bool more = !last || l + 1 < rb;
-        int64_t p1n = p1, e1n = e1;
-        if (last && more) {
-          e1n = a.row_ptr[l + 2];
-          p1n = MP ? min(e1n, pend) : e1n;
-        }
-        if (more) {
-          const int64_t i = pn + lane;
-          jl = 0;
-          if (lane < STEP && i < pend) {
-            jl = __ldg(a.col + i);
-            if (WEIGHTED) wl = __ldg(a.val + i);
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-          if (u * NPI + q < rem) S::fma(acc, wv[u], v[u]);
-        if (last) {
-#pragma unroll
-          for (int off = LPN; off < 32; off <<= 1)
-#pragma unroll
-            for (int i = 0; i < VPL; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], off);
-          const bool cut_tail = MP && p1 < e1;  // the row goes on in a later warp
-          if (MP && (cut_head || cut_tail)) {
-            // a share of a split row: its partial sum for k_spmm_fixup (slot 1: unfinished here)
-            const int64_t slot = 2 * (int64_t)gw + (cut_tail ? 1 : 0);
-            if (lane < LPN && active) {
-#pragma unroll
-              for (int i = 0; i < VPL; i += 4)
-                *(float4*)(a.carry + slot * a.kp + c + i) = make_float4(acc[i], acc[i + 1], acc[i + 2], acc[i + 3]);
-            }
-            if (lane == 0) a.carry_row[slot] = (cut_tail && cut_head) ? -((int64_t)l + 2) : (int64_t)l;
-          } else if (lane < LPN && active) {
-            float r[VPL];
-#pragma unroll
-            for (int i = 0; i < VPL; ++i) r[i] = -fmaf(s, acc[i], base[i]);
-#pragma unroll
-            for (int i = 0; i < VPL; i += 4)
-              *(float4*)(a.out + (int64_t)l * a.kp + c + i) = make_float4(r[i], r[i + 1], r[i + 2], r[i + 3]);
-            if (DOTS) {
-#pragma unroll
-              for (int i = 0; i < VPL; ++i) rr[c + i] = fmaf(base[i], r[i], rr[c + i]);
-            }
-          }
-          if (!more) break;
-          cut_head = false;
-          ++l;
-          p1 = p1n;
-          e1 = e1n;
-#pragma unroll
-          for (int i = 0; i < VPL; ++i) acc[i] = 0.0f;
-        }
-        pb = pn;
-      }
-    }
-  }
-  if (DOTS && gw < a.groups) {  // one row of partials per warp: no block-wide barrier
-    __syncwarp();
-    for (int j = lane; j < a.kp; j += 32) a.dots[(int64_t)gw * a.kp + j] = (double)rr[j];
-  }
+__global__ void OFSC_DIR_BOUNDS k_spmm_dir(SpmmArgs a) {
+#define OFSC_VB_X blockIdx.x
+#include "spmm_dir_body.inc"
+#undef OFSC_VB_X
 }
+
+// The same product for every graph of a batch in one launch (see group.cuh).
+template <int LPN, int VPL, bool WEIGHTED, bool BF16, bool DOTS, int UU, bool MP>
+__global__ void OFSC_DIR_BOUNDS k_spmm_dir_g(const __grid_constant__ GroupParams<SpmmArgs> p) {
+  VBlock vb;
+  const SpmmArgs& a = group_find(p, &vb);
+#define OFSC_VB_X ((unsigned)vb.x)
+#include "spmm_dir_body.inc"
+#undef OFSC_VB_X
+}
+#undef OFSC_DIR_BOUNDS
 
 // Rows split across warps by the merge-path shares: the warp that starts a row and leaves it
 // unfinished adds, in warp order, its partial sums and those of the following warps up to the one
 // that finishes the row, then writes W = -V - D^-1/2 (sum) for the row and adds the row's share of
 // diag(V^T AV) to its own row of dots partials. One warp per warp of the product, four columns
 // per lane (kp <= 128).
-__global__ void __launch_bounds__(256) k_spmm_fixup(SpmmArgs a) {
+__device__ __forceinline__ void spmm_fixup_body(const SpmmArgs& a, const VBlock vb) {
   if (!a.ignore_done && a.ctrl->done) return;
   const int lane = threadIdx.x & 31;
-  const int64_t w = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int64_t w = (int64_t)vb.x * 8 + (threadIdx.x >> 5);
   if (w >= a.groups) return;
   const int64_t r = a.carry_row[2 * w + 1];
   if (r < 0) return;  // no row that this warp started and left unfinished
@@ -291,6 +166,14 @@ __global__ void __launch_bounds__(256) k_spmm_fixup(SpmmArgs a) {
   }
 }
 
+__global__ void __launch_bounds__(256) k_spmm_fixup(const __grid_constant__ SpmmArgs a) { spmm_fixup_body(a, hw_block()); }
+
+__global__ void __launch_bounds__(256) k_spmm_fixup_g(const __grid_constant__ GroupParams<SpmmArgs> p) {
+  VBlock vb;
+  const SpmmArgs& a = group_find(p, &vb);
+  spmm_fixup_body(a, vb);
+}
+
 // mp[w] = first row and mp[warps + 1 + w] = first nonzero of warp w's share of the merged list of
 // row ends and nonzeros: the point (i, d - i) of diagonal d = w (n + nnz) / warps, with i the
 // number of rows whose end, row_ptr[i + 1] + i in merged order, lies before d.
@@ -319,6 +202,11 @@ __global__ void k_max_row(int64_t n, const int64_t* __restrict__ row_ptr, unsign
 
 template <int LPN, int VPL, bool WEIGHTED, bool BF16, bool DOTS, int UU, bool MP>
 void launch_dir_u(const SpmmArgs& a, cudaStream_t s) {
+  if (DOTS) {  // the iteration's product (the one a replayed update holds) can run grouped
+    OFSC_GROUPABLE((k_spmm_dir<LPN, VPL, WEIGHTED, BF16, DOTS, UU, MP>),
+                   (k_spmm_dir_g<LPN, VPL, WEIGHTED, BF16, DOTS, UU, MP>), SpmmArgs);
+    if (MP) OFSC_GROUPABLE(k_spmm_fixup, k_spmm_fixup_g, SpmmArgs);
+  }
   k_spmm_dir<LPN, VPL, WEIGHTED, BF16, DOTS, UU, MP><<<a.groups / kRowWarpsPerBlock, 32 * kRowWarpsPerBlock, 0, s>>>(a);
   if (MP) k_spmm_fixup<<<(a.groups + 7) / 8, 256, 0, s>>>(a);
 }

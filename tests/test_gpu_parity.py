@@ -753,9 +753,11 @@ def batch_problems(scale, count):
 
 @pytest.mark.parametrize("method", METHODS)
 def test_batched_equals_single_bit_for_bit(method):
-    """ofsc_iterate_batched gives every problem the launches ofsc_iterate gives it: same X, same
-    result fields, bit for bit, with CUDA graph replay and with direct launches. maxit = 40 spans
-    two host flag reads and one exact refresh of AX; tol = 1e-3 lets some problems stop early."""
+    """ofsc_iterate_batched gives every problem the arithmetic ofsc_iterate gives it: same X, same
+    result fields, bit for bit, with the replayed updates launched per graph on the graphs' streams
+    (the default), grouped (one launch per kernel over the blocks of the graphs of a lane; two
+    lanes here), and launched directly. maxit = 40 spans two host flag reads and one exact refresh
+    of AX; tol = 1e-3 lets some problems stop early. Grouping takes fewer launches."""
     import torch
     probs = batch_problems(0.02, 6)
     graphs = [gpu_graph(e) for e, _ in probs]
@@ -764,21 +766,55 @@ def test_batched_equals_single_bit_for_bit(method):
         X = torch.from_numpy(x0).cuda()
         r = ofsc.ofsc_iterate(g, method, X, 1e-3, 40) if e.n > 0 else None
         singles.append((X.cpu().numpy(), r))
-    for direct in (False, True):
+    totals = {}
+    for direct, group in ((False, 0), (False, 2), (True, 0)):
         Xs = [torch.from_numpy(x0).cuda() for _, x0 in probs]
-        rs = ofsc.ofsc_iterate_batched(graphs, method, Xs, 1e-3, 40, direct_launch=direct)
+        rs = ofsc.ofsc_iterate_batched(graphs, method, Xs, 1e-3, 40, direct_launch=direct, group_launches=group)
         assert len(rs) == len(probs)
         stopped_early = 0
         for (Xr, r), X, rb, (e, _) in zip(singles, Xs, rs, probs):
-            assert np.array_equal(X.cpu().numpy(), Xr)
+            assert np.array_equal(X.cpu().numpy(), Xr), (direct, group)
             if e.n == 0:
                 assert rb.iterations == 0
                 continue
             assert (rb.iterations, rb.status, rb.rel_dir_norm, rb.f, rb.g0_norm) == \
                    (r.iterations, r.status, r.rel_dir_norm, r.f, r.g0_norm)
-            assert rb.kernel_launches >= r.kernel_launches
+            if group == 0:
+                assert rb.kernel_launches >= r.kernel_launches
             stopped_early += rb.iterations < 40
         assert stopped_early >= 1
+        totals[(direct, group)] = sum(r.kernel_launches for r in rs)
+    assert totals[(False, 2)] < totals[(False, 0)]
+
+
+@pytest.mark.parametrize("gather", [0, 1])
+def test_grouped_launches_match_per_graph_launches(gather):
+    """The grouped form of a batch's replayed updates on graphs that take every variant of the
+    direction product the grouping covers: weighted and binary S, hub rows split by merge path
+    (with its fixup launch), k from 3 to 64, FP32 and BF16 gathers; the same bits as one launch per
+    graph and kernel, for every method, and a single graph grouped on its own (group_launches = 1)
+    as well. Lanes change only which graphs share a launch, never the bits."""
+    import torch
+    probs = synth.batch("sbm_batch32", 0.02)[:4]
+    probs.append((hub_graph(True, 230), synth.initial_block(6000, 20, 231)))
+    probs.append((hub_graph(False, 232), synth.initial_block(6000, 3, 233)))
+    e = synth.sbm(2500, 7, 14.0, 4.0, ratio_kind="count", weighted=True, seed=234)
+    probs.append((e, synth.initial_block(e.n, 64, 235)))
+    graphs = [gpu_graph(e) for e, _ in probs]
+    for method in METHODS:
+        out = {}
+        for group in (0, 1, 3, 7):  # per graph; one lane; three lanes; one graph per lane
+            Xs = [torch.from_numpy(x0).cuda() for _, x0 in probs]
+            rs = ofsc.ofsc_iterate_batched(graphs, method, Xs, 0.0, 37, gather=gather, group_launches=group)
+            out[group] = ([X.cpu().numpy() for X in Xs], [(r.iterations, r.status, r.rel_dir_norm, r.f) for r in rs])
+            for a, b in zip(out[group][0], out[0][0]):
+                assert np.array_equal(a, b), (method, group)
+            assert out[group][1] == out[0][1]
+    X1 = torch.from_numpy(probs[4][1]).cuda()
+    X2 = X1.clone()
+    r1 = ofsc.ofsc_iterate(graphs[4], o.OFM_F1, X1, 0.0, 20, gather=gather, group_launches=1)
+    r2 = ofsc.ofsc_iterate(graphs[4], o.OFM_F1, X2, 0.0, 20, gather=gather)
+    assert torch.equal(X1, X2) and r1.rel_dir_norm == r2.rel_dir_norm
 
 
 def test_batched_matches_oracle():

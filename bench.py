@@ -44,7 +44,7 @@ def load_peaks() -> dict:
     return {"hbm_gbs": 6800.0, "source": "fallback"}
 
 
-DIR_PRODUCT_SOURCES = ("spmm_dir.cu", "spmm_dir.cuh")  # the direction product and its argument header
+DIR_PRODUCT_SOURCES = ("spmm_dir.cu", "spmm_dir.cuh", "spmm_dir_body.inc")  # the direction product, its body and header
 
 
 def source_digest(names=None) -> str:

@@ -11,6 +11,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libofsc.so")
+BUILD_DEBUG = os.path.join(PKG, "_build_debug")
+LIB_DEBUG = os.path.join(PKG, "libofsc_debug.so")
 SOURCES = ["api.cu", "graph.cu", "iterate.cu", "spmm_dir.cu", "cluster.cu", "gram_tc.cu", "spmm_tma.cu", "direction_tc.cu", "ritz.cu", "wgrad.cu", "unroll.cu", "group.cu"]
 HEADERS = [os.path.join(CSRC, "common.cuh"), os.path.join(CSRC, "spmm_dir.cuh"), os.path.join(CSRC, "tcgen05.cuh"), os.path.join(CSRC, "cubic.cuh"), os.path.join(CSRC, "group.cuh"), os.path.join(CSRC, "spmm_dir_body.inc"), os.path.join(CSRC, "direction_body.inc"), os.path.join(ROOT, "include", "ofsc.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -32,18 +34,23 @@ def _stale(target: str, deps: list[str]) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(verbose: bool = False, force: bool = False) -> str:
-    """Compiles every CUDA translation unit for sm_103a and links libofsc.so; returns its path."""
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose: bool = False, force: bool = False, debug: bool = False) -> str:
+    """Compiles every CUDA translation unit for sm_103a and links libofsc.so; returns its path.
+    debug=True builds the checked library libofsc_debug.so instead (-DOFSC_DEBUG=1: the direction
+    product checks its column indices and row ranges and the calls report a violation)."""
+    bdir = BUILD_DEBUG if debug else BUILD
+    lib = LIB_DEBUG if debug else LIB
+    flags = FLAGS + (["-DOFSC_DEBUG=1"] if debug else [])
+    os.makedirs(bdir, exist_ok=True)
     cc = nvcc()
     jobs = []
     objs = []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD, src.replace(".cu", ".o"))
+        o = os.path.join(bdir, src.replace(".cu", ".o"))
         objs.append(o)
         if force or _stale(o, [s] + HEADERS):
-            jobs.append([cc, *ARCH, *FLAGS, "-c", s, "-o", o])
+            jobs.append([cc, *ARCH, *flags, "-c", s, "-o", o])
 
     def run(cmd):
         if verbose:
@@ -55,11 +62,11 @@ def build(verbose: bool = False, force: bool = False) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 1))) as ex:
         list(ex.map(run, jobs))
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + ".tmp"
+    if force or jobs or _stale(lib, objs):
+        tmp = lib + ".tmp"
         run([cc, *ARCH, "-shared", "-o", tmp, *objs])
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -1,6 +1,13 @@
 // Internal declarations shared by the translation units of libofsc (not part of the C ABI).
 #pragma once
 
+// Checked build (-DOFSC_DEBUG=1): the direction product checks every column index and row range
+// before it uses them, records the first violation instead of making the access, and the calls
+// that run it return OFSC_ERR_INVALID_ARG naming it.
+#ifndef OFSC_DEBUG
+#define OFSC_DEBUG 0
+#endif
+
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>

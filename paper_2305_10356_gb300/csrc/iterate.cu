@@ -1163,6 +1163,20 @@ int spmm_dir(const SpmmArgs& a, bool weighted, bool bf16, int slots, cudaStream_
   return launch_spmm_dir(a, weighted, bf16, slots, s);
 }
 
+// Checked builds: a recorded out-of-range access of the direction product makes the call fail
+// (its results are not meaningful), whatever else it returned; release builds return st.
+ofsc_status bounds_checked(ofsc_status st, const char* who) {
+  unsigned long long code = 0;
+  const cudaError_t e = spmm_dir_take_bounds(&code);
+  if (e != cudaSuccess) return cuda_fail(e, "bounds check");
+  if (code == 0) return st;
+  const unsigned kind = (unsigned)(code >> 60);
+  long long v = (long long)(code & ((1ull << 60) - 1));
+  if (v & (1ll << 59)) v -= (1ll << 60);  // sign of a negative column index
+  return fail(OFSC_ERR_INVALID_ARG, "%s: bounds check: %s %lld", who,
+              kind == 1 ? "column index outside [0, n):" : "row or nonzero range outside the CSR, warp", v);
+}
+
 // Whether the direction product runs on the merge-path shares: forced on or off by `setting`
 // (> 0, < 0); else the form ofsc_autotune timed faster for this padded width and gather storage;
 // else when the longest row holds at least 1024 nonzeros and more than four warps' shares (the
@@ -1823,6 +1837,8 @@ extern "C" ofsc_status ofsc_objective_grad(ofsc_graph* g, int32_t objective, int
     }
     st = finish(ws, s, &c);
     if (st != OFSC_OK) return st;
+    st = bounds_checked(OFSC_OK, "ofsc_objective_grad");
+    if (st != OFSC_OK) return st;
   } else {
     c.f = objective == OFSC_F1 ? 0.0 : 0.0;
   }
@@ -2183,7 +2199,8 @@ extern "C" ofsc_status ofsc_iterate(ofsc_graph* g, int32_t method, int32_t k, fl
     ofsc_graph* gs[1] = {g};
     const int32_t kk[1] = {k};
     float* xs[1] = {X};
-    return iterate_lockstep(1, gs, method, kk, xs, tol, maxit, o, out, s, "ofsc_iterate");
+    return bounds_checked(iterate_lockstep(1, gs, method, kk, xs, tol, maxit, o, out, s, "ofsc_iterate"),
+                          "ofsc_iterate");
   }
   Job job(g, method, k, X, tol, maxit, o, s);
   st = job.prepare();
@@ -2211,7 +2228,7 @@ extern "C" ofsc_status ofsc_iterate(ofsc_graph* g, int32_t method, int32_t k, fl
   if (st != OFSC_OK) return st;
   OFSC_CUDA(cudaStreamSynchronize(s));
   job.prof.collect();
-  return result_error(job.result(out), "ofsc_iterate");
+  return bounds_checked(result_error(job.result(out), "ofsc_iterate"), "ofsc_iterate");
 }
 
 // ==========================================================================================
@@ -2564,8 +2581,9 @@ extern "C" ofsc_status ofsc_iterate_batched(int32_t count, ofsc_graph* const* gr
   }
   if (outs)
     for (int i = 0; i < count; ++i) outs[i] = ofsc_result{0, OFSC_OK, 0.0, 0.0, 0.0, 0, -1, -1};
-  return iterate_lockstep(count, graphs, method, ks, Xs, tol, maxit, o, outs, (cudaStream_t)stream_,
-                          "ofsc_iterate_batched");
+  return bounds_checked(iterate_lockstep(count, graphs, method, ks, Xs, tol, maxit, o, outs, (cudaStream_t)stream_,
+                                         "ofsc_iterate_batched"),
+                        "ofsc_iterate_batched");
 }
 
 // ==========================================================================================

@@ -10,6 +10,16 @@
 namespace ofsc {
 namespace {
 
+#if OFSC_DEBUG
+// Checked build: the first out-of-range access the direction product met, (kind << 60) | value
+// (kind 1: a column index outside [0, n), value the index; kind 2: a warp's row or nonzero range
+// outside the CSR, value the warp), 0 if none. Read and cleared by spmm_dir_take_bounds.
+__device__ unsigned long long g_bounds_bad = 0ull;
+__device__ __forceinline__ void bounds_bad(unsigned kind, long long value) {
+  atomicCAS(&g_bounds_bad, 0ull, ((unsigned long long)kind << 60) | ((unsigned long long)value & ((1ull << 60) - 1)));
+}
+#endif
+
 #ifndef OFSC_ROW_U32
 #define OFSC_ROW_U32 8  // gathers in flight per lane when a warp covers a row of 128 columns
 #endif
@@ -291,6 +301,20 @@ cudaError_t max_row_length(int64_t n, const int64_t* row_ptr, unsigned long long
   const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4 * kNumSMs);
   k_max_row<<<(int)blocks, 256, 0, s>>>(n, row_ptr, max_row);
   return cudaGetLastError();
+}
+
+cudaError_t spmm_dir_take_bounds(unsigned long long* code) {
+  *code = 0;
+#if OFSC_DEBUG
+  cudaError_t e = cudaMemcpyFromSymbol(code, g_bounds_bad, sizeof(*code));
+  if (e == cudaSuccess && *code) {
+    const unsigned long long zero = 0;
+    e = cudaMemcpyToSymbol(g_bounds_bad, &zero, sizeof(zero));
+  }
+  return e;
+#else
+  return cudaSuccess;
+#endif
 }
 
 int launch_spmm_dir(const SpmmArgs& a, bool weighted, bool bf16, int slots, cudaStream_t s) {

@@ -47,5 +47,9 @@ int launch_spmm_dir(const SpmmArgs& a, bool weighted, bool bf16, int slots, cuda
 // and the largest row (nonzeros) into *max_row (device int64, atomically maximised: zero it first).
 cudaError_t merge_partition(int64_t n, const int64_t* row_ptr, int warps, int64_t* mp, cudaStream_t s);
 cudaError_t max_row_length(int64_t n, const int64_t* row_ptr, unsigned long long* max_row, cudaStream_t s);
+// Checked builds (OFSC_DEBUG): the first out-of-range access the direction product recorded since
+// the last call, (kind << 60) | value, or 0, and clears it (synchronous: call after the stream
+// has drained). Release builds: always 0.
+cudaError_t spmm_dir_take_bounds(unsigned long long* code);
 
 }  // namespace ofsc

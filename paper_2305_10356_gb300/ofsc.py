@@ -12,6 +12,10 @@ import re
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libofsc.so")
+# OFSC_LIB (an absolute path) selects another build of the library, e.g. the checked build
+# libofsc_debug.so; it is read when this module is imported.
+if os.environ.get("OFSC_LIB"):
+    LIB_PATH = os.environ["OFSC_LIB"]
 HEADER = os.path.join(os.path.dirname(_PKG), "include", "ofsc.h")
 
 OK, ERR_INVALID_ARG, ERR_OOM, ERR_NONFINITE, ERR_TIMEOUT, ERR_NOT_CONVERGED, ERR_CUDA = range(7)

@@ -71,6 +71,8 @@ enum { OFSC_GRAM_AUTO = 0, OFSC_GRAM_SIMT = 1, OFSC_GRAM_TC = 2 };
 enum { OFSC_SPMM_AUTO = 0, OFSC_SPMM_SIMT = 1, OFSC_SPMM_TMA = 2 };
 
 typedef struct ofsc_graph ofsc_graph;
+/* The state of Algorithm 2's conjugate-gradient recurrence between calls (ofsc_state_create). */
+typedef struct ofsc_state ofsc_state;
 
 typedef struct {
   int64_t n;            /* nodes */
@@ -232,6 +234,14 @@ typedef struct {
                             work list of (graph, block) pairs, with the same results bit for bit;
                             the graphs are dealt into n lanes of similar work, grouped within a
                             lane, and the lanes overlap */
+  ofsc_state* state;     /* ofsc_iterate only (NULL: none): the CG state to resume and to leave
+                            for the next call. If it holds a run (t > 0) the call continues that
+                            run: X must be the X that run returned, and the first update takes
+                            beta from the saved G_{t-1} and extends the saved V_{t-1} (no step of
+                            steepest descent); relative norms stay relative to that run's
+                            ||G_0||. A call that performs all maxit > 0 updates without stopping
+                            leaves its own state in it (t grows by maxit); a call that stops or
+                            fails leaves it empty. */
 } ofsc_opts;
 
 typedef struct {
@@ -329,6 +339,26 @@ ofsc_status ofsc_unrolled_grad(ofsc_graph* g, int32_t k, const float* X0, int32_
                                float* grad, float* grad_w, void* stream);
 
 /*
+ * ofsc_state_create - an empty CG state for ofsc_iterate on graph g with k columns (opts.state):
+ * the last direction V_{t-1}, gradient G_{t-1}, V's column scales and V_{t-1}^T V_{t-1} of a run
+ * of Algorithm 2, with its update count t and ||G_0||. Owns 8 n kp + 8 kp (kp + 1) bytes of device
+ * memory (kp = k rounded up to a multiple of 8) on g's device; usable with g (or a graph of the
+ * same n) and the same k and method. Resuming continues the CG recurrence exactly (Algorithm 2
+ * as one run); the first update of a resumed call evaluates G_t from an exact A X, as every call
+ * does at its start. Errors: OFSC_ERR_INVALID_ARG, OFSC_ERR_OOM, OFSC_ERR_CUDA.
+ */
+ofsc_status ofsc_state_create(const ofsc_graph* g, int32_t k, ofsc_state** out);
+ofsc_status ofsc_state_free(ofsc_state* st);
+/* t_out: updates of the run the state holds (0: empty); bytes_out: size of its host image. */
+ofsc_status ofsc_state_info(const ofsc_state* st, int64_t* t_out, int64_t* bytes_out);
+/* The state to a HOST buffer of exactly ofsc_state_info's bytes (a checkpoint), and back into a
+ * state created for the same n and k (load checks the image's header: OFSC_ERR_INVALID_ARG on a
+ * mismatch). Both synchronise `stream`. */
+ofsc_status ofsc_state_save(const ofsc_state* st, void* host, int64_t bytes, void* stream);
+ofsc_status ofsc_state_load(ofsc_state* st, const void* host, int64_t bytes, void* stream);
+
+/*
+ * ofsc_autotune/*
  * ofsc_autotune - picks, by timing, the shape of the direction product (the sparse product of
  * Sec. 3.3, the largest part of an update of Algorithm 2) for this graph, k columns and the given
  * gather storage: how finely its rows are split among warps (4, 8, 16 or 32 warps per SM, coarser

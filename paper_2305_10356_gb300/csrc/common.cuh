@@ -203,6 +203,20 @@ struct Workspace {
 
 }  // namespace ofsc
 
+// The CG state between calls (ofsc_state_create): V_{t-1}, G_{t-1} (n x kp FP32), V's column
+// scales (kp), V_{t-1}^T V_{t-1} (kp x kp), the run's update count t (0: empty), ||G_0|| and the
+// method that made it.
+struct ofsc_state {
+  int64_t n = 0;
+  int k = 0, kp = 0, method = -1, device = 0;
+  int64_t t = 0;
+  double g0 = 0.0;
+  float* V = nullptr;
+  float* G = nullptr;
+  double* vscale = nullptr;
+  double* Q = nullptr;
+};
+
 struct ofsc_graph {
   int64_t n = 0;
   int64_t m_in = 0;

@@ -19,6 +19,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <memory>
 #include <mutex>
 #include <vector>
@@ -2023,6 +2024,9 @@ struct Job {
   bool exact = false;
   int exact_at = -1;
   int forced_refresh = -1;
+  // opts.state: the CG state to resume (resume: it holds a run) and to leave for the next call
+  ofsc_state* cg = nullptr;
+  bool resume = false;
 
   Job(ofsc_graph* g_, int method_, int k_, float* X_, double tol_, int maxit_, const ofsc_opts& o_, cudaStream_t s_)
       : g(g_), method(method_), k(k_), kp(round_up(k_, 8)),
@@ -2056,6 +2060,17 @@ struct Job {
 
   // Workspace, engines and TMA maps; call before any launch (allocates, so never under capture).
   ofsc_status prepare() {
+    cg = o.state;
+    if (cg) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      if (cg->n != g->n || cg->k != k || cg->kp != kp || cg->device != dev)
+        return fail(OFSC_ERR_INVALID_ARG, "opts.state: made for n=%lld, k=%d on device %d, not n=%lld, k=%d on %d",
+                    (long long)cg->n, cg->k, cg->device, (long long)g->n, k, dev);
+      if (cg->t > 0 && cg->method != method)
+        return fail(OFSC_ERR_INVALID_ARG, "opts.state: holds a run of method %d, not %d", cg->method, method);
+      resume = cg->t > 0;
+    }
     ofsc_status st = ensure_workspace(g, kp);
     if (st != OFSC_OK) return st;
     Workspace& ws = g->ws;
@@ -2091,8 +2106,50 @@ struct Job {
     ++g_launches;
     OFSC_LAUNCH_CHECK("k_pad_in");
     OFSC_CUDA(run.refresh(objective, 0));
+    if (resume) {  // the saved run: V_{t-1}, G_{t-1}, V's scales, V_{t-1}^T V_{t-1}, ||G_0||
+      const size_t blk = (size_t)g->n * kp * sizeof(float);
+      OFSC_CUDA(cudaMemcpyAsync(ws.V, cg->V, blk, cudaMemcpyDeviceToDevice, s));
+      OFSC_CUDA(cudaMemcpyAsync(ws.G, cg->G, blk, cudaMemcpyDeviceToDevice, s));
+      OFSC_CUDA(cudaMemcpyAsync(ws.vscale, cg->vscale, (size_t)kp * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      OFSC_CUDA(cudaMemcpyAsync(ws.gram + G_Q * (size_t)kp * kp, cg->Q, (size_t)kp * kp * sizeof(double),
+                                cudaMemcpyDeviceToDevice, s));
+      OFSC_CUDA(cudaMemcpyAsync(&ws.ctrl->g0, &cg->g0, sizeof(double), cudaMemcpyHostToDevice, s));
+    }
     launches += g_launches - l0;
     return OFSC_OK;
+  }
+
+  // Before the final update overwrites them: G_{t-1}, V's scales and V_{t-1}^T V_{t-1} into the
+  // CG state (V_{t-1} itself is kept by keep_state once the call has ended).
+  cudaError_t save_before_final() {
+    Workspace& ws = g->ws;
+    const size_t blk = (size_t)g->n * kp * sizeof(float);
+    cudaError_t e = cudaMemcpyAsync(cg->G, ws.G, blk, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(cg->vscale, ws.vscale, (size_t)kp * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(cg->Q, ws.gram + G_Q * (size_t)kp * kp, (size_t)kp * kp * sizeof(double),
+                          cudaMemcpyDeviceToDevice, s);
+    return e;
+  }
+
+  // After the final report (c: the control block it read): a run that performed all maxit > 0
+  // updates without stopping leaves its state (t grows by maxit); any other leaves it empty.
+  cudaError_t keep_state(const Ctrl& c) {
+    if (!cg) return cudaSuccess;
+    if (maxit > 0 && c.status == OFSC_OK && !c.converged && c.it == maxit) {
+      cudaError_t e = cudaMemcpyAsync(cg->V, g->ws.V, (size_t)g->n * kp * sizeof(float), cudaMemcpyDeviceToDevice, s);
+      if (e != cudaSuccess) {
+        cg->t = 0;
+        return e;
+      }
+      cg->t += maxit;
+      cg->g0 = c.g0;
+      cg->method = method;
+    } else if (maxit > 0 || c.status != OFSC_OK) {
+      cg->t = 0;
+    }
+    return cudaSuccess;
   }
 
   // Iteration t: G_t (with the update of X_t fused in, or an exact refresh of AX every y_refresh
@@ -2103,6 +2160,18 @@ struct Job {
     const int64_t l0 = g_launches;
     Workspace& ws = g->ws;
     int nblk = 0;
+    if (cg && t == maxit && maxit > 0) OFSC_CUDA(save_before_final());
+    if (t == 0 && resume) {
+      // update t of the saved run: G from start()'s exact AX, beta against the saved G_{t-1}
+      OFSC_CUDA(run.rowpass(method, 0, 0, 0, &nblk, 1));
+      prof.begin(OFSC_PHASE_BETA);
+      run.beta(nblk, 0, 0, 1);
+      prof.end();
+      OFSC_LAUNCH_CHECK("k_beta");
+      if (t < maxit) OFSC_CUDA(run.direction_and_linesearch(0, o, k, 0.0));
+      launches += g_launches - l0;
+      return OFSC_OK;
+    }
     if (is_refresh(t)) {
       prof.begin(OFSC_PHASE_OTHER);
       k_update_x<<<grid_elems(g->n * kp), 256, 0, s>>>(g->n, kp, ws.X, ws.V, ws.alpha, ws.ctrl);
@@ -2226,6 +2295,7 @@ extern "C" ofsc_status ofsc_iterate(ofsc_graph* g, int32_t method, int32_t k, fl
   if (st != OFSC_OK) return st;
   st = job.report(c);
   if (st != OFSC_OK) return st;
+  OFSC_CUDA(job.keep_state(c));
   OFSC_CUDA(cudaStreamSynchronize(s));
   job.prof.collect();
   return bounds_checked(result_error(job.result(out), "ofsc_iterate"), "ofsc_iterate");
@@ -2547,6 +2617,7 @@ ofsc_status iterate_lockstep(int32_t count, ofsc_graph* const* graphs, int32_t m
     const Ctrl c = *j->g->ws.ctrl_host;
     ofsc_status st = j->report(c);
     if (st != OFSC_OK) return st;
+    OFSC_CUDA(j->keep_state(c));
   }
   OFSC_CUDA(join_jobs(main, jobs, jev));
   OFSC_CUDA(cudaEventRecord(fev, main));
@@ -2573,6 +2644,8 @@ extern "C" ofsc_status ofsc_iterate_batched(int32_t count, ofsc_graph* const* gr
   if (opts) o = *opts;
   if (o.trace || o.profile)
     return fail(OFSC_ERR_INVALID_ARG, "ofsc_iterate_batched: opts.trace and opts.profile must be NULL");
+  if (opts && opts->state)
+    return fail(OFSC_ERR_INVALID_ARG, "ofsc_iterate_batched: opts.state must be NULL (one state per call)");
   for (int i = 0; i < count; ++i) {
     ofsc_status st = check_iterate_args(graphs[i], method, ks[i], Xs[i], tol, maxit, o, "ofsc_iterate_batched");
     if (st != OFSC_OK) return st;
@@ -2762,5 +2835,116 @@ extern "C" ofsc_status ofsc_objective_grad_noalloc(const ofsc_graph* gc, int32_t
   if (c.status != OFSC_OK) return fail(c.status, "ofsc_objective_grad_noalloc: non-finite value in X");
   if (!std::isfinite(c.f)) return fail(OFSC_ERR_NONFINITE, "ofsc_objective_grad_noalloc: non-finite objective");
   if (f_out) *f_out = c.f;
+  return OFSC_OK;
+}
+
+// ==========================================================================================
+// The CG state between calls (opts.state): create, free, and its host image (a checkpoint).
+// ==========================================================================================
+
+namespace {
+
+struct StateHeader {
+  uint64_t magic;  // "OFSCSTAT"
+  int64_t n, t;
+  int32_t k, kp, method, reserved;
+  double g0;
+};
+constexpr uint64_t kStateMagic = 0x5441545343534f46ull;
+
+int64_t state_bytes(const ofsc_state* st) {
+  return (int64_t)sizeof(StateHeader) + 2 * st->n * st->kp * (int64_t)sizeof(float) +
+         ((int64_t)st->kp + (int64_t)st->kp * st->kp) * (int64_t)sizeof(double);
+}
+
+}  // namespace
+
+extern "C" ofsc_status ofsc_state_create(const ofsc_graph* g, int32_t k, ofsc_state** out) {
+  clear_error();
+  if (!out) return fail(OFSC_ERR_INVALID_ARG, "ofsc_state_create: out is NULL");
+  *out = nullptr;
+  if (!g) return fail(OFSC_ERR_INVALID_ARG, "ofsc_state_create: graph is NULL");
+  if (k < 1 || k > kMaxK) return fail(OFSC_ERR_INVALID_ARG, "ofsc_state_create: k=%d outside [1, %d]", k, kMaxK);
+  ofsc_state* st = new ofsc_state();
+  st->n = g->n;
+  st->k = k;
+  st->kp = round_up(k, 8);
+  cudaGetDevice(&st->device);
+  const size_t blk = (size_t)std::max<int64_t>(g->n, 1) * st->kp * sizeof(float);
+  cudaError_t e = dev_alloc(&st->V, blk);
+  if (e == cudaSuccess) e = dev_alloc(&st->G, blk);
+  if (e == cudaSuccess) e = dev_alloc(&st->vscale, (size_t)st->kp * sizeof(double));
+  if (e == cudaSuccess) e = dev_alloc(&st->Q, (size_t)st->kp * st->kp * sizeof(double));
+  if (e != cudaSuccess) {
+    ofsc_state_free(st);
+    return cuda_fail(e, "ofsc_state_create");
+  }
+  *out = st;
+  return OFSC_OK;
+}
+
+extern "C" ofsc_status ofsc_state_free(ofsc_state* st) {
+  clear_error();
+  if (!st) return OFSC_OK;
+  dev_free(st->V);
+  dev_free(st->G);
+  dev_free(st->vscale);
+  dev_free(st->Q);
+  delete st;
+  return OFSC_OK;
+}
+
+extern "C" ofsc_status ofsc_state_info(const ofsc_state* st, int64_t* t_out, int64_t* bytes_out) {
+  clear_error();
+  if (!st) return fail(OFSC_ERR_INVALID_ARG, "ofsc_state_info: state is NULL");
+  if (t_out) *t_out = st->t;
+  if (bytes_out) *bytes_out = state_bytes(st);
+  return OFSC_OK;
+}
+
+extern "C" ofsc_status ofsc_state_save(const ofsc_state* st, void* host, int64_t bytes, void* stream_) {
+  clear_error();
+  if (!st || !host) return fail(OFSC_ERR_INVALID_ARG, "ofsc_state_save: NULL argument");
+  if (bytes != state_bytes(st))
+    return fail(OFSC_ERR_INVALID_ARG, "ofsc_state_save: %lld bytes, the image takes %lld", (long long)bytes,
+                (long long)state_bytes(st));
+  cudaStream_t s = (cudaStream_t)stream_;
+  StateHeader h{kStateMagic, st->n, st->t, st->k, st->kp, st->method, 0, st->g0};
+  unsigned char* p = (unsigned char*)host;
+  std::memcpy(p, &h, sizeof(h));
+  p += sizeof(h);
+  const size_t blk = (size_t)st->n * st->kp * sizeof(float);
+  OFSC_CUDA(cudaMemcpyAsync(p, st->V, blk, cudaMemcpyDeviceToHost, s));
+  OFSC_CUDA(cudaMemcpyAsync(p + blk, st->G, blk, cudaMemcpyDeviceToHost, s));
+  OFSC_CUDA(cudaMemcpyAsync(p + 2 * blk, st->vscale, (size_t)st->kp * sizeof(double), cudaMemcpyDeviceToHost, s));
+  OFSC_CUDA(cudaMemcpyAsync(p + 2 * blk + st->kp * sizeof(double), st->Q, (size_t)st->kp * st->kp * sizeof(double),
+                            cudaMemcpyDeviceToHost, s));
+  OFSC_CUDA(cudaStreamSynchronize(s));
+  return OFSC_OK;
+}
+
+extern "C" ofsc_status ofsc_state_load(ofsc_state* st, const void* host, int64_t bytes, void* stream_) {
+  clear_error();
+  if (!st || !host) return fail(OFSC_ERR_INVALID_ARG, "ofsc_state_load: NULL argument");
+  if (bytes != state_bytes(st))
+    return fail(OFSC_ERR_INVALID_ARG, "ofsc_state_load: %lld bytes, the image takes %lld", (long long)bytes,
+                (long long)state_bytes(st));
+  StateHeader h;
+  std::memcpy(&h, host, sizeof(h));
+  if (h.magic != kStateMagic || h.n != st->n || h.k != st->k || h.kp != st->kp || h.t < 0 ||
+      (h.t > 0 && (h.method < OFSC_OFM_F1 || h.method > OFSC_TRI_F2)))
+    return fail(OFSC_ERR_INVALID_ARG, "ofsc_state_load: not a state image for n=%lld, k=%d", (long long)st->n, st->k);
+  cudaStream_t s = (cudaStream_t)stream_;
+  const unsigned char* p = (const unsigned char*)host + sizeof(h);
+  const size_t blk = (size_t)st->n * st->kp * sizeof(float);
+  OFSC_CUDA(cudaMemcpyAsync(st->V, p, blk, cudaMemcpyHostToDevice, s));
+  OFSC_CUDA(cudaMemcpyAsync(st->G, p + blk, blk, cudaMemcpyHostToDevice, s));
+  OFSC_CUDA(cudaMemcpyAsync(st->vscale, p + 2 * blk, (size_t)st->kp * sizeof(double), cudaMemcpyHostToDevice, s));
+  OFSC_CUDA(cudaMemcpyAsync(st->Q, p + 2 * blk + st->kp * sizeof(double), (size_t)st->kp * st->kp * sizeof(double),
+                            cudaMemcpyHostToDevice, s));
+  OFSC_CUDA(cudaStreamSynchronize(s));
+  st->t = h.t;
+  st->method = h.method;
+  st->g0 = h.g0;
   return OFSC_OK;
 }

@@ -60,7 +60,8 @@ class Opts(ctypes.Structure):
                 ("cg_restart", ctypes.c_int32), ("refine_tol", ctypes.c_double),
                 ("exact_tail", ctypes.c_double), ("vscale_exp", ctypes.c_int32),
                 ("spin_limit", ctypes.c_int64), ("withhold_arrivals", ctypes.c_int32),
-                ("merge_path", ctypes.c_int32), ("group_launches", ctypes.c_int32)]
+                ("merge_path", ctypes.c_int32), ("group_launches", ctypes.c_int32),
+                ("state", ctypes.c_void_p)]
 
 
 class Result(ctypes.Structure):
@@ -115,6 +116,11 @@ def lib() -> ctypes.CDLL:
             "ofsc_gram": [i64, i32, i32, vp, i32, ctypes.POINTER(vp), i64, vp, vp],
             "ofsc_kmeans": [i64, i32, vp, i32, u64, i32, i32, vp, ctypes.POINTER(dbl), vp],
             "ofsc_set_allocator": [ALLOC_FN, FREE_FN, vp],
+            "ofsc_state_create": [vp, i32, ctypes.POINTER(vp)],
+            "ofsc_state_free": [vp],
+            "ofsc_state_info": [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)],
+            "ofsc_state_save": [vp, vp, i64, vp],
+            "ofsc_state_load": [vp, vp, i64, vp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -250,15 +256,16 @@ def ofsc_iterate(g: Graph, method: int, X, tol: float, maxit: int, *, gather: in
                  spmm_engine: int = SPMM_AUTO, cg_restart: bool = False, refine_tol: float = 0.0,
                  exact_tail: float = 0.0, vscale_exp: int = 0, direct_launch: bool = False,
                  spin_limit: int = 0, withhold_arrivals: bool = False, merge_path: int = 0,
-                 group_launches: int = 0, stream=None) -> Result:
-    """Algorithm 2 in place on the device block X (n x k, FP32). Returns the ofsc_result."""
+                 group_launches: int = 0, state: "State | None" = None, stream=None) -> Result:
+    """Algorithm 2 in place on the device block X (n x k, FP32). Returns the ofsc_result. With a
+    State, the call continues the run the state holds and leaves its own state in it."""
     px = _arg(X, "X", "float32", rows=_rows(g))
     o = Opts(gather, y_refresh, check_every, alpha0, _arg(trace, "trace", "float64"),
              0 if trace is None else int(trace.shape[0]),
              ctypes.pointer(profile) if profile is not None else None, gram_engine, spmm_engine,
              1 if direct_launch else 0, 1 if cg_restart else 0, float(refine_tol), float(exact_tail),
              int(vscale_exp), int(spin_limit), 1 if withhold_arrivals else 0, int(merge_path),
-             int(group_launches))
+             int(group_launches), None if state is None else state.handle)
     r = Result()
     _check(lib().ofsc_iterate(g.handle, method, int(X.shape[1]), px, float(tol), int(maxit),
                               ctypes.byref(o), ctypes.byref(r), _stream(stream)),
@@ -271,7 +278,7 @@ def ofsc_iterate_batched(graphs: list[Graph], method: int, Xs: list, tol: float,
                          alpha0: float = 0.0, gram_engine: int = GRAM_AUTO, spmm_engine: int = SPMM_AUTO,
                          direct_launch: bool = False, cg_restart: bool = False, refine_tol: float = 0.0,
                          exact_tail: float = 0.0, vscale_exp: int = 0, merge_path: int = 0,
-                         group_launches: int = 0, stream=None) -> list[Result]:
+                         group_launches: int = 0, state=None, stream=None) -> list[Result]:
     """Algorithm 2 in place on every device block Xs[i] (n_i x k_i, FP32) of the graphs, in one
     call. Returns one ofsc_result per problem, in order."""
     count = len(graphs)
@@ -279,7 +286,8 @@ def ofsc_iterate_batched(graphs: list[Graph], method: int, Xs: list, tol: float,
         raise ValueError("ofsc_iterate_batched: one X per graph")
     o = Opts(gather, y_refresh, check_every, alpha0, None, 0, None, gram_engine, spmm_engine,
              1 if direct_launch else 0, 1 if cg_restart else 0, float(refine_tol), float(exact_tail),
-             int(vscale_exp), 0, 0, int(merge_path), int(group_launches))
+             int(vscale_exp), 0, 0, int(merge_path), int(group_launches),
+             None if state is None else state.handle)
     hs = (ctypes.c_void_p * count)(*[g.handle for g in graphs])
     ks = (ctypes.c_int32 * count)(*[int(X.shape[1]) for X in Xs])
     xs = (ctypes.c_void_p * count)(*[_arg(X, f"Xs[{i}]", "float32", rows=_rows(g))
@@ -367,6 +375,44 @@ def objective(X, w, src, dst, n: int, which: int = 1):
             return gX, gw
 
     return _Objective.apply(X, w)
+
+
+class State:
+    """The CG state of Algorithm 2 between ofsc_iterate calls on one graph with k columns
+    (ofsc_state_create): resume a run exactly, or checkpoint it to host memory."""
+
+    def __init__(self, g: Graph, k: int):
+        self.handle = ctypes.c_void_p()
+        _check(lib().ofsc_state_create(g.handle, int(k), ctypes.byref(self.handle)))
+
+    def info(self) -> tuple[int, int]:
+        """(updates of the run it holds, 0 if empty; bytes of its host image)."""
+        t, b = ctypes.c_int64(0), ctypes.c_int64(0)
+        _check(lib().ofsc_state_info(self.handle, ctypes.byref(t), ctypes.byref(b)))
+        return t.value, b.value
+
+    def save(self, stream=None) -> bytes:
+        """The state's host image (a checkpoint)."""
+        _, nbytes = self.info()
+        buf = ctypes.create_string_buffer(nbytes)
+        _check(lib().ofsc_state_save(self.handle, ctypes.cast(buf, ctypes.c_void_p), nbytes, _stream(stream)))
+        return buf.raw
+
+    def load(self, image: bytes, stream=None) -> None:
+        """Replaces the state by a host image of a state of the same n and k."""
+        buf = ctypes.create_string_buffer(bytes(image), len(image))
+        _check(lib().ofsc_state_load(self.handle, ctypes.cast(buf, ctypes.c_void_p), len(image), _stream(stream)))
+
+    def free(self):
+        if self.handle is not None and self.handle.value:
+            lib().ofsc_state_free(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
 
 
 def ofsc_rayleigh_ritz(g: Graph, X, ritz, stream=None) -> float:

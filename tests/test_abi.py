@@ -56,6 +56,18 @@ def test_host_side_argument_checks_of_the_widened_entry_points(lib):
     assert lib.ofsc_autotune(None, 4, 0, ctypes.byref(w), None, None, None, None) == ofsc.ERR_INVALID_ARG
 
 
+def test_state_api_argument_checks(lib):
+    """The CG state calls reject NULL handles and bad sizes on the host; freeing NULL is a no-op."""
+    import ctypes
+    h = ctypes.c_void_p()
+    assert lib.ofsc_state_create(None, 4, ctypes.byref(h)) == ofsc.ERR_INVALID_ARG
+    assert lib.ofsc_state_create(None, 4, None) == ofsc.ERR_INVALID_ARG
+    assert lib.ofsc_state_free(None) == ofsc.OK
+    assert lib.ofsc_state_info(None, None, None) == ofsc.ERR_INVALID_ARG
+    assert lib.ofsc_state_save(None, None, 0, None) == ofsc.ERR_INVALID_ARG
+    assert lib.ofsc_state_load(None, None, 0, None) == ofsc.ERR_INVALID_ARG
+
+
 def test_no_cpu_fallback_when_library_missing(monkeypatch, tmp_path):
     monkeypatch.setattr(ofsc, "_lib", None)
     monkeypatch.setattr(ofsc, "LIB_PATH", str(tmp_path / "missing.so"))

@@ -146,6 +146,76 @@ def test_first_updates_match_oracle(c1, method, restart):
         assert tr[t, 0] == t
 
 
+@pytest.mark.parametrize("method,gather", [(o.OFM_F1, 0), (o.TRI_F1, 0), (o.OFM_F2, 1), (o.TRI_F2, 0)])
+def test_cg_state_resumes_algorithm_2(c1, method, gather):
+    """Eight updates run as 5 + 3 with the CG state carried between the calls are Algorithm 2 as
+    one run: element by element against the oracle's eight updates, and within rounding of one
+    8-update call (the second call evaluates G_5 from an exact AX, the single call from the
+    recurrence). Resuming from a host checkpoint of the state gives the same bits; without the
+    state the second call restarts from steepest descent and departs from Algorithm 2."""
+    import torch
+    e, x0, og = c1
+    g = gpu_graph(e)
+    k = x0.shape[1]
+    rtol = 2e-3 if gather else 1e-4
+    ref = o.iterate(og, method, x0, 0.0, 8)
+    X1, _, _ = run_iterate(g, method, x0, 0.0, 8, gather=gather)
+    st = ofsc.State(g, k)
+    assert st.info()[0] == 0
+    X = torch.from_numpy(x0).cuda()
+    ra = ofsc.ofsc_iterate(g, method, X, 0.0, 5, gather=gather, state=st)
+    assert ra.iterations == 5 and st.info()[0] == 5
+    image = st.save()
+    Xmid = X.clone()
+    rb = ofsc.ofsc_iterate(g, method, X, 0.0, 3, gather=gather, state=st)
+    assert rb.iterations == 3 and st.info()[0] == 8
+    Xr = X.cpu().numpy()
+    assert_elementwise(Xr, ref.X, rtol, "resumed")
+    assert np.linalg.norm(Xr - X1) <= rtol * np.linalg.norm(X1)
+    # the same run from the host checkpoint, in a new state object
+    st2 = ofsc.State(g, k)
+    st2.load(image)
+    assert st2.info()[0] == 5
+    X2 = Xmid.clone()
+    ofsc.ofsc_iterate(g, method, X2, 0.0, 3, gather=gather, state=st2)
+    assert np.array_equal(X2.cpu().numpy(), Xr)
+    # no state: the second call restarts from steepest descent
+    X3 = Xmid.clone()
+    ofsc.ofsc_iterate(g, method, X3, 0.0, 3, gather=gather)
+    d_resumed = np.linalg.norm(Xr - ref.X)
+    d_restart = np.linalg.norm(X3.cpu().numpy() - ref.X)
+    assert d_restart > 10 * d_resumed, (d_restart, d_resumed)
+
+
+def test_cg_state_rules(c1):
+    """A state is for one n, k and method; a call that stops early leaves it empty; checkpoints
+    are checked; ofsc_iterate_batched takes none."""
+    import torch
+    e, x0, og = c1
+    g = gpu_graph(e)
+    k = x0.shape[1]
+    st = ofsc.State(g, k)
+    X = torch.from_numpy(x0).cuda()
+    ofsc.ofsc_iterate(g, o.OFM_F1, X, 0.0, 4, state=st)
+    assert st.info()[0] == 4
+    with pytest.raises(ofsc.OfscError) as ei:  # another method
+        ofsc.ofsc_iterate(g, o.TRI_F1, X.clone(), 0.0, 2, state=st)
+    assert ei.value.status == ofsc.ERR_INVALID_ARG
+    with pytest.raises(ofsc.OfscError) as ei:  # another k
+        ofsc.ofsc_iterate(g, o.OFM_F1, torch.from_numpy(x0[:, :k - 3].copy()).cuda(), 0.0, 2, state=st)
+    assert ei.value.status == ofsc.ERR_INVALID_ARG
+    with pytest.raises(ofsc.OfscError) as ei:
+        ofsc.ofsc_iterate_batched([g], o.OFM_F1, [X.clone()], 0.0, 2, state=st)
+    assert ei.value.status == ofsc.ERR_INVALID_ARG
+    image = st.save()
+    with pytest.raises(ofsc.OfscError) as ei:  # a damaged header
+        st.load(b"x" * len(image))
+    assert ei.value.status == ofsc.ERR_INVALID_ARG
+    assert st.info()[0] == 4
+    r = ofsc.ofsc_iterate(g, o.OFM_F1, X, 1e-1, 400, state=st)  # stops on tol: the state is emptied
+    assert r.status == ofsc.OK and st.info()[0] == 0
+
+
 def column_match(X, ref):
     """Columns equal up to sign (TriOFM fixed points are unique up to D = diag(+-1))."""
     s = np.sign(np.sum(X * ref, axis=0))

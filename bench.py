@@ -723,7 +723,6 @@ def run_gpu(args):
 
     for _ in range(args.warmup):
         step()
-    prof = ofsc.Profile()
     dev_id = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local if world > 1 else 0]
     try:
         dev_id = "GPU-" + str(torch.cuda.get_device_properties(local).uuid).replace("GPU-", "")
@@ -739,7 +738,7 @@ def run_gpu(args):
     t_start.record(stream)
     launches = 0
     for _ in range(args.steps):
-        r = step(prof)
+        r = step()  # the library's default path: repeating updates replayed from a CUDA graph
         launches += r.kernel_launches + 1  # + the X0 copy
     t_end.record(stream)
     torch.cuda.synchronize()
@@ -748,6 +747,20 @@ def run_gpu(args):
     elapsed_ms = max_over_ranks(elapsed_ms, world)
     updates = args.iters * args.steps * world
     value = updates / (elapsed_ms / 1000.0)
+
+    # per-phase device times from separate, untimed steps with CUDA events around every launch
+    # (direct launches; the events and launches cost host time, so these steps are not `value`)
+    prof = ofsc.Profile()
+    prof_steps = min(args.steps, 3)
+    torch.cuda.synchronize()
+    pp_start = torch.cuda.Event(enable_timing=True)
+    pp_end = torch.cuda.Event(enable_timing=True)
+    pp_start.record(stream)
+    for _ in range(prof_steps):
+        step(prof)
+    pp_end.record(stream)
+    torch.cuda.synchronize()
+    profiled_ms_per_step = pp_start.elapsed_time(pp_end) / prof_steps
 
     # the plain FP32 path on the same steps, for the mixed-vs-plain comparison of the metric
     plain = None
@@ -865,9 +878,10 @@ def run_gpu(args):
     # ncu capture, profiles/traffic.json) over the device time per update. `frac` divides by the
     # full time per update, exact refreshes included (they are part of every call); `frac_steady`
     # by the time of the updates without a refresh.
-    n_up = args.iters * args.steps
-    all_ms = sum(pd[p]["ms"] for p in pd) / n_up
-    upd_ms = (sum(pd[p]["ms"] for p in pd) - pd["refresh"]["ms"]) / n_up
+    # time per update from the timed steps (graph replay, no host gaps); the exact refreshes'
+    # share of it from the profiled steps
+    all_ms = elapsed_ms / (args.iters * args.steps)
+    upd_ms = all_ms - pd["refresh"]["ms"] / (args.iters * prof_steps)
     tu = measured_traffic(f"{args.workload}/{args.gather}" if args.nodes is None else "", "update")
     nkp = e.n * kp
     useful = (alg["total"]                      # the direction product (gathers net of L2 hits)
@@ -904,7 +918,8 @@ def run_gpu(args):
                 "data": "synthetic", "config": workload_config(args), "impl": "gpu",
                 "roofline": roof, "iteration_hbm": iteration, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": launches, "plain_fp32": plain, "time_to_tol": ttt, "legs": legs,
-                "phases_ms_per_step": {p: pd[p]["ms"] / args.steps for p in pd},
+                "phases_ms_per_step": {p: pd[p]["ms"] / prof_steps for p in pd},
+                "profiled_ms_per_step": profiled_ms_per_step,
                 "parallelism": "replicas only" if world > 1 else "single GPU"}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -224,10 +224,10 @@ typedef struct {
   int32_t merge_path;    /* 0 (default): the direction product (Sec. 3.3) splits its work by merge
                             path (equal shares of rows + nonzeros, so a long row spans several
                             warps, whose partial sums are added in warp order) when ofsc_autotune
-                            chose it for this k and gather storage, or, untuned, when the graph's
-                            longest row holds at least 1024 nonzeros and more than four warps'
-                            shares of the row partition; else by whole rows; 1: always by merge
-                            path; -1: never */
+                            chose it for this k and gather storage, or, untuned, when the graph
+                            holds at least 2^23 stored entries or its longest row holds at least
+                            1024 nonzeros and more than four warps' shares of the row partition;
+                            else by whole rows; 1: always by merge path; -1: never */
   int32_t group_launches; /* replayed updates: 0 (default) one launch per graph and kernel, on
                             the graphs' own streams; n in [1, 64]: grouped launches, where one
                             launch runs a kernel of the update for up to 32 graphs, its blocks a

@@ -1180,13 +1180,16 @@ ofsc_status bounds_checked(ofsc_status st, const char* who) {
 
 // Whether the direction product runs on the merge-path shares: forced on or off by `setting`
 // (> 0, < 0); else the form ofsc_autotune timed faster for this padded width and gather storage;
-// else when the longest row holds at least 1024 nonzeros and more than four warps' shares (the
-// warp that takes it whole then runs a chain of at least 128 dependent gather steps, several
-// times as long as the other warps').
+// else on graphs of at least 2^23 stored entries, where equal shares of rows + nonzeros balance
+// the rows' epilogues as well as the gathers and the fixup's launch is negligible (2M-node
+// DC-SBM, 60.6M entries: 2.26 -> 2.12 ms per BF16 product); else when the longest row holds at
+// least 1024 nonzeros and more than four warps' shares (the warp that takes it whole then runs a
+// chain of at least 128 dependent gather steps, several times as long as the other warps').
 bool use_merge_path(const ofsc_graph* g, int setting, int kp, bool bf16) {
   if (g->mp == nullptr || g->nnz <= 0 || g->groups[kRowPart] <= 0) return false;
   if (setting != 0) return setting > 0;
   if (g->dir_mp != 0 && g->dir_tuned_kp == kp && g->dir_tuned_bf16 == (bf16 ? 1 : 0)) return g->dir_mp > 0;
+  if (g->nnz >= (int64_t(1) << 23)) return true;
   return g->max_row >= 1024 && g->max_row * g->groups[kRowPart] > 4 * g->nnz;
 }
 

@@ -346,6 +346,27 @@ def ofsc_weight_grad(g: Graph, objective: int, X, src, dst, grad, stream=None) -
                                   _arg(grad, "grad", "float32", numel=m), _stream(stream)))
 
 
+_OBJ_GRAPHS: dict = {}  # graphs of objective(): key -> (Graph, src, dst, w), most recent last
+_OBJ_GRAPHS_MAX = 4
+
+
+def _objective_graph(n: int, src, dst, w) -> "Graph":
+    """The graph of (src, dst, w), built once and reused while the same tensors are passed again
+    unchanged (same objects, same in-place version counters; the cache holds references to them,
+    so their memory cannot be reused by other tensors meanwhile)."""
+    key = (int(n), src.data_ptr(), src._version, dst.data_ptr(), dst._version,
+           None if w is None else (w.data_ptr(), w._version))
+    hit = _OBJ_GRAPHS.get(key)
+    if hit is not None and hit[1] is src and hit[2] is dst and hit[3] is w:
+        _OBJ_GRAPHS[key] = _OBJ_GRAPHS.pop(key)
+        return hit[0]
+    g = ofsc_graph_build(n, src, dst, w)
+    _OBJ_GRAPHS[key] = (g, src, dst, w)
+    while len(_OBJ_GRAPHS) > _OBJ_GRAPHS_MAX:
+        _OBJ_GRAPHS.pop(next(iter(_OBJ_GRAPHS)))
+    return g
+
+
 def objective(X, w, src, dst, n: int, which: int = 1):
     """f1 (which=1) or f2 (which=2) of the graph with edge list (src, dst) and weights w at the
     feature block X, as a differentiable scalar (float64): backward gives df/dX (Eqs. (5), (10))
@@ -355,7 +376,7 @@ def objective(X, w, src, dst, n: int, which: int = 1):
     class _Objective(torch.autograd.Function):
         @staticmethod
         def forward(ctx, X, w):
-            g = ofsc_graph_build(n, src, dst, w)
+            g = _objective_graph(n, src, dst, w)
             G = torch.empty_like(X)
             f = ofsc_objective_grad(g, which, X, G)
             ctx.g = g

@@ -946,6 +946,32 @@ def test_batched_rejects_bad_arguments():
     assert ofsc.ofsc_iterate_batched([], o.OFM_F1, [], 0.0, 3) == []
 
 
+def test_objective_reuses_its_graph_until_the_edges_change():
+    """ofsc.objective builds the graph of (src, dst, w) once and reuses it while the same tensors
+    come back unchanged; an in-place change of w (an optimiser step) builds it again, and f follows
+    the new weights (against the oracle)."""
+    import torch
+    e = synth.sbm(2000, 8, 16.0, 6.0, weighted=True, seed=270)
+    x0 = synth.initial_block(e.n, 8, 271) * 4.0
+    src, dst, w = upload(e)
+    w = w.clone().requires_grad_(True)
+    X = torch.from_numpy(x0).cuda().requires_grad_(True)
+    ofsc._OBJ_GRAPHS.clear()
+    f1 = ofsc.objective(X, w, src, dst, e.n, 1)
+    g_first = next(iter(ofsc._OBJ_GRAPHS.values()))[0]
+    f1b = ofsc.objective(X, w, src, dst, e.n, 1)
+    assert len(ofsc._OBJ_GRAPHS) == 1 and next(iter(ofsc._OBJ_GRAPHS.values()))[0] is g_first
+    assert float(f1) == float(f1b)
+    with torch.no_grad():
+        w.mul_(1.25)
+    f2 = ofsc.objective(X, w, src, dst, e.n, 1)
+    assert len(ofsc._OBJ_GRAPHS) == 2
+    f_ref = o.objective_of_weights(e.n, e.src, e.dst, e.w.astype(np.float64) * 1.25, x0.astype(np.float64), 1)
+    assert abs(float(f2.detach()) - f_ref) <= 1e-5 * max(1.0, abs(f_ref))
+    f2.backward()
+    assert w.grad is not None and torch.isfinite(w.grad).all()
+
+
 @pytest.mark.parametrize("case", ["sbm_k8", "wsbm_k32"])
 def test_unrolled_grad_matches_oracle(case):
     """d f1(X_20) / d X_0 (and d/dw on the weighted graph) through 20 updates of OFM-f1,

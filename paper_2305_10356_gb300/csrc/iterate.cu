@@ -1364,6 +1364,10 @@ cudaError_t launch_gram(Workspace& ws, const GramPairs& pairs, int npairs, int s
   a.nt = gram_nt_for(ws.kp);
   int gy = 1;
   a.rows_per_group = gram_rows_per_group(ws.n, ws.kp, npairs, &gy);
+  if (gy > ws.gram_gy) {  // the workspace holds ws.gram_gy row groups: fewer, larger ones
+    a.rows_per_group = ceil_div(ceil_div(ws.n, (int64_t)ws.gram_gy), (int64_t)kGramChunk) * kGramChunk;
+    gy = (int)ceil_div(ws.n, a.rows_per_group);
+  }
   a.pairs = pairs;
   a.part = ws.gram_part;
   a.ctrl = ws.ctrl;
@@ -1819,9 +1823,12 @@ extern "C" ofsc_status ofsc_objective_grad(ofsc_graph* g, int32_t objective, int
   Prof prof{ws, nullptr, s};
   Runner run{g, ws, s, method, false, prof};
   run.mp = use_merge_path(g, 0, kp, false);
-  run.tc = kp > 64;
-  // a single evaluation: the direction pass in plain FP32 on the CUDA cores (the iteration's
-  // tensor-core pass accumulates its K = 128 or 256 products in FP32 tensor memory)
+  // a single evaluation, on the CUDA cores at every k: the Grams as FP32 products summed in FP64,
+  // and the direction pass in plain FP32. The iteration's tensor-core engines accumulate in FP32
+  // tensor memory, which at N = 2M biases the diagonal of X^T X by a few 1e-6 (512-row segments,
+  // rounding toward zero), and grad f = 4 (AX + X X^T X) cancels its two terms to 1.5e-5 of its
+  // largest entry there.
+  run.tc = false;
   run.tc_dir = false;
   k_init_ctrl<<<1, 1, 0, s>>>(ws.ctrl, 0.0, 0, k, g->normA2, 0);
   ++g_launches;
@@ -1871,7 +1878,7 @@ extern "C" ofsc_status ofsc_weight_grad(ofsc_graph* g, int32_t objective, int32_
   Prof prof{ws, nullptr, s};
   Runner run{g, ws, s, objective == OFSC_F1 ? M_OFM_F1 : M_OFM_F2, false, prof};
   run.mp = use_merge_path(g, 0, kp, false);
-  run.tc = kp > 64;
+  run.tc = false;  // a single evaluation: the CUDA-core Grams (FP64 sums), as ofsc_objective_grad
   DevBuf sbuf;
   OFSC_CUDA(dev_alloc(&sbuf.p, (size_t)(g->n + 1) * sizeof(float) + 16));
   void* scratch = sbuf.p;
@@ -1931,7 +1938,7 @@ extern "C" ofsc_status ofsc_rayleigh_ritz(ofsc_graph* g, int32_t k, const float*
   Prof prof{ws, nullptr, s};
   Runner run{g, ws, s, M_OFM_F1, false, prof};
   run.mp = use_merge_path(g, 0, kp, false);
-  run.tc = kp > 64;
+  run.tc = false;  // a single evaluation: the CUDA-core Grams (FP64 sums), as ofsc_objective_grad
   DevBuf wbuf;
   OFSC_CUDA(dev_alloc(&wbuf.p, (4 * (size_t)kp * kp + 2) * sizeof(double)));
   double* work = (double*)wbuf.p;

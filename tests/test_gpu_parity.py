@@ -95,7 +95,7 @@ def test_graph_build_rejects_bad_input(cuda_lib):
         assert ei.value.status == ofsc.ERR_INVALID_ARG
 
 
-OBJ_CASES = [("sbm_n1000_k11", None, None), ("dcsbm_n50k_k44", 8000, None),
+OBJ_CASES = [("sbm_n1000_k11", None, None), ("dcsbm_n50k_k44", 8000, None), ("dcsbm_n50k_k44", None, None),
              ("wsbm_n20k_k32", 4000, None), ("dcsbm_n2m_k128", 3001, 128)]
 
 
@@ -459,7 +459,8 @@ def test_column_scales_leave_the_bits_unchanged(method):
             assert ra.rel_dir_norm == rb.rel_dir_norm
 
 
-BF16_CASES = [("sbm_n1000_k11", None, None), ("dcsbm_n50k_k44", 8000, None), ("dcsbm_n2m_k128", 4000, 128)]
+BF16_CASES = [("sbm_n1000_k11", None, None), ("dcsbm_n50k_k44", 8000, None), ("dcsbm_n50k_k44", None, None),
+              ("dcsbm_n2m_k128", 4000, 128)]
 
 
 @pytest.mark.parametrize("name,n,k", BF16_CASES)
@@ -957,6 +958,26 @@ def test_grouped_launches_match_per_graph_launches(gather):
     r1 = ofsc.ofsc_iterate(graphs[4], o.OFM_F1, X1, 0.0, 20, gather=gather, group_launches=1)
     r2 = ofsc.ofsc_iterate(graphs[4], o.OFM_F1, X2, 0.0, 20, gather=gather)
     assert torch.equal(X1, X2) and r1.rel_dir_norm == r2.rel_dir_norm
+
+
+def test_batched_full_size_in_the_bench_configuration():
+    """The 32-graph batch at full size (N from 3.5K to 99K, k from 8 to 64, sum N = 1.53M) as
+    bench.py --workload sbm_batch32 runs it (one batched call, BF16 gathers, the product's shape
+    autotuned per graph), five updates of OFM-f1; the smallest, the median and the largest graph
+    against the oracle element by element (2e-3 of max|X|, one BF16 unit roundoff)."""
+    import torch
+    probs = synth.batch("sbm_batch32", 1.0)
+    graphs = [gpu_graph(e) for e, _ in probs]
+    for g, (e, x0) in zip(graphs, probs):
+        ofsc.ofsc_autotune(g, x0.shape[1], ofsc.GATHER_BF16)
+    Xs = [torch.from_numpy(x0).cuda() for _, x0 in probs]
+    rs = ofsc.ofsc_iterate_batched(graphs, o.OFM_F1, Xs, 0.0, 5, gather=ofsc.GATHER_BF16)
+    assert all(r.iterations == 5 for r in rs)
+    order = np.argsort([e.n for e, _ in probs])
+    for i in (order[0], order[len(order) // 2], order[-1]):
+        e, x0 = probs[i]
+        ref = o.iterate(o.build_graph(e.n, e.src, e.dst), o.OFM_F1, x0, 0.0, 5)
+        assert_elementwise(Xs[i].cpu().numpy(), ref.X, 2e-3, f"graph {i} (N = {e.n}, k = {x0.shape[1]})")
 
 
 def test_batched_matches_oracle():

@@ -804,6 +804,53 @@ def test_streaming_snapshots_warm_start_match_oracle():
     assert warm.iterations < cold.iterations
 
 
+@pytest.mark.parametrize("gather,rtol", [(ofsc.GATHER_FP32, 1e-4), (ofsc.GATHER_BF16, 5e-3)])
+def test_streaming_full_size_in_the_bench_configuration(gather, rtol):
+    """The stream of bench.py --workload sbm_stream_n200k_k71 at full size (200,000 nodes, k = 71,
+    cumulative edge-sampled snapshots; the bench's BF16 gathers, and FP32), its first three
+    snapshots with X carried from each into the next, five updates each: every snapshot against the
+    oracle started from the same X (the GPU's X after the previous snapshot), element by element.
+    FP32 within 1e-4. BF16 within 5e-3 of max|X|: the first snapshot holds 10% of the edges, about
+    three neighbours a node, so a row's A V carries its few gathered values' BF16 rounding (2^-9)
+    unaveraged, and five line-searched updates compound it to about two units (measured 1.9e-4
+    against max|X| = 0.048 in 51 of 14.2M entries)."""
+    import torch
+    snaps, x0 = synth.stream("sbm_stream_n200k_k71")
+    X = torch.from_numpy(x0).cuda()
+    for e in snaps[:3]:
+        g = gpu_graph(e)
+        x_in = X.cpu().numpy()
+        r = ofsc.ofsc_iterate(g, o.OFM_F1, X, 0.0, 5, gather=gather)
+        assert r.iterations == 5
+        ref = o.iterate(o.build_graph(e.n, e.src, e.dst), o.OFM_F1, x_in, 0.0, 5)
+        assert_elementwise(X.cpu().numpy(), ref.X, rtol, f"snapshot with {e.src.size} listed edges")
+        g.free()
+
+
+def test_unrolled_grad_full_size():
+    """The unrolled gradient on C5 at full size (weighted SBM, 20,000 nodes, k = 32, the graph of
+    bench.py --workload wsbm_n20k_k32 --unrolled 20), through T = 5 updates with checkpoints every
+    5 (the launches of every update are those of T = 20; five line-searched updates keep the
+    gradient well conditioned): f1(X_T) within 1e-5, d/dX_0 and d/dw within 1e-3 (norm) of the
+    oracle's reverse sweep, and every weight-gradient entry within 1e-3 of the largest."""
+    import torch
+    e, x0 = synth.workload("wsbm_n20k_k32")
+    og = o.build_graph(e.n, e.src, e.dst, e.w.astype(np.float64), exact=True)
+    g = gpu_graph(e)
+    T = 5
+    f_ref, g_ref, w_ref = o.unrolled_grad(og, x0.astype(np.float64), T, edges=(e.src, e.dst, e.w.astype(np.float64)))
+    X0 = torch.from_numpy(x0).cuda()
+    src, dst, _ = upload(e)
+    grad = torch.empty_like(X0)
+    gw = torch.full((e.src.size,), float("nan"), dtype=torch.float32, device="cuda")
+    f = ofsc.ofsc_unrolled_grad(g, X0, T, grad, ckpt=5, src=src, dst=dst, grad_w=gw)
+    G, W = grad.cpu().numpy(), gw.cpu().numpy()
+    assert abs(f - f_ref) <= 1e-5 * abs(f_ref)
+    assert np.linalg.norm(G - g_ref) <= 1e-3 * np.linalg.norm(g_ref)
+    assert np.linalg.norm(W - w_ref) <= 1e-3 * np.linalg.norm(w_ref)
+    assert np.abs(W - w_ref).max() <= 1e-3 * np.abs(w_ref).max()
+
+
 @pytest.mark.parametrize("k,n", [(8, 2500), (128, 2500), (8, 12000)])
 def test_rayleigh_ritz_matches_oracle(k, n):
     """Ritz values of B = -A on span(X) and relerr (Sec. 5) from the device's Grams and FP64 k x k

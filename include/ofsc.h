@@ -242,6 +242,14 @@ typedef struct {
                             ||G_0||. A call that performs all maxit > 0 updates without stopping
                             leaves its own state in it (t grows by maxit); a call that stops or
                             fails leaves it empty. */
+  int32_t overlap_gram;  /* where each update's Grams V^T X, V^T V (Sec. 3.3) run. 1: on a second
+                            stream of the graph, at the same time as the direction product (both
+                            read the V that the V pass wrote; neither writes what the other reads),
+                            and the line search waits for both; -1: after the product on the
+                            call's stream; 0 (default): 1 for a call on one graph with n kp <= 2^23
+                            (padded k), else -1. Same kernels, same results bit for bit. Ignored
+                            with group_launches > 0 or `profile`; for the f2 methods only with the
+                            tensor-core Grams, whose V^T AX, V^T AV launch follows the product */
 } ofsc_opts;
 
 typedef struct {

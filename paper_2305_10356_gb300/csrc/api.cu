@@ -139,6 +139,9 @@ ofsc_status ofsc_graph_free(ofsc_graph* g) {
   for (int i = 0; i < 6; ++i) ofsc::dev_free(g->bnd[i]);
   ofsc::dev_free(g->mp);
   if (g->stream) cudaStreamDestroy(g->stream);
+  if (g->side) cudaStreamDestroy(g->side);
+  if (g->side_fork) cudaEventDestroy(g->side_fork);
+  if (g->side_join) cudaEventDestroy(g->side_join);
   cudaSetDevice(prev);
   delete g;
   return OFSC_OK;

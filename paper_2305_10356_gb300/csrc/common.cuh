@@ -250,6 +250,10 @@ struct ofsc_graph {
   int groups[6] = {0, 0, 0, 0, 0, 0};
   ofsc::Workspace ws;
   cudaStream_t stream = nullptr;  // this graph's stream in ofsc_iterate_batched (created on first use)
+  // opts.overlap_gram: the stream the Grams V^T X, V^T V run on beside the direction product, and
+  // the events that fork it from and join it to the update's stream (created on first use)
+  cudaStream_t side = nullptr;
+  cudaEvent_t side_fork = nullptr, side_join = nullptr;
 };
 
 namespace ofsc {

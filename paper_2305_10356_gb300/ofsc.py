@@ -61,7 +61,7 @@ class Opts(ctypes.Structure):
                 ("exact_tail", ctypes.c_double), ("vscale_exp", ctypes.c_int32),
                 ("spin_limit", ctypes.c_int64), ("withhold_arrivals", ctypes.c_int32),
                 ("merge_path", ctypes.c_int32), ("group_launches", ctypes.c_int32),
-                ("state", ctypes.c_void_p)]
+                ("state", ctypes.c_void_p), ("overlap_gram", ctypes.c_int32)]
 
 
 class Result(ctypes.Structure):
@@ -256,7 +256,8 @@ def ofsc_iterate(g: Graph, method: int, X, tol: float, maxit: int, *, gather: in
                  spmm_engine: int = SPMM_AUTO, cg_restart: bool = False, refine_tol: float = 0.0,
                  exact_tail: float = 0.0, vscale_exp: int = 0, direct_launch: bool = False,
                  spin_limit: int = 0, withhold_arrivals: bool = False, merge_path: int = 0,
-                 group_launches: int = 0, state: "State | None" = None, stream=None) -> Result:
+                 group_launches: int = 0, state: "State | None" = None, overlap_gram: int = 0,
+                 stream=None) -> Result:
     """Algorithm 2 in place on the device block X (n x k, FP32). Returns the ofsc_result. With a
     State, the call continues the run the state holds and leaves its own state in it."""
     px = _arg(X, "X", "float32", rows=_rows(g))
@@ -265,7 +266,7 @@ def ofsc_iterate(g: Graph, method: int, X, tol: float, maxit: int, *, gather: in
              ctypes.pointer(profile) if profile is not None else None, gram_engine, spmm_engine,
              1 if direct_launch else 0, 1 if cg_restart else 0, float(refine_tol), float(exact_tail),
              int(vscale_exp), int(spin_limit), 1 if withhold_arrivals else 0, int(merge_path),
-             int(group_launches), None if state is None else state.handle)
+             int(group_launches), None if state is None else state.handle, int(overlap_gram))
     r = Result()
     _check(lib().ofsc_iterate(g.handle, method, int(X.shape[1]), px, float(tol), int(maxit),
                               ctypes.byref(o), ctypes.byref(r), _stream(stream)),
@@ -278,7 +279,8 @@ def ofsc_iterate_batched(graphs: list[Graph], method: int, Xs: list, tol: float,
                          alpha0: float = 0.0, gram_engine: int = GRAM_AUTO, spmm_engine: int = SPMM_AUTO,
                          direct_launch: bool = False, cg_restart: bool = False, refine_tol: float = 0.0,
                          exact_tail: float = 0.0, vscale_exp: int = 0, merge_path: int = 0,
-                         group_launches: int = 0, state=None, stream=None) -> list[Result]:
+                         group_launches: int = 0, state=None, overlap_gram: int = 0,
+                         stream=None) -> list[Result]:
     """Algorithm 2 in place on every device block Xs[i] (n_i x k_i, FP32) of the graphs, in one
     call. Returns one ofsc_result per problem, in order."""
     count = len(graphs)
@@ -287,7 +289,7 @@ def ofsc_iterate_batched(graphs: list[Graph], method: int, Xs: list, tol: float,
     o = Opts(gather, y_refresh, check_every, alpha0, None, 0, None, gram_engine, spmm_engine,
              1 if direct_launch else 0, 1 if cg_restart else 0, float(refine_tol), float(exact_tail),
              int(vscale_exp), 0, 0, int(merge_path), int(group_launches),
-             None if state is None else state.handle)
+             None if state is None else state.handle, int(overlap_gram))
     hs = (ctypes.c_void_p * count)(*[g.handle for g in graphs])
     ks = (ctypes.c_int32 * count)(*[int(X.shape[1]) for X in Xs])
     xs = (ctypes.c_void_p * count)(*[_arg(X, f"Xs[{i}]", "float32", rows=_rows(g))

@@ -1007,6 +1007,45 @@ def test_grouped_launches_match_per_graph_launches(gather):
     assert torch.equal(X1, X2) and r1.rel_dir_norm == r2.rel_dir_norm
 
 
+@pytest.mark.parametrize("gather", [0, 1])
+def test_overlapped_grams_match_serial(gather):
+    """opts.overlap_gram = 1 runs V^T X and V^T V on a second stream beside the direction product
+    (the default for one graph of n kp <= 2^23, as here): the same kernels on the same inputs, so
+    the same bits as the serial order (overlap_gram = -1), for every method,
+    with the tensor-core Grams (k = 128) and the CUDA-core ones (k = 20), on whole rows and on
+    merge-path shares, replayed and launched directly, and in a batched call."""
+    import torch
+    e = synth.sbm(6000, 8, 18.0, 5.0, ratio_kind="count", seed=250)
+    cases = [(gpu_graph(e), synth.initial_block(e.n, 128, 251), 0),
+             (gpu_graph(e), synth.initial_block(e.n, 20, 252), 0),
+             (gpu_graph(hub_graph(False, 253)), synth.initial_block(6000, 128, 254), 1)]
+    for method in METHODS:
+        for g, x0, mp in cases:
+            for direct in (False, True):
+                out = []
+                for ov in (-1, 0, 1):  # serial; the default (overlapped at these sizes); overlapped
+                    X = torch.from_numpy(x0).cuda()
+                    r = ofsc.ofsc_iterate(g, method, X, 0.0, 40, gather=gather, merge_path=mp,
+                                          direct_launch=direct, overlap_gram=ov)
+                    out.append((X.cpu().numpy(), (r.iterations, r.status, r.rel_dir_norm, r.f)))
+                for x, res in out[1:]:
+                    assert np.array_equal(out[0][0], x), (method, x0.shape, mp, direct)
+                    assert out[0][1] == res
+        graphs = [c[0] for c in cases]
+        outs = []
+        for ov in (-1, 1):
+            Xs = [torch.from_numpy(c[1]).cuda() for c in cases]
+            rs = ofsc.ofsc_iterate_batched(graphs, method, Xs, 0.0, 37, gather=gather, overlap_gram=ov)
+            outs.append(([X.cpu().numpy() for X in Xs], [(r.iterations, r.status, r.rel_dir_norm) for r in rs]))
+        for a, b in zip(outs[0][0], outs[1][0]):
+            assert np.array_equal(a, b), method
+        assert outs[0][1] == outs[1][1]
+    for bad in (-2, 2):
+        with pytest.raises(ofsc.OfscError) as ei:
+            ofsc.ofsc_iterate(cases[1][0], o.OFM_F1, torch.from_numpy(cases[1][1]).cuda(), 0.0, 2, overlap_gram=bad)
+        assert ei.value.status == ofsc.ERR_INVALID_ARG and "overlap_gram" in str(ei.value)
+
+
 def test_batched_full_size_in_the_bench_configuration():
     """The 32-graph batch at full size (N from 3.5K to 99K, k from 8 to 64, sum N = 1.53M) as
     bench.py --workload sbm_batch32 runs it (one batched call, BF16 gathers, the product's shape

@@ -166,17 +166,33 @@ def max_over_ranks(x: float, world: int) -> float:
     return float(t.item())
 
 
+L2_BYTES = 129 * 2**20  # GB300's L2 (126.5 MiB reported), rounded up
+
+
+def l2_flushed(args) -> bool:
+    """Whether the steps flush the L2: unless every N x kp block and the CSR (stored entries about
+    N times the mean degree) are each more than twice the L2."""
+    from paper_2305_10356_gb300 import synth
+    spec = synth.WORKLOADS[args.workload]
+    n = args.nodes or spec["n"]
+    kp = ((spec["n_blocks"] + 7) // 8) * 8
+    csr = 8 * (n + 1) + 4 * n * spec["mean_degree"]
+    return min(4 * n * kp, csr) <= 2 * L2_BYTES
+
+
 def workload_config(args) -> dict:
     from paper_2305_10356_gb300 import synth
     spec = synth.WORKLOADS[args.workload]
     n = args.nodes or spec["n"]
     kind = "degree-corrected SBM" if spec.get("gamma") else "SBM"
+    l2 = (f"L2 flushed at the start of every step by a {2 * L2_BYTES >> 20} MB write inside the timed region "
+          "(the inputs are smaller than the L2)" if l2_flushed(args) else
+          "inputs larger than L2 (X, state and CSR are each > 129 MB)")
     return {"workload": f"{args.workload}: {kind}, N={n}, k={spec['n_blocks']}, mean degree "
                         f"{spec['mean_degree']:g}, power-law {spec.get('gamma')}, within:between "
                         f"{spec['ratio']:g}:1 ({spec['ratio_kind']}), int32 CSR, seeded synthetic",
             "n": n, "k": spec["n_blocks"], "method": METHOD_LABEL[args.method],
-            "gather": args.gather, "updates_per_step": args.iters,
-            "l2": "inputs larger than L2 (X, state and CSR are each > 129 MB)"}
+            "gather": args.gather, "updates_per_step": args.iters, "l2": l2}
 
 
 SAMPLE_FRACTION = 5  # the CPU oracle runs on a graph of N / 5 nodes drawn with the same recipe
@@ -470,7 +486,10 @@ def run_stream(args):
     X = torch.empty_like(X0)
     stream = torch.cuda.current_stream()
 
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")  # the state is below 2x L2
+
     def step():
+        flush.zero_()
         X.copy_(X0)
         n_up = 0
         for (src, dst), e in zip(dev, snaps):
@@ -504,7 +523,9 @@ def run_stream(args):
                 "config": {"workload": f"{args.workload}: SBM, N={args.nodes or spec['n']}, k={spec['n_blocks']}, "
                                        f"mean degree {spec['mean_degree']:g} at 100%, {spec['parts']} cumulative "
                                        f"edge-sampled snapshots, warm start, graph builds timed",
-                           "updates_per_snapshot": args.iters, "method": METHOD_LABEL[args.method]},
+                           "updates_per_snapshot": args.iters, "method": METHOD_LABEL[args.method],
+                           "l2": f"L2 flushed at the start of every step by a {2 * L2_BYTES >> 20} MB write "
+                                 "inside the timed region"},
                 "impl": "gpu", "parallelism": "replicas only" if world > 1 else "single GPU"}
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -652,8 +673,11 @@ def run_unrolled(args):
     gw = torch.empty(e.src.size, dtype=torch.float32, device="cuda") if w is not None else None
     stream = torch.cuda.current_stream()
     T = args.unrolled
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda") if l2_flushed(args) else None
 
     def step():
+        if flush is not None:
+            flush.zero_()
         return ofsc.ofsc_unrolled_grad(g, X0, T, grad, ckpt=args.ckpt, src=src if w is not None else None,
                                        dst=dst if w is not None else None, grad_w=gw)
 
@@ -692,7 +716,7 @@ def run_unrolled(args):
                                        f"{'weighted' if e.w is not None else 'binary'}; d f1(X_T)/dX_0"
                                        f"{' and d/dw' if e.w is not None else ''} through T={T} OFM-f1 updates, "
                                        f"checkpoint every {args.ckpt}",
-                           "T": T, "ckpt": args.ckpt},
+                           "T": T, "ckpt": args.ckpt, "l2": workload_config(args)["l2"]},
                 "impl": "gpu", "cpu_baseline": cpu,
                 "parallelism": "replicas only" if world > 1 else "single GPU"}
         print(json.dumps(line), flush=True)
@@ -720,8 +744,14 @@ def run_gpu(args):
     X = torch.empty_like(X0)
     stream = torch.cuda.current_stream()
     eng = {"auto": ofsc.SPMM_AUTO, "simt": ofsc.SPMM_SIMT, "tma": ofsc.SPMM_TMA}[args.spmm_engine]
+    # Between steps no input may be served from L2: either every N x kp block and the CSR are
+    # larger than the L2, or the L2 is flushed (a write of twice its size) at the start of every
+    # step, inside the timed region.
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda") if l2_flushed(args) else None
 
     def step(prof=None):
+        if flush is not None:
+            flush.zero_()
         X.copy_(X0)
         return ofsc.ofsc_iterate(g, method, X, 0.0, args.iters, gather=gather, profile=prof, spmm_engine=eng)
 
@@ -743,7 +773,7 @@ def run_gpu(args):
     launches = 0
     for _ in range(args.steps):
         r = step()  # the library's default path: repeating updates replayed from a CUDA graph
-        launches += r.kernel_launches + 1  # + the X0 copy
+        launches += r.kernel_launches  # the library's kernels (not the X0 copy or the L2 flush)
     t_end.record(stream)
     torch.cuda.synchronize()
     clocks = sampler.stop()
@@ -770,6 +800,8 @@ def run_gpu(args):
     plain = None
     if gather == ofsc.GATHER_BF16 and not args.no_fp32_compare:
         def step32():
+            if flush is not None:
+                flush.zero_()
             X.copy_(X0)
             return ofsc.ofsc_iterate(g, method, X, 0.0, args.iters, gather=ofsc.GATHER_FP32, spmm_engine=eng)
         step32()
@@ -820,6 +852,8 @@ def run_gpu(args):
                         ev_in[nxt].record(copy)
             else:
                 Xd[cur].copy_(Xh0, non_blocking=True)
+            if flush is not None:
+                flush.zero_()
             ofsc.ofsc_iterate(g, method, Xd[cur], 0.0, args.iters, gather=gather, spmm_engine=eng)
             if pipelined:
                 ev_done[cur].record(stream)
@@ -893,9 +927,24 @@ def run_gpu(args):
               + 12 * nkp + gb * nkp             # V pass: read G, V; write V, D^-1/2 V
               + 8 * nkp)                        # Grams: read V, X
     useful_gbs = useful / (all_ms / 1000.0) / 1e9
+    # All the compulsory bytes of one call: its updates, the exact refreshes at its start and end
+    # (D^-1/2 X; A X with FP32 gathers; X^T X and X^T AX), the direction pass of update maxit,
+    # the evaluation pass of the report, and the copies of X in and out of the padded layout.
+    # The FP32 product's gathers hit L2 at the rate of that kernel's capture, else at this one's.
+    tr32 = measured_traffic(wk, "fp32", any_build=True)
+    h32 = h
+    if tr32 is not None:
+        b32 = spmm_bytes(e.n, kp, int(info.nnz), 4, bool(info.weighted), 0.0)
+        h32 = min(1.0, max(0.0, 1.0 - (tr32["dram_read_bytes"] - b32["csr"] - b32["epilogue"]) / b32["gather_all"]))
+    refresh = 8 * nkp + spmm_bytes(e.n, kp, int(info.nnz), 4, bool(info.weighted), h32)["total"] + 8 * nkp
+    nk = e.n * e.n_blocks
+    call = (args.iters * useful + 2 * refresh + 32 * nkp + 8 * nkp
+            + (4 * nk + 4 * nkp) + (4 * nkp + 4 * nk))
+    call_frac = call / (all_ms * args.iters / 1000.0) / 1e9 / peaks["hbm_gbs"]
     iteration = {"ms_per_update": all_ms, "ms_per_update_steady": upd_ms, "useful_bytes": useful,
                  "useful_gbs": useful_gbs, "frac": useful_gbs / peaks["hbm_gbs"],
                  "frac_steady": useful / (upd_ms / 1000.0) / 1e9 / peaks["hbm_gbs"],
+                 "useful_bytes_per_call": call, "refresh_gather_l2_hit": round(h32, 4), "frac_call": call_frac,
                  "target_frac": 0.70, "gap_to_target": 0.70 - useful_gbs / peaks["hbm_gbs"],
                  "dram_bytes": (tu["dram_read_bytes"] + tu["dram_write_bytes"]) if tu else None}
     if tu:

@@ -485,17 +485,24 @@ __device__ __forceinline__ void beta_body(const BetaArgs& a) {
     }
   }
   __syncthreads();
+  // the lane groups in group order, one thread per (sum, column): spread over the warps, as an
+  // FP64 add chain in one warp per column would hold one sub-partition's FP64 unit for all of it
+  __shared__ double tot[kColSums * kMaxK];  // [kColSums][kp]
+  for (int t = j; t < kColSums * kp; t += 256) {
+    const int q = t / kp, c = t % kp;
+    double acc = 0.0;
+    for (int l = 0; l < 256 / kp; ++l) acc += lanes[(l * kColSums + q) * kp + c];
+    tot[t] = acc;
+  }
+  __syncthreads();
   double gg = 0.0, num = 0.0, den = 0.0, gy = 0.0, vy = 0.0, vg = 0.0;
   if (j < kp) {
-    for (int l = 0; l < 256 / kp; ++l) {
-      const double* p = lanes + l * kColSums * kp;
-      gg += p[j];
-      num += p[kp + j];
-      den += p[2 * kp + j];
-      gy += p[3 * kp + j];
-      vy += p[4 * kp + j];
-      vg += p[5 * kp + j];
-    }
+    gg = tot[j];
+    num = tot[kp + j];
+    den = tot[2 * kp + j];
+    gy = tot[3 * kp + j];
+    vy = tot[4 * kp + j];
+    vg = tot[5 * kp + j];
   }
   sh[j] = gg;
   __syncthreads();
@@ -553,7 +560,7 @@ __device__ __forceinline__ void beta_body(const BetaArgs& a) {
     // column scale of V_t: |V_t,j| <= |G_t,j| + |beta_j| s_old |Vs_{t-1,j}| = mu; s_t = 1 while
     // mu <= 2^vscale_exp ||G_0||, else the power of two that brings the stored column back under it
     // (scaling by powers of two is exact, so the stored values carry the same bits of V)
-    double s_new = 1.0;
+    double s_new = 1.0, inv_s = 1.0;  // 1 / s_new, exact for a power of two (no FP64 division)
     if (!first) {
       const double mu = sqrt(gg) + fabs(b) * s_old * sqrt(fmax(qprev[(int64_t)j * kp + j], 0.0));
       const double ref = ldexp(ctrl->g0, ctrl->vscale_exp);
@@ -561,11 +568,12 @@ __device__ __forceinline__ void beta_body(const BetaArgs& a) {
         int e = 0;
         frexp(mu / ref, &e);  // mu / ref in [2^(e-1), 2^e)
         s_new = ldexp(1.0, e);
+        inv_s = ldexp(1.0, -e);
       }
     }
     vscale[j] = s_new;
-    vinv[j] = (float)(1.0 / s_new);
-    beta[j] = (float)(b * s_old / s_new);
+    vinv[j] = (float)inv_s;
+    beta[j] = (float)(b * s_old * inv_s);
     beta64[j] = b;
     // diag(V_t^T AX_t) with V_t = -G_t + V_{t-1} diag(beta): -diag(G^T AX) + beta diag(V_prev^T AX)
     if (dE) dE[j] = first ? -gy : -gy + b * s_old * vy;
@@ -773,16 +781,44 @@ __global__ void __launch_bounds__(256) k_gram_reduce_g(const __grid_constant__ G
 // ------------------------------------------------------------------------------------------
 
 
+// Sum over the 256 threads of each of NV <= 16 values, every thread receiving the totals. Value
+// q is summed by warp q mod 8: lane l adds the values of threads l, l + 32, ..., l + 224 in that
+// order, then the lanes are added pairwise (offsets 16, 8, 4, 2, 1). A fixed order, so the sums
+// repeat bit for bit. On GB300 an FP64 warp instruction occupies its sub-partition's FP64 unit for
+// tens of cycles, so the cost is the number of FP64 instructions on the busiest sub-partition:
+// about 3,800 cycles for 15 values, against 14,000 for a pairwise tree over the threads, whose
+// last levels run in one warp.
 template <int NV>
 __device__ void block_sum(double (&v)[NV], double* sh) {
-  const int tid = threadIdx.x;
+  static_assert(NV <= 16, "two values per warp");
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+#pragma unroll
   for (int q = 0; q < NV; ++q) sh[q * 256 + tid] = v[q];
   __syncthreads();
-  for (int s = 128; s > 0; s >>= 1) {
-    if (tid < s)
-      for (int q = 0; q < NV; ++q) sh[q * 256 + tid] += sh[q * 256 + tid + s];
-    __syncthreads();
+  double t[2] = {0.0, 0.0};
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const int q = w + 8 * u;
+    if (q < NV) {
+      double s = sh[q * 256 + lane];
+#pragma unroll
+      for (int i = 1; i < 8; ++i) s += sh[q * 256 + lane + 32 * i];
+      t[u] = s;
+    }
   }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+      if (w + 8 * u < NV) t[u] += __shfl_down_sync(0xffffffffu, t[u], off);
+  __syncthreads();  // every thread has read its rows before the totals are written over them
+  if (lane == 0) {
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+      if (w + 8 * u < NV) sh[(w + 8 * u) * 256] = t[u];
+  }
+  __syncthreads();
+#pragma unroll
   for (int q = 0; q < NV; ++q) v[q] = sh[q * 256];
   __syncthreads();
 }
@@ -994,12 +1030,15 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, const VBlock vb) 
       c1 = 2.0 * (2.0 * v[12] - 2.0 * v[6] - 2.0 * v[7] - v[8] - v[9]);
       c0 = v[14];  // = 2 tr(2E - P B - R E) = tr(V^T grad f2)
     }
-    // one thread solves the cubic (FP64 issue is scarce: 8 warps solving it would cost 8x)
-    if (tid == 0) {
+    // warp 0 solves the cubic, its three real roots (if it has three) in lanes 0-2 at once (FP64
+    // issue is scarce: 8 warps solving it would cost 8x)
+    if (tid < 32) {
       int b = 0;
-      const double st = pick_step(c3, c2, c1, c0, &b);
-      bad |= b;
-      al[0] = st;
+      const double st = pick_step_warp(c3, c2, c1, c0, &b);
+      if (tid == 0) {
+        bad |= b;
+        al[0] = st;
+      }
     }
     __syncthreads();
     const double st = al[0];

@@ -462,6 +462,26 @@ ofsc_status ofsc_gram(int64_t n, int32_t k, int32_t ld, const float* L, int32_t 
                       int64_t rows_per_block, double* out, void* stream);
 
 /*
+ * ofsc_line_search_step - the step of the exact line search (Sec. 3.2) for n cubics
+ * c3 a^3 + c2 a^2 + c1 a + c0 (the derivative of the objective along the direction, up to a
+ * positive factor): among the real roots (Cardano's formula, each root polished by two Newton
+ * steps), the one where q(a) = c3 a^4/4 + c2 a^3/3 + c1 a^2/2 + c0 a is smallest, ties to the
+ * smaller |a| and then the smaller a; 0 when the cubic has no real root or is identically zero.
+ * These are the solvers ofsc_iterate runs: solver 0 takes one thread per cubic (the per-column
+ * cubics of TriOFM, Eqs. (16)/(18)), solver 1 one warp per cubic, the three roots of a cubic with
+ * three real roots in three lanes (the single cubic of OFM, Eqs. (15)/(17)); both give the same
+ * bits.
+ *   coef   device float64 [n][4], {c3, c2, c1, c0} per cubic
+ *   steps  device float64 [n] (written)
+ *   bad    device int32 [n] or NULL: 1 where a coefficient is not finite (its step is then 0)
+ * Asynchronous on `stream`; allocates nothing.
+ * Errors: OFSC_ERR_INVALID_ARG (n < 0, NULL coef or steps with n > 0, solver not 0 or 1),
+ * OFSC_ERR_CUDA.
+ */
+ofsc_status ofsc_line_search_step(int64_t n, const double* coef, int32_t solver, double* steps, int32_t* bad,
+                                  void* stream);
+
+/*
  * ofsc_set_allocator - makes the library take every device block it allocates (graph arrays,
  * workspaces, scratch) from the caller's allocator instead of cudaMalloc, for a process whose device
  * memory belongs to another allocator (a framework's caching pool). Not in the paper.

@@ -13,7 +13,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libofsc.so")
 BUILD_DEBUG = os.path.join(PKG, "_build_debug")
 LIB_DEBUG = os.path.join(PKG, "libofsc_debug.so")
-SOURCES = ["api.cu", "graph.cu", "iterate.cu", "spmm_dir.cu", "cluster.cu", "gram_tc.cu", "spmm_tma.cu", "direction_tc.cu", "ritz.cu", "wgrad.cu", "unroll.cu", "group.cu"]
+SOURCES = ["api.cu", "graph.cu", "iterate.cu", "spmm_dir.cu", "cluster.cu", "gram_tc.cu", "spmm_tma.cu", "direction_tc.cu", "ritz.cu", "wgrad.cu", "unroll.cu", "group.cu", "linesearch.cu"]
 HEADERS = [os.path.join(CSRC, "common.cuh"), os.path.join(CSRC, "spmm_dir.cuh"), os.path.join(CSRC, "tcgen05.cuh"), os.path.join(CSRC, "cubic.cuh"), os.path.join(CSRC, "group.cuh"), os.path.join(CSRC, "spmm_dir_body.inc"), os.path.join(CSRC, "direction_body.inc"), os.path.join(ROOT, "include", "ofsc.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

@@ -121,6 +121,7 @@ def lib() -> ctypes.CDLL:
             "ofsc_state_info": [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)],
             "ofsc_state_save": [vp, vp, i64, vp],
             "ofsc_state_load": [vp, vp, i64, vp],
+            "ofsc_line_search_step": [i64, vp, i32, vp, vp, vp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -462,6 +463,18 @@ def ofsc_set_allocator(alloc=None, free=None) -> None:
     _check(lib().ofsc_set_allocator(cb[0], cb[1], None))
     # callbacks of blocks still owned by the library must outlive them: keep every pair set
     _allocator = (_allocator or ()) + (cb,)
+
+
+def ofsc_line_search_step(coef, steps, bad=None, solver: int = 1, stream=None) -> None:
+    """The exact line search's step (Sec. 3.2) of each cubic coef[i] = (c3, c2, c1, c0) (device
+    FP64 [n, 4]) into steps (device FP64 [n]); bad (device int32 [n] or None) marks cubics with a
+    coefficient that is not finite. solver 0: one thread per cubic; 1: one warp per cubic."""
+    if coef.dim() != 2 or coef.shape[1] != 4:
+        raise OfscError(ERR_INVALID_ARG, f"coef: shape {tuple(coef.shape)}, expected (n, 4)")
+    n = int(coef.shape[0])
+    _check(lib().ofsc_line_search_step(n, _arg(coef, "coef", "float64"), int(solver),
+                                       _arg(steps, "steps", "float64", numel=n),
+                                       None if bad is None else _arg(bad, "bad", "int32", numel=n), _stream(stream)))
 
 
 def ofsc_row_normalize(X, stream=None) -> None:

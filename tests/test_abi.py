@@ -68,6 +68,15 @@ def test_state_api_argument_checks(lib):
     assert lib.ofsc_state_load(None, None, 0, None) == ofsc.ERR_INVALID_ARG
 
 
+def test_line_search_step_argument_checks(lib):
+    """The batch line-search step rejects a negative count, a solver other than 0 or 1 and NULL
+    arrays on the host, and returns at once for n = 0 (no GPU needed)."""
+    assert lib.ofsc_line_search_step(-1, None, 0, None, None, None) == ofsc.ERR_INVALID_ARG
+    assert lib.ofsc_line_search_step(0, None, 2, None, None, None) == ofsc.ERR_INVALID_ARG
+    assert lib.ofsc_line_search_step(3, None, 1, None, None, None) == ofsc.ERR_INVALID_ARG
+    assert lib.ofsc_line_search_step(0, None, 1, None, None, None) == ofsc.OK
+
+
 def test_no_cpu_fallback_when_library_missing(monkeypatch, tmp_path):
     monkeypatch.setattr(ofsc, "_lib", None)
     monkeypatch.setattr(ofsc, "LIB_PATH", str(tmp_path / "missing.so"))

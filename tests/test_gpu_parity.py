@@ -1211,3 +1211,61 @@ def test_autotune_keeps_results_within_rounding():
     assert u2 in (2, 4, 6, 8)
     X2, _, _ = run_iterate(g2, o.OFM_F1, x2, 0.0, 5, gather=ofsc.GATHER_BF16)
     assert_elementwise(X2, o.iterate(og2, o.OFM_F1, x2, 0.0, 5).X, 2e-3)
+
+
+def cubic_cases(seed):
+    """Seeded cubics {c3, c2, c1, c0} with three well-separated real roots or one real root,
+    scales from 1e-6 to 1e6, whose antiderivative values at the roots differ by more than 1e-6
+    (so that the root choice is not a near-tie that rounding may flip), and the edge cases."""
+    rng = np.random.default_rng(seed)
+    out = []
+    while len(out) < 6000:
+        s = 10.0 ** rng.uniform(-6, 6) * rng.choice([-1.0, 1.0])
+        if len(out) % 2 == 0:
+            r = np.sort(rng.uniform(-10, 10, 3))
+            if np.min(np.diff(r)) < 0.1:
+                continue
+            c = (s, -s * r.sum(), s * (r[0] * r[1] + r[0] * r[2] + r[1] * r[2]), -s * r.prod())
+            qv = sorted(o.quartic_antiderivative(c, x) for x in r)
+            if qv[1] - qv[0] <= 1e-6 * max(1.0, abs(qv[0])):
+                continue
+        else:  # (a - r)(a^2 + b a + d) with b^2 < 4 d
+            r0, b = rng.uniform(-10, 10, 2)
+            d = b * b / 4.0 + rng.uniform(0.5, 20.0)
+            c = (s, s * (b - r0), s * (d - b * r0), -s * d * r0)
+        out.append(c)
+    edge = [(0.0, 1.0, -3.0, 2.0),    # quadratic, roots 1 and 2
+            (0.0, 0.0, 2.0, -1.0),    # linear
+            (0.0, 1.0, 0.0, 1.0),     # quadratic without a real root
+            (0.0, 0.0, 0.0, 0.0),     # zero
+            (1.0, 0.0, -3.0, 2.0),    # (a - 1)^2 (a + 2): a double root
+            (1.0, -6.0, 12.0, -8.0),  # (a - 2)^3
+            (2.0, 0.0, 0.0, 0.0)]     # 2 a^3
+    return np.array(out + edge, dtype=np.float64), len(edge)
+
+
+def test_line_search_step_matches_oracle():
+    """The exact line search's root choice (Sec. 3.2) on its own: the one-thread and the one-warp
+    device solvers give the same bits on every cubic, and match the oracle's Cardano roots and
+    choice within 1e-10 relative on well-separated roots, one-root cubics and the edge cases
+    (quadratic, linear, none, zero, double and triple roots); non-finite coefficients are flagged
+    and give 0."""
+    import torch
+    c, n_edge = cubic_cases(260)
+    bad_rows = np.array([[np.inf, 1.0, 1.0, 1.0], [1.0, np.nan, 0.0, 0.0]])
+    coef = torch.from_numpy(np.vstack([c, bad_rows])).cuda()
+    n = coef.shape[0]
+    steps = [torch.empty(n, dtype=torch.float64, device="cuda") for _ in range(2)]
+    bads = [torch.full((n,), -1, dtype=torch.int32, device="cuda") for _ in range(2)]
+    for solver in (0, 1):
+        ofsc.ofsc_line_search_step(coef, steps[solver], bads[solver], solver=solver)
+    s0, s1 = steps[0].cpu().numpy(), steps[1].cpu().numpy()
+    b0, b1 = bads[0].cpu().numpy(), bads[1].cpu().numpy()
+    assert np.array_equal(s0.view(np.int64), s1.view(np.int64)) and np.array_equal(b0, b1)
+    assert b0[-2:].tolist() == [1, 1] and s0[-2:].tolist() == [0.0, 0.0] and not b0[:-2].any()
+    ref = np.array([o.choose_root(tuple(row)) for row in c])
+    np.testing.assert_allclose(s0[:len(c)], ref, rtol=1e-10, atol=1e-12)
+    assert s0[len(c) - n_edge:len(c)].tolist() == pytest.approx([2.0, 0.5, 0.0, 0.0, -2.0, 2.0, 0.0])
+    with pytest.raises(ofsc.OfscError) as ei:
+        ofsc.ofsc_line_search_step(coef, steps[0], solver=2)
+    assert ei.value.status == ofsc.ERR_INVALID_ARG

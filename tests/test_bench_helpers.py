@@ -45,3 +45,30 @@ def test_source_digest_covers_the_kernel_sources():
 
 def test_max_over_ranks_single_rank():
     assert bench.max_over_ranks(3.25, 1) == 3.25
+
+
+def test_l2_flush_rule_and_config_note():
+    """The steps flush the L2 unless every N x kp block and the CSR are each more than twice its
+    size: the 2M-node graph keeps its inputs larger than L2, the smaller workloads flush, and the
+    config's note says which, for both arms."""
+    import argparse
+
+    def args(workload, nodes=None):
+        return argparse.Namespace(workload=workload, nodes=nodes, method="ofm_f1", gather="bf16", iters=30)
+
+    assert not bench.l2_flushed(args("dcsbm_n2m_k128"))
+    for wl in ("sbm_n1000_k11", "dcsbm_n50k_k44", "wsbm_n20k_k32"):
+        assert bench.l2_flushed(args(wl))
+        assert bench.workload_config(args(wl))["l2"].startswith("L2 flushed")
+    assert bench.l2_flushed(args("dcsbm_n2m_k128", nodes=100_000))
+    assert bench.workload_config(args("dcsbm_n2m_k128"))["l2"].startswith("inputs larger than L2")
+
+
+def test_whole_update_traffic_entry():
+    """profiles/traffic.json holds the measured DRAM bytes of one whole update (keyed to the digest
+    of every source, so bench.py reports them only for the build they were taken on), with its
+    per-kernel breakdown adding up to the total."""
+    e = bench.measured_traffic("dcsbm_n2m_k128/bf16", "update", any_build=True)
+    assert e is not None
+    assert sum(k["read"] for k in e["kernels"].values()) == e["dram_read_bytes"]
+    assert sum(k["write"] for k in e["kernels"].values()) == e["dram_write_bytes"]

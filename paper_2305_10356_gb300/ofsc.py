@@ -469,10 +469,11 @@ def ofsc_line_search_step(coef, steps, bad=None, solver: int = 1, stream=None) -
     """The exact line search's step (Sec. 3.2) of each cubic coef[i] = (c3, c2, c1, c0) (device
     FP64 [n, 4]) into steps (device FP64 [n]); bad (device int32 [n] or None) marks cubics with a
     coefficient that is not finite. solver 0: one thread per cubic; 1: one warp per cubic."""
+    pc = _arg(coef, "coef", "float64")
     if coef.dim() != 2 or coef.shape[1] != 4:
         raise OfscError(ERR_INVALID_ARG, f"coef: shape {tuple(coef.shape)}, expected (n, 4)")
     n = int(coef.shape[0])
-    _check(lib().ofsc_line_search_step(n, _arg(coef, "coef", "float64"), int(solver),
+    _check(lib().ofsc_line_search_step(n, pc, int(solver),
                                        _arg(steps, "steps", "float64", numel=n),
                                        None if bad is None else _arg(bad, "bad", "int32", numel=n), _stream(stream)))
 

@@ -31,3 +31,7 @@ def test_dtype_layout_and_device_are_checked_before_the_call():
     s32 = src.int()
     _raises(lambda: ofsc.ofsc_graph_build(4, s32, s32), "CUDA")
     _raises(lambda: ofsc.ofsc_gram(x, [x], torch.zeros((1, 8, 8), dtype=torch.float32)), "CUDA")
+    c = torch.zeros((5, 4), dtype=torch.float64)
+    _raises(lambda: ofsc.ofsc_line_search_step(c.float(), torch.zeros(5, dtype=torch.float64)), "dtype")
+    _raises(lambda: ofsc.ofsc_line_search_step(c, torch.zeros(5, dtype=torch.float64)), "CUDA")
+    _raises(lambda: ofsc.ofsc_line_search_step(c.numpy(), None), "torch tensor")
